@@ -1,0 +1,71 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This module holds only workload descriptions (mesh sizes, partitions, physical
+parameters from Table 1 of the paper) and the seeded random draws.  It holds
+none of the method's arithmetic: no assembly, no ionic model, no solver.  Both
+the CPU oracle and the CUDA path receive the arrays it produces as inputs.
+
+Workloads (all Q1 hexahedral slabs, h = element size):
+
+* ``tiny``     2x2x2 elements, one element per subdomain: edge cases.
+* ``ragged``   10x9x7 elements, 4^3-element blocks with ragged last blocks.
+* ``cube8``    8x8x8 elements of a 0.4 cm cube, 2x2x2 subdomains, H/h = 4,
+               vertex primal space (1,458 unknowns).
+* ``slab32``   32x32x16 elements of a 1.6x1.6x0.8 cm slab, 4x4x2 subdomains,
+               H/h = 8, vertex + edge-average primal space (37,026 unknowns).
+* ``opt<k>``   (4k)^3 elements of a 0.8 cm cube, 4x4x4 subdomains, H/h = k.
+* ``slab128``  128x128x32 elements of a 3.2x3.2x0.8 cm slab, 16x16x4
+               subdomains, H/h = 8 (1,098,306 unknowns).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# Table 1: conductivities (S/cm) along fibre, cross-fibre, sheet normal.
+SIGMA_I = (3.0e-3, 3.1525e-4, 3.1525e-5)
+SIGMA_E = (2.0e-3, 1.3514e-3, 6.757e-4)
+# Table 1: Rogers-McCulloch parameters; chi*Cm in mF/cm^3 (Fig. 1 caption).
+IONIC = dict(G=1.2, eta1=4.4, eta2=0.012, vth=13.0, vp=100.0, chi_cm=1.0, v_rest=-85.0)
+TAU = 0.05  # ms
+# Section 6: 100 mA/cm^3 for 1 ms in a slab corner (here a 0.1 cm corner cube).
+STIMULUS = dict(amp=100.0, t_on=0.0, t_off=1.0, box=(0.0, 0.1, 0.0, 0.1, 0.0, 0.1))
+
+WORKLOADS = {
+    "tiny": dict(n=(2, 2, 2), l=(0.1, 0.1, 0.1), s=(1, 1, 1), primal="V", steps=1),
+    "ragged": dict(n=(10, 9, 7), l=(0.5, 0.45, 0.35), s=(4, 4, 4), primal="VE", steps=2),
+    "cube8": dict(n=(8, 8, 8), l=(0.4, 0.4, 0.4), s=(4, 4, 4), primal="V", steps=1),
+    "cube8ve": dict(n=(8, 8, 8), l=(0.4, 0.4, 0.4), s=(4, 4, 4), primal="VE", steps=1),
+    "slab32": dict(n=(32, 32, 16), l=(1.6, 1.6, 0.8), s=(8, 8, 8), primal="VE", steps=20),
+    "slab128": dict(n=(128, 128, 32), l=(3.2, 3.2, 0.8), s=(8, 8, 8), primal="VE", steps=400),
+}
+for _k in (4, 8, 12, 16, 20):
+    WORKLOADS[f"opt{_k}"] = dict(n=(4 * _k,) * 3, l=(0.8, 0.8, 0.8), s=(_k,) * 3,
+                                 primal="VE", steps=40)
+
+
+def workload(name: str) -> dict:
+    """Return a copy of a named workload description."""
+    w = dict(WORKLOADS[name])
+    w["name"] = name
+    return w
+
+
+def n_nodes(w: dict) -> int:
+    nx, ny, nz = w["n"]
+    return (nx + 1) * (ny + 1) * (nz + 1)
+
+
+def initial_state(n: int, seed: int = 0, sigma_mv: float = 1.0):
+    """Resting state plus seeded noise: V0 ~ N(0, sigma) mV, u_e = 0, w = 0.
+
+    Returns (u_i, u_e, w) as float64 arrays of length n, with u_i = V0 so that
+    the transmembrane potential u_i - u_e equals V0.
+    """
+    rng = np.random.default_rng(seed)
+    v0 = rng.normal(0.0, sigma_mv, size=n)
+    return v0.astype(np.float64), np.zeros(n), np.zeros(n)
+
+
+def random_vector(n: int, seed: int) -> np.ndarray:
+    """A seeded N(0,1) float64 vector (right-hand sides for operator tests)."""
+    return np.random.default_rng(seed).standard_normal(n)

@@ -1,0 +1,120 @@
+"""Pins for the oracle's BDDC / FETI-DP deluxe solvers and Krylov methods (Sections 4-5)."""
+import numpy as np
+import pytest
+
+import synth
+from conftest import oracle_problem
+from oracle import ionic
+from oracle.bidomain import direct_solve
+from oracle.dd import DDSolver
+from oracle.krylov import gmres, lanczos_cond, pcg
+
+
+def _jacobian_system(prob, seed=0):
+    ui, ue, w = synth.initial_state(prob.N, seed)
+    ui = ui + 30.0 * np.exp(-np.sum(prob.mesh.coords ** 2, axis=1) / 0.01)
+    w1 = ionic.gating_step(ui - ue, w, prob.tau, prob.p)
+    r_i, r_e = prob.residual(ui, ue, w1, ui - 1.0, ue, prob.tau)
+    kc = prob.kc(ui, ue, w1)
+    return kc, -r_i, -r_e
+
+
+@pytest.mark.parametrize("name", ["tiny", "cube8", "cube8ve", "ragged"])
+@pytest.mark.parametrize("method", ["bddc", "fetidp"])
+@pytest.mark.parametrize("krylov", ["pcg", "gmres"])
+def test_dd_matches_direct(name, method, krylov):
+    prob = oracle_problem(name)
+    kc, f_i, f_e = _jacobian_system(prob)
+    si, se, _ = direct_solve(prob, kc, f_i, f_e)
+    dd = DDSolver(prob, method=method, krylov=krylov, rtol=1e-13, atol=0.0)
+    ai, ae, info = dd.solve(kc / prob.fem.M, f_i, f_e)
+    assert info["reason"] == "converged"
+    err = np.linalg.norm(np.r_[ai - si, ae - se]) / np.linalg.norm(np.r_[si, se])
+    assert err < 1e-10
+
+
+def _local_dual_vectors(dd, seed):
+    rng = np.random.default_rng(seed)
+    return [rng.standard_normal(len(L["dual"])) for L in dd.loc]
+
+
+@pytest.mark.parametrize("name", ["cube8", "cube8ve", "ragged"])
+def test_deluxe_projection_and_pd(name):
+    prob = oracle_problem(name)
+    kc, _, _ = _jacobian_system(prob)
+    dd = DDSolver(prob)
+    dd.setup(kc / prob.fem.M)
+    w = _local_dual_vectors(dd, 5)
+    e1 = dd.e_d(w)
+    e2 = dd.e_d(e1)
+    for a, b in zip(e1, e2):
+        np.testing.assert_allclose(a, b, rtol=1e-9, atol=1e-12)
+    # B_D^T B = P_D = I - E_D (eq. PdDeluxe) for fully redundant multipliers
+    lay, nlam = dd._lambda_layout()
+    pd = dd.bd_t(dd.b(w, lay, nlam), lay)
+    for a, x, e in zip(pd, w, e1):
+        np.testing.assert_allclose(a, x - e, rtol=1e-9, atol=1e-12)
+
+
+def _dense(apply, n, keep):
+    A = np.zeros((n, n))
+    for k in np.nonzero(keep)[0]:
+        e = np.zeros(n)
+        e[k] = 1.0
+        A[:, k] = apply(e)
+    return A[np.ix_(keep, keep)]
+
+
+@pytest.mark.parametrize("name", ["cube8", "cube8ve"])
+def test_bddc_fetidp_spectra(name):
+    """BDDC eigenvalues are >= 1; FETI-DP has the same ones apart from 0 and 1."""
+    prob = oracle_problem(name)
+    kc, _, _ = _jacobian_system(prob)
+    dd = DDSolver(prob)
+    dd.setup(kc / prob.fem.M)
+    n = prob.dofs.n_iface
+    keep = np.ones(n, bool)
+    keep[dd.g_iface] = False
+    S = _dense(dd.schur_apply, n, keep)
+    Minv = _dense(dd.bddc_apply, n, keep)
+    ev_b = np.sort(np.linalg.eigvals(Minv @ S).real)
+    assert ev_b[0] > 1.0 - 1e-8
+    F, Mf, lay, nlam = dd.fetidp_operators()
+    allk = np.ones(nlam, bool)
+    Fm = _dense(F, nlam, allk)
+    Mm = _dense(Mf, nlam, allk)
+    ev_f = np.sort(np.linalg.eigvals(Mm @ Fm).real)
+    big_b = ev_b[ev_b > 1.0 + 1e-6]
+    big_f = ev_f[ev_f > 1.0 + 1e-6]
+    assert len(big_b) == len(big_f)
+    np.testing.assert_allclose(big_b, big_f, rtol=1e-7)
+
+
+def test_primal_space_ordering_of_cond():
+    """A richer primal space gives a smaller condition number (Table 7, V vs V+E)."""
+    conds = {}
+    for prim in ("V", "VE"):
+        prob = oracle_problem("cube8", prim)
+        kc, f_i, f_e = _jacobian_system(prob)
+        dd = DDSolver(prob, rtol=1e-10, atol=0.0)
+        _, _, info = dd.solve(kc / prob.fem.M, f_i, f_e)
+        conds[prim] = info["cond"]
+    assert 1.0 <= conds["VE"] < conds["V"]
+
+
+def test_pcg_gmres_lanczos_small_spd():
+    rng = np.random.default_rng(2)
+    n = 12
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    ev = np.linspace(1.0, 40.0, n)
+    A = Q @ np.diag(ev) @ Q.T
+    b = rng.standard_normal(n)
+    x, info = pcg(lambda v: A @ v, lambda v: v, b, rtol=1e-14, atol=0.0, maxit=50)
+    np.testing.assert_allclose(x, np.linalg.solve(A, b), rtol=1e-9)
+    assert info["its"] <= n + 2
+    # after n steps the Lanczos matrix holds the whole spectrum
+    _, info_n = pcg(lambda v: A @ v, lambda v: v, b, rtol=0.0, atol=0.0, maxit=n)
+    assert abs(lanczos_cond(info_n["alphas"][:n], info_n["betas"][:n - 1]) - 40.0) < 1e-6
+    N = rng.standard_normal((n, n)) + 5 * np.eye(n)
+    x, info = gmres(lambda v: N @ v, lambda v: v, b, rtol=1e-13, atol=0.0, restart=5, maxit=200)
+    np.testing.assert_allclose(x, np.linalg.solve(N, b), rtol=1e-8)
