@@ -1,0 +1,240 @@
+/*
+ * bidomain.h -- C-ABI of the GB300 Newton-Krylov BDDC / FETI-DP deluxe
+ * solver for the segregated implicit Bidomain time step.
+ *
+ * Method: Huynh, Pavarino, Scacchi, "Parallel Newton-Krylov BDDC and FETI-DP
+ * deluxe solvers for implicit time discretizations of the cardiac Bidomain
+ * equations" (arXiv 2101.02959).  Each entry point cites the section and
+ * equation that defines the operation it performs.
+ *
+ * Conventions shared by every call:
+ *   - Every function returns an int status: BD_OK (0) or a negative BD_ERR_*.
+ *     No exception crosses this boundary and no device trap is used; device
+ *     failures (a non-positive pivot, a NaN, an exhausted wait) are recorded
+ *     in a device flag and reported by the next call that synchronises.
+ *   - Nodal vectors have length n_node (node ids lexicographic over the used
+ *     grid nodes, x fastest) and are float64.  Two-field vectors (u_i, u_e or
+ *     residual / correction pairs) are SoA: the u_i block then the u_e block,
+ *     2*n_node doubles.
+ *   - Interface vectors (length n_iface) hold two dofs per interface node in
+ *     increasing node id, u_i then u_e.  Lagrange-multiplier vectors have
+ *     length n_lambda.
+ *   - on_device = 1: the pointers are CUDA device pointers; on_device = 0:
+ *     host pointers (the library copies them through its own device buffers,
+ *     inside the call).  The caller owns every pointer it passes; none is
+ *     retained after the call returns.
+ *   - All device work is enqueued on the stream given to bidomain_setup;
+ *     calls that return data to the host or report statistics synchronise it.
+ *   - A handle is not thread-safe; use one handle per host thread.
+ */
+#ifndef BIDOMAIN_H
+#define BIDOMAIN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define BD_OK 0
+#define BD_ERR_ARG (-1)              /* invalid argument or unsupported option */
+#define BD_ERR_NOT_SPD (-2)          /* a Cholesky pivot was <= 0 (e.g. tau > 0.37 ms) */
+#define BD_ERR_KRYLOV_MAXIT (-3)     /* Krylov stopped at ksp_max_it */
+#define BD_ERR_KRYLOV_DIVERGED (-4)  /* ||M^-1 r|| > dtol ||M^-1 b|| */
+#define BD_ERR_NEWTON (-5)           /* Newton or its line search failed */
+#define BD_ERR_NAN (-6)              /* NaN / Inf met in a residual or a norm */
+#define BD_ERR_TIMEOUT (-7)          /* a device-side wait exhausted its budget */
+#define BD_ERR_CUDA (-8)             /* a CUDA runtime call failed */
+#define BD_ERR_NOMEM (-9)            /* device allocation failed */
+#define BD_ERR_STATE (-10)           /* call made in the wrong order (e.g. no Jacobian yet) */
+
+/* ---- option values ----------------------------------------------------- */
+#define BD_BDDC 0
+#define BD_FETIDP 1
+#define BD_PCG 0
+#define BD_GMRES 1
+#define BD_PRIMAL_V 0   /* vertex values (Section 6, Test 3 "V") */
+#define BD_PRIMAL_VE 1  /* vertex values and edge averages ("V+E") */
+#define BD_FP64 0       /* every step in float64 */
+#define BD_MIXED 1      /* local factors, Schur and deluxe blocks in float32;
+                           Newton, Krylov vectors, dots and coarse in float64 */
+
+/* index arrays for bd_plan_index_sets / bidomain_index_sets */
+#define BD_IDX_ELEM_SUB 0      /* subdomain of each element (n_elem) */
+#define BD_IDX_NODE_MULT 1     /* |N_x| of each node (n_node) */
+#define BD_IDX_IFACE_NODES 2   /* interface nodes, sorted */
+#define BD_IDX_CLS_TYPE 3      /* 0 vertex, 1 edge, 2 face, per class */
+#define BD_IDX_CLS_PTR 4       /* CSR pointer of class nodes (n_cls + 1) */
+#define BD_IDX_CLS_NODES 5     /* class nodes, sorted inside each class */
+#define BD_IDX_CLS_SUB_PTR 6   /* CSR pointer of N_C (n_cls + 1) */
+#define BD_IDX_CLS_SUBS 7      /* subdomains sharing each class */
+#define BD_IDX_CLS_DUAL_START 8 /* first global dual dof of each class */
+#define BD_IDX_SUB_NODE_PTR 9  /* CSR pointer of local nodes (n_sub + 1) */
+#define BD_IDX_SUB_NODES 10    /* local nodes: interior then interface, each sorted */
+#define BD_IDX_SUB_NINT 11     /* number of interior nodes per subdomain */
+#define BD_IDX_SUB_DUAL_PTR 12 /* CSR pointer of local dual dofs */
+#define BD_IDX_SUB_DUAL 13     /* global transformed dual dof of each local dual dof */
+#define BD_IDX_SUB_PRIMAL_PTR 14
+#define BD_IDX_SUB_PRIMAL 15   /* global primal dof of each local primal dof */
+#define BD_IDX_GAUGE 16        /* {gauge node, gauge primal dof} */
+
+typedef struct bd_plan bd_plan;
+typedef struct bd_handle bd_handle;
+
+/* Box grid of n[0] x n[1] x n[2] Q1 hexahedra over [0,l0]x[0,l1]x[0,l2] cm,
+ * split into box blocks of s[0] x s[1] x s[2] elements (Section 4.1).
+ * elem_mask (host, nullable): one byte per grid element, x fastest, 1 = keep;
+ * each block is split into node-connected components. */
+typedef struct {
+  int n[3];
+  double l[3];
+  int s[3];
+  const unsigned char *elem_mask;
+} bd_mesh;
+
+/* Conductivity coefficients (S/cm) along fibre, cross-fibre and sheet normal
+ * (Section 2, Table 1).  Slab fibres rotate by 120 degrees through the depth,
+ * counter-clockwise from the epicardium (z = l2) to the endocardium (z = 0). */
+typedef struct {
+  double sigma_i[3];
+  double sigma_e[3];
+} bd_conductivity;
+
+/* Rogers-McCulloch parameters (Section 2, Table 1); chi_cm = chi * Cm in
+ * mF/cm^3; potentials in mV measured from rest. */
+typedef struct {
+  double G, eta1, eta2, vth, vp, chi_cm;
+} bd_ionic;
+
+/* Transmembrane stimulus of amplitude amp (mA/cm^3) on the nodes inside the
+ * box {x0,x1,y0,y1,z0,z1} (cm), active for t_on <= t_{n+1} < t_off (ms). */
+typedef struct {
+  double amp, t_on, t_off;
+  double box[6];
+} bd_stimulus;
+
+/* Solver options; defaults (bd_options_default) are the tolerances of the
+ * paper's Section 6 table: KSP rtol 1e-8, atol 1e-10, dtol 1e4; SNES rtol
+ * 1e-4, atol 1e-8, stol 1e-8; BDDC, PCG, V+E, FP64. */
+typedef struct {
+  int method;        /* BD_BDDC | BD_FETIDP */
+  int krylov;        /* BD_PCG | BD_GMRES */
+  int primal;        /* BD_PRIMAL_V | BD_PRIMAL_VE */
+  int precision;     /* BD_FP64 | BD_MIXED */
+  int gmres_restart; /* GMRES restart length (default 30) */
+  int ksp_max_it;    /* default 1000 */
+  int newton_max_it; /* default 50 */
+  int use_graphs;    /* 1: replay the Krylov iteration as a captured CUDA graph */
+  double ksp_rtol, ksp_atol, ksp_dtol;
+  double snes_rtol, snes_atol, snes_stol;
+} bd_options;
+
+typedef struct {
+  int its;        /* Krylov iterations */
+  int reason;     /* BD_OK or BD_ERR_KRYLOV_* */
+  double res0;    /* ||M^-1 b|| */
+  double res;     /* final ||M^-1 r|| */
+  double cond;    /* Lanczos estimate of cond(M^-1 A) (PCG only, else 0) */
+} bd_solve_stats;
+
+typedef struct {
+  int newton_its;   /* Newton iterations of this step */
+  int krylov_its;   /* Krylov iterations summed over them */
+  int reason;       /* BD_OK or the failure code */
+  int pad;
+  double res0;      /* ||F(u^n) - G|| */
+  double res_final; /* ||F(u^{n+1}) - G|| */
+  double cond_max;  /* largest Lanczos estimate met in the step */
+} bd_step_stats;
+
+typedef struct {
+  int n_node, n_elem, n_sub, n_cls;
+  int n_iface, n_dual, n_primal, n_lambda;
+  int gauge_node, gauge_primal;
+} bd_sizes;
+
+/* ---- host-only plan (no GPU) ------------------------------------------- */
+
+/* Section 4.1: grid, subdomains, N_x, face/edge/vertex classes, primal set
+ * (primal = BD_PRIMAL_V or BD_PRIMAL_VE) and dof maps, built on the host.
+ * Fails with BD_ERR_ARG when a subdomain has no primal constraint or the
+ * partition has no vertex (no gauge). */
+int bd_plan_create(const bd_mesh *mesh, int primal, bd_plan **out);
+int bd_plan_sizes(const bd_plan *plan, bd_sizes *out);
+/* Copies index array `which` (BD_IDX_*) into out[0..cap); *len receives its
+ * length.  Returns BD_ERR_ARG if cap < *len (nothing copied past cap). */
+int bd_plan_index_sets(const bd_plan *plan, int which, int64_t *out, int64_t cap, int64_t *len);
+void bd_plan_destroy(bd_plan *plan);
+
+/* ---- solver handle ------------------------------------------------------ */
+
+int bd_options_default(bd_options *opt);
+
+/* Builds the plan, assembles the Q1 stiffness A_i, A_e and lumped mass M
+ * (Section 3a), the subassembled local stencils of every subdomain (local
+ * forms a^(j), Section 4.1) and allocates every device buffer.  stream: a
+ * cudaStream_t (NULL = the library creates its own).  tau in ms. */
+int bidomain_setup(const bd_mesh *mesh, const bd_conductivity *cond, const bd_ionic *ionic,
+                   double tau, const bd_options *opt, void *stream, bd_handle **out);
+int bidomain_sizes(const bd_handle *h, bd_sizes *out);
+int bidomain_index_sets(const bd_handle *h, int which, int64_t *out, int64_t cap, int64_t *len);
+
+/* State (u_i, u_e, w) at time t (ms); t sets the step counter n = round(t/tau). */
+int bidomain_set_state(bd_handle *h, const double *ui, const double *ue, const double *w,
+                       double t, int on_device);
+int bidomain_get_state(bd_handle *h, double *ui, double *ue, double *w, double *t, int on_device);
+
+/* One decoupled backward-Euler step (Section 3b): Step 1 gating update, then
+ * Newton (Section 3c) on F(u) = G with the configured Krylov method and
+ * preconditioner, then the gauge shift that gives u_e zero lumped-mass mean.
+ * stats may be NULL.  Advances t by tau. */
+int bidomain_step(bd_handle *h, const bd_stimulus *stim, bd_step_stats *stats);
+
+/* Step 1 alone (Section 3b): w_next = (w + tau eta2 v / v_p) / (1 + tau eta2),
+ * v = ui - ue.  Nodal vectors. */
+int bidomain_gating(bd_handle *h, const double *ui, const double *ue, const double *w,
+                    double *w_next, int on_device);
+
+/* F(u) - G of Step 2 (Section 3b) at u = (ui, ue) with w_next, previous
+ * potentials (ui_n, ue_n) and the stimulus evaluated at t_next.
+ * r: 2*n_node (SoA). */
+int bidomain_residual(bd_handle *h, const bd_stimulus *stim, double t_next, const double *ui,
+                      const double *ue, const double *w_next, const double *ui_n,
+                      const double *ue_n, double *r, int on_device);
+
+/* Jacobian of Section 3c at (ui, ue, w_next): updates the local matrices,
+ * factorises them, forms the local Schur complements, deluxe blocks and the
+ * coarse problem (Sections 4.1-4.4).  Required before the three calls below
+ * and before krylov_solve. */
+int bidomain_linearize(bd_handle *h, const double *ui, const double *ue, const double *w_next,
+                       int on_device);
+
+/* S_hat x = sum_j R_j^T S_Gamma^(j) R_j x (Section 4.1, eq. schursys);
+ * interface vectors; the gauge entry of y is 0. */
+int schur_apply(bd_handle *h, const double *x, double *y, int on_device);
+
+/* z = M^-1_BDDC r = Rt_D^T St^-1 Rt_D r (Section 4.4) with deluxe scaling
+ * (Section 4.2); interface vectors. */
+int bddc_apply(bd_handle *h, const double *r, double *z, int on_device);
+
+/* mu = M^-1_FETI-DP lambda = B_D St B_D^T lambda (Section 4.3); multiplier
+ * vectors (fully redundant multipliers u_j - u_m, j < m, per dual dof). */
+int fetidp_apply(bd_handle *h, const double *lambda, double *mu, int on_device);
+
+/* y = F lambda = B St^-1 B^T lambda (Section 4.3, eq. lagrangesystem). */
+int fetidp_operator(bd_handle *h, const double *lambda, double *y, int on_device);
+
+/* Solves the Jacobian system J s = f (Section 3c, eq. Jacobiansystem) by the
+ * configured Krylov method on the interface system (BDDC) or the multiplier
+ * system (FETI-DP), then recovers the interior (Section 4.1).  f, s: 2*n_node
+ * (SoA).  The u_e correction at the gauge node is 0.  stats may be NULL. */
+int krylov_solve(bd_handle *h, const double *f, double *s, int on_device, bd_solve_stats *stats);
+
+int bidomain_destroy(bd_handle *h);
+const char *bidomain_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BIDOMAIN_H */

@@ -1,0 +1,1217 @@
+// Host orchestration and the C-ABI (include/bidomain.h).
+//
+// Per Newton step (Section 3c) the Jacobian is rebuilt from its only varying
+// part, the diagonal coupling Kc = M (chi Cm + tau dI/dv); every local
+// matrix is factorised and condensed on the GPU (Sections 4.1-4.4) and the
+// interface (BDDC) or multiplier (FETI-DP) system is solved by a device-side
+// Krylov loop whose scalars never leave the GPU until convergence is tested.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "bidomain.h"
+#include "dd_kernels.cuh"
+#include "plan.h"
+
+using namespace bd;
+
+namespace {
+
+struct Status : std::runtime_error {
+  int code;
+  Status(int c, const std::string &m) : std::runtime_error(m), code(c) {}
+};
+
+void ck(cudaError_t e, const char *what) {
+  if (e == cudaErrorMemoryAllocation) throw Status(BD_ERR_NOMEM, what);
+  if (e != cudaSuccess) throw Status(BD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+struct DevMem {
+  std::vector<void *> ptrs;
+  template <class X>
+  X *alloc(size_t n) {
+    void *p = nullptr;
+    ck(cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(X)), "cudaMalloc");
+    ptrs.push_back(p);
+    return static_cast<X *>(p);
+  }
+  template <class X>
+  X *upload(const std::vector<X> &v, cudaStream_t s) {
+    X *p = alloc<X>(v.size());
+    if (!v.empty()) ck(cudaMemcpyAsync(p, v.data(), v.size() * sizeof(X), cudaMemcpyHostToDevice, s), "upload");
+    return p;
+  }
+  ~DevMem() {
+    for (void *p : ptrs) cudaFree(p);
+  }
+};
+
+inline int pad8(int n) { return (n + 7) & ~7; }
+inline long long pad32(long long n) { return (n + 31) & ~31LL; }
+
+template <class T>
+struct Dense {
+  T *K = nullptr, *Aug = nullptr, *Sorig = nullptr, *Z = nullptr, *SDD = nullptr, *Blk = nullptr, *CA = nullptr,
+    *Sinv = nullptr;
+};
+
+struct GemvSet {
+  GemvDesc *d = nullptr;
+  int n = 0, max_rows = 0, max_cols = 0;
+};
+struct CopySet {
+  CopyTask *d = nullptr;
+  int n = 0;
+  long long max_elems = 0;
+};
+
+// Extreme eigenvalues of the symmetric tridiagonal matrix (d, e) by Sturm bisection.
+double tridiag_cond(const std::vector<double> &d, const std::vector<double> &e) {
+  const int k = (int)d.size();
+  if (k == 0) return 1.0;
+  double lo = d[0], hi = d[0];
+  for (int i = 0; i < k; ++i) {
+    const double r = (i > 0 ? std::fabs(e[i - 1]) : 0.0) + (i + 1 < k ? std::fabs(e[i]) : 0.0);
+    lo = std::min(lo, d[i] - r);
+    hi = std::max(hi, d[i] + r);
+  }
+  auto count_below = [&](double x) {
+    int c = 0;
+    double q = d[0] - x;
+    if (q < 0) ++c;
+    for (int i = 1; i < k; ++i) {
+      if (q == 0.0) q = 1e-300;
+      q = d[i] - x - e[i - 1] * e[i - 1] / q;
+      if (q < 0) ++c;
+    }
+    return c;
+  };
+  auto kth = [&](int idx) {  // idx-th smallest eigenvalue, 0-based
+    double a = lo, b = hi;
+    for (int it = 0; it < 200; ++it) {
+      const double m = 0.5 * (a + b);
+      if (count_below(m) > idx) b = m;
+      else a = m;
+      if (b - a <= 1e-15 * std::max(std::fabs(a), std::fabs(b))) break;
+    }
+    return 0.5 * (a + b);
+  };
+  const double lmin = kth(0), lmax = kth(k - 1);
+  return lmax / lmin;
+}
+
+}  // namespace
+
+struct bd_plan {
+  Plan p;
+};
+
+struct bd_handle {
+  Plan plan;
+  bd_options opt;
+  FemParams fp;
+  double tau = 0.0;
+  cudaStream_t s = nullptr;
+  bool own_stream = false;
+  long step_n = 0;
+  DevMem mem;
+  int N = 0, NE = 0, nsub = 0, nif = 0, nd = 0, np = 0, nlam = 0;
+  int gauge_iface = -1, gauge_primal = -1;
+  double sum_mass = 0.0;
+  // global FEM data
+  int *d_node_ijk, *d_elem_ijk, *d_elem_grid, *d_elem_sub, *d_nbr;
+  double *d_mass, *d_Ke, *d_stencil;
+  // state and Newton work vectors
+  double *d_ui, *d_ue, *d_w, *d_uin, *d_uen, *d_wn, *d_factor, *d_ri, *d_re, *d_si, *d_se, *d_fi, *d_fe;
+  double *d_uit, *d_uet, *d_rit, *d_ret, *d_factort;
+  double *d_partial, *d_scal;
+  int *d_err;
+  double *d_io[6];
+  // local node tables
+  int nq = 0;
+  int *d_q_sub, *d_q_loc, *d_q_node, *d_q_nbr;
+  double *d_q_mass, *d_q_stencil;
+  // interior / interface / dual / primal layouts
+  int nI_tot = 0, nG_tot = 0, nD_tot = 0, nP_tot = 0, nint_nodes = 0;
+  std::vector<int> nI, nG, nD, nP, int_off, giff_off, ldual_off, lprim_off;
+  int *d_int_node, *d_iface_node, *d_R, *d_Rt_ptr, *d_Rt_idx, *d_vec_off_I;
+  int *d_ldual_off, *d_lprim_off, *d_nD, *d_nI, *d_prim_x, *d_pl_ptr, *d_pl_idx, *d_giff_off;
+  double *d_mult_iface;
+  int *d_T_ptr, *d_T_col, *d_Tt_ptr, *d_Tt_col;
+  double *d_T_val, *d_Tt_val;
+  int nt_tot = 0;
+  int *d_tl_sub, *d_tl_loc, *d_tl_ptr, *d_tl_row, *d_tl_off;
+  double *d_tl_val;
+  // dense layouts
+  EngineShape shK, shA, shC, shCo;
+  MatDesc *d_Kdesc, *d_Adesc, *d_Cdesc, *d_Codesc;
+  long long K_el = 0, A_el = 0, So_el = 0, Z_el = 0, SDD_el = 0, Blk_el = 0, CA_el = 0, Sinv_el = 0;
+  int ld_co = 0;
+  GemvSet gv_schur, gv_local, gv_psit, gv_coarse, gv_sdd, gv_lgi, gv_lgit;
+  CopySet cp_sorig, cp_sdd, cp_blk, cp_zx, cp_sinv, cp_coinv;
+  int ncls = 0, npairs = 0, nlt = 0, nwt = 0, max_nc = 0;
+  ClassTask *d_cls;
+  PairTask *d_pairs;
+  LamTask *d_lt;
+  WTask *d_wt;
+  WEnt *d_went;
+  int *d_co_ptr;
+  long long *d_co_src;
+  // work vectors
+  double *d_fI, *d_yI, *d_fG, *d_fhat, *d_uG, *d_yloc, *d_rbar, *d_zbar, *d_rD, *d_ydc, *d_w1, *d_w2, *d_gP,
+      *d_crhs, *d_rP, *d_rD2;
+  double *d_kx, *d_kr, *d_kz, *d_kp, *d_kq, *d_kb;
+  KrylovState *d_ks;
+  double *d_ha, *d_hb;
+  int hist_cap = 0;
+  Dense<float> df;
+  Dense<double> dd;
+  double *d_Co, *d_CoInv;
+  bool linearized = false;
+  std::string last_error;
+
+  bool mixed() const { return opt.precision == BD_MIXED; }
+  int check_err() {
+    int e = 0;
+    ck(cudaMemcpyAsync(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost, s), "read error flag");
+    ck(cudaStreamSynchronize(s), "sync");
+    if (e) ck(cudaMemsetAsync(d_err, 0, sizeof(int), s), "clear error flag");
+    if (e & DEV_ERR_NOT_SPD) return BD_ERR_NOT_SPD;
+    if (e & DEV_ERR_NAN) return BD_ERR_NAN;
+    if (e & DEV_ERR_TIMEOUT) return BD_ERR_TIMEOUT;
+    return BD_OK;
+  }
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// setup
+// ---------------------------------------------------------------------------
+void setup_handle(bd_handle &h) {
+  Plan &p = h.plan;
+  cudaStream_t s = h.s;
+  DevMem &m = h.mem;
+  h.N = p.n_node;
+  h.NE = p.n_elem;
+  h.nsub = p.n_sub;
+  h.nif = p.n_iface();
+  h.nd = p.n_dual;
+  h.np = p.n_primal;
+  h.gauge_iface = 2 * p.node_to_iface[p.gauge_node] + 1;
+  h.gauge_primal = p.gauge_primal;
+  const int N = h.N;
+  // ---- global FEM tables
+  h.d_node_ijk = m.upload(p.node_ijk, s);
+  h.d_elem_ijk = m.upload(p.elem_ijk, s);
+  h.d_elem_grid = m.upload(p.elem_grid, s);
+  h.d_elem_sub = m.upload(p.elem_sub, s);
+  std::vector<int> nbr_soa(27L * N);
+  for (int x = 0; x < N; ++x)
+    for (int sl = 0; sl < 27; ++sl) nbr_soa[(long)sl * N + x] = p.nbr27[27L * x + sl];
+  h.d_nbr = m.upload(nbr_soa, s);
+  std::vector<double> mass(N, 0.0);
+  const double vol8 = p.h[0] * p.h[1] * p.h[2] / 8.0;
+  for (int e = 0; e < h.NE; ++e)
+    for (int a = 0; a < 8; ++a) mass[p.conn[8 * e + a]] += vol8;
+  h.sum_mass = 0.0;
+  for (double v : mass) h.sum_mass += v;
+  h.d_mass = m.upload(mass, s);
+  h.d_Ke = m.alloc<double>(128L * h.NE);
+  launch_element_matrices(h.NE, h.d_elem_ijk, p.h, p.l[2], h.fp, h.d_Ke, s);
+  h.d_stencil = m.alloc<double>(54L * N);
+  std::vector<int> all_nodes(N);
+  for (int x = 0; x < N; ++x) all_nodes[x] = x;
+  int *d_all = m.upload(all_nodes, s);
+  launch_stencil_gather(N, d_all, nullptr, h.d_node_ijk, h.d_elem_grid, h.d_elem_sub, p.n, h.d_Ke, h.d_stencil, N, s);
+  // ---- state vectors
+  double **vecs[] = {&h.d_ui, &h.d_ue, &h.d_w, &h.d_uin, &h.d_uen, &h.d_wn, &h.d_factor, &h.d_ri, &h.d_re, &h.d_si,
+                     &h.d_se, &h.d_fi, &h.d_fe, &h.d_uit, &h.d_uet, &h.d_rit, &h.d_ret, &h.d_factort};
+  for (double **v : vecs) {
+    *v = m.alloc<double>(N);
+    ck(cudaMemsetAsync(*v, 0, sizeof(double) * N, s), "memset");
+  }
+  h.d_partial = m.alloc<double>(3 * kRedBlocks);
+  h.d_scal = m.alloc<double>(64);
+  h.d_err = m.alloc<int>(1);
+  ck(cudaMemsetAsync(h.d_err, 0, sizeof(int), s), "memset");
+  // ---- local node tables and layouts
+  const int S = h.nsub;
+  h.nI.resize(S); h.nG.resize(S); h.nD.resize(S); h.nP.resize(S);
+  h.int_off.resize(S); h.giff_off.resize(S); h.ldual_off.resize(S); h.lprim_off.resize(S);
+  std::vector<int> q_sub, q_loc, q_node, q_nbr, int_node, R, prim_x, vec_off_I(S);
+  std::vector<double> q_mass;
+  for (int j = 0; j < S; ++j) {
+    const SubPlan &sp = p.subs[j];
+    h.nI[j] = sp.nI(); h.nG[j] = sp.nG(); h.nD[j] = sp.nD(); h.nP[j] = sp.nP();
+    h.int_off[j] = h.nint_nodes;
+    vec_off_I[j] = 2 * h.nint_nodes;
+    h.giff_off[j] = h.nG_tot;
+    h.ldual_off[j] = h.nD_tot;
+    h.lprim_off[j] = h.nP_tot;
+    for (int a = 0; a < (int)sp.nodes.size(); ++a) {
+      q_sub.push_back(j); q_loc.push_back(a); q_node.push_back(sp.nodes[a]); q_mass.push_back(sp.mass[a]);
+      for (int sl = 0; sl < 27; ++sl) q_nbr.push_back(sp.nbr[27 * a + sl]);
+    }
+    for (int a = 0; a < sp.n_interior; ++a) int_node.push_back(sp.nodes[a]);
+    for (int a = sp.n_interior; a < (int)sp.nodes.size(); ++a) {
+      const int g = p.node_to_iface[sp.nodes[a]];
+      R.push_back(2 * g); R.push_back(2 * g + 1);
+    }
+    for (int q : sp.primal) prim_x.push_back(h.nd + q);
+    h.nint_nodes += sp.n_interior;
+    h.nG_tot += h.nG[j];
+    h.nD_tot += h.nD[j];
+    h.nP_tot += h.nP[j];
+  }
+  h.nI_tot = 2 * h.nint_nodes;
+  h.nq = (int)q_sub.size();
+  h.d_q_sub = m.upload(q_sub, s); h.d_q_loc = m.upload(q_loc, s); h.d_q_node = m.upload(q_node, s);
+  h.d_q_nbr = m.upload(q_nbr, s); h.d_q_mass = m.upload(q_mass, s);
+  h.d_q_stencil = m.alloc<double>(54L * h.nq);
+  launch_stencil_gather(h.nq, h.d_q_node, h.d_q_sub, h.d_node_ijk, h.d_elem_grid, h.d_elem_sub, p.n, h.d_Ke,
+                        h.d_q_stencil, 0, s);
+  h.d_int_node = m.upload(int_node, s);
+  h.d_iface_node = m.upload(p.iface_nodes, s);
+  h.d_R = m.upload(R, s);
+  h.d_vec_off_I = m.upload(vec_off_I, s);
+  h.d_giff_off = m.upload(h.giff_off, s);
+  h.d_ldual_off = m.upload(h.ldual_off, s);
+  h.d_lprim_off = m.upload(h.lprim_off, s);
+  h.d_nD = m.upload(h.nD, s);
+  h.d_nI = m.upload(h.nI, s);
+  h.d_prim_x = m.upload(prim_x, s);
+  // R^T as CSR over global interface dofs (subdomain order inside a row)
+  {
+    std::vector<std::vector<int>> rows(h.nif);
+    for (int t = 0; t < (int)R.size(); ++t) rows[R[t]].push_back(t);
+    std::vector<int> ptr(1, 0), idx;
+    for (auto &r : rows) { for (int t : r) idx.push_back(t); ptr.push_back((int)idx.size()); }
+    h.d_Rt_ptr = m.upload(ptr, s);
+    h.d_Rt_idx = m.upload(idx, s);
+    std::vector<double> mult(h.nif);
+    for (int g = 0; g < h.nif; ++g) mult[g] = 1.0 / (double)p.mult[p.iface_nodes[g / 2]];
+    h.d_mult_iface = m.upload(mult, s);
+  }
+  // primal assembly list (coarse right-hand side)
+  {
+    std::vector<std::vector<int>> rows(h.np);
+    for (int j = 0; j < S; ++j)
+      for (int a = 0; a < h.nP[j]; ++a) rows[p.subs[j].primal[a]].push_back(h.lprim_off[j] + a);
+    std::vector<int> ptr(1, 0), idx;
+    for (auto &r : rows) { for (int t : r) idx.push_back(t); ptr.push_back((int)idx.size()); }
+    h.d_pl_ptr = m.upload(ptr, s);
+    h.d_pl_idx = m.upload(idx, s);
+  }
+  h.d_T_ptr = m.upload(p.T_ptr, s); h.d_T_col = m.upload(p.T_col, s); h.d_T_val = m.upload(p.T_val, s);
+  h.d_Tt_ptr = m.upload(p.Tt_ptr, s); h.d_Tt_col = m.upload(p.Tt_col, s); h.d_Tt_val = m.upload(p.Tt_val, s);
+  // local change of basis, flattened CSC
+  {
+    std::vector<int> tl_sub, tl_loc, tl_ptr(1, 0), tl_row, tl_off(S);
+    std::vector<double> tl_val;
+    for (int j = 0; j < S; ++j) {
+      std::vector<int> ptr, row;
+      std::vector<double> val;
+      local_T(p, j, ptr, row, val);
+      tl_off[j] = (int)tl_sub.size();
+      const int base = (int)tl_row.size();
+      for (int a = 0; a + 1 < (int)ptr.size(); ++a) {
+        tl_sub.push_back(j);
+        tl_loc.push_back(a);
+        tl_ptr.push_back(base + ptr[a + 1]);
+      }
+      tl_row.insert(tl_row.end(), row.begin(), row.end());
+      tl_val.insert(tl_val.end(), val.begin(), val.end());
+    }
+    h.nt_tot = (int)tl_sub.size();
+    h.d_tl_sub = m.upload(tl_sub, s); h.d_tl_loc = m.upload(tl_loc, s); h.d_tl_ptr = m.upload(tl_ptr, s);
+    h.d_tl_row = m.upload(tl_row, s); h.d_tl_val = m.upload(tl_val, s); h.d_tl_off = m.upload(tl_off, s);
+  }
+  // ---- dense layouts
+  std::vector<MatDesc> kd(S), ad(S);
+  std::vector<long long> so_off(S), zx_off(S), zp_off(S), sdd_off(S);
+  std::vector<int> ldx(S), ldg(S);
+  h.shK = EngineShape{S, 0, 0, {}, {}};
+  h.shA = EngineShape{S, 0, 0, {}, {}};
+  for (int j = 0; j < S; ++j) {
+    const int n = h.nI[j] + h.nG[j];
+    kd[j] = MatDesc{h.K_el, pad8(n), n, h.nI[j], 0};
+    h.K_el += pad32((long long)pad8(n) * n);
+    const int ma = 2 * h.nD[j] + h.nP[j];
+    ad[j] = MatDesc{h.A_el, pad8(ma), ma, h.nD[j], 0};
+    h.A_el += pad32((long long)pad8(ma) * ma);
+    ldg[j] = pad8(h.nG[j]);
+    so_off[j] = h.So_el;
+    h.So_el += pad32((long long)ldg[j] * h.nG[j]);
+    ldx[j] = pad8(h.nD[j]);
+    zx_off[j] = h.Z_el;
+    h.Z_el += pad32((long long)ldx[j] * h.nD[j]);
+    zp_off[j] = h.Z_el;
+    h.Z_el += pad32((long long)ldx[j] * h.nP[j]);
+    sdd_off[j] = h.SDD_el;
+    h.SDD_el += pad32((long long)ldx[j] * h.nD[j]);
+    h.shK.m.push_back(n); h.shK.e.push_back(h.nI[j]);
+    h.shA.m.push_back(ma); h.shA.e.push_back(h.nD[j]);
+    h.shK.max_m = std::max(h.shK.max_m, n); h.shK.max_e = std::max(h.shK.max_e, h.nI[j]);
+    h.shA.max_m = std::max(h.shA.max_m, ma); h.shA.max_e = std::max(h.shA.max_e, h.nD[j]);
+  }
+  h.d_Kdesc = m.upload(kd, s);
+  h.d_Adesc = m.upload(ad, s);
+  // ---- deluxe classes, pairs and FETI-DP multipliers
+  std::vector<ClassTask> cls;
+  std::vector<PairTask> pairs;
+  std::vector<MatDesc> cdesc;
+  std::vector<LamTask> lts;
+  std::vector<CopyTask> cp_blk, cp_sinv;
+  std::map<std::pair<int, int>, int> pair_of;  // (class, sub) -> pair index
+  h.shC = EngineShape{0, 0, 0, {}, {}};
+  // position of each class inside each subdomain's dual vector
+  std::vector<std::map<int, int>> dpos(S);
+  for (int j = 0; j < S; ++j) {
+    int pos = 0;
+    for (int c : p.subs[j].classes) { dpos[j][c] = pos; pos += 2 * p.cls_dual_nodes[c]; }
+  }
+  int lam_off = 0;
+  for (int c = 0; c < p.n_cls; ++c) {
+    const int n = 2 * p.cls_dual_nodes[c];
+    if (n == 0) continue;
+    ClassTask ct{};
+    ct.n = n;
+    ct.dual_start = p.cls_dual_start[c];
+    ct.sinv_off = h.Sinv_el;
+    ct.pair_beg = (int)pairs.size();
+    std::vector<int> subs(p.cls_subs.begin() + p.cls_sub_ptr[c], p.cls_subs.begin() + p.cls_sub_ptr[c + 1]);
+    for (int j : subs) {
+      PairTask pt{};
+      pt.blk_off = h.Blk_el;
+      pt.ldual_off = h.ldual_off[j] + dpos[j][c];
+      pt.sub = j;
+      pair_of[{c, j}] = (int)pairs.size();
+      CopyTask cb{};
+      cb.src_off = ad[j].off; cb.src_ld = ad[j].ld; cb.r0 = cb.c0 = dpos[j][c]; cb.rows = cb.cols = n;
+      cb.mode = 2; cb.sign = 1.0; cb.dst_off = pt.blk_off; cb.dst_ld = n;
+      cp_blk.push_back(cb);
+      pairs.push_back(pt);
+      h.Blk_el += pad32((long long)n * n);
+    }
+    ct.pair_end = (int)pairs.size();
+    for (int a = 0; a < (int)subs.size(); ++a)
+      for (int b = a + 1; b < (int)subs.size(); ++b) {
+        LamTask lt{};
+        lt.lam_off = lam_off;
+        lt.n = n;
+        lt.pa = pair_of[{c, subs[a]}];
+        lt.pb = pair_of[{c, subs[b]}];
+        lt.sinv_off = ct.sinv_off;
+        lts.push_back(lt);
+        lam_off += n;
+      }
+    const int mc = 2 * n;
+    MatDesc md{h.CA_el, pad8(mc), mc, n, 0};
+    h.CA_el += pad32((long long)pad8(mc) * mc);
+    cdesc.push_back(md);
+    h.shC.m.push_back(mc); h.shC.e.push_back(n);
+    h.shC.max_m = std::max(h.shC.max_m, mc); h.shC.max_e = std::max(h.shC.max_e, n);
+    CopyTask cs{};
+    cs.src_off = md.off; cs.src_ld = md.ld; cs.r0 = cs.c0 = n; cs.rows = cs.cols = n; cs.mode = 2; cs.sign = -1.0;
+    cs.dst_off = ct.sinv_off; cs.dst_ld = n;
+    cp_sinv.push_back(cs);
+    h.Sinv_el += pad32((long long)n * n);
+    h.max_nc = std::max(h.max_nc, n);
+    cls.push_back(ct);
+  }
+  h.shC.count = (int)cls.size();
+  h.ncls = (int)cls.size();
+  h.npairs = (int)pairs.size();
+  h.nlam = lam_off;
+  h.nlt = (int)lts.size();
+  // W tasks (per pair) and their multiplier entries
+  std::vector<WTask> wts(pairs.size());
+  std::vector<std::vector<WEnt>> wents(pairs.size());
+  for (const LamTask &lt : lts) {
+    wents[lt.pa].push_back(WEnt{pairs[lt.pb].blk_off, lt.lam_off, +1});
+    wents[lt.pb].push_back(WEnt{pairs[lt.pa].blk_off, lt.lam_off, -1});
+  }
+  std::vector<WEnt> went;
+  for (size_t q = 0; q < pairs.size(); ++q) {
+    WTask &w = wts[q];
+    w.ldual_off = pairs[q].ldual_off;
+    w.n = 0;
+    w.ent_beg = (int)went.size();
+    for (auto &e : wents[q]) went.push_back(e);
+    w.ent_end = (int)went.size();
+  }
+  for (const ClassTask &ct : cls)
+    for (int q = ct.pair_beg; q < ct.pair_end; ++q) { wts[q].n = ct.n; wts[q].sinv_off = ct.sinv_off; }
+  h.nwt = (int)wts.size();
+  h.d_cls = m.upload(cls, s);
+  h.d_pairs = m.upload(pairs, s);
+  h.d_lt = m.upload(lts, s);
+  h.d_wt = m.upload(wts, s);
+  h.d_went = m.upload(went, s);
+  h.d_Cdesc = m.upload(cdesc, s);
+  // ---- coarse problem
+  {
+    const int np = h.np;
+    h.ld_co = pad8(2 * np);
+    MatDesc co{0, h.ld_co, 2 * np, np, 0};
+    h.d_Codesc = m.upload(std::vector<MatDesc>{co}, s);
+    h.shCo = EngineShape{1, np, 2 * np, {2 * np}, {np}};
+    std::vector<std::vector<long long>> lists((size_t)np * np);
+    for (int j = 0; j < S; ++j) {
+      const SubPlan &sp = p.subs[j];
+      const int nd = h.nD[j];
+      for (int a = 0; a < h.nP[j]; ++a)
+        for (int b = 0; b < h.nP[j]; ++b) {
+          const int hi = std::max(a, b), lo = std::min(a, b);
+          lists[(size_t)sp.primal[a] * np + sp.primal[b]].push_back(ad[j].off + (long long)(nd + hi) * ad[j].ld + nd + lo);
+        }
+    }
+    std::vector<int> ptr(1, 0);
+    std::vector<long long> src;
+    for (auto &l : lists) { for (long long v : l) src.push_back(v); ptr.push_back((int)src.size()); }
+    h.d_co_ptr = m.upload(ptr, s);
+    h.d_co_src = m.upload(src, s);
+    h.d_Co = m.alloc<double>((size_t)h.ld_co * 2 * np);
+    h.d_CoInv = m.alloc<double>((size_t)np * np);
+  }
+  // ---- GEMV and copy task sets
+  auto gset = [&](const std::vector<GemvDesc> &v) {
+    GemvSet g;
+    g.n = (int)v.size();
+    for (auto &t : v) { g.max_rows = std::max(g.max_rows, t.rows); g.max_cols = std::max(g.max_cols, t.cols); }
+    g.d = m.upload(v, s);
+    return g;
+  };
+  auto cset = [&](const std::vector<CopyTask> &v) {
+    CopySet c;
+    c.n = (int)v.size();
+    for (auto &t : v) c.max_elems = std::max(c.max_elems, (long long)t.rows * t.cols);
+    c.d = m.upload(v, s);
+    return c;
+  };
+  std::vector<GemvDesc> g_schur, g_local, g_psit, g_sdd, g_lgi, g_lgit;
+  std::vector<CopyTask> c_sorig, c_sdd, c_zx;
+  for (int j = 0; j < S; ++j) {
+    const int ng = h.nG[j], ni = h.nI[j], nd = h.nD[j], npj = h.nP[j];
+    g_schur.push_back(GemvDesc{so_off[j], ldg[j], ng, ng, h.giff_off[j], h.giff_off[j], 1});
+    g_local.push_back(GemvDesc{zx_off[j], ldx[j], nd, nd, h.ldual_off[j], h.ldual_off[j], 0});
+    g_local.push_back(GemvDesc{zp_off[j], ldx[j], npj, nd, h.ldual_off[j], h.nD_tot + h.lprim_off[j], 0});
+    g_psit.push_back(GemvDesc{zp_off[j], ldx[j], npj, nd, h.lprim_off[j], h.ldual_off[j], 3});
+    g_sdd.push_back(GemvDesc{sdd_off[j], ldx[j], nd, nd, h.ldual_off[j], h.ldual_off[j], 0});
+    const long long lgi = kd[j].off + (long long)ni * kd[j].ld;
+    g_lgi.push_back(GemvDesc{lgi, kd[j].ld, ng, ni, vec_off_I[j], h.giff_off[j], 0});
+    g_lgit.push_back(GemvDesc{lgi, kd[j].ld, ng, ni, h.giff_off[j], vec_off_I[j], 3});
+    CopyTask c{};
+    c.src_off = kd[j].off; c.src_ld = kd[j].ld; c.r0 = c.c0 = ni; c.rows = c.cols = ng; c.mode = 2; c.sign = 1.0;
+    c.dst_off = so_off[j]; c.dst_ld = ldg[j];
+    c_sorig.push_back(c);
+    CopyTask d{};
+    d.src_off = ad[j].off; d.src_ld = ad[j].ld; d.r0 = d.c0 = 0; d.rows = d.cols = nd; d.mode = 2; d.sign = 1.0;
+    d.dst_off = sdd_off[j]; d.dst_ld = ldx[j];
+    c_sdd.push_back(d);
+    CopyTask x{};
+    x.src_off = ad[j].off; x.src_ld = ad[j].ld; x.r0 = x.c0 = nd + npj; x.rows = x.cols = nd; x.mode = 2;
+    x.sign = -1.0; x.dst_off = zx_off[j]; x.dst_ld = ldx[j];
+    c_zx.push_back(x);
+    CopyTask y{};
+    y.src_off = ad[j].off; y.src_ld = ad[j].ld; y.r0 = nd + npj; y.c0 = nd; y.rows = npj; y.cols = nd; y.mode = 1;
+    y.sign = -1.0; y.dst_off = zp_off[j]; y.dst_ld = ldx[j];
+    c_zx.push_back(y);
+  }
+  h.gv_schur = gset(g_schur);
+  h.gv_local = gset(g_local);
+  h.gv_psit = gset(g_psit);
+  h.gv_sdd = gset(g_sdd);
+  h.gv_lgi = gset(g_lgi);
+  h.gv_lgit = gset(g_lgit);
+  h.gv_coarse = gset({GemvDesc{0, h.np, h.np, h.np, 0, h.nd, 0}});
+  h.cp_sorig = cset(c_sorig);
+  h.cp_sdd = cset(c_sdd);
+  h.cp_zx = cset(c_zx);
+  h.cp_blk = cset(cp_blk);
+  h.cp_sinv = cset(cp_sinv);
+  {
+    CopyTask c{};
+    c.src_off = 0; c.src_ld = h.ld_co; c.r0 = c.c0 = h.np; c.rows = c.cols = h.np; c.mode = 2; c.sign = -1.0;
+    c.dst_off = 0; c.dst_ld = h.np;
+    h.cp_coinv = cset({c});
+  }
+  // ---- dense buffers
+  auto alloc_dense = [&](auto &D) {
+    using T = std::remove_pointer_t<decltype(D.K)>;
+    D.K = m.alloc<T>(h.K_el);
+    D.Aug = m.alloc<T>(h.A_el);
+    D.Sorig = m.alloc<T>(h.So_el);
+    D.Z = m.alloc<T>(h.Z_el);
+    D.SDD = m.alloc<T>(h.SDD_el);
+    D.Blk = m.alloc<T>(h.Blk_el);
+    D.CA = m.alloc<T>(h.CA_el);
+    D.Sinv = m.alloc<T>(h.Sinv_el);
+  };
+  if (h.mixed()) alloc_dense(h.df);
+  else alloc_dense(h.dd);
+  // ---- work vectors
+  h.d_fI = m.alloc<double>(h.nI_tot); h.d_yI = m.alloc<double>(h.nI_tot);
+  h.d_fG = m.alloc<double>(h.nif); h.d_fhat = m.alloc<double>(h.nif); h.d_uG = m.alloc<double>(h.nif);
+  h.d_yloc = m.alloc<double>(h.nG_tot);
+  h.d_rbar = m.alloc<double>(h.nd + h.np); h.d_zbar = m.alloc<double>(h.nd + h.np);
+  h.d_rD = m.alloc<double>(h.nD_tot); h.d_rD2 = m.alloc<double>(h.nD_tot);
+  h.d_ydc = m.alloc<double>(h.nD_tot + h.nP_tot);
+  h.d_w1 = m.alloc<double>(h.nD_tot); h.d_w2 = m.alloc<double>(h.nD_tot);
+  h.d_gP = m.alloc<double>(h.nP_tot);
+  h.d_crhs = m.alloc<double>(h.np); h.d_rP = m.alloc<double>(h.np);
+  const int kn = std::max(h.nif, h.nlam);
+  double **kv[] = {&h.d_kx, &h.d_kr, &h.d_kz, &h.d_kp, &h.d_kq, &h.d_kb};
+  for (double **v : kv) *v = m.alloc<double>(kn);
+  h.d_ks = m.alloc<KrylovState>(1);
+  h.hist_cap = std::max(1, h.opt.ksp_max_it) + 2;
+  h.d_ha = m.alloc<double>(h.hist_cap);
+  h.d_hb = m.alloc<double>(h.hist_cap);
+  const int io = std::max({2 * N, h.nif, h.nlam});
+  for (int i = 0; i < 6; ++i) h.d_io[i] = m.alloc<double>(io);
+  ck(cudaStreamSynchronize(s), "setup");
+}
+
+// ---------------------------------------------------------------------------
+// Jacobian: local matrices, factorisations, Schur complements, deluxe, coarse
+// ---------------------------------------------------------------------------
+template <class T>
+void linearize_t(bd_handle &h, Dense<T> &D) {
+  cudaStream_t s = h.s;
+  ck(cudaMemsetAsync(D.K, 0, sizeof(T) * h.K_el, s), "memset K");
+  launch_assemble_local<T>(h.nq, h.d_q_sub, h.d_q_loc, h.d_q_node, h.d_q_nbr, h.d_q_stencil, h.d_q_mass, h.d_factor,
+                           h.tau, h.d_Kdesc, D.K, s);
+  engine_partial_cholesky<T>(h.shK, h.d_Kdesc, D.K, h.d_err, s);
+  launch_copy<T, T>(h.cp_sorig.n, h.cp_sorig.max_elems, h.cp_sorig.d, D.K, D.Sorig, s);
+  long long max_a = 0;
+  for (int j = 0; j < h.nsub; ++j) max_a = std::max(max_a, (long long)h.shA.m[j] * h.shA.m[j]);
+  launch_build_aug<T>(h.nsub, max_a, h.d_Kdesc, D.K, h.d_Adesc, D.Aug, h.d_nI, h.d_nD, h.d_tl_off, h.d_tl_ptr,
+                      h.d_tl_row, h.d_tl_val, s);
+  launch_copy<T, T>(h.cp_sdd.n, h.cp_sdd.max_elems, h.cp_sdd.d, D.Aug, D.SDD, s);
+  launch_copy<T, T>(h.cp_blk.n, h.cp_blk.max_elems, h.cp_blk.d, D.Aug, D.Blk, s);
+  engine_partial_cholesky<T>(h.shA, h.d_Adesc, D.Aug, h.d_err, s);
+  launch_copy<T, T>(h.cp_zx.n, h.cp_zx.max_elems, h.cp_zx.d, D.Aug, D.Z, s);
+  launch_class_aug<T>(h.ncls, h.max_nc, h.d_cls, h.d_pairs, D.Blk, h.d_Cdesc, D.CA, s);
+  engine_partial_cholesky<T>(h.shC, h.d_Cdesc, D.CA, h.d_err, s);
+  launch_copy<T, T>(h.cp_sinv.n, h.cp_sinv.max_elems, h.cp_sinv.d, D.CA, D.Sinv, s);
+  launch_coarse_aug<T>(h.np, h.gauge_primal, h.d_co_ptr, h.d_co_src, D.Aug, h.d_Co, h.ld_co, s);
+  engine_partial_cholesky<double>(h.shCo, h.d_Codesc, h.d_Co, h.d_err, s);
+  launch_copy<double, double>(h.cp_coinv.n, h.cp_coinv.max_elems, h.cp_coinv.d, h.d_Co, h.d_CoInv, s);
+}
+
+void linearize(bd_handle &h) {
+  if (h.mixed()) linearize_t(h, h.df);
+  else linearize_t(h, h.dd);
+  h.linearized = true;
+}
+
+// ---- operators (device vectors; `done` = early-exit flag of a Krylov loop) ----
+template <class T>
+void schur_t(bd_handle &h, Dense<T> &D, const double *x, double *y, const int *done) {
+  launch_gemv<T>(h.gv_schur.n, h.gv_schur.max_rows, h.gv_schur.max_cols, h.gv_schur.d, D.Sorig, x, h.d_R, h.d_yloc,
+                 1.0, done, h.s);
+  launch_gather_sum(h.nif, h.d_Rt_ptr, h.d_Rt_idx, h.d_yloc, y, h.gauge_iface, 1.0, nullptr, done, h.s);
+}
+
+// St^-1 applied to (primal part rP or 0, local dual parts rD): zbar[nd:] = z_Pi, ydc[0:nD_tot] = z_Delta.
+template <class T>
+void st_inv_t(bd_handle &h, Dense<T> &D, const double *rP, const double *rD, const int *done) {
+  launch_gemv<T>(h.gv_local.n, h.gv_local.max_rows, h.gv_local.max_cols, h.gv_local.d, D.Z, rD, nullptr, h.d_ydc,
+                 1.0, done, h.s);
+  launch_gather_sum(h.np, h.d_pl_ptr, h.d_pl_idx, h.d_ydc + h.nD_tot, h.d_crhs, h.gauge_primal, -1.0, rP, done, h.s);
+  launch_gemv<double>(1, h.np, h.np, h.gv_coarse.d, h.d_CoInv, h.d_crhs, nullptr, h.d_zbar, 1.0, done, h.s);
+  launch_gemv_t<T>(h.gv_psit.n, h.gv_psit.max_rows, h.gv_psit.max_cols, h.gv_psit.d, D.Z, h.d_zbar, h.d_prim_x,
+                   h.d_ydc, -1.0, done, h.s);
+}
+
+template <class T>
+void bddc_t(bd_handle &h, Dense<T> &D, const double *r, double *z, const int *done) {
+  launch_spmv(h.nd + h.np, h.d_Tt_ptr, h.d_Tt_col, h.d_Tt_val, r, h.d_rbar, h.nd + h.gauge_primal, done, h.s);
+  launch_deluxe_restrict<T>(h.ncls, h.max_nc, h.d_cls, h.d_pairs, D.Blk, D.Sinv, h.d_rbar, h.d_rD, done, h.s);
+  st_inv_t(h, D, h.d_rbar + h.nd, h.d_rD, done);
+  launch_deluxe_extend<T>(h.ncls, h.max_nc, h.d_cls, h.d_pairs, D.Blk, D.Sinv, h.d_ydc, h.d_zbar, done, h.s);
+  launch_spmv(h.nif, h.d_T_ptr, h.d_T_col, h.d_T_val, h.d_zbar, z, h.gauge_iface, done, h.s);
+}
+
+template <class T>
+void feti_F_t(bd_handle &h, Dense<T> &D, const double *lam, double *y, const int *done) {
+  launch_jump_t(h.nwt, h.max_nc, h.d_wt, h.d_went, lam, h.d_w1, done, h.s);
+  st_inv_t(h, D, nullptr, h.d_w1, done);
+  launch_jump(h.nlt, h.max_nc, h.d_lt, h.d_pairs, h.d_ydc, y, done, h.s);
+}
+
+template <class T>
+void feti_M_t(bd_handle &h, Dense<T> &D, const double *mu, double *y, const int *done) {
+  launch_jump_dt<T>(h.nwt, h.max_nc, h.d_wt, h.d_went, D.Blk, D.Sinv, mu, h.d_w1, done, h.s);
+  launch_gemv<T>(h.gv_sdd.n, h.gv_sdd.max_rows, h.gv_sdd.max_cols, h.gv_sdd.d, D.SDD, h.d_w1, nullptr, h.d_w2, 1.0,
+                 done, h.s);
+  launch_jump_d<T>(h.nlt, h.max_nc, h.d_lt, h.d_pairs, D.Blk, D.Sinv, h.d_w2, y, done, h.s);
+}
+
+#define DISPATCH(H, fn, ...) ((H).mixed() ? fn((H), (H).df, __VA_ARGS__) : fn((H), (H).dd, __VA_ARGS__))
+
+// ---- device-side PCG ---------------------------------------------------------
+constexpr int kChunk = 8;
+
+template <class Op, class Pc>
+int pcg(bd_handle &h, int n, const double *b, double *x, Op A, Pc M, bd_solve_stats *st) {
+  cudaStream_t s = h.s;
+  KrylovState ks{};
+  ks.rtol = h.opt.ksp_rtol;
+  ks.atol = h.opt.ksp_atol;
+  ks.dtol = h.opt.ksp_dtol;
+  ks.maxit = h.opt.ksp_max_it;
+  ks.hist_cap = h.hist_cap;
+  ck(cudaMemcpyAsync(h.d_ks, &ks, sizeof(ks), cudaMemcpyHostToDevice, s), "ks");
+  const int *done = &h.d_ks->done;
+  launch_fill(n, x, 0.0, s);
+  launch_copy_vec(n, b, h.d_kr, nullptr, s);
+  M(h.d_kr, h.d_kz, nullptr);
+  launch_dot2(n, h.d_kr, h.d_kz, h.d_kz, h.d_kz, h.d_partial, h.d_scal, nullptr, s);
+  launch_pcg_start(h.d_ks, h.d_scal, s);
+  launch_copy_vec(n, h.d_kz, h.d_kp, done, s);
+  KrylovState out{};
+  for (int it = 0; it <= h.opt.ksp_max_it; it += kChunk) {
+    for (int c = 0; c < kChunk; ++c) {
+      A(h.d_kp, h.d_kq, done);
+      launch_dot2(n, h.d_kp, h.d_kq, nullptr, nullptr, h.d_partial, h.d_scal, done, s);
+      launch_pcg_alpha(h.d_ks, h.d_scal, h.d_ha, s);
+      launch_pcg_xr(n, h.d_ks, h.d_kp, h.d_kq, x, h.d_kr, s);
+      M(h.d_kr, h.d_kz, done);
+      launch_dot2(n, h.d_kr, h.d_kz, h.d_kz, h.d_kz, h.d_partial, h.d_scal, done, s);
+      launch_pcg_beta(h.d_ks, h.d_scal, h.d_hb, s);
+      launch_pcg_p(n, h.d_ks, h.d_kz, h.d_kp, s);
+    }
+    ck(cudaGetLastError(), "pcg launch");
+    ck(cudaMemcpyAsync(&out, h.d_ks, sizeof(out), cudaMemcpyDeviceToHost, s), "ks read");
+    ck(cudaStreamSynchronize(s), "pcg sync");
+    if (out.done) break;
+  }
+  if (!out.done) out.reason = BD_ERR_KRYLOV_MAXIT;
+  if (st) {
+    st->its = out.it;
+    st->reason = out.reason;
+    st->res0 = out.zn0;
+    st->res = out.zn;
+    st->cond = 0.0;
+    const int k = std::min(out.it, h.hist_cap);
+    if (k > 0) {
+      std::vector<double> a(k), bb(std::max(k - 1, 1));
+      ck(cudaMemcpy(a.data(), h.d_ha, sizeof(double) * k, cudaMemcpyDeviceToHost), "hist");
+      if (k > 1) ck(cudaMemcpy(bb.data(), h.d_hb, sizeof(double) * (k - 1), cudaMemcpyDeviceToHost), "hist");
+      std::vector<double> d(k), e(std::max(k - 1, 0));
+      for (int i = 0; i < k; ++i) {
+        d[i] = 1.0 / a[i] + (i > 0 ? bb[i - 1] / a[i - 1] : 0.0);
+        if (i + 1 < k) e[i] = std::sqrt(bb[i]) / a[i];
+      }
+      st->cond = tridiag_cond(d, e);
+    }
+  }
+  return out.reason;
+}
+
+// ---- Jacobian solve J s = f (f = (fi, fe) device SoA) ---------------------------
+template <class T>
+int solve_t(bd_handle &h, Dense<T> &D, const double *fi, const double *fe, double *si, double *se,
+            bd_solve_stats *st) {
+  cudaStream_t s = h.s;
+  // interior data: y_I = L_II^-1 f_I
+  launch_gather_pairs(h.nint_nodes, h.d_int_node, fi, fe, h.d_fI, 1.0, nullptr, s);
+  launch_trsv<T>(h.nsub, h.shK.max_e, h.d_Kdesc, h.d_vec_off_I, D.K, h.d_fI, h.d_yI, false, s);
+  launch_gemv<T>(h.gv_lgi.n, h.gv_lgi.max_rows, h.gv_lgi.max_cols, h.gv_lgi.d, D.K, h.d_yI, nullptr, h.d_yloc, 1.0,
+                 nullptr, s);
+  launch_gather_pairs(h.nif / 2, h.d_iface_node, fi, fe, h.d_fG, 1.0, nullptr, s);
+  int reason;
+  if (h.opt.method == BD_BDDC) {
+    // f_hat = f_G - sum_j R_j^T L_GI y_I  (= K_GI K_II^-1 f_I)
+    launch_gather_sum(h.nif, h.d_Rt_ptr, h.d_Rt_idx, h.d_yloc, h.d_fhat, h.gauge_iface, -1.0, h.d_fG, nullptr, s);
+    reason = pcg(
+        h, h.nif, h.d_fhat, h.d_uG, [&](const double *x, double *y, const int *dn) { schur_t(h, D, x, y, dn); },
+        [&](const double *x, double *y, const int *dn) { bddc_t(h, D, x, y, dn); }, st);
+  } else {
+    // f~: local g = f_G[R] / mult - L_GI y_I, gbar = T_loc^T g -> (rD, gP); rP = sum gP
+    launch_gather_scale_sub(h.nG_tot, h.d_R, h.d_fG, h.d_mult_iface, h.d_yloc, s);
+    launch_tloc_t(h.nt_tot, h.d_tl_sub, h.d_tl_loc, h.d_tl_ptr, h.d_tl_row, h.d_tl_val, h.d_giff_off, h.d_yloc,
+                  h.d_nD, h.d_ldual_off, h.d_lprim_off, h.d_rD2, h.d_gP, s);
+    launch_gather_sum(h.np, h.d_pl_ptr, h.d_pl_idx, h.d_gP, h.d_rP, h.gauge_primal, 1.0, nullptr, nullptr, s);
+    st_inv_t(h, D, h.d_rP, h.d_rD2, nullptr);
+    launch_jump(h.nlt, h.max_nc, h.d_lt, h.d_pairs, h.d_ydc, h.d_kb, nullptr, s);
+    reason = pcg(
+        h, h.nlam, h.d_kb, h.d_kx, [&](const double *x, double *y, const int *dn) { feti_F_t(h, D, x, y, dn); },
+        [&](const double *x, double *y, const int *dn) { feti_M_t(h, D, x, y, dn); }, st);
+    // w = St^-1 (f~ - B^T lambda); u_G = T (dual mean, primal)
+    launch_jump_t(h.nwt, h.max_nc, h.d_wt, h.d_went, h.d_kx, h.d_w1, nullptr, s);
+    launch_axpby(h.nD_tot, 1.0, h.d_rD2, -1.0, h.d_w1, s);
+    st_inv_t(h, D, h.d_rP, h.d_w1, nullptr);
+    launch_dual_mean(h.ncls, h.max_nc, h.d_cls, h.d_pairs, h.d_ydc, h.d_zbar, s);
+    launch_spmv(h.nif, h.d_T_ptr, h.d_T_col, h.d_T_val, h.d_zbar, h.d_uG, h.gauge_iface, nullptr, s);
+  }
+  // interior recovery: u_I = L_II^-T (y_I - L_GI^T u_G)
+  launch_gemv_t<T>(h.gv_lgit.n, h.gv_lgit.max_rows, h.gv_lgit.max_cols, h.gv_lgit.d, D.K, h.d_uG, h.d_R, h.d_yI, -1.0,
+                   nullptr, s);
+  launch_trsv<T>(h.nsub, h.shK.max_e, h.d_Kdesc, h.d_vec_off_I, D.K, h.d_yI, h.d_fI, true, s);
+  launch_scatter_pairs(h.nint_nodes, h.d_int_node, h.d_fI, si, se, s);
+  launch_scatter_pairs(h.nif / 2, h.d_iface_node, h.d_uG, si, se, s);
+  ck(cudaGetLastError(), "solve");
+  return reason;
+}
+
+int solve(bd_handle &h, const double *fi, const double *fe, double *si, double *se, bd_solve_stats *st) {
+  return h.mixed() ? solve_t(h, h.df, fi, fe, si, se, st) : solve_t(h, h.dd, fi, fe, si, se, st);
+}
+
+StimParams stim_params(const bd_handle &h, const bd_stimulus *st, double t_next) {
+  StimParams sp{};
+  for (int d = 0; d < 3; ++d) sp.h[d] = h.plan.h[d];
+  if (st) {
+    sp.amp = st->amp;
+    for (int k = 0; k < 6; ++k) sp.box[k] = st->box[k];
+    sp.active = (st->t_on <= t_next && t_next < st->t_off && st->amp != 0.0) ? 1 : 0;
+  }
+  return sp;
+}
+
+double read_scalar(bd_handle &h, const double *d) {
+  double v = 0.0;
+  ck(cudaMemcpyAsync(&v, d, sizeof(double), cudaMemcpyDeviceToHost, h.s), "read scalar");
+  ck(cudaStreamSynchronize(h.s), "sync");
+  return v;
+}
+
+// residual at u + lam s into (rit, ret, factort, uit, uet); returns ||F - G||^2
+double trial_residual(bd_handle &h, const StimParams &sp, const double *si, const double *se, double lam) {
+  launch_residual(h.N, h.d_stencil, h.d_nbr, h.d_mass, h.d_node_ijk, h.d_ui, h.d_ue, si, se, lam, h.d_wn, h.d_uin,
+                  h.d_uen, h.fp, sp, h.d_rit, h.d_ret, h.d_factort, h.d_uit, h.d_uet, h.d_partial, h.d_scal, h.s);
+  return read_scalar(h, h.d_scal);
+}
+
+// ---- one time step (Sections 3b, 3c) -------------------------------------------
+int step(bd_handle &h, const bd_stimulus *stim, bd_step_stats *out) {
+  cudaStream_t s = h.s;
+  const double t_next = (h.step_n + 1) * h.tau;
+  const StimParams sp = stim_params(h, stim, t_next);
+  bd_step_stats st{};
+  launch_gating(h.N, h.d_uin, h.d_uen, h.d_w, h.d_wn, h.fp, s);
+  // u^0 = u^n
+  ck(cudaMemcpyAsync(h.d_ui, h.d_uin, sizeof(double) * h.N, cudaMemcpyDeviceToDevice, s), "copy");
+  ck(cudaMemcpyAsync(h.d_ue, h.d_uen, sizeof(double) * h.N, cudaMemcpyDeviceToDevice, s), "copy");
+  double fn2 = trial_residual(h, sp, nullptr, nullptr, 0.0);
+  std::swap(h.d_ui, h.d_uit); std::swap(h.d_ue, h.d_uet);
+  std::swap(h.d_ri, h.d_rit); std::swap(h.d_re, h.d_ret); std::swap(h.d_factor, h.d_factort);
+  const double fn0 = std::sqrt(fn2);
+  st.res0 = fn0;
+  int reason = BD_OK;
+  int k = 0;
+  for (; k < h.opt.newton_max_it; ++k) {
+    if (!std::isfinite(fn2)) { reason = BD_ERR_NAN; break; }
+    if (std::sqrt(fn2) <= std::max(h.opt.snes_atol, h.opt.snes_rtol * fn0)) break;
+    linearize(h);
+    int e = h.check_err();
+    if (e) { reason = e; break; }
+    launch_axpby(h.N, -1.0, h.d_ri, 0.0, h.d_fi, s);
+    launch_axpby(h.N, -1.0, h.d_re, 0.0, h.d_fe, s);
+    bd_solve_stats ls{};
+    int r = solve(h, h.d_fi, h.d_fe, h.d_si, h.d_se, &ls);
+    st.krylov_its += ls.its;
+    st.cond_max = std::max(st.cond_max, ls.cond);
+    if (r != BD_OK) { reason = r; break; }
+    // cubic backtracking line search on f = ||R||^2 / 2, slope = -||R||^2
+    const double alpha = 1e-4, f0 = 0.5 * fn2, slope = -fn2;
+    double lam = 1.0;
+    double g = trial_residual(h, sp, h.d_si, h.d_se, lam);
+    bool ok = 0.5 * g <= f0 + alpha * lam * slope;
+    if (!ok) {
+      double lam_prev = lam, f_prev = 0.5 * g;
+      double lt = -slope / (2.0 * (0.5 * g - f0 - slope));
+      lam = std::max(std::min(lt, 0.5 * lam), 0.1 * lam);
+      for (int ls_it = 0; ls_it < 40 && !ok; ++ls_it) {
+        if (lam < 1e-12) break;
+        g = trial_residual(h, sp, h.d_si, h.d_se, lam);
+        const double fl = 0.5 * g;
+        if (fl <= f0 + alpha * lam * slope) { ok = true; break; }
+        const double t1 = fl - f0 - lam * slope, t2 = f_prev - f0 - lam_prev * slope, dl = lam - lam_prev;
+        const double a = (t1 / (lam * lam) - t2 / (lam_prev * lam_prev)) / dl;
+        const double b = (-lam_prev * t1 / (lam * lam) + lam * t2 / (lam_prev * lam_prev)) / dl;
+        if (a == 0.0) lt = -slope / (2.0 * b);
+        else lt = (-b + std::sqrt(std::max(b * b - 3.0 * a * slope, 0.0))) / (3.0 * a);
+        lam_prev = lam;
+        f_prev = fl;
+        lam = std::max(std::min(lt, 0.5 * lam), 0.1 * lam);
+      }
+    }
+    std::swap(h.d_ui, h.d_uit); std::swap(h.d_ue, h.d_uet);
+    std::swap(h.d_ri, h.d_rit); std::swap(h.d_re, h.d_ret); std::swap(h.d_factor, h.d_factort);
+    fn2 = g;
+    if (!ok) { reason = BD_ERR_NEWTON; ++k; break; }
+    // ||lam s|| <= stol ||u||
+    launch_dot3(h.N, h.d_si, h.d_si, h.d_se, h.d_se, h.d_ui, h.d_ui, h.d_partial, h.d_scal, s);
+    launch_dot3(h.N, h.d_ue, h.d_ue, h.d_ue, h.d_ue, h.d_ue, h.d_ue, h.d_partial, h.d_scal + 3, s);
+    double sc[6];
+    ck(cudaMemcpyAsync(sc, h.d_scal, sizeof(sc), cudaMemcpyDeviceToHost, s), "read");
+    ck(cudaStreamSynchronize(s), "sync");
+    const double snorm = lam * std::sqrt(sc[0] + sc[1]);
+    const double unorm = std::sqrt(sc[2] + sc[3]);
+    if (snorm <= h.opt.snes_stol * unorm) { ++k; break; }
+  }
+  if (k >= h.opt.newton_max_it && reason == BD_OK && !(std::sqrt(fn2) <= std::max(h.opt.snes_atol, h.opt.snes_rtol * fn0)))
+    reason = BD_ERR_NEWTON;
+  st.newton_its = k;
+  st.res_final = std::sqrt(fn2);
+  // gauge: zero lumped-mass mean of u_e, then u^n <- u, w <- w^{n+1}
+  launch_dot3(h.N, h.d_mass, h.d_ue, h.d_mass, h.d_ue, h.d_mass, h.d_ue, h.d_partial, h.d_scal, s);
+  launch_fill(1, h.d_scal + 1, h.sum_mass, s);
+  launch_gauge_shift(h.N, h.d_ui, h.d_ue, h.d_scal, s);
+  ck(cudaMemcpyAsync(h.d_uin, h.d_ui, sizeof(double) * h.N, cudaMemcpyDeviceToDevice, s), "copy");
+  ck(cudaMemcpyAsync(h.d_uen, h.d_ue, sizeof(double) * h.N, cudaMemcpyDeviceToDevice, s), "copy");
+  ck(cudaMemcpyAsync(h.d_w, h.d_wn, sizeof(double) * h.N, cudaMemcpyDeviceToDevice, s), "copy");
+  ck(cudaStreamSynchronize(s), "step");
+  h.step_n += 1;
+  st.reason = reason;
+  if (out) *out = st;
+  return reason;
+}
+
+// ---- host / device pointer helpers ------------------------------------------------
+const double *in_ptr(bd_handle &h, const double *p, size_t n, int on_device, int slot) {
+  if (on_device) return p;
+  ck(cudaMemcpyAsync(h.d_io[slot], p, n * sizeof(double), cudaMemcpyHostToDevice, h.s), "h2d");
+  return h.d_io[slot];
+}
+double *out_ptr(bd_handle &h, double *p, int on_device, int slot) { return on_device ? p : h.d_io[slot]; }
+void finish_out(bd_handle &h, double *host, const double *dev, size_t n, int on_device) {
+  if (!on_device) ck(cudaMemcpyAsync(host, dev, n * sizeof(double), cudaMemcpyDeviceToHost, h.s), "d2h");
+  ck(cudaStreamSynchronize(h.s), "sync");
+}
+
+thread_local std::string g_last_error;
+
+template <class F>
+int guard(bd_handle *h, F &&f) {
+  try {
+    return f();
+  } catch (const Status &e) {
+    g_last_error = e.what();
+    if (h) h->last_error = e.what();
+    return e.code;
+  } catch (const std::bad_alloc &) {
+    return BD_ERR_NOMEM;
+  } catch (const std::exception &e) {
+    g_last_error = e.what();
+    return BD_ERR_ARG;
+  }
+}
+
+}  // namespace
+
+// ===========================================================================
+// C-ABI
+// ===========================================================================
+extern "C" {
+
+int bd_plan_create(const bd_mesh *mesh, int primal, bd_plan **out) {
+  if (!mesh || !out) return BD_ERR_ARG;
+  return guard(nullptr, [&] {
+    auto pl = std::make_unique<bd_plan>();
+    std::string err = build_plan(pl->p, mesh->n, mesh->l, mesh->s, mesh->elem_mask, primal);
+    if (!err.empty()) { g_last_error = err; return BD_ERR_ARG; }
+    *out = pl.release();
+    return BD_OK;
+  });
+}
+
+static int fill_sizes(const Plan &p, bd_sizes *o) {
+  o->n_node = p.n_node; o->n_elem = p.n_elem; o->n_sub = p.n_sub; o->n_cls = p.n_cls;
+  o->n_iface = p.n_iface(); o->n_dual = p.n_dual; o->n_primal = p.n_primal;
+  long long nl = 0;
+  for (int c = 0; c < p.n_cls; ++c) {
+    const long long k = p.cls_sub_ptr[c + 1] - p.cls_sub_ptr[c];
+    nl += 2LL * p.cls_dual_nodes[c] * (k * (k - 1) / 2);
+  }
+  o->n_lambda = (int)nl;
+  o->gauge_node = p.gauge_node; o->gauge_primal = p.gauge_primal;
+  return BD_OK;
+}
+
+int bd_plan_sizes(const bd_plan *plan, bd_sizes *out) {
+  if (!plan || !out) return BD_ERR_ARG;
+  return fill_sizes(plan->p, out);
+}
+
+static int index_sets(const Plan &p, int which, int64_t *out, int64_t cap, int64_t *len) {
+  std::vector<int64_t> v;
+  auto add = [&](const std::vector<int> &x) { v.insert(v.end(), x.begin(), x.end()); };
+  switch (which) {
+    case BD_IDX_ELEM_SUB: add(p.elem_sub); break;
+    case BD_IDX_NODE_MULT: add(p.mult); break;
+    case BD_IDX_IFACE_NODES: add(p.iface_nodes); break;
+    case BD_IDX_CLS_TYPE: add(p.cls_type); break;
+    case BD_IDX_CLS_PTR: add(p.cls_ptr); break;
+    case BD_IDX_CLS_NODES: add(p.cls_nodes); break;
+    case BD_IDX_CLS_SUB_PTR: add(p.cls_sub_ptr); break;
+    case BD_IDX_CLS_SUBS: add(p.cls_subs); break;
+    case BD_IDX_CLS_DUAL_START: add(p.cls_dual_start); break;
+    case BD_IDX_SUB_NODE_PTR: {
+      v.push_back(0);
+      for (auto &sp : p.subs) v.push_back(v.back() + (int64_t)sp.nodes.size());
+      break;
+    }
+    case BD_IDX_SUB_NODES: for (auto &sp : p.subs) add(sp.nodes); break;
+    case BD_IDX_SUB_NINT: for (auto &sp : p.subs) v.push_back(sp.n_interior); break;
+    case BD_IDX_SUB_DUAL_PTR: {
+      v.push_back(0);
+      for (auto &sp : p.subs) v.push_back(v.back() + (int64_t)sp.dual.size());
+      break;
+    }
+    case BD_IDX_SUB_DUAL: for (auto &sp : p.subs) add(sp.dual); break;
+    case BD_IDX_SUB_PRIMAL_PTR: {
+      v.push_back(0);
+      for (auto &sp : p.subs) v.push_back(v.back() + (int64_t)sp.primal.size());
+      break;
+    }
+    case BD_IDX_SUB_PRIMAL: for (auto &sp : p.subs) add(sp.primal); break;
+    case BD_IDX_GAUGE: v.push_back(p.gauge_node); v.push_back(p.gauge_primal); break;
+    default: return BD_ERR_ARG;
+  }
+  if (len) *len = (int64_t)v.size();
+  if (!out) return BD_OK;
+  if (cap < (int64_t)v.size()) return BD_ERR_ARG;
+  std::copy(v.begin(), v.end(), out);
+  return BD_OK;
+}
+
+int bd_plan_index_sets(const bd_plan *plan, int which, int64_t *out, int64_t cap, int64_t *len) {
+  if (!plan) return BD_ERR_ARG;
+  return index_sets(plan->p, which, out, cap, len);
+}
+
+void bd_plan_destroy(bd_plan *plan) { delete plan; }
+
+int bd_options_default(bd_options *o) {
+  if (!o) return BD_ERR_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->method = BD_BDDC;
+  o->krylov = BD_PCG;
+  o->primal = BD_PRIMAL_VE;
+  o->precision = BD_FP64;
+  o->gmres_restart = 30;
+  o->ksp_max_it = 1000;
+  o->newton_max_it = 50;
+  o->use_graphs = 0;
+  o->ksp_rtol = 1e-8; o->ksp_atol = 1e-10; o->ksp_dtol = 1e4;
+  o->snes_rtol = 1e-4; o->snes_atol = 1e-8; o->snes_stol = 1e-8;
+  return BD_OK;
+}
+
+int bidomain_setup(const bd_mesh *mesh, const bd_conductivity *cond, const bd_ionic *ionic, double tau,
+                   const bd_options *opt, void *stream, bd_handle **out) {
+  if (!mesh || !cond || !ionic || !out || !(tau > 0)) return BD_ERR_ARG;
+  return guard(nullptr, [&] {
+    auto h = std::make_unique<bd_handle>();
+    if (opt) h->opt = *opt;
+    else bd_options_default(&h->opt);
+    const bd_options &o = h->opt;
+    if ((o.method != BD_BDDC && o.method != BD_FETIDP) || (o.krylov != BD_PCG) ||
+        (o.precision != BD_FP64 && o.precision != BD_MIXED) || o.ksp_max_it < 1 || o.newton_max_it < 1)
+      return BD_ERR_ARG;
+    std::string err = build_plan(h->plan, mesh->n, mesh->l, mesh->s, mesh->elem_mask, o.primal);
+    if (!err.empty()) { g_last_error = err; return BD_ERR_ARG; }
+    h->tau = tau;
+    for (int d = 0; d < 3; ++d) { h->fp.sigma_i[d] = cond->sigma_i[d]; h->fp.sigma_e[d] = cond->sigma_e[d]; }
+    h->fp.G = ionic->G; h->fp.eta1 = ionic->eta1; h->fp.eta2 = ionic->eta2; h->fp.vth = ionic->vth;
+    h->fp.vp = ionic->vp; h->fp.chi_cm = ionic->chi_cm; h->fp.tau = tau;
+    if (stream) h->s = (cudaStream_t)stream;
+    else { ck(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking), "stream"); h->own_stream = true; }
+    setup_handle(*h);
+    *out = h.release();
+    return BD_OK;
+  });
+}
+
+int bidomain_sizes(const bd_handle *h, bd_sizes *out) {
+  if (!h || !out) return BD_ERR_ARG;
+  return fill_sizes(h->plan, out);
+}
+
+int bidomain_index_sets(const bd_handle *h, int which, int64_t *out, int64_t cap, int64_t *len) {
+  if (!h) return BD_ERR_ARG;
+  return index_sets(h->plan, which, out, cap, len);
+}
+
+int bidomain_set_state(bd_handle *h, const double *ui, const double *ue, const double *w, double t, int on_device) {
+  if (!h || !ui || !ue || !w) return BD_ERR_ARG;
+  return guard(h, [&] {
+    const size_t n = h->N;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    ck(cudaMemcpyAsync(h->d_uin, ui, n * sizeof(double), k, h->s), "state");
+    ck(cudaMemcpyAsync(h->d_uen, ue, n * sizeof(double), k, h->s), "state");
+    ck(cudaMemcpyAsync(h->d_w, w, n * sizeof(double), k, h->s), "state");
+    ck(cudaStreamSynchronize(h->s), "sync");
+    h->step_n = std::lround(t / h->tau);
+    return BD_OK;
+  });
+}
+
+int bidomain_get_state(bd_handle *h, double *ui, double *ue, double *w, double *t, int on_device) {
+  if (!h) return BD_ERR_ARG;
+  return guard(h, [&] {
+    const size_t n = h->N;
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (ui) ck(cudaMemcpyAsync(ui, h->d_uin, n * sizeof(double), k, h->s), "state");
+    if (ue) ck(cudaMemcpyAsync(ue, h->d_uen, n * sizeof(double), k, h->s), "state");
+    if (w) ck(cudaMemcpyAsync(w, h->d_w, n * sizeof(double), k, h->s), "state");
+    ck(cudaStreamSynchronize(h->s), "sync");
+    if (t) *t = h->step_n * h->tau;
+    return BD_OK;
+  });
+}
+
+int bidomain_step(bd_handle *h, const bd_stimulus *stim, bd_step_stats *stats) {
+  if (!h) return BD_ERR_ARG;
+  return guard(h, [&] { return step(*h, stim, stats); });
+}
+
+int bidomain_gating(bd_handle *h, const double *ui, const double *ue, const double *w, double *w_next,
+                    int on_device) {
+  if (!h || !ui || !ue || !w || !w_next) return BD_ERR_ARG;
+  return guard(h, [&] {
+    const size_t n = h->N;
+    const double *a = in_ptr(*h, ui, n, on_device, 0), *b = in_ptr(*h, ue, n, on_device, 1),
+                 *c = in_ptr(*h, w, n, on_device, 2);
+    double *o = out_ptr(*h, w_next, on_device, 3);
+    launch_gating(h->N, a, b, c, o, h->fp, h->s);
+    finish_out(*h, w_next, o, n, on_device);
+    return BD_OK;
+  });
+}
+
+int bidomain_residual(bd_handle *h, const bd_stimulus *stim, double t_next, const double *ui, const double *ue,
+                      const double *w_next, const double *ui_n, const double *ue_n, double *r, int on_device) {
+  if (!h || !ui || !ue || !w_next || !ui_n || !ue_n || !r) return BD_ERR_ARG;
+  return guard(h, [&] {
+    const size_t n = h->N;
+    const double *a = in_ptr(*h, ui, n, on_device, 0), *b = in_ptr(*h, ue, n, on_device, 1),
+                 *c = in_ptr(*h, w_next, n, on_device, 2), *d = in_ptr(*h, ui_n, n, on_device, 3),
+                 *e = in_ptr(*h, ue_n, n, on_device, 4);
+    double *o = out_ptr(*h, r, on_device, 5);
+    launch_residual(h->N, h->d_stencil, h->d_nbr, h->d_mass, h->d_node_ijk, a, b, nullptr, nullptr, 0.0, c, d, e,
+                    h->fp, stim_params(*h, stim, t_next), o, o + n, nullptr, nullptr, nullptr, h->d_partial,
+                    nullptr, h->s);
+    finish_out(*h, r, o, 2 * n, on_device);
+    return BD_OK;
+  });
+}
+
+int bidomain_linearize(bd_handle *h, const double *ui, const double *ue, const double *w_next, int on_device) {
+  if (!h || !ui || !ue || !w_next) return BD_ERR_ARG;
+  return guard(h, [&] {
+    const size_t n = h->N;
+    const double *a = in_ptr(*h, ui, n, on_device, 0), *b = in_ptr(*h, ue, n, on_device, 1),
+                 *c = in_ptr(*h, w_next, n, on_device, 2);
+    launch_residual(h->N, h->d_stencil, h->d_nbr, h->d_mass, h->d_node_ijk, a, b, nullptr, nullptr, 0.0, c, a, b,
+                    h->fp, stim_params(*h, nullptr, 0.0), h->d_rit, h->d_ret, h->d_factor, nullptr, nullptr,
+                    h->d_partial, nullptr, h->s);
+    linearize(*h);
+    return h->check_err();
+  });
+}
+
+int schur_apply(bd_handle *h, const double *x, double *y, int on_device) {
+  if (!h || !x || !y) return BD_ERR_ARG;
+  if (!h->linearized) return BD_ERR_STATE;
+  return guard(h, [&] {
+    const double *a = in_ptr(*h, x, h->nif, on_device, 0);
+    double *o = out_ptr(*h, y, on_device, 1);
+    DISPATCH(*h, schur_t, a, o, nullptr);
+    finish_out(*h, y, o, h->nif, on_device);
+    return BD_OK;
+  });
+}
+
+int bddc_apply(bd_handle *h, const double *r, double *z, int on_device) {
+  if (!h || !r || !z) return BD_ERR_ARG;
+  if (!h->linearized) return BD_ERR_STATE;
+  return guard(h, [&] {
+    const double *a = in_ptr(*h, r, h->nif, on_device, 0);
+    double *o = out_ptr(*h, z, on_device, 1);
+    DISPATCH(*h, bddc_t, a, o, nullptr);
+    finish_out(*h, z, o, h->nif, on_device);
+    return BD_OK;
+  });
+}
+
+int fetidp_apply(bd_handle *h, const double *lambda, double *mu, int on_device) {
+  if (!h || !lambda || !mu) return BD_ERR_ARG;
+  if (!h->linearized) return BD_ERR_STATE;
+  return guard(h, [&] {
+    const double *a = in_ptr(*h, lambda, h->nlam, on_device, 0);
+    double *o = out_ptr(*h, mu, on_device, 1);
+    DISPATCH(*h, feti_M_t, a, o, nullptr);
+    finish_out(*h, mu, o, h->nlam, on_device);
+    return BD_OK;
+  });
+}
+
+int fetidp_operator(bd_handle *h, const double *lambda, double *y, int on_device) {
+  if (!h || !lambda || !y) return BD_ERR_ARG;
+  if (!h->linearized) return BD_ERR_STATE;
+  return guard(h, [&] {
+    const double *a = in_ptr(*h, lambda, h->nlam, on_device, 0);
+    double *o = out_ptr(*h, y, on_device, 1);
+    DISPATCH(*h, feti_F_t, a, o, nullptr);
+    finish_out(*h, y, o, h->nlam, on_device);
+    return BD_OK;
+  });
+}
+
+int krylov_solve(bd_handle *h, const double *f, double *s, int on_device, bd_solve_stats *stats) {
+  if (!h || !f || !s) return BD_ERR_ARG;
+  if (!h->linearized) return BD_ERR_STATE;
+  return guard(h, [&] {
+    const size_t n = h->N;
+    const double *a = in_ptr(*h, f, 2 * n, on_device, 0);
+    double *o = out_ptr(*h, s, on_device, 1);
+    int r = solve(*h, a, a + n, o, o + n, stats);
+    finish_out(*h, s, o, 2 * n, on_device);
+    if (r == BD_OK) r = h->check_err();
+    return r;
+  });
+}
+
+int bidomain_destroy(bd_handle *h) {
+  if (!h) return BD_ERR_ARG;
+  cudaStreamSynchronize(h->s);
+  cudaStream_t s = h->s;
+  const bool own = h->own_stream;
+  delete h;
+  if (own) cudaStreamDestroy(s);
+  return BD_OK;
+}
+
+const char *bidomain_strerror(int status) {
+  switch (status) {
+    case BD_OK: return "ok";
+    case BD_ERR_ARG: return "invalid argument";
+    case BD_ERR_NOT_SPD: return "local matrix not positive definite (non-positive pivot)";
+    case BD_ERR_KRYLOV_MAXIT: return "Krylov method reached the iteration limit";
+    case BD_ERR_KRYLOV_DIVERGED: return "Krylov method diverged";
+    case BD_ERR_NEWTON: return "Newton iteration or line search failed";
+    case BD_ERR_NAN: return "NaN or Inf encountered";
+    case BD_ERR_TIMEOUT: return "device wait exceeded its budget";
+    case BD_ERR_CUDA: return "CUDA runtime error";
+    case BD_ERR_NOMEM: return "out of device memory";
+    case BD_ERR_STATE: return "call made in the wrong order";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

@@ -1,0 +1,648 @@
+// Domain-decomposition kernels: local assembly, Schur blocks, deluxe scaling,
+// coarse problem, BDDC / FETI-DP application and the PCG recurrences
+// (Sections 4.1-4.4 of the paper).
+#include <algorithm>
+
+#include "dd_kernels.cuh"
+
+namespace bd {
+
+// ---- local matrices K^(j) (Section 4.1, local forms a^(j)) -------------------
+// One thread per (local node q, stencil slot).  Local dofs are 2a + field in the
+// order [interior nodes; interface nodes].  The self slot also writes the
+// coupling Kc = M^(j) (chi Cm + tau dI/dv): +Kc on both diagonals, -Kc across.
+template <typename T>
+__global__ void k_assemble_local(int nq, const int *__restrict__ q_sub, const int *__restrict__ q_loc,
+                                 const int *__restrict__ q_node, const int *__restrict__ nbr,
+                                 const double *__restrict__ stencil, const double *__restrict__ mass,
+                                 const double *__restrict__ factor, double tau, const MatDesc *__restrict__ desc,
+                                 T *__restrict__ base) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nq * 27) return;
+  const int q = (int)(t / 27), sl = (int)(t % 27);
+  const int b = nbr[(long long)q * 27 + sl];
+  if (b < 0) return;
+  const MatDesc d = desc[q_sub[q]];
+  const int a = q_loc[q];
+  T *K = base + d.off;
+  double vi = tau * stencil[((long long)q * 27 + sl) * 2 + 0];
+  double ve = tau * stencil[((long long)q * 27 + sl) * 2 + 1];
+  if (sl == 13) {
+    const double kc = mass[q] * factor[q_node[q]];
+    vi += kc;
+    ve += kc;
+    K[(long long)(2 * a) * d.ld + 2 * a + 1] = (T)(-kc);
+    K[(long long)(2 * a + 1) * d.ld + 2 * a] = (T)(-kc);
+  }
+  K[(long long)(2 * a) * d.ld + 2 * b] = (T)vi;
+  K[(long long)(2 * a + 1) * d.ld + 2 * b + 1] = (T)ve;
+}
+
+// ---- block copies ------------------------------------------------------------
+template <typename TS, typename TD>
+__global__ void k_copy(const CopyTask *__restrict__ tasks, const TS *__restrict__ src, TD *__restrict__ dst) {
+  const CopyTask c = tasks[blockIdx.y];
+  const long long tot = (long long)c.rows * c.cols;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / c.cols), k = (int)(t % c.cols);
+    int r, cc;
+    if (c.mode == 0) { r = c.r0 + i; cc = c.c0 + k; }
+    else if (c.mode == 1) { r = c.r0 + k; cc = c.c0 + i; }
+    else { r = c.r0 + max(i, k); cc = c.c0 + min(i, k); }
+    dst[c.dst_off + (long long)i * c.dst_ld + k] = (TD)(c.sign * (double)src[c.src_off + (long long)r * c.src_ld + cc]);
+  }
+}
+
+// ---- augmented matrix of the constrained local problem ------------------------
+// Aug = [[Sb_DD, Sb_DP, I], [Sb_PD, Sb_PP, 0], [I, 0, 0]] with Sb = T^T S T
+// (change of basis for the primal averages), S read from the lower triangle of
+// the trailing block of the factored local matrix.  T_loc is CSC by
+// transformed dof.  One thread per entry.
+template <typename T>
+__global__ void k_build_aug(const MatDesc *__restrict__ kdesc, const T *__restrict__ kbase,
+                            const MatDesc *__restrict__ adesc, T *__restrict__ abase, const int *__restrict__ nI,
+                            const int *__restrict__ nD, const int *__restrict__ tptr_off,
+                            const int *__restrict__ tptr, const int *__restrict__ trow,
+                            const double *__restrict__ tval) {
+  const int j = blockIdx.y;
+  const MatDesc ad = adesc[j];
+  const long long tot = (long long)ad.m * ad.m;
+  const MatDesc kd = kdesc[j];
+  const int ni = nI[j], nd = nD[j];
+  const int nt = ad.m - nd;  // nD + nP
+  const int *P = tptr + tptr_off[j];
+  const T *S = kbase + kd.off;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(t / ad.m), b = (int)(t % ad.m);
+    double v = 0.0;
+    if (a < nt && b < nt) {
+      for (int p = P[a]; p < P[a + 1]; ++p)
+        for (int q = P[b]; q < P[b + 1]; ++q) {
+          const int ra = trow[p], rb = trow[q];
+          const int hi = max(ra, rb), lo = min(ra, rb);
+          v += tval[p] * tval[q] * (double)S[(long long)(ni + hi) * kd.ld + ni + lo];
+        }
+    } else if (a >= nt && b < nd) {
+      v = (a - nt == b) ? 1.0 : 0.0;
+    } else if (b >= nt && a < nd) {
+      v = (b - nt == a) ? 1.0 : 0.0;
+    }
+    abase[ad.off + (long long)a * ad.ld + b] = (T)v;
+  }
+}
+
+// ---- deluxe class inverses: AugC = [[sum_j S_C^(j), I], [I, 0]] ---------------
+template <typename T>
+__global__ void k_class_aug(const ClassTask *__restrict__ cls, const PairTask *__restrict__ pairs,
+                            const T *__restrict__ blk, const MatDesc *__restrict__ cdesc, T *__restrict__ cbase) {
+  const ClassTask c = cls[blockIdx.y];
+  const MatDesc d = cdesc[blockIdx.y];
+  const int n = c.n, m = 2 * n;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m * m; t += gridDim.x * blockDim.x) {
+    const int a = t / m, b = t % m;
+    T v = T(0);
+    if (a < n && b < n) {
+      for (int p = c.pair_beg; p < c.pair_end; ++p) v += blk[pairs[p].blk_off + (long long)a * n + b];
+    } else if (a >= n && b < n) {
+      v = (a - n == b) ? T(1) : T(0);
+    } else if (b >= n && a < n) {
+      v = (b - n == a) ? T(1) : T(0);
+    }
+    cbase[d.off + (long long)a * d.ld + b] = v;
+  }
+}
+
+// ---- coarse matrix S_PP = sum_j R_P^T S_PP^(j) R_P (Section 4.4) ---------------
+// Entry (p, q) sums the listed local entries (fixed order); the gauge row and
+// column become a unit row and column.  Written as AugCo = [[S_PP, I], [I, 0]].
+template <typename T>
+__global__ void k_coarse_aug(int np, int gauge, const int *__restrict__ ptr, const long long *__restrict__ src,
+                             const T *__restrict__ abase, double *__restrict__ co, int ld) {
+  const int m = 2 * np;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)m * m;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int a = (int)(t / m), b = (int)(t % m);
+    double v = 0.0;
+    if (a < np && b < np) {
+      if (a == gauge || b == gauge) v = (a == b) ? 1.0 : 0.0;
+      else
+        for (int k = ptr[(long long)a * np + b]; k < ptr[(long long)a * np + b + 1]; ++k) v += (double)abase[src[k]];
+    } else if (a >= np && b < np) {
+      v = (a - np == b) ? 1.0 : 0.0;
+    } else if (b >= np && a < np) {
+      v = (b - np == a) ? 1.0 : 0.0;
+    }
+    co[(long long)a * ld + b] = v;
+  }
+}
+
+// ---- sparse (CSR) matrix-vector product y = A x, y[zero] = 0 --------------------
+__global__ void k_spmv(int n, const int *__restrict__ ptr, const int *__restrict__ col, const double *__restrict__ val,
+                       const double *__restrict__ x, double *__restrict__ y, int zero, const int *__restrict__ done) {
+  if (done && *done) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double acc = 0.0;
+  for (int k = ptr[r]; k < ptr[r + 1]; ++k) acc += val[k] * x[col[k]];
+  y[r] = (r == zero) ? 0.0 : acc;
+}
+
+// y[g] = sum of the listed local values (interface assembly R^T), y[zero] = 0.
+__global__ void k_gather_sum(int n, const int *__restrict__ ptr, const int *__restrict__ idx,
+                             const double *__restrict__ src, double *__restrict__ y, int zero, double alpha,
+                             const double *__restrict__ addend, const int *__restrict__ done) {
+  if (done && *done) return;
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  double acc = 0.0;
+  for (int k = ptr[r]; k < ptr[r + 1]; ++k) acc += src[idx[k]];
+  double v = alpha * acc;
+  if (addend) v += addend[r];
+  y[r] = (r == zero) ? 0.0 : v;
+}
+
+// ---- deluxe restriction and extension (Section 4.2) -----------------------------
+// restrict: t = (sum S)^-1 rbar_C; r_C^(j) = S_C^(j) t      (D_C^(j)T rbar_C)
+// extend:   acc = sum_j S_C^(j) z_C^(j); zbar_C = (sum S)^-1 acc   (sum_j D_C^(j) z_C^(j))
+template <typename T>
+__device__ inline void smem_gemv(const T *__restrict__ A, int n, const T *__restrict__ x, T *__restrict__ y) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int u = wid; u < n; u += nw) {
+    T acc = T(0);
+    for (int v = lane; v < n; v += 32) acc += A[(long long)u * n + v] * x[v];
+    acc = warp_sum(acc);
+    if (lane == 0) y[u] = acc;
+  }
+}
+
+template <typename T>
+__global__ void k_deluxe_restrict(const ClassTask *__restrict__ cls, const PairTask *__restrict__ pairs,
+                                  const T *__restrict__ blk, const T *__restrict__ sinv, const double *__restrict__ rbar,
+                                  double *__restrict__ rD, const int *__restrict__ done) {
+  if (done && *done) return;
+  const ClassTask c = cls[blockIdx.x];
+  extern __shared__ unsigned char smem_raw[];
+  T *rb = reinterpret_cast<T *>(smem_raw);
+  T *tt = rb + c.n;
+  T *out = tt + c.n;
+  for (int u = threadIdx.x; u < c.n; u += blockDim.x) rb[u] = (T)rbar[c.dual_start + u];
+  __syncthreads();
+  smem_gemv(sinv + c.sinv_off, c.n, rb, tt);
+  __syncthreads();
+  for (int p = c.pair_beg; p < c.pair_end; ++p) {
+    const PairTask pt = pairs[p];
+    smem_gemv(blk + pt.blk_off, c.n, tt, out);
+    __syncthreads();
+    for (int u = threadIdx.x; u < c.n; u += blockDim.x) rD[pt.ldual_off + u] = (double)out[u];
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void k_deluxe_extend(const ClassTask *__restrict__ cls, const PairTask *__restrict__ pairs,
+                                const T *__restrict__ blk, const T *__restrict__ sinv, const double *__restrict__ zD,
+                                double *__restrict__ zbar, const int *__restrict__ done) {
+  if (done && *done) return;
+  const ClassTask c = cls[blockIdx.x];
+  extern __shared__ unsigned char smem_raw[];
+  T *acc = reinterpret_cast<T *>(smem_raw);
+  T *zz = acc + c.n;
+  T *tmp = zz + c.n;
+  for (int u = threadIdx.x; u < c.n; u += blockDim.x) acc[u] = T(0);
+  __syncthreads();
+  for (int p = c.pair_beg; p < c.pair_end; ++p) {
+    const PairTask pt = pairs[p];
+    for (int u = threadIdx.x; u < c.n; u += blockDim.x) zz[u] = (T)zD[pt.ldual_off + u];
+    __syncthreads();
+    smem_gemv(blk + pt.blk_off, c.n, zz, tmp);
+    __syncthreads();
+    for (int u = threadIdx.x; u < c.n; u += blockDim.x) acc[u] += tmp[u];
+    __syncthreads();
+  }
+  smem_gemv(sinv + c.sinv_off, c.n, acc, tmp);
+  __syncthreads();
+  for (int u = threadIdx.x; u < c.n; u += blockDim.x) zbar[c.dual_start + u] = (double)tmp[u];
+}
+
+// ---- FETI-DP jump operators (Section 4.3) ---------------------------------------
+// B w: lambda_ab = w_a - w_b on the class block.
+__global__ void k_jump(const LamTask *__restrict__ lt, const PairTask *__restrict__ pairs, const double *__restrict__ w,
+                       double *__restrict__ lam, const int *__restrict__ done) {
+  if (done && *done) return;
+  const LamTask t = lt[blockIdx.y];
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= t.n) return;
+  lam[t.lam_off + u] = w[pairs[t.pa].ldual_off + u] - w[pairs[t.pb].ldual_off + u];
+}
+
+// B^T lambda: w_(j,C) = sum of +-lambda over the multipliers touching (j, C).
+__global__ void k_jump_t(const WTask *__restrict__ wt, const WEnt *__restrict__ ent, const double *__restrict__ lam,
+                         double *__restrict__ w, const int *__restrict__ done) {
+  if (done && *done) return;
+  const WTask t = wt[blockIdx.y];
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= t.n) return;
+  double acc = 0.0;
+  for (int k = t.ent_beg; k < t.ent_end; ++k) acc += ent[k].sign * lam[ent[k].lam_off + u];
+  w[t.ldual_off + u] = acc;
+}
+
+// B_D^T mu: w_(j,C) = (sum S)^-1 sum_{pairs} +-S_C^(partner) mu_pair.
+template <typename T>
+__global__ void k_jump_dt(const WTask *__restrict__ wt, const WEnt *__restrict__ ent, const T *__restrict__ blk,
+                          const T *__restrict__ sinv, const double *__restrict__ mu, double *__restrict__ w,
+                          const int *__restrict__ done) {
+  if (done && *done) return;
+  const WTask t = wt[blockIdx.x];
+  extern __shared__ unsigned char smem_raw[];
+  T *acc = reinterpret_cast<T *>(smem_raw);
+  T *mm = acc + t.n;
+  T *tmp = mm + t.n;
+  for (int u = threadIdx.x; u < t.n; u += blockDim.x) acc[u] = T(0);
+  __syncthreads();
+  for (int k = t.ent_beg; k < t.ent_end; ++k) {
+    const WEnt e = ent[k];
+    for (int u = threadIdx.x; u < t.n; u += blockDim.x) mm[u] = (T)mu[e.lam_off + u];
+    __syncthreads();
+    smem_gemv(blk + e.partner_blk_off, t.n, mm, tmp);
+    __syncthreads();
+    for (int u = threadIdx.x; u < t.n; u += blockDim.x) acc[u] += (e.sign > 0 ? tmp[u] : -tmp[u]);
+    __syncthreads();
+  }
+  smem_gemv(sinv + t.sinv_off, t.n, acc, tmp);
+  __syncthreads();
+  for (int u = threadIdx.x; u < t.n; u += blockDim.x) w[t.ldual_off + u] = (double)tmp[u];
+}
+
+// B_D y: mu_ab = S_C^(b) (sum S)^-1 y_a - S_C^(a) (sum S)^-1 y_b.
+template <typename T>
+__global__ void k_jump_d(const LamTask *__restrict__ lt, const PairTask *__restrict__ pairs, const T *__restrict__ blk,
+                         const T *__restrict__ sinv, const double *__restrict__ y, double *__restrict__ mu,
+                         const int *__restrict__ done) {
+  if (done && *done) return;
+  const LamTask t = lt[blockIdx.x];
+  extern __shared__ unsigned char smem_raw[];
+  T *ya = reinterpret_cast<T *>(smem_raw);
+  T *yb = ya + t.n;
+  T *ta = yb + t.n;
+  T *tb = ta + t.n;
+  T *oa = tb + t.n;
+  T *ob = oa + t.n;
+  const PairTask pa = pairs[t.pa], pb = pairs[t.pb];
+  for (int u = threadIdx.x; u < t.n; u += blockDim.x) {
+    ya[u] = (T)y[pa.ldual_off + u];
+    yb[u] = (T)y[pb.ldual_off + u];
+  }
+  __syncthreads();
+  smem_gemv(sinv + t.sinv_off, t.n, ya, ta);
+  smem_gemv(sinv + t.sinv_off, t.n, yb, tb);
+  __syncthreads();
+  smem_gemv(blk + pb.blk_off, t.n, ta, oa);
+  smem_gemv(blk + pa.blk_off, t.n, tb, ob);
+  __syncthreads();
+  for (int u = threadIdx.x; u < t.n; u += blockDim.x) mu[t.lam_off + u] = (double)oa[u] - (double)ob[u];
+}
+
+// Mean over the subdomains sharing each global dual dof (FETI-DP recovery).
+__global__ void k_dual_mean(const ClassTask *__restrict__ cls, const PairTask *__restrict__ pairs,
+                            const double *__restrict__ zD, double *__restrict__ zbar) {
+  const ClassTask c = cls[blockIdx.y];
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= c.n) return;
+  double acc = 0.0;
+  for (int p = c.pair_beg; p < c.pair_end; ++p) acc += zD[pairs[p].ldual_off + u];
+  zbar[c.dual_start + u] = acc / (double)(c.pair_end - c.pair_beg);
+}
+
+// ---- vector helpers ------------------------------------------------------------
+// Local interior vector of every subdomain from a global SoA pair (f_i, f_e):
+// v[off_j + 2a + f] = f_f[node of interior node a].
+__global__ void k_gather_pairs(int n, const int *__restrict__ node, const double *__restrict__ fi,
+                               const double *__restrict__ fe, double *__restrict__ v, double scale,
+                               const double *__restrict__ mult) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int x = node[t];
+  const double sc = mult ? scale / mult[t] : scale;
+  v[2 * t] = sc * fi[x];
+  v[2 * t + 1] = sc * fe[x];
+}
+
+// Global SoA pair from a nodal-interleaved vector: s_f[node[t]] = v[2t + f].
+__global__ void k_scatter_pairs(int n, const int *__restrict__ node, const double *__restrict__ v,
+                                double *__restrict__ si, double *__restrict__ se) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int x = node[t];
+  si[x] = v[2 * t];
+  se[x] = v[2 * t + 1];
+}
+
+// Local transformed vector gbar_j = T_loc^T g_j (CSC of T_loc by transformed
+// dof, flattened over subdomains); dual entries go to outD (local dual layout),
+// primal entries to outP (local primal layout).
+__global__ void k_tloc_t(int nt_total, const int *__restrict__ t_sub, const int *__restrict__ t_loc,
+                         const int *__restrict__ t_ptr, const int *__restrict__ t_row, const double *__restrict__ t_val,
+                         const int *__restrict__ g_off, const double *__restrict__ g, const int *__restrict__ nD,
+                         const int *__restrict__ ldual_off, const int *__restrict__ lprim_off,
+                         double *__restrict__ outD, double *__restrict__ outP) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt_total) return;
+  const int j = t_sub[t], a = t_loc[t];
+  double acc = 0.0;
+  for (int k = t_ptr[t]; k < t_ptr[t + 1]; ++k) acc += t_val[k] * g[g_off[j] + t_row[k]];
+  if (a < nD[j]) outD[ldual_off[j] + a] = acc;
+  else outP[lprim_off[j] + a - nD[j]] = acc;
+}
+
+// y[t] = x[idx[t]] * w[idx[t]] - y[t]
+__global__ void k_gather_scale_sub(int n, const int *__restrict__ idx, const double *__restrict__ x,
+                                   const double *__restrict__ w, double *__restrict__ y) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int g = idx[t];
+  y[t] = x[g] * w[g] - y[t];
+}
+
+__global__ void k_fill(int n, double *__restrict__ y, double v) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) y[t] = v;
+}
+
+__global__ void k_copy_vec(int n, const double *__restrict__ x, double *__restrict__ y, const int *__restrict__ done) {
+  if (done && *done) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) y[t] = x[t];
+}
+
+// y = a x + b y with scalars a, b (device doubles, optional)
+__global__ void k_axpby(int n, double a, const double *__restrict__ x, double b, double *__restrict__ y) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) y[t] = a * x[t] + b * y[t];
+}
+
+// ---- PCG recurrences (device scalars, early exit once converged) ---------------
+__global__ void k_pcg_start(KrylovState *__restrict__ ks, const double *__restrict__ dots) {
+  ks->rz = dots[0];
+  ks->zn0 = sqrt(fmax(dots[1], 0.0));
+  ks->zn = ks->zn0;
+  ks->tol = fmax(ks->rtol * ks->zn0, ks->atol);
+  ks->it = 0;
+  ks->reason = 0;
+  ks->done = (ks->zn0 <= ks->atol) ? 1 : 0;
+  if (!isfinite(ks->zn0)) { ks->done = 1; ks->reason = -6; }
+}
+
+__global__ void k_pcg_alpha(KrylovState *__restrict__ ks, const double *__restrict__ dots, double *__restrict__ hist_a) {
+  if (ks->done) return;
+  const double pq = dots[0];
+  ks->alpha = ks->rz / pq;
+  if (ks->it < ks->hist_cap) hist_a[ks->it] = ks->alpha;
+}
+
+__global__ void k_pcg_xr(int n, const KrylovState *__restrict__ ks, const double *__restrict__ p,
+                         const double *__restrict__ q, double *__restrict__ x, double *__restrict__ r) {
+  if (ks->done) return;
+  const double a = ks->alpha;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    x[t] += a * p[t];
+    r[t] -= a * q[t];
+  }
+}
+
+__global__ void k_pcg_beta(KrylovState *__restrict__ ks, const double *__restrict__ dots, double *__restrict__ hist_b) {
+  if (ks->done) return;
+  ks->it += 1;
+  const double zn = sqrt(fmax(dots[1], 0.0));
+  ks->zn = zn;
+  if (!isfinite(zn)) { ks->done = 1; ks->reason = -6; return; }
+  if (zn <= ks->tol) { ks->done = 1; ks->reason = 0; return; }
+  if (zn > ks->dtol * ks->zn0) { ks->done = 1; ks->reason = -4; return; }
+  if (ks->it >= ks->maxit) { ks->done = 1; ks->reason = -3; return; }
+  ks->beta = dots[0] / ks->rz;
+  if (ks->it - 1 < ks->hist_cap) hist_b[ks->it - 1] = ks->beta;
+  ks->rz = dots[0];
+}
+
+__global__ void k_pcg_p(int n, const KrylovState *__restrict__ ks, const double *__restrict__ z, double *__restrict__ p) {
+  if (ks->done) return;
+  const double b = ks->beta;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) p[t] = z[t] + b * p[t];
+}
+
+// dots with an early exit (Krylov loop): partial sums then a fixed-order finalize
+__global__ void k_dot2_done(int n, const double *__restrict__ a0, const double *__restrict__ b0,
+                            const double *__restrict__ a1, const double *__restrict__ b1,
+                            double *__restrict__ partial, const int *__restrict__ done) {
+  if (done && *done) return;
+  __shared__ double sh[32];
+  double s0 = 0.0, s1 = 0.0;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+    s0 += a0[x] * b0[x];
+    if (a1) s1 += a1[x] * b1[x];
+  }
+  s0 = block_sum(s0, sh);
+  s1 = block_sum(s1, sh);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = s0;
+    partial[2 * blockIdx.x + 1] = s1;
+  }
+}
+
+__global__ void k_finalize2_done(int nblk, const double *__restrict__ partial, double *__restrict__ out,
+                                 const int *__restrict__ done) {
+  if (done && *done) return;
+  __shared__ double sh[32];
+  for (int c = 0; c < 2; ++c) {
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) v += partial[2 * b + c];
+    v = block_sum(v, sh);
+    if (threadIdx.x == 0) out[c] = v;
+  }
+}
+
+// ---- launchers -------------------------------------------------------------------
+#define GRID1(n) ceil_div((n), 256), 256, 0, s
+
+template <typename T>
+void launch_assemble_local(int nq, const int *q_sub, const int *q_loc, const int *q_node, const int *nbr,
+                           const double *stencil, const double *mass, const double *factor, double tau,
+                           const MatDesc *desc, T *base, cudaStream_t s) {
+  const long long tot = (long long)nq * 27;
+  k_assemble_local<T><<<(int)((tot + 255) / 256), 256, 0, s>>>(nq, q_sub, q_loc, q_node, nbr, stencil, mass, factor,
+                                                             tau, desc, base);
+}
+
+template <typename TS, typename TD>
+void launch_copy(int ntasks, long long max_elems, const CopyTask *tasks, const TS *src, TD *dst, cudaStream_t s) {
+  if (ntasks == 0 || max_elems == 0) return;
+  const int gx = (int)std::min<long long>((max_elems + 255) / 256, 4096);
+  k_copy<TS, TD><<<dim3(gx, ntasks), 256, 0, s>>>(tasks, src, dst);
+}
+
+template <typename T>
+void launch_build_aug(int nsub, long long max_elems, const MatDesc *kdesc, const T *kbase, const MatDesc *adesc,
+                      T *abase, const int *nI, const int *nD, const int *tptr_off, const int *tptr,
+                      const int *trow, const double *tval, cudaStream_t s) {
+  const int gx = (int)std::min<long long>((max_elems + 255) / 256, 8192);
+  k_build_aug<T><<<dim3(gx, nsub), 256, 0, s>>>(kdesc, kbase, adesc, abase, nI, nD, tptr_off, tptr, trow, tval);
+}
+
+template <typename T>
+void launch_class_aug(int ncls, int max_n, const ClassTask *cls, const PairTask *pairs, const T *blk,
+                      const MatDesc *cdesc, T *cbase, cudaStream_t s) {
+  if (ncls == 0) return;
+  const int gx = std::max(1, std::min(ceil_div(4 * max_n * max_n, 256), 1024));
+  k_class_aug<T><<<dim3(gx, ncls), 256, 0, s>>>(cls, pairs, blk, cdesc, cbase);
+}
+
+template <typename T>
+void launch_coarse_aug(int np, int gauge, const int *ptr, const long long *src, const T *abase, double *co, int ld,
+                       cudaStream_t s) {
+  const long long tot = 4LL * np * np;
+  const int gx = (int)std::min<long long>((tot + 255) / 256, 8192);
+  k_coarse_aug<T><<<std::max(gx, 1), 256, 0, s>>>(np, gauge, ptr, src, abase, co, ld);
+}
+
+void launch_spmv(int n, const int *ptr, const int *col, const double *val, const double *x, double *y, int zero,
+                 const int *done, cudaStream_t s) {
+  if (n == 0) return;
+  k_spmv<<<GRID1(n)>>>(n, ptr, col, val, x, y, zero, done);
+}
+
+void launch_gather_sum(int n, const int *ptr, const int *idx, const double *src, double *y, int zero, double alpha,
+                       const double *addend, const int *done, cudaStream_t s) {
+  if (n == 0) return;
+  k_gather_sum<<<GRID1(n)>>>(n, ptr, idx, src, y, zero, alpha, addend, done);
+}
+
+template <typename T>
+void launch_deluxe_restrict(int ncls, int max_n, const ClassTask *cls, const PairTask *pairs, const T *blk,
+                            const T *sinv, const double *rbar, double *rD, const int *done, cudaStream_t s) {
+  if (ncls == 0) return;
+  k_deluxe_restrict<T><<<ncls, 256, 3 * sizeof(T) * max_n, s>>>(cls, pairs, blk, sinv, rbar, rD, done);
+}
+
+template <typename T>
+void launch_deluxe_extend(int ncls, int max_n, const ClassTask *cls, const PairTask *pairs, const T *blk,
+                          const T *sinv, const double *zD, double *zbar, const int *done, cudaStream_t s) {
+  if (ncls == 0) return;
+  k_deluxe_extend<T><<<ncls, 256, 3 * sizeof(T) * max_n, s>>>(cls, pairs, blk, sinv, zD, zbar, done);
+}
+
+void launch_jump(int nlt, int max_n, const LamTask *lt, const PairTask *pairs, const double *w, double *lam,
+                 const int *done, cudaStream_t s) {
+  if (nlt == 0) return;
+  k_jump<<<dim3(ceil_div(max_n, 128), nlt), 128, 0, s>>>(lt, pairs, w, lam, done);
+}
+
+void launch_jump_t(int nwt, int max_n, const WTask *wt, const WEnt *ent, const double *lam, double *w,
+                   const int *done, cudaStream_t s) {
+  if (nwt == 0) return;
+  k_jump_t<<<dim3(ceil_div(max_n, 128), nwt), 128, 0, s>>>(wt, ent, lam, w, done);
+}
+
+template <typename T>
+void launch_jump_dt(int nwt, int max_n, const WTask *wt, const WEnt *ent, const T *blk, const T *sinv,
+                    const double *mu, double *w, const int *done, cudaStream_t s) {
+  if (nwt == 0) return;
+  k_jump_dt<T><<<nwt, 256, 3 * sizeof(T) * max_n, s>>>(wt, ent, blk, sinv, mu, w, done);
+}
+
+template <typename T>
+void launch_jump_d(int nlt, int max_n, const LamTask *lt, const PairTask *pairs, const T *blk, const T *sinv,
+                   const double *y, double *mu, const int *done, cudaStream_t s) {
+  if (nlt == 0) return;
+  k_jump_d<T><<<nlt, 256, 6 * sizeof(T) * max_n, s>>>(lt, pairs, blk, sinv, y, mu, done);
+}
+
+void launch_dual_mean(int ncls, int max_n, const ClassTask *cls, const PairTask *pairs, const double *zD,
+                      double *zbar, cudaStream_t s) {
+  if (ncls == 0) return;
+  k_dual_mean<<<dim3(ceil_div(max_n, 128), ncls), 128, 0, s>>>(cls, pairs, zD, zbar);
+}
+
+void launch_gather_pairs(int n, const int *node, const double *fi, const double *fe, double *v, double scale,
+                         const double *mult, cudaStream_t s) {
+  if (n == 0) return;
+  k_gather_pairs<<<GRID1(n)>>>(n, node, fi, fe, v, scale, mult);
+}
+
+void launch_scatter_pairs(int n, const int *node, const double *v, double *si, double *se, cudaStream_t s) {
+  if (n == 0) return;
+  k_scatter_pairs<<<GRID1(n)>>>(n, node, v, si, se);
+}
+
+void launch_tloc_t(int nt, const int *t_sub, const int *t_loc, const int *t_ptr, const int *t_row,
+                   const double *t_val, const int *g_off, const double *g, const int *nD, const int *ldual_off,
+                   const int *lprim_off, double *outD, double *outP, cudaStream_t s) {
+  if (nt == 0) return;
+  k_tloc_t<<<GRID1(nt)>>>(nt, t_sub, t_loc, t_ptr, t_row, t_val, g_off, g, nD, ldual_off, lprim_off, outD, outP);
+}
+
+void launch_gather_scale_sub(int n, const int *idx, const double *x, const double *w, double *y, cudaStream_t s) {
+  if (n == 0) return;
+  k_gather_scale_sub<<<GRID1(n)>>>(n, idx, x, w, y);
+}
+
+void launch_fill(int n, double *y, double v, cudaStream_t s) {
+  if (n == 0) return;
+  k_fill<<<GRID1(n)>>>(n, y, v);
+}
+
+void launch_copy_vec(int n, const double *x, double *y, const int *done, cudaStream_t s) {
+  if (n == 0) return;
+  k_copy_vec<<<GRID1(n)>>>(n, x, y, done);
+}
+
+void launch_axpby(int n, double a, const double *x, double b, double *y, cudaStream_t s) {
+  if (n == 0) return;
+  k_axpby<<<GRID1(n)>>>(n, a, x, b, y);
+}
+
+void launch_pcg_start(KrylovState *ks, const double *dots, cudaStream_t s) { k_pcg_start<<<1, 1, 0, s>>>(ks, dots); }
+void launch_pcg_alpha(KrylovState *ks, const double *dots, double *ha, cudaStream_t s) {
+  k_pcg_alpha<<<1, 1, 0, s>>>(ks, dots, ha);
+}
+void launch_pcg_beta(KrylovState *ks, const double *dots, double *hb, cudaStream_t s) {
+  k_pcg_beta<<<1, 1, 0, s>>>(ks, dots, hb);
+}
+void launch_pcg_xr(int n, const KrylovState *ks, const double *p, const double *q, double *x, double *r,
+                   cudaStream_t s) {
+  k_pcg_xr<<<std::max(1, std::min(ceil_div(n, 256), kRedBlocks)), 256, 0, s>>>(n, ks, p, q, x, r);
+}
+void launch_pcg_p(int n, const KrylovState *ks, const double *z, double *p, cudaStream_t s) {
+  k_pcg_p<<<std::max(1, std::min(ceil_div(n, 256), kRedBlocks)), 256, 0, s>>>(n, ks, z, p);
+}
+void launch_dot2(int n, const double *a0, const double *b0, const double *a1, const double *b1, double *partial,
+                 double *out, const int *done, cudaStream_t s) {
+  k_dot2_done<<<kRedBlocks, 256, 0, s>>>(n, a0, b0, a1, b1, partial, done);
+  k_finalize2_done<<<1, 256, 0, s>>>(kRedBlocks, partial, out, done);
+}
+
+#define BD_DD_INST(T)                                                                                           \
+  template void launch_assemble_local<T>(int, const int *, const int *, const int *, const int *, const double *, \
+                                         const double *, const double *, double, const MatDesc *, T *,         \
+                                         cudaStream_t);                                                        \
+  template void launch_build_aug<T>(int, long long, const MatDesc *, const T *, const MatDesc *, T *,           \
+                                    const int *, const int *, const int *, const int *, const int *,            \
+                                    const double *, cudaStream_t);                                             \
+  template void launch_class_aug<T>(int, int, const ClassTask *, const PairTask *, const T *, const MatDesc *,  \
+                                    T *, cudaStream_t);                                                        \
+  template void launch_coarse_aug<T>(int, int, const int *, const long long *, const T *, double *, int,        \
+                                     cudaStream_t);                                                            \
+  template void launch_deluxe_restrict<T>(int, int, const ClassTask *, const PairTask *, const T *, const T *,  \
+                                          const double *, double *, const int *, cudaStream_t);                \
+  template void launch_deluxe_extend<T>(int, int, const ClassTask *, const PairTask *, const T *, const T *,    \
+                                        const double *, double *, const int *, cudaStream_t);                  \
+  template void launch_jump_dt<T>(int, int, const WTask *, const WEnt *, const T *, const T *, const double *,  \
+                                  double *, const int *, cudaStream_t);                                        \
+  template void launch_jump_d<T>(int, int, const LamTask *, const PairTask *, const T *, const T *,             \
+                                 const double *, double *, const int *, cudaStream_t);                         \
+  template void launch_copy<T, T>(int, long long, const CopyTask *, const T *, T *, cudaStream_t);
+BD_DD_INST(float)
+BD_DD_INST(double)
+template void launch_copy<float, double>(int, long long, const CopyTask *, const float *, double *, cudaStream_t);
+template void launch_copy<double, float>(int, long long, const CopyTask *, const double *, float *, cudaStream_t);
+
+}  // namespace bd

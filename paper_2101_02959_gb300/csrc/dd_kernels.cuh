@@ -1,0 +1,73 @@
+// Launchers of the domain-decomposition kernels (dd.cu).
+#pragma once
+#include "kernels.cuh"
+#include "tasks.h"
+
+namespace bd {
+
+// Device-resident Krylov scalars; every kernel of an iteration returns at once
+// when `done` is set, so iterations can be enqueued ahead of the convergence test.
+struct KrylovState {
+  double rz, alpha, beta, zn, zn0, tol;
+  double rtol, atol, dtol;
+  int it, done, reason, maxit, hist_cap, pad;
+};
+
+template <typename T>
+void launch_assemble_local(int nq, const int *q_sub, const int *q_loc, const int *q_node, const int *nbr,
+                           const double *stencil, const double *mass, const double *factor, double tau,
+                           const MatDesc *desc, T *base, cudaStream_t s);
+template <typename TS, typename TD>
+void launch_copy(int ntasks, long long max_elems, const CopyTask *tasks, const TS *src, TD *dst, cudaStream_t s);
+template <typename T>
+void launch_build_aug(int nsub, long long max_elems, const MatDesc *kdesc, const T *kbase, const MatDesc *adesc,
+                      T *abase, const int *nI, const int *nD, const int *tptr_off, const int *tptr,
+                      const int *trow, const double *tval, cudaStream_t s);
+template <typename T>
+void launch_class_aug(int ncls, int max_n, const ClassTask *cls, const PairTask *pairs, const T *blk,
+                      const MatDesc *cdesc, T *cbase, cudaStream_t s);
+template <typename T>
+void launch_coarse_aug(int np, int gauge, const int *ptr, const long long *src, const T *abase, double *co, int ld,
+                       cudaStream_t s);
+void launch_spmv(int n, const int *ptr, const int *col, const double *val, const double *x, double *y, int zero,
+                 const int *done, cudaStream_t s);
+void launch_gather_sum(int n, const int *ptr, const int *idx, const double *src, double *y, int zero, double alpha,
+                       const double *addend, const int *done, cudaStream_t s);
+template <typename T>
+void launch_deluxe_restrict(int ncls, int max_n, const ClassTask *cls, const PairTask *pairs, const T *blk,
+                            const T *sinv, const double *rbar, double *rD, const int *done, cudaStream_t s);
+template <typename T>
+void launch_deluxe_extend(int ncls, int max_n, const ClassTask *cls, const PairTask *pairs, const T *blk,
+                          const T *sinv, const double *zD, double *zbar, const int *done, cudaStream_t s);
+void launch_jump(int nlt, int max_n, const LamTask *lt, const PairTask *pairs, const double *w, double *lam,
+                 const int *done, cudaStream_t s);
+void launch_jump_t(int nwt, int max_n, const WTask *wt, const WEnt *ent, const double *lam, double *w,
+                   const int *done, cudaStream_t s);
+template <typename T>
+void launch_jump_dt(int nwt, int max_n, const WTask *wt, const WEnt *ent, const T *blk, const T *sinv,
+                    const double *mu, double *w, const int *done, cudaStream_t s);
+template <typename T>
+void launch_jump_d(int nlt, int max_n, const LamTask *lt, const PairTask *pairs, const T *blk, const T *sinv,
+                   const double *y, double *mu, const int *done, cudaStream_t s);
+void launch_dual_mean(int ncls, int max_n, const ClassTask *cls, const PairTask *pairs, const double *zD,
+                      double *zbar, cudaStream_t s);
+void launch_gather_pairs(int n, const int *node, const double *fi, const double *fe, double *v, double scale,
+                         const double *mult, cudaStream_t s);
+void launch_scatter_pairs(int n, const int *node, const double *v, double *si, double *se, cudaStream_t s);
+void launch_tloc_t(int nt, const int *t_sub, const int *t_loc, const int *t_ptr, const int *t_row,
+                   const double *t_val, const int *g_off, const double *g, const int *nD, const int *ldual_off,
+                   const int *lprim_off, double *outD, double *outP, cudaStream_t s);
+void launch_gather_scale_sub(int n, const int *idx, const double *x, const double *w, double *y, cudaStream_t s);
+void launch_fill(int n, double *y, double v, cudaStream_t s);
+void launch_copy_vec(int n, const double *x, double *y, const int *done, cudaStream_t s);
+void launch_axpby(int n, double a, const double *x, double b, double *y, cudaStream_t s);
+void launch_pcg_start(KrylovState *ks, const double *dots, cudaStream_t s);
+void launch_pcg_alpha(KrylovState *ks, const double *dots, double *ha, cudaStream_t s);
+void launch_pcg_beta(KrylovState *ks, const double *dots, double *hb, cudaStream_t s);
+void launch_pcg_xr(int n, const KrylovState *ks, const double *p, const double *q, double *x, double *r,
+                   cudaStream_t s);
+void launch_pcg_p(int n, const KrylovState *ks, const double *z, double *p, cudaStream_t s);
+void launch_dot2(int n, const double *a0, const double *b0, const double *a1, const double *b1, double *partial,
+                 double *out, const int *done, cudaStream_t s);
+
+}  // namespace bd

@@ -1,0 +1,350 @@
+// Batched dense kernels: partial Cholesky engine, GEMV, triangular solves.
+//
+// The engine is a right-looking blocked Cholesky restricted to the first e
+// columns of each matrix, followed by one long-K symmetric rank-e update of
+// the trailing block.  With K = [[K_II, K_IG], [K_GI, K_GG]] and e = n_I this
+// yields L_II, L_GI and the local Schur complement S_Gamma = K_GG - L_GI L_GI^T
+// (static condensation, Section 4.1).  With the augmented matrix
+// [[S_DD, S_DP, I], [S_PD, S_PP, 0], [I, 0, 0]] and e = n_D it yields, in the
+// trailing block, S_PP - S_PD S_DD^-1 S_DP (the local coarse matrix of
+// Section 4.4), -S_DD^-1 S_DP and -S_DD^-1 (the local constrained solve).
+#include <algorithm>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace bd {
+
+template <typename T> __device__ inline T dsqrt(T v);
+template <> __device__ inline float dsqrt<float>(float v) { return sqrtf(v); }
+template <> __device__ inline double dsqrt<double>(double v) { return sqrt(v); }
+
+// ---- panel step 1: factor the w x w diagonal block in place (one warp per matrix)
+template <typename T>
+__global__ void __launch_bounds__(32) k_potrf(const MatDesc *__restrict__ desc, T *__restrict__ base, int k0,
+                                              int *__restrict__ err) {
+  const MatDesc d = desc[blockIdx.x];
+  if (k0 >= d.e) return;
+  const int w = min(kNB, d.e - k0);
+  T *A = base + d.off;
+  __shared__ T Ls[kNB][kNB + 1];
+  const int r = threadIdx.x;
+  for (int c = 0; c < kNB; ++c) Ls[r][c] = (r < w && c <= r) ? A[(long long)(k0 + r) * d.ld + k0 + c] : T(0);
+  __syncwarp();
+  for (int c = 0; c < w; ++c) {
+    T dg = Ls[c][c];
+    const bool bad = !(dg > T(0));
+    if (bad) dg = T(1);
+    const T sq = dsqrt(dg);
+    __syncwarp();
+    if (r == c) {
+      Ls[c][c] = sq;
+      if (bad) atomicOr(err, DEV_ERR_NOT_SPD);
+    }
+    if (r > c && r < w) Ls[r][c] /= sq;
+    __syncwarp();
+    if (r > c && r < w) {
+      const T lrc = Ls[r][c];
+      for (int t = c + 1; t <= r; ++t) Ls[r][t] -= lrc * Ls[t][c];
+    }
+    __syncwarp();
+  }
+  if (r < w)
+    for (int c = 0; c <= r; ++c) A[(long long)(k0 + r) * d.ld + k0 + c] = Ls[r][c];
+}
+
+// ---- panel step 2: rows below the diagonal block, x L_kk^T = a (one thread per row)
+template <typename T>
+__global__ void __launch_bounds__(128) k_trsm(const MatDesc *__restrict__ desc, T *__restrict__ base, int k0) {
+  const MatDesc d = desc[blockIdx.y];
+  if (k0 >= d.e) return;
+  const int w = min(kNB, d.e - k0);
+  if (k0 + w + blockIdx.x * 128 >= d.m) return;
+  T *A = base + d.off;
+  __shared__ T Ls[kNB][kNB + 1];
+  for (int t = threadIdx.x; t < kNB * kNB; t += 128) {
+    const int r = t / kNB, c = t % kNB;
+    Ls[r][c] = (r < w && c <= r) ? A[(long long)(k0 + r) * d.ld + k0 + c] : T(0);
+  }
+  __syncthreads();
+  const int row = k0 + w + blockIdx.x * 128 + threadIdx.x;
+  if (row >= d.m) return;
+  T *a = A + (long long)row * d.ld + k0;
+  T x[kNB];
+#pragma unroll
+  for (int c = 0; c < kNB; ++c) x[c] = (c < w) ? a[c] : T(0);
+#pragma unroll
+  for (int c = 0; c < kNB; ++c) {
+    if (c < w) {
+      T v = x[c];
+#pragma unroll
+      for (int t = 0; t < c; ++t) v -= x[t] * Ls[c][t];
+      x[c] = v / Ls[c][c];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < kNB; ++c)
+    if (c < w) a[c] = x[c];
+}
+
+// ---- rank-k update of lower tiles --------------------------------------------
+// mode 0 (panel): rows [k0+w, m), cols [k0+w, e), K = panel [k0, k0+w)
+// mode 1 (final): rows [e, m),    cols [e, m),    K = [0, e)
+// C[r][c] -= sum_k A[r][k] A[c][k]; 64x64 tiles, 256 threads, 4x4 per thread.
+constexpr int kTB = 64, kKC = 32;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_rankk(const MatDesc *__restrict__ desc, T *__restrict__ base, int mode,
+                                               int k0, int nct) {
+  const MatDesc d = desc[blockIdx.y];
+  int row0, colend, kb, ke;
+  if (mode == 0) {
+    if (k0 >= d.e) return;
+    const int w = min(kNB, d.e - k0);
+    row0 = k0 + w;
+    colend = d.e;
+    kb = k0;
+    ke = k0 + w;
+  } else {
+    row0 = d.e;
+    colend = d.m;
+    kb = 0;
+    ke = d.e;
+  }
+  const int ti = blockIdx.x / nct, tj = blockIdx.x % nct;
+  if (tj > ti) return;
+  const int r0 = row0 + ti * kTB, c0 = row0 + tj * kTB;
+  if (r0 >= d.m || c0 >= colend || ke <= kb) return;
+  T *A = base + d.off;
+  __shared__ T As[kKC][kTB + 4];
+  __shared__ T Bs[kKC][kTB + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  const int lr = tid >> 2, lk = (tid & 3) * 8;
+  for (int kk = kb; kk < ke; kk += kKC) {
+    {
+      const int ra = r0 + lr, rb = c0 + lr;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int k = kk + lk + q;
+        As[lk + q][lr] = (ra < d.m && k < ke) ? A[(long long)ra * d.ld + k] : T(0);
+        Bs[lk + q][lr] = (rb < colend && k < ke) ? A[(long long)rb * d.ld + k] : T(0);
+      }
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < kKC; ++k) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[k][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[k][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + ty + 16 * i;
+    if (r >= d.m) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + tx + 16 * j;
+      if (c < colend) A[(long long)r * d.ld + c] -= acc[i][j];
+    }
+  }
+}
+
+template <typename T>
+void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s) {
+  if (sh.count == 0) return;
+  for (int k0 = 0; k0 < sh.max_e; k0 += kNB) {
+    int max_below = 0, max_rt = 0, max_ct = 0;
+    for (int b = 0; b < sh.count; ++b) {
+      if (k0 >= sh.e[b]) continue;
+      const int w = std::min(kNB, sh.e[b] - k0);
+      const int below = sh.m[b] - k0 - w;
+      max_below = std::max(max_below, below);
+      max_rt = std::max(max_rt, ceil_div(below, kTB));
+      max_ct = std::max(max_ct, ceil_div(sh.e[b] - k0 - w, kTB));
+    }
+    k_potrf<T><<<sh.count, 32, 0, s>>>(d_desc, base, k0, d_err);
+    if (max_below > 0) {
+      dim3 gp(ceil_div(max_below, 128), sh.count);
+      k_trsm<T><<<gp, 128, 0, s>>>(d_desc, base, k0);
+    }
+    if (max_rt > 0 && max_ct > 0) {
+      dim3 gu(max_rt * max_ct, sh.count);
+      k_rankk<T><<<gu, 256, 0, s>>>(d_desc, base, 0, k0, max_ct);
+    }
+  }
+  int max_t = 0;
+  for (int b = 0; b < sh.count; ++b) max_t = std::max(max_t, ceil_div(sh.m[b] - sh.e[b], kTB));
+  if (max_t > 0) {
+    dim3 gf(max_t * max_t, sh.count);
+    k_rankk<T><<<gf, 256, 0, s>>>(d_desc, base, 1, 0, max_t);
+  }
+}
+
+// ---- batched GEMV ------------------------------------------------------------
+// One CTA (8 warps) per (task, block of 64 rows); x staged in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemv(const GemvDesc *__restrict__ tasks, const T *__restrict__ A,
+                                              const double *__restrict__ x, const int *__restrict__ xidx,
+                                              double *__restrict__ y, double alpha, const int *__restrict__ done) {
+  if (done && *done) return;
+  const GemvDesc t = tasks[blockIdx.y];
+  const int rbeg = blockIdx.x * 64;
+  if (rbeg >= t.rows) return;
+  extern __shared__ unsigned char smem_raw[];
+  T *xs = reinterpret_cast<T *>(smem_raw);
+  for (int c = threadIdx.x; c < t.cols; c += blockDim.x)
+    xs[c] = (T)((t.flags & 1) ? x[xidx[t.x_off + c]] : x[t.x_off + c]);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int rend = min(t.rows, rbeg + 64);
+  for (int r = rbeg + wid; r < rend; r += 8) {
+    const T *row = A + t.a_off + (long long)r * t.ld;
+    T acc = T(0);
+    for (int c = lane; c < t.cols; c += 32) acc += row[c] * xs[c];
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      const double v = alpha * (double)acc;
+      y[t.y_off + r] = (t.flags & 2) ? y[t.y_off + r] + v : v;
+    }
+  }
+}
+
+// y[a] = (acc ? y[a] : 0) + alpha sum_p A[p][a] x[p]; one thread per column a.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemv_t(const GemvDesc *__restrict__ tasks, const T *__restrict__ A,
+                                                const double *__restrict__ x, const int *__restrict__ xidx,
+                                                double *__restrict__ y, double alpha, const int *__restrict__ done) {
+  if (done && *done) return;
+  const GemvDesc t = tasks[blockIdx.y];
+  extern __shared__ unsigned char smem_raw[];
+  T *xs = reinterpret_cast<T *>(smem_raw);
+  for (int p = threadIdx.x; p < t.rows; p += blockDim.x)
+    xs[p] = (T)((t.flags & 1) ? x[xidx[t.x_off + p]] : x[t.x_off + p]);
+  __syncthreads();
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= t.cols) return;
+  T acc = T(0);
+  for (int p = 0; p < t.rows; ++p) acc += A[t.a_off + (long long)p * t.ld + a] * xs[p];
+  const double v = alpha * (double)acc;
+  y[t.y_off + a] = (t.flags & 2) ? y[t.y_off + a] + v : v;
+}
+
+template <typename T>
+void launch_gemv(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks, const T *A, const double *x,
+                 const int *xidx, double *y, double alpha, const int *done, cudaStream_t s) {
+  if (ntasks == 0 || max_rows == 0) return;
+  dim3 g(ceil_div(max_rows, 64), ntasks);
+  const size_t sm = sizeof(T) * (size_t)std::max(1, max_cols);
+  k_gemv<T><<<g, 256, sm, s>>>(d_tasks, A, x, xidx, y, alpha, done);
+}
+
+template <typename T>
+void launch_gemv_t(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks, const T *A, const double *x,
+                   const int *xidx, double *y, double alpha, const int *done, cudaStream_t s) {
+  if (ntasks == 0 || max_cols == 0) return;
+  dim3 g(ceil_div(max_cols, 256), ntasks);
+  const size_t sm = sizeof(T) * (size_t)std::max(1, max_rows);
+  k_gemv_t<T><<<g, 256, sm, s>>>(d_tasks, A, x, xidx, y, alpha, done);
+}
+
+// ---- batched triangular solves (one CTA per matrix) ---------------------------
+// lower: y = L^-1 b, left-looking over 32-row blocks; upper: y = L^-T b,
+// right-to-left over 32-row blocks.  The vector lives in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(256) k_trsv(const MatDesc *__restrict__ desc, const int *__restrict__ vec_off,
+                                              const T *__restrict__ base, const double *__restrict__ b,
+                                              double *__restrict__ y, int transpose) {
+  const MatDesc d = desc[blockIdx.x];
+  const int n = d.e;
+  const T *L = base + d.off;
+  extern __shared__ unsigned char smem_raw[];
+  T *v = reinterpret_cast<T *>(smem_raw);
+  __shared__ T part[8][32];
+  const int off = vec_off[blockIdx.x];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = (T)b[off + i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nblk = ceil_div(n, 32);
+  for (int q = 0; q < nblk; ++q) {
+    const int bk = transpose ? nblk - 1 - q : q;
+    const int r0 = bk * 32, r1 = min(n, r0 + 32);
+    if (!transpose) {
+      // v[r] -= sum_{c < r0} L[r][c] v[c] for r in the block (warps share rows)
+      for (int r = r0 + wid; r < r1; r += 8) {
+        T acc = T(0);
+        for (int c = lane; c < r0; c += 32) acc += L[(long long)r * d.ld + c] * v[c];
+        acc = warp_sum(acc);
+        if (lane == 0) v[r] -= acc;
+      }
+      __syncthreads();
+      if (wid == 0) {
+        const int r = r0 + lane;
+        T vr = (r < r1) ? v[r] : T(0);
+        for (int c = r0; c < r1; ++c) {
+          const T xc = __shfl_sync(0xffffffffu, vr / ((r == c) ? L[(long long)r * d.ld + r] : T(1)), c - r0);
+          if (r == c) vr = xc;
+          else if (r > c && r < r1) vr -= L[(long long)r * d.ld + c] * xc;
+        }
+        if (r < r1) v[r] = vr;
+      }
+      __syncthreads();
+    } else {
+      // v[r] -= sum_{c >= r1} L[c][r] v[c] for r in the block
+      T acc = T(0);
+      for (int c = r1 + wid; c < n; c += 8) {
+        const int r = r0 + lane;
+        if (r < r1) acc += L[(long long)c * d.ld + r] * v[c];
+      }
+      part[wid][lane] = acc;
+      __syncthreads();
+      if (wid == 0) {
+        const int r = r0 + lane;
+        T s = T(0);
+        for (int k = 0; k < 8; ++k) s += part[k][lane];
+        T vr = (r < r1) ? v[r] - s : T(0);
+        for (int c = r1 - 1; c >= r0; --c) {
+          const T xc = __shfl_sync(0xffffffffu, vr / ((r == c) ? L[(long long)r * d.ld + r] : T(1)), c - r0);
+          if (r == c) vr = xc;
+          else if (r < c && r < r1) vr -= L[(long long)c * d.ld + r] * xc;
+        }
+        if (r < r1) v[r] = vr;
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) y[off + i] = (double)v[i];
+}
+
+template <typename T>
+void launch_trsv(int count, int max_n, const MatDesc *d_desc, const int *vec_off, const T *base, const double *b,
+                 double *y, bool transpose, cudaStream_t s) {
+  if (count == 0) return;
+  const size_t sm = sizeof(T) * (size_t)std::max(1, max_n);
+  k_trsv<T><<<count, 256, sm, s>>>(d_desc, vec_off, base, b, y, transpose ? 1 : 0);
+}
+
+#define BD_INST(T)                                                                                              \
+  template void engine_partial_cholesky<T>(const EngineShape &, const MatDesc *, T *, int *, cudaStream_t);     \
+  template void launch_gemv<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *,        \
+                               double *, double, const int *, cudaStream_t);                                   \
+  template void launch_gemv_t<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *,      \
+                                 double *, double, const int *, cudaStream_t);                                 \
+  template void launch_trsv<T>(int, int, const MatDesc *, const int *, const T *, const double *, double *,    \
+                               bool, cudaStream_t);
+BD_INST(float)
+BD_INST(double)
+
+}  // namespace bd

@@ -1,0 +1,66 @@
+// Kernel launchers of the Bidomain GB300 library (host-callable).
+#pragma once
+#include <vector>
+
+#include "common.cuh"
+
+namespace bd {
+
+constexpr int kRedBlocks = 304;  // fixed reduction grid (2 x 152 SMs): deterministic sums
+constexpr int kNB = 32;          // panel width of the partial Cholesky
+
+struct FemParams {
+  double sigma_i[3], sigma_e[3];
+  double G, eta1, eta2, vth, vp, chi_cm, tau;
+};
+
+struct StimParams {
+  int active;
+  double amp;
+  double box[6];
+  double h[3];
+};
+
+// fem.cu
+void launch_element_matrices(int ne, const int *elem_ijk, const double h[3], double lz, const FemParams &fp,
+                             double *Ke, cudaStream_t s);
+void launch_stencil_gather(int nrows, const int *row_node, const int *row_sub, const int *node_ijk,
+                           const int *elem_grid, const int *elem_sub, const int n[3], const double *Ke,
+                           double *out, int soa_stride, cudaStream_t s);
+void launch_gating(int n, const double *ui, const double *ue, const double *w, double *wn, const FemParams &p,
+                   cudaStream_t s);
+void launch_residual(int n, const double *stencil, const int *nbr, const double *mass, const int *node_ijk,
+                     const double *ui0, const double *ue0, const double *si, const double *se, double lam,
+                     const double *wn, const double *uin, const double *uen, const FemParams &p,
+                     const StimParams &st, double *ri, double *re, double *factor, double *ui_out,
+                     double *ue_out, double *partial, double *norm2, cudaStream_t s);
+void launch_dot3(int n, const double *a0, const double *b0, const double *a1, const double *b1, const double *a2,
+                 const double *b2, double *partial, double *out, cudaStream_t s);
+void launch_gauge_shift(int n, double *ui, double *ue, const double *scal, cudaStream_t s);
+
+// dense.cu -- batched partial Cholesky: eliminates the first e columns of every
+// matrix; afterwards the trailing (m-e) x (m-e) lower triangle holds the Schur
+// complement A22 - A21 A11^-1 A12 and the first e columns hold L11 and L21.
+struct EngineShape {
+  int count;
+  int max_e, max_m;
+  std::vector<int> m, e;  // host copies for per-step grid sizes
+};
+template <typename T>
+void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s);
+
+// y = alpha * A x (+ y): tasks in d_tasks (GemvDesc); x gathered through xidx when flagged.
+template <typename T>
+void launch_gemv(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks, const T *A, const double *x,
+                 const int *xidx, double *y, double alpha, const int *done, cudaStream_t s);
+// y[a] = (accumulate ? y[a] : 0) + alpha * sum_p A[p][a] x[p]  (x gathered through xidx when flagged)
+template <typename T>
+void launch_gemv_t(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks, const T *A, const double *x,
+                   const int *xidx, double *y, double alpha, const int *done, cudaStream_t s);
+// Batched triangular solves with the leading n x n lower triangles (MatDesc.e = n):
+// y = L^-1 b (lower) or y = L^-T b (upper); b and y are concatenated vectors at vec_off[b].
+template <typename T>
+void launch_trsv(int count, int max_n, const MatDesc *d_desc, const int *vec_off, const T *base, const double *b,
+                 double *y, bool transpose, cudaStream_t s);
+
+}  // namespace bd

@@ -1,0 +1,184 @@
+"""GPU parity: every step of the path through the C-ABI against the CPU oracle.
+
+Tolerances (relative, in the 2-norm unless stated):
+  pointwise kernels (gating, residual)            1e-12
+  operator applications (S_hat, BDDC, FETI-DP)    1e-9   (FP64; K_II^-1 and the coarse solve
+                                                          amplify rounding by their condition numbers)
+  Jacobian solve, FP64                            1e-10  with Krylov iterations within +-1
+  time step, FP64 / mixed                         1e-9 / 1e-8 in v and u_e
+"""
+import numpy as np
+import pytest
+
+import synth
+from conftest import oracle_problem
+from oracle import ionic
+from oracle.bidomain import direct_solve, time_step
+from oracle.dd import DDSolver
+
+pytestmark = pytest.mark.gpu
+
+
+def _solver(name, **opt):
+    from paper_2101_02959_gb300 import binding, build
+    build.build()
+    w = synth.workload(name)
+    return binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, **opt)
+
+
+def _state(prob, seed=0):
+    ui, ue, w = synth.initial_state(prob.N, seed)
+    ui = ui + 30.0 * np.exp(-np.sum(prob.mesh.coords ** 2, axis=1) / 0.01)
+    ue = ue + 0.5 * synth.random_vector(prob.N, seed + 11)
+    w = 0.01 * np.abs(synth.random_vector(prob.N, seed + 12))
+    return ui + ue, ue, w
+
+
+def _rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+@pytest.mark.parametrize("name", ["tiny", "ragged"])
+def test_gating_and_residual(name):
+    prob = oracle_problem(name)
+    s = _solver(name)
+    ui, ue, w = _state(prob)
+    wn = s.gating(ui, ue, w)
+    assert _rel(wn, ionic.gating_step(ui - ue, w, prob.tau, prob.p)) < 1e-14
+    for t_next in (0.5, 2.0):  # stimulus on / off
+        r = s.residual(synth.STIMULUS, t_next, ui, ue, wn, ui * 0.99, ue + 0.1)
+        ri, re = prob.residual(ui, ue, wn, ui * 0.99, ue + 0.1, t_next)
+        assert _rel(r, np.concatenate([ri, re])) < 1e-12
+
+
+def _linearized(name, **opt):
+    prob = oracle_problem(name)
+    s = _solver(name, **opt)
+    ui, ue, w = _state(prob)
+    wn = ionic.gating_step(ui - ue, w, prob.tau, prob.p)
+    s.linearize(ui, ue, wn)
+    dd = DDSolver(prob)
+    dd.setup(prob.p["chi_cm"] + prob.tau * ionic.di_ion_dv(ui - ue, wn, prob.p))
+    return prob, s, dd, (ui, ue, wn)
+
+
+@pytest.mark.parametrize("name", ["tiny", "cube8", "cube8ve", "ragged"])
+def test_operators_match_oracle(name):
+    prob, s, dd, _ = _linearized(name, precision="fp64")
+    n = prob.dofs.n_iface
+    x = synth.random_vector(n, 3)
+    x[dd.g_iface] = 0.0
+    assert _rel(s.schur_apply(x), dd.schur_apply(x)) < 1e-9
+    assert _rel(s.bddc_apply(x), dd.bddc_apply(x)) < 1e-9
+    F, Minv, lay, nlam = dd.fetidp_operators()
+    assert s.sizes["n_lambda"] == nlam
+    lam = synth.random_vector(nlam, 4)
+    assert _rel(s.fetidp_operator(lam), F(lam)) < 1e-9
+    assert _rel(s.fetidp_apply(lam), Minv(lam)) < 1e-9
+
+
+@pytest.mark.parametrize("name", ["tiny", "cube8", "cube8ve", "ragged"])
+@pytest.mark.parametrize("method", ["bddc", "fetidp"])
+def test_jacobian_solve_fp64(name, method):
+    prob = oracle_problem(name)
+    ui, ue, w = _state(prob)
+    wn = ionic.gating_step(ui - ue, w, prob.tau, prob.p)
+    r_i, r_e = prob.residual(ui, ue, wn, ui - 1.0, ue, prob.tau)
+    kc = prob.kc(ui, ue, wn)
+    si, se, _ = direct_solve(prob, kc, -r_i, -r_e)
+    f = -np.concatenate([r_i, r_e])
+    # tight tolerance: the exact solution to 1e-10
+    s = _solver(name, method=method, precision="fp64", ksp_rtol=1e-13, ksp_atol=0.0)
+    s.linearize(ui, ue, wn)
+    x, st = s.krylov_solve(f)
+    assert st["reason"] == 0
+    assert _rel(x, np.concatenate([si, se])) < 1e-10
+    # paper tolerance: same iteration count as the oracle within +-1 (V+E).  With the
+    # vertex-only primal space the preconditioned residual norm oscillates by up to 10x
+    # near the threshold, and the oracle alone gives 18 (x86) or 19 (Arm) iterations on
+    # this system, so there the bar is +-2.
+    s2 = _solver(name, method=method, precision="fp64")
+    s2.linearize(ui, ue, wn)
+    _, st2 = s2.krylov_solve(f)
+    dd = DDSolver(prob, method=method)
+    _, _, info = dd.solve(kc / prob.fem.M, -r_i, -r_e)
+    assert abs(st2["its"] - info["its"]) <= (1 if prob.part.primal_kind == "VE" else 2)
+    assert abs(st2["cond"] - info["cond"]) < 1e-3 * info["cond"]
+
+
+def _oracle_steps(prob, nsteps, method="bddc"):
+    ui, ue, w = synth.initial_state(prob.N, 0)
+    dd = DDSolver(prob, method=method, rtol=1e-12, atol=0.0)
+    out = []
+    for n in range(nsteps):
+        ui, ue, w, st = time_step(prob, ui, ue, w, n, dd.linsolve(), rtol=1e-10, atol=1e-16)
+        out.append((ui.copy(), ue.copy(), st))
+    return out
+
+
+@pytest.mark.parametrize("name,method,precision,tol", [
+    ("cube8", "bddc", "fp64", 1e-9),
+    ("cube8ve", "fetidp", "fp64", 1e-9),
+    ("cube8ve", "bddc", "mixed", 1e-8),
+    ("ragged", "bddc", "mixed", 1e-8),
+])
+def test_time_steps_match_oracle(name, method, precision, tol):
+    prob = oracle_problem(name)
+    ref = _oracle_steps(prob, 3, method)
+    s = _solver(name, method=method, precision=precision, ksp_rtol=1e-12, ksp_atol=0.0, snes_rtol=1e-10,
+                snes_atol=1e-16)
+    ui, ue, w = synth.initial_state(prob.N, 0)
+    s.set_state(ui, ue, w, 0.0)
+    for n in range(3):
+        st = s.step(synth.STIMULUS)
+        assert st["reason"] == 0
+        gui, gue, gw, t = s.get_state()
+        rui, rue, rst = ref[n]
+        assert abs(t - (n + 1) * prob.tau) < 1e-12
+        assert _rel(gui - gue, rui - rue) < tol
+        assert _rel(gue, rue) < tol
+
+
+def test_device_pointers_and_paper_tolerances():
+    torch = pytest.importorskip("torch")
+    prob = oracle_problem("cube8ve")
+    s = _solver("cube8ve", precision="fp64")
+    ui, ue, w = synth.initial_state(prob.N, 0)
+    dev = [torch.from_numpy(a).cuda() for a in (ui, ue, w)]
+    s.set_state(*dev, 0.0)
+    st = s.step(synth.STIMULUS)
+    assert st["reason"] == 0 and 1 <= st["newton_its"] <= 3
+    gui, gue, gw, _ = s.get_state(like=dev[0])
+    assert gui.is_cuda
+    rui, rue, rw, _ = time_step(prob, ui, ue, w, 0, lambda kc, a, b: direct_solve(prob, kc, a, b))
+    # default tolerances (Section 6 table): agreement limited by SNES rtol 1e-4
+    assert _rel(gue.cpu().numpy(), rue) < 1e-4
+
+
+def test_slab32_first_step_vs_direct_solve():
+    """Full-size bench workload: one GPU step against the oracle with the direct solve."""
+    prob = oracle_problem("slab32")
+    ui, ue, w = synth.initial_state(prob.N, 0)
+    rui, rue, _, _ = time_step(prob, ui, ue, w, 0, lambda kc, a, b: direct_solve(prob, kc, a, b),
+                               rtol=1e-10, atol=1e-16)
+    for precision in ("fp64", "mixed"):
+        s = _solver("slab32", precision=precision, ksp_rtol=1e-12, ksp_atol=0.0, snes_rtol=1e-10, snes_atol=1e-16)
+        s.set_state(ui, ue, w, 0.0)
+        st = s.step(synth.STIMULUS)
+        assert st["reason"] == 0
+        gui, gue, _, _ = s.get_state()
+        assert _rel(gui - gue, rui - rue) < 1e-8
+        assert _rel(gue, rue) < 1e-8
+
+
+def test_not_spd_is_reported():
+    """tau far above 0.37 ms with a depolarised state: Kc < 0, a pivot fails, status says so."""
+    from paper_2101_02959_gb300 import binding
+    prob = oracle_problem("cube8")
+    w = synth.workload("cube8")
+    s = binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, 5.0, precision="fp64")
+    ui = np.full(prob.N, 37.67)
+    z = np.zeros(prob.N)
+    with pytest.raises(binding.BidomainError) as e:
+        s.linearize(ui, z, z)
+    assert e.value.code == -2
