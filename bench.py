@@ -1,0 +1,322 @@
+"""Benchmark of the Bidomain time step on one GB300 (driver contract: one JSON line).
+
+Workload (default): 32x32x16 Q1 elements on a 1.6x1.6x0.8 cm slab, 4x4x2
+subdomains (H/h = 8), vertex + edge-average primal space, Table-1 physics,
+tau = 0.05 ms, seeded resting state with N(0, 1 mV) noise and the corner
+stimulus; 20 time steps.  A "step" is one time step: gating, then Newton with
+the Jacobian solved by PCG + BDDC deluxe (or FETI-DP), at the paper's
+tolerances (KSP rtol 1e-8, SNES rtol 1e-4).
+
+The chosen solver (mixed precision: float32 local factors and Schur
+complements, float64 Krylov / Newton / coarse) is timed next to the plain
+float64 GPU solver on the same mesh.  Inputs are resident in HBM for `value`;
+`e2e` repeats the chosen run through the C-ABI with host buffers (state copied
+in and out every step).  With --gpus N > 1 every rank runs an independent
+replica (the path does not shard across GPUs); timings are max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms/time step and Krylov solves/s at rel. res 1e-8, chosen vs plain FP64 GPU"
+FP32_SIMT_PEAK = 152 * 128 * 2 * 2.07e9 / 1e12   # TFLOP/s: SMs x FP32 lanes x FMA x max SM clock
+FP64_PEAK = 1.25                                  # TFLOP/s, nominal GB300 FP64
+
+
+def describe(w):
+    nx, ny, nz = w["n"]
+    sx, sy, sz = w["s"]
+    return (f"{w['name']}: {nx}x{ny}x{nz} Q1 slab {w['l'][0]}x{w['l'][1]}x{w['l'][2]} cm, "
+            f"{nx // sx}x{ny // sy}x{nz // sz} subdomains H/h={sx}, primal {w['primal']}, tau=0.05 ms")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.rows, self.proc = index, [], None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            threading.Thread(target=self._read, daemon=True).start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "fallback": True}
+
+
+def run_gpu(args, w, rank, world):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_2101_02959_gb300 import binding, build
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    build.build()
+    binding.load()
+    stream = torch.cuda.current_stream()
+    N = synth.n_nodes(w)
+    ui0, ue0, w0 = synth.initial_state(N, 0)
+    dstate = [torch.from_numpy(a).cuda() for a in (ui0, ue0, w0)]
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(precision, method, profile=False, clocks=None):
+        s = binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, stream=stream.cuda_stream,
+                           precision=precision, method=method)
+        s.set_state(*dstate, 0.0)
+        for _ in range(args.warmup):
+            s.step(synth.STIMULUS)
+        s.set_state(*dstate, 0.0)
+        if profile:
+            s.profile(True)
+        stats = []
+        barrier()
+        torch.cuda.synchronize()
+        if clocks:
+            clocks.start()
+        l0 = binding.launch_count()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            stats.append(s.step(synth.STIMULUS))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        launches = binding.launch_count() - l0
+        clk = clocks.stop() if clocks else None
+        ms = max_over_ranks(e0.elapsed_time(e1))
+        prof = {k: s.profile_read(k) for k in binding.PROF} if profile else None
+        final = s.get_state(like=dstate[0])
+        s.close()
+        newton = sum(st["newton_its"] for st in stats)
+        kry = sum(st["krylov_its"] for st in stats)
+        bad = [st["reason"] for st in stats if st["reason"] != 0]
+        return dict(ms=ms, newton=newton, krylov=kry, launches=launches, prof=prof, clocks=clk, bad=bad,
+                    cond=max(st["cond_max"] for st in stats), final=final)
+
+    chosen = timed(args.precision, args.method, profile=True, clocks=ClockSampler(dev))
+    plain = timed("fp64", args.method) if not args.no_plain else None
+
+    # e2e: the same chosen run through host buffers, state copied in and out every step
+    s = binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, stream=stream.cuda_stream,
+                       precision=args.precision, method=args.method)
+    hs = (ui0.copy(), ue0.copy(), w0.copy())
+    s.set_state(*hs, 0.0)
+    for _ in range(args.warmup):
+        s.step(synth.STIMULUS)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    state, t = hs, 0.0
+    e2e_newton = 0
+    for _ in range(args.steps):
+        s.set_state(*state, t)
+        st = s.step(synth.STIMULUS)
+        e2e_newton += st["newton_its"]
+        ui, ue, wv, t = s.get_state()
+        state = (ui, ue, wv)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3)
+    s.close()
+
+    K = args.steps
+    out = dict(chosen=chosen, plain=plain, e2e_ms=e2e_ms, e2e_newton=e2e_newton, N=N)
+    # final-state agreement of the chosen and the plain FP64 solvers after K steps
+    if plain is not None:
+        a, b = chosen["final"], plain["final"]
+        va, vb = (a[0] - a[1]).double(), (b[0] - b[1]).double()
+        out["v_rel_diff_vs_plain"] = float(torch.linalg.norm(va - vb) / torch.linalg.norm(vb))
+        out["ue_rel_diff_vs_plain"] = float(torch.linalg.norm(a[1] - b[1]) / torch.linalg.norm(b[1]))
+    out["K"] = K
+    return out
+
+
+def roofline(prof, precision):
+    """Dominant profiled kernel class against its roofline."""
+    pk = peaks()
+    dom = max(prof, key=lambda k: prof[k]["ms"])
+    p = prof[dom]
+    if p["launches"] == 0 or p["ms"] <= 0:
+        return None, dom
+    if dom in ("rankk", "panel"):
+        achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12
+        peak = FP32_SIMT_PEAK if precision == "mixed" else FP64_PEAK
+        r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+             "traffic": None, "kernel": "k_rankk" if dom == "rankk" else "k_potrf+k_trsm",
+             "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz" if precision == "mixed"
+                             else "nominal GB300 FP64 (recipe table)")}
+    else:
+        achieved = p["bytes"] / (p["ms"] * 1e-3) / 1e9
+        peak = pk.get("hbm_gbs", 6800.0)
+        r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+             "traffic": None, "kernel": "k_gemv" if dom == "gemv" else "k_residual",
+             "peak_source": "of measured" if "fallback" not in pk else "of fallback"}
+    r["launches"] = p["launches"]
+    r["avg_launch_us"] = p["ms"] * 1e3 / p["launches"]
+    return r, dom
+
+
+def cpu_baseline(w, steps=1):
+    """The oracle (numpy, FP64) on the host cores: `steps` time steps of the same workload."""
+    import synth
+    from oracle.bidomain import Problem, time_step
+    from oracle.dd import DDSolver
+    prob = Problem(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, synth.STIMULUS)
+    ui, ue, wv = synth.initial_state(prob.N, 0)
+    dd = DDSolver(prob)
+    newton = 0
+    t0 = time.perf_counter()
+    for n in range(steps):
+        ui, ue, wv, st = time_step(prob, ui, ue, wv, n, dd.linsolve())
+        newton += st["newton_its"]
+    sec = time.perf_counter() - t0
+    try:
+        from threadpoolctl import threadpool_info
+        cores = max(i.get("num_threads", 1) for i in threadpool_info()) or os.cpu_count()
+    except Exception:  # threadpoolctl is not installed on every host
+        cores = os.cpu_count()
+    return dict(ms_per_step=sec * 1e3 / steps, solves_per_s=newton / sec, cores=cores, steps=steps,
+                seconds=sec)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="slab32")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--method", default="bddc", choices=["bddc", "fetidp"])
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=1, help="oracle time steps in the CPU baseline (0: skip)")
+    args = ap.parse_args()
+
+    import synth
+    w = synth.workload(args.workload)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        # the oracle is the reference arm: bounded sample of the same workload (about 3 minutes at most)
+        one = cpu_baseline(w, 1)
+        steps = max(1, min(args.steps, int(150.0 / max(one["seconds"], 1e-3))))
+        res = cpu_baseline(w, steps) if steps > 1 else one
+        line = {"impl": "reference", "metric": METRIC, "value": res["ms_per_step"], "unit": "ms/time step",
+                "n_gpus": args.gpus, "steps": res["steps"], "warmup": 0, "ms_per_step": res["ms_per_step"],
+                "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": {"workload": describe(w), "method": "bddc-deluxe", "krylov": "pcg"},
+                "krylov_solves_per_s": res["solves_per_s"],
+                "cpu_baseline": {"value": res["ms_per_step"], "unit": "ms/time step", "cores": res["cores"],
+                                 "kind": "oracle", "sample": f"{res['steps']} time step(s) of {w['name']}"},
+                "e2e": {"value": res["ms_per_step"], "unit": "ms/time step", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    r = run_gpu(args, w, rank, world)
+    if rank != 0:
+        return
+    K, ch, pl = r["K"], r["chosen"], r["plain"]
+    ms = ch["ms"] / K
+    sec = ch["ms"] * 1e-3
+    roof, dom = roofline(ch["prof"], args.precision)
+    cpu = None
+    if world == 1 and args.cpu_steps > 0:
+        c = cpu_baseline(w, args.cpu_steps)
+        cpu = {"value": c["ms_per_step"], "unit": "ms/time step", "cores": c["cores"], "kind": "oracle",
+               "sample": f"{c['steps']} time step(s) of {w['name']} ({c['seconds']:.1f} s)",
+               "krylov_solves_per_s": c["solves_per_s"]}
+    nbytes = 3 * r["N"] * 8
+    line = {
+        "metric": METRIC, "value": ms, "unit": "ms/time step", "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 local factors + f64 Krylov/Newton/coarse" if args.precision == "mixed"
+        else "f64", "data": "synthetic",
+        "config": {"workload": describe(w), "unknowns": 2 * r["N"], "method": args.method + "-deluxe",
+                   "krylov": "pcg", "precision": args.precision, "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "l2": "per-step working set > 129 MB L2 (local matrices 0.27 GB f32 / 0.54 GB f64)"},
+        "krylov_solves_per_s": ch["newton"] / sec,
+        "dof_iterations_per_s": 2 * r["N"] * ch["krylov"] / sec,
+        "newton_its": ch["newton"], "krylov_its": ch["krylov"], "cond_max": ch["cond"],
+        "aggregate_steps_per_s": world * K / sec,
+        "e2e": {"value": r["e2e_ms"] / K, "unit": "ms/time step", "h2d_bytes_per_step": nbytes,
+                "d2h_bytes_per_step": nbytes},
+        "gpu_launches": ch["launches"],
+        "roofline": roof,
+        "kernels": {k: dict(v, avg_us=(v["ms"] * 1e3 / v["launches"] if v["launches"] else 0.0))
+                    for k, v in ch["prof"].items()},
+        "clocks": ch["clocks"],
+        "cpu_baseline": cpu,
+        "failures": ch["bad"],
+    }
+    if pl is not None:
+        line["plain_fp64"] = {"ms_per_step": pl["ms"] / K, "krylov_solves_per_s": pl["newton"] / (pl["ms"] * 1e-3),
+                              "newton_its": pl["newton"], "krylov_its": pl["krylov"], "failures": pl["bad"]}
+        line["speedup_vs_plain_fp64"] = (pl["ms"] / K) / ms
+        line["v_rel_diff_vs_plain"] = r.get("v_rel_diff_vs_plain")
+        line["ue_rel_diff_vs_plain"] = r.get("ue_rel_diff_vs_plain")
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -231,6 +231,24 @@ int fetidp_operator(bd_handle *h, const double *lambda, double *y, int on_device
  * (SoA).  The u_e correction at the gauge node is 0.  stats may be NULL. */
 int krylov_solve(bd_handle *h, const double *f, double *s, int on_device, bd_solve_stats *stats);
 
+/* ---- instrumentation (no counterpart in the paper) ------------------------- */
+
+/* Kernel classes timed by bidomain_profile_read. */
+#define BD_PROF_RANKK 0  /* rank-k updates of the batched partial Cholesky (Schur formation) */
+#define BD_PROF_PANEL 1  /* diagonal-block factorisation and panel solves */
+#define BD_PROF_GEMV 2   /* dense local matvecs of every Krylov iteration (S_Gamma, S_DD^-1, Psi) */
+#define BD_PROF_RESID 3  /* Newton residual F(u) - G */
+
+/* enable = 1 records a CUDA event pair on the handle's stream around every
+ * launch of the classes above (and clears the totals); 0 stops recording. */
+int bidomain_profile(bd_handle *h, int enable);
+/* out[4] = {launches, total milliseconds, algorithmic flops, algorithmic bytes}
+ * summed over the launches of class `which` since profiling was enabled.
+ * Synchronises the stream. */
+int bidomain_profile_read(bd_handle *h, int which, double *out);
+/* Kernel launches issued by this library in this process so far. */
+int64_t bidomain_launch_count(void);
+
 int bidomain_destroy(bd_handle *h);
 const char *bidomain_strerror(int status);
 

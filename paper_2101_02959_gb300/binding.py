@@ -30,8 +30,9 @@ IDX = dict(ELEM_SUB=0, NODE_MULT=1, IFACE_NODES=2, CLS_TYPE=3, CLS_PTR=4, CLS_NO
 EXPORTED = ["bd_plan_create", "bd_plan_sizes", "bd_plan_index_sets", "bd_plan_destroy", "bd_options_default",
             "bidomain_setup", "bidomain_sizes", "bidomain_index_sets", "bidomain_set_state",
             "bidomain_get_state", "bidomain_step", "bidomain_gating", "bidomain_residual", "bidomain_linearize",
-            "schur_apply", "bddc_apply", "fetidp_apply", "fetidp_operator", "krylov_solve", "bidomain_destroy",
-            "bidomain_strerror"]
+            "schur_apply", "bddc_apply", "fetidp_apply", "fetidp_operator", "krylov_solve", "bidomain_profile",
+            "bidomain_profile_read", "bidomain_launch_count", "bidomain_destroy", "bidomain_strerror"]
+PROF = dict(rankk=0, panel=1, gemv=2, resid=3)
 
 
 class BdMesh(C.Structure):
@@ -107,6 +108,9 @@ def load(build_if_missing: bool = False):
         "fetidp_apply": (I, [P, P, P, I]),
         "fetidp_operator": (I, [P, P, P, I]),
         "krylov_solve": (I, [P, P, P, I, C.POINTER(BdSolveStats)]),
+        "bidomain_profile": (I, [P, I]),
+        "bidomain_profile_read": (I, [P, I, C.POINTER(C.c_double)]),
+        "bidomain_launch_count": (C.c_int64, []),
         "bidomain_destroy": (I, [P]),
         "bidomain_strerror": (C.c_char_p, [I]),
     }
@@ -116,6 +120,10 @@ def load(build_if_missing: bool = False):
         f.argtypes = args
     _LIB = lib
     return lib
+
+
+def launch_count():
+    return int(load().bidomain_launch_count())
 
 
 class BidomainError(RuntimeError):
@@ -303,6 +311,14 @@ class Solver:
 
     def fetidp_operator(self, lam):
         return self._apply(self._lib.fetidp_operator, lam, self.sizes["n_lambda"], "fetidp_operator")
+
+    def profile(self, enable=True):
+        _check(self._lib.bidomain_profile(self._h, 1 if enable else 0), "bidomain_profile")
+
+    def profile_read(self, which):
+        out = (C.c_double * 4)()
+        _check(self._lib.bidomain_profile_read(self._h, PROF[which], out), "bidomain_profile_read")
+        return dict(launches=int(out[0]), ms=out[1], flops=out[2], bytes=out[3])
 
     def krylov_solve(self, f):
         out = _same_kind(f, 2 * self.N)

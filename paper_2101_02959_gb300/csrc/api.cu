@@ -109,6 +109,62 @@ double tridiag_cond(const std::vector<double> &d, const std::vector<double> &e) 
   return lmax / lmin;
 }
 
+// Per-launch CUDA-event timing of selected kernel classes.
+struct Profiler : ProfHook {
+  bool on = false;
+  struct Rec {
+    int id;
+    cudaEvent_t a, b;
+    double flops, bytes;
+  };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  double tot[PROF_NCLASS][4] = {};
+  cudaEvent_t get() {
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      ck(cudaEventCreate(&e), "event");
+      pool.push_back(e);
+    }
+    return pool[used++];
+  }
+  void begin(int id, cudaStream_t s) override {
+    if (!on) return;
+    cudaEvent_t a = get();
+    ck(cudaEventRecord(a, s), "event");
+    recs.push_back(Rec{id, a, nullptr, 0.0, 0.0});
+  }
+  void end(int id, cudaStream_t s, double flops, double bytes) override {
+    if (!on) return;
+    cudaEvent_t b = get();
+    ck(cudaEventRecord(b, s), "event");
+    recs.back().b = b;
+    recs.back().flops = flops;
+    recs.back().bytes = bytes;
+  }
+  void harvest() {
+    for (auto &r : recs) {
+      float ms = 0.f;
+      ck(cudaEventSynchronize(r.b), "event sync");
+      ck(cudaEventElapsedTime(&ms, r.a, r.b), "event time");
+      tot[r.id][0] += 1.0;
+      tot[r.id][1] += ms;
+      tot[r.id][2] += r.flops;
+      tot[r.id][3] += r.bytes;
+    }
+    recs.clear();
+    used = 0;
+  }
+  void reset() {
+    harvest();
+    for (auto &t : tot) for (double &v : t) v = 0.0;
+  }
+  ~Profiler() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
 }  // namespace
 
 struct bd_plan {
@@ -178,6 +234,8 @@ struct bd_handle {
   double *d_Co, *d_CoInv;
   bool linearized = false;
   std::string last_error;
+  Profiler prof;
+  double gemv_schur_flops = 0, gemv_schur_bytes = 0, gemv_local_flops = 0, gemv_local_bytes = 0;
 
   bool mixed() const { return opt.precision == BD_MIXED; }
   int check_err() {
@@ -528,6 +586,8 @@ void setup_handle(bd_handle &h) {
     y.sign = -1.0; y.dst_off = zp_off[j]; y.dst_ld = ldx[j];
     c_zx.push_back(y);
   }
+  for (auto &t : g_schur) { h.gemv_schur_flops += 2.0 * t.rows * t.cols; h.gemv_schur_bytes += (double)t.rows * t.cols; }
+  for (auto &t : g_local) { h.gemv_local_flops += 2.0 * t.rows * t.cols; h.gemv_local_bytes += (double)t.rows * t.cols; }
   h.gv_schur = gset(g_schur);
   h.gv_local = gset(g_local);
   h.gv_psit = gset(g_psit);
@@ -591,7 +651,7 @@ void linearize_t(bd_handle &h, Dense<T> &D) {
   ck(cudaMemsetAsync(D.K, 0, sizeof(T) * h.K_el, s), "memset K");
   launch_assemble_local<T>(h.nq, h.d_q_sub, h.d_q_loc, h.d_q_node, h.d_q_nbr, h.d_q_stencil, h.d_q_mass, h.d_factor,
                            h.tau, h.d_Kdesc, D.K, s);
-  engine_partial_cholesky<T>(h.shK, h.d_Kdesc, D.K, h.d_err, s);
+  engine_partial_cholesky<T>(h.shK, h.d_Kdesc, D.K, h.d_err, s, &h.prof);
   launch_copy<T, T>(h.cp_sorig.n, h.cp_sorig.max_elems, h.cp_sorig.d, D.K, D.Sorig, s);
   long long max_a = 0;
   for (int j = 0; j < h.nsub; ++j) max_a = std::max(max_a, (long long)h.shA.m[j] * h.shA.m[j]);
@@ -599,7 +659,7 @@ void linearize_t(bd_handle &h, Dense<T> &D) {
                       h.d_tl_row, h.d_tl_val, s);
   launch_copy<T, T>(h.cp_sdd.n, h.cp_sdd.max_elems, h.cp_sdd.d, D.Aug, D.SDD, s);
   launch_copy<T, T>(h.cp_blk.n, h.cp_blk.max_elems, h.cp_blk.d, D.Aug, D.Blk, s);
-  engine_partial_cholesky<T>(h.shA, h.d_Adesc, D.Aug, h.d_err, s);
+  engine_partial_cholesky<T>(h.shA, h.d_Adesc, D.Aug, h.d_err, s, &h.prof);
   launch_copy<T, T>(h.cp_zx.n, h.cp_zx.max_elems, h.cp_zx.d, D.Aug, D.Z, s);
   launch_class_aug<T>(h.ncls, h.max_nc, h.d_cls, h.d_pairs, D.Blk, h.d_Cdesc, D.CA, s);
   engine_partial_cholesky<T>(h.shC, h.d_Cdesc, D.CA, h.d_err, s);
@@ -618,16 +678,20 @@ void linearize(bd_handle &h) {
 // ---- operators (device vectors; `done` = early-exit flag of a Krylov loop) ----
 template <class T>
 void schur_t(bd_handle &h, Dense<T> &D, const double *x, double *y, const int *done) {
+  h.prof.begin(PROF_GEMV, h.s);
   launch_gemv<T>(h.gv_schur.n, h.gv_schur.max_rows, h.gv_schur.max_cols, h.gv_schur.d, D.Sorig, x, h.d_R, h.d_yloc,
                  1.0, done, h.s);
+  h.prof.end(PROF_GEMV, h.s, h.gemv_schur_flops, h.gemv_schur_bytes * sizeof(T));
   launch_gather_sum(h.nif, h.d_Rt_ptr, h.d_Rt_idx, h.d_yloc, y, h.gauge_iface, 1.0, nullptr, done, h.s);
 }
 
 // St^-1 applied to (primal part rP or 0, local dual parts rD): zbar[nd:] = z_Pi, ydc[0:nD_tot] = z_Delta.
 template <class T>
 void st_inv_t(bd_handle &h, Dense<T> &D, const double *rP, const double *rD, const int *done) {
+  h.prof.begin(PROF_GEMV, h.s);
   launch_gemv<T>(h.gv_local.n, h.gv_local.max_rows, h.gv_local.max_cols, h.gv_local.d, D.Z, rD, nullptr, h.d_ydc,
                  1.0, done, h.s);
+  h.prof.end(PROF_GEMV, h.s, h.gemv_local_flops, h.gemv_local_bytes * sizeof(T));
   launch_gather_sum(h.np, h.d_pl_ptr, h.d_pl_idx, h.d_ydc + h.nD_tot, h.d_crhs, h.gauge_primal, -1.0, rP, done, h.s);
   launch_gemv<double>(1, h.np, h.np, h.gv_coarse.d, h.d_CoInv, h.d_crhs, nullptr, h.d_zbar, 1.0, done, h.s);
   launch_gemv_t<T>(h.gv_psit.n, h.gv_psit.max_rows, h.gv_psit.max_cols, h.gv_psit.d, D.Z, h.d_zbar, h.d_prim_x,
@@ -790,8 +854,11 @@ double read_scalar(bd_handle &h, const double *d) {
 
 // residual at u + lam s into (rit, ret, factort, uit, uet); returns ||F - G||^2
 double trial_residual(bd_handle &h, const StimParams &sp, const double *si, const double *se, double lam) {
+  h.prof.begin(PROF_RESID, h.s);
   launch_residual(h.N, h.d_stencil, h.d_nbr, h.d_mass, h.d_node_ijk, h.d_ui, h.d_ue, si, se, lam, h.d_wn, h.d_uin,
                   h.d_uen, h.fp, sp, h.d_rit, h.d_ret, h.d_factort, h.d_uit, h.d_uet, h.d_partial, h.d_scal, h.s);
+  // moved per node: 54 stencil values, 27 neighbour ids, M, w, u^n (2), u (2), s (2), i,j,k; written: r (2), factor, u (2)
+  h.prof.end(PROF_RESID, h.s, 0.0, (double)h.N * (54 * 8 + 27 * 4 + 12 + 8 * (si ? 8 : 6) + 8 * 5));
   return read_scalar(h, h.d_scal);
 }
 
@@ -875,6 +942,7 @@ int step(bd_handle &h, const bd_stimulus *stim, bd_step_stats *out) {
   ck(cudaMemcpyAsync(h.d_uen, h.d_ue, sizeof(double) * h.N, cudaMemcpyDeviceToDevice, s), "copy");
   ck(cudaMemcpyAsync(h.d_w, h.d_wn, sizeof(double) * h.N, cudaMemcpyDeviceToDevice, s), "copy");
   ck(cudaStreamSynchronize(s), "step");
+  if (h.prof.on) h.prof.harvest();
   h.step_n += 1;
   st.reason = reason;
   if (out) *out = st;
@@ -1186,6 +1254,28 @@ int krylov_solve(bd_handle *h, const double *f, double *s, int on_device, bd_sol
     return r;
   });
 }
+
+int bidomain_profile(bd_handle *h, int enable) {
+  if (!h) return BD_ERR_ARG;
+  return guard(h, [&] {
+    ck(cudaStreamSynchronize(h->s), "sync");
+    h->prof.reset();
+    h->prof.on = enable != 0;
+    return BD_OK;
+  });
+}
+
+int bidomain_profile_read(bd_handle *h, int which, double *out) {
+  if (!h || !out || which < 0 || which >= PROF_NCLASS) return BD_ERR_ARG;
+  return guard(h, [&] {
+    ck(cudaStreamSynchronize(h->s), "sync");
+    h->prof.harvest();
+    for (int k = 0; k < 4; ++k) out[k] = h->prof.tot[which][k];
+    return BD_OK;
+  });
+}
+
+int64_t bidomain_launch_count(void) { return (int64_t)launch_count(); }
 
 int bidomain_destroy(bd_handle *h) {
   if (!h) return BD_ERR_ARG;

@@ -471,6 +471,7 @@ void launch_assemble_local(int nq, const int *q_sub, const int *q_loc, const int
   const long long tot = (long long)nq * 27;
   k_assemble_local<T><<<(int)((tot + 255) / 256), 256, 0, s>>>(nq, q_sub, q_loc, q_node, nbr, stencil, mass, factor,
                                                              tau, desc, base);
+  count_launch();
 }
 
 template <typename TS, typename TD>
@@ -478,6 +479,7 @@ void launch_copy(int ntasks, long long max_elems, const CopyTask *tasks, const T
   if (ntasks == 0 || max_elems == 0) return;
   const int gx = (int)std::min<long long>((max_elems + 255) / 256, 4096);
   k_copy<TS, TD><<<dim3(gx, ntasks), 256, 0, s>>>(tasks, src, dst);
+  count_launch();
 }
 
 template <typename T>
@@ -486,6 +488,7 @@ void launch_build_aug(int nsub, long long max_elems, const MatDesc *kdesc, const
                       const int *trow, const double *tval, cudaStream_t s) {
   const int gx = (int)std::min<long long>((max_elems + 255) / 256, 8192);
   k_build_aug<T><<<dim3(gx, nsub), 256, 0, s>>>(kdesc, kbase, adesc, abase, nI, nD, tptr_off, tptr, trow, tval);
+  count_launch();
 }
 
 template <typename T>
@@ -494,6 +497,7 @@ void launch_class_aug(int ncls, int max_n, const ClassTask *cls, const PairTask 
   if (ncls == 0) return;
   const int gx = std::max(1, std::min(ceil_div(4 * max_n * max_n, 256), 1024));
   k_class_aug<T><<<dim3(gx, ncls), 256, 0, s>>>(cls, pairs, blk, cdesc, cbase);
+  count_launch();
 }
 
 template <typename T>
@@ -502,18 +506,21 @@ void launch_coarse_aug(int np, int gauge, const int *ptr, const long long *src, 
   const long long tot = 4LL * np * np;
   const int gx = (int)std::min<long long>((tot + 255) / 256, 8192);
   k_coarse_aug<T><<<std::max(gx, 1), 256, 0, s>>>(np, gauge, ptr, src, abase, co, ld);
+  count_launch();
 }
 
 void launch_spmv(int n, const int *ptr, const int *col, const double *val, const double *x, double *y, int zero,
                  const int *done, cudaStream_t s) {
   if (n == 0) return;
   k_spmv<<<GRID1(n)>>>(n, ptr, col, val, x, y, zero, done);
+  count_launch();
 }
 
 void launch_gather_sum(int n, const int *ptr, const int *idx, const double *src, double *y, int zero, double alpha,
                        const double *addend, const int *done, cudaStream_t s) {
   if (n == 0) return;
   k_gather_sum<<<GRID1(n)>>>(n, ptr, idx, src, y, zero, alpha, addend, done);
+  count_launch();
 }
 
 template <typename T>
@@ -521,6 +528,7 @@ void launch_deluxe_restrict(int ncls, int max_n, const ClassTask *cls, const Pai
                             const T *sinv, const double *rbar, double *rD, const int *done, cudaStream_t s) {
   if (ncls == 0) return;
   k_deluxe_restrict<T><<<ncls, 256, 3 * sizeof(T) * max_n, s>>>(cls, pairs, blk, sinv, rbar, rD, done);
+  count_launch();
 }
 
 template <typename T>
@@ -528,18 +536,21 @@ void launch_deluxe_extend(int ncls, int max_n, const ClassTask *cls, const PairT
                           const T *sinv, const double *zD, double *zbar, const int *done, cudaStream_t s) {
   if (ncls == 0) return;
   k_deluxe_extend<T><<<ncls, 256, 3 * sizeof(T) * max_n, s>>>(cls, pairs, blk, sinv, zD, zbar, done);
+  count_launch();
 }
 
 void launch_jump(int nlt, int max_n, const LamTask *lt, const PairTask *pairs, const double *w, double *lam,
                  const int *done, cudaStream_t s) {
   if (nlt == 0) return;
   k_jump<<<dim3(ceil_div(max_n, 128), nlt), 128, 0, s>>>(lt, pairs, w, lam, done);
+  count_launch();
 }
 
 void launch_jump_t(int nwt, int max_n, const WTask *wt, const WEnt *ent, const double *lam, double *w,
                    const int *done, cudaStream_t s) {
   if (nwt == 0) return;
   k_jump_t<<<dim3(ceil_div(max_n, 128), nwt), 128, 0, s>>>(wt, ent, lam, w, done);
+  count_launch();
 }
 
 template <typename T>
@@ -547,6 +558,7 @@ void launch_jump_dt(int nwt, int max_n, const WTask *wt, const WEnt *ent, const 
                     const double *mu, double *w, const int *done, cudaStream_t s) {
   if (nwt == 0) return;
   k_jump_dt<T><<<nwt, 256, 3 * sizeof(T) * max_n, s>>>(wt, ent, blk, sinv, mu, w, done);
+  count_launch();
 }
 
 template <typename T>
@@ -554,23 +566,27 @@ void launch_jump_d(int nlt, int max_n, const LamTask *lt, const PairTask *pairs,
                    const double *y, double *mu, const int *done, cudaStream_t s) {
   if (nlt == 0) return;
   k_jump_d<T><<<nlt, 256, 6 * sizeof(T) * max_n, s>>>(lt, pairs, blk, sinv, y, mu, done);
+  count_launch();
 }
 
 void launch_dual_mean(int ncls, int max_n, const ClassTask *cls, const PairTask *pairs, const double *zD,
                       double *zbar, cudaStream_t s) {
   if (ncls == 0) return;
   k_dual_mean<<<dim3(ceil_div(max_n, 128), ncls), 128, 0, s>>>(cls, pairs, zD, zbar);
+  count_launch();
 }
 
 void launch_gather_pairs(int n, const int *node, const double *fi, const double *fe, double *v, double scale,
                          const double *mult, cudaStream_t s) {
   if (n == 0) return;
   k_gather_pairs<<<GRID1(n)>>>(n, node, fi, fe, v, scale, mult);
+  count_launch();
 }
 
 void launch_scatter_pairs(int n, const int *node, const double *v, double *si, double *se, cudaStream_t s) {
   if (n == 0) return;
   k_scatter_pairs<<<GRID1(n)>>>(n, node, v, si, se);
+  count_launch();
 }
 
 void launch_tloc_t(int nt, const int *t_sub, const int *t_loc, const int *t_ptr, const int *t_row,
@@ -578,46 +594,60 @@ void launch_tloc_t(int nt, const int *t_sub, const int *t_loc, const int *t_ptr,
                    const int *lprim_off, double *outD, double *outP, cudaStream_t s) {
   if (nt == 0) return;
   k_tloc_t<<<GRID1(nt)>>>(nt, t_sub, t_loc, t_ptr, t_row, t_val, g_off, g, nD, ldual_off, lprim_off, outD, outP);
+  count_launch();
 }
 
 void launch_gather_scale_sub(int n, const int *idx, const double *x, const double *w, double *y, cudaStream_t s) {
   if (n == 0) return;
   k_gather_scale_sub<<<GRID1(n)>>>(n, idx, x, w, y);
+  count_launch();
 }
 
 void launch_fill(int n, double *y, double v, cudaStream_t s) {
   if (n == 0) return;
   k_fill<<<GRID1(n)>>>(n, y, v);
+  count_launch();
 }
 
 void launch_copy_vec(int n, const double *x, double *y, const int *done, cudaStream_t s) {
   if (n == 0) return;
   k_copy_vec<<<GRID1(n)>>>(n, x, y, done);
+  count_launch();
 }
 
 void launch_axpby(int n, double a, const double *x, double b, double *y, cudaStream_t s) {
   if (n == 0) return;
   k_axpby<<<GRID1(n)>>>(n, a, x, b, y);
+  count_launch();
 }
 
-void launch_pcg_start(KrylovState *ks, const double *dots, cudaStream_t s) { k_pcg_start<<<1, 1, 0, s>>>(ks, dots); }
+void launch_pcg_start(KrylovState *ks, const double *dots, cudaStream_t s) {
+  k_pcg_start<<<1, 1, 0, s>>>(ks, dots);
+  count_launch();
+}
 void launch_pcg_alpha(KrylovState *ks, const double *dots, double *ha, cudaStream_t s) {
   k_pcg_alpha<<<1, 1, 0, s>>>(ks, dots, ha);
+  count_launch();
 }
 void launch_pcg_beta(KrylovState *ks, const double *dots, double *hb, cudaStream_t s) {
   k_pcg_beta<<<1, 1, 0, s>>>(ks, dots, hb);
+  count_launch();
 }
 void launch_pcg_xr(int n, const KrylovState *ks, const double *p, const double *q, double *x, double *r,
                    cudaStream_t s) {
   k_pcg_xr<<<std::max(1, std::min(ceil_div(n, 256), kRedBlocks)), 256, 0, s>>>(n, ks, p, q, x, r);
+  count_launch();
 }
 void launch_pcg_p(int n, const KrylovState *ks, const double *z, double *p, cudaStream_t s) {
   k_pcg_p<<<std::max(1, std::min(ceil_div(n, 256), kRedBlocks)), 256, 0, s>>>(n, ks, z, p);
+  count_launch();
 }
 void launch_dot2(int n, const double *a0, const double *b0, const double *a1, const double *b1, double *partial,
                  double *out, const int *done, cudaStream_t s) {
   k_dot2_done<<<kRedBlocks, 256, 0, s>>>(n, a0, b0, a1, b1, partial, done);
+  count_launch();
   k_finalize2_done<<<1, 256, 0, s>>>(kRedBlocks, partial, out, done);
+  count_launch();
 }
 
 #define BD_DD_INST(T)                                                                                           \

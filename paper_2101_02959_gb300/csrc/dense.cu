@@ -9,6 +9,7 @@
 // trailing block, S_PP - S_PD S_DD^-1 S_DP (the local coarse matrix of
 // Section 4.4), -S_DD^-1 S_DP and -S_DD^-1 (the local constrained solve).
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "kernels.cuh"
@@ -162,11 +163,23 @@ __global__ void __launch_bounds__(256) k_rankk(const MatDesc *__restrict__ desc,
   }
 }
 
+std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches += n; }
+long long launch_count() { return g_launches.load(); }
+
+// Lower-triangle entries updated by a rank-k launch: panel mode rows [t0, m) x cols [t0, e), c <= r.
+static double trapezoid(long long t0, long long e, long long m) {
+  const long long k = e - t0;
+  return (double)(k * (m - t0) - k * (k - 1) / 2);
+}
+
 template <typename T>
-void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s) {
+void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s,
+                             ProfHook *prof) {
   if (sh.count == 0) return;
   for (int k0 = 0; k0 < sh.max_e; k0 += kNB) {
     int max_below = 0, max_rt = 0, max_ct = 0;
+    double fl_panel = 0.0, fl_upd = 0.0, by_upd = 0.0;
     for (int b = 0; b < sh.count; ++b) {
       if (k0 >= sh.e[b]) continue;
       const int w = std::min(kNB, sh.e[b] - k0);
@@ -174,22 +187,43 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
       max_below = std::max(max_below, below);
       max_rt = std::max(max_rt, ceil_div(below, kTB));
       max_ct = std::max(max_ct, ceil_div(sh.e[b] - k0 - w, kTB));
+      fl_panel += (double)w * w * w / 3.0 + (double)below * w * w;
+      const double ent = trapezoid(k0 + w, sh.e[b], sh.m[b]);
+      fl_upd += 2.0 * w * ent;
+      by_upd += sizeof(T) * (2.0 * ent + (double)w * (below + sh.e[b] - k0 - w));
     }
+    if (prof) prof->begin(PROF_PANEL, s);
     k_potrf<T><<<sh.count, 32, 0, s>>>(d_desc, base, k0, d_err);
+    count_launch();
     if (max_below > 0) {
       dim3 gp(ceil_div(max_below, 128), sh.count);
       k_trsm<T><<<gp, 128, 0, s>>>(d_desc, base, k0);
+      count_launch();
     }
+    if (prof) prof->end(PROF_PANEL, s, fl_panel, 0.0);
     if (max_rt > 0 && max_ct > 0) {
       dim3 gu(max_rt * max_ct, sh.count);
+      if (prof) prof->begin(PROF_RANKK, s);
       k_rankk<T><<<gu, 256, 0, s>>>(d_desc, base, 0, k0, max_ct);
+      count_launch();
+      if (prof) prof->end(PROF_RANKK, s, fl_upd, by_upd);
     }
   }
   int max_t = 0;
-  for (int b = 0; b < sh.count; ++b) max_t = std::max(max_t, ceil_div(sh.m[b] - sh.e[b], kTB));
+  double fl = 0.0, by = 0.0;
+  for (int b = 0; b < sh.count; ++b) {
+    max_t = std::max(max_t, ceil_div(sh.m[b] - sh.e[b], kTB));
+    const double n2 = sh.m[b] - sh.e[b];
+    const double ent = n2 * (n2 + 1) / 2.0;
+    fl += 2.0 * sh.e[b] * ent;
+    by += sizeof(T) * (2.0 * ent + n2 * sh.e[b]);
+  }
   if (max_t > 0) {
     dim3 gf(max_t * max_t, sh.count);
+    if (prof) prof->begin(PROF_RANKK, s);
     k_rankk<T><<<gf, 256, 0, s>>>(d_desc, base, 1, 0, max_t);
+    count_launch();
+    if (prof) prof->end(PROF_RANKK, s, fl, by);
   }
 }
 
@@ -249,6 +283,7 @@ void launch_gemv(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks
   dim3 g(ceil_div(max_rows, 64), ntasks);
   const size_t sm = sizeof(T) * (size_t)std::max(1, max_cols);
   k_gemv<T><<<g, 256, sm, s>>>(d_tasks, A, x, xidx, y, alpha, done);
+  count_launch();
 }
 
 template <typename T>
@@ -258,6 +293,7 @@ void launch_gemv_t(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tas
   dim3 g(ceil_div(max_cols, 256), ntasks);
   const size_t sm = sizeof(T) * (size_t)std::max(1, max_rows);
   k_gemv_t<T><<<g, 256, sm, s>>>(d_tasks, A, x, xidx, y, alpha, done);
+  count_launch();
 }
 
 // ---- batched triangular solves (one CTA per matrix) ---------------------------
@@ -334,10 +370,12 @@ void launch_trsv(int count, int max_n, const MatDesc *d_desc, const int *vec_off
   if (count == 0) return;
   const size_t sm = sizeof(T) * (size_t)std::max(1, max_n);
   k_trsv<T><<<count, 256, sm, s>>>(d_desc, vec_off, base, b, y, transpose ? 1 : 0);
+  count_launch();
 }
 
 #define BD_INST(T)                                                                                              \
-  template void engine_partial_cholesky<T>(const EngineShape &, const MatDesc *, T *, int *, cudaStream_t);     \
+  template void engine_partial_cholesky<T>(const EngineShape &, const MatDesc *, T *, int *, cudaStream_t,    \
+                                           ProfHook *);     \
   template void launch_gemv<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *,        \
                                double *, double, const int *, cudaStream_t);                                   \
   template void launch_gemv_t<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *,      \

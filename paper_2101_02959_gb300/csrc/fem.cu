@@ -213,6 +213,7 @@ __global__ void k_gauge_shift(int n, double *__restrict__ ui, double *__restrict
 void launch_element_matrices(int ne, const int *elem_ijk, const double h[3], double lz, const FemParams &fp,
                              double *Ke, cudaStream_t s) {
   k_element_matrices<<<ceil_div(ne, 128), 128, 0, s>>>(ne, elem_ijk, h[0], h[1], h[2], lz, fp, Ke);
+  count_launch();
 }
 
 void launch_stencil_gather(int nrows, const int *row_node, const int *row_sub, const int *node_ijk,
@@ -221,11 +222,13 @@ void launch_stencil_gather(int nrows, const int *row_node, const int *row_sub, c
   const long long tot = (long long)nrows * 27;
   k_stencil_gather<<<(int)((tot + 255) / 256), 256, 0, s>>>(nrows, row_node, row_sub, node_ijk, elem_grid, elem_sub,
                                                           n[0], n[1], n[2], Ke, out, soa_stride);
+  count_launch();
 }
 
 void launch_gating(int n, const double *ui, const double *ue, const double *w, double *wn, const FemParams &p,
                    cudaStream_t s) {
   k_gating<<<ceil_div(n, 256), 256, 0, s>>>(n, ui, ue, w, wn, p);
+  count_launch();
 }
 
 void launch_residual(int n, const double *stencil, const int *nbr, const double *mass, const int *node_ijk,
@@ -235,17 +238,24 @@ void launch_residual(int n, const double *stencil, const int *nbr, const double 
                      double *ue_out, double *partial, double *norm2, cudaStream_t s) {
   k_residual<<<kRedBlocks, 256, 0, s>>>(n, stencil, nbr, mass, node_ijk, ui0, ue0, si, se, lam, wn, uin, uen, p, st,
                                         ri, re, factor, ui_out, ue_out, partial);
-  if (norm2) k_finalize<<<1, 256, 0, s>>>(kRedBlocks, 1, partial, norm2);
+  count_launch();
+  if (norm2) {
+    k_finalize<<<1, 256, 0, s>>>(kRedBlocks, 1, partial, norm2);
+    count_launch();
+  }
 }
 
 void launch_dot3(int n, const double *a0, const double *b0, const double *a1, const double *b1, const double *a2,
                  const double *b2, double *partial, double *out, cudaStream_t s) {
   k_dot3<<<kRedBlocks, 256, 0, s>>>(n, a0, b0, a1, b1, a2, b2, partial);
+  count_launch();
   k_finalize<<<1, 256, 0, s>>>(kRedBlocks, 3, partial, out);
+  count_launch();
 }
 
 void launch_gauge_shift(int n, double *ui, double *ue, const double *scal, cudaStream_t s) {
   k_gauge_shift<<<ceil_div(n, 256), 256, 0, s>>>(n, ui, ue, scal);
+  count_launch();
 }
 
 }  // namespace bd

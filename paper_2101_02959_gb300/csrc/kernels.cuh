@@ -9,6 +9,17 @@ namespace bd {
 constexpr int kRedBlocks = 304;  // fixed reduction grid (2 x 152 SMs): deterministic sums
 constexpr int kNB = 32;          // panel width of the partial Cholesky
 
+// Per-launch timing hook (CUDA events recorded on the launch stream) and
+// the library-wide kernel launch counter.
+enum { PROF_RANKK = 0, PROF_PANEL = 1, PROF_GEMV = 2, PROF_RESID = 3, PROF_NCLASS = 4 };
+struct ProfHook {
+  virtual void begin(int id, cudaStream_t s) = 0;
+  virtual void end(int id, cudaStream_t s, double flops, double bytes) = 0;
+  virtual ~ProfHook() {}
+};
+void count_launch(int n = 1);
+long long launch_count();
+
 struct FemParams {
   double sigma_i[3], sigma_e[3];
   double G, eta1, eta2, vth, vp, chi_cm, tau;
@@ -47,7 +58,8 @@ struct EngineShape {
   std::vector<int> m, e;  // host copies for per-step grid sizes
 };
 template <typename T>
-void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s);
+void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s,
+                             ProfHook *prof = nullptr);
 
 // y = alpha * A x (+ y): tasks in d_tasks (GemvDesc); x gathered through xidx when flagged.
 template <typename T>
