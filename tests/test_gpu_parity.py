@@ -102,8 +102,10 @@ def test_jacobian_solve_fp64(name, method):
     _, st2 = s2.krylov_solve(f)
     dd = DDSolver(prob, method=method)
     _, _, info = dd.solve(kc / prob.fem.M, -r_i, -r_e)
-    assert abs(st2["its"] - info["its"]) <= (1 if prob.part.primal_kind == "VE" else 2)
-    assert abs(st2["cond"] - info["cond"]) < 1e-3 * info["cond"]
+    ve = prob.part.primal_kind == "VE"
+    assert abs(st2["its"] - info["its"]) <= (1 if ve else 2)
+    # the Lanczos estimate follows the iteration count: 1e-3 (V+E), 1e-2 when it differs (V)
+    assert abs(st2["cond"] - info["cond"]) < (1e-3 if ve else 1e-2) * info["cond"]
 
 
 def _oracle_steps(prob, nsteps, method="bddc"):
