@@ -48,6 +48,7 @@ extern "C" {
 #define BD_ERR_CUDA (-8)             /* a CUDA runtime call failed */
 #define BD_ERR_NOMEM (-9)            /* device allocation failed */
 #define BD_ERR_STATE (-10)           /* call made in the wrong order (e.g. no Jacobian yet) */
+#define BD_ERR_SCRATCH (-11)         /* too large for the static scratch of schur_apply_noalloc */
 
 /* ---- option values ----------------------------------------------------- */
 #define BD_BDDC 0
@@ -230,6 +231,28 @@ int fetidp_operator(bd_handle *h, const double *lambda, double *y, int on_device
  * system (FETI-DP), then recovers the interior (Section 4.1).  f, s: 2*n_node
  * (SoA).  The u_e correction at the gauge node is 0.  stats may be NULL. */
 int krylov_solve(bd_handle *h, const double *f, double *s, int on_device, bd_solve_stats *stats);
+
+/* ---- no-allocation variant ------------------------------------------------
+ * The paper has no counterpart: this is a deployment variant of schur_apply.
+ * It computes the same y = S_hat x, but keeps its scratch (the per-subdomain
+ * products S_Gamma^(j) R_j x before they are summed onto the interface) in a
+ * fixed device array compiled into the library instead of memory obtained
+ * with cudaMalloc.  It is meant for callers that must not allocate device
+ * memory when they apply the operator: code running under a fixed device-
+ * memory budget, or inside a host framework that owns every allocation.
+ *   - x, y: device pointers to interface vectors (n_iface doubles).
+ *   - The handle must have been linearised (BD_ERR_STATE otherwise).
+ *   - Capacity: the sum over subdomains of their interface unknowns must not
+ *     exceed 524288 doubles (4 MiB); larger problems get BD_ERR_SCRATCH.
+ *     Every GPU that loads the library holds this 4 MiB until the process exits.
+ *   - The first call on a device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - Every call shares the one array and overwrites all of it that it reads,
+ *     so nothing needs clearing between calls; calls that overlap on the GPU
+ *     (other streams, other threads) race on it.
+ *   - No cudaMalloc, cudaFree or allocating library routine is called.
+ *     The call synchronises the handle's stream. */
+int schur_apply_noalloc(bd_handle *h, const double *x, double *y);
 
 /* ---- instrumentation (no counterpart in the paper) ------------------------- */
 

@@ -17,7 +17,7 @@ from . import build as _build
 BD_OK = 0
 ERRORS = {-1: "BD_ERR_ARG", -2: "BD_ERR_NOT_SPD", -3: "BD_ERR_KRYLOV_MAXIT", -4: "BD_ERR_KRYLOV_DIVERGED",
           -5: "BD_ERR_NEWTON", -6: "BD_ERR_NAN", -7: "BD_ERR_TIMEOUT", -8: "BD_ERR_CUDA", -9: "BD_ERR_NOMEM",
-          -10: "BD_ERR_STATE"}
+          -10: "BD_ERR_STATE", -11: "BD_ERR_SCRATCH"}
 BDDC, FETIDP = 0, 1
 PCG, GMRES = 0, 1
 PRIMAL = {"V": 0, "VE": 1}
@@ -31,7 +31,8 @@ EXPORTED = ["bd_plan_create", "bd_plan_sizes", "bd_plan_index_sets", "bd_plan_de
             "bidomain_setup", "bidomain_sizes", "bidomain_index_sets", "bidomain_set_state",
             "bidomain_get_state", "bidomain_step", "bidomain_gating", "bidomain_residual", "bidomain_linearize",
             "schur_apply", "bddc_apply", "fetidp_apply", "fetidp_operator", "krylov_solve", "bidomain_profile",
-            "bidomain_profile_read", "bidomain_launch_count", "bidomain_destroy", "bidomain_strerror"]
+            "bidomain_profile_read", "bidomain_launch_count", "schur_apply_noalloc", "bidomain_destroy",
+            "bidomain_strerror"]
 PROF = dict(rankk=0, panel=1, gemv=2, resid=3)
 
 
@@ -111,6 +112,7 @@ def load(build_if_missing: bool = False):
         "bidomain_profile": (I, [P, I]),
         "bidomain_profile_read": (I, [P, I, C.POINTER(C.c_double)]),
         "bidomain_launch_count": (C.c_int64, []),
+        "schur_apply_noalloc": (I, [P, P, P]),
         "bidomain_destroy": (I, [P]),
         "bidomain_strerror": (C.c_char_p, [I]),
     }

@@ -12,6 +12,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <stdexcept>
 #include <string>
 #include <type_traits>
@@ -981,6 +982,61 @@ int guard(bd_handle *h, F &&f) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// schur_apply_noalloc: the S_hat x product of schur_apply with its scratch (the
+// per-subdomain products S_Gamma^(j) R_j x before interface assembly) in a
+// file-scope device array instead of the handle's cudaMalloc'd buffer.  For
+// callers that must not allocate device memory when they apply the operator,
+// e.g. code that runs under a fixed device-memory budget or inside a host
+// framework that owns every allocation.  Capacity: kNoAllocScratch doubles
+// (4 MiB, held by every GPU that loads this library until the process exits).
+// ---------------------------------------------------------------------------
+static constexpr long long kNoAllocScratch = 1LL << 19;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratch];
+
+namespace {
+
+// Device address of the scratch array, looked up once per device with that
+// device current (the host-side symbol is only a stand-in, not an address).
+int noalloc_scratch(double **out) {
+  static std::mutex mu;
+  static std::map<int, double *> addr;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return BD_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = addr.find(dev);
+  if (it == addr.end()) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return BD_ERR_CUDA;
+    it = addr.emplace(dev, static_cast<double *>(p)).first;
+  }
+  *out = it->second;
+  return BD_OK;
+}
+
+template <class T>
+void schur_noalloc_t(bd_handle &h, Dense<T> &D, const double *x, double *y, double *scratch) {
+  launch_gemv<T>(h.gv_schur.n, h.gv_schur.max_rows, h.gv_schur.max_cols, h.gv_schur.d, D.Sorig, x, h.d_R, scratch,
+                 1.0, nullptr, h.s);
+  launch_gather_sum(h.nif, h.d_Rt_ptr, h.d_Rt_idx, scratch, y, h.gauge_iface, 1.0, nullptr, nullptr, h.s);
+}
+
+}  // namespace
+
+extern "C" int schur_apply_noalloc(bd_handle *h, const double *x, double *y) {
+  if (!h || !x || !y) return BD_ERR_ARG;
+  if (!h->linearized) return BD_ERR_STATE;
+  if ((long long)h->nG_tot > kNoAllocScratch) return BD_ERR_SCRATCH;
+  double *scratch = nullptr;
+  int st = noalloc_scratch(&scratch);
+  if (st != BD_OK) return st;
+  if (h->mixed()) schur_noalloc_t(*h, h->df, x, y, scratch);
+  else schur_noalloc_t(*h, h->dd, x, y, scratch);
+  if (cudaGetLastError() != cudaSuccess) return BD_ERR_CUDA;
+  if (cudaStreamSynchronize(h->s) != cudaSuccess) return BD_ERR_CUDA;
+  return BD_OK;
+}
+
 // ===========================================================================
 // C-ABI
 // ===========================================================================
@@ -1300,6 +1356,7 @@ const char *bidomain_strerror(int status) {
     case BD_ERR_CUDA: return "CUDA runtime error";
     case BD_ERR_NOMEM: return "out of device memory";
     case BD_ERR_STATE: return "call made in the wrong order";
+    case BD_ERR_SCRATCH: return "problem exceeds the static scratch of the no-allocation entry point";
     default: return "unknown status";
   }
 }
