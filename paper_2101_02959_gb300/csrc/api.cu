@@ -62,7 +62,7 @@ inline long long pad32(long long n) { return (n + 31) & ~31LL; }
 template <class T>
 struct Dense {
   T *K = nullptr, *Aug = nullptr, *Sorig = nullptr, *Z = nullptr, *SDD = nullptr, *Blk = nullptr, *CA = nullptr,
-    *Sinv = nullptr;
+    *Sinv = nullptr, *Dd = nullptr, *Linv = nullptr;
 };
 
 struct GemvSet {
@@ -211,9 +211,13 @@ struct bd_handle {
   // dense layouts
   EngineShape shK, shA, shC, shCo;
   MatDesc *d_Kdesc, *d_Adesc, *d_Cdesc, *d_Codesc;
-  long long K_el = 0, A_el = 0, So_el = 0, Z_el = 0, SDD_el = 0, Blk_el = 0, CA_el = 0, Sinv_el = 0;
+  long long K_el = 0, A_el = 0, So_el = 0, Z_el = 0, SDD_el = 0, Blk_el = 0, CA_el = 0, Sinv_el = 0, Dd_el = 0;
   int ld_co = 0;
-  GemvSet gv_schur, gv_local, gv_psit, gv_coarse, gv_sdd, gv_lgi, gv_lgit;
+  GemvSet gv_schur, gv_local, gv_psit, gv_coarse, gv_sdd, gv_lgi, gv_lgit, gv_drest, gv_dext;
+  GemmTask *d_gemm = nullptr;
+  int n_gemm = 0;
+  int *d_ext_idx = nullptr;
+  MatDesc *d_Sdesc = nullptr;
   CopySet cp_sorig, cp_sdd, cp_blk, cp_zx, cp_sinv, cp_coinv;
   int ncls = 0, npairs = 0, nlt = 0, nwt = 0, max_nc = 0;
   ClassTask *d_cls;
@@ -232,10 +236,12 @@ struct bd_handle {
   int hist_cap = 0;
   Dense<float> df;
   Dense<double> dd;
-  double *d_Co, *d_CoInv;
+  double *d_Co, *d_CoInv, *d_linv_co;
   bool linearized = false;
   std::string last_error;
   Profiler prof;
+  cudaGraphExec_t pcg_exec[2] = {nullptr, nullptr};  // captured PCG chunk per method
+  size_t pcg_nodes[2] = {0, 0};
   double gemv_schur_flops = 0, gemv_schur_bytes = 0, gemv_local_flops = 0, gemv_local_bytes = 0;
 
   bool mixed() const { return opt.precision == BD_MIXED; }
@@ -425,6 +431,11 @@ void setup_handle(bd_handle &h) {
   }
   h.d_Kdesc = m.upload(kd, s);
   h.d_Adesc = m.upload(ad, s);
+  {
+    std::vector<MatDesc> sdv(S);
+    for (int j = 0; j < S; ++j) sdv[j] = MatDesc{so_off[j], ldg[j], h.nG[j], 0, 0};
+    h.d_Sdesc = m.upload(sdv, s);
+  }
   // ---- deluxe classes, pairs and FETI-DP multipliers
   std::vector<ClassTask> cls;
   std::vector<PairTask> pairs;
@@ -457,7 +468,7 @@ void setup_handle(bd_handle &h) {
       pair_of[{c, j}] = (int)pairs.size();
       CopyTask cb{};
       cb.src_off = ad[j].off; cb.src_ld = ad[j].ld; cb.r0 = cb.c0 = dpos[j][c]; cb.rows = cb.cols = n;
-      cb.mode = 2; cb.sign = 1.0; cb.dst_off = pt.blk_off; cb.dst_ld = n;
+      cb.mode = 3; cb.sign = 1.0; cb.dst_off = pt.blk_off; cb.dst_ld = n;
       cp_blk.push_back(cb);
       pairs.push_back(pt);
       h.Blk_el += pad32((long long)n * n);
@@ -481,7 +492,7 @@ void setup_handle(bd_handle &h) {
     h.shC.m.push_back(mc); h.shC.e.push_back(n);
     h.shC.max_m = std::max(h.shC.max_m, mc); h.shC.max_e = std::max(h.shC.max_e, n);
     CopyTask cs{};
-    cs.src_off = md.off; cs.src_ld = md.ld; cs.r0 = cs.c0 = n; cs.rows = cs.cols = n; cs.mode = 2; cs.sign = -1.0;
+    cs.src_off = md.off; cs.src_ld = md.ld; cs.r0 = cs.c0 = n; cs.rows = cs.cols = n; cs.mode = 3; cs.sign = -1.0;
     cs.dst_off = ct.sinv_off; cs.dst_ld = n;
     cp_sinv.push_back(cs);
     h.Sinv_el += pad32((long long)n * n);
@@ -518,6 +529,37 @@ void setup_handle(bd_handle &h) {
   h.d_wt = m.upload(wts, s);
   h.d_went = m.upload(went, s);
   h.d_Cdesc = m.upload(cdesc, s);
+  // explicit deluxe operators: per class, D_C = [D_C^(j1) | D_C^(j2) | ...] (n x k n, row-major)
+  {
+    std::vector<GemmTask> gt;
+    std::vector<GemvDesc> rest, ext;
+    std::vector<int> ext_idx;
+    for (const ClassTask &ct : cls) {
+      const int n = ct.n, k = ct.pair_end - ct.pair_beg;
+      const long long base = h.Dd_el;
+      for (int q = ct.pair_beg; q < ct.pair_end; ++q) {
+        const int pl = q - ct.pair_beg;
+        gt.push_back(GemmTask{ct.sinv_off, pairs[q].blk_off, base + (long long)pl * n, n, k * n});
+        rest.push_back(GemvDesc{base + (long long)pl * n, k * n, n, n, ct.dual_start, pairs[q].ldual_off, 0});
+      }
+      ext.push_back(GemvDesc{base, k * n, n, k * n, (int)ext_idx.size(), ct.dual_start, 1});
+      for (int q = ct.pair_beg; q < ct.pair_end; ++q)
+        for (int v = 0; v < n; ++v) ext_idx.push_back(pairs[q].ldual_off + v);
+      h.Dd_el += pad32((long long)n * k * n);
+    }
+    h.n_gemm = (int)gt.size();
+    h.d_gemm = m.upload(gt, s);
+    h.d_ext_idx = m.upload(ext_idx, s);
+    auto mk = [&](const std::vector<GemvDesc> &v) {
+      GemvSet g;
+      g.n = (int)v.size();
+      for (auto &t : v) { g.max_rows = std::max(g.max_rows, t.rows); g.max_cols = std::max(g.max_cols, t.cols); }
+      g.d = m.upload(v, s);
+      return g;
+    };
+    h.gv_drest = mk(rest);
+    h.gv_dext = mk(ext);
+  }
   // ---- coarse problem
   {
     const int np = h.np;
@@ -542,6 +584,7 @@ void setup_handle(bd_handle &h) {
     h.d_co_src = m.upload(src, s);
     h.d_Co = m.alloc<double>((size_t)h.ld_co * 2 * np);
     h.d_CoInv = m.alloc<double>((size_t)np * np);
+    h.d_linv_co = m.alloc<double>(kNB * kNB);
   }
   // ---- GEMV and copy task sets
   auto gset = [&](const std::vector<GemvDesc> &v) {
@@ -571,15 +614,15 @@ void setup_handle(bd_handle &h) {
     g_lgi.push_back(GemvDesc{lgi, kd[j].ld, ng, ni, vec_off_I[j], h.giff_off[j], 0});
     g_lgit.push_back(GemvDesc{lgi, kd[j].ld, ng, ni, h.giff_off[j], vec_off_I[j], 3});
     CopyTask c{};
-    c.src_off = kd[j].off; c.src_ld = kd[j].ld; c.r0 = c.c0 = ni; c.rows = c.cols = ng; c.mode = 2; c.sign = 1.0;
+    c.src_off = kd[j].off; c.src_ld = kd[j].ld; c.r0 = c.c0 = ni; c.rows = c.cols = ng; c.mode = 3; c.sign = 1.0;
     c.dst_off = so_off[j]; c.dst_ld = ldg[j];
     c_sorig.push_back(c);
     CopyTask d{};
-    d.src_off = ad[j].off; d.src_ld = ad[j].ld; d.r0 = d.c0 = 0; d.rows = d.cols = nd; d.mode = 2; d.sign = 1.0;
+    d.src_off = ad[j].off; d.src_ld = ad[j].ld; d.r0 = d.c0 = 0; d.rows = d.cols = nd; d.mode = 3; d.sign = 1.0;
     d.dst_off = sdd_off[j]; d.dst_ld = ldx[j];
     c_sdd.push_back(d);
     CopyTask x{};
-    x.src_off = ad[j].off; x.src_ld = ad[j].ld; x.r0 = x.c0 = nd + npj; x.rows = x.cols = nd; x.mode = 2;
+    x.src_off = ad[j].off; x.src_ld = ad[j].ld; x.r0 = x.c0 = nd + npj; x.rows = x.cols = nd; x.mode = 3;
     x.sign = -1.0; x.dst_off = zx_off[j]; x.dst_ld = ldx[j];
     c_zx.push_back(x);
     CopyTask y{};
@@ -603,7 +646,7 @@ void setup_handle(bd_handle &h) {
   h.cp_sinv = cset(cp_sinv);
   {
     CopyTask c{};
-    c.src_off = 0; c.src_ld = h.ld_co; c.r0 = c.c0 = h.np; c.rows = c.cols = h.np; c.mode = 2; c.sign = -1.0;
+    c.src_off = 0; c.src_ld = h.ld_co; c.r0 = c.c0 = h.np; c.rows = c.cols = h.np; c.mode = 3; c.sign = -1.0;
     c.dst_off = 0; c.dst_ld = h.np;
     h.cp_coinv = cset({c});
   }
@@ -618,6 +661,8 @@ void setup_handle(bd_handle &h) {
     D.Blk = m.alloc<T>(h.Blk_el);
     D.CA = m.alloc<T>(h.CA_el);
     D.Sinv = m.alloc<T>(h.Sinv_el);
+    D.Dd = m.alloc<T>(h.Dd_el);
+    D.Linv = m.alloc<T>((size_t)std::max({h.nsub, h.ncls, 1}) * kNB * kNB);
   };
   if (h.mixed()) alloc_dense(h.df);
   else alloc_dense(h.dd);
@@ -652,21 +697,22 @@ void linearize_t(bd_handle &h, Dense<T> &D) {
   ck(cudaMemsetAsync(D.K, 0, sizeof(T) * h.K_el, s), "memset K");
   launch_assemble_local<T>(h.nq, h.d_q_sub, h.d_q_loc, h.d_q_node, h.d_q_nbr, h.d_q_stencil, h.d_q_mass, h.d_factor,
                            h.tau, h.d_Kdesc, D.K, s);
-  engine_partial_cholesky<T>(h.shK, h.d_Kdesc, D.K, h.d_err, s, &h.prof);
+  engine_partial_cholesky<T>(h.shK, h.d_Kdesc, D.K, h.d_err, s, D.Linv, &h.prof);
   launch_copy<T, T>(h.cp_sorig.n, h.cp_sorig.max_elems, h.cp_sorig.d, D.K, D.Sorig, s);
   long long max_a = 0;
   for (int j = 0; j < h.nsub; ++j) max_a = std::max(max_a, (long long)h.shA.m[j] * h.shA.m[j]);
-  launch_build_aug<T>(h.nsub, max_a, h.d_Kdesc, D.K, h.d_Adesc, D.Aug, h.d_nI, h.d_nD, h.d_tl_off, h.d_tl_ptr,
+  launch_build_aug<T>(h.nsub, max_a, h.d_Sdesc, D.Sorig, h.d_Adesc, D.Aug, h.d_nD, h.d_tl_off, h.d_tl_ptr,
                       h.d_tl_row, h.d_tl_val, s);
   launch_copy<T, T>(h.cp_sdd.n, h.cp_sdd.max_elems, h.cp_sdd.d, D.Aug, D.SDD, s);
   launch_copy<T, T>(h.cp_blk.n, h.cp_blk.max_elems, h.cp_blk.d, D.Aug, D.Blk, s);
-  engine_partial_cholesky<T>(h.shA, h.d_Adesc, D.Aug, h.d_err, s, &h.prof);
+  engine_partial_cholesky<T>(h.shA, h.d_Adesc, D.Aug, h.d_err, s, D.Linv, &h.prof);
   launch_copy<T, T>(h.cp_zx.n, h.cp_zx.max_elems, h.cp_zx.d, D.Aug, D.Z, s);
   launch_class_aug<T>(h.ncls, h.max_nc, h.d_cls, h.d_pairs, D.Blk, h.d_Cdesc, D.CA, s);
-  engine_partial_cholesky<T>(h.shC, h.d_Cdesc, D.CA, h.d_err, s);
+  engine_partial_cholesky<T>(h.shC, h.d_Cdesc, D.CA, h.d_err, s, D.Linv);
   launch_copy<T, T>(h.cp_sinv.n, h.cp_sinv.max_elems, h.cp_sinv.d, D.CA, D.Sinv, s);
+  launch_small_gemm<T>(h.n_gemm, h.max_nc, h.d_gemm, D.Sinv, D.Blk, D.Dd, s);
   launch_coarse_aug<T>(h.np, h.gauge_primal, h.d_co_ptr, h.d_co_src, D.Aug, h.d_Co, h.ld_co, s);
-  engine_partial_cholesky<double>(h.shCo, h.d_Codesc, h.d_Co, h.d_err, s);
+  engine_partial_cholesky<double>(h.shCo, h.d_Codesc, h.d_Co, h.d_err, s, h.d_linv_co);
   launch_copy<double, double>(h.cp_coinv.n, h.cp_coinv.max_elems, h.cp_coinv.d, h.d_Co, h.d_CoInv, s);
 }
 
@@ -702,9 +748,13 @@ void st_inv_t(bd_handle &h, Dense<T> &D, const double *rP, const double *rD, con
 template <class T>
 void bddc_t(bd_handle &h, Dense<T> &D, const double *r, double *z, const int *done) {
   launch_spmv(h.nd + h.np, h.d_Tt_ptr, h.d_Tt_col, h.d_Tt_val, r, h.d_rbar, h.nd + h.gauge_primal, done, h.s);
-  launch_deluxe_restrict<T>(h.ncls, h.max_nc, h.d_cls, h.d_pairs, D.Blk, D.Sinv, h.d_rbar, h.d_rD, done, h.s);
+  // deluxe restriction r_C^(j) = D_C^(j)T rbar_C (one thread per output, column reads)
+  launch_gemv_t<T>(h.gv_drest.n, h.gv_drest.max_rows, h.gv_drest.max_cols, h.gv_drest.d, D.Dd, h.d_rbar, nullptr,
+                   h.d_rD, 1.0, done, h.s);
   st_inv_t(h, D, h.d_rbar + h.nd, h.d_rD, done);
-  launch_deluxe_extend<T>(h.ncls, h.max_nc, h.d_cls, h.d_pairs, D.Blk, D.Sinv, h.d_ydc, h.d_zbar, done, h.s);
+  // deluxe extension zbar_C = sum_j D_C^(j) z_C^(j) (one row of [D^(j1) | D^(j2) | ...] per output)
+  launch_gemv<T>(h.gv_dext.n, h.gv_dext.max_rows, h.gv_dext.max_cols, h.gv_dext.d, D.Dd, h.d_ydc, h.d_ext_idx,
+                 h.d_zbar, 1.0, done, h.s);
   launch_spmv(h.nif, h.d_T_ptr, h.d_T_col, h.d_T_val, h.d_zbar, z, h.gauge_iface, done, h.s);
 }
 
@@ -746,7 +796,7 @@ int pcg(bd_handle &h, int n, const double *b, double *x, Op A, Pc M, bd_solve_st
   launch_pcg_start(h.d_ks, h.d_scal, s);
   launch_copy_vec(n, h.d_kz, h.d_kp, done, s);
   KrylovState out{};
-  for (int it = 0; it <= h.opt.ksp_max_it; it += kChunk) {
+  auto body = [&]() {
     for (int c = 0; c < kChunk; ++c) {
       A(h.d_kp, h.d_kq, done);
       launch_dot2(n, h.d_kp, h.d_kq, nullptr, nullptr, h.d_partial, h.d_scal, done, s);
@@ -756,6 +806,30 @@ int pcg(bd_handle &h, int n, const double *b, double *x, Op A, Pc M, bd_solve_st
       launch_dot2(n, h.d_kr, h.d_kz, h.d_kz, h.d_kz, h.d_partial, h.d_scal, done, s);
       launch_pcg_beta(h.d_ks, h.d_scal, h.d_hb, s);
       launch_pcg_p(n, h.d_ks, h.d_kz, h.d_kp, s);
+    }
+  };
+  const int key = h.opt.method == BD_FETIDP ? 1 : 0;
+  if (h.opt.use_graphs && !h.pcg_exec[key]) {
+    // capture one chunk of iterations once; every launch reads fixed handle buffers
+    const bool prof_on = h.prof.on;
+    h.prof.on = false;
+    const long long l0 = launch_count();
+    cudaGraph_t g = nullptr;
+    ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
+    body();
+    ck(cudaStreamEndCapture(s, &g), "capture end");
+    count_launch((int)(l0 - launch_count()));
+    ck(cudaGraphGetNodes(g, nullptr, &h.pcg_nodes[key]), "graph nodes");
+    ck(cudaGraphInstantiate(&h.pcg_exec[key], g, 0), "graph instantiate");
+    cudaGraphDestroy(g);
+    h.prof.on = prof_on;
+  }
+  for (int it = 0; it <= h.opt.ksp_max_it; it += kChunk) {
+    if (h.opt.use_graphs) {
+      ck(cudaGraphLaunch(h.pcg_exec[key], s), "graph launch");
+      count_launch((int)h.pcg_nodes[key]);
+    } else {
+      body();
     }
     ck(cudaGetLastError(), "pcg launch");
     ck(cudaMemcpyAsync(&out, h.d_ks, sizeof(out), cudaMemcpyDeviceToHost, s), "ks read");
@@ -1338,6 +1412,8 @@ int bidomain_destroy(bd_handle *h) {
   cudaStreamSynchronize(h->s);
   cudaStream_t s = h->s;
   const bool own = h->own_stream;
+  for (auto &g : h->pcg_exec)
+    if (g) cudaGraphExecDestroy(g);
   delete h;
   if (own) cudaStreamDestroy(s);
   return BD_OK;

@@ -46,6 +46,13 @@ __global__ void k_copy(const CopyTask *__restrict__ tasks, const TS *__restrict_
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     const int i = (int)(t / c.cols), k = (int)(t % c.cols);
     int r, cc;
+    if (c.mode == 3) {  // lower entry (i, k), k <= i, read along k; written to both halves
+      if (k > i) continue;
+      const TD v = (TD)(c.sign * (double)src[c.src_off + (long long)(c.r0 + i) * c.src_ld + c.c0 + k]);
+      dst[c.dst_off + (long long)i * c.dst_ld + k] = v;
+      dst[c.dst_off + (long long)k * c.dst_ld + i] = v;
+      continue;
+    }
     if (c.mode == 0) { r = c.r0 + i; cc = c.c0 + k; }
     else if (c.mode == 1) { r = c.r0 + k; cc = c.c0 + i; }
     else { r = c.r0 + max(i, k); cc = c.c0 + min(i, k); }
@@ -55,32 +62,30 @@ __global__ void k_copy(const CopyTask *__restrict__ tasks, const TS *__restrict_
 
 // ---- augmented matrix of the constrained local problem ------------------------
 // Aug = [[Sb_DD, Sb_DP, I], [Sb_PD, Sb_PP, 0], [I, 0, 0]] with Sb = T^T S T
-// (change of basis for the primal averages), S read from the lower triangle of
-// the trailing block of the factored local matrix.  T_loc is CSC by
-// transformed dof.  One thread per entry.
+// (change of basis for the primal averages), S read from the full symmetric
+// copy of S_Gamma.  T_loc is CSC by transformed dof.  One thread per entry.
 template <typename T>
-__global__ void k_build_aug(const MatDesc *__restrict__ kdesc, const T *__restrict__ kbase,
-                            const MatDesc *__restrict__ adesc, T *__restrict__ abase, const int *__restrict__ nI,
+__global__ void k_build_aug(const MatDesc *__restrict__ sdesc, const T *__restrict__ sbase,
+                            const MatDesc *__restrict__ adesc, T *__restrict__ abase,
                             const int *__restrict__ nD, const int *__restrict__ tptr_off,
                             const int *__restrict__ tptr, const int *__restrict__ trow,
                             const double *__restrict__ tval) {
   const int j = blockIdx.y;
   const MatDesc ad = adesc[j];
   const long long tot = (long long)ad.m * ad.m;
-  const MatDesc kd = kdesc[j];
-  const int ni = nI[j], nd = nD[j];
+  const MatDesc sd = sdesc[j];
+  const int nd = nD[j];
   const int nt = ad.m - nd;  // nD + nP
   const int *P = tptr + tptr_off[j];
-  const T *S = kbase + kd.off;
+  const T *S = sbase + sd.off;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
     const int a = (int)(t / ad.m), b = (int)(t % ad.m);
+    if (b > a) continue;  // the factorisation and the copies read the lower triangle only
     double v = 0.0;
     if (a < nt && b < nt) {
       for (int p = P[a]; p < P[a + 1]; ++p)
         for (int q = P[b]; q < P[b + 1]; ++q) {
-          const int ra = trow[p], rb = trow[q];
-          const int hi = max(ra, rb), lo = min(ra, rb);
-          v += tval[p] * tval[q] * (double)S[(long long)(ni + hi) * kd.ld + ni + lo];
+          v += tval[p] * tval[q] * (double)S[(long long)trow[p] * sd.ld + trow[q]];
         }
     } else if (a >= nt && b < nd) {
       v = (a - nt == b) ? 1.0 : 0.0;
@@ -161,9 +166,44 @@ __global__ void k_gather_sum(int n, const int *__restrict__ ptr, const int *__re
   y[r] = (r == zero) ? 0.0 : v;
 }
 
-// ---- deluxe restriction and extension (Section 4.2) -----------------------------
-// restrict: t = (sum S)^-1 rbar_C; r_C^(j) = S_C^(j) t      (D_C^(j)T rbar_C)
-// extend:   acc = sum_j S_C^(j) z_C^(j); zbar_C = (sum S)^-1 acc   (sum_j D_C^(j) z_C^(j))
+// ---- batched small GEMM C = A B (deluxe D_C^(j) = (sum S)^-1 S_C^(j)) ----------
+// 32x32 output tiles, 256 threads (2x2 per thread), K in chunks of 32.
+template <typename T>
+__global__ void __launch_bounds__(256) k_small_gemm(const GemmTask *__restrict__ tasks, const T *__restrict__ A,
+                                                    const T *__restrict__ B, T *__restrict__ C) {
+  const GemmTask t = tasks[blockIdx.y];
+  const int nt = ceil_div(t.n, 32);
+  if ((int)blockIdx.x >= nt * nt) return;
+  const int ti = blockIdx.x / nt, tj = blockIdx.x % nt;
+  __shared__ T As[32][33], Bs[32][33];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  T acc[2][2] = {{T(0), T(0)}, {T(0), T(0)}};
+  for (int k0 = 0; k0 < t.n; k0 += 32) {
+    for (int q = threadIdx.x; q < 32 * 32; q += 256) {
+      const int i = q >> 5, k = q & 31;
+      const int ra = ti * 32 + i, ca = k0 + k;
+      As[i][k] = (ra < t.n && ca < t.n) ? A[t.a_off + (long long)ra * t.n + ca] : T(0);
+      const int rb = k0 + i, cb = tj * 32 + k;
+      Bs[i][k] = (rb < t.n && cb < t.n) ? B[t.b_off + (long long)rb * t.n + cb] : T(0);
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < 32; ++k) {
+      const T a0 = As[ty][k], a1 = As[ty + 16][k];
+      const T b0 = Bs[k][tx], b1 = Bs[k][tx + 16];
+      acc[0][0] += a0 * b0; acc[0][1] += a0 * b1;
+      acc[1][0] += a1 * b0; acc[1][1] += a1 * b1;
+    }
+    __syncthreads();
+  }
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      const int r = ti * 32 + ty + 16 * i, c = tj * 32 + tx + 16 * j;
+      if (r < t.n && c < t.n) C[t.c_off + (long long)r * t.ldc + c] = acc[i][j];
+    }
+}
+
+// ---- small dense matvec in shared memory (FETI-DP scaled jumps) --------------
 template <typename T>
 __device__ inline void smem_gemv(const T *__restrict__ A, int n, const T *__restrict__ x, T *__restrict__ y) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -173,55 +213,6 @@ __device__ inline void smem_gemv(const T *__restrict__ A, int n, const T *__rest
     acc = warp_sum(acc);
     if (lane == 0) y[u] = acc;
   }
-}
-
-template <typename T>
-__global__ void k_deluxe_restrict(const ClassTask *__restrict__ cls, const PairTask *__restrict__ pairs,
-                                  const T *__restrict__ blk, const T *__restrict__ sinv, const double *__restrict__ rbar,
-                                  double *__restrict__ rD, const int *__restrict__ done) {
-  if (done && *done) return;
-  const ClassTask c = cls[blockIdx.x];
-  extern __shared__ unsigned char smem_raw[];
-  T *rb = reinterpret_cast<T *>(smem_raw);
-  T *tt = rb + c.n;
-  T *out = tt + c.n;
-  for (int u = threadIdx.x; u < c.n; u += blockDim.x) rb[u] = (T)rbar[c.dual_start + u];
-  __syncthreads();
-  smem_gemv(sinv + c.sinv_off, c.n, rb, tt);
-  __syncthreads();
-  for (int p = c.pair_beg; p < c.pair_end; ++p) {
-    const PairTask pt = pairs[p];
-    smem_gemv(blk + pt.blk_off, c.n, tt, out);
-    __syncthreads();
-    for (int u = threadIdx.x; u < c.n; u += blockDim.x) rD[pt.ldual_off + u] = (double)out[u];
-    __syncthreads();
-  }
-}
-
-template <typename T>
-__global__ void k_deluxe_extend(const ClassTask *__restrict__ cls, const PairTask *__restrict__ pairs,
-                                const T *__restrict__ blk, const T *__restrict__ sinv, const double *__restrict__ zD,
-                                double *__restrict__ zbar, const int *__restrict__ done) {
-  if (done && *done) return;
-  const ClassTask c = cls[blockIdx.x];
-  extern __shared__ unsigned char smem_raw[];
-  T *acc = reinterpret_cast<T *>(smem_raw);
-  T *zz = acc + c.n;
-  T *tmp = zz + c.n;
-  for (int u = threadIdx.x; u < c.n; u += blockDim.x) acc[u] = T(0);
-  __syncthreads();
-  for (int p = c.pair_beg; p < c.pair_end; ++p) {
-    const PairTask pt = pairs[p];
-    for (int u = threadIdx.x; u < c.n; u += blockDim.x) zz[u] = (T)zD[pt.ldual_off + u];
-    __syncthreads();
-    smem_gemv(blk + pt.blk_off, c.n, zz, tmp);
-    __syncthreads();
-    for (int u = threadIdx.x; u < c.n; u += blockDim.x) acc[u] += tmp[u];
-    __syncthreads();
-  }
-  smem_gemv(sinv + c.sinv_off, c.n, acc, tmp);
-  __syncthreads();
-  for (int u = threadIdx.x; u < c.n; u += blockDim.x) zbar[c.dual_start + u] = (double)tmp[u];
 }
 
 // ---- FETI-DP jump operators (Section 4.3) ---------------------------------------
@@ -483,11 +474,11 @@ void launch_copy(int ntasks, long long max_elems, const CopyTask *tasks, const T
 }
 
 template <typename T>
-void launch_build_aug(int nsub, long long max_elems, const MatDesc *kdesc, const T *kbase, const MatDesc *adesc,
-                      T *abase, const int *nI, const int *nD, const int *tptr_off, const int *tptr,
-                      const int *trow, const double *tval, cudaStream_t s) {
+void launch_build_aug(int nsub, long long max_elems, const MatDesc *sdesc, const T *sbase, const MatDesc *adesc,
+                      T *abase, const int *nD, const int *tptr_off, const int *tptr, const int *trow,
+                      const double *tval, cudaStream_t s) {
   const int gx = (int)std::min<long long>((max_elems + 255) / 256, 8192);
-  k_build_aug<T><<<dim3(gx, nsub), 256, 0, s>>>(kdesc, kbase, adesc, abase, nI, nD, tptr_off, tptr, trow, tval);
+  k_build_aug<T><<<dim3(gx, nsub), 256, 0, s>>>(sdesc, sbase, adesc, abase, nD, tptr_off, tptr, trow, tval);
   count_launch();
 }
 
@@ -509,6 +500,14 @@ void launch_coarse_aug(int np, int gauge, const int *ptr, const long long *src, 
   count_launch();
 }
 
+template <typename T>
+void launch_small_gemm(int ntasks, int max_n, const GemmTask *tasks, const T *A, const T *B, T *C, cudaStream_t s) {
+  if (ntasks == 0) return;
+  const int nt = ceil_div(max_n, 32);
+  k_small_gemm<T><<<dim3(nt * nt, ntasks), 256, 0, s>>>(tasks, A, B, C);
+  count_launch();
+}
+
 void launch_spmv(int n, const int *ptr, const int *col, const double *val, const double *x, double *y, int zero,
                  const int *done, cudaStream_t s) {
   if (n == 0) return;
@@ -520,22 +519,6 @@ void launch_gather_sum(int n, const int *ptr, const int *idx, const double *src,
                        const double *addend, const int *done, cudaStream_t s) {
   if (n == 0) return;
   k_gather_sum<<<GRID1(n)>>>(n, ptr, idx, src, y, zero, alpha, addend, done);
-  count_launch();
-}
-
-template <typename T>
-void launch_deluxe_restrict(int ncls, int max_n, const ClassTask *cls, const PairTask *pairs, const T *blk,
-                            const T *sinv, const double *rbar, double *rD, const int *done, cudaStream_t s) {
-  if (ncls == 0) return;
-  k_deluxe_restrict<T><<<ncls, 256, 3 * sizeof(T) * max_n, s>>>(cls, pairs, blk, sinv, rbar, rD, done);
-  count_launch();
-}
-
-template <typename T>
-void launch_deluxe_extend(int ncls, int max_n, const ClassTask *cls, const PairTask *pairs, const T *blk,
-                          const T *sinv, const double *zD, double *zbar, const int *done, cudaStream_t s) {
-  if (ncls == 0) return;
-  k_deluxe_extend<T><<<ncls, 256, 3 * sizeof(T) * max_n, s>>>(cls, pairs, blk, sinv, zD, zbar, done);
   count_launch();
 }
 
@@ -655,16 +638,13 @@ void launch_dot2(int n, const double *a0, const double *b0, const double *a1, co
                                          const double *, const double *, double, const MatDesc *, T *,         \
                                          cudaStream_t);                                                        \
   template void launch_build_aug<T>(int, long long, const MatDesc *, const T *, const MatDesc *, T *,           \
-                                    const int *, const int *, const int *, const int *, const int *,            \
-                                    const double *, cudaStream_t);                                             \
+                                    const int *, const int *, const int *, const int *, const double *,         \
+                                    cudaStream_t);                                                             \
+  template void launch_small_gemm<T>(int, int, const GemmTask *, const T *, const T *, T *, cudaStream_t);      \
   template void launch_class_aug<T>(int, int, const ClassTask *, const PairTask *, const T *, const MatDesc *,  \
                                     T *, cudaStream_t);                                                        \
   template void launch_coarse_aug<T>(int, int, const int *, const long long *, const T *, double *, int,        \
                                      cudaStream_t);                                                            \
-  template void launch_deluxe_restrict<T>(int, int, const ClassTask *, const PairTask *, const T *, const T *,  \
-                                          const double *, double *, const int *, cudaStream_t);                \
-  template void launch_deluxe_extend<T>(int, int, const ClassTask *, const PairTask *, const T *, const T *,    \
-                                        const double *, double *, const int *, cudaStream_t);                  \
   template void launch_jump_dt<T>(int, int, const WTask *, const WEnt *, const T *, const T *, const double *,  \
                                   double *, const int *, cudaStream_t);                                        \
   template void launch_jump_d<T>(int, int, const LamTask *, const PairTask *, const T *, const T *,             \

@@ -20,9 +20,11 @@ void launch_assemble_local(int nq, const int *q_sub, const int *q_loc, const int
 template <typename TS, typename TD>
 void launch_copy(int ntasks, long long max_elems, const CopyTask *tasks, const TS *src, TD *dst, cudaStream_t s);
 template <typename T>
-void launch_build_aug(int nsub, long long max_elems, const MatDesc *kdesc, const T *kbase, const MatDesc *adesc,
-                      T *abase, const int *nI, const int *nD, const int *tptr_off, const int *tptr,
-                      const int *trow, const double *tval, cudaStream_t s);
+void launch_build_aug(int nsub, long long max_elems, const MatDesc *sdesc, const T *sbase, const MatDesc *adesc,
+                      T *abase, const int *nD, const int *tptr_off, const int *tptr, const int *trow,
+                      const double *tval, cudaStream_t s);
+template <typename T>
+void launch_small_gemm(int ntasks, int max_n, const GemmTask *tasks, const T *A, const T *B, T *C, cudaStream_t s);
 template <typename T>
 void launch_class_aug(int ncls, int max_n, const ClassTask *cls, const PairTask *pairs, const T *blk,
                       const MatDesc *cdesc, T *cbase, cudaStream_t s);
@@ -33,12 +35,6 @@ void launch_spmv(int n, const int *ptr, const int *col, const double *val, const
                  const int *done, cudaStream_t s);
 void launch_gather_sum(int n, const int *ptr, const int *idx, const double *src, double *y, int zero, double alpha,
                        const double *addend, const int *done, cudaStream_t s);
-template <typename T>
-void launch_deluxe_restrict(int ncls, int max_n, const ClassTask *cls, const PairTask *pairs, const T *blk,
-                            const T *sinv, const double *rbar, double *rD, const int *done, cudaStream_t s);
-template <typename T>
-void launch_deluxe_extend(int ncls, int max_n, const ClassTask *cls, const PairTask *pairs, const T *blk,
-                          const T *sinv, const double *zD, double *zbar, const int *done, cudaStream_t s);
 void launch_jump(int nlt, int max_n, const LamTask *lt, const PairTask *pairs, const double *w, double *lam,
                  const int *done, cudaStream_t s);
 void launch_jump_t(int nwt, int max_n, const WTask *wt, const WEnt *ent, const double *lam, double *w,

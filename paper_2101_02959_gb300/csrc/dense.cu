@@ -20,53 +20,76 @@ template <typename T> __device__ inline T dsqrt(T v);
 template <> __device__ inline float dsqrt<float>(float v) { return sqrtf(v); }
 template <> __device__ inline double dsqrt<double>(double v) { return sqrt(v); }
 
-// ---- panel step 1: factor the w x w diagonal block in place (one warp per matrix)
+// ---- panel step 1: factor the w x w diagonal block in place and form L_kk^-1 --
+// One warp per matrix.  Lane r keeps row r of the block in registers; column c
+// of L is broadcast with shuffles, so the right-looking update has no shared-
+// memory dependency chain.  L_kk^-1 (used by the panel solve) goes to `linv`.
 template <typename T>
 __global__ void __launch_bounds__(32) k_potrf(const MatDesc *__restrict__ desc, T *__restrict__ base, int k0,
-                                              int *__restrict__ err) {
+                                              int *__restrict__ err, T *__restrict__ linv) {
   const MatDesc d = desc[blockIdx.x];
   if (k0 >= d.e) return;
   const int w = min(kNB, d.e - k0);
   T *A = base + d.off;
   __shared__ T Ls[kNB][kNB + 1];
   const int r = threadIdx.x;
-  for (int c = 0; c < kNB; ++c) Ls[r][c] = (r < w && c <= r) ? A[(long long)(k0 + r) * d.ld + k0 + c] : T(0);
+#pragma unroll 8
+  for (int q = 0; q < kNB; ++q)  // row q, lane = column: coalesced, independent loads
+    Ls[q][r] = (q < w && r <= q) ? A[(long long)(k0 + q) * d.ld + k0 + r] : T(0);
   __syncwarp();
-  for (int c = 0; c < w; ++c) {
-    T dg = Ls[c][c];
-    const bool bad = !(dg > T(0));
-    if (bad) dg = T(1);
-    const T sq = dsqrt(dg);
-    __syncwarp();
-    if (r == c) {
-      Ls[c][c] = sq;
-      if (bad) atomicOr(err, DEV_ERR_NOT_SPD);
+  T row[kNB];
+#pragma unroll
+  for (int c = 0; c < kNB; ++c) row[c] = Ls[r][c];
+  bool bad = false;
+#pragma unroll
+  for (int c = 0; c < kNB; ++c) {
+    if (c < w) {
+      T dg = __shfl_sync(0xffffffffu, row[c], c);
+      if (!(dg > T(0))) { bad = true; dg = T(1); }
+      const T sq = dsqrt(dg);
+      if (r == c) row[c] = sq;
+      else if (r > c) row[c] = row[c] / sq;
+      const T lrc = row[c];
+#pragma unroll
+      for (int t = c + 1; t < kNB; ++t) {
+        const T ltc = __shfl_sync(0xffffffffu, row[c], t);
+        if (r >= t) row[t] -= lrc * ltc;
+      }
     }
-    if (r > c && r < w) Ls[r][c] /= sq;
-    __syncwarp();
-    if (r > c && r < w) {
-      const T lrc = Ls[r][c];
-      for (int t = c + 1; t <= r; ++t) Ls[r][t] -= lrc * Ls[t][c];
-    }
-    __syncwarp();
   }
-  if (r < w)
-    for (int c = 0; c <= r; ++c) A[(long long)(k0 + r) * d.ld + k0 + c] = Ls[r][c];
+  if (bad && r == 0) atomicOr(err, DEV_ERR_NOT_SPD);
+#pragma unroll
+  for (int c = 0; c < kNB; ++c) Ls[r][c] = (c <= r && r < w && c < w) ? row[c] : (r == c ? T(1) : T(0));
+  __syncwarp();
+#pragma unroll 8
+  for (int q = 0; q < w; ++q)  // write back row q, lane = column
+    if (r <= q) A[(long long)(k0 + q) * d.ld + k0 + r] = Ls[q][r];
+  // L_kk^-1: lane j solves L y = e_j by forward substitution (column j of the inverse)
+  T y[kNB];
+#pragma unroll
+  for (int i = 0; i < kNB; ++i) {
+    T v = (i == r) ? T(1) : T(0);
+#pragma unroll
+    for (int t = 0; t < i; ++t) v -= Ls[i][t] * y[t];
+    y[i] = (i >= r) ? v / Ls[i][i] : T(0);
+  }
+  T *Li = linv + (long long)blockIdx.x * kNB * kNB;
+#pragma unroll
+  for (int i = 0; i < kNB; ++i) Li[i * kNB + r] = y[i];  // Li[i][j] = (L^-1)[i][j], lane = j
 }
 
-// ---- panel step 2: rows below the diagonal block, x L_kk^T = a (one thread per row)
+// ---- panel step 2: rows below the diagonal block, x = a L_kk^-T (one thread per row)
 template <typename T>
-__global__ void __launch_bounds__(128) k_trsm(const MatDesc *__restrict__ desc, T *__restrict__ base, int k0) {
+__global__ void __launch_bounds__(128) k_trsm(const MatDesc *__restrict__ desc, T *__restrict__ base, int k0,
+                                              const T *__restrict__ linv) {
   const MatDesc d = desc[blockIdx.y];
   if (k0 >= d.e) return;
   const int w = min(kNB, d.e - k0);
   if (k0 + w + blockIdx.x * 128 >= d.m) return;
   T *A = base + d.off;
-  __shared__ T Ls[kNB][kNB + 1];
-  for (int t = threadIdx.x; t < kNB * kNB; t += 128) {
-    const int r = t / kNB, c = t % kNB;
-    Ls[r][c] = (r < w && c <= r) ? A[(long long)(k0 + r) * d.ld + k0 + c] : T(0);
-  }
+  __shared__ T Li[kNB][kNB];
+  const T *src = linv + (long long)blockIdx.y * kNB * kNB;
+  for (int t = threadIdx.x; t < kNB * kNB; t += 128) Li[t / kNB][t % kNB] = src[t];
   __syncthreads();
   const int row = k0 + w + blockIdx.x * 128 + threadIdx.x;
   if (row >= d.m) return;
@@ -74,14 +97,13 @@ __global__ void __launch_bounds__(128) k_trsm(const MatDesc *__restrict__ desc, 
   T x[kNB];
 #pragma unroll
   for (int c = 0; c < kNB; ++c) x[c] = (c < w) ? a[c] : T(0);
+  // x_out[c] = sum_{t <= c} x[t] (L^-1)[c][t]: independent dot products
 #pragma unroll
-  for (int c = 0; c < kNB; ++c) {
-    if (c < w) {
-      T v = x[c];
+  for (int c = kNB - 1; c >= 0; --c) {
+    T v = T(0);
 #pragma unroll
-      for (int t = 0; t < c; ++t) v -= x[t] * Ls[c][t];
-      x[c] = v / Ls[c][c];
-    }
+    for (int t = 0; t <= c; ++t) v += x[t] * Li[c][t];
+    x[c] = v;
   }
 #pragma unroll
   for (int c = 0; c < kNB; ++c)
@@ -117,8 +139,8 @@ __global__ void __launch_bounds__(256) k_rankk(const MatDesc *__restrict__ desc,
   const int r0 = row0 + ti * kTB, c0 = row0 + tj * kTB;
   if (r0 >= d.m || c0 >= colend || ke <= kb) return;
   T *A = base + d.off;
-  __shared__ T As[kKC][kTB + 4];
-  __shared__ T Bs[kKC][kTB + 4];
+  __shared__ T As[kKC][kTB + 1];  // row pad 65: the strided stores below hit distinct banks
+  __shared__ T Bs[kKC][kTB + 1];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   T acc[4][4];
 #pragma unroll
@@ -175,7 +197,7 @@ static double trapezoid(long long t0, long long e, long long m) {
 
 template <typename T>
 void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s,
-                             ProfHook *prof) {
+                             T *linv, ProfHook *prof) {
   if (sh.count == 0) return;
   for (int k0 = 0; k0 < sh.max_e; k0 += kNB) {
     int max_below = 0, max_rt = 0, max_ct = 0;
@@ -193,11 +215,11 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
       by_upd += sizeof(T) * (2.0 * ent + (double)w * (below + sh.e[b] - k0 - w));
     }
     if (prof) prof->begin(PROF_PANEL, s);
-    k_potrf<T><<<sh.count, 32, 0, s>>>(d_desc, base, k0, d_err);
+    k_potrf<T><<<sh.count, 32, 0, s>>>(d_desc, base, k0, d_err, linv);
     count_launch();
     if (max_below > 0) {
       dim3 gp(ceil_div(max_below, 128), sh.count);
-      k_trsm<T><<<gp, 128, 0, s>>>(d_desc, base, k0);
+      k_trsm<T><<<gp, 128, 0, s>>>(d_desc, base, k0, linv);
       count_launch();
     }
     if (prof) prof->end(PROF_PANEL, s, fl_panel, 0.0);
@@ -246,9 +268,16 @@ __global__ void __launch_bounds__(256) k_gemv(const GemvDesc *__restrict__ tasks
   const int rend = min(t.rows, rbeg + 64);
   for (int r = rbeg + wid; r < rend; r += 8) {
     const T *row = A + t.a_off + (long long)r * t.ld;
-    T acc = T(0);
-    for (int c = lane; c < t.cols; c += 32) acc += row[c] * xs[c];
-    acc = warp_sum(acc);
+    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+    int c = lane;
+    for (; c + 96 < t.cols; c += 128) {
+      a0 += row[c] * xs[c];
+      a1 += row[c + 32] * xs[c + 32];
+      a2 += row[c + 64] * xs[c + 64];
+      a3 += row[c + 96] * xs[c + 96];
+    }
+    for (; c < t.cols; c += 32) a0 += row[c] * xs[c];
+    const T acc = warp_sum((a0 + a1) + (a2 + a3));
     if (lane == 0) {
       const double v = alpha * (double)acc;
       y[t.y_off + r] = (t.flags & 2) ? y[t.y_off + r] + v : v;
@@ -270,9 +299,17 @@ __global__ void __launch_bounds__(256) k_gemv_t(const GemvDesc *__restrict__ tas
   __syncthreads();
   const int a = blockIdx.x * blockDim.x + threadIdx.x;
   if (a >= t.cols) return;
-  T acc = T(0);
-  for (int p = 0; p < t.rows; ++p) acc += A[t.a_off + (long long)p * t.ld + a] * xs[p];
-  const double v = alpha * (double)acc;
+  const T *col = A + t.a_off + a;
+  T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+  int p = 0;
+  for (; p + 3 < t.rows; p += 4) {
+    a0 += col[(long long)p * t.ld] * xs[p];
+    a1 += col[(long long)(p + 1) * t.ld] * xs[p + 1];
+    a2 += col[(long long)(p + 2) * t.ld] * xs[p + 2];
+    a3 += col[(long long)(p + 3) * t.ld] * xs[p + 3];
+  }
+  for (; p < t.rows; ++p) a0 += col[(long long)p * t.ld] * xs[p];
+  const double v = alpha * (double)((a0 + a1) + (a2 + a3));
   y[t.y_off + a] = (t.flags & 2) ? y[t.y_off + a] + v : v;
 }
 
@@ -296,33 +333,48 @@ void launch_gemv_t(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tas
   count_launch();
 }
 
-// ---- batched triangular solves (one CTA per matrix) ---------------------------
-// lower: y = L^-1 b, left-looking over 32-row blocks; upper: y = L^-T b,
-// right-to-left over 32-row blocks.  The vector lives in shared memory.
+// ---- batched triangular solves (one CTA of 32 warps per matrix) ---------------
+// lower: y = L^-1 b, left-looking over 32-row blocks, one warp per block row;
+// upper: y = L^-T b, right-to-left, warps striding over the rows below the block.
+// The 32x32 diagonal block is staged in shared memory; the vector lives there too.
 template <typename T>
-__global__ void __launch_bounds__(256) k_trsv(const MatDesc *__restrict__ desc, const int *__restrict__ vec_off,
-                                              const T *__restrict__ base, const double *__restrict__ b,
-                                              double *__restrict__ y, int transpose) {
+__global__ void __launch_bounds__(1024) k_trsv(const MatDesc *__restrict__ desc, const int *__restrict__ vec_off,
+                                               const T *__restrict__ base, const double *__restrict__ b,
+                                               double *__restrict__ y, int transpose) {
   const MatDesc d = desc[blockIdx.x];
   const int n = d.e;
   const T *L = base + d.off;
   extern __shared__ unsigned char smem_raw[];
   T *v = reinterpret_cast<T *>(smem_raw);
-  __shared__ T part[8][32];
+  __shared__ T part[32][33];
+  __shared__ T Lb[32][33];
   const int off = vec_off[blockIdx.x];
   for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = (T)b[off + i];
-  __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nblk = ceil_div(n, 32);
   for (int q = 0; q < nblk; ++q) {
     const int bk = transpose ? nblk - 1 - q : q;
     const int r0 = bk * 32, r1 = min(n, r0 + 32);
+    {  // diagonal block, coalesced: warp wid loads row r0 + wid
+      const int i = wid, k = lane;
+      Lb[i][k] = (r0 + i < r1 && k <= i) ? L[(long long)(r0 + i) * d.ld + r0 + k] : T(0);
+    }
+    __syncthreads();
     if (!transpose) {
-      // v[r] -= sum_{c < r0} L[r][c] v[c] for r in the block (warps share rows)
-      for (int r = r0 + wid; r < r1; r += 8) {
-        T acc = T(0);
-        for (int c = lane; c < r0; c += 32) acc += L[(long long)r * d.ld + c] * v[c];
-        acc = warp_sum(acc);
+      // v[r] -= sum_{c < r0} L[r][c] v[c]; warp wid owns row r0 + wid
+      const int r = r0 + wid;
+      if (r < r1) {
+        const T *Lr = L + (long long)r * d.ld;
+        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+        int c = lane;
+        for (; c + 96 < r0; c += 128) {
+          a0 += Lr[c] * v[c];
+          a1 += Lr[c + 32] * v[c + 32];
+          a2 += Lr[c + 64] * v[c + 64];
+          a3 += Lr[c + 96] * v[c + 96];
+        }
+        for (; c < r0; c += 32) a0 += Lr[c] * v[c];
+        const T acc = warp_sum((a0 + a1) + (a2 + a3));
         if (lane == 0) v[r] -= acc;
       }
       __syncthreads();
@@ -330,31 +382,36 @@ __global__ void __launch_bounds__(256) k_trsv(const MatDesc *__restrict__ desc, 
         const int r = r0 + lane;
         T vr = (r < r1) ? v[r] : T(0);
         for (int c = r0; c < r1; ++c) {
-          const T xc = __shfl_sync(0xffffffffu, vr / ((r == c) ? L[(long long)r * d.ld + r] : T(1)), c - r0);
+          const T xc = __shfl_sync(0xffffffffu, vr / ((r == c) ? Lb[lane][lane] : T(1)), c - r0);
           if (r == c) vr = xc;
-          else if (r > c && r < r1) vr -= L[(long long)r * d.ld + c] * xc;
+          else if (r > c && r < r1) vr -= Lb[lane][c - r0] * xc;
         }
         if (r < r1) v[r] = vr;
       }
       __syncthreads();
     } else {
-      // v[r] -= sum_{c >= r1} L[c][r] v[c] for r in the block
-      T acc = T(0);
-      for (int c = r1 + wid; c < n; c += 8) {
-        const int r = r0 + lane;
-        if (r < r1) acc += L[(long long)c * d.ld + r] * v[c];
+      // v[r] -= sum_{c >= r1} L[c][r] v[c] for r in the block; warp wid takes rows r1 + wid + 32 k
+      T a0 = T(0), a1 = T(0);
+      const int r = r0 + lane;
+      if (r < r1) {
+        int c = r1 + wid;
+        for (; c + 32 < n; c += 64) {
+          a0 += L[(long long)c * d.ld + r] * v[c];
+          a1 += L[(long long)(c + 32) * d.ld + r] * v[c + 32];
+        }
+        for (; c < n; c += 32) a0 += L[(long long)c * d.ld + r] * v[c];
       }
-      part[wid][lane] = acc;
+      part[wid][lane] = a0 + a1;
       __syncthreads();
       if (wid == 0) {
-        const int r = r0 + lane;
         T s = T(0);
-        for (int k = 0; k < 8; ++k) s += part[k][lane];
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) s += part[k][lane];
         T vr = (r < r1) ? v[r] - s : T(0);
         for (int c = r1 - 1; c >= r0; --c) {
-          const T xc = __shfl_sync(0xffffffffu, vr / ((r == c) ? L[(long long)r * d.ld + r] : T(1)), c - r0);
+          const T xc = __shfl_sync(0xffffffffu, vr / ((r == c) ? Lb[lane][lane] : T(1)), c - r0);
           if (r == c) vr = xc;
-          else if (r < c && r < r1) vr -= L[(long long)c * d.ld + r] * xc;
+          else if (r < c && r < r1) vr -= Lb[c - r0][lane] * xc;
         }
         if (r < r1) v[r] = vr;
       }
@@ -369,13 +426,13 @@ void launch_trsv(int count, int max_n, const MatDesc *d_desc, const int *vec_off
                  double *y, bool transpose, cudaStream_t s) {
   if (count == 0) return;
   const size_t sm = sizeof(T) * (size_t)std::max(1, max_n);
-  k_trsv<T><<<count, 256, sm, s>>>(d_desc, vec_off, base, b, y, transpose ? 1 : 0);
+  k_trsv<T><<<count, 1024, sm, s>>>(d_desc, vec_off, base, b, y, transpose ? 1 : 0);
   count_launch();
 }
 
 #define BD_INST(T)                                                                                              \
   template void engine_partial_cholesky<T>(const EngineShape &, const MatDesc *, T *, int *, cudaStream_t,    \
-                                           ProfHook *);     \
+                                           T *, ProfHook *);     \
   template void launch_gemv<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *,        \
                                double *, double, const int *, cudaStream_t);                                   \
   template void launch_gemv_t<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *,      \

@@ -57,9 +57,10 @@ struct EngineShape {
   int max_e, max_m;
   std::vector<int> m, e;  // host copies for per-step grid sizes
 };
+// linv: scratch of count * kNB * kNB elements (the inverse of each diagonal block).
 template <typename T>
 void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s,
-                             ProfHook *prof = nullptr);
+                             T *linv, ProfHook *prof = nullptr);
 
 // y = alpha * A x (+ y): tasks in d_tasks (GemvDesc); x gathered through xidx when flagged.
 template <typename T>

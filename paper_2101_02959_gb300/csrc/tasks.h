@@ -7,10 +7,17 @@ namespace bd {
 //   mode 0: src[r0 + i][c0 + k]
 //   mode 1: src[r0 + k][c0 + i]              (transpose)
 //   mode 2: src[r0 + max(i,k)][c0 + min(i,k)] (symmetric matrix from its lower triangle)
+//   mode 3: as mode 2, reading only lower entries (coalesced) and writing both halves
 struct CopyTask {
   long long src_off, dst_off;
   int src_ld, dst_ld, r0, c0, rows, cols, mode, pad;
   double sign;
+};
+
+// C = A B for n x n blocks (A, B with leading dimension n; C with ldc).
+struct GemmTask {
+  long long a_off, b_off, c_off;
+  int n, ldc;
 };
 
 // One dual class (deluxe scaling, Section 4.2).

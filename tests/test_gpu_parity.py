@@ -118,17 +118,17 @@ def _oracle_steps(prob, nsteps, method="bddc"):
     return out
 
 
-@pytest.mark.parametrize("name,method,precision,tol", [
-    ("cube8", "bddc", "fp64", 1e-9),
-    ("cube8ve", "fetidp", "fp64", 1e-9),
-    ("cube8ve", "bddc", "mixed", 1e-8),
-    ("ragged", "bddc", "mixed", 1e-8),
+@pytest.mark.parametrize("name,method,precision,tol,graphs", [
+    ("cube8", "bddc", "fp64", 1e-9, 0),
+    ("cube8ve", "fetidp", "fp64", 1e-9, 1),
+    ("cube8ve", "bddc", "mixed", 1e-8, 1),
+    ("ragged", "bddc", "mixed", 1e-8, 0),
 ])
-def test_time_steps_match_oracle(name, method, precision, tol):
+def test_time_steps_match_oracle(name, method, precision, tol, graphs):
     prob = oracle_problem(name)
     ref = _oracle_steps(prob, 3, method)
     s = _solver(name, method=method, precision=precision, ksp_rtol=1e-12, ksp_atol=0.0, snes_rtol=1e-10,
-                snes_atol=1e-16)
+                snes_atol=1e-16, use_graphs=graphs)
     ui, ue, w = synth.initial_state(prob.N, 0)
     s.set_state(ui, ue, w, 0.0)
     for n in range(3):
