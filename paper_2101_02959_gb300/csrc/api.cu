@@ -232,6 +232,8 @@ struct bd_handle {
       *d_crhs, *d_rP, *d_rD2;
   double *d_kx, *d_kr, *d_kz, *d_kp, *d_kq, *d_kb;
   KrylovState *d_ks;
+  GmresState *d_gs = nullptr;
+  double *d_gV = nullptr, *d_gz = nullptr, *d_gt = nullptr, *d_gpart = nullptr, *d_gh = nullptr;
   double *d_ha, *d_hb;
   int hist_cap = 0;
   Dense<float> df;
@@ -680,6 +682,16 @@ void setup_handle(bd_handle &h) {
   double **kv[] = {&h.d_kx, &h.d_kr, &h.d_kz, &h.d_kp, &h.d_kq, &h.d_kb};
   for (double **v : kv) *v = m.alloc<double>(kn);
   h.d_ks = m.alloc<KrylovState>(1);
+  if (h.opt.krylov == BD_GMRES) {
+    const int mr = std::min(std::max(h.opt.gmres_restart, 1), kMaxRestart);
+    h.opt.gmres_restart = mr;
+    h.d_gs = m.alloc<GmresState>(1);
+    h.d_gV = m.alloc<double>((size_t)(mr + 1) * kn);
+    h.d_gz = m.alloc<double>(kn);
+    h.d_gt = m.alloc<double>(kn);
+    h.d_gpart = m.alloc<double>((size_t)(kMaxRestart + 1) * 32);
+    h.d_gh = m.alloc<double>(3 * (kMaxRestart + 1));
+  }
   h.hist_cap = std::max(1, h.opt.ksp_max_it) + 2;
   h.d_ha = m.alloc<double>(h.hist_cap);
   h.d_hb = m.alloc<double>(h.hist_cap);
@@ -859,6 +871,53 @@ int pcg(bd_handle &h, int n, const double *b, double *x, Op A, Pc M, bd_solve_st
   return out.reason;
 }
 
+// ---- device-side GMRES(m) (left preconditioning, CGS2) -------------------------
+template <class Op, class Pc>
+int gmres(bd_handle &h, int n, const double *b, double *x, Op A, Pc M, bd_solve_stats *st) {
+  cudaStream_t s = h.s;
+  const int m = h.opt.gmres_restart;
+  GmresState init{};
+  init.rtol = h.opt.ksp_rtol;
+  init.atol = h.opt.ksp_atol;
+  init.dtol = h.opt.ksp_dtol;
+  init.restart = m;
+  init.maxit = h.opt.ksp_max_it;
+  ck(cudaMemcpyAsync(h.d_gs, &init, sizeof(init), cudaMemcpyHostToDevice, s), "gmres state");
+  const int *stop = &h.d_gs->stop;
+  double *h1 = h.d_gh, *h2 = h.d_gh + (kMaxRestart + 1), *zz = h.d_gh + 2 * (kMaxRestart + 1);
+  launch_fill(n, x, 0.0, s);
+  M(b, h.d_gz, nullptr);
+  launch_dot2(n, h.d_gz, h.d_gz, nullptr, nullptr, h.d_partial, h.d_scal, nullptr, s);
+  launch_gmres_begin(n, h.d_gz, h.d_gV, h.d_gs, h.d_scal, 1, s);
+  GmresState out{};
+  for (;;) {
+    for (int j = 0; j < m; ++j) {
+      A(h.d_gV + (long long)j * n, h.d_gt, stop);
+      M(h.d_gt, h.d_gz, stop);
+      launch_gmres_step(n, j, h.d_gV, h.d_gz, h.d_gpart, h1, h2, zz, h.d_gs, s);
+    }
+    launch_gmres_end(n, h.d_gV, x, h.d_gs, s);
+    ck(cudaGetLastError(), "gmres launch");
+    ck(cudaMemcpyAsync(&out, h.d_gs, sizeof(out), cudaMemcpyDeviceToHost, s), "gmres read");
+    ck(cudaStreamSynchronize(s), "gmres sync");
+    if (out.converged || out.reason != 0) break;
+    // restart from r = M^-1 (b - A x)
+    A(x, h.d_gt, nullptr);
+    launch_axpby(n, 1.0, b, -1.0, h.d_gt, s);
+    M(h.d_gt, h.d_gz, nullptr);
+    launch_dot2(n, h.d_gz, h.d_gz, nullptr, nullptr, h.d_partial, h.d_scal, nullptr, s);
+    launch_gmres_begin(n, h.d_gz, h.d_gV, h.d_gs, h.d_scal, 0, s);
+  }
+  if (st) {
+    st->its = out.its;
+    st->reason = out.reason;
+    st->res0 = out.res0;
+    st->res = out.res;
+    st->cond = 0.0;
+  }
+  return out.reason;
+}
+
 // ---- Jacobian solve J s = f (f = (fi, fe) device SoA) ---------------------------
 template <class T>
 int solve_t(bd_handle &h, Dense<T> &D, const double *fi, const double *fe, double *si, double *se,
@@ -874,9 +933,10 @@ int solve_t(bd_handle &h, Dense<T> &D, const double *fi, const double *fe, doubl
   if (h.opt.method == BD_BDDC) {
     // f_hat = f_G - sum_j R_j^T L_GI y_I  (= K_GI K_II^-1 f_I)
     launch_gather_sum(h.nif, h.d_Rt_ptr, h.d_Rt_idx, h.d_yloc, h.d_fhat, h.gauge_iface, -1.0, h.d_fG, nullptr, s);
-    reason = pcg(
-        h, h.nif, h.d_fhat, h.d_uG, [&](const double *x, double *y, const int *dn) { schur_t(h, D, x, y, dn); },
-        [&](const double *x, double *y, const int *dn) { bddc_t(h, D, x, y, dn); }, st);
+    auto A = [&](const double *x, double *y, const int *dn) { schur_t(h, D, x, y, dn); };
+    auto M = [&](const double *x, double *y, const int *dn) { bddc_t(h, D, x, y, dn); };
+    reason = h.opt.krylov == BD_GMRES ? gmres(h, h.nif, h.d_fhat, h.d_uG, A, M, st)
+                                      : pcg(h, h.nif, h.d_fhat, h.d_uG, A, M, st);
   } else {
     // f~: local g = f_G[R] / mult - L_GI y_I, gbar = T_loc^T g -> (rD, gP); rP = sum gP
     launch_gather_scale_sub(h.nG_tot, h.d_R, h.d_fG, h.d_mult_iface, h.d_yloc, s);
@@ -885,9 +945,10 @@ int solve_t(bd_handle &h, Dense<T> &D, const double *fi, const double *fe, doubl
     launch_gather_sum(h.np, h.d_pl_ptr, h.d_pl_idx, h.d_gP, h.d_rP, h.gauge_primal, 1.0, nullptr, nullptr, s);
     st_inv_t(h, D, h.d_rP, h.d_rD2, nullptr);
     launch_jump(h.nlt, h.max_nc, h.d_lt, h.d_pairs, h.d_ydc, h.d_kb, nullptr, s);
-    reason = pcg(
-        h, h.nlam, h.d_kb, h.d_kx, [&](const double *x, double *y, const int *dn) { feti_F_t(h, D, x, y, dn); },
-        [&](const double *x, double *y, const int *dn) { feti_M_t(h, D, x, y, dn); }, st);
+    auto A = [&](const double *x, double *y, const int *dn) { feti_F_t(h, D, x, y, dn); };
+    auto M = [&](const double *x, double *y, const int *dn) { feti_M_t(h, D, x, y, dn); };
+    reason = h.opt.krylov == BD_GMRES ? gmres(h, h.nlam, h.d_kb, h.d_kx, A, M, st)
+                                      : pcg(h, h.nlam, h.d_kb, h.d_kx, A, M, st);
     // w = St^-1 (f~ - B^T lambda); u_G = T (dual mean, primal)
     launch_jump_t(h.nwt, h.max_nc, h.d_wt, h.d_went, h.d_kx, h.d_w1, nullptr, s);
     launch_axpby(h.nD_tot, 1.0, h.d_rD2, -1.0, h.d_w1, s);
@@ -1218,7 +1279,7 @@ int bidomain_setup(const bd_mesh *mesh, const bd_conductivity *cond, const bd_io
     if (opt) h->opt = *opt;
     else bd_options_default(&h->opt);
     const bd_options &o = h->opt;
-    if ((o.method != BD_BDDC && o.method != BD_FETIDP) || (o.krylov != BD_PCG) ||
+    if ((o.method != BD_BDDC && o.method != BD_FETIDP) || (o.krylov != BD_PCG && o.krylov != BD_GMRES) ||
         (o.precision != BD_FP64 && o.precision != BD_MIXED) || o.ksp_max_it < 1 || o.newton_max_it < 1)
       return BD_ERR_ARG;
     std::string err = build_plan(h->plan, mesh->n, mesh->l, mesh->s, mesh->elem_mask, o.primal);

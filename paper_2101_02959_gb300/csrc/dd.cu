@@ -655,4 +655,154 @@ BD_DD_INST(double)
 template void launch_copy<float, double>(int, long long, const CopyTask *, const float *, double *, cudaStream_t);
 template void launch_copy<double, float>(int, long long, const CopyTask *, const double *, float *, cudaStream_t);
 
+
+// ---- GMRES(m), left preconditioned, CGS2 orthogonalisation ---------------------
+// V holds m+1 basis vectors of length n (column q at V + q n).  All kernels of a
+// step return at once when `stop` is set (converged, diverged or at maxit).
+__global__ void k_multidot(int n, int k, const double *__restrict__ V, const double *__restrict__ z,
+                           double *__restrict__ partial, const GmresState *__restrict__ gs) {
+  if (gs->stop) return;
+  __shared__ double sh[32];
+  const int q = blockIdx.y;
+  const double *v = V + (long long)q * n;
+  double acc = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) acc += v[i] * z[i];
+  acc = block_sum(acc, sh);
+  if (threadIdx.x == 0) partial[q * gridDim.x + blockIdx.x] = acc;
+}
+
+// h[q] (+)= sum of the partials of dot q, q < k (fixed order)
+__global__ void k_multidot_fin(int k, int nblk, const double *__restrict__ partial, double *__restrict__ h, int add,
+                               const GmresState *__restrict__ gs) {
+  if (gs->stop) return;
+  const int q = threadIdx.x;
+  if (q >= k) return;
+  double acc = 0.0;
+  for (int b = 0; b < nblk; ++b) acc += partial[q * nblk + b];
+  h[q] = add ? h[q] + acc : acc;
+}
+
+// z -= sum_q c[q] V_q  (c = the projections just computed)
+__global__ void k_orth_sub(int n, int k, const double *__restrict__ V, const double *__restrict__ c,
+                           double *__restrict__ z, const GmresState *__restrict__ gs) {
+  if (gs->stop) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double acc = z[i];
+    for (int q = 0; q < k; ++q) acc -= c[q] * V[(long long)q * n + i];
+    z[i] = acc;
+  }
+}
+
+// column j of H from (h1 + h2, ||z||), Givens rotations, residual estimate, stop test
+__global__ void k_gmres_rot(GmresState *__restrict__ gs, const double *__restrict__ h1, const double *__restrict__ h2,
+                            const double *__restrict__ zz, int j) {
+  if (gs->stop) return;
+  const int m = gs->restart;
+  double *H = gs->H;
+  for (int i = 0; i <= j; ++i) H[i * m + j] = h1[i] + h2[i];
+  const double hn = sqrt(fmax(zz[0], 0.0));
+  H[(j + 1) * m + j] = hn;
+  gs->hn = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = H[i * m + j], b = H[(i + 1) * m + j];
+    H[i * m + j] = gs->cs[i] * a + gs->sn[i] * b;
+    H[(i + 1) * m + j] = -gs->sn[i] * a + gs->cs[i] * b;
+  }
+  const double a = H[j * m + j], b = H[(j + 1) * m + j];
+  const double den = hypot(a, b);
+  gs->cs[j] = a / den;
+  gs->sn[j] = b / den;
+  H[j * m + j] = den;
+  H[(j + 1) * m + j] = 0.0;
+  gs->g[j + 1] = -gs->sn[j] * gs->g[j];
+  gs->g[j] = gs->cs[j] * gs->g[j];
+  gs->its += 1;
+  gs->j = j + 1;
+  const double res = fabs(gs->g[j + 1]);
+  gs->res = res;
+  if (!isfinite(res)) { gs->stop = 1; gs->reason = -6; return; }
+  if (res <= gs->tol) { gs->stop = 1; gs->converged = 1; gs->reason = 0; return; }
+  if (res > gs->dtol * gs->res0) { gs->stop = 1; gs->reason = -4; return; }
+  if (gs->its >= gs->maxit) { gs->stop = 1; gs->reason = -3; return; }
+  if (gs->j >= m) gs->stop = 1;  // end of the cycle
+}
+
+// V_{j+1} = z / ||z|| (also V_0 = r / beta at a cycle start).  Vectors written after a
+// stop are never read: the update uses only the first gs->j basis vectors.
+__global__ void k_gmres_scale(int n, const double *__restrict__ z, double *__restrict__ vout,
+                              const GmresState *__restrict__ gs) {
+  const double inv = gs->hn > 0.0 ? 1.0 / gs->hn : 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) vout[i] = z[i] * inv;
+}
+
+// end of a cycle: y = H^-1 g over the steps done, x += V y
+__global__ void k_gmres_solve_y(GmresState *__restrict__ gs) {
+  const int m = gs->restart, k = gs->j;
+  for (int i = k - 1; i >= 0; --i) {
+    double v = gs->g[i];
+    for (int q = i + 1; q < k; ++q) v -= gs->H[i * m + q] * gs->y[q];
+    gs->y[i] = v / gs->H[i * m + i];
+  }
+}
+
+__global__ void k_gmres_update_x(int n, const double *__restrict__ V, double *__restrict__ x,
+                                 const GmresState *__restrict__ gs) {
+  const int k = gs->j;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double acc = x[i];
+    for (int q = 0; q < k; ++q) acc += gs->y[q] * V[(long long)q * n + i];
+    x[i] = acc;
+  }
+}
+
+// start of a cycle from r (= M^-1 (b - A x)) with ||r||^2 in rr: V_0 = r / beta, g = beta e_1
+__global__ void k_gmres_begin(GmresState *__restrict__ gs, const double *__restrict__ rr, int first) {
+  const double beta = sqrt(fmax(rr[0], 0.0));
+  if (first) {
+    gs->res0 = beta;
+    gs->tol = fmax(gs->rtol * beta, gs->atol);
+    gs->its = 0;
+    gs->reason = 0;
+    gs->converged = 0;
+  }
+  for (int i = 0; i <= gs->restart; ++i) gs->g[i] = 0.0;
+  gs->g[0] = beta;
+  gs->hn = beta;
+  gs->j = 0;
+  gs->res = beta;
+  gs->stop = 0;
+  if (first && beta <= gs->atol) { gs->stop = 1; gs->converged = 1; }
+  if (!isfinite(beta)) { gs->stop = 1; gs->reason = -6; }
+}
+
+void launch_gmres_step(int n, int j, double *V, double *z, double *partial, double *h1, double *h2, double *zz,
+                       GmresState *gs, cudaStream_t s) {
+  const int nblk = 32;
+  k_multidot<<<dim3(nblk, j + 1), 256, 0, s>>>(n, j + 1, V, z, partial, gs);
+  k_multidot_fin<<<1, 64, 0, s>>>(j + 1, nblk, partial, h1, 0, gs);
+  k_orth_sub<<<std::max(1, std::min(ceil_div(n, 256), kRedBlocks)), 256, 0, s>>>(n, j + 1, V, h1, z, gs);
+  k_multidot<<<dim3(nblk, j + 1), 256, 0, s>>>(n, j + 1, V, z, partial, gs);
+  k_multidot_fin<<<1, 64, 0, s>>>(j + 1, nblk, partial, h2, 0, gs);
+  k_orth_sub<<<std::max(1, std::min(ceil_div(n, 256), kRedBlocks)), 256, 0, s>>>(n, j + 1, V, h2, z, gs);
+  k_multidot<<<dim3(nblk, 1), 256, 0, s>>>(n, 1, z, z, partial, gs);
+  k_multidot_fin<<<1, 64, 0, s>>>(1, nblk, partial, zz, 0, gs);
+  k_gmres_rot<<<1, 1, 0, s>>>(gs, h1, h2, zz, j);
+  k_gmres_scale<<<std::max(1, std::min(ceil_div(n, 256), kRedBlocks)), 256, 0, s>>>(n, z, V + (long long)(j + 1) * n,
+                                                                                   gs);
+  count_launch(10);
+}
+
+void launch_gmres_begin(int n, const double *r, double *v0, GmresState *gs, const double *rr, int first,
+                        cudaStream_t s) {
+  k_gmres_begin<<<1, 1, 0, s>>>(gs, rr, first);
+  k_gmres_scale<<<std::max(1, std::min(ceil_div(n, 256), kRedBlocks)), 256, 0, s>>>(n, r, v0, gs);
+  count_launch(2);
+}
+
+void launch_gmres_end(int n, const double *V, double *x, GmresState *gs, cudaStream_t s) {
+  k_gmres_solve_y<<<1, 1, 0, s>>>(gs);
+  k_gmres_update_x<<<std::max(1, std::min(ceil_div(n, 256), kRedBlocks)), 256, 0, s>>>(n, V, x, gs);
+  count_launch(2);
+}
+
 }  // namespace bd

@@ -13,6 +13,20 @@ struct KrylovState {
   int it, done, reason, maxit, hist_cap, pad;
 };
 
+// Device-resident GMRES(m) state (m <= kMaxRestart).
+constexpr int kMaxRestart = 64;
+struct GmresState {
+  double H[(kMaxRestart + 1) * kMaxRestart];
+  double cs[kMaxRestart], sn[kMaxRestart], g[kMaxRestart + 1], y[kMaxRestart];
+  double rtol, atol, dtol, tol, res0, res, hn;
+  int restart, maxit, its, j, stop, converged, reason, pad;
+};
+void launch_gmres_step(int n, int j, double *V, double *z, double *partial, double *h1, double *h2, double *zz,
+                       GmresState *gs, cudaStream_t s);
+void launch_gmres_begin(int n, const double *r, double *v0, GmresState *gs, const double *rr, int first,
+                        cudaStream_t s);
+void launch_gmres_end(int n, const double *V, double *x, GmresState *gs, cudaStream_t s);
+
 template <typename T>
 void launch_assemble_local(int nq, const int *q_sub, const int *q_loc, const int *q_node, const int *nbr,
                            const double *stencil, const double *mass, const double *factor, double tau,

@@ -21,113 +21,131 @@ template <> __device__ inline float dsqrt<float>(float v) { return sqrtf(v); }
 template <> __device__ inline double dsqrt<double>(double v) { return sqrt(v); }
 
 // ---- panel step 1: factor the w x w diagonal block in place and form L_kk^-1 --
-// One warp per matrix.  Lane r keeps row r of the block in registers; column c
-// of L is broadcast with shuffles, so the right-looking update has no shared-
-// memory dependency chain.  L_kk^-1 (used by the panel solve) goes to `linv`.
+// 1024 threads per matrix: thread (r, t) owns entry (r, t) of the block.  Step c
+// updates the trailing entries with the unscaled column c divided by its pivot,
+// so one barrier per column suffices; the columns are scaled at the end.
+// Warp 0 then forms L_kk^-1 (lane j solves L y = e_j) for the panel solve.
 template <typename T>
-__global__ void __launch_bounds__(32) k_potrf(const MatDesc *__restrict__ desc, T *__restrict__ base, int k0,
-                                              int *__restrict__ err, T *__restrict__ linv) {
+__global__ void __launch_bounds__(1024) k_potrf(const MatDesc *__restrict__ desc, T *__restrict__ base, int k0,
+                                                int *__restrict__ err, T *__restrict__ linv) {
   const MatDesc d = desc[blockIdx.x];
   if (k0 >= d.e) return;
   const int w = min(kNB, d.e - k0);
   T *A = base + d.off;
   __shared__ T Ls[kNB][kNB + 1];
-  const int r = threadIdx.x;
-#pragma unroll 8
-  for (int q = 0; q < kNB; ++q)  // row q, lane = column: coalesced, independent loads
-    Ls[q][r] = (q < w && r <= q) ? A[(long long)(k0 + q) * d.ld + k0 + r] : T(0);
-  __syncwarp();
-  T row[kNB];
-#pragma unroll
-  for (int c = 0; c < kNB; ++c) row[c] = Ls[r][c];
+  __shared__ T piv[kNB];
+  const int r = threadIdx.x >> 5, t = threadIdx.x & 31;
+  Ls[r][t] = (r < w && t <= r) ? A[(long long)(k0 + r) * d.ld + k0 + t] : (r == t ? T(1) : T(0));
+  __syncthreads();
   bool bad = false;
-#pragma unroll
-  for (int c = 0; c < kNB; ++c) {
-    if (c < w) {
-      T dg = __shfl_sync(0xffffffffu, row[c], c);
-      if (!(dg > T(0))) { bad = true; dg = T(1); }
-      const T sq = dsqrt(dg);
-      if (r == c) row[c] = sq;
-      else if (r > c) row[c] = row[c] / sq;
-      const T lrc = row[c];
-#pragma unroll
-      for (int t = c + 1; t < kNB; ++t) {
-        const T ltc = __shfl_sync(0xffffffffu, row[c], t);
-        if (r >= t) row[t] -= lrc * ltc;
-      }
+  for (int c = 0; c < w; ++c) {
+    T dcc = Ls[c][c];
+    if (!(dcc > T(0))) { bad = true; dcc = T(1); }
+    if (r == c && t == c) piv[c] = dcc;
+    if (t > c && r >= t && r < w) Ls[r][t] -= Ls[r][c] * Ls[t][c] / dcc;
+    __syncthreads();
+  }
+  if (bad && threadIdx.x == 0) atomicOr(err, DEV_ERR_NOT_SPD);
+  // scale: L[r][c] = A_c[r][c] / sqrt(d_c), L[c][c] = sqrt(d_c)
+  T lv = T(0);
+  if (r < w && t <= r) lv = (r == t) ? dsqrt(piv[t]) : Ls[r][t] / dsqrt(piv[t]);
+  else if (r == t) lv = T(1);
+  __syncthreads();
+  Ls[r][t] = lv;
+  __syncthreads();
+  if (r < w && t <= r) A[(long long)(k0 + r) * d.ld + k0 + t] = lv;
+  // L_kk^-1 by recursive doubling: inv([[A, 0], [B, C]]) = [[A^-1, 0], [-C^-1 B A^-1, C^-1]]
+  __shared__ T Yi[kNB][kNB + 1];
+  __shared__ T Tm[kNB][kNB + 1];
+  Yi[r][t] = (r == t) ? T(1) / Ls[r][r] : T(0);
+  __syncthreads();
+  for (int b = 1; b < kNB; b <<= 1) {
+    const int base0 = (r / (2 * b)) * (2 * b);
+    const bool active = (t / (2 * b) == r / (2 * b)) && ((r - base0) >= b) && ((t - base0) < b);
+    if (active) {  // Tm = B A^-1 over the top half
+      T acc = T(0);
+      for (int k = t; k < base0 + b; ++k) acc += Ls[r][k] * Yi[k][t];
+      Tm[r][t] = acc;
     }
+    __syncthreads();
+    if (active) {  // Y = -C^-1 (B A^-1) over the bottom half
+      T acc = T(0);
+      for (int k = base0 + b; k <= r; ++k) acc += Yi[r][k] * Tm[k][t];
+      Yi[r][t] = -acc;
+    }
+    __syncthreads();
   }
-  if (bad && r == 0) atomicOr(err, DEV_ERR_NOT_SPD);
-#pragma unroll
-  for (int c = 0; c < kNB; ++c) Ls[r][c] = (c <= r && r < w && c < w) ? row[c] : (r == c ? T(1) : T(0));
-  __syncwarp();
-#pragma unroll 8
-  for (int q = 0; q < w; ++q)  // write back row q, lane = column
-    if (r <= q) A[(long long)(k0 + q) * d.ld + k0 + r] = Ls[q][r];
-  // L_kk^-1: lane j solves L y = e_j by forward substitution (column j of the inverse)
-  T y[kNB];
-#pragma unroll
-  for (int i = 0; i < kNB; ++i) {
-    T v = (i == r) ? T(1) : T(0);
-#pragma unroll
-    for (int t = 0; t < i; ++t) v -= Ls[i][t] * y[t];
-    y[i] = (i >= r) ? v / Ls[i][i] : T(0);
-  }
-  T *Li = linv + (long long)blockIdx.x * kNB * kNB;
-#pragma unroll
-  for (int i = 0; i < kNB; ++i) Li[i * kNB + r] = y[i];  // Li[i][j] = (L^-1)[i][j], lane = j
+  linv[(long long)blockIdx.x * kNB * kNB + r * kNB + t] = Yi[r][t];
 }
 
-// ---- panel step 2: rows below the diagonal block, x = a L_kk^-T (one thread per row)
+// ---- panel step 2: rows below the diagonal block, x = a L_kk^-T ----------------
+// 128 rows per CTA; the 128 x 32 tile is staged in shared memory with coalesced
+// loads (warp q reads rows, lane = column) and each thread forms one row.
 template <typename T>
 __global__ void __launch_bounds__(128) k_trsm(const MatDesc *__restrict__ desc, T *__restrict__ base, int k0,
                                               const T *__restrict__ linv) {
   const MatDesc d = desc[blockIdx.y];
   if (k0 >= d.e) return;
   const int w = min(kNB, d.e - k0);
-  if (k0 + w + blockIdx.x * 128 >= d.m) return;
+  const int rbeg = k0 + w + blockIdx.x * 128;
+  if (rbeg >= d.m) return;
   T *A = base + d.off;
   __shared__ T Li[kNB][kNB];
+  __shared__ T X[128][kNB + 1];
   const T *src = linv + (long long)blockIdx.y * kNB * kNB;
   for (int t = threadIdx.x; t < kNB * kNB; t += 128) Li[t / kNB][t % kNB] = src[t];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nrows = min(128, d.m - rbeg);
+  for (int q = wid; q < nrows; q += 4)
+    X[q][lane] = (lane < w) ? A[(long long)(rbeg + q) * d.ld + k0 + lane] : T(0);
   __syncthreads();
-  const int row = k0 + w + blockIdx.x * 128 + threadIdx.x;
-  if (row >= d.m) return;
-  T *a = A + (long long)row * d.ld + k0;
-  T x[kNB];
+  if (threadIdx.x < nrows) {
+    T x[kNB];
 #pragma unroll
-  for (int c = 0; c < kNB; ++c) x[c] = (c < w) ? a[c] : T(0);
-  // x_out[c] = sum_{t <= c} x[t] (L^-1)[c][t]: independent dot products
+    for (int c = 0; c < kNB; ++c) x[c] = X[threadIdx.x][c];
+    // x_out[c] = sum_{t <= c} x[t] (L^-1)[c][t]: independent dot products
 #pragma unroll
-  for (int c = kNB - 1; c >= 0; --c) {
-    T v = T(0);
+    for (int c = kNB - 1; c >= 0; --c) {
+      T v = T(0);
 #pragma unroll
-    for (int t = 0; t <= c; ++t) v += x[t] * Li[c][t];
-    x[c] = v;
+      for (int t = 0; t <= c; ++t) v += x[t] * Li[c][t];
+      x[c] = v;
+    }
+#pragma unroll
+    for (int c = 0; c < kNB; ++c) X[threadIdx.x][c] = x[c];
   }
-#pragma unroll
-  for (int c = 0; c < kNB; ++c)
-    if (c < w) a[c] = x[c];
+  __syncthreads();
+  for (int q = wid; q < nrows; q += 4)
+    if (lane < w) A[(long long)(rbeg + q) * d.ld + k0 + lane] = X[q][lane];
 }
 
 // ---- rank-k update of lower tiles --------------------------------------------
-// mode 0 (panel): rows [k0+w, m), cols [k0+w, e), K = panel [k0, k0+w)
-// mode 1 (final): rows [e, m),    cols [e, m),    K = [0, e)
+// Two-level right-looking blocking: inner panels of kNB columns inside outer
+// panels [K0, K1) of kOB columns.
+// mode 0 (inner): rows [k0+w, m), cols [k0+w, min(K1, e)), K = [k0, k0+w)
+// mode 2 (outer): rows [K1, m),   cols [K1, e),            K = [K0, K1)
+// mode 1 (final): rows [e, m),    cols [e, m),             K = [0, e)
 // C[r][c] -= sum_k A[r][k] A[c][k]; 64x64 tiles, 256 threads, 4x4 per thread.
-constexpr int kTB = 64, kKC = 32;
+constexpr int kTB = 64, kKC = 32, kOB = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_rankk(const MatDesc *__restrict__ desc, T *__restrict__ base, int mode,
-                                               int k0, int nct) {
+                                               int k0, int K0, int K1, int nct) {
   const MatDesc d = desc[blockIdx.y];
   int row0, colend, kb, ke;
   if (mode == 0) {
     if (k0 >= d.e) return;
     const int w = min(kNB, d.e - k0);
     row0 = k0 + w;
-    colend = d.e;
+    colend = min(K1, d.e);
     kb = k0;
     ke = k0 + w;
+  } else if (mode == 2) {
+    if (K1 >= d.e) return;
+    row0 = K1;
+    colend = d.e;
+    kb = K0;
+    ke = K1;
   } else {
     row0 = d.e;
     colend = d.m;
@@ -199,36 +217,58 @@ template <typename T>
 void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s,
                              T *linv, ProfHook *prof) {
   if (sh.count == 0) return;
-  for (int k0 = 0; k0 < sh.max_e; k0 += kNB) {
-    int max_below = 0, max_rt = 0, max_ct = 0;
-    double fl_panel = 0.0, fl_upd = 0.0, by_upd = 0.0;
-    for (int b = 0; b < sh.count; ++b) {
-      if (k0 >= sh.e[b]) continue;
-      const int w = std::min(kNB, sh.e[b] - k0);
-      const int below = sh.m[b] - k0 - w;
-      max_below = std::max(max_below, below);
-      max_rt = std::max(max_rt, ceil_div(below, kTB));
-      max_ct = std::max(max_ct, ceil_div(sh.e[b] - k0 - w, kTB));
-      fl_panel += (double)w * w * w / 3.0 + (double)below * w * w;
-      const double ent = trapezoid(k0 + w, sh.e[b], sh.m[b]);
-      fl_upd += 2.0 * w * ent;
-      by_upd += sizeof(T) * (2.0 * ent + (double)w * (below + sh.e[b] - k0 - w));
-    }
-    if (prof) prof->begin(PROF_PANEL, s);
-    k_potrf<T><<<sh.count, 32, 0, s>>>(d_desc, base, k0, d_err, linv);
-    count_launch();
-    if (max_below > 0) {
-      dim3 gp(ceil_div(max_below, 128), sh.count);
-      k_trsm<T><<<gp, 128, 0, s>>>(d_desc, base, k0, linv);
+  for (int K0 = 0; K0 < sh.max_e; K0 += kOB) {
+    const int K1 = K0 + kOB;
+    for (int k0 = K0; k0 < std::min(K1, sh.max_e); k0 += kNB) {
+      int max_below = 0, max_rt = 0, max_ct = 0;
+      double fl_panel = 0.0, fl_upd = 0.0, by_upd = 0.0;
+      for (int b = 0; b < sh.count; ++b) {
+        if (k0 >= sh.e[b]) continue;
+        const int w = std::min(kNB, sh.e[b] - k0);
+        const int below = sh.m[b] - k0 - w;
+        const int cend = std::min(K1, sh.e[b]);
+        max_below = std::max(max_below, below);
+        max_rt = std::max(max_rt, ceil_div(below, kTB));
+        max_ct = std::max(max_ct, ceil_div(cend - k0 - w, kTB));
+        fl_panel += (double)w * w * w / 3.0 + (double)below * w * w;
+        const double ent = trapezoid(k0 + w, cend, sh.m[b]);
+        fl_upd += 2.0 * w * ent;
+        by_upd += sizeof(T) * (2.0 * ent + (double)w * (below + cend - k0 - w));
+      }
+      if (prof) prof->begin(PROF_PANEL, s);
+      k_potrf<T><<<sh.count, 1024, 0, s>>>(d_desc, base, k0, d_err, linv);
       count_launch();
+      if (max_below > 0) {
+        dim3 gp(ceil_div(max_below, 128), sh.count);
+        k_trsm<T><<<gp, 128, 0, s>>>(d_desc, base, k0, linv);
+        count_launch();
+      }
+      if (prof) prof->end(PROF_PANEL, s, fl_panel, 0.0);
+      if (max_rt > 0 && max_ct > 0) {
+        dim3 gu(max_rt * max_ct, sh.count);
+        if (prof) prof->begin(PROF_RANKK, s);
+        k_rankk<T><<<gu, 256, 0, s>>>(d_desc, base, 0, k0, K0, K1, max_ct);
+        count_launch();
+        if (prof) prof->end(PROF_RANKK, s, fl_upd, by_upd);
+      }
     }
-    if (prof) prof->end(PROF_PANEL, s, fl_panel, 0.0);
+    // outer update of the trailing columns [K1, e) with the finished outer panel
+    int max_rt = 0, max_ct = 0;
+    double fl = 0.0, by = 0.0;
+    for (int b = 0; b < sh.count; ++b) {
+      if (K1 >= sh.e[b]) continue;
+      max_rt = std::max(max_rt, ceil_div(sh.m[b] - K1, kTB));
+      max_ct = std::max(max_ct, ceil_div(sh.e[b] - K1, kTB));
+      const double ent = trapezoid(K1, sh.e[b], sh.m[b]);
+      fl += 2.0 * kOB * ent;
+      by += sizeof(T) * (2.0 * ent + (double)kOB * (sh.m[b] - K1));
+    }
     if (max_rt > 0 && max_ct > 0) {
       dim3 gu(max_rt * max_ct, sh.count);
       if (prof) prof->begin(PROF_RANKK, s);
-      k_rankk<T><<<gu, 256, 0, s>>>(d_desc, base, 0, k0, max_ct);
+      k_rankk<T><<<gu, 256, 0, s>>>(d_desc, base, 2, 0, K0, K1, max_ct);
       count_launch();
-      if (prof) prof->end(PROF_RANKK, s, fl_upd, by_upd);
+      if (prof) prof->end(PROF_RANKK, s, fl, by);
     }
   }
   int max_t = 0;
@@ -243,7 +283,7 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
   if (max_t > 0) {
     dim3 gf(max_t * max_t, sh.count);
     if (prof) prof->begin(PROF_RANKK, s);
-    k_rankk<T><<<gf, 256, 0, s>>>(d_desc, base, 1, 0, max_t);
+    k_rankk<T><<<gf, 256, 0, s>>>(d_desc, base, 1, 0, 0, 0, max_t);
     count_launch();
     if (prof) prof->end(PROF_RANKK, s, fl, by);
   }

@@ -77,9 +77,10 @@ def test_operators_match_oracle(name):
     assert _rel(s.fetidp_apply(lam), Minv(lam)) < 1e-9
 
 
-@pytest.mark.parametrize("name", ["tiny", "cube8", "cube8ve", "ragged"])
+@pytest.mark.parametrize("name,krylov", [("tiny", "pcg"), ("cube8", "pcg"), ("cube8ve", "pcg"), ("ragged", "pcg"),
+                                         ("cube8ve", "gmres"), ("ragged", "gmres")])
 @pytest.mark.parametrize("method", ["bddc", "fetidp"])
-def test_jacobian_solve_fp64(name, method):
+def test_jacobian_solve_fp64(name, method, krylov):
     prob = oracle_problem(name)
     ui, ue, w = _state(prob)
     wn = ionic.gating_step(ui - ue, w, prob.tau, prob.p)
@@ -88,7 +89,7 @@ def test_jacobian_solve_fp64(name, method):
     si, se, _ = direct_solve(prob, kc, -r_i, -r_e)
     f = -np.concatenate([r_i, r_e])
     # tight tolerance: the exact solution to 1e-10
-    s = _solver(name, method=method, precision="fp64", ksp_rtol=1e-13, ksp_atol=0.0)
+    s = _solver(name, method=method, krylov=krylov, precision="fp64", ksp_rtol=1e-13, ksp_atol=0.0)
     s.linearize(ui, ue, wn)
     x, st = s.krylov_solve(f)
     assert st["reason"] == 0
@@ -97,20 +98,21 @@ def test_jacobian_solve_fp64(name, method):
     # vertex-only primal space the preconditioned residual norm oscillates by up to 10x
     # near the threshold, and the oracle alone gives 18 (x86) or 19 (Arm) iterations on
     # this system, so there the bar is +-2.
-    s2 = _solver(name, method=method, precision="fp64")
+    s2 = _solver(name, method=method, krylov=krylov, precision="fp64")
     s2.linearize(ui, ue, wn)
     _, st2 = s2.krylov_solve(f)
-    dd = DDSolver(prob, method=method)
+    dd = DDSolver(prob, method=method, krylov=krylov)
     _, _, info = dd.solve(kc / prob.fem.M, -r_i, -r_e)
     ve = prob.part.primal_kind == "VE"
     assert abs(st2["its"] - info["its"]) <= (1 if ve else 2)
-    # the Lanczos estimate follows the iteration count: 1e-3 (V+E), 1e-2 when it differs (V)
-    assert abs(st2["cond"] - info["cond"]) < (1e-3 if ve else 1e-2) * info["cond"]
+    if krylov == "pcg":
+        # the Lanczos estimate follows the iteration count: 1e-3 (V+E), 1e-2 when it differs (V)
+        assert abs(st2["cond"] - info["cond"]) < (1e-3 if ve else 1e-2) * info["cond"]
 
 
-def _oracle_steps(prob, nsteps, method="bddc"):
+def _oracle_steps(prob, nsteps, method="bddc", krylov="pcg"):
     ui, ue, w = synth.initial_state(prob.N, 0)
-    dd = DDSolver(prob, method=method, rtol=1e-12, atol=0.0)
+    dd = DDSolver(prob, method=method, krylov=krylov, rtol=1e-12, atol=0.0)
     out = []
     for n in range(nsteps):
         ui, ue, w, st = time_step(prob, ui, ue, w, n, dd.linsolve(), rtol=1e-10, atol=1e-16)
@@ -118,17 +120,18 @@ def _oracle_steps(prob, nsteps, method="bddc"):
     return out
 
 
-@pytest.mark.parametrize("name,method,precision,tol,graphs", [
-    ("cube8", "bddc", "fp64", 1e-9, 0),
-    ("cube8ve", "fetidp", "fp64", 1e-9, 1),
-    ("cube8ve", "bddc", "mixed", 1e-8, 1),
-    ("ragged", "bddc", "mixed", 1e-8, 0),
+@pytest.mark.parametrize("name,method,precision,tol,graphs,krylov", [
+    ("cube8", "bddc", "fp64", 1e-9, 0, "pcg"),
+    ("cube8ve", "fetidp", "fp64", 1e-9, 1, "pcg"),
+    ("cube8ve", "bddc", "mixed", 1e-8, 1, "pcg"),
+    ("ragged", "bddc", "mixed", 1e-8, 0, "pcg"),
+    ("cube8ve", "bddc", "fp64", 1e-9, 0, "gmres"),
 ])
-def test_time_steps_match_oracle(name, method, precision, tol, graphs):
+def test_time_steps_match_oracle(name, method, precision, tol, graphs, krylov):
     prob = oracle_problem(name)
-    ref = _oracle_steps(prob, 3, method)
-    s = _solver(name, method=method, precision=precision, ksp_rtol=1e-12, ksp_atol=0.0, snes_rtol=1e-10,
-                snes_atol=1e-16, use_graphs=graphs)
+    ref = _oracle_steps(prob, 3, method, krylov)
+    s = _solver(name, method=method, krylov=krylov, precision=precision, ksp_rtol=1e-12, ksp_atol=0.0,
+                snes_rtol=1e-10, snes_atol=1e-16, use_graphs=graphs)
     ui, ue, w = synth.initial_state(prob.N, 0)
     s.set_state(ui, ue, w, 0.0)
     for n in range(3):
