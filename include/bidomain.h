@@ -129,6 +129,14 @@ typedef struct {
   int use_graphs;    /* 1: replay the Krylov iteration as a captured CUDA graph */
   double ksp_rtol, ksp_atol, ksp_dtol;
   double snes_rtol, snes_atol, snes_stol;
+  /* learned initial guess (not in the paper): 1 = predict u^0 with the
+   * per-subdomain MLP once two previous states exist; it is trained online with
+   * Adam (learning rate mlp_lr) on the steps before mlp_train_steps and used
+   * from mlp_warmup training steps on, only when its residual is below the
+   * previous-step residual (the fallback); tolerances stay anchored to the
+   * fallback residual. */
+  int learned_guess, mlp_train_steps, mlp_warmup, mlp_epochs;
+  double mlp_lr;
 } bd_options;
 
 typedef struct {
@@ -147,6 +155,10 @@ typedef struct {
   double res0;      /* ||F(u^n) - G|| */
   double res_final; /* ||F(u^{n+1}) - G|| */
   double cond_max;  /* largest Lanczos estimate met in the step */
+  int guess_used;   /* 1 when Newton started from the learned guess */
+  int pad2;
+  double res_guess; /* ||F(u_guess) - G|| (0 when no guess was formed) */
+  double mlp_loss;  /* training loss of this step (0 when not training) */
 } bd_step_stats;
 
 typedef struct {
@@ -231,6 +243,22 @@ int fetidp_operator(bd_handle *h, const double *lambda, double *y, int on_device
  * system (FETI-DP), then recovers the interior (Section 4.1).  f, s: 2*n_node
  * (SoA).  The u_e correction at the gauge node is 0.  stats may be NULL. */
 int krylov_solve(bd_handle *h, const double *f, double *s, int on_device, bd_solve_stats *stats);
+
+/* ---- learned initial guess (not in the paper) ------------------------------
+ * The per-subdomain MLP maps local traces of the last three states (6 per
+ * node: v^n, v^n - v^{n-1}, v^{n-1} - v^{n-2}, u_e^n and its two differences,
+ * all / 100 mV, padded to the largest subdomain) to the increment u^{n+1} - u^n
+ * at its nodes (2 per node).  Layers: n_in -> 256 -> 256 -> n_out, ReLU,
+ * bfloat16 weights, float32 accumulation.  Parameters are packed float32:
+ * W1 (256 x n_in), b1, W2 (256 x 256), b2, W3 (n_out x 256), b3. */
+int bidomain_mlp_sizes(bd_handle *h, int *n_in, int *n_hidden, int *n_out, int *batch);
+/* set = 1: upload the packed parameters from host memory (and refresh the
+ * bfloat16 copies); set = 0: download them. */
+int bidomain_mlp_params(bd_handle *h, float *w, int set);
+/* Loss sum(mask (y - t)^2) / sum(mask) and its packed gradient for host
+ * inputs X (batch x n_in), targets T and mask (batch x n_out). */
+int bidomain_mlp_loss_grad(bd_handle *h, const float *X, const float *T, const float *mask, double *loss,
+                           float *grad);
 
 /* ---- no-allocation variant ------------------------------------------------
  * The paper has no counterpart: this is a deployment variant of schur_apply.

@@ -31,8 +31,8 @@ EXPORTED = ["bd_plan_create", "bd_plan_sizes", "bd_plan_index_sets", "bd_plan_de
             "bidomain_setup", "bidomain_sizes", "bidomain_index_sets", "bidomain_set_state",
             "bidomain_get_state", "bidomain_step", "bidomain_gating", "bidomain_residual", "bidomain_linearize",
             "schur_apply", "bddc_apply", "fetidp_apply", "fetidp_operator", "krylov_solve", "bidomain_profile",
-            "bidomain_profile_read", "bidomain_launch_count", "schur_apply_noalloc", "bidomain_destroy",
-            "bidomain_strerror"]
+            "bidomain_profile_read", "bidomain_launch_count", "schur_apply_noalloc", "bidomain_mlp_sizes",
+            "bidomain_mlp_params", "bidomain_mlp_loss_grad", "bidomain_destroy", "bidomain_strerror"]
 PROF = dict(rankk=0, panel=1, gemv=2, resid=3)
 
 
@@ -56,7 +56,9 @@ class BdOptions(C.Structure):
     _fields_ = [(k, C.c_int) for k in ("method", "krylov", "primal", "precision", "gmres_restart", "ksp_max_it",
                                        "newton_max_it", "use_graphs")] + \
                [(k, C.c_double) for k in ("ksp_rtol", "ksp_atol", "ksp_dtol", "snes_rtol", "snes_atol",
-                                          "snes_stol")]
+                                          "snes_stol")] + \
+               [(k, C.c_int) for k in ("learned_guess", "mlp_train_steps", "mlp_warmup", "mlp_epochs")] + \
+               [("mlp_lr", C.c_double)]
 
 
 class BdSolveStats(C.Structure):
@@ -66,7 +68,8 @@ class BdSolveStats(C.Structure):
 
 class BdStepStats(C.Structure):
     _fields_ = [("newton_its", C.c_int), ("krylov_its", C.c_int), ("reason", C.c_int), ("pad", C.c_int),
-                ("res0", C.c_double), ("res_final", C.c_double), ("cond_max", C.c_double)]
+                ("res0", C.c_double), ("res_final", C.c_double), ("cond_max", C.c_double),
+                ("guess_used", C.c_int), ("pad2", C.c_int), ("res_guess", C.c_double), ("mlp_loss", C.c_double)]
 
 
 class BdSizes(C.Structure):
@@ -113,6 +116,9 @@ def load(build_if_missing: bool = False):
         "bidomain_profile_read": (I, [P, I, C.POINTER(C.c_double)]),
         "bidomain_launch_count": (C.c_int64, []),
         "schur_apply_noalloc": (I, [P, P, P]),
+        "bidomain_mlp_sizes": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
+        "bidomain_mlp_params": (I, [P, P, I]),
+        "bidomain_mlp_loss_grad": (I, [P, P, P, P, C.POINTER(D), P]),
         "bidomain_destroy": (I, [P]),
         "bidomain_strerror": (C.c_char_p, [I]),
     }
@@ -274,7 +280,7 @@ class Solver:
         st = BdStepStats()
         s = _stim(stim)
         code = self._lib.bidomain_step(self._h, None if s is None else C.byref(s), C.byref(st))
-        out = {k: getattr(st, k) for k, _ in BdStepStats._fields_ if k != "pad"}
+        out = {k: getattr(st, k) for k, _ in BdStepStats._fields_ if not k.startswith("pad")}
         _check(code, "bidomain_step")
         return out
 
@@ -321,6 +327,33 @@ class Solver:
         out = (C.c_double * 4)()
         _check(self._lib.bidomain_profile_read(self._h, PROF[which], out), "bidomain_profile_read")
         return dict(launches=int(out[0]), ms=out[1], flops=out[2], bytes=out[3])
+
+    def mlp_sizes(self):
+        v = [C.c_int() for _ in range(4)]
+        _check(self._lib.bidomain_mlp_sizes(self._h, *[C.byref(x) for x in v]), "bidomain_mlp_sizes")
+        return dict(zip(("n_in", "n_hidden", "n_out", "batch"), (x.value for x in v)))
+
+    def mlp_params(self, w=None):
+        """Packed float32 parameters: upload `w` when given, else download."""
+        if w is not None:
+            w = np.ascontiguousarray(w, dtype=np.float32)
+            _check(self._lib.bidomain_mlp_params(self._h, w.ctypes.data, 1), "bidomain_mlp_params")
+            return w
+        sz = self.mlp_sizes()
+        n = sz["n_hidden"] * (sz["n_in"] + 1) + sz["n_hidden"] * (sz["n_hidden"] + 1) + \
+            sz["n_out"] * (sz["n_hidden"] + 1)
+        out = np.zeros(n, np.float32)
+        _check(self._lib.bidomain_mlp_params(self._h, out.ctypes.data, 0), "bidomain_mlp_params")
+        return out
+
+    def mlp_loss_grad(self, X, T, mask):
+        X, T, mask = (np.ascontiguousarray(a, dtype=np.float32) for a in (X, T, mask))
+        w = self.mlp_params()
+        g = np.zeros_like(w)
+        loss = C.c_double()
+        _check(self._lib.bidomain_mlp_loss_grad(self._h, X.ctypes.data, T.ctypes.data, mask.ctypes.data,
+                                                C.byref(loss), g.ctypes.data), "bidomain_mlp_loss_grad")
+        return loss.value, g
 
     def krylov_solve(self, f):
         out = _same_kind(f, 2 * self.N)

@@ -20,6 +20,7 @@
 
 #include "bidomain.h"
 #include "dd_kernels.cuh"
+#include "mlp.cuh"
 #include "plan.h"
 
 using namespace bd;
@@ -242,6 +243,13 @@ struct bd_handle {
   bool linearized = false;
   std::string last_error;
   Profiler prof;
+  // learned initial guess
+  MlpDev mlp;
+  bool mlp_on = false;
+  int hist_count = 0, mlp_steps_trained = 0;
+  int *d_node_ptr = nullptr, *d_node_ent = nullptr;
+  double *d_uh1i, *d_uh1e, *d_uh2i, *d_uh2e, *d_gi, *d_ge;
+  double rtol_scale = 1.0;
   cudaGraphExec_t pcg_exec[2] = {nullptr, nullptr};  // captured PCG chunk per method
   size_t pcg_nodes[2] = {0, 0};
   double gemv_schur_flops = 0, gemv_schur_bytes = 0, gemv_local_flops = 0, gemv_local_bytes = 0;
@@ -260,6 +268,96 @@ struct bd_handle {
 };
 
 namespace {
+
+// ---------------------------------------------------------------------------
+// learned initial guess: buffers, deterministic He-uniform initialisation
+// ---------------------------------------------------------------------------
+void setup_mlp(bd_handle &h) {
+  DevMem &m = h.mem;
+  cudaStream_t s = h.s;
+  MlpDev &M = h.mlp;
+  int maxq = 0;
+  for (auto &sp : h.plan.subs) maxq = std::max(maxq, (int)sp.nodes.size());
+  M.maxq = maxq;
+  M.batch = h.nsub;
+  M.n_in = 6 * maxq;
+  M.n_out = 2 * maxq;
+  const int H = M.n_hidden, B = M.batch;
+  M.off_W1 = 0;
+  M.off_b1 = M.off_W1 + (long long)H * M.n_in;
+  M.off_W2 = M.off_b1 + H;
+  M.off_b2 = M.off_W2 + (long long)H * H;
+  M.off_W3 = M.off_b2 + H;
+  M.off_b3 = M.off_W3 + (long long)M.n_out * H;
+  M.n_params = M.off_b3 + M.n_out;
+  M.w = m.alloc<float>(M.n_params);
+  M.g = m.alloc<float>(M.n_params);
+  M.am = m.alloc<float>(M.n_params);
+  M.av = m.alloc<float>(M.n_params);
+  ck(cudaMemsetAsync(M.am, 0, sizeof(float) * M.n_params, s), "memset");
+  ck(cudaMemsetAsync(M.av, 0, sizeof(float) * M.n_params, s), "memset");
+  M.b1 = M.w + M.off_b1;
+  M.b2 = M.w + M.off_b2;
+  M.b3 = M.w + M.off_b3;
+  M.Wb1 = m.alloc<__nv_bfloat16>((size_t)H * M.n_in);
+  M.Wb2 = m.alloc<__nv_bfloat16>((size_t)H * H);
+  M.Wb3 = m.alloc<__nv_bfloat16>((size_t)M.n_out * H);
+  M.X = m.alloc<float>((size_t)B * M.n_in);
+  M.Z1 = m.alloc<float>((size_t)B * H);
+  M.H1 = m.alloc<float>((size_t)B * H);
+  M.Z2 = m.alloc<float>((size_t)B * H);
+  M.H2 = m.alloc<float>((size_t)B * H);
+  M.Y = m.alloc<float>((size_t)B * M.n_out);
+  M.T = m.alloc<float>((size_t)B * M.n_out);
+  M.mask = m.alloc<float>((size_t)B * M.n_out);
+  M.dY = m.alloc<float>((size_t)B * M.n_out);
+  M.dZ1 = m.alloc<float>((size_t)B * H);
+  M.dZ2 = m.alloc<float>((size_t)B * H);
+  ck(cudaMemsetAsync(M.X, 0, sizeof(float) * B * M.n_in, s), "memset");
+  // He-uniform weights from a fixed splitmix64 stream, zero biases, last layer scaled by 0.1
+  std::vector<float> w(M.n_params, 0.f);
+  uint64_t st = 0x9E3779B97F4A7C15ULL;
+  auto uni = [&]() {
+    st += 0x9E3779B97F4A7C15ULL;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  };
+  auto fill = [&](long long off, long long n, int fan_in, double scale) {
+    const double lim = std::sqrt(6.0 / fan_in) * scale;
+    for (long long i = 0; i < n; ++i) w[off + i] = (float)((2.0 * uni() - 1.0) * lim);
+  };
+  fill(M.off_W1, (long long)H * M.n_in, M.n_in, 1.0);
+  fill(M.off_W2, (long long)H * H, H, 1.0);
+  fill(M.off_W3, (long long)M.n_out * H, H, 0.1);
+  ck(cudaMemcpyAsync(M.w, w.data(), sizeof(float) * M.n_params, cudaMemcpyHostToDevice, s), "mlp init");
+  mlp_refresh_bf16(M, s);
+  // node -> (subdomain, local node) entries for the prediction average
+  std::vector<std::vector<int>> lists(h.N);
+  for (int j = 0; j < h.nsub; ++j) {
+    const SubPlan &sp = h.plan.subs[j];
+    for (int a = 0; a < (int)sp.nodes.size(); ++a) lists[sp.nodes[a]].push_back(j * maxq + a);
+  }
+  std::vector<int> ptr(1, 0), ent;
+  for (auto &l : lists) { for (int v : l) ent.push_back(v); ptr.push_back((int)ent.size()); }
+  h.d_node_ptr = m.upload(ptr, s);
+  h.d_node_ent = m.upload(ent, s);
+  double **hv[] = {&h.d_uh1i, &h.d_uh1e, &h.d_uh2i, &h.d_uh2e, &h.d_gi, &h.d_ge};
+  for (double **v : hv) *v = m.alloc<double>(h.N);
+  h.mlp_on = true;
+}
+
+// One Adam step of the MLP on the features / targets / mask already in place;
+// returns nothing (the loss lands in d_scal[4] when `want_loss`).
+void mlp_train_once(bd_handle &h, bool want_loss) {
+  MlpDev &M = h.mlp;
+  mlp_forward(M, M.batch, h.s);
+  mlp_backward(M, M.batch, 1.f / (2.f * h.nq), h.d_partial, h.s);
+  if (want_loss) launch_sum_partials(kRedBlocks, h.d_partial, h.d_scal + 4, h.s);
+  mlp_adam(M, (float)h.opt.mlp_lr, h.s);
+}
 
 // ---------------------------------------------------------------------------
 // setup
@@ -697,6 +795,7 @@ void setup_handle(bd_handle &h) {
   h.d_hb = m.alloc<double>(h.hist_cap);
   const int io = std::max({2 * N, h.nif, h.nlam});
   for (int i = 0; i < 6; ++i) h.d_io[i] = m.alloc<double>(io);
+  if (h.opt.learned_guess) setup_mlp(h);
   ck(cudaStreamSynchronize(s), "setup");
 }
 
@@ -794,7 +893,7 @@ template <class Op, class Pc>
 int pcg(bd_handle &h, int n, const double *b, double *x, Op A, Pc M, bd_solve_stats *st) {
   cudaStream_t s = h.s;
   KrylovState ks{};
-  ks.rtol = h.opt.ksp_rtol;
+  ks.rtol = std::min(h.opt.ksp_rtol * h.rtol_scale, 0.1);
   ks.atol = h.opt.ksp_atol;
   ks.dtol = h.opt.ksp_dtol;
   ks.maxit = h.opt.ksp_max_it;
@@ -877,7 +976,7 @@ int gmres(bd_handle &h, int n, const double *b, double *x, Op A, Pc M, bd_solve_
   cudaStream_t s = h.s;
   const int m = h.opt.gmres_restart;
   GmresState init{};
-  init.rtol = h.opt.ksp_rtol;
+  init.rtol = std::min(h.opt.ksp_rtol * h.rtol_scale, 0.1);
   init.atol = h.opt.ksp_atol;
   init.dtol = h.opt.ksp_dtol;
   init.restart = m;
@@ -1005,14 +1104,34 @@ int step(bd_handle &h, const bd_stimulus *stim, bd_step_stats *out) {
   const StimParams sp = stim_params(h, stim, t_next);
   bd_step_stats st{};
   launch_gating(h.N, h.d_uin, h.d_uen, h.d_w, h.d_wn, h.fp, s);
-  // u^0 = u^n
+  // u^0 = u^n (the fallback)
   ck(cudaMemcpyAsync(h.d_ui, h.d_uin, sizeof(double) * h.N, cudaMemcpyDeviceToDevice, s), "copy");
   ck(cudaMemcpyAsync(h.d_ue, h.d_uen, sizeof(double) * h.N, cudaMemcpyDeviceToDevice, s), "copy");
   double fn2 = trial_residual(h, sp, nullptr, nullptr, 0.0);
   std::swap(h.d_ui, h.d_uit); std::swap(h.d_ue, h.d_uet);
   std::swap(h.d_ri, h.d_rit); std::swap(h.d_re, h.d_ret); std::swap(h.d_factor, h.d_factort);
+  // tolerances stay anchored to the fallback residual ||F(u^n) - G||
   const double fn0 = std::sqrt(fn2);
   st.res0 = fn0;
+  h.rtol_scale = 1.0;
+  if (h.mlp_on && h.hist_count >= 2) {
+    // learned guess u^n + MLP(traces of u^n, u^{n-1}, u^{n-2}); kept only if its residual is smaller
+    mlp_features(h.mlp, h.nq, h.d_q_sub, h.d_q_loc, h.d_q_node, h.d_uin, h.d_uen, h.d_uh1i, h.d_uh1e, h.d_uh2i,
+                 h.d_uh2e, nullptr, nullptr, s);
+    mlp_forward(h.mlp, h.mlp.batch, s);
+    mlp_guess(h.mlp, h.N, h.d_node_ptr, h.d_node_ent, h.d_uin, h.d_uen, h.d_gi, h.d_ge, s);
+    std::swap(h.d_ui, h.d_gi); std::swap(h.d_ue, h.d_ge);  // residual at the guess
+    const double g2 = trial_residual(h, sp, nullptr, nullptr, 0.0);
+    std::swap(h.d_ui, h.d_gi); std::swap(h.d_ue, h.d_ge);
+    st.res_guess = std::sqrt(g2);
+    if (h.mlp_steps_trained >= h.opt.mlp_warmup && std::isfinite(g2) && g2 < fn2) {
+      std::swap(h.d_ui, h.d_uit); std::swap(h.d_ue, h.d_uet);
+      std::swap(h.d_ri, h.d_rit); std::swap(h.d_re, h.d_ret); std::swap(h.d_factor, h.d_factort);
+      h.rtol_scale = std::min(fn0 / std::sqrt(std::max(g2, 1e-300)), 1e4);
+      fn2 = g2;
+      st.guess_used = 1;
+    }
+  }
   int reason = BD_OK;
   int k = 0;
   for (; k < h.opt.newton_max_it; ++k) {
@@ -1025,6 +1144,7 @@ int step(bd_handle &h, const bd_stimulus *stim, bd_step_stats *out) {
     launch_axpby(h.N, -1.0, h.d_re, 0.0, h.d_fe, s);
     bd_solve_stats ls{};
     int r = solve(h, h.d_fi, h.d_fe, h.d_si, h.d_se, &ls);
+    h.rtol_scale = 1.0;
     st.krylov_its += ls.its;
     st.cond_max = std::max(st.cond_max, ls.cond);
     if (r != BD_OK) { reason = r; break; }
@@ -1070,6 +1190,24 @@ int step(bd_handle &h, const bd_stimulus *stim, bd_step_stats *out) {
     reason = BD_ERR_NEWTON;
   st.newton_its = k;
   st.res_final = std::sqrt(fn2);
+  if (h.mlp_on && h.hist_count >= 2 && h.step_n < h.opt.mlp_train_steps && reason == BD_OK) {
+    // online training on (traces, u^{n+1} - u^n), before the gauge shift
+    MlpDev &M = h.mlp;
+    ck(cudaMemsetAsync(M.T, 0, sizeof(float) * M.batch * M.n_out, s), "memset");
+    ck(cudaMemsetAsync(M.mask, 0, sizeof(float) * M.batch * M.n_out, s), "memset");
+    mlp_features(M, h.nq, h.d_q_sub, h.d_q_loc, h.d_q_node, h.d_uin, h.d_uen, h.d_uh1i, h.d_uh1e, h.d_uh2i,
+                 h.d_uh2e, h.d_ui, h.d_ue, s);
+    for (int ep = 0; ep < std::max(1, h.opt.mlp_epochs); ++ep) mlp_train_once(h, ep == 0);
+    st.mlp_loss = read_scalar(h, h.d_scal + 4);
+    h.mlp_steps_trained += 1;
+  }
+  if (h.mlp_on) {  // history of the last states (gauge as stored)
+    ck(cudaMemcpyAsync(h.d_uh2i, h.d_uh1i, sizeof(double) * h.N, cudaMemcpyDeviceToDevice, s), "copy");
+    ck(cudaMemcpyAsync(h.d_uh2e, h.d_uh1e, sizeof(double) * h.N, cudaMemcpyDeviceToDevice, s), "copy");
+    ck(cudaMemcpyAsync(h.d_uh1i, h.d_uin, sizeof(double) * h.N, cudaMemcpyDeviceToDevice, s), "copy");
+    ck(cudaMemcpyAsync(h.d_uh1e, h.d_uen, sizeof(double) * h.N, cudaMemcpyDeviceToDevice, s), "copy");
+    h.hist_count = std::min(h.hist_count + 1, 2);
+  }
   // gauge: zero lumped-mass mean of u_e, then u^n <- u, w <- w^{n+1}
   launch_dot3(h.N, h.d_mass, h.d_ue, h.d_mass, h.d_ue, h.d_mass, h.d_ue, h.d_partial, h.d_scal, s);
   launch_fill(1, h.d_scal + 1, h.sum_mass, s);
@@ -1268,6 +1406,7 @@ int bd_options_default(bd_options *o) {
   o->use_graphs = 0;
   o->ksp_rtol = 1e-8; o->ksp_atol = 1e-10; o->ksp_dtol = 1e4;
   o->snes_rtol = 1e-4; o->snes_atol = 1e-8; o->snes_stol = 1e-8;
+  o->learned_guess = 0; o->mlp_train_steps = 200; o->mlp_warmup = 5; o->mlp_epochs = 4; o->mlp_lr = 1e-3;
   return BD_OK;
 }
 
@@ -1316,6 +1455,7 @@ int bidomain_set_state(bd_handle *h, const double *ui, const double *ue, const d
     ck(cudaMemcpyAsync(h->d_w, w, n * sizeof(double), k, h->s), "state");
     ck(cudaStreamSynchronize(h->s), "sync");
     h->step_n = std::lround(t / h->tau);
+    h->hist_count = 0;
     return BD_OK;
   });
 }
@@ -1443,6 +1583,55 @@ int krylov_solve(bd_handle *h, const double *f, double *s, int on_device, bd_sol
     finish_out(*h, s, o, 2 * n, on_device);
     if (r == BD_OK) r = h->check_err();
     return r;
+  });
+}
+
+int bidomain_mlp_sizes(bd_handle *h, int *n_in, int *n_hidden, int *n_out, int *batch) {
+  if (!h) return BD_ERR_ARG;
+  if (!h->mlp_on) return BD_ERR_STATE;
+  if (n_in) *n_in = h->mlp.n_in;
+  if (n_hidden) *n_hidden = h->mlp.n_hidden;
+  if (n_out) *n_out = h->mlp.n_out;
+  if (batch) *batch = h->mlp.batch;
+  return BD_OK;
+}
+
+int bidomain_mlp_params(bd_handle *h, float *w, int set) {
+  if (!h || !w) return BD_ERR_ARG;
+  if (!h->mlp_on) return BD_ERR_STATE;
+  return guard(h, [&] {
+    MlpDev &M = h->mlp;
+    if (set) {
+      ck(cudaMemcpyAsync(M.w, w, sizeof(float) * M.n_params, cudaMemcpyHostToDevice, h->s), "mlp params");
+      mlp_refresh_bf16(M, h->s);
+    } else {
+      ck(cudaMemcpyAsync(w, M.w, sizeof(float) * M.n_params, cudaMemcpyDeviceToHost, h->s), "mlp params");
+    }
+    ck(cudaStreamSynchronize(h->s), "sync");
+    return BD_OK;
+  });
+}
+
+int bidomain_mlp_loss_grad(bd_handle *h, const float *X, const float *T, const float *mask, double *loss,
+                           float *grad) {
+  if (!h || !X || !T || !mask) return BD_ERR_ARG;
+  if (!h->mlp_on) return BD_ERR_STATE;
+  return guard(h, [&] {
+    MlpDev &M = h->mlp;
+    const size_t nx = (size_t)M.batch * M.n_in, ny = (size_t)M.batch * M.n_out;
+    std::vector<float> mk(mask, mask + ny);
+    double cnt = 0.0;
+    for (float v : mk) cnt += v;
+    ck(cudaMemcpyAsync(M.X, X, sizeof(float) * nx, cudaMemcpyHostToDevice, h->s), "mlp X");
+    ck(cudaMemcpyAsync(M.T, T, sizeof(float) * ny, cudaMemcpyHostToDevice, h->s), "mlp T");
+    ck(cudaMemcpyAsync(M.mask, mask, sizeof(float) * ny, cudaMemcpyHostToDevice, h->s), "mlp mask");
+    mlp_forward(M, M.batch, h->s);
+    mlp_backward(M, M.batch, (float)(1.0 / std::max(cnt, 1.0)), h->d_partial, h->s);
+    launch_sum_partials(kRedBlocks, h->d_partial, h->d_scal + 4, h->s);
+    if (loss) *loss = read_scalar(*h, h->d_scal + 4);
+    if (grad) ck(cudaMemcpyAsync(grad, M.g, sizeof(float) * M.n_params, cudaMemcpyDeviceToHost, h->s), "grad");
+    ck(cudaStreamSynchronize(h->s), "sync");
+    return BD_OK;
   });
 }
 

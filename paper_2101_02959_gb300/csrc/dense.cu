@@ -213,6 +213,126 @@ static double trapezoid(long long t0, long long e, long long m) {
   return (double)(k * (m - t0) - k * (k - 1) / 2);
 }
 
+// ---- FP32 rank-k update: 128x128 CTA tiles, 8x8 outputs per thread ----------
+// Same modes and index ranges as k_rankk.  K is consumed in chunks of 16 with
+// the next chunk prefetched into registers while the current one is used.
+constexpr int kTB2 = 128, kKC2 = 16;
+
+__global__ void __launch_bounds__(256) k_rankk128(const MatDesc *__restrict__ desc, float *__restrict__ base,
+                                                  int mode, int k0, int K0, int K1, int nct) {
+  const MatDesc d = desc[blockIdx.y];
+  int row0, colend, kb, ke;
+  if (mode == 0) {
+    if (k0 >= d.e) return;
+    const int w = min(kNB, d.e - k0);
+    row0 = k0 + w; colend = min(K1, d.e); kb = k0; ke = k0 + w;
+  } else if (mode == 2) {
+    if (K1 >= d.e) return;
+    row0 = K1; colend = d.e; kb = K0; ke = K1;
+  } else {
+    row0 = d.e; colend = d.m; kb = 0; ke = d.e;
+  }
+  const int ti = blockIdx.x / nct, tj = blockIdx.x % nct;
+  if (tj > ti) return;
+  const int r0 = row0 + ti * kTB2, c0 = row0 + tj * kTB2;
+  if (r0 >= d.m || c0 >= colend || ke <= kb) return;
+  float *A = base + d.off;
+  __shared__ __align__(16) float As[2][kKC2][kTB2 + 4];
+  __shared__ __align__(16) float Bs[2][kKC2][kTB2 + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  // loader: thread -> (row lr, k offset lk): 128 rows x 16 k = 2 x 4 floats per thread per operand
+  const int lr = tid >> 1, lk = (tid & 1) * 8;
+  const int ra = r0 + lr, rb = c0 + lr;
+  const bool va = ra < d.m, vb = rb < colend;
+  const float *pa = A + (long long)ra * d.ld, *pb = A + (long long)rb * d.ld;
+  float la[8], lb[8];
+  auto load = [&](int kk) {
+#pragma unroll
+    for (int q = 0; q < 8; q += 4) {
+      const int k = kk + lk + q;
+      if (k + 3 < ke) {
+        const float4 x = va ? *reinterpret_cast<const float4 *>(pa + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 y = vb ? *reinterpret_cast<const float4 *>(pb + k) : make_float4(0.f, 0.f, 0.f, 0.f);
+        la[q] = x.x; la[q + 1] = x.y; la[q + 2] = x.z; la[q + 3] = x.w;
+        lb[q] = y.x; lb[q + 1] = y.y; lb[q + 2] = y.z; lb[q + 3] = y.w;
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          la[q + u] = (va && k + u < ke) ? pa[k + u] : 0.f;
+          lb[q + u] = (vb && k + u < ke) ? pb[k + u] : 0.f;
+        }
+      }
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      As[buf][lk + q][lr] = la[q];
+      Bs[buf][lk + q][lr] = lb[q];
+    }
+  };
+  float acc[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+  load(kb);
+  store(0);
+  __syncthreads();
+  int buf = 0;
+  for (int kk = kb; kk < ke; kk += kKC2) {
+    const bool more = kk + kKC2 < ke;
+    if (more) load(kk + kKC2);
+#pragma unroll
+    for (int k = 0; k < kKC2; ++k) {
+      const float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][k][ty * 4]);
+      const float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][k][64 + ty * 4]);
+      const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][k][tx * 4]);
+      const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][k][64 + tx * 4]);
+      const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+      const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] += av[i] * bv[j];
+    }
+    if (more) {
+      store(buf ^ 1);
+      __syncthreads();
+      buf ^= 1;
+    }
+  }
+  // thread owns rows {ty*4 + i, 64 + ty*4 + i} and columns {tx*4 + j, 64 + tx*4 + j}
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = r0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+    if (r >= d.m) continue;
+    float *crow = A + (long long)r * d.ld;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int c = c0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+      if (c < colend) crow[c] -= acc[i][j];
+    }
+  }
+}
+
+template <typename T>
+static void launch_rankk(const MatDesc *d_desc, T *base, int mode, int k0, int K0, int K1, int max_rows, int max_cols,
+                         int count, cudaStream_t s) {
+  const int nrt = ceil_div(max_rows, kTB), nct = ceil_div(max_cols, kTB);
+  if (nrt == 0 || nct == 0) return;
+  k_rankk<T><<<dim3(nrt * nct, count), 256, 0, s>>>(d_desc, base, mode, k0, K0, K1, nct);
+  count_launch();
+}
+template <>
+void launch_rankk<float>(const MatDesc *d_desc, float *base, int mode, int k0, int K0, int K1, int max_rows,
+                         int max_cols, int count, cudaStream_t s) {
+  const int nrt = ceil_div(max_rows, kTB2), nct = ceil_div(max_cols, kTB2);
+  if (nrt == 0 || nct == 0) return;
+  k_rankk128<<<dim3(nrt * nct, count), 256, 0, s>>>(d_desc, base, mode, k0, K0, K1, nct);
+  count_launch();
+}
+
 template <typename T>
 void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s,
                              T *linv, ProfHook *prof) {
@@ -220,7 +340,7 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
   for (int K0 = 0; K0 < sh.max_e; K0 += kOB) {
     const int K1 = K0 + kOB;
     for (int k0 = K0; k0 < std::min(K1, sh.max_e); k0 += kNB) {
-      int max_below = 0, max_rt = 0, max_ct = 0;
+      int max_below = 0, max_cols = 0;
       double fl_panel = 0.0, fl_upd = 0.0, by_upd = 0.0;
       for (int b = 0; b < sh.count; ++b) {
         if (k0 >= sh.e[b]) continue;
@@ -228,8 +348,7 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
         const int below = sh.m[b] - k0 - w;
         const int cend = std::min(K1, sh.e[b]);
         max_below = std::max(max_below, below);
-        max_rt = std::max(max_rt, ceil_div(below, kTB));
-        max_ct = std::max(max_ct, ceil_div(cend - k0 - w, kTB));
+        max_cols = std::max(max_cols, cend - k0 - w);
         fl_panel += (double)w * w * w / 3.0 + (double)below * w * w;
         const double ent = trapezoid(k0 + w, cend, sh.m[b]);
         fl_upd += 2.0 * w * ent;
@@ -244,47 +363,41 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
         count_launch();
       }
       if (prof) prof->end(PROF_PANEL, s, fl_panel, 0.0);
-      if (max_rt > 0 && max_ct > 0) {
-        dim3 gu(max_rt * max_ct, sh.count);
+      if (max_below > 0 && max_cols > 0) {
         if (prof) prof->begin(PROF_RANKK, s);
-        k_rankk<T><<<gu, 256, 0, s>>>(d_desc, base, 0, k0, K0, K1, max_ct);
-        count_launch();
+        launch_rankk<T>(d_desc, base, 0, k0, K0, K1, max_below, max_cols, sh.count, s);
         if (prof) prof->end(PROF_RANKK, s, fl_upd, by_upd);
       }
     }
     // outer update of the trailing columns [K1, e) with the finished outer panel
-    int max_rt = 0, max_ct = 0;
+    int max_rows = 0, max_cols = 0;
     double fl = 0.0, by = 0.0;
     for (int b = 0; b < sh.count; ++b) {
       if (K1 >= sh.e[b]) continue;
-      max_rt = std::max(max_rt, ceil_div(sh.m[b] - K1, kTB));
-      max_ct = std::max(max_ct, ceil_div(sh.e[b] - K1, kTB));
+      max_rows = std::max(max_rows, sh.m[b] - K1);
+      max_cols = std::max(max_cols, sh.e[b] - K1);
       const double ent = trapezoid(K1, sh.e[b], sh.m[b]);
       fl += 2.0 * kOB * ent;
       by += sizeof(T) * (2.0 * ent + (double)kOB * (sh.m[b] - K1));
     }
-    if (max_rt > 0 && max_ct > 0) {
-      dim3 gu(max_rt * max_ct, sh.count);
+    if (max_rows > 0 && max_cols > 0) {
       if (prof) prof->begin(PROF_RANKK, s);
-      k_rankk<T><<<gu, 256, 0, s>>>(d_desc, base, 2, 0, K0, K1, max_ct);
-      count_launch();
+      launch_rankk<T>(d_desc, base, 2, 0, K0, K1, max_rows, max_cols, sh.count, s);
       if (prof) prof->end(PROF_RANKK, s, fl, by);
     }
   }
   int max_t = 0;
   double fl = 0.0, by = 0.0;
   for (int b = 0; b < sh.count; ++b) {
-    max_t = std::max(max_t, ceil_div(sh.m[b] - sh.e[b], kTB));
+    max_t = std::max(max_t, sh.m[b] - sh.e[b]);
     const double n2 = sh.m[b] - sh.e[b];
     const double ent = n2 * (n2 + 1) / 2.0;
     fl += 2.0 * sh.e[b] * ent;
     by += sizeof(T) * (2.0 * ent + n2 * sh.e[b]);
   }
   if (max_t > 0) {
-    dim3 gf(max_t * max_t, sh.count);
     if (prof) prof->begin(PROF_RANKK, s);
-    k_rankk<T><<<gf, 256, 0, s>>>(d_desc, base, 1, 0, 0, 0, max_t);
-    count_launch();
+    launch_rankk<T>(d_desc, base, 1, 0, 0, 0, max_t, max_t, sh.count, s);
     if (prof) prof->end(PROF_RANKK, s, fl, by);
   }
 }

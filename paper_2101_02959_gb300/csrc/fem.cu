@@ -253,6 +253,11 @@ void launch_dot3(int n, const double *a0, const double *b0, const double *a1, co
   count_launch();
 }
 
+void launch_sum_partials(int nblk, const double *partial, double *out, cudaStream_t s) {
+  k_finalize<<<1, 256, 0, s>>>(nblk, 1, partial, out);
+  count_launch();
+}
+
 void launch_gauge_shift(int n, double *ui, double *ue, const double *scal, cudaStream_t s) {
   k_gauge_shift<<<ceil_div(n, 256), 256, 0, s>>>(n, ui, ue, scal);
   count_launch();

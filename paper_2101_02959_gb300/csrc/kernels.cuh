@@ -48,6 +48,7 @@ void launch_residual(int n, const double *stencil, const int *nbr, const double 
 void launch_dot3(int n, const double *a0, const double *b0, const double *a1, const double *b1, const double *a2,
                  const double *b2, double *partial, double *out, cudaStream_t s);
 void launch_gauge_shift(int n, double *ui, double *ue, const double *scal, cudaStream_t s);
+void launch_sum_partials(int nblk, const double *partial, double *out, cudaStream_t s);
 
 // dense.cu -- batched partial Cholesky: eliminates the first e columns of every
 // matrix; afterwards the trailing (m-e) x (m-e) lower triangle holds the Schur

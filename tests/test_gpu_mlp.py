@@ -1,0 +1,81 @@
+"""Learned initial guess on the GPU: gradients against the FP64 oracle, and its gain."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import mlp
+
+pytestmark = pytest.mark.gpu
+
+
+def _solver(name, **opt):
+    from paper_2101_02959_gb300 import binding, build
+    build.build()
+    return binding.Solver(synth.workload(name), synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, **opt)
+
+
+def _bf16(a):
+    """Round float32 values to bfloat16 (round to nearest even), as the GPU weights are."""
+    b = np.ascontiguousarray(a, np.float32).view(np.uint32)
+    r = ((b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32)
+
+
+def test_mlp_loss_and_gradients_match_oracle():
+    s = _solver("cube8ve", learned_guess=1)
+    sz = s.mlp_sizes()
+    n_in, H, n_out, B = sz["n_in"], sz["n_hidden"], sz["n_out"], sz["batch"]
+    rng = np.random.default_rng(7)
+    p = mlp.init_params(n_in, H, n_out, seed=3)
+    for k in ("b1", "b2", "b3"):
+        p[k] = 0.01 * rng.standard_normal(p[k].shape)
+    for k in ("W1", "W2", "W3"):
+        p[k] = _bf16(p[k]).astype(np.float64)  # the oracle runs on the bfloat16 weights
+    w = np.concatenate([p["W1"].ravel(), p["b1"], p["W2"].ravel(), p["b2"], p["W3"].ravel(), p["b3"]])
+    s.mlp_params(w.astype(np.float32))
+    X = rng.standard_normal((B, n_in)).astype(np.float32)
+    T = rng.standard_normal((B, n_out)).astype(np.float32)
+    mask = (rng.random((B, n_out)) < 0.8).astype(np.float32)
+    loss, g = s.mlp_loss_grad(X, T, mask)
+    L, gr = mlp.loss_and_grads(p, X.astype(np.float64), T.astype(np.float64), mask.astype(np.float64))
+    assert abs(loss - L) < 1e-5 * L
+    off = 0
+    for k, shape in (("W1", (H, n_in)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (n_out, H)),
+                     ("b3", (n_out,))):
+        n = int(np.prod(shape))
+        got = g[off:off + n].astype(np.float64)
+        ref = gr[k].ravel()
+        assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref), k
+        off += n
+    assert off == g.size
+
+
+def _run(name, steps, **opt):
+    s = _solver(name, **opt)
+    ui, ue, w = synth.initial_state(s.N, 0)
+    s.set_state(ui, ue, w, 0.0)
+    stats = [s.step(synth.STIMULUS) for _ in range(steps)]
+    out = s.get_state()
+    s.close()
+    return stats, out
+
+
+def test_learned_guess_gain_and_agreement():
+    """Trained online, the guess beats the previous-step state and saves Krylov iterations."""
+    steps = 40
+    base, (bi, be, _, _) = _run("cube8ve", steps)
+    lg, (li, le, _, _) = _run("cube8ve", steps, learned_guess=1, mlp_train_steps=steps, mlp_warmup=5)
+    assert all(st["reason"] == 0 for st in base + lg)
+    late = lg[15:]
+    used = [st for st in late if st["guess_used"]]
+    assert len(used) >= 0.6 * len(late)
+    ratio = np.median([st["res_guess"] / st["res0"] for st in late])
+    assert ratio < 0.6
+    kry_base = sum(st["krylov_its"] for st in base[15:])
+    kry_lg = sum(st["krylov_its"] for st in late)
+    assert kry_lg < kry_base
+    # both runs satisfy the same anchored Newton test: states agree to the SNES tolerance level
+    assert np.linalg.norm(le - be) / np.linalg.norm(be) < 1e-3
+    assert np.linalg.norm((li - le) - (bi - be)) / np.linalg.norm(bi - be) < 1e-3
+    print(f"krylov its (last {len(late)} steps): previous-step guess {kry_base}, learned guess {kry_lg}; "
+          f"median residual ratio {ratio:.3f}")
