@@ -115,9 +115,10 @@ def run_gpu(args, w, rank, world):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         return float(t.item())
 
-    def timed(precision, method, profile=False, clocks=None, graphs=1):
+    def timed(precision, method, profile=False, clocks=None, graphs=1, learned=0):
         s = binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, stream=stream.cuda_stream,
-                           precision=precision, method=method, use_graphs=graphs)
+                           precision=precision, method=method, use_graphs=graphs, learned_guess=learned,
+                           mlp_train_steps=args.steps + args.warmup + 1)
         s.set_state(*dstate, 0.0)
         for _ in range(args.warmup):
             s.step(synth.STIMULUS)
@@ -146,19 +147,22 @@ def run_gpu(args, w, rank, world):
         newton = sum(st["newton_its"] for st in stats)
         kry = sum(st["krylov_its"] for st in stats)
         bad = [st["reason"] for st in stats if st["reason"] != 0]
+        used = sum(st.get("guess_used", 0) for st in stats)
         return dict(ms=ms, newton=newton, krylov=kry, launches=launches, prof=prof, clocks=clk, bad=bad,
-                    cond=max(st["cond_max"] for st in stats), final=final)
+                    cond=max(st["cond_max"] for st in stats), final=final, guess_used=used)
 
-    chosen = timed(args.precision, args.method, clocks=ClockSampler(dev))
+    chosen = timed(args.precision, args.method, clocks=ClockSampler(dev), learned=args.learned)
+    other = timed(args.precision, args.method, learned=1 - args.learned)
     # per-launch CUDA events need stream launches: a second pass of the same K steps, profiled
-    profiled = timed(args.precision, args.method, profile=True, graphs=0)
+    profiled = timed(args.precision, args.method, profile=True, graphs=0, learned=args.learned)
     chosen["prof"] = profiled["prof"]
     chosen["prof_ms"] = profiled["ms"]
     plain = timed("fp64", args.method) if not args.no_plain else None
 
     # e2e: the same chosen run through host buffers, state copied in and out every step
     s = binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, stream=stream.cuda_stream,
-                       precision=args.precision, method=args.method, use_graphs=1)
+                       precision=args.precision, method=args.method, use_graphs=1, learned_guess=args.learned,
+                       mlp_train_steps=args.steps + args.warmup + 1)
     hs = (ui0.copy(), ue0.copy(), w0.copy())
     s.set_state(*hs, 0.0)
     for _ in range(args.warmup):
@@ -179,7 +183,7 @@ def run_gpu(args, w, rank, world):
     s.close()
 
     K = args.steps
-    out = dict(chosen=chosen, plain=plain, e2e_ms=e2e_ms, e2e_newton=e2e_newton, N=N)
+    out = dict(chosen=chosen, plain=plain, other=other, e2e_ms=e2e_ms, e2e_newton=e2e_newton, N=N)
     # final-state agreement of the chosen and the plain FP64 solvers after K steps
     if plain is not None:
         a, b = chosen["final"], plain["final"]
@@ -249,6 +253,7 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--method", default="bddc", choices=["bddc", "fetidp"])
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--learned", type=int, default=1, help="1: learned initial guess in the chosen solver")
     ap.add_argument("--cpu-steps", type=int, default=1, help="oracle time steps in the CPU baseline (0: skip)")
     args = ap.parse_args()
 
@@ -299,11 +304,15 @@ def main():
         "vs_baseline": None, "dtype": "f32 local factors + f64 Krylov/Newton/coarse" if args.precision == "mixed"
         else "f64", "data": "synthetic",
         "config": {"workload": describe(w), "unknowns": 2 * r["N"], "method": args.method + "-deluxe",
-                   "krylov": "pcg", "precision": args.precision, "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "krylov": "pcg", "precision": args.precision, "learned_guess": bool(args.learned), "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "per-step working set > 129 MB L2 (local matrices 0.27 GB f32 / 0.54 GB f64)"},
         "krylov_solves_per_s": ch["newton"] / sec,
         "dof_iterations_per_s": 2 * r["N"] * ch["krylov"] / sec,
         "newton_its": ch["newton"], "krylov_its": ch["krylov"], "cond_max": ch["cond"],
+        "learned_guess": {"enabled": bool(args.learned), "steps_using_guess": ch["guess_used"],
+                          "other_variant": {"learned_guess": bool(1 - args.learned),
+                                            "ms_per_step": r["other"]["ms"] / K,
+                                            "krylov_its": r["other"]["krylov"], "newton_its": r["other"]["newton"]}},
         "aggregate_steps_per_s": world * K / sec,
         "e2e": {"value": r["e2e_ms"] / K, "unit": "ms/time step", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},

@@ -137,6 +137,10 @@ typedef struct {
    * fallback residual. */
   int learned_guess, mlp_train_steps, mlp_warmup, mlp_epochs;
   double mlp_lr;
+  /* BD_MIXED only: 1 = the long-K Schur updates of the factorisations run on
+   * the tensor cores (tcgen05, TF32 split in hi + lo parts, FP32 accumulation) */
+  int use_tensor_cores;
+  int pad_;
 } bd_options;
 
 typedef struct {

@@ -808,7 +808,7 @@ void linearize_t(bd_handle &h, Dense<T> &D) {
   ck(cudaMemsetAsync(D.K, 0, sizeof(T) * h.K_el, s), "memset K");
   launch_assemble_local<T>(h.nq, h.d_q_sub, h.d_q_loc, h.d_q_node, h.d_q_nbr, h.d_q_stencil, h.d_q_mass, h.d_factor,
                            h.tau, h.d_Kdesc, D.K, s);
-  engine_partial_cholesky<T>(h.shK, h.d_Kdesc, D.K, h.d_err, s, D.Linv, &h.prof);
+  engine_partial_cholesky<T>(h.shK, h.d_Kdesc, D.K, h.d_err, s, D.Linv, &h.prof, h.opt.use_tensor_cores != 0);
   launch_copy<T, T>(h.cp_sorig.n, h.cp_sorig.max_elems, h.cp_sorig.d, D.K, D.Sorig, s);
   long long max_a = 0;
   for (int j = 0; j < h.nsub; ++j) max_a = std::max(max_a, (long long)h.shA.m[j] * h.shA.m[j]);
@@ -816,7 +816,7 @@ void linearize_t(bd_handle &h, Dense<T> &D) {
                       h.d_tl_row, h.d_tl_val, s);
   launch_copy<T, T>(h.cp_sdd.n, h.cp_sdd.max_elems, h.cp_sdd.d, D.Aug, D.SDD, s);
   launch_copy<T, T>(h.cp_blk.n, h.cp_blk.max_elems, h.cp_blk.d, D.Aug, D.Blk, s);
-  engine_partial_cholesky<T>(h.shA, h.d_Adesc, D.Aug, h.d_err, s, D.Linv, &h.prof);
+  engine_partial_cholesky<T>(h.shA, h.d_Adesc, D.Aug, h.d_err, s, D.Linv, &h.prof, h.opt.use_tensor_cores != 0);
   launch_copy<T, T>(h.cp_zx.n, h.cp_zx.max_elems, h.cp_zx.d, D.Aug, D.Z, s);
   launch_class_aug<T>(h.ncls, h.max_nc, h.d_cls, h.d_pairs, D.Blk, h.d_Cdesc, D.CA, s);
   engine_partial_cholesky<T>(h.shC, h.d_Cdesc, D.CA, h.d_err, s, D.Linv);
@@ -1407,6 +1407,7 @@ int bd_options_default(bd_options *o) {
   o->ksp_rtol = 1e-8; o->ksp_atol = 1e-10; o->ksp_dtol = 1e4;
   o->snes_rtol = 1e-4; o->snes_atol = 1e-8; o->snes_stol = 1e-8;
   o->learned_guess = 0; o->mlp_train_steps = 200; o->mlp_warmup = 5; o->mlp_epochs = 4; o->mlp_lr = 1e-3;
+  o->use_tensor_cores = 0;
   return BD_OK;
 }
 
@@ -1429,6 +1430,11 @@ int bidomain_setup(const bd_mesh *mesh, const bd_conductivity *cond, const bd_io
     h->fp.vp = ionic->vp; h->fp.chi_cm = ionic->chi_cm; h->fp.tau = tau;
     if (stream) h->s = (cudaStream_t)stream;
     else { ck(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking), "stream"); h->own_stream = true; }
+    if (h->opt.use_tensor_cores && h->opt.precision == BD_MIXED && !tc_configure()) {
+      g_last_error = "tensor-core kernel configuration failed";
+      return BD_ERR_CUDA;
+    }
+    if (h->opt.precision != BD_MIXED) h->opt.use_tensor_cores = 0;
     setup_handle(*h);
     *out = h.release();
     return BD_OK;

@@ -10,6 +10,7 @@
 // Section 4.4), -S_DD^-1 S_DP and -S_DD^-1 (the local constrained solve).
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 #include <vector>
 
 #include "kernels.cuh"
@@ -335,7 +336,7 @@ void launch_rankk<float>(const MatDesc *d_desc, float *base, int mode, int k0, i
 
 template <typename T>
 void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s,
-                             T *linv, ProfHook *prof) {
+                             T *linv, ProfHook *prof, bool tc) {
   if (sh.count == 0) return;
   for (int K0 = 0; K0 < sh.max_e; K0 += kOB) {
     const int K1 = K0 + kOB;
@@ -382,7 +383,12 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
     }
     if (max_rows > 0 && max_cols > 0) {
       if (prof) prof->begin(PROF_RANKK, s);
-      launch_rankk<T>(d_desc, base, 2, 0, K0, K1, max_rows, max_cols, sh.count, s);
+      if constexpr (std::is_same<T, float>::value) {
+        if (tc) launch_rankk_tc(d_desc, base, 2, K0, K1, max_rows, max_cols, sh.count, d_err, s);
+        else launch_rankk<T>(d_desc, base, 2, 0, K0, K1, max_rows, max_cols, sh.count, s);
+      } else {
+        launch_rankk<T>(d_desc, base, 2, 0, K0, K1, max_rows, max_cols, sh.count, s);
+      }
       if (prof) prof->end(PROF_RANKK, s, fl, by);
     }
   }
@@ -397,7 +403,12 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
   }
   if (max_t > 0) {
     if (prof) prof->begin(PROF_RANKK, s);
-    launch_rankk<T>(d_desc, base, 1, 0, 0, 0, max_t, max_t, sh.count, s);
+    if constexpr (std::is_same<T, float>::value) {
+      if (tc) launch_rankk_tc(d_desc, base, 1, 0, 0, max_t, max_t, sh.count, d_err, s);
+      else launch_rankk<T>(d_desc, base, 1, 0, 0, 0, max_t, max_t, sh.count, s);
+    } else {
+      launch_rankk<T>(d_desc, base, 1, 0, 0, 0, max_t, max_t, sh.count, s);
+    }
     if (prof) prof->end(PROF_RANKK, s, fl, by);
   }
 }
@@ -585,7 +596,7 @@ void launch_trsv(int count, int max_n, const MatDesc *d_desc, const int *vec_off
 
 #define BD_INST(T)                                                                                              \
   template void engine_partial_cholesky<T>(const EngineShape &, const MatDesc *, T *, int *, cudaStream_t,    \
-                                           T *, ProfHook *);     \
+                                           T *, ProfHook *, bool);     \
   template void launch_gemv<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *,        \
                                double *, double, const int *, cudaStream_t);                                   \
   template void launch_gemv_t<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *,      \

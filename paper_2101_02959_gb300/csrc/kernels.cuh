@@ -59,9 +59,15 @@ struct EngineShape {
   std::vector<int> m, e;  // host copies for per-step grid sizes
 };
 // linv: scratch of count * kNB * kNB elements (the inverse of each diagonal block).
+// tc: FP32 only, run the long-K updates on the tensor cores (tc.cu).
 template <typename T>
 void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s,
-                             T *linv, ProfHook *prof = nullptr);
+                             T *linv, ProfHook *prof = nullptr, bool tc = false);
+
+// tc.cu
+bool tc_configure();
+void launch_rankk_tc(const MatDesc *d_desc, float *base, int mode, int K0, int K1, int max_rows, int max_cols,
+                     int count, int *err, cudaStream_t s);
 
 // y = alpha * A x (+ y): tasks in d_tasks (GemvDesc); x gathered through xidx when flagged.
 template <typename T>

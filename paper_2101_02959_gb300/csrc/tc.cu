@@ -1,0 +1,237 @@
+// Rank-k Schur updates on the 5th-generation tensor cores (tcgen05, kind::tf32).
+//
+// C[r][c] -= sum_k A[r][k] A[c][k] over one 128 x 128 lower tile per CTA, for
+// the long-K updates of the partial Cholesky (outer panels and the final Schur
+// complement S = K_GG - L_GI L_GI^T, Section 4.1).  FP32 operands are split as
+// a = a_hi + a_lo with a_hi, a_lo TF32, and a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi
+// (three MMAs per K step, FP32 accumulation in tensor memory), which keeps the
+// Schur complement at FP32 accuracy.
+//
+// Per K chunk of 32: 128 threads load the two 128 x 32 tiles (coalesced),
+// split them and store hi / lo copies in shared memory in the K-major layout
+// with the 128-byte swizzle; one thread issues the MMAs and commits them to an
+// mbarrier; the CTA waits on it (bounded) before reusing the buffers.  The
+// epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM lanes
+// 32w .. 32w+31 = tile rows) and subtracts it from C.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "kernels.cuh"
+
+namespace bd {
+
+namespace {
+
+constexpr int kTM = 128;          // tile rows (MMA M) and columns (MMA N)
+constexpr int kKc = 32;           // fp32 K elements per chunk = one 128-byte swizzle row
+constexpr int kTileBytes = kTM * kKc * 4;  // 16 KB per operand copy
+constexpr uint32_t kTmemCols = 128;
+constexpr long long kWaitLimit = 1LL << 22;
+
+__device__ inline uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ inline uint64_t sw128_desc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);          // start address
+  d |= (uint64_t)(16 >> 4) << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                         // descriptor version for tcgen05
+  d |= (uint64_t)2 << 61;                         // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor: D f32, A and B tf32, both K-major, M = N = 128.
+__device__ inline uint32_t idesc_tf32() {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTM >> 3) << 17) | ((uint32_t)(kTM >> 4) << 24);
+}
+
+__device__ inline float tf32_round(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+__device__ inline void mma_tf32(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "setp.ne.u32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(accum));
+}
+
+// Bounded wait on an mbarrier phase; false on timeout.
+__device__ inline bool mbar_wait(uint32_t bar, uint32_t phase) {
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(phase));
+    if (ok) return true;
+  }
+  return false;
+}
+
+}  // namespace
+
+// mode 1: rows/cols [e, m), K = [0, e); mode 2: rows [K1, m), cols [K1, e), K = [K0, K1).
+__global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__ desc, float *__restrict__ base,
+                                                     int mode, int K0, int K1, int nct, int *__restrict__ err) {
+  const MatDesc d = desc[blockIdx.y];
+  int row0, colend, kb, ke;
+  if (mode == 2) {
+    if (K1 >= d.e) return;
+    row0 = K1; colend = d.e; kb = K0; ke = K1;
+  } else {
+    row0 = d.e; colend = d.m; kb = 0; ke = d.e;
+  }
+  const int ti = blockIdx.x / nct, tj = blockIdx.x % nct;
+  if (tj > ti) return;
+  const int r0 = row0 + ti * kTM, c0 = row0 + tj * kTM;
+  if (r0 >= d.m || c0 >= colend || ke <= kb) return;
+  float *A = base + d.off;
+
+  extern __shared__ unsigned char smem_raw[];
+  __shared__ uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  const uint32_t raw = smem_addr(smem_raw);
+  const uint32_t tiles = (raw + 1023u) & ~1023u;  // 1024-byte aligned: swizzle atoms
+  unsigned char *tile_ptr = smem_raw + (tiles - raw);
+  // four operand copies: A_hi, A_lo, B_hi, B_lo
+  const uint32_t sA_hi = tiles, sA_lo = tiles + kTileBytes, sB_hi = tiles + 2 * kTileBytes,
+                 sB_lo = tiles + 3 * kTileBytes;
+  const int tid = threadIdx.x, warp = tid >> 5;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  const uint32_t bar = smem_addr(&mbar);
+  const uint32_t idesc = idesc_tf32();
+
+  // loader mapping: thread -> 16-byte chunk j of rows (tid / 8) + 16 i
+  const int j = tid & 7, rr = tid >> 3;
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int kk = kb; kk < ke && ok; kk += kKc) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int r = rr + 16 * i;
+      const int k = kk + 4 * j;
+      const int ra = r0 + r, rb = c0 + r;
+      float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+      if (k + 3 < ke) {
+        if (ra < d.m) a = *reinterpret_cast<const float4 *>(A + (long long)ra * d.ld + k);
+        if (rb < colend) b = *reinterpret_cast<const float4 *>(A + (long long)rb * d.ld + k);
+      } else {
+        float *pa = &a.x, *pb = &b.x;
+        for (int u = 0; u < 4; ++u) {
+          if (k + u < ke && ra < d.m) pa[u] = A[(long long)ra * d.ld + k + u];
+          if (k + u < ke && rb < colend) pb[u] = A[(long long)rb * d.ld + k + u];
+        }
+      }
+      const float4 ah = make_float4(tf32_round(a.x), tf32_round(a.y), tf32_round(a.z), tf32_round(a.w));
+      const float4 al = make_float4(tf32_round(a.x - ah.x), tf32_round(a.y - ah.y), tf32_round(a.z - ah.z),
+                                    tf32_round(a.w - ah.w));
+      const float4 bh = make_float4(tf32_round(b.x), tf32_round(b.y), tf32_round(b.z), tf32_round(b.w));
+      const float4 bl = make_float4(tf32_round(b.x - bh.x), tf32_round(b.y - bh.y), tf32_round(b.z - bh.z),
+                                    tf32_round(b.w - bh.w));
+      const uint32_t off = (uint32_t)r * 128u + (uint32_t)((j ^ (r & 7)) * 16);
+      *reinterpret_cast<float4 *>(tile_ptr + off) = ah;
+      *reinterpret_cast<float4 *>(tile_ptr + kTileBytes + off) = al;
+      *reinterpret_cast<float4 *>(tile_ptr + 2 * kTileBytes + off) = bh;
+      *reinterpret_cast<float4 *>(tile_ptr + 3 * kTileBytes + off) = bl;
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+      for (int t = 0; t < kKc / 8; ++t) {  // K = 8 tf32 = 32 bytes per MMA
+        const uint32_t adv = (uint32_t)t * 32u;
+        const uint32_t first = (kk == kb && t == 0) ? 0u : 1u;
+        mma_tf32(tmem, sw128_desc(sA_hi + adv), sw128_desc(sB_hi + adv), idesc, first);
+        mma_tf32(tmem, sw128_desc(sA_hi + adv), sw128_desc(sB_lo + adv), idesc, 1u);
+        mma_tf32(tmem, sw128_desc(sA_lo + adv), sw128_desc(sB_hi + adv), idesc, 1u);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
+    }
+    // the MMAs read the staged tiles: wait before they are overwritten (and before the epilogue);
+    // the timeout decision is made uniform across the CTA by the barrier itself
+    const bool late = __syncthreads_or(!mbar_wait(bar, phase) ? 1 : 0) != 0;
+    phase ^= 1u;
+    if (late) {
+      ok = false;
+      if (tid == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+    }
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    // epilogue: warp w reads TMEM lanes 32w + lane (tile row), 32 columns per load
+    const int r = r0 + warp * 32 + (tid & 31);
+    for (int cc = 0; cc < kTM; cc += 32) {
+      uint32_t v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+          "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+            "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+            "=r"(v[30]), "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (r < d.m) {
+        float *crow = A + (long long)r * d.ld;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+          const int c = c0 + cc + q;
+          if (c < colend) crow[c] -= __uint_as_float(v[q]);
+        }
+      }
+    }
+  } else {
+    // an MMA never completed: give it one more bounded wait before the accumulator is released
+    mbar_wait(bar, phase ^ 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  }
+}
+
+static constexpr int kTcSmem = 4 * kTileBytes + 1024;
+
+bool tc_configure() {
+  return cudaFuncSetAttribute(k_rankk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) == cudaSuccess;
+}
+
+void launch_rankk_tc(const MatDesc *d_desc, float *base, int mode, int K0, int K1, int max_rows, int max_cols,
+                     int count, int *err, cudaStream_t s) {
+  const int nrt = ceil_div(max_rows, kTM), nct = ceil_div(max_cols, kTM);
+  if (nrt == 0 || nct == 0) return;
+  k_rankk_tc<<<dim3(nrt * nct, count), 128, kTcSmem, s>>>(d_desc, base, mode, K0, K1, nct, err);
+  count_launch();
+}
+
+}  // namespace bd
