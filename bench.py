@@ -118,7 +118,9 @@ def run_gpu(args, w, rank, world):
     def timed(precision, method, profile=False, clocks=None, graphs=1, learned=0):
         s = binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, stream=stream.cuda_stream,
                            precision=precision, method=method, use_graphs=graphs, learned_guess=learned,
-                           mlp_train_steps=args.steps + args.warmup + 1)
+                           mlp_train_steps=args.steps + args.warmup + 1,
+                           use_tensor_cores=int(precision == "mixed" and args.tc),
+                           lag_jacobian=int(precision == "mixed" and args.lag))
         s.set_state(*dstate, 0.0)
         for _ in range(args.warmup):
             s.step(synth.STIMULUS)
@@ -162,7 +164,9 @@ def run_gpu(args, w, rank, world):
     # e2e: the same chosen run through host buffers, state copied in and out every step
     s = binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, stream=stream.cuda_stream,
                        precision=args.precision, method=args.method, use_graphs=1, learned_guess=args.learned,
-                       mlp_train_steps=args.steps + args.warmup + 1)
+                       mlp_train_steps=args.steps + args.warmup + 1,
+                       use_tensor_cores=int(args.precision == "mixed" and args.tc),
+                       lag_jacobian=int(args.precision == "mixed" and args.lag))
     hs = (ui0.copy(), ue0.copy(), w0.copy())
     s.set_state(*hs, 0.0)
     for _ in range(args.warmup):
@@ -243,6 +247,45 @@ def cpu_baseline(w, steps=1):
                 seconds=sec)
 
 
+def sweep(args):
+    """Optimality sweep (Section 6, Test 3 shape): 4x4x4 subdomains, H/h = 4, 8, 12, 16, V+E primal.
+
+    One time step of the 0.8 cm cube per H/h (after one warm-up step), mixed and FP64: Krylov
+    iterations, Lanczos condition number and ms per step.
+    """
+    import torch
+
+    import synth
+    from paper_2101_02959_gb300 import binding, build
+    build.build()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    rows = []
+    for k in args.sweep_hh:
+        w = synth.workload(f"opt{k}")
+        for prec in ("mixed", "fp64"):
+            if prec == "fp64" and k > 12:  # ~20 s per FP64 factorisation at this size: mixed only
+                continue
+            s = binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, stream=stream.cuda_stream,
+                               precision=prec, use_graphs=1, use_tensor_cores=int(prec == "mixed"))
+            ui, ue, wv = synth.initial_state(s.N, 0)
+            s.set_state(ui, ue, wv, 0.0)
+            s.step(synth.STIMULUS)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = s.step(synth.STIMULUS)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            rows.append(dict(hh=k, precision=prec, unknowns=2 * s.N, newton=st["newton_its"],
+                             krylov_per_newton=st["krylov_its"] / max(st["newton_its"], 1),
+                             cond=st["cond_max"], ms=e0.elapsed_time(e1), reason=st["reason"]))
+            s.close()
+            del s
+            torch.cuda.empty_cache()
+    print(json.dumps({"sweep": "opt (4x4x4 subdomains, V+E, deluxe BDDC, PCG)", "rows": rows}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -254,8 +297,15 @@ def main():
     ap.add_argument("--method", default="bddc", choices=["bddc", "fetidp"])
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--learned", type=int, default=1, help="1: learned initial guess in the chosen solver")
+    ap.add_argument("--tc", type=int, default=1, help="1: tensor-core (tcgen05) Schur updates in mixed precision")
+    ap.add_argument("--lag", type=int, default=1, help="1: chord Newton (one factorisation per time step), mixed only")
     ap.add_argument("--cpu-steps", type=int, default=1, help="oracle time steps in the CPU baseline (0: skip)")
+    ap.add_argument("--sweep", action="store_true", help="H/h optimality sweep instead of the benchmark")
+    ap.add_argument("--sweep-hh", type=int, nargs="*", default=[4, 8, 12, 16])
     args = ap.parse_args()
+    if args.sweep:
+        sweep(args)
+        return
 
     import synth
     w = synth.workload(args.workload)
@@ -304,7 +354,9 @@ def main():
         "vs_baseline": None, "dtype": "f32 local factors + f64 Krylov/Newton/coarse" if args.precision == "mixed"
         else "f64", "data": "synthetic",
         "config": {"workload": describe(w), "unknowns": 2 * r["N"], "method": args.method + "-deluxe",
-                   "krylov": "pcg", "precision": args.precision, "learned_guess": bool(args.learned), "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "krylov": "pcg", "precision": args.precision, "learned_guess": bool(args.learned),
+                   "tensor_cores": bool(args.tc and args.precision == "mixed"),
+                   "chord_newton": bool(args.lag and args.precision == "mixed"), "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "per-step working set > 129 MB L2 (local matrices 0.27 GB f32 / 0.54 GB f64)"},
         "krylov_solves_per_s": ch["newton"] / sec,
         "dof_iterations_per_s": 2 * r["N"] * ch["krylov"] / sec,

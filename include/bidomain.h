@@ -140,7 +140,11 @@ typedef struct {
   /* BD_MIXED only: 1 = the long-K Schur updates of the factorisations run on
    * the tensor cores (tcgen05, TF32 split in hi + lo parts, FP32 accumulation) */
   int use_tensor_cores;
-  int pad_;
+  /* 1 = chord Newton: factorise the Jacobian at the first Newton iterate of a
+   * time step and reuse it for the later iterations of that step (every iterate
+   * is still tested with the exact FP64 residual); 0 = factorise at every
+   * Newton iterate (the paper's setting, the default). */
+  int lag_jacobian;
 } bd_options;
 
 typedef struct {

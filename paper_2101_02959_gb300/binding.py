@@ -58,7 +58,7 @@ class BdOptions(C.Structure):
                [(k, C.c_double) for k in ("ksp_rtol", "ksp_atol", "ksp_dtol", "snes_rtol", "snes_atol",
                                           "snes_stol")] + \
                [(k, C.c_int) for k in ("learned_guess", "mlp_train_steps", "mlp_warmup", "mlp_epochs")] + \
-               [("mlp_lr", C.c_double), ("use_tensor_cores", C.c_int), ("pad_", C.c_int)]
+               [("mlp_lr", C.c_double), ("use_tensor_cores", C.c_int), ("lag_jacobian", C.c_int)]
 
 
 class BdSolveStats(C.Structure):

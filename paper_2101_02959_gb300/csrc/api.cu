@@ -1137,9 +1137,11 @@ int step(bd_handle &h, const bd_stimulus *stim, bd_step_stats *out) {
   for (; k < h.opt.newton_max_it; ++k) {
     if (!std::isfinite(fn2)) { reason = BD_ERR_NAN; break; }
     if (std::sqrt(fn2) <= std::max(h.opt.snes_atol, h.opt.snes_rtol * fn0)) break;
-    linearize(h);
-    int e = h.check_err();
-    if (e) { reason = e; break; }
+    if (k == 0 || !h.opt.lag_jacobian) {
+      linearize(h);
+      int e = h.check_err();
+      if (e) { reason = e; break; }
+    }
     launch_axpby(h.N, -1.0, h.d_ri, 0.0, h.d_fi, s);
     launch_axpby(h.N, -1.0, h.d_re, 0.0, h.d_fe, s);
     bd_solve_stats ls{};
@@ -1408,6 +1410,7 @@ int bd_options_default(bd_options *o) {
   o->snes_rtol = 1e-4; o->snes_atol = 1e-8; o->snes_stol = 1e-8;
   o->learned_guess = 0; o->mlp_train_steps = 200; o->mlp_warmup = 5; o->mlp_epochs = 4; o->mlp_lr = 1e-3;
   o->use_tensor_cores = 0;
+  o->lag_jacobian = 0;
   return BD_OK;
 }
 
@@ -1435,6 +1438,10 @@ int bidomain_setup(const bd_mesh *mesh, const bd_conductivity *cond, const bd_io
       return BD_ERR_CUDA;
     }
     if (h->opt.precision != BD_MIXED) h->opt.use_tensor_cores = 0;
+    if (!dense_configure()) {
+      g_last_error = "dense kernel configuration failed";
+      return BD_ERR_CUDA;
+    }
     setup_handle(*h);
     *out = h.release();
     return BD_OK;

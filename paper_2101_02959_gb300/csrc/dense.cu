@@ -594,6 +594,19 @@ void launch_trsv(int count, int max_n, const MatDesc *d_desc, const int *vec_off
   count_launch();
 }
 
+// Large local problems stage vectors of up to ~25k entries in shared memory.
+bool dense_configure() {
+  const int lim = 200 * 1024;
+  bool ok = true;
+  ok &= cudaFuncSetAttribute(k_trsv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_trsv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_gemv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_gemv_t<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_gemv_t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
+  return ok;
+}
+
 #define BD_INST(T)                                                                                              \
   template void engine_partial_cholesky<T>(const EngineShape &, const MatDesc *, T *, int *, cudaStream_t,    \
                                            T *, ProfHook *, bool);     \

@@ -64,6 +64,8 @@ template <typename T>
 void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s,
                              T *linv, ProfHook *prof = nullptr, bool tc = false);
 
+bool dense_configure();
+
 // tc.cu
 bool tc_configure();
 void launch_rankk_tc(const MatDesc *d_desc, float *base, int mode, int K0, int K1, int max_rows, int max_cols,

@@ -81,7 +81,15 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t phase) {
 
 }  // namespace
 
+__device__ inline void cp_async16(uint32_t dst, const void *src, uint32_t bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes));
+}
+
 // mode 1: rows/cols [e, m), K = [0, e); mode 2: rows [K1, m), cols [K1, e), K = [K0, K1).
+// Pipeline per K chunk i (buffers b = i % 2):
+//   raw[b] (FP32 A and B tiles, cp.async, swizzled) -> split into hi/lo[b] -> 12 MMAs on hi/lo[b]
+// with chunk i+1's loads in flight during the split of chunk i and the MMAs of chunk i
+// running while chunk i+1 is split (mbar[b] guards hi/lo[b] against reuse).
 __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__ desc, float *__restrict__ base,
                                                      int mode, int K0, int K1, int nct, int *__restrict__ err) {
   const MatDesc d = desc[blockIdx.y];
@@ -99,14 +107,14 @@ __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__
   float *A = base + d.off;
 
   extern __shared__ unsigned char smem_raw[];
-  __shared__ uint64_t mbar;
+  __shared__ uint64_t mbar[2];
   __shared__ uint32_t tmem_slot;
-  const uint32_t raw = smem_addr(smem_raw);
-  const uint32_t tiles = (raw + 1023u) & ~1023u;  // 1024-byte aligned: swizzle atoms
-  unsigned char *tile_ptr = smem_raw + (tiles - raw);
-  // four operand copies: A_hi, A_lo, B_hi, B_lo
-  const uint32_t sA_hi = tiles, sA_lo = tiles + kTileBytes, sB_hi = tiles + 2 * kTileBytes,
-                 sB_lo = tiles + 3 * kTileBytes;
+  const uint32_t raw0 = smem_addr(smem_raw);
+  const uint32_t tiles = (raw0 + 1023u) & ~1023u;
+  unsigned char *tp = smem_raw + (tiles - raw0);
+  // layout: raw A/B per buffer (2 x 2 x 16 KB), then hi/lo A/B per buffer (2 x 4 x 16 KB)
+  auto raw_off = [](int b, int op) { return (uint32_t)((b * 2 + op) * kTileBytes); };
+  auto op_off = [](int b, int q) { return (uint32_t)(4 * kTileBytes + (b * 4 + q) * kTileBytes); };
   const int tid = threadIdx.x, warp = tid >> 5;
 
   if (warp == 0) {
@@ -115,71 +123,105 @@ __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[0])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[1])), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
-  const uint32_t bar = smem_addr(&mbar);
   const uint32_t idesc = idesc_tf32();
-
-  // loader mapping: thread -> 16-byte chunk j of rows (tid / 8) + 16 i
   const int j = tid & 7, rr = tid >> 3;
-  uint32_t phase = 0;
-  bool ok = true;
-  for (int kk = kb; kk < ke && ok; kk += kKc) {
+
+  // asynchronous load of chunk starting at kk into raw buffer b (zero fill outside the matrix / K range)
+  auto load = [&](int kk, int b) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int r = rr + 16 * i;
       const int k = kk + 4 * j;
-      const int ra = r0 + r, rb = c0 + r;
-      float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
-      if (k + 3 < ke) {
-        if (ra < d.m) a = *reinterpret_cast<const float4 *>(A + (long long)ra * d.ld + k);
-        if (rb < colend) b = *reinterpret_cast<const float4 *>(A + (long long)rb * d.ld + k);
-      } else {
-        float *pa = &a.x, *pb = &b.x;
-        for (int u = 0; u < 4; ++u) {
-          if (k + u < ke && ra < d.m) pa[u] = A[(long long)ra * d.ld + k + u];
-          if (k + u < ke && rb < colend) pb[u] = A[(long long)rb * d.ld + k + u];
-        }
-      }
-      const float4 ah = make_float4(tf32_round(a.x), tf32_round(a.y), tf32_round(a.z), tf32_round(a.w));
-      const float4 al = make_float4(tf32_round(a.x - ah.x), tf32_round(a.y - ah.y), tf32_round(a.z - ah.z),
-                                    tf32_round(a.w - ah.w));
-      const float4 bh = make_float4(tf32_round(b.x), tf32_round(b.y), tf32_round(b.z), tf32_round(b.w));
-      const float4 bl = make_float4(tf32_round(b.x - bh.x), tf32_round(b.y - bh.y), tf32_round(b.z - bh.z),
-                                    tf32_round(b.w - bh.w));
       const uint32_t off = (uint32_t)r * 128u + (uint32_t)((j ^ (r & 7)) * 16);
-      *reinterpret_cast<float4 *>(tile_ptr + off) = ah;
-      *reinterpret_cast<float4 *>(tile_ptr + kTileBytes + off) = al;
-      *reinterpret_cast<float4 *>(tile_ptr + 2 * kTileBytes + off) = bh;
-      *reinterpret_cast<float4 *>(tile_ptr + 3 * kTileBytes + off) = bl;
+      const int kv = max(0, min(4, ke - k));
+      const int ra = r0 + r, rb = c0 + r;
+      const uint32_t na = (ra < d.m) ? 4u * kv : 0u, nb = (rb < colend) ? 4u * kv : 0u;
+      const float *sa = na ? A + (long long)ra * d.ld + k : A;
+      const float *sb = nb ? A + (long long)rb * d.ld + k : A;
+      cp_async16(tiles + raw_off(b, 0) + off, sa, na);
+      cp_async16(tiles + raw_off(b, 1) + off, sb, nb);
+    }
+    asm volatile("cp.async.commit_group;");
+  };
+
+  const int nchunk = (ke - kb + kKc - 1) / kKc;
+  uint32_t phase[2] = {0u, 0u};
+  int pending[2] = {0, 0};  // an MMA batch is in flight on hi/lo[b]
+  bool ok = true;
+  load(kb, 0);
+  for (int i = 0; i < nchunk && ok; ++i) {
+    const int b = i & 1;
+    if (i + 1 < nchunk) {
+      load(kb + (i + 1) * kKc, b ^ 1);
+      asm volatile("cp.async.wait_group 1;");
+    } else {
+      asm volatile("cp.async.wait_group 0;");
+    }
+    // hi/lo[b] was last read by the MMAs of chunk i - 2
+    bool late = false;
+    if (pending[b]) {
+      late = !mbar_wait(smem_addr(&mbar[b]), phase[b]);
+      phase[b] ^= 1u;
+      pending[b] = 0;
+    }
+    if (__syncthreads_or(late ? 1 : 0)) {
+      ok = false;
+      if (tid == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+      break;
+    }
+    // split raw[b] into TF32 hi and lo parts (same swizzled offsets)
+#pragma unroll
+    for (int i2 = 0; i2 < 8; ++i2) {
+      const int r = rr + 16 * i2;
+      const uint32_t off = (uint32_t)r * 128u + (uint32_t)((j ^ (r & 7)) * 16);
+#pragma unroll
+      for (int op = 0; op < 2; ++op) {
+        const float4 x = *reinterpret_cast<const float4 *>(tp + raw_off(b, op) + off);
+        const float4 hi = make_float4(tf32_round(x.x), tf32_round(x.y), tf32_round(x.z), tf32_round(x.w));
+        const float4 lo = make_float4(tf32_round(x.x - hi.x), tf32_round(x.y - hi.y), tf32_round(x.z - hi.z),
+                                      tf32_round(x.w - hi.w));
+        *reinterpret_cast<float4 *>(tp + op_off(b, 2 * op) + off) = hi;
+        *reinterpret_cast<float4 *>(tp + op_off(b, 2 * op + 1) + off) = lo;
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t ah = tiles + op_off(b, 0), al = tiles + op_off(b, 1);
+      const uint32_t bh = tiles + op_off(b, 2), bl = tiles + op_off(b, 3);
 #pragma unroll
       for (int t = 0; t < kKc / 8; ++t) {  // K = 8 tf32 = 32 bytes per MMA
         const uint32_t adv = (uint32_t)t * 32u;
-        const uint32_t first = (kk == kb && t == 0) ? 0u : 1u;
-        mma_tf32(tmem, sw128_desc(sA_hi + adv), sw128_desc(sB_hi + adv), idesc, first);
-        mma_tf32(tmem, sw128_desc(sA_hi + adv), sw128_desc(sB_lo + adv), idesc, 1u);
-        mma_tf32(tmem, sw128_desc(sA_lo + adv), sw128_desc(sB_hi + adv), idesc, 1u);
+        const uint32_t first = (i == 0 && t == 0) ? 0u : 1u;
+        mma_tf32(tmem, sw128_desc(ah + adv), sw128_desc(bh + adv), idesc, first);
+        mma_tf32(tmem, sw128_desc(ah + adv), sw128_desc(bl + adv), idesc, 1u);
+        mma_tf32(tmem, sw128_desc(al + adv), sw128_desc(bh + adv), idesc, 1u);
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar));
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_addr(&mbar[b])));
     }
-    // the MMAs read the staged tiles: wait before they are overwritten (and before the epilogue);
-    // the timeout decision is made uniform across the CTA by the barrier itself
-    const bool late = __syncthreads_or(!mbar_wait(bar, phase) ? 1 : 0) != 0;
-    phase ^= 1u;
-    if (late) {
-      ok = false;
-      if (tid == 0) atomicOr(err, DEV_ERR_TIMEOUT);
+    pending[b] = 1;
+  }
+  asm volatile("cp.async.wait_group 0;");
+  // drain: wait for every MMA batch still in flight
+  bool late = false;
+  for (int b = 0; b < 2; ++b)
+    if (pending[b]) {
+      late |= !mbar_wait(smem_addr(&mbar[b]), phase[b]);
+      phase[b] ^= 1u;
     }
+  if (__syncthreads_or(late ? 1 : 0)) {
+    ok = false;
+    if (tid == 0) atomicOr(err, DEV_ERR_TIMEOUT);
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
@@ -208,9 +250,6 @@ __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__
         }
       }
     }
-  } else {
-    // an MMA never completed: give it one more bounded wait before the accumulator is released
-    mbar_wait(bar, phase ^ 1u);
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -220,7 +259,7 @@ __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__
   }
 }
 
-static constexpr int kTcSmem = 4 * kTileBytes + 1024;
+static constexpr int kTcSmem = 12 * kTileBytes + 1024;  // 2 x raw A/B + 2 x hi/lo A/B + alignment
 
 bool tc_configure() {
   return cudaFuncSetAttribute(k_rankk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) == cudaSuccess;

@@ -127,13 +127,15 @@ def _oracle_steps(prob, nsteps, method="bddc", krylov="pcg"):
     ("ragged", "bddc", "mixed", 1e-8, 0, "pcg"),
     ("cube8ve", "bddc", "fp64", 1e-9, 0, "gmres"),
     ("ragged", "bddc", "mixed+tc", 1e-8, 1, "pcg"),
+    ("cube8ve", "bddc", "mixed+tc+lag", 1e-8, 1, "pcg"),
 ])
 def test_time_steps_match_oracle(name, method, precision, tol, graphs, krylov):
     prob = oracle_problem(name)
     ref = _oracle_steps(prob, 3, method, krylov)
-    tc = precision.endswith("+tc")
-    s = _solver(name, method=method, krylov=krylov, precision=precision.replace("+tc", ""), ksp_rtol=1e-12,
-                ksp_atol=0.0, snes_rtol=1e-10, snes_atol=1e-16, use_graphs=graphs, use_tensor_cores=int(tc))
+    tc, lag = "+tc" in precision, "+lag" in precision
+    s = _solver(name, method=method, krylov=krylov, precision=precision.split("+")[0], ksp_rtol=1e-12,
+                ksp_atol=0.0, snes_rtol=1e-10, snes_atol=1e-16, use_graphs=graphs, use_tensor_cores=int(tc),
+                lag_jacobian=int(lag))
     ui, ue, w = synth.initial_state(prob.N, 0)
     s.set_state(ui, ue, w, 0.0)
     for n in range(3):
