@@ -124,6 +124,7 @@ def run_gpu(args, w, rank, world):
         s.set_state(*dstate, 0.0)
         for _ in range(args.warmup):
             s.step(synth.STIMULUS)
+        tune = s.autotune() if args.autotune else None
         s.set_state(*dstate, 0.0)
         if profile:
             s.profile(True)
@@ -151,7 +152,7 @@ def run_gpu(args, w, rank, world):
         bad = [st["reason"] for st in stats if st["reason"] != 0]
         used = sum(st.get("guess_used", 0) for st in stats)
         return dict(ms=ms, newton=newton, krylov=kry, launches=launches, prof=prof, clocks=clk, bad=bad,
-                    cond=max(st["cond_max"] for st in stats), final=final, guess_used=used)
+                    cond=max(st["cond_max"] for st in stats), final=final, guess_used=used, tune=tune)
 
     chosen = timed(args.precision, args.method, clocks=ClockSampler(dev), learned=args.learned)
     other = timed(args.precision, args.method, learned=1 - args.learned)
@@ -299,6 +300,7 @@ def main():
     ap.add_argument("--learned", type=int, default=1, help="1: learned initial guess in the chosen solver")
     ap.add_argument("--tc", type=int, default=1, help="1: tensor-core (tcgen05) Schur updates in mixed precision")
     ap.add_argument("--lag", type=int, default=1, help="1: chord Newton (one factorisation per time step), mixed only")
+    ap.add_argument("--autotune", type=int, default=1, help="1: autotune the factorisation after the warm-up")
     ap.add_argument("--cpu-steps", type=int, default=1, help="oracle time steps in the CPU baseline (0: skip)")
     ap.add_argument("--sweep", action="store_true", help="H/h optimality sweep instead of the benchmark")
     ap.add_argument("--sweep-hh", type=int, nargs="*", default=[4, 8, 12, 16])
@@ -369,6 +371,7 @@ def main():
         "e2e": {"value": r["e2e_ms"] / K, "unit": "ms/time step", "h2d_bytes_per_step": nbytes,
                 "d2h_bytes_per_step": nbytes},
         "gpu_launches": ch["launches"],
+        "autotune": ch["tune"],
         "roofline": roof,
         "profiled_pass_ms_per_step": ch["prof_ms"] / K,
         "kernels": {k: dict(v, avg_us=(v["ms"] * 1e3 / v["launches"] if v["launches"] else 0.0))

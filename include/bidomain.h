@@ -252,6 +252,19 @@ int fetidp_operator(bd_handle *h, const double *lambda, double *y, int on_device
  * (SoA).  The u_e correction at the gauge node is 0.  stats may be NULL. */
 int krylov_solve(bd_handle *h, const double *f, double *s, int on_device, bd_solve_stats *stats);
 
+/* ---- autotuner (not in the paper) ----------------------------------------------
+ * Times the whole factorisation sequence of bidomain_linearize (CUDA events,
+ * best of two after a warm-up) at the current Jacobian for every combination of
+ * outer panel width {128, 256, 512}, number of subdomain groups {1, 2, 4}
+ * and, in BD_MIXED, tensor cores on/off; keeps the fastest for the handle and
+ * leaves the Jacobian factorised with it.  Requires bidomain_linearize (or a
+ * step) first.  Results are identical up to rounding for every choice. */
+typedef struct {
+  int outer_panel, groups, tensor_cores, candidates;
+  double best_ms, default_ms;
+} bd_tune_result;
+int bidomain_autotune(bd_handle *h, bd_tune_result *out);
+
 /* ---- learned initial guess (not in the paper) ------------------------------
  * The per-subdomain MLP maps local traces of the last three states (6 per
  * node: v^n, v^n - v^{n-1}, v^{n-1} - v^{n-2}, u_e^n and its two differences,

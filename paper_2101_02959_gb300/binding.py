@@ -32,7 +32,8 @@ EXPORTED = ["bd_plan_create", "bd_plan_sizes", "bd_plan_index_sets", "bd_plan_de
             "bidomain_get_state", "bidomain_step", "bidomain_gating", "bidomain_residual", "bidomain_linearize",
             "schur_apply", "bddc_apply", "fetidp_apply", "fetidp_operator", "krylov_solve", "bidomain_profile",
             "bidomain_profile_read", "bidomain_launch_count", "schur_apply_noalloc", "bidomain_mlp_sizes",
-            "bidomain_mlp_params", "bidomain_mlp_loss_grad", "bidomain_destroy", "bidomain_strerror"]
+            "bidomain_mlp_params", "bidomain_mlp_loss_grad", "bidomain_autotune", "bidomain_destroy",
+            "bidomain_strerror"]
 PROF = dict(rankk=0, panel=1, gemv=2, resid=3)
 
 
@@ -70,6 +71,11 @@ class BdStepStats(C.Structure):
     _fields_ = [("newton_its", C.c_int), ("krylov_its", C.c_int), ("reason", C.c_int), ("pad", C.c_int),
                 ("res0", C.c_double), ("res_final", C.c_double), ("cond_max", C.c_double),
                 ("guess_used", C.c_int), ("pad2", C.c_int), ("res_guess", C.c_double), ("mlp_loss", C.c_double)]
+
+
+class BdTuneResult(C.Structure):
+    _fields_ = [("outer_panel", C.c_int), ("groups", C.c_int), ("tensor_cores", C.c_int), ("candidates", C.c_int),
+                ("best_ms", C.c_double), ("default_ms", C.c_double)]
 
 
 class BdSizes(C.Structure):
@@ -119,6 +125,7 @@ def load(build_if_missing: bool = False):
         "bidomain_mlp_sizes": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
         "bidomain_mlp_params": (I, [P, P, I]),
         "bidomain_mlp_loss_grad": (I, [P, P, P, P, C.POINTER(D), P]),
+        "bidomain_autotune": (I, [P, C.POINTER(BdTuneResult)]),
         "bidomain_destroy": (I, [P]),
         "bidomain_strerror": (C.c_char_p, [I]),
     }
@@ -327,6 +334,11 @@ class Solver:
         out = (C.c_double * 4)()
         _check(self._lib.bidomain_profile_read(self._h, PROF[which], out), "bidomain_profile_read")
         return dict(launches=int(out[0]), ms=out[1], flops=out[2], bytes=out[3])
+
+    def autotune(self):
+        r = BdTuneResult()
+        _check(self._lib.bidomain_autotune(self._h, C.byref(r)), "bidomain_autotune")
+        return {k: getattr(r, k) for k, _ in BdTuneResult._fields_}
 
     def mlp_sizes(self):
         v = [C.c_int() for _ in range(4)]

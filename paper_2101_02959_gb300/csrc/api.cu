@@ -233,6 +233,7 @@ struct bd_handle {
       *d_crhs, *d_rP, *d_rD2;
   double *d_kx, *d_kr, *d_kz, *d_kp, *d_kq, *d_kb;
   KrylovState *d_ks;
+  unsigned int *d_counter = nullptr;
   GmresState *d_gs = nullptr;
   double *d_gV = nullptr, *d_gz = nullptr, *d_gt = nullptr, *d_gpart = nullptr, *d_gh = nullptr;
   double *d_ha, *d_hb;
@@ -250,6 +251,8 @@ struct bd_handle {
   int *d_node_ptr = nullptr, *d_node_ent = nullptr;
   double *d_uh1i, *d_uh1e, *d_uh2i, *d_uh2e, *d_gi, *d_ge;
   double rtol_scale = 1.0;
+  // factorisation tuning (bidomain_autotune): outer panel width, batch groups, tensor cores
+  int tune_ob = 256, tune_groups = 1;
   cudaGraphExec_t pcg_exec[2] = {nullptr, nullptr};  // captured PCG chunk per method
   size_t pcg_nodes[2] = {0, 0};
   double gemv_schur_flops = 0, gemv_schur_bytes = 0, gemv_local_flops = 0, gemv_local_bytes = 0;
@@ -780,6 +783,8 @@ void setup_handle(bd_handle &h) {
   double **kv[] = {&h.d_kx, &h.d_kr, &h.d_kz, &h.d_kp, &h.d_kq, &h.d_kb};
   for (double **v : kv) *v = m.alloc<double>(kn);
   h.d_ks = m.alloc<KrylovState>(1);
+  h.d_counter = m.alloc<unsigned int>(1);
+  ck(cudaMemsetAsync(h.d_counter, 0, sizeof(unsigned int), s), "memset");
   if (h.opt.krylov == BD_GMRES) {
     const int mr = std::min(std::max(h.opt.gmres_restart, 1), kMaxRestart);
     h.opt.gmres_restart = mr;
@@ -791,8 +796,8 @@ void setup_handle(bd_handle &h) {
     h.d_gh = m.alloc<double>(3 * (kMaxRestart + 1));
   }
   h.hist_cap = std::max(1, h.opt.ksp_max_it) + 2;
-  h.d_ha = m.alloc<double>(h.hist_cap);
-  h.d_hb = m.alloc<double>(h.hist_cap);
+  h.d_ha = m.alloc<double>(2 * (size_t)h.hist_cap);  // alphas then betas
+  h.d_hb = h.d_ha + h.hist_cap;
   const int io = std::max({2 * N, h.nif, h.nlam});
   for (int i = 0; i < 6; ++i) h.d_io[i] = m.alloc<double>(io);
   if (h.opt.learned_guess) setup_mlp(h);
@@ -802,13 +807,33 @@ void setup_handle(bd_handle &h) {
 // ---------------------------------------------------------------------------
 // Jacobian: local matrices, factorisations, Schur complements, deluxe, coarse
 // ---------------------------------------------------------------------------
+// The subdomain batch is factorised in tune_groups consecutive groups (smaller
+// groups keep their trailing matrices in L2), with outer panels of tune_ob columns.
+template <class T>
+void run_engine_groups(bd_handle &h, const EngineShape &all, const MatDesc *d_desc, T *base, T *linv) {
+  const int G = std::max(1, std::min(h.tune_groups, all.count));
+  const int per = (all.count + G - 1) / G;
+  for (int a = 0; a < all.count; a += per) {
+    const int b = std::min(all.count, a + per);
+    EngineShape g{b - a, 0, 0, {}, {}};
+    g.ob = h.tune_ob;
+    for (int q = a; q < b; ++q) {
+      g.m.push_back(all.m[q]);
+      g.e.push_back(all.e[q]);
+      g.max_m = std::max(g.max_m, all.m[q]);
+      g.max_e = std::max(g.max_e, all.e[q]);
+    }
+    engine_partial_cholesky<T>(g, d_desc + a, base, h.d_err, h.s, linv, &h.prof, h.opt.use_tensor_cores != 0);
+  }
+}
+
 template <class T>
 void linearize_t(bd_handle &h, Dense<T> &D) {
   cudaStream_t s = h.s;
   ck(cudaMemsetAsync(D.K, 0, sizeof(T) * h.K_el, s), "memset K");
   launch_assemble_local<T>(h.nq, h.d_q_sub, h.d_q_loc, h.d_q_node, h.d_q_nbr, h.d_q_stencil, h.d_q_mass, h.d_factor,
                            h.tau, h.d_Kdesc, D.K, s);
-  engine_partial_cholesky<T>(h.shK, h.d_Kdesc, D.K, h.d_err, s, D.Linv, &h.prof, h.opt.use_tensor_cores != 0);
+  run_engine_groups<T>(h, h.shK, h.d_Kdesc, D.K, D.Linv);
   launch_copy<T, T>(h.cp_sorig.n, h.cp_sorig.max_elems, h.cp_sorig.d, D.K, D.Sorig, s);
   long long max_a = 0;
   for (int j = 0; j < h.nsub; ++j) max_a = std::max(max_a, (long long)h.shA.m[j] * h.shA.m[j]);
@@ -816,7 +841,7 @@ void linearize_t(bd_handle &h, Dense<T> &D) {
                       h.d_tl_row, h.d_tl_val, s);
   launch_copy<T, T>(h.cp_sdd.n, h.cp_sdd.max_elems, h.cp_sdd.d, D.Aug, D.SDD, s);
   launch_copy<T, T>(h.cp_blk.n, h.cp_blk.max_elems, h.cp_blk.d, D.Aug, D.Blk, s);
-  engine_partial_cholesky<T>(h.shA, h.d_Adesc, D.Aug, h.d_err, s, D.Linv, &h.prof, h.opt.use_tensor_cores != 0);
+  run_engine_groups<T>(h, h.shA, h.d_Adesc, D.Aug, D.Linv);
   launch_copy<T, T>(h.cp_zx.n, h.cp_zx.max_elems, h.cp_zx.d, D.Aug, D.Z, s);
   launch_class_aug<T>(h.ncls, h.max_nc, h.d_cls, h.d_pairs, D.Blk, h.d_Cdesc, D.CA, s);
   engine_partial_cholesky<T>(h.shC, h.d_Cdesc, D.CA, h.d_err, s, D.Linv);
@@ -910,12 +935,10 @@ int pcg(bd_handle &h, int n, const double *b, double *x, Op A, Pc M, bd_solve_st
   auto body = [&]() {
     for (int c = 0; c < kChunk; ++c) {
       A(h.d_kp, h.d_kq, done);
-      launch_dot2(n, h.d_kp, h.d_kq, nullptr, nullptr, h.d_partial, h.d_scal, done, s);
-      launch_pcg_alpha(h.d_ks, h.d_scal, h.d_ha, s);
+      launch_pcg_dot_step(n, 0, h.d_kp, h.d_kq, nullptr, nullptr, h.d_partial, h.d_counter, h.d_ks, h.d_ha, s);
       launch_pcg_xr(n, h.d_ks, h.d_kp, h.d_kq, x, h.d_kr, s);
       M(h.d_kr, h.d_kz, done);
-      launch_dot2(n, h.d_kr, h.d_kz, h.d_kz, h.d_kz, h.d_partial, h.d_scal, done, s);
-      launch_pcg_beta(h.d_ks, h.d_scal, h.d_hb, s);
+      launch_pcg_dot_step(n, 1, h.d_kr, h.d_kz, h.d_kz, h.d_kz, h.d_partial, h.d_counter, h.d_ks, h.d_ha, s);
       launch_pcg_p(n, h.d_ks, h.d_kz, h.d_kp, s);
     }
   };
@@ -1645,6 +1668,67 @@ int bidomain_mlp_loss_grad(bd_handle *h, const float *X, const float *T, const f
     if (grad) ck(cudaMemcpyAsync(grad, M.g, sizeof(float) * M.n_params, cudaMemcpyDeviceToHost, h->s), "grad");
     ck(cudaStreamSynchronize(h->s), "sync");
     return BD_OK;
+  });
+}
+
+int bidomain_autotune(bd_handle *h, bd_tune_result *out) {
+  if (!h) return BD_ERR_ARG;
+  if (!h->linearized) return BD_ERR_STATE;
+  return guard(h, [&] {
+    cudaStream_t s = h->s;
+    cudaEvent_t e0, e1;
+    ck(cudaEventCreate(&e0), "event");
+    ck(cudaEventCreate(&e1), "event");
+    const bool prof_on = h->prof.on;
+    h->prof.on = false;
+    const int tc0 = h->opt.use_tensor_cores, ob0 = h->tune_ob, g0 = h->tune_groups;
+    auto time_it = [&]() {
+      linearize(*h);  // warm
+      float best = 1e30f;
+      for (int r = 0; r < 2; ++r) {
+        ck(cudaEventRecord(e0, s), "event");
+        linearize(*h);
+        ck(cudaEventRecord(e1, s), "event");
+        ck(cudaEventSynchronize(e1), "event");
+        float ms = 0.f;
+        ck(cudaEventElapsedTime(&ms, e0, e1), "event");
+        best = std::min(best, ms);
+      }
+      return best;
+    };
+    const float base_ms = time_it();
+    float best_ms = base_ms;
+    int best_ob = ob0, best_g = g0, best_tc = tc0, n = 0;
+    const int tcs[2] = {0, 1};
+    for (int tc : tcs) {
+      if (tc && !h->mixed()) continue;
+      for (int ob : {128, 256, 512})
+        for (int g : {1, 2, 4}) {
+          h->opt.use_tensor_cores = tc;
+          h->tune_ob = ob;
+          h->tune_groups = g;
+          const float ms = time_it();
+          ++n;
+          if (ms < best_ms) { best_ms = ms; best_ob = ob; best_g = g; best_tc = tc; }
+        }
+    }
+    h->opt.use_tensor_cores = best_tc;
+    h->tune_ob = best_ob;
+    h->tune_groups = best_g;
+    linearize(*h);
+    h->prof.on = prof_on;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    int st = h->check_err();
+    if (out) {
+      out->outer_panel = best_ob;
+      out->groups = best_g;
+      out->tensor_cores = best_tc;
+      out->candidates = n;
+      out->best_ms = best_ms;
+      out->default_ms = base_ms;
+    }
+    return st;
   });
 }
 

@@ -421,6 +421,59 @@ __global__ void k_pcg_p(int n, const KrylovState *__restrict__ ks, const double 
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) p[t] = z[t] + b * p[t];
 }
 
+// Fused PCG reductions: every block writes its partial sums; the last block to
+// finish (counter) adds the partials in block order (deterministic) and applies
+// the scalar recurrence.  which = 0: p.q -> alpha; which = 1: (r.z, z.z) -> beta and
+// the convergence test.
+__global__ void k_pcg_dot_step(int n, int which, const double *__restrict__ a0, const double *__restrict__ b0,
+                               const double *__restrict__ a1, const double *__restrict__ b1,
+                               double *__restrict__ partial, unsigned int *__restrict__ counter,
+                               KrylovState *__restrict__ ks, double *__restrict__ hist) {
+  if (ks->done) return;
+  __shared__ double sh[32];
+  __shared__ bool last;
+  double s0 = 0.0, s1 = 0.0;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+    s0 += a0[x] * b0[x];
+    if (a1) s1 += a1[x] * b1[x];
+  }
+  s0 = block_sum(s0, sh);
+  s1 = block_sum(s1, sh);
+  if (threadIdx.x == 0) {
+    partial[2 * blockIdx.x] = s0;
+    partial[2 * blockIdx.x + 1] = s1;
+    __threadfence();
+    last = atomicAdd(counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double t0 = 0.0, t1 = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    t0 += ((volatile double *)partial)[2 * b];
+    t1 += ((volatile double *)partial)[2 * b + 1];
+  }
+  t0 = block_sum(t0, sh);
+  t1 = block_sum(t1, sh);
+  if (threadIdx.x != 0) return;
+  *counter = 0u;
+  if (which == 0) {
+    ks->alpha = ks->rz / t0;
+    if (ks->it < ks->hist_cap) hist[ks->it] = ks->alpha;
+    return;
+  }
+  ks->it += 1;
+  const double zn = sqrt(fmax(t1, 0.0));
+  ks->zn = zn;
+  if (!isfinite(zn)) { ks->done = 1; ks->reason = -6; return; }
+  if (zn <= ks->tol) { ks->done = 1; ks->reason = 0; return; }
+  if (zn > ks->dtol * ks->zn0) { ks->done = 1; ks->reason = -4; return; }
+  if (ks->it >= ks->maxit) { ks->done = 1; ks->reason = -3; return; }
+  ks->beta = t0 / ks->rz;
+  if (ks->it - 1 < ks->hist_cap) hist[ks->hist_cap + ks->it - 1] = ks->beta;
+  ks->rz = t0;
+}
+
 // dots with an early exit (Krylov loop): partial sums then a fixed-order finalize
 __global__ void k_dot2_done(int n, const double *__restrict__ a0, const double *__restrict__ b0,
                             const double *__restrict__ a1, const double *__restrict__ b1,
@@ -625,6 +678,12 @@ void launch_pcg_p(int n, const KrylovState *ks, const double *z, double *p, cuda
   k_pcg_p<<<std::max(1, std::min(ceil_div(n, 256), kRedBlocks)), 256, 0, s>>>(n, ks, z, p);
   count_launch();
 }
+void launch_pcg_dot_step(int n, int which, const double *a0, const double *b0, const double *a1, const double *b1,
+                        double *partial, unsigned int *counter, KrylovState *ks, double *hist, cudaStream_t s) {
+  k_pcg_dot_step<<<kRedBlocks, 256, 0, s>>>(n, which, a0, b0, a1, b1, partial, counter, ks, hist);
+  count_launch();
+}
+
 void launch_dot2(int n, const double *a0, const double *b0, const double *a1, const double *b1, double *partial,
                  double *out, const int *done, cudaStream_t s) {
   k_dot2_done<<<kRedBlocks, 256, 0, s>>>(n, a0, b0, a1, b1, partial, done);

@@ -77,6 +77,9 @@ void launch_pcg_beta(KrylovState *ks, const double *dots, double *hb, cudaStream
 void launch_pcg_xr(int n, const KrylovState *ks, const double *p, const double *q, double *x, double *r,
                    cudaStream_t s);
 void launch_pcg_p(int n, const KrylovState *ks, const double *z, double *p, cudaStream_t s);
+// hist: alphas at [0, cap), betas at [cap, 2 cap)
+void launch_pcg_dot_step(int n, int which, const double *a0, const double *b0, const double *a1, const double *b1,
+                         double *partial, unsigned int *counter, KrylovState *ks, double *hist, cudaStream_t s);
 void launch_dot2(int n, const double *a0, const double *b0, const double *a1, const double *b1, double *partial,
                  double *out, const int *done, cudaStream_t s);
 

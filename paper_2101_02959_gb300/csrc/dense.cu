@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(128) k_trsm(const MatDesc *__restrict__ desc, 
 // mode 2 (outer): rows [K1, m),   cols [K1, e),            K = [K0, K1)
 // mode 1 (final): rows [e, m),    cols [e, m),             K = [0, e)
 // C[r][c] -= sum_k A[r][k] A[c][k]; 64x64 tiles, 256 threads, 4x4 per thread.
-constexpr int kTB = 64, kKC = 32, kOB = 256;
+constexpr int kTB = 64, kKC = 32;
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_rankk(const MatDesc *__restrict__ desc, T *__restrict__ base, int mode,
@@ -338,8 +338,9 @@ template <typename T>
 void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s,
                              T *linv, ProfHook *prof, bool tc) {
   if (sh.count == 0) return;
-  for (int K0 = 0; K0 < sh.max_e; K0 += kOB) {
-    const int K1 = K0 + kOB;
+  const int ob = std::max(kNB, (sh.ob / kNB) * kNB);
+  for (int K0 = 0; K0 < sh.max_e; K0 += ob) {
+    const int K1 = K0 + ob;
     for (int k0 = K0; k0 < std::min(K1, sh.max_e); k0 += kNB) {
       int max_below = 0, max_cols = 0;
       double fl_panel = 0.0, fl_upd = 0.0, by_upd = 0.0;
@@ -378,8 +379,8 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
       max_rows = std::max(max_rows, sh.m[b] - K1);
       max_cols = std::max(max_cols, sh.e[b] - K1);
       const double ent = trapezoid(K1, sh.e[b], sh.m[b]);
-      fl += 2.0 * kOB * ent;
-      by += sizeof(T) * (2.0 * ent + (double)kOB * (sh.m[b] - K1));
+      fl += 2.0 * ob * ent;
+      by += sizeof(T) * (2.0 * ent + (double)ob * (sh.m[b] - K1));
     }
     if (max_rows > 0 && max_cols > 0) {
       if (prof) prof->begin(PROF_RANKK, s);
@@ -414,14 +415,17 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
 }
 
 // ---- batched GEMV ------------------------------------------------------------
-// One CTA (8 warps) per (task, block of 64 rows); x staged in shared memory.
+// One CTA (8 warps) per (task, block of kGemvRows rows): each warp owns two rows
+// with independent accumulators; x is staged in shared memory.
+constexpr int kGemvRows = 16;
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemv(const GemvDesc *__restrict__ tasks, const T *__restrict__ A,
                                               const double *__restrict__ x, const int *__restrict__ xidx,
                                               double *__restrict__ y, double alpha, const int *__restrict__ done) {
   if (done && *done) return;
   const GemvDesc t = tasks[blockIdx.y];
-  const int rbeg = blockIdx.x * 64;
+  const int rbeg = blockIdx.x * kGemvRows;
   if (rbeg >= t.rows) return;
   extern __shared__ unsigned char smem_raw[];
   T *xs = reinterpret_cast<T *>(smem_raw);
@@ -429,22 +433,32 @@ __global__ void __launch_bounds__(256) k_gemv(const GemvDesc *__restrict__ tasks
     xs[c] = (T)((t.flags & 1) ? x[xidx[t.x_off + c]] : x[t.x_off + c]);
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int rend = min(t.rows, rbeg + 64);
-  for (int r = rbeg + wid; r < rend; r += 8) {
-    const T *row = A + t.a_off + (long long)r * t.ld;
-    T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-    int c = lane;
-    for (; c + 96 < t.cols; c += 128) {
-      a0 += row[c] * xs[c];
-      a1 += row[c + 32] * xs[c + 32];
-      a2 += row[c + 64] * xs[c + 64];
-      a3 += row[c + 96] * xs[c + 96];
+  const int r0 = rbeg + wid, r1 = rbeg + wid + 8;
+  const bool v0 = r0 < t.rows, v1 = r1 < t.rows;
+  const T *row0 = A + t.a_off + (long long)(v0 ? r0 : rbeg) * t.ld;
+  const T *row1 = A + t.a_off + (long long)(v1 ? r1 : rbeg) * t.ld;
+  T a0 = T(0), a1 = T(0), b0 = T(0), b1 = T(0);
+  int c = lane;
+  for (; c + 32 < t.cols; c += 64) {
+    const T x0 = xs[c], x1 = xs[c + 32];
+    a0 += row0[c] * x0;
+    a1 += row0[c + 32] * x1;
+    b0 += row1[c] * x0;
+    b1 += row1[c + 32] * x1;
+  }
+  if (c < t.cols) {
+    a0 += row0[c] * xs[c];
+    b0 += row1[c] * xs[c];
+  }
+  const T s0 = warp_sum(a0 + a1), s1 = warp_sum(b0 + b1);
+  if (lane == 0) {
+    if (v0) {
+      const double v = alpha * (double)s0;
+      y[t.y_off + r0] = (t.flags & 2) ? y[t.y_off + r0] + v : v;
     }
-    for (; c < t.cols; c += 32) a0 += row[c] * xs[c];
-    const T acc = warp_sum((a0 + a1) + (a2 + a3));
-    if (lane == 0) {
-      const double v = alpha * (double)acc;
-      y[t.y_off + r] = (t.flags & 2) ? y[t.y_off + r] + v : v;
+    if (v1) {
+      const double v = alpha * (double)s1;
+      y[t.y_off + r1] = (t.flags & 2) ? y[t.y_off + r1] + v : v;
     }
   }
 }
@@ -481,7 +495,7 @@ template <typename T>
 void launch_gemv(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks, const T *A, const double *x,
                  const int *xidx, double *y, double alpha, const int *done, cudaStream_t s) {
   if (ntasks == 0 || max_rows == 0) return;
-  dim3 g(ceil_div(max_rows, 64), ntasks);
+  dim3 g(ceil_div(max_rows, kGemvRows), ntasks);
   const size_t sm = sizeof(T) * (size_t)std::max(1, max_cols);
   k_gemv<T><<<g, 256, sm, s>>>(d_tasks, A, x, xidx, y, alpha, done);
   count_launch();

@@ -57,6 +57,7 @@ struct EngineShape {
   int count;
   int max_e, max_m;
   std::vector<int> m, e;  // host copies for per-step grid sizes
+  int ob = 256;           // outer panel width (columns per trailing long-K update)
 };
 // linv: scratch of count * kNB * kNB elements (the inverse of each diagonal block).
 // tc: FP32 only, run the long-K updates on the tensor cores (tc.cu).

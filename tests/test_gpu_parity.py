@@ -217,6 +217,23 @@ def test_tensor_core_schur_matches_fp64():
     assert _rel(out["tc"][0], out["simt"][0]) < 2e-5
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotune_keeps_results(precision):
+    """The autotuner only changes blocking, grouping and the engine's GEMM path."""
+    prob = oracle_problem("ragged")
+    ui, ue, w = _state(prob)
+    wn = ionic.gating_step(ui - ue, w, prob.tau, prob.p)
+    s = _solver("ragged", precision=precision, use_tensor_cores=int(precision == "mixed"))
+    s.linearize(ui, ue, wn)
+    x = synth.random_vector(prob.dofs.n_iface, 9)
+    y0 = s.schur_apply(x)
+    r = s.autotune()
+    assert r["candidates"] >= 9 and r["best_ms"] <= r["default_ms"]
+    assert r["outer_panel"] in (128, 256, 512) and r["groups"] in (1, 2, 4)
+    y1 = s.schur_apply(x)
+    assert _rel(y1, y0) < (1e-12 if precision == "fp64" else 2e-5)
+
+
 def test_not_spd_is_reported():
     """tau far above 0.37 ms with a depolarised state: Kc < 0, a pivot fails, status says so."""
     from paper_2101_02959_gb300 import binding
