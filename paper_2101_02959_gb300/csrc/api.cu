@@ -63,7 +63,9 @@ inline long long pad32(long long n) { return (n + 31) & ~31LL; }
 template <class T>
 struct Dense {
   T *K = nullptr, *Aug = nullptr, *Sorig = nullptr, *Z = nullptr, *SDD = nullptr, *Blk = nullptr, *CA = nullptr,
-    *Sinv = nullptr, *Dd = nullptr, *Linv = nullptr;
+    *Sinv = nullptr, *Dd = nullptr, *Linv = nullptr, *LdK = nullptr;  // Linv: block store scratch; LdK: K's
+  // coarse problem in the local precision: augmented matrix, its block store, S_PiPi^-1
+  T *Co = nullptr, *LdCo = nullptr, *CoInv = nullptr;
 };
 
 struct GemvSet {
@@ -213,6 +215,7 @@ struct bd_handle {
   EngineShape shK, shA, shC, shCo;
   MatDesc *d_Kdesc, *d_Adesc, *d_Cdesc, *d_Codesc;
   long long K_el = 0, A_el = 0, So_el = 0, Z_el = 0, SDD_el = 0, Blk_el = 0, CA_el = 0, Sinv_el = 0, Dd_el = 0;
+  int K_blk = 0, A_blk = 0, C_blk = 0;  // slots of the diagonal-block stores
   int ld_co = 0;
   GemvSet gv_schur, gv_local, gv_psit, gv_coarse, gv_sdd, gv_lgi, gv_lgit, gv_drest, gv_dext;
   GemmTask *d_gemm = nullptr;
@@ -240,7 +243,7 @@ struct bd_handle {
   int hist_cap = 0;
   Dense<float> df;
   Dense<double> dd;
-  double *d_Co, *d_CoInv, *d_linv_co;
+
   bool linearized = false;
   std::string last_error;
   Profiler prof;
@@ -512,10 +515,12 @@ void setup_handle(bd_handle &h) {
   h.shA = EngineShape{S, 0, 0, {}, {}};
   for (int j = 0; j < S; ++j) {
     const int n = h.nI[j] + h.nG[j];
-    kd[j] = MatDesc{h.K_el, pad8(n), n, h.nI[j], 0};
+    kd[j] = MatDesc{h.K_el, pad8(n), n, h.nI[j], h.K_blk};
+    h.K_blk += ceil_div(h.nI[j], kNB);
     h.K_el += pad32((long long)pad8(n) * n);
     const int ma = 2 * h.nD[j] + h.nP[j];
-    ad[j] = MatDesc{h.A_el, pad8(ma), ma, h.nD[j], 0};
+    ad[j] = MatDesc{h.A_el, pad8(ma), ma, h.nD[j], h.A_blk};
+    h.A_blk += ceil_div(h.nD[j], kNB);
     h.A_el += pad32((long long)pad8(ma) * ma);
     ldg[j] = pad8(h.nG[j]);
     so_off[j] = h.So_el;
@@ -589,7 +594,8 @@ void setup_handle(bd_handle &h) {
         lam_off += n;
       }
     const int mc = 2 * n;
-    MatDesc md{h.CA_el, pad8(mc), mc, n, 0};
+    MatDesc md{h.CA_el, pad8(mc), mc, n, h.C_blk};
+    h.C_blk += ceil_div(n, kNB);
     h.CA_el += pad32((long long)pad8(mc) * mc);
     cdesc.push_back(md);
     h.shC.m.push_back(mc); h.shC.e.push_back(n);
@@ -685,9 +691,7 @@ void setup_handle(bd_handle &h) {
     for (auto &l : lists) { for (long long v : l) src.push_back(v); ptr.push_back((int)src.size()); }
     h.d_co_ptr = m.upload(ptr, s);
     h.d_co_src = m.upload(src, s);
-    h.d_Co = m.alloc<double>((size_t)h.ld_co * 2 * np);
-    h.d_CoInv = m.alloc<double>((size_t)np * np);
-    h.d_linv_co = m.alloc<double>(kNB * kNB);
+
   }
   // ---- GEMV and copy task sets
   auto gset = [&](const std::vector<GemvDesc> &v) {
@@ -753,6 +757,16 @@ void setup_handle(bd_handle &h) {
     c.dst_off = 0; c.dst_ld = h.np;
     h.cp_coinv = cset({c});
   }
+  {  // the dense kernels stage vectors and tiles in shared memory
+    const size_t el = h.mixed() ? sizeof(float) : sizeof(double);
+    size_t need = el * (6 * 32 * 33 + (size_t)h.shK.max_e + 4);
+    for (const GemvSet *g : {&h.gv_schur, &h.gv_local, &h.gv_psit, &h.gv_coarse, &h.gv_sdd, &h.gv_lgi, &h.gv_lgit,
+                             &h.gv_drest, &h.gv_dext})
+      need = std::max(need, el * (size_t)std::max(g->max_rows, g->max_cols));
+    if (need > dense_smem_limit())
+      throw Status(BD_ERR_ARG, "local problem too large for the shared-memory staging of the dense kernels (" +
+                                   std::to_string(need) + " bytes); use more subdomains");
+  }
   // ---- dense buffers
   auto alloc_dense = [&](auto &D) {
     using T = std::remove_pointer_t<decltype(D.K)>;
@@ -765,7 +779,11 @@ void setup_handle(bd_handle &h) {
     D.CA = m.alloc<T>(h.CA_el);
     D.Sinv = m.alloc<T>(h.Sinv_el);
     D.Dd = m.alloc<T>(h.Dd_el);
-    D.Linv = m.alloc<T>((size_t)std::max({h.nsub, h.ncls, 1}) * kNB * kNB);
+    D.Linv = m.alloc<T>((size_t)std::max({h.A_blk, h.C_blk, 1}) * kNB * kNB);
+    D.LdK = m.alloc<T>((size_t)std::max(h.K_blk, 1) * kNB * kNB);
+    D.Co = m.alloc<T>((size_t)h.ld_co * 2 * h.np);
+    D.LdCo = m.alloc<T>((size_t)std::max(1, ceil_div(h.np, kNB)) * kNB * kNB);
+    D.CoInv = m.alloc<T>((size_t)h.np * h.np);
   };
   if (h.mixed()) alloc_dense(h.df);
   else alloc_dense(h.dd);
@@ -833,7 +851,7 @@ void linearize_t(bd_handle &h, Dense<T> &D) {
   ck(cudaMemsetAsync(D.K, 0, sizeof(T) * h.K_el, s), "memset K");
   launch_assemble_local<T>(h.nq, h.d_q_sub, h.d_q_loc, h.d_q_node, h.d_q_nbr, h.d_q_stencil, h.d_q_mass, h.d_factor,
                            h.tau, h.d_Kdesc, D.K, s);
-  run_engine_groups<T>(h, h.shK, h.d_Kdesc, D.K, D.Linv);
+  run_engine_groups<T>(h, h.shK, h.d_Kdesc, D.K, D.LdK);
   launch_copy<T, T>(h.cp_sorig.n, h.cp_sorig.max_elems, h.cp_sorig.d, D.K, D.Sorig, s);
   long long max_a = 0;
   for (int j = 0; j < h.nsub; ++j) max_a = std::max(max_a, (long long)h.shA.m[j] * h.shA.m[j]);
@@ -847,9 +865,9 @@ void linearize_t(bd_handle &h, Dense<T> &D) {
   engine_partial_cholesky<T>(h.shC, h.d_Cdesc, D.CA, h.d_err, s, D.Linv);
   launch_copy<T, T>(h.cp_sinv.n, h.cp_sinv.max_elems, h.cp_sinv.d, D.CA, D.Sinv, s);
   launch_small_gemm<T>(h.n_gemm, h.max_nc, h.d_gemm, D.Sinv, D.Blk, D.Dd, s);
-  launch_coarse_aug<T>(h.np, h.gauge_primal, h.d_co_ptr, h.d_co_src, D.Aug, h.d_Co, h.ld_co, s);
-  engine_partial_cholesky<double>(h.shCo, h.d_Codesc, h.d_Co, h.d_err, s, h.d_linv_co);
-  launch_copy<double, double>(h.cp_coinv.n, h.cp_coinv.max_elems, h.cp_coinv.d, h.d_Co, h.d_CoInv, s);
+  launch_coarse_aug<T>(h.np, h.gauge_primal, h.d_co_ptr, h.d_co_src, D.Aug, D.Co, h.ld_co, s);
+  engine_partial_cholesky<T>(h.shCo, h.d_Codesc, D.Co, h.d_err, s, D.LdCo);
+  launch_copy<T, T>(h.cp_coinv.n, h.cp_coinv.max_elems, h.cp_coinv.d, D.Co, D.CoInv, s);
 }
 
 void linearize(bd_handle &h) {
@@ -876,7 +894,7 @@ void st_inv_t(bd_handle &h, Dense<T> &D, const double *rP, const double *rD, con
                  1.0, done, h.s);
   h.prof.end(PROF_GEMV, h.s, h.gemv_local_flops, h.gemv_local_bytes * sizeof(T));
   launch_gather_sum(h.np, h.d_pl_ptr, h.d_pl_idx, h.d_ydc + h.nD_tot, h.d_crhs, h.gauge_primal, -1.0, rP, done, h.s);
-  launch_gemv<double>(1, h.np, h.np, h.gv_coarse.d, h.d_CoInv, h.d_crhs, nullptr, h.d_zbar, 1.0, done, h.s);
+  launch_gemv<T>(1, h.np, h.np, h.gv_coarse.d, D.CoInv, h.d_crhs, nullptr, h.d_zbar, 1.0, done, h.s);
   launch_gemv_t<T>(h.gv_psit.n, h.gv_psit.max_rows, h.gv_psit.max_cols, h.gv_psit.d, D.Z, h.d_zbar, h.d_prim_x,
                    h.d_ydc, -1.0, done, h.s);
 }
@@ -1047,7 +1065,7 @@ int solve_t(bd_handle &h, Dense<T> &D, const double *fi, const double *fe, doubl
   cudaStream_t s = h.s;
   // interior data: y_I = L_II^-1 f_I
   launch_gather_pairs(h.nint_nodes, h.d_int_node, fi, fe, h.d_fI, 1.0, nullptr, s);
-  launch_trsv<T>(h.nsub, h.shK.max_e, h.d_Kdesc, h.d_vec_off_I, D.K, h.d_fI, h.d_yI, false, s);
+  launch_trsv<T>(h.nsub, h.shK.max_e, h.d_Kdesc, h.d_vec_off_I, D.K, D.LdK, h.d_fI, h.d_yI, false, s);
   launch_gemv<T>(h.gv_lgi.n, h.gv_lgi.max_rows, h.gv_lgi.max_cols, h.gv_lgi.d, D.K, h.d_yI, nullptr, h.d_yloc, 1.0,
                  nullptr, s);
   launch_gather_pairs(h.nif / 2, h.d_iface_node, fi, fe, h.d_fG, 1.0, nullptr, s);
@@ -1081,7 +1099,7 @@ int solve_t(bd_handle &h, Dense<T> &D, const double *fi, const double *fe, doubl
   // interior recovery: u_I = L_II^-T (y_I - L_GI^T u_G)
   launch_gemv_t<T>(h.gv_lgit.n, h.gv_lgit.max_rows, h.gv_lgit.max_cols, h.gv_lgit.d, D.K, h.d_uG, h.d_R, h.d_yI, -1.0,
                    nullptr, s);
-  launch_trsv<T>(h.nsub, h.shK.max_e, h.d_Kdesc, h.d_vec_off_I, D.K, h.d_yI, h.d_fI, true, s);
+  launch_trsv<T>(h.nsub, h.shK.max_e, h.d_Kdesc, h.d_vec_off_I, D.K, D.LdK, h.d_yI, h.d_fI, true, s);
   launch_scatter_pairs(h.nint_nodes, h.d_int_node, h.d_fI, si, se, s);
   launch_scatter_pairs(h.nif / 2, h.d_iface_node, h.d_uG, si, se, s);
   ck(cudaGetLastError(), "solve");
@@ -1157,13 +1175,16 @@ int step(bd_handle &h, const bd_stimulus *stim, bd_step_stats *out) {
   }
   int reason = BD_OK;
   int k = 0;
+  bool refresh = true;  // form J at the current iterate (always without lagging)
   for (; k < h.opt.newton_max_it; ++k) {
     if (!std::isfinite(fn2)) { reason = BD_ERR_NAN; break; }
     if (std::sqrt(fn2) <= std::max(h.opt.snes_atol, h.opt.snes_rtol * fn0)) break;
-    if (k == 0 || !h.opt.lag_jacobian) {
+    const bool fresh = refresh || !h.opt.lag_jacobian;
+    if (fresh) {
       linearize(h);
       int e = h.check_err();
       if (e) { reason = e; break; }
+      refresh = false;
     }
     launch_axpby(h.N, -1.0, h.d_ri, 0.0, h.d_fi, s);
     launch_axpby(h.N, -1.0, h.d_re, 0.0, h.d_fe, s);
@@ -1196,6 +1217,10 @@ int step(bd_handle &h, const bd_stimulus *stim, bd_step_stats *out) {
         f_prev = fl;
         lam = std::max(std::min(lt, 0.5 * lam), 0.1 * lam);
       }
+    }
+    if (!ok && !fresh) {  // a lagged Jacobian gave no descent: keep the iterate, form J here
+      refresh = true;
+      continue;
     }
     std::swap(h.d_ui, h.d_uit); std::swap(h.d_ue, h.d_uet);
     std::swap(h.d_ri, h.d_rit); std::swap(h.d_re, h.d_ret); std::swap(h.d_factor, h.d_factort);

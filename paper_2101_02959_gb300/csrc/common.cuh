@@ -39,7 +39,7 @@ struct MatDesc {
   int ld;         // leading dimension (elements)
   int m;          // order
   int e;          // columns to eliminate (partial Cholesky) / rows used
-  int pad;
+  int dblk;       // first slot of this matrix in the block store of factored kNB x kNB diagonal blocks
 };
 
 // Generic batched GEMV task: y[y_idx?] = alpha * op(A) x + beta * y.

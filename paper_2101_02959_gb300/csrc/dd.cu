@@ -122,7 +122,7 @@ __global__ void k_class_aug(const ClassTask *__restrict__ cls, const PairTask *_
 // column become a unit row and column.  Written as AugCo = [[S_PP, I], [I, 0]].
 template <typename T>
 __global__ void k_coarse_aug(int np, int gauge, const int *__restrict__ ptr, const long long *__restrict__ src,
-                             const T *__restrict__ abase, double *__restrict__ co, int ld) {
+                             const T *__restrict__ abase, T *__restrict__ co, int ld) {
   const int m = 2 * np;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)m * m;
        t += (long long)gridDim.x * blockDim.x) {
@@ -137,7 +137,7 @@ __global__ void k_coarse_aug(int np, int gauge, const int *__restrict__ ptr, con
     } else if (b >= np && a < np) {
       v = (b - np == a) ? 1.0 : 0.0;
     }
-    co[(long long)a * ld + b] = v;
+    co[(long long)a * ld + b] = (T)v;
   }
 }
 
@@ -545,7 +545,7 @@ void launch_class_aug(int ncls, int max_n, const ClassTask *cls, const PairTask 
 }
 
 template <typename T>
-void launch_coarse_aug(int np, int gauge, const int *ptr, const long long *src, const T *abase, double *co, int ld,
+void launch_coarse_aug(int np, int gauge, const int *ptr, const long long *src, const T *abase, T *co, int ld,
                        cudaStream_t s) {
   const long long tot = 4LL * np * np;
   const int gx = (int)std::min<long long>((tot + 255) / 256, 8192);
@@ -702,7 +702,7 @@ void launch_dot2(int n, const double *a0, const double *b0, const double *a1, co
   template void launch_small_gemm<T>(int, int, const GemmTask *, const T *, const T *, T *, cudaStream_t);      \
   template void launch_class_aug<T>(int, int, const ClassTask *, const PairTask *, const T *, const MatDesc *,  \
                                     T *, cudaStream_t);                                                        \
-  template void launch_coarse_aug<T>(int, int, const int *, const long long *, const T *, double *, int,        \
+  template void launch_coarse_aug<T>(int, int, const int *, const long long *, const T *, T *, int,             \
                                      cudaStream_t);                                                            \
   template void launch_jump_dt<T>(int, int, const WTask *, const WEnt *, const T *, const T *, const double *,  \
                                   double *, const int *, cudaStream_t);                                        \

@@ -43,7 +43,8 @@ template <typename T>
 void launch_class_aug(int ncls, int max_n, const ClassTask *cls, const PairTask *pairs, const T *blk,
                       const MatDesc *cdesc, T *cbase, cudaStream_t s);
 template <typename T>
-void launch_coarse_aug(int np, int gauge, const int *ptr, const long long *src, const T *abase, double *co, int ld,
+// coarse augmented matrix [[S_PiPi, I], [I, 0]] (assembled in FP64, stored as T)
+void launch_coarse_aug(int np, int gauge, const int *ptr, const long long *src, const T *abase, T *co, int ld,
                        cudaStream_t s);
 void launch_spmv(int n, const int *ptr, const int *col, const double *val, const double *x, double *y, int zero,
                  const int *done, cudaStream_t s);

@@ -21,103 +21,145 @@ template <typename T> __device__ inline T dsqrt(T v);
 template <> __device__ inline float dsqrt<float>(float v) { return sqrtf(v); }
 template <> __device__ inline double dsqrt<double>(double v) { return sqrt(v); }
 
-// ---- panel step 1: factor the w x w diagonal block in place and form L_kk^-1 --
-// 1024 threads per matrix: thread (r, t) owns entry (r, t) of the block.  Step c
-// updates the trailing entries with the unscaled column c divided by its pivot,
-// so one barrier per column suffices; the columns are scaled at the end.
-// Warp 0 then forms L_kk^-1 (lane j solves L y = e_j) for the panel solve.
-template <typename T>
-__global__ void __launch_bounds__(1024) k_potrf(const MatDesc *__restrict__ desc, T *__restrict__ base, int k0,
-                                                int *__restrict__ err, T *__restrict__ linv) {
-  const MatDesc d = desc[blockIdx.x];
-  if (k0 >= d.e) return;
-  const int w = min(kNB, d.e - k0);
-  T *A = base + d.off;
-  __shared__ T Ls[kNB][kNB + 1];
-  __shared__ T piv[kNB];
-  const int r = threadIdx.x >> 5, t = threadIdx.x & 31;
-  Ls[r][t] = (r < w && t <= r) ? A[(long long)(k0 + r) * d.ld + k0 + t] : (r == t ? T(1) : T(0));
-  __syncthreads();
-  bool bad = false;
-  for (int c = 0; c < w; ++c) {
-    T dcc = Ls[c][c];
-    if (!(dcc > T(0))) { bad = true; dcc = T(1); }
-    if (r == c && t == c) piv[c] = dcc;
-    if (t > c && r >= t && r < w) Ls[r][t] -= Ls[r][c] * Ls[t][c] / dcc;
-    __syncthreads();
+// 16-byte vectors of T (row starts of the batched matrices are 32-byte aligned).
+template <typename T> struct Vec16;
+template <> struct Vec16<float> {
+  using V = float4;
+  static constexpr int N = 4;
+  __device__ static float dot(const float4 a, const float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+  __device__ static void axpy(float *acc, const float4 a, float s) {
+    acc[0] += a.x * s; acc[1] += a.y * s; acc[2] += a.z * s; acc[3] += a.w * s;
   }
-  if (bad && threadIdx.x == 0) atomicOr(err, DEV_ERR_NOT_SPD);
-  // scale: L[r][c] = A_c[r][c] / sqrt(d_c), L[c][c] = sqrt(d_c)
-  T lv = T(0);
-  if (r < w && t <= r) lv = (r == t) ? dsqrt(piv[t]) : Ls[r][t] / dsqrt(piv[t]);
-  else if (r == t) lv = T(1);
-  __syncthreads();
-  Ls[r][t] = lv;
-  __syncthreads();
-  if (r < w && t <= r) A[(long long)(k0 + r) * d.ld + k0 + t] = lv;
-  // L_kk^-1 by recursive doubling: inv([[A, 0], [B, C]]) = [[A^-1, 0], [-C^-1 B A^-1, C^-1]]
-  __shared__ T Yi[kNB][kNB + 1];
-  __shared__ T Tm[kNB][kNB + 1];
-  Yi[r][t] = (r == t) ? T(1) / Ls[r][r] : T(0);
-  __syncthreads();
-  for (int b = 1; b < kNB; b <<= 1) {
-    const int base0 = (r / (2 * b)) * (2 * b);
-    const bool active = (t / (2 * b) == r / (2 * b)) && ((r - base0) >= b) && ((t - base0) < b);
-    if (active) {  // Tm = B A^-1 over the top half
-      T acc = T(0);
-      for (int k = t; k < base0 + b; ++k) acc += Ls[r][k] * Yi[k][t];
-      Tm[r][t] = acc;
-    }
-    __syncthreads();
-    if (active) {  // Y = -C^-1 (B A^-1) over the bottom half
-      T acc = T(0);
-      for (int k = base0 + b; k <= r; ++k) acc += Yi[r][k] * Tm[k][t];
-      Yi[r][t] = -acc;
-    }
-    __syncthreads();
-  }
-  linv[(long long)blockIdx.x * kNB * kNB + r * kNB + t] = Yi[r][t];
-}
+};
+template <> struct Vec16<double> {
+  using V = double2;
+  static constexpr int N = 2;
+  __device__ static double dot(const double2 a, const double2 b) { return a.x * b.x + a.y * b.y; }
+  __device__ static void axpy(double *acc, const double2 a, double s) { acc[0] += a.x * s; acc[1] += a.y * s; }
+};
 
-// ---- panel step 2: rows below the diagonal block, x = a L_kk^-T ----------------
-// 128 rows per CTA; the 128 x 32 tile is staged in shared memory with coalesced
-// loads (warp q reads rows, lane = column) and each thread forms one row.
+// ---- panel: factor the diagonal block and solve the rows below it -------------
+// Every CTA of a matrix factors the w x w diagonal block (read from A, which no
+// CTA of this launch writes): warp 0 holds it in registers, lane r = row r, and
+// eliminates column by column with shuffles.  Each thread then forms one row of
+// the panel below, L_ik = A_ik L_kk^-T, by substitution with the transposed
+// factor from shared memory.  CTA 0 stores L_kk in the block store at slot
+// dblk + k0 / kNB (identity outside w); the in-place diagonal block is left as it
+// was, since another CTA may still be reading it.
+constexpr int kPanelRows = 128;
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_trsm(const MatDesc *__restrict__ desc, T *__restrict__ base, int k0,
-                                              const T *__restrict__ linv) {
+__global__ void __launch_bounds__(kPanelRows) k_panel(const MatDesc *__restrict__ desc, T *__restrict__ base, int k0,
+                                                      int *__restrict__ err, T *__restrict__ store) {
   const MatDesc d = desc[blockIdx.y];
   if (k0 >= d.e) return;
   const int w = min(kNB, d.e - k0);
-  const int rbeg = k0 + w + blockIdx.x * 128;
-  if (rbeg >= d.m) return;
+  const int rbeg = k0 + w + blockIdx.x * kPanelRows;
+  if (rbeg >= d.m && blockIdx.x != 0) return;
   T *A = base + d.off;
-  __shared__ T Li[kNB][kNB];
-  __shared__ T X[128][kNB + 1];
-  const T *src = linv + (long long)blockIdx.y * kNB * kNB;
-  for (int t = threadIdx.x; t < kNB * kNB; t += 128) Li[t / kNB][t % kNB] = src[t];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int nrows = min(128, d.m - rbeg);
-  for (int q = wid; q < nrows; q += 4)
-    X[q][lane] = (lane < w) ? A[(long long)(rbeg + q) * d.ld + k0 + lane] : T(0);
-  __syncthreads();
-  if (threadIdx.x < nrows) {
-    T x[kNB];
+  using VT = typename Vec16<T>::V;
+  constexpr int VN = Vec16<T>::N, VPR = kNB / VN;
+  __shared__ __align__(16) T Lt[kNB][kNB];  // Lt[c][t] = L[t][c] for t >= c, 0 for t < c
+  __shared__ T rd[kNB];                     // 1 / L[c][c]
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int row = rbeg + tid;
+  const bool has_row = row < d.m;
+  // this thread's panel row, all vector loads in flight together (a vector is read
+  // when it holds a column below w; it then ends within the padded row)
+  T x[kNB];
+  {
+    VT xv[VPR];
+    const T *src = A + (long long)(has_row ? row : 0) * d.ld + k0;
 #pragma unroll
-    for (int c = 0; c < kNB; ++c) x[c] = X[threadIdx.x][c];
-    // x_out[c] = sum_{t <= c} x[t] (L^-1)[c][t]: independent dot products
+    for (int i = 0; i < VPR; ++i)
+      if (has_row && i * VN < w) xv[i] = *reinterpret_cast<const VT *>(src + i * VN);
 #pragma unroll
-    for (int c = kNB - 1; c >= 0; --c) {
-      T v = T(0);
+    for (int i = 0; i < VPR; ++i) {
+      const T *e = reinterpret_cast<const T *>(&xv[i]);
 #pragma unroll
-      for (int t = 0; t <= c; ++t) v += x[t] * Li[c][t];
-      x[c] = v;
+      for (int u = 0; u < VN; ++u) x[i * VN + u] = (has_row && i * VN + u < w) ? e[u] : T(0);
     }
+  }
+  if (tid < 32) {
+    T a[kNB];
+    {
+      VT dv[VPR];
+      const T *src = A + (long long)(k0 + (lane < w ? lane : 0)) * d.ld + k0;
 #pragma unroll
-    for (int c = 0; c < kNB; ++c) X[threadIdx.x][c] = x[c];
+      for (int i = 0; i < VPR; ++i)
+        if (lane < w && i * VN <= lane) dv[i] = *reinterpret_cast<const VT *>(src + i * VN);
+#pragma unroll
+      for (int i = 0; i < VPR; ++i) {
+        const T *e = reinterpret_cast<const T *>(&dv[i]);
+#pragma unroll
+        for (int u = 0; u < VN; ++u) {
+          const int t = i * VN + u;
+          a[t] = (lane < w && t <= lane) ? e[u] : (t == lane ? T(1) : T(0));
+        }
+      }
+    }
+    bool bad = false;
+#pragma unroll
+    for (int c = 0; c < kNB; ++c) {
+      if (c < w) {  // uniform across the warp
+        T piv = __shfl_sync(0xffffffffu, a[c], c);
+        if (!(piv > T(0))) { bad = true; piv = T(1); }
+        const T sd = dsqrt(piv), inv = T(1) / sd;
+        a[c] = (lane == c) ? sd : a[c] * inv;  // rows above c hold 0 here
+#pragma unroll
+        for (int t = c + 1; t < kNB; ++t) {
+          const T lt = __shfl_sync(0xffffffffu, a[c], t);
+          if (lane >= t) a[t] -= a[c] * lt;
+        }
+      }
+    }
+    if (bad && lane == 0 && blockIdx.x == 0) atomicOr(err, DEV_ERR_NOT_SPD);
+#pragma unroll
+    for (int t = 0; t < kNB; ++t) Lt[t][lane] = (t <= lane) ? a[t] : T(0);
+    rd[lane] = T(1) / a[lane];
+    if (blockIdx.x == 0) {
+      T *dst = store + ((long long)d.dblk + k0 / kNB) * kNB * kNB + lane * kNB;
+#pragma unroll
+      for (int i = 0; i < VPR; ++i) {
+        VT o;
+        T *e = reinterpret_cast<T *>(&o);
+#pragma unroll
+        for (int u = 0; u < VN; ++u) e[u] = (i * VN + u <= lane) ? a[i * VN + u] : T(0);
+        *reinterpret_cast<VT *>(dst + i * VN) = o;
+      }
+    }
   }
   __syncthreads();
-  for (int q = wid; q < nrows; q += 4)
-    if (lane < w) A[(long long)(rbeg + q) * d.ld + k0 + lane] = X[q][lane];
+  if (!has_row) return;
+  // x L^T = a, right-looking over the columns; Lt rows are read as 16-byte vectors
+#pragma unroll
+  for (int c = 0; c < kNB; ++c) {
+    x[c] *= rd[c];
+#pragma unroll
+    for (int i = (c + 1) / VN; i < VPR; ++i) {
+      const VT lv = *reinterpret_cast<const VT *>(&Lt[c][i * VN]);
+      const T *e = reinterpret_cast<const T *>(&lv);
+#pragma unroll
+      for (int u = 0; u < VN; ++u)
+        if (i * VN + u > c) x[i * VN + u] -= e[u] * x[c];
+    }
+  }
+  T *dst = A + (long long)row * d.ld + k0;
+#pragma unroll
+  for (int i = 0; i < VPR; ++i) {
+    if (i * VN >= w) continue;
+    if (i * VN + VN <= w) {
+      VT o;
+      T *e = reinterpret_cast<T *>(&o);
+#pragma unroll
+      for (int u = 0; u < VN; ++u) e[u] = x[i * VN + u];
+      *reinterpret_cast<VT *>(dst + i * VN) = o;
+    } else {
+#pragma unroll
+      for (int u = 0; u < VN; ++u)
+        if (i * VN + u < w) dst[i * VN + u] = x[i * VN + u];
+    }
+  }
 }
 
 // ---- rank-k update of lower tiles --------------------------------------------
@@ -336,7 +378,7 @@ void launch_rankk<float>(const MatDesc *d_desc, float *base, int mode, int k0, i
 
 template <typename T>
 void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s,
-                             T *linv, ProfHook *prof, bool tc) {
+                             T *store, ProfHook *prof, bool tc) {
   if (sh.count == 0) return;
   const int ob = std::max(kNB, (sh.ob / kNB) * kNB);
   for (int K0 = 0; K0 < sh.max_e; K0 += ob) {
@@ -357,13 +399,9 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
         by_upd += sizeof(T) * (2.0 * ent + (double)w * (below + cend - k0 - w));
       }
       if (prof) prof->begin(PROF_PANEL, s);
-      k_potrf<T><<<sh.count, 1024, 0, s>>>(d_desc, base, k0, d_err, linv);
+      dim3 gp(std::max(1, ceil_div(max_below, kPanelRows)), sh.count);
+      k_panel<T><<<gp, kPanelRows, 0, s>>>(d_desc, base, k0, d_err, store);
       count_launch();
-      if (max_below > 0) {
-        dim3 gp(ceil_div(max_below, 128), sh.count);
-        k_trsm<T><<<gp, 128, 0, s>>>(d_desc, base, k0, linv);
-        count_launch();
-      }
       if (prof) prof->end(PROF_PANEL, s, fl_panel, 0.0);
       if (max_below > 0 && max_cols > 0) {
         if (prof) prof->begin(PROF_RANKK, s);
@@ -427,7 +465,7 @@ __global__ void __launch_bounds__(256) k_gemv(const GemvDesc *__restrict__ tasks
   const GemvDesc t = tasks[blockIdx.y];
   const int rbeg = blockIdx.x * kGemvRows;
   if (rbeg >= t.rows) return;
-  extern __shared__ unsigned char smem_raw[];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T *xs = reinterpret_cast<T *>(smem_raw);
   for (int c = threadIdx.x; c < t.cols; c += blockDim.x)
     xs[c] = (T)((t.flags & 1) ? x[xidx[t.x_off + c]] : x[t.x_off + c]);
@@ -463,32 +501,46 @@ __global__ void __launch_bounds__(256) k_gemv(const GemvDesc *__restrict__ tasks
   }
 }
 
-// y[a] = (acc ? y[a] : 0) + alpha sum_p A[p][a] x[p]; one thread per column a.
+// y[a] = (acc ? y[a] : 0) + alpha sum_p A[p][a] x[p]: one CTA per (task, 32 columns);
+// lane = column (coalesced rows), the 8 warps split the rows with 4 loads in flight
+// each and add up their partial sums in shared memory in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemv_t(const GemvDesc *__restrict__ tasks, const T *__restrict__ A,
                                                 const double *__restrict__ x, const int *__restrict__ xidx,
                                                 double *__restrict__ y, double alpha, const int *__restrict__ done) {
   if (done && *done) return;
   const GemvDesc t = tasks[blockIdx.y];
-  extern __shared__ unsigned char smem_raw[];
+  const int c0 = blockIdx.x * 32;
+  if (c0 >= t.cols) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
   T *xs = reinterpret_cast<T *>(smem_raw);
+  __shared__ T part[8][33];
   for (int p = threadIdx.x; p < t.rows; p += blockDim.x)
     xs[p] = (T)((t.flags & 1) ? x[xidx[t.x_off + p]] : x[t.x_off + p]);
   __syncthreads();
-  const int a = blockIdx.x * blockDim.x + threadIdx.x;
-  if (a >= t.cols) return;
-  const T *col = A + t.a_off + a;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int a = c0 + lane;
+  const bool va = a < t.cols;
+  const T *col = A + t.a_off + (va ? a : c0);
+  const long long ld = t.ld;
   T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-  int p = 0;
-  for (; p + 3 < t.rows; p += 4) {
-    a0 += col[(long long)p * t.ld] * xs[p];
-    a1 += col[(long long)(p + 1) * t.ld] * xs[p + 1];
-    a2 += col[(long long)(p + 2) * t.ld] * xs[p + 2];
-    a3 += col[(long long)(p + 3) * t.ld] * xs[p + 3];
+  int p = wid;
+  for (; p + 24 < t.rows; p += 32) {
+    a0 += col[p * ld] * xs[p];
+    a1 += col[(p + 8) * ld] * xs[p + 8];
+    a2 += col[(p + 16) * ld] * xs[p + 16];
+    a3 += col[(p + 24) * ld] * xs[p + 24];
   }
-  for (; p < t.rows; ++p) a0 += col[(long long)p * t.ld] * xs[p];
-  const double v = alpha * (double)((a0 + a1) + (a2 + a3));
-  y[t.y_off + a] = (t.flags & 2) ? y[t.y_off + a] + v : v;
+  for (; p < t.rows; p += 8) a0 += col[p * ld] * xs[p];
+  part[wid][lane] = (a0 + a1) + (a2 + a3);
+  __syncthreads();
+  if (wid == 0 && va) {
+    T sum = T(0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sum += part[k][lane];
+    const double v = alpha * (double)sum;
+    y[t.y_off + a] = (t.flags & 2) ? y[t.y_off + a] + v : v;
+  }
 }
 
 template <typename T>
@@ -505,112 +557,165 @@ template <typename T>
 void launch_gemv_t(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks, const T *A, const double *x,
                    const int *xidx, double *y, double alpha, const int *done, cudaStream_t s) {
   if (ntasks == 0 || max_cols == 0) return;
-  dim3 g(ceil_div(max_cols, 256), ntasks);
+  dim3 g(ceil_div(max_cols, 32), ntasks);
   const size_t sm = sizeof(T) * (size_t)std::max(1, max_rows);
   k_gemv_t<T><<<g, 256, sm, s>>>(d_tasks, A, x, xidx, y, alpha, done);
   count_launch();
 }
 
 // ---- batched triangular solves (one CTA of 32 warps per matrix) ---------------
-// lower: y = L^-1 b, left-looking over 32-row blocks, one warp per block row;
-// upper: y = L^-T b, right-to-left, warps striding over the rows below the block.
-// The 32x32 diagonal block is staged in shared memory; the vector lives there too.
+// y = L^-1 b (lower, blocks in increasing order) or y = L^-T b (upper, decreasing),
+// 32-row blocks, one barrier per block.  While warp 0 finishes block k (adds the
+// contributions gathered for it, then substitutes with the factored diagonal block
+// from the engine's store), warps 1..31 gather everything the next block needs
+// that is already final: its diagonal block, the sums over the solved blocks before
+// k (16-byte vector loads, several in flight per lane) and the 32 x 32 tile that
+// couples it to block k.  Buffers alternate between blocks; the vector lives in
+// shared memory.
 template <typename T>
 __global__ void __launch_bounds__(1024) k_trsv(const MatDesc *__restrict__ desc, const int *__restrict__ vec_off,
-                                               const T *__restrict__ base, const double *__restrict__ b,
-                                               double *__restrict__ y, int transpose) {
+                                               const T *__restrict__ base, const T *__restrict__ store,
+                                               const double *__restrict__ b, double *__restrict__ y, int transpose) {
+  using VT = typename Vec16<T>::V;
+  constexpr int VN = Vec16<T>::N, VPR = kNB / VN, RPW = 32 / VPR;
   const MatDesc d = desc[blockIdx.x];
   const int n = d.e;
   const T *L = base + d.off;
-  extern __shared__ unsigned char smem_raw[];
-  T *v = reinterpret_cast<T *>(smem_raw);
-  __shared__ T part[32][33];
-  __shared__ T Lb[32][33];
+  // dynamic shared memory: six 32 x 33 tiles, then the vector
+  typedef T Tile[32][33];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Tile *Lb = reinterpret_cast<Tile *>(smem_raw);  // [2] diagonal block
+  Tile *Lt = Lb + 2;    // [2] coupling tile: lower Lt[j][c] = L[r0n + j][r0 + c]; upper Lt[c][j] = L[r0 + c][r0n + j]
+  Tile *part = Lb + 4;  // [2] lower: part[0][j] = prefix sums; upper: part[w][j] per warp
+  T *v = reinterpret_cast<T *>(Lb + 6);
   const int off = vec_off[blockIdx.x];
-  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = (T)b[off + i];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int nblk = ceil_div(n, 32);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = (T)b[off + i];
+  if (nblk > 0) {
+    const int b0 = transpose ? nblk - 1 : 0;
+    Lb[0][wid][lane] = store[((long long)d.dblk + b0) * kNB * kNB + wid * kNB + lane];
+  }
+  __syncthreads();
   for (int q = 0; q < nblk; ++q) {
+    const int buf = q & 1, nb = buf ^ 1;
     const int bk = transpose ? nblk - 1 - q : q;
     const int r0 = bk * 32, r1 = min(n, r0 + 32);
-    {  // diagonal block, coalesced: warp wid loads row r0 + wid
-      const int i = wid, k = lane;
-      Lb[i][k] = (r0 + i < r1 && k <= i) ? L[(long long)(r0 + i) * d.ld + r0 + k] : T(0);
+    if (wid == 0) {
+      const int r = r0 + lane;
+      T vr = (r < r1) ? v[r] : T(0);
+      if (q > 0) {
+        if (!transpose) {  // previous block [r0 - 32, r0)
+          T s = part[buf][0][lane];
+#pragma unroll 8
+          for (int c = 0; c < 32; ++c) s += Lt[buf][lane][c] * v[r0 - 32 + c];
+          vr -= s;
+        } else {  // previous block [r1, min(n, r1 + 32))
+          T s = T(0);
+#pragma unroll 8
+          for (int k = 1; k < 32; ++k) s += part[buf][k][lane];
+          const int cnt = min(32, n - r1);
+          for (int c = 0; c < cnt; ++c) s += Lt[buf][c][lane] * v[r1 + c];
+          vr -= s;
+        }
+      }
+      const T rdl = T(1) / Lb[buf][lane][lane];
+      if (!transpose) {
+        for (int c = 0; c < r1 - r0; ++c) {
+          const T xc = __shfl_sync(0xffffffffu, vr * rdl, c);
+          if (lane == c) vr = xc;
+          else if (lane > c) vr -= Lb[buf][lane][c] * xc;
+        }
+      } else {
+        for (int c = r1 - r0 - 1; c >= 0; --c) {
+          const T xc = __shfl_sync(0xffffffffu, vr * rdl, c);
+          if (lane == c) vr = xc;
+          else if (lane < c) vr -= Lb[buf][c][lane] * xc;
+        }
+      }
+      if (r < r1) v[r] = vr;
+    } else {
+      const int bn = transpose ? bk - 1 : bk + 1;  // next block
+      if (bn >= 0 && bn < nblk) {
+        const int r0n = bn * 32;
+        for (int j = wid - 1; j < 32; j += 31)
+          Lb[nb][j][lane] = store[((long long)d.dblk + bn) * kNB * kNB + j * kNB + lane];
+        if (!transpose) {
+          // rows r0n + j: prefix over the columns [0, r0) and the tile against [r0, r1)
+          for (int j = wid - 1; j < 32; j += 31) {
+            const int rn = r0n + j;
+            T s = T(0), tv = T(0);
+            if (rn < n) {
+              const T *Lr = L + (long long)rn * d.ld;
+              tv = Lr[r0 + lane];  // r1 - r0 = 32 here: block k is not the last one
+              const VT *Lv = reinterpret_cast<const VT *>(Lr);
+              const VT *vv = reinterpret_cast<const VT *>(v);
+              const int nv = r0 / VN;
+              T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
+              int i = lane;
+              for (; i + 96 < nv; i += 128) {
+                const VT l0 = Lv[i], l1 = Lv[i + 32], l2 = Lv[i + 64], l3 = Lv[i + 96];
+                a0 += Vec16<T>::dot(l0, vv[i]);
+                a1 += Vec16<T>::dot(l1, vv[i + 32]);
+                a2 += Vec16<T>::dot(l2, vv[i + 64]);
+                a3 += Vec16<T>::dot(l3, vv[i + 96]);
+              }
+              for (; i < nv; i += 32) a0 += Vec16<T>::dot(Lv[i], vv[i]);
+              s = warp_sum((a0 + a1) + (a2 + a3));
+            }
+            Lt[nb][j][lane] = tv;
+            if (lane == 0) part[nb][0][j] = s;
+          }
+        } else {
+          // columns r0n + j (the next block): sums over the rows [r1, n), tile against the rows [r0, r1)
+          const int cq = lane % VPR, rq = lane / VPR;
+          T acc[VN];
+#pragma unroll
+          for (int u = 0; u < VN; ++u) acc[u] = T(0);
+          const T *Lc = L + r0n + VN * cq;
+          constexpr int kStep = 31 * RPW;
+          int c = r1 + RPW * (wid - 1) + rq;
+          for (; c + 3 * kStep < n; c += 4 * kStep) {
+            const VT l0 = *reinterpret_cast<const VT *>(Lc + (long long)c * d.ld);
+            const VT l1 = *reinterpret_cast<const VT *>(Lc + (long long)(c + kStep) * d.ld);
+            const VT l2 = *reinterpret_cast<const VT *>(Lc + (long long)(c + 2 * kStep) * d.ld);
+            const VT l3 = *reinterpret_cast<const VT *>(Lc + (long long)(c + 3 * kStep) * d.ld);
+            Vec16<T>::axpy(acc, l0, v[c]);
+            Vec16<T>::axpy(acc, l1, v[c + kStep]);
+            Vec16<T>::axpy(acc, l2, v[c + 2 * kStep]);
+            Vec16<T>::axpy(acc, l3, v[c + 3 * kStep]);
+          }
+          for (; c < n; c += kStep) Vec16<T>::axpy(acc, *reinterpret_cast<const VT *>(Lc + (long long)c * d.ld), v[c]);
+#pragma unroll
+          for (int u = 0; u < VN; ++u)
+#pragma unroll
+            for (int o = VPR; o < 32; o <<= 1) acc[u] += __shfl_xor_sync(0xffffffffu, acc[u], o);
+          if (rq == 0)
+#pragma unroll
+            for (int u = 0; u < VN; ++u) part[nb][wid][VN * cq + u] = acc[u];
+          for (int j = wid - 1; j < 32; j += 31)
+            Lt[nb][j][lane] = (r0 + j < r1) ? L[(long long)(r0 + j) * d.ld + r0n + lane] : T(0);
+        }
+      }
     }
     __syncthreads();
-    if (!transpose) {
-      // v[r] -= sum_{c < r0} L[r][c] v[c]; warp wid owns row r0 + wid
-      const int r = r0 + wid;
-      if (r < r1) {
-        const T *Lr = L + (long long)r * d.ld;
-        T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-        int c = lane;
-        for (; c + 96 < r0; c += 128) {
-          a0 += Lr[c] * v[c];
-          a1 += Lr[c + 32] * v[c + 32];
-          a2 += Lr[c + 64] * v[c + 64];
-          a3 += Lr[c + 96] * v[c + 96];
-        }
-        for (; c < r0; c += 32) a0 += Lr[c] * v[c];
-        const T acc = warp_sum((a0 + a1) + (a2 + a3));
-        if (lane == 0) v[r] -= acc;
-      }
-      __syncthreads();
-      if (wid == 0) {
-        const int r = r0 + lane;
-        T vr = (r < r1) ? v[r] : T(0);
-        for (int c = r0; c < r1; ++c) {
-          const T xc = __shfl_sync(0xffffffffu, vr / ((r == c) ? Lb[lane][lane] : T(1)), c - r0);
-          if (r == c) vr = xc;
-          else if (r > c && r < r1) vr -= Lb[lane][c - r0] * xc;
-        }
-        if (r < r1) v[r] = vr;
-      }
-      __syncthreads();
-    } else {
-      // v[r] -= sum_{c >= r1} L[c][r] v[c] for r in the block; warp wid takes rows r1 + wid + 32 k
-      T a0 = T(0), a1 = T(0);
-      const int r = r0 + lane;
-      if (r < r1) {
-        int c = r1 + wid;
-        for (; c + 32 < n; c += 64) {
-          a0 += L[(long long)c * d.ld + r] * v[c];
-          a1 += L[(long long)(c + 32) * d.ld + r] * v[c + 32];
-        }
-        for (; c < n; c += 32) a0 += L[(long long)c * d.ld + r] * v[c];
-      }
-      part[wid][lane] = a0 + a1;
-      __syncthreads();
-      if (wid == 0) {
-        T s = T(0);
-#pragma unroll 8
-        for (int k = 0; k < 32; ++k) s += part[k][lane];
-        T vr = (r < r1) ? v[r] - s : T(0);
-        for (int c = r1 - 1; c >= r0; --c) {
-          const T xc = __shfl_sync(0xffffffffu, vr / ((r == c) ? Lb[lane][lane] : T(1)), c - r0);
-          if (r == c) vr = xc;
-          else if (r < c && r < r1) vr -= Lb[c - r0][lane] * xc;
-        }
-        if (r < r1) v[r] = vr;
-      }
-      __syncthreads();
-    }
   }
   for (int i = threadIdx.x; i < n; i += blockDim.x) y[off + i] = (double)v[i];
 }
 
 template <typename T>
-void launch_trsv(int count, int max_n, const MatDesc *d_desc, const int *vec_off, const T *base, const double *b,
-                 double *y, bool transpose, cudaStream_t s) {
+void launch_trsv(int count, int max_n, const MatDesc *d_desc, const int *vec_off, const T *base, const T *store,
+                 const double *b, double *y, bool transpose, cudaStream_t s) {
   if (count == 0) return;
-  const size_t sm = sizeof(T) * (size_t)std::max(1, max_n);
-  k_trsv<T><<<count, 1024, sm, s>>>(d_desc, vec_off, base, b, y, transpose ? 1 : 0);
+  const size_t sm = sizeof(T) * (6 * 32 * 33 + (size_t)std::max(4, max_n + 4));
+  k_trsv<T><<<count, 1024, sm, s>>>(d_desc, vec_off, base, store, b, y, transpose ? 1 : 0);
   count_launch();
 }
 
 // Large local problems stage vectors of up to ~25k entries in shared memory.
+size_t dense_smem_limit() { return 200 * 1024; }
 bool dense_configure() {
-  const int lim = 200 * 1024;
+  const int lim = (int)dense_smem_limit();
   bool ok = true;
   ok &= cudaFuncSetAttribute(k_trsv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_trsv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
@@ -628,8 +733,8 @@ bool dense_configure() {
                                double *, double, const int *, cudaStream_t);                                   \
   template void launch_gemv_t<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *,      \
                                  double *, double, const int *, cudaStream_t);                                 \
-  template void launch_trsv<T>(int, int, const MatDesc *, const int *, const T *, const double *, double *,    \
-                               bool, cudaStream_t);
+  template void launch_trsv<T>(int, int, const MatDesc *, const int *, const T *, const T *, const double *,   \
+                               double *, bool, cudaStream_t);
 BD_INST(float)
 BD_INST(double)
 

@@ -59,13 +59,16 @@ struct EngineShape {
   std::vector<int> m, e;  // host copies for per-step grid sizes
   int ob = 256;           // outer panel width (columns per trailing long-K update)
 };
-// linv: scratch of count * kNB * kNB elements (the inverse of each diagonal block).
+// store: block store receiving the factored kNB x kNB diagonal blocks L_kk; matrix b
+// uses slots [desc[b].dblk, desc[b].dblk + ceil(e_b / kNB)) (row-major, identity
+// outside the last block's width).  The in-place diagonal blocks are not factored.
 // tc: FP32 only, run the long-K updates on the tensor cores (tc.cu).
 template <typename T>
 void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s,
-                             T *linv, ProfHook *prof = nullptr, bool tc = false);
+                             T *store, ProfHook *prof = nullptr, bool tc = false);
 
 bool dense_configure();
+size_t dense_smem_limit();  // bytes of shared memory the dense kernels may stage per CTA
 
 // tc.cu
 bool tc_configure();
@@ -80,10 +83,11 @@ void launch_gemv(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks
 template <typename T>
 void launch_gemv_t(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks, const T *A, const double *x,
                    const int *xidx, double *y, double alpha, const int *done, cudaStream_t s);
-// Batched triangular solves with the leading n x n lower triangles (MatDesc.e = n):
+// Batched triangular solves with the leading n x n lower triangles (MatDesc.e = n) left
+// by the engine (off-diagonal blocks in base, diagonal blocks in the engine's store):
 // y = L^-1 b (lower) or y = L^-T b (upper); b and y are concatenated vectors at vec_off[b].
 template <typename T>
-void launch_trsv(int count, int max_n, const MatDesc *d_desc, const int *vec_off, const T *base, const double *b,
-                 double *y, bool transpose, cudaStream_t s);
+void launch_trsv(int count, int max_n, const MatDesc *d_desc, const int *vec_off, const T *base, const T *store,
+                 const double *b, double *y, bool transpose, cudaStream_t s);
 
 }  // namespace bd
