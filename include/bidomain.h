@@ -142,8 +142,10 @@ typedef struct {
   int use_tensor_cores;
   /* 1 = chord Newton: factorise the Jacobian at the first Newton iterate of a
    * time step and reuse it for the later iterations of that step (every iterate
-   * is still tested with the exact FP64 residual); 0 = factorise at every
-   * Newton iterate (the paper's setting, the default). */
+   * is still tested with the exact FP64 residual; when the line search finds no
+   * decrease along a lagged direction, the Jacobian is formed at the current
+   * iterate and the iteration repeated); 0 = factorise at every Newton iterate
+   * (the paper's setting, the default). */
   int lag_jacobian;
 } bd_options;
 
@@ -255,10 +257,11 @@ int krylov_solve(bd_handle *h, const double *f, double *s, int on_device, bd_sol
 /* ---- autotuner (not in the paper) ----------------------------------------------
  * Times the whole factorisation sequence of bidomain_linearize (CUDA events,
  * best of two after a warm-up) at the current Jacobian for every combination of
- * outer panel width {128, 256, 512}, number of subdomain groups {1, 2, 4}
- * and, in BD_MIXED, tensor cores on/off; keeps the fastest for the handle and
- * leaves the Jacobian factorised with it.  Requires bidomain_linearize (or a
- * step) first.  Results are identical up to rounding for every choice. */
+ * the number of subdomain groups the batch is factorised in {1, 2, 4, 8} and, in
+ * BD_MIXED, tensor cores on/off; keeps the fastest for the handle and leaves the
+ * Jacobian factorised with it.  outer_panel reports the engine's fixed outer panel
+ * width (128).  Requires bidomain_linearize (or a step) first.  Results are
+ * identical up to rounding for every choice. */
 typedef struct {
   int outer_panel, groups, tensor_cores, candidates;
   double best_ms, default_ms;

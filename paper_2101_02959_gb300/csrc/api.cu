@@ -255,7 +255,7 @@ struct bd_handle {
   double *d_uh1i, *d_uh1e, *d_uh2i, *d_uh2e, *d_gi, *d_ge;
   double rtol_scale = 1.0;
   // factorisation tuning (bidomain_autotune): outer panel width, batch groups, tensor cores
-  int tune_ob = 256, tune_groups = 1;
+  int tune_groups = 1;
   cudaGraphExec_t pcg_exec[2] = {nullptr, nullptr};  // captured PCG chunk per method
   size_t pcg_nodes[2] = {0, 0};
   double gemv_schur_flops = 0, gemv_schur_bytes = 0, gemv_local_flops = 0, gemv_local_bytes = 0;
@@ -826,7 +826,7 @@ void setup_handle(bd_handle &h) {
 // Jacobian: local matrices, factorisations, Schur complements, deluxe, coarse
 // ---------------------------------------------------------------------------
 // The subdomain batch is factorised in tune_groups consecutive groups (smaller
-// groups keep their trailing matrices in L2), with outer panels of tune_ob columns.
+// groups keep their trailing matrices in L2).
 template <class T>
 void run_engine_groups(bd_handle &h, const EngineShape &all, const MatDesc *d_desc, T *base, T *linv) {
   const int G = std::max(1, std::min(h.tune_groups, all.count));
@@ -834,7 +834,6 @@ void run_engine_groups(bd_handle &h, const EngineShape &all, const MatDesc *d_de
   for (int a = 0; a < all.count; a += per) {
     const int b = std::min(all.count, a + per);
     EngineShape g{b - a, 0, 0, {}, {}};
-    g.ob = h.tune_ob;
     for (int q = a; q < b; ++q) {
       g.m.push_back(all.m[q]);
       g.e.push_back(all.e[q]);
@@ -1706,7 +1705,7 @@ int bidomain_autotune(bd_handle *h, bd_tune_result *out) {
     ck(cudaEventCreate(&e1), "event");
     const bool prof_on = h->prof.on;
     h->prof.on = false;
-    const int tc0 = h->opt.use_tensor_cores, ob0 = h->tune_ob, g0 = h->tune_groups;
+    const int tc0 = h->opt.use_tensor_cores, g0 = h->tune_groups;
     auto time_it = [&]() {
       linearize(*h);  // warm
       float best = 1e30f;
@@ -1723,22 +1722,19 @@ int bidomain_autotune(bd_handle *h, bd_tune_result *out) {
     };
     const float base_ms = time_it();
     float best_ms = base_ms;
-    int best_ob = ob0, best_g = g0, best_tc = tc0, n = 0;
+    int best_g = g0, best_tc = tc0, n = 0;
     const int tcs[2] = {0, 1};
     for (int tc : tcs) {
       if (tc && !h->mixed()) continue;
-      for (int ob : {128, 256, 512})
-        for (int g : {1, 2, 4}) {
-          h->opt.use_tensor_cores = tc;
-          h->tune_ob = ob;
-          h->tune_groups = g;
-          const float ms = time_it();
-          ++n;
-          if (ms < best_ms) { best_ms = ms; best_ob = ob; best_g = g; best_tc = tc; }
-        }
+      for (int g : {1, 2, 4, 8}) {
+        h->opt.use_tensor_cores = tc;
+        h->tune_groups = g;
+        const float ms = time_it();
+        ++n;
+        if (ms < best_ms) { best_ms = ms; best_g = g; best_tc = tc; }
+      }
     }
     h->opt.use_tensor_cores = best_tc;
-    h->tune_ob = best_ob;
     h->tune_groups = best_g;
     linearize(*h);
     h->prof.on = prof_on;
@@ -1746,7 +1742,7 @@ int bidomain_autotune(bd_handle *h, bd_tune_result *out) {
     cudaEventDestroy(e1);
     int st = h->check_err();
     if (out) {
-      out->outer_panel = best_ob;
+      out->outer_panel = kEnginePanel;
       out->groups = best_g;
       out->tensor_cores = best_tc;
       out->candidates = n;

@@ -20,12 +20,21 @@ namespace bd {
 template <typename T> __device__ inline T dsqrt(T v);
 template <> __device__ inline float dsqrt<float>(float v) { return sqrtf(v); }
 template <> __device__ inline double dsqrt<double>(double v) { return sqrt(v); }
+// 1 / sqrt(v): the hardware estimate for float (relative error a few units in the
+// last place, the level of FP32 rounding in the factors), the library routine for double
+template <typename T> __device__ inline T drsqrt(T v);
+template <> __device__ inline float drsqrt<float>(float v) { return rsqrtf(v); }
+template <> __device__ inline double drsqrt<double>(double v) { return rsqrt(v); }
 
 // 16-byte vectors of T (row starts of the batched matrices are 32-byte aligned).
 template <typename T> struct Vec16;
 template <> struct Vec16<float> {
   using V = float4;
   static constexpr int N = 4;
+  __device__ static float get(const float4 &v, int q) { return q == 0 ? v.x : q == 1 ? v.y : q == 2 ? v.z : v.w; }
+  __device__ static void set(float4 &v, int q, float a) {
+    if (q == 0) v.x = a; else if (q == 1) v.y = a; else if (q == 2) v.z = a; else v.w = a;
+  }
   __device__ static float dot(const float4 a, const float4 b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
   __device__ static void axpy(float *acc, const float4 a, float s) {
     acc[0] += a.x * s; acc[1] += a.y * s; acc[2] += a.z * s; acc[3] += a.w * s;
@@ -34,130 +43,261 @@ template <> struct Vec16<float> {
 template <> struct Vec16<double> {
   using V = double2;
   static constexpr int N = 2;
+  __device__ static double get(const double2 &v, int q) { return q == 0 ? v.x : v.y; }
+  __device__ static void set(double2 &v, int q, double a) {
+    if (q == 0) v.x = a; else v.y = a;
+  }
   __device__ static double dot(const double2 a, const double2 b) { return a.x * b.x + a.y * b.y; }
   __device__ static void axpy(double *acc, const double2 a, double s) { acc[0] += a.x * s; acc[1] += a.y * s; }
 };
 
-// ---- panel: factor the diagonal block and solve the rows below it -------------
-// Every CTA of a matrix factors the w x w diagonal block (read from A, which no
-// CTA of this launch writes): warp 0 holds it in registers, lane r = row r, and
-// eliminates column by column with shuffles.  Each thread then forms one row of
-// the panel below, L_ik = A_ik L_kk^-T, by substitution with the transposed
-// factor from shared memory.  CTA 0 stores L_kk in the block store at slot
-// dblk + k0 / kNB (identity outside w); the in-place diagonal block is left as it
-// was, since another CTA may still be reading it.
-constexpr int kPanelRows = 128;
-
+// ---- 32 x 32 Cholesky in one warp: lane r holds row r in registers ------------
+// Columns c < wb are eliminated (pivot broadcast by shuffle, scaled column, rank-1
+// update of the rows below); rows and columns from wb on must hold the identity.
 template <typename T>
-__global__ void __launch_bounds__(kPanelRows) k_panel(const MatDesc *__restrict__ desc, T *__restrict__ base, int k0,
-                                                      int *__restrict__ err, T *__restrict__ store) {
-  const MatDesc d = desc[blockIdx.y];
-  if (k0 >= d.e) return;
-  const int w = min(kNB, d.e - k0);
-  const int rbeg = k0 + w + blockIdx.x * kPanelRows;
-  if (rbeg >= d.m && blockIdx.x != 0) return;
-  T *A = base + d.off;
+__device__ __forceinline__ void warp_chol32(T (&a)[32], int lane, int wb, bool &bad) {
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    if (c < wb) {  // uniform across the warp
+      T piv = __shfl_sync(0xffffffffu, a[c], c);
+      if (!(piv > T(0))) { bad = true; piv = T(1); }
+      const T inv = drsqrt(piv), sd = piv * inv;
+      a[c] = (lane == c) ? sd : a[c] * inv;  // rows above c hold 0 here
+#pragma unroll
+      for (int t = c + 1; t < 32; ++t) {
+        const T lt = __shfl_sync(0xffffffffu, a[c], t);
+        if (lane >= t) a[t] -= a[c] * lt;
+      }
+    }
+  }
+}
+
+// ---- outer panel: partial Cholesky of the columns [K0, K0 + w), w <= kPW ---------
+// Two launches per outer panel.  The diagonal launch (ROWS = false, one CTA per
+// matrix) stages the w x w diagonal block (lower triangle, identity outside w) in
+// shared memory and factors it 32 columns at a time: warp 0 factors the 32 x 32
+// diagonal sub-block in registers, one thread per remaining row solves
+// x L_bb^T = a, and all threads apply the rank-32 update to the remaining columns
+// (4 x 4 register tiles over a transposed copy of the solved columns).  It writes
+// L_11 in place and the factored 32 x 32 diagonal sub-blocks to the block store
+// (slots dblk + K0 / 32 + q).  The rows launch (ROWS = true) then solves the rows
+// below, RB per CTA, the same way, reading the finished L_11 one 32-column slice at
+// a time instead of factoring it.
+constexpr int kPW = kEnginePanel;  // outer panel width
+constexpr int kLDP = kPW + 4;      // row stride of the staged panel (16-byte aligned rows)
+template <typename T> struct PanelRows;
+template <> struct PanelRows<float> { static constexpr int RB = 128; };
+template <> struct PanelRows<double> { static constexpr int RB = 16; };
+
+template <typename T, bool ROWS>
+constexpr size_t bigpanel_smem() {
+  constexpr int RB = PanelRows<T>::RB, NR = kPW + RB, NS = ROWS ? RB : kPW;
+  return sizeof(T) * ((size_t)NS * kLDP + 32 * NR + 32 * 32 + 32);
+}
+
+template <typename T, bool ROWS>
+__global__ void __launch_bounds__(256, ROWS ? 2 : 1) k_bigpanel(const MatDesc *__restrict__ desc, T *__restrict__ base, int K0,
+                                                     int *__restrict__ err, T *__restrict__ store) {
+  constexpr int RB = PanelRows<T>::RB, NR = kPW + RB;
+  constexpr int NS = ROWS ? RB : kPW;         // staged rows
+  constexpr int OWN0 = ROWS ? 0 : kPW;        // staged index of the first own row (rows launch only)
   using VT = typename Vec16<T>::V;
-  constexpr int VN = Vec16<T>::N, VPR = kNB / VN;
-  __shared__ __align__(16) T Lt[kNB][kNB];  // Lt[c][t] = L[t][c] for t >= c, 0 for t < c
-  __shared__ T rd[kNB];                     // 1 / L[c][c]
-  const int tid = threadIdx.x, lane = tid & 31;
-  const int row = rbeg + tid;
-  const bool has_row = row < d.m;
-  // this thread's panel row, all vector loads in flight together (a vector is read
-  // when it holds a column below w; it then ends within the padded row)
-  T x[kNB];
-  {
-    VT xv[VPR];
-    const T *src = A + (long long)(has_row ? row : 0) * d.ld + k0;
+  constexpr int VN = Vec16<T>::N, VPP = kPW / VN;  // vectors per staged row
+  const MatDesc d = desc[blockIdx.y];
+  if (K0 >= d.e) return;
+  const int w = min(kPW, d.e - K0);
+  const int rbeg = K0 + w + blockIdx.x * RB;
+  if (ROWS && rbeg >= d.m) return;
+  const int nrows = ROWS ? min(RB, d.m - rbeg) : 0;
+  T *A = base + d.off;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *P = reinterpret_cast<T *>(smem_raw);  // [NS][kLDP]: (diagonal rows,) own rows
+  T *PT = P + NS * kLDP;                   // [32][NR]: the current 32 columns, transposed (row p of the panel)
+  T *Lt = PT + 32 * NR;                    // [32][32]: Lt[c][t] = L_bb[t][c]
+  T *rd = Lt + 32 * 32;                    // [32]: 1 / L_bb[c][c]
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // panel row p (diagonal rows p < kPW, own rows kPW + q) -> staged row
+  auto prow = [&](int p) { return P + (p - kPW + OWN0) * kLDP; };
+  // ---- stage: kBatch vector loads in flight per thread and batch
+  constexpr int kVec = NS * VPP, kBatch = 8;
+  for (int base_i = 0; base_i < kVec; base_i += 256 * kBatch) {
+    VT buf[kBatch];
 #pragma unroll
-    for (int i = 0; i < VPR; ++i)
-      if (has_row && i * VN < w) xv[i] = *reinterpret_cast<const VT *>(src + i * VN);
-#pragma unroll
-    for (int i = 0; i < VPR; ++i) {
-      const T *e = reinterpret_cast<const T *>(&xv[i]);
-#pragma unroll
-      for (int u = 0; u < VN; ++u) x[i * VN + u] = (has_row && i * VN + u < w) ? e[u] : T(0);
+    for (int u = 0; u < kBatch; ++u) {
+      const int idx = base_i + tid + 256 * u;
+      const int sr = idx / VPP, cv = idx % VPP;
+      const bool diag = !ROWS && sr < kPW;
+      const bool ok = idx < kVec && cv * VN < w && (diag ? sr < w : sr - OWN0 < nrows);
+      const long long grow = diag ? K0 + sr : rbeg + sr - OWN0;
+      buf[u] = ok ? *reinterpret_cast<const VT *>(A + grow * d.ld + K0 + cv * VN) : VT{};
     }
-  }
-  if (tid < 32) {
-    T a[kNB];
-    {
-      VT dv[VPR];
-      const T *src = A + (long long)(k0 + (lane < w ? lane : 0)) * d.ld + k0;
 #pragma unroll
-      for (int i = 0; i < VPR; ++i)
-        if (lane < w && i * VN <= lane) dv[i] = *reinterpret_cast<const VT *>(src + i * VN);
-#pragma unroll
-      for (int i = 0; i < VPR; ++i) {
-        const T *e = reinterpret_cast<const T *>(&dv[i]);
-#pragma unroll
-        for (int u = 0; u < VN; ++u) {
-          const int t = i * VN + u;
-          a[t] = (lane < w && t <= lane) ? e[u] : (t == lane ? T(1) : T(0));
-        }
-      }
-    }
-    bool bad = false;
-#pragma unroll
-    for (int c = 0; c < kNB; ++c) {
-      if (c < w) {  // uniform across the warp
-        T piv = __shfl_sync(0xffffffffu, a[c], c);
-        if (!(piv > T(0))) { bad = true; piv = T(1); }
-        const T sd = dsqrt(piv), inv = T(1) / sd;
-        a[c] = (lane == c) ? sd : a[c] * inv;  // rows above c hold 0 here
-#pragma unroll
-        for (int t = c + 1; t < kNB; ++t) {
-          const T lt = __shfl_sync(0xffffffffu, a[c], t);
-          if (lane >= t) a[t] -= a[c] * lt;
-        }
-      }
-    }
-    if (bad && lane == 0 && blockIdx.x == 0) atomicOr(err, DEV_ERR_NOT_SPD);
-#pragma unroll
-    for (int t = 0; t < kNB; ++t) Lt[t][lane] = (t <= lane) ? a[t] : T(0);
-    rd[lane] = T(1) / a[lane];
-    if (blockIdx.x == 0) {
-      T *dst = store + ((long long)d.dblk + k0 / kNB) * kNB * kNB + lane * kNB;
-#pragma unroll
-      for (int i = 0; i < VPR; ++i) {
+    for (int u = 0; u < kBatch; ++u) {
+      const int idx = base_i + tid + 256 * u;
+      const int sr = idx / VPP, cv = idx % VPP;
+      if (idx < kVec) {
+        const bool diag = !ROWS && sr < kPW;
         VT o;
-        T *e = reinterpret_cast<T *>(&o);
 #pragma unroll
-        for (int u = 0; u < VN; ++u) e[u] = (i * VN + u <= lane) ? a[i * VN + u] : T(0);
-        *reinterpret_cast<VT *>(dst + i * VN) = o;
+        for (int q = 0; q < VN; ++q) {
+          const int j = cv * VN + q;
+          const T e = Vec16<T>::get(buf[u], q);
+          if (diag) Vec16<T>::set(o, q, (sr < w && j < w && j <= sr) ? e : (j == sr ? T(1) : T(0)));
+          else Vec16<T>::set(o, q, (sr - OWN0 < nrows && j < w) ? e : T(0));
+        }
+        *reinterpret_cast<VT *>(P + sr * kLDP + cv * VN) = o;
       }
     }
   }
-  __syncthreads();
-  if (!has_row) return;
-  // x L^T = a, right-looking over the columns; Lt rows are read as 16-byte vectors
+  bool bad = false;
+  const int nbk = ceil_div(w, 32);
+  for (int bq = 0; bq < nbk; ++bq) {
+    const int c0 = 32 * bq, wb = min(32, w - c0);
+    const int nbelow = max(0, w - c0 - 32);  // diagonal-block rows below the sub-block
+    __syncthreads();
+    if (wid == 0) {
+      T a[32];
+      {
+        const T *src = ROWS ? A + (long long)(K0 + c0 + (lane < wb ? lane : 0)) * d.ld + K0 + c0
+                            : P + (c0 + lane) * kLDP + c0;
 #pragma unroll
-  for (int c = 0; c < kNB; ++c) {
-    x[c] *= rd[c];
+        for (int i = 0; i < 32 / VN; ++i) {
+          const bool rd_ok = !ROWS || (lane < wb && i * VN <= lane);
+          const VT v = rd_ok ? *reinterpret_cast<const VT *>(src + i * VN) : VT{};
 #pragma unroll
-    for (int i = (c + 1) / VN; i < VPR; ++i) {
-      const VT lv = *reinterpret_cast<const VT *>(&Lt[c][i * VN]);
-      const T *e = reinterpret_cast<const T *>(&lv);
+          for (int q = 0; q < VN; ++q) {
+            const int t = i * VN + q;
+            a[t] = (lane < wb && t <= lane) ? Vec16<T>::get(v, q) : (t == lane ? T(1) : T(0));
+          }
+        }
+      }
+      if (!ROWS) warp_chol32(a, lane, wb, bad);
+      T dg = T(1);
 #pragma unroll
-      for (int u = 0; u < VN; ++u)
-        if (i * VN + u > c) x[i * VN + u] -= e[u] * x[c];
+      for (int t = 0; t < 32; ++t) {
+        const T v = (t <= lane) ? a[t] : T(0);
+        if (t == lane) dg = v;
+        if (!ROWS) P[(c0 + lane) * kLDP + c0 + t] = v;
+        Lt[t * 32 + lane] = v;
+      }
+      rd[lane] = T(1) / dg;
+      if (!ROWS) {
+        T *sb = store + ((long long)d.dblk + K0 / kNB + bq) * kNB * kNB + lane * kNB;
+#pragma unroll
+        for (int i = 0; i < 32 / VN; ++i) {
+          VT o;
+#pragma unroll
+          for (int q = 0; q < VN; ++q) Vec16<T>::set(o, q, (i * VN + q <= lane) ? a[i * VN + q] : T(0));
+          *reinterpret_cast<VT *>(sb + i * VN) = o;
+        }
+      }
+    } else if (ROWS) {
+      // the finished L_11 rows below the sub-block, columns [c0, c0 + 32), transposed
+      for (int idx = tid - 32; idx < nbelow * (32 / VN); idx += 256 - 32) {
+        const int r = idx / (32 / VN), cv = idx % (32 / VN), p = c0 + 32 + r;
+        const VT v = *reinterpret_cast<const VT *>(A + (long long)(K0 + p) * d.ld + K0 + c0 + cv * VN);
+#pragma unroll
+        for (int q = 0; q < VN; ++q) PT[(cv * VN + q) * NR + p] = Vec16<T>::get(v, q);
+      }
+    }
+    __syncthreads();
+    // rows below the sub-block: (diagonal rows [c0 + 32, w),) then the own rows
+    const int ndiag = ROWS ? 0 : nbelow;
+    const int nsolve = ndiag + nrows;
+    for (int qr = tid; qr < nsolve; qr += 256) {
+      const int p = qr < ndiag ? c0 + 32 + qr : kPW + (qr - ndiag);
+      T x[32];
+      T *src = prow(p) + c0;
+#pragma unroll
+      for (int i = 0; i < 32 / VN; ++i) {
+        const VT v = *reinterpret_cast<const VT *>(src + i * VN);
+#pragma unroll
+        for (int q = 0; q < VN; ++q) x[i * VN + q] = Vec16<T>::get(v, q);
+      }
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        x[c] *= rd[c];
+#pragma unroll
+        for (int i = (c + 1) / VN; i < 32 / VN; ++i) {
+          const VT lv = *reinterpret_cast<const VT *>(&Lt[c * 32 + i * VN]);
+#pragma unroll
+          for (int q = 0; q < VN; ++q)
+            if (i * VN + q > c) x[i * VN + q] -= Vec16<T>::get(lv, q) * x[c];
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 32 / VN; ++i) {
+        VT o;
+#pragma unroll
+        for (int q = 0; q < VN; ++q) Vec16<T>::set(o, q, x[i * VN + q]);
+        *reinterpret_cast<VT *>(src + i * VN) = o;
+      }
+#pragma unroll
+      for (int t = 0; t < 32; ++t) PT[t * NR + p] = x[t];
+    }
+    __syncthreads();
+    // rank-32 update of the panel columns [c0 + 32, w): rows as above (lower part for
+    // the diagonal rows), 4 x 4 tiles; tiles straddle no part (both parts 4-aligned)
+    const int jb = c0 + 32, ncol = w - jb;
+    if (ncol > 0) {
+      const int nd4 = (ndiag + 3) / 4, nr4 = (nrows + 3) / 4, nc4 = (ncol + 3) / 4;
+      const int ntiles = (nd4 + nr4) * nc4;
+      for (int mt = tid; mt < ntiles; mt += 256) {
+        const int rq = mt / nc4, cq = mt % nc4;
+        const bool own = rq >= nd4;
+        const int p0 = own ? kPW + 4 * (rq - nd4) : jb + 4 * rq;
+        const int j0 = jb + 4 * cq;
+        if (!own && p0 + 3 < j0) continue;  // strictly above the diagonal
+        T acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+          T av[4], bv[4];
+#pragma unroll
+          for (int i = 0; i < 4; i += VN) {
+            const VT x = *reinterpret_cast<const VT *>(&PT[k * NR + p0 + i]);
+            const VT y = *reinterpret_cast<const VT *>(&PT[k * NR + j0 + i]);
+#pragma unroll
+            for (int q = 0; q < VN; ++q) { av[i + q] = Vec16<T>::get(x, q); bv[i + q] = Vec16<T>::get(y, q); }
+          }
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] += av[i] * bv[j];
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const int p = p0 + i;
+          if (own ? (p - kPW >= nrows) : (p >= w)) continue;
+          T *row = prow(p);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (j0 + j < w) row[j0 + j] -= acc[i][j];
+        }
+      }
     }
   }
-  T *dst = A + (long long)row * d.ld + k0;
-#pragma unroll
-  for (int i = 0; i < VPR; ++i) {
-    if (i * VN >= w) continue;
-    if (i * VN + VN <= w) {
-      VT o;
-      T *e = reinterpret_cast<T *>(&o);
-#pragma unroll
-      for (int u = 0; u < VN; ++u) e[u] = x[i * VN + u];
-      *reinterpret_cast<VT *>(dst + i * VN) = o;
+  if (bad && tid == 0) atomicOr(err, DEV_ERR_NOT_SPD);
+  __syncthreads();
+  // own rows back to the matrix; the diagonal launch also writes L_11 (lower part)
+  for (int idx = tid; idx < nrows * VPP; idx += 256) {
+    const int q = idx / VPP, cv = idx % VPP;
+    if (cv * VN >= w) continue;
+    const T *src = P + (OWN0 + q) * kLDP + cv * VN;
+    T *dst = A + (long long)(rbeg + q) * d.ld + K0 + cv * VN;
+    if (cv * VN + VN <= w) {
+      *reinterpret_cast<VT *>(dst) = *reinterpret_cast<const VT *>(src);
     } else {
-#pragma unroll
-      for (int u = 0; u < VN; ++u)
-        if (i * VN + u < w) dst[i * VN + u] = x[i * VN + u];
+      for (int u = 0; cv * VN + u < w; ++u) dst[u] = src[u];
+    }
+  }
+  if (!ROWS) {
+    for (int idx = tid; idx < w * w; idx += 256) {
+      const int i = idx / w, j = idx % w;
+      if (j <= i) A[(long long)(K0 + i) * d.ld + K0 + j] = P[i * kLDP + j];
     }
   }
 }
@@ -380,35 +520,27 @@ template <typename T>
 void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s,
                              T *store, ProfHook *prof, bool tc) {
   if (sh.count == 0) return;
-  const int ob = std::max(kNB, (sh.ob / kNB) * kNB);
-  for (int K0 = 0; K0 < sh.max_e; K0 += ob) {
-    const int K1 = K0 + ob;
-    for (int k0 = K0; k0 < std::min(K1, sh.max_e); k0 += kNB) {
-      int max_below = 0, max_cols = 0;
-      double fl_panel = 0.0, fl_upd = 0.0, by_upd = 0.0;
-      for (int b = 0; b < sh.count; ++b) {
-        if (k0 >= sh.e[b]) continue;
-        const int w = std::min(kNB, sh.e[b] - k0);
-        const int below = sh.m[b] - k0 - w;
-        const int cend = std::min(K1, sh.e[b]);
-        max_below = std::max(max_below, below);
-        max_cols = std::max(max_cols, cend - k0 - w);
-        fl_panel += (double)w * w * w / 3.0 + (double)below * w * w;
-        const double ent = trapezoid(k0 + w, cend, sh.m[b]);
-        fl_upd += 2.0 * w * ent;
-        by_upd += sizeof(T) * (2.0 * ent + (double)w * (below + cend - k0 - w));
-      }
-      if (prof) prof->begin(PROF_PANEL, s);
-      dim3 gp(std::max(1, ceil_div(max_below, kPanelRows)), sh.count);
-      k_panel<T><<<gp, kPanelRows, 0, s>>>(d_desc, base, k0, d_err, store);
-      count_launch();
-      if (prof) prof->end(PROF_PANEL, s, fl_panel, 0.0);
-      if (max_below > 0 && max_cols > 0) {
-        if (prof) prof->begin(PROF_RANKK, s);
-        launch_rankk<T>(d_desc, base, 0, k0, K0, K1, max_below, max_cols, sh.count, s);
-        if (prof) prof->end(PROF_RANKK, s, fl_upd, by_upd);
-      }
+  constexpr int RB = PanelRows<T>::RB;
+  for (int K0 = 0; K0 < sh.max_e; K0 += kPW) {
+    const int K1 = K0 + kPW;
+    int max_below = 0;
+    double fl_panel = 0.0;
+    for (int b = 0; b < sh.count; ++b) {
+      if (K0 >= sh.e[b]) continue;
+      const int w = std::min(kPW, sh.e[b] - K0);
+      const int below = sh.m[b] - K0 - w;
+      max_below = std::max(max_below, below);
+      fl_panel += (double)w * w * w / 3.0 + (double)below * w * w;
     }
+    if (prof) prof->begin(PROF_PANEL, s);
+    k_bigpanel<T, false><<<dim3(1, sh.count), 256, bigpanel_smem<T, false>(), s>>>(d_desc, base, K0, d_err, store);
+    count_launch();
+    if (max_below > 0) {
+      k_bigpanel<T, true><<<dim3(ceil_div(max_below, RB), sh.count), 256, bigpanel_smem<T, true>(), s>>>(
+          d_desc, base, K0, d_err, store);
+      count_launch();
+    }
+    if (prof) prof->end(PROF_PANEL, s, fl_panel, 0.0);
     // outer update of the trailing columns [K1, e) with the finished outer panel
     int max_rows = 0, max_cols = 0;
     double fl = 0.0, by = 0.0;
@@ -417,8 +549,8 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
       max_rows = std::max(max_rows, sh.m[b] - K1);
       max_cols = std::max(max_cols, sh.e[b] - K1);
       const double ent = trapezoid(K1, sh.e[b], sh.m[b]);
-      fl += 2.0 * ob * ent;
-      by += sizeof(T) * (2.0 * ent + (double)ob * (sh.m[b] - K1));
+      fl += 2.0 * kPW * ent;
+      by += sizeof(T) * (2.0 * ent + (double)kPW * (sh.m[b] - K1));
     }
     if (max_rows > 0 && max_cols > 0) {
       if (prof) prof->begin(PROF_RANKK, s);
@@ -717,6 +849,14 @@ size_t dense_smem_limit() { return 200 * 1024; }
 bool dense_configure() {
   const int lim = (int)dense_smem_limit();
   bool ok = true;
+  ok &= cudaFuncSetAttribute(k_bigpanel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bigpanel_smem<float, false>()) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_bigpanel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bigpanel_smem<float, true>()) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_bigpanel<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bigpanel_smem<double, false>()) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_bigpanel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)bigpanel_smem<double, true>()) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_trsv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_trsv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
@@ -728,7 +868,7 @@ bool dense_configure() {
 
 #define BD_INST(T)                                                                                              \
   template void engine_partial_cholesky<T>(const EngineShape &, const MatDesc *, T *, int *, cudaStream_t,    \
-                                           T *, ProfHook *, bool);     \
+                                           T *, ProfHook *, bool);                                             \
   template void launch_gemv<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *,        \
                                double *, double, const int *, cudaStream_t);                                   \
   template void launch_gemv_t<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *,      \

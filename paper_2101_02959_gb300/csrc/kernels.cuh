@@ -57,12 +57,13 @@ struct EngineShape {
   int count;
   int max_e, max_m;
   std::vector<int> m, e;  // host copies for per-step grid sizes
-  int ob = 256;           // outer panel width (columns per trailing long-K update)
 };
-// store: block store receiving the factored kNB x kNB diagonal blocks L_kk; matrix b
-// uses slots [desc[b].dblk, desc[b].dblk + ceil(e_b / kNB)) (row-major, identity
-// outside the last block's width).  The in-place diagonal blocks are not factored.
-// tc: FP32 only, run the long-K updates on the tensor cores (tc.cu).
+// The engine works through outer panels of kEnginePanel columns (k_bigpanel), each
+// followed by one long-K update of the trailing columns.  store: block store
+// receiving the factored kNB x kNB diagonal blocks L_kk; matrix b uses slots
+// [desc[b].dblk, desc[b].dblk + ceil(e_b / kNB)) (row-major, identity outside the last
+// block's width).  tc: FP32 only, run the long-K updates on the tensor cores (tc.cu).
+constexpr int kEnginePanel = 128;
 template <typename T>
 void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s,
                              T *store, ProfHook *prof = nullptr, bool tc = false);
