@@ -211,6 +211,7 @@ struct bd_handle {
   int nt_tot = 0;
   int *d_tl_sub, *d_tl_loc, *d_tl_ptr, *d_tl_row, *d_tl_off;
   double *d_tl_val;
+  float *d_tl_valf;  // float copy of d_tl_val for the FP32 augmented-matrix build
   // dense layouts
   EngineShape shK, shA, shC, shCo;
   MatDesc *d_Kdesc, *d_Adesc, *d_Cdesc, *d_Codesc;
@@ -505,7 +506,8 @@ void setup_handle(bd_handle &h) {
     }
     h.nt_tot = (int)tl_sub.size();
     h.d_tl_sub = m.upload(tl_sub, s); h.d_tl_loc = m.upload(tl_loc, s); h.d_tl_ptr = m.upload(tl_ptr, s);
-    h.d_tl_row = m.upload(tl_row, s); h.d_tl_val = m.upload(tl_val, s); h.d_tl_off = m.upload(tl_off, s);
+    h.d_tl_row = m.upload(tl_row, s); h.d_tl_val = m.upload(tl_val, s);
+    h.d_tl_valf = m.upload(std::vector<float>(tl_val.begin(), tl_val.end()), s); h.d_tl_off = m.upload(tl_off, s);
   }
   // ---- dense layouts
   std::vector<MatDesc> kd(S), ad(S);
@@ -852,10 +854,11 @@ void linearize_t(bd_handle &h, Dense<T> &D) {
                            h.tau, h.d_Kdesc, D.K, s);
   run_engine_groups<T>(h, h.shK, h.d_Kdesc, D.K, D.LdK);
   launch_copy<T, T>(h.cp_sorig.n, h.cp_sorig.max_elems, h.cp_sorig.d, D.K, D.Sorig, s);
-  long long max_a = 0;
-  for (int j = 0; j < h.nsub; ++j) max_a = std::max(max_a, (long long)h.shA.m[j] * h.shA.m[j]);
-  launch_build_aug<T>(h.nsub, max_a, h.d_Sdesc, D.Sorig, h.d_Adesc, D.Aug, h.d_nD, h.d_tl_off, h.d_tl_ptr,
-                      h.d_tl_row, h.d_tl_val, s);
+  const T *tval;
+  if constexpr (std::is_same<T, float>::value) tval = h.d_tl_valf;
+  else tval = h.d_tl_val;
+  launch_build_aug<T>(h.nsub, h.shA.max_m, h.d_Sdesc, D.Sorig, h.d_Adesc, D.Aug, h.d_nD, h.d_tl_off, h.d_tl_ptr,
+                      h.d_tl_row, tval, s);
   launch_copy<T, T>(h.cp_sdd.n, h.cp_sdd.max_elems, h.cp_sdd.d, D.Aug, D.SDD, s);
   launch_copy<T, T>(h.cp_blk.n, h.cp_blk.max_elems, h.cp_blk.d, D.Aug, D.Blk, s);
   run_engine_groups<T>(h, h.shA, h.d_Adesc, D.Aug, D.Linv);
@@ -877,38 +880,48 @@ void linearize(bd_handle &h) {
 
 // ---- operators (device vectors; `done` = early-exit flag of a Krylov loop) ----
 template <class T>
-void schur_t(bd_handle &h, Dense<T> &D, const double *x, double *y, const int *done) {
+// f: the PCG reduction to fuse into the last kernel (nullptr: none)
+void schur_t(bd_handle &h, Dense<T> &D, const double *x, double *y, const int *done, const DotFuse *f = nullptr) {
   h.prof.begin(PROF_GEMV, h.s);
   launch_gemv<T>(h.gv_schur.n, h.gv_schur.max_rows, h.gv_schur.max_cols, h.gv_schur.d, D.Sorig, x, h.d_R, h.d_yloc,
                  1.0, done, h.s);
   h.prof.end(PROF_GEMV, h.s, h.gemv_schur_flops, h.gemv_schur_bytes * sizeof(T));
-  launch_gather_sum(h.nif, h.d_Rt_ptr, h.d_Rt_idx, h.d_yloc, y, h.gauge_iface, 1.0, nullptr, done, h.s);
+  if (f) launch_gather_sum_dot(h.nif, h.d_Rt_ptr, h.d_Rt_idx, h.d_yloc, y, h.gauge_iface, *f, h.s);
+  else launch_gather_sum(h.nif, h.d_Rt_ptr, h.d_Rt_idx, h.d_yloc, y, h.gauge_iface, 1.0, nullptr, done, h.s);
 }
 
 // St^-1 applied to (primal part rP or 0, local dual parts rD): zbar[nd:] = z_Pi, ydc[0:nD_tot] = z_Delta.
+// rP_csr: the primal part as a sparse product instead (rP unused).
 template <class T>
-void st_inv_t(bd_handle &h, Dense<T> &D, const double *rP, const double *rD, const int *done) {
+void st_inv_t(bd_handle &h, Dense<T> &D, const double *rP, const double *rD, const int *done,
+              const CsrIn *rP_csr = nullptr) {
   h.prof.begin(PROF_GEMV, h.s);
   launch_gemv<T>(h.gv_local.n, h.gv_local.max_rows, h.gv_local.max_cols, h.gv_local.d, D.Z, rD, nullptr, h.d_ydc,
                  1.0, done, h.s);
   h.prof.end(PROF_GEMV, h.s, h.gemv_local_flops, h.gemv_local_bytes * sizeof(T));
-  launch_gather_sum(h.np, h.d_pl_ptr, h.d_pl_idx, h.d_ydc + h.nD_tot, h.d_crhs, h.gauge_primal, -1.0, rP, done, h.s);
+  launch_gather_sum(h.np, h.d_pl_ptr, h.d_pl_idx, h.d_ydc + h.nD_tot, h.d_crhs, h.gauge_primal, -1.0,
+                    rP_csr ? nullptr : rP, done, h.s, rP_csr);
   launch_gemv<T>(1, h.np, h.np, h.gv_coarse.d, D.CoInv, h.d_crhs, nullptr, h.d_zbar, 1.0, done, h.s);
   launch_gemv_t<T>(h.gv_psit.n, h.gv_psit.max_rows, h.gv_psit.max_cols, h.gv_psit.d, D.Z, h.d_zbar, h.d_prim_x,
                    h.d_ydc, -1.0, done, h.s);
 }
 
 template <class T>
-void bddc_t(bd_handle &h, Dense<T> &D, const double *r, double *z, const int *done) {
-  launch_spmv(h.nd + h.np, h.d_Tt_ptr, h.d_Tt_col, h.d_Tt_val, r, h.d_rbar, h.nd + h.gauge_primal, done, h.s);
-  // deluxe restriction r_C^(j) = D_C^(j)T rbar_C (one thread per output, column reads)
-  launch_gemv_t<T>(h.gv_drest.n, h.gv_drest.max_rows, h.gv_drest.max_cols, h.gv_drest.d, D.Dd, h.d_rbar, nullptr,
-                   h.d_rD, 1.0, done, h.s);
-  st_inv_t(h, D, h.d_rbar + h.nd, h.d_rD, done);
+// rbar = T^T r is never stored: the deluxe restriction evaluates its dual rows while
+// staging, the coarse right-hand side its primal rows (row nd + gauge_primal is
+// zeroed there).  f: the PCG reduction to fuse into the last kernel.
+void bddc_t(bd_handle &h, Dense<T> &D, const double *r, double *z, const int *done, const DotFuse *f = nullptr) {
+  const CsrIn rbar{h.d_Tt_ptr, h.d_Tt_col, h.d_Tt_val, r};
+  const CsrIn rbar_p{h.d_Tt_ptr + h.nd, h.d_Tt_col, h.d_Tt_val, r};
+  // deluxe restriction r_C^(j) = D_C^(j)T rbar_C
+  launch_gemv_t<T>(h.gv_drest.n, h.gv_drest.max_rows, h.gv_drest.max_cols, h.gv_drest.d, D.Dd, nullptr, nullptr,
+                   h.d_rD, 1.0, done, h.s, &rbar);
+  st_inv_t(h, D, nullptr, h.d_rD, done, &rbar_p);
   // deluxe extension zbar_C = sum_j D_C^(j) z_C^(j) (one row of [D^(j1) | D^(j2) | ...] per output)
   launch_gemv<T>(h.gv_dext.n, h.gv_dext.max_rows, h.gv_dext.max_cols, h.gv_dext.d, D.Dd, h.d_ydc, h.d_ext_idx,
                  h.d_zbar, 1.0, done, h.s);
-  launch_spmv(h.nif, h.d_T_ptr, h.d_T_col, h.d_T_val, h.d_zbar, z, h.gauge_iface, done, h.s);
+  if (f) launch_spmv_dot(h.nif, h.d_T_ptr, h.d_T_col, h.d_T_val, h.d_zbar, z, h.gauge_iface, *f, h.s);
+  else launch_spmv(h.nif, h.d_T_ptr, h.d_T_col, h.d_T_val, h.d_zbar, z, h.gauge_iface, done, h.s);
 }
 
 template <class T>
@@ -931,8 +944,8 @@ void feti_M_t(bd_handle &h, Dense<T> &D, const double *mu, double *y, const int 
 // ---- device-side PCG ---------------------------------------------------------
 constexpr int kChunk = 8;
 
-template <class Op, class Pc>
-int pcg(bd_handle &h, int n, const double *b, double *x, Op A, Pc M, bd_solve_stats *st) {
+template <class Op, class Pc, class OpF, class PcF>
+int pcg(bd_handle &h, int n, const double *b, double *x, Op A, Pc M, bd_solve_stats *st, OpF AF, PcF MF) {
   cudaStream_t s = h.s;
   KrylovState ks{};
   ks.rtol = std::min(h.opt.ksp_rtol * h.rtol_scale, 0.1);
@@ -950,12 +963,20 @@ int pcg(bd_handle &h, int n, const double *b, double *x, Op A, Pc M, bd_solve_st
   launch_copy_vec(n, h.d_kz, h.d_kp, done, s);
   KrylovState out{};
   auto body = [&]() {
+    // AF / MF apply the operator / preconditioner with the following reduction fused
+    // into their last kernel and return true, or return false to leave it separate
+    const DotFuse f0{0, h.d_kp, h.d_partial, h.d_counter, h.d_ks, h.d_ha};
+    const DotFuse f1{1, h.d_kr, h.d_partial, h.d_counter, h.d_ks, h.d_ha};
     for (int c = 0; c < kChunk; ++c) {
-      A(h.d_kp, h.d_kq, done);
-      launch_pcg_dot_step(n, 0, h.d_kp, h.d_kq, nullptr, nullptr, h.d_partial, h.d_counter, h.d_ks, h.d_ha, s);
+      if (!AF(h.d_kp, h.d_kq, done, f0)) {
+        A(h.d_kp, h.d_kq, done);
+        launch_pcg_dot_step(n, 0, h.d_kp, h.d_kq, nullptr, nullptr, h.d_partial, h.d_counter, h.d_ks, h.d_ha, s);
+      }
       launch_pcg_xr(n, h.d_ks, h.d_kp, h.d_kq, x, h.d_kr, s);
-      M(h.d_kr, h.d_kz, done);
-      launch_pcg_dot_step(n, 1, h.d_kr, h.d_kz, h.d_kz, h.d_kz, h.d_partial, h.d_counter, h.d_ks, h.d_ha, s);
+      if (!MF(h.d_kr, h.d_kz, done, f1)) {
+        M(h.d_kr, h.d_kz, done);
+        launch_pcg_dot_step(n, 1, h.d_kr, h.d_kz, h.d_kz, h.d_kz, h.d_partial, h.d_counter, h.d_ks, h.d_ha, s);
+      }
       launch_pcg_p(n, h.d_ks, h.d_kz, h.d_kp, s);
     }
   };
@@ -1074,8 +1095,16 @@ int solve_t(bd_handle &h, Dense<T> &D, const double *fi, const double *fe, doubl
     launch_gather_sum(h.nif, h.d_Rt_ptr, h.d_Rt_idx, h.d_yloc, h.d_fhat, h.gauge_iface, -1.0, h.d_fG, nullptr, s);
     auto A = [&](const double *x, double *y, const int *dn) { schur_t(h, D, x, y, dn); };
     auto M = [&](const double *x, double *y, const int *dn) { bddc_t(h, D, x, y, dn); };
+    auto AF = [&](const double *x, double *y, const int *dn, const DotFuse &f) {
+      schur_t(h, D, x, y, dn, &f);
+      return true;
+    };
+    auto MF = [&](const double *x, double *y, const int *dn, const DotFuse &f) {
+      bddc_t(h, D, x, y, dn, &f);
+      return true;
+    };
     reason = h.opt.krylov == BD_GMRES ? gmres(h, h.nif, h.d_fhat, h.d_uG, A, M, st)
-                                      : pcg(h, h.nif, h.d_fhat, h.d_uG, A, M, st);
+                                      : pcg(h, h.nif, h.d_fhat, h.d_uG, A, M, st, AF, MF);
   } else {
     // f~: local g = f_G[R] / mult - L_GI y_I, gbar = T_loc^T g -> (rD, gP); rP = sum gP
     launch_gather_scale_sub(h.nG_tot, h.d_R, h.d_fG, h.d_mult_iface, h.d_yloc, s);
@@ -1086,8 +1115,9 @@ int solve_t(bd_handle &h, Dense<T> &D, const double *fi, const double *fe, doubl
     launch_jump(h.nlt, h.max_nc, h.d_lt, h.d_pairs, h.d_ydc, h.d_kb, nullptr, s);
     auto A = [&](const double *x, double *y, const int *dn) { feti_F_t(h, D, x, y, dn); };
     auto M = [&](const double *x, double *y, const int *dn) { feti_M_t(h, D, x, y, dn); };
+    auto unfused = [](const double *, double *, const int *, const DotFuse &) { return false; };
     reason = h.opt.krylov == BD_GMRES ? gmres(h, h.nlam, h.d_kb, h.d_kx, A, M, st)
-                                      : pcg(h, h.nlam, h.d_kb, h.d_kx, A, M, st);
+                                      : pcg(h, h.nlam, h.d_kb, h.d_kx, A, M, st, unfused, unfused);
     // w = St^-1 (f~ - B^T lambda); u_G = T (dual mean, primal)
     launch_jump_t(h.nwt, h.max_nc, h.d_wt, h.d_went, h.d_kx, h.d_w1, nullptr, s);
     launch_axpby(h.nD_tot, 1.0, h.d_rD2, -1.0, h.d_w1, s);

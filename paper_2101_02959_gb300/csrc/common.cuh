@@ -53,4 +53,16 @@ struct GemvDesc {
 
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
+// A sparse product used as a kernel operand: entry i = sum_k val[k] v[col[k]] over
+// k in [ptr[i], ptr[i + 1]); ptr == nullptr means "not used".
+struct CsrIn {
+  const int *ptr, *col;
+  const double *val, *v;
+};
+__device__ __forceinline__ double csr_row(const CsrIn &c, int i) {
+  double a = 0.0;
+  for (int k = c.ptr[i]; k < c.ptr[i + 1]; ++k) a += c.val[k] * c.v[c.col[k]];
+  return a;
+}
+
 }  // namespace bd

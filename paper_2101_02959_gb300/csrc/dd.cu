@@ -40,59 +40,89 @@ __global__ void k_assemble_local(int nq, const int *__restrict__ q_sub, const in
 
 // ---- block copies ------------------------------------------------------------
 template <typename TS, typename TD>
-__global__ void k_copy(const CopyTask *__restrict__ tasks, const TS *__restrict__ src, TD *__restrict__ dst) {
+__global__ void __launch_bounds__(256) k_copy(const CopyTask *__restrict__ tasks, const TS *__restrict__ src,
+                                              TD *__restrict__ dst) {
+  // 32 x 32 tiles through shared memory, so reads and writes stay coalesced however
+  // the tile is transposed.  mode 0: dst(i, k) = src(r0 + i, c0 + k); mode 1:
+  // dst(i, k) = src(r0 + k, c0 + i); modes 2 and 3: the full symmetric matrix from
+  // the lower triangle, dst(i, k) = src(r0 + max, c0 + min).  sign is +1 or -1.
   const CopyTask c = tasks[blockIdx.y];
-  const long long tot = (long long)c.rows * c.cols;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(t / c.cols), k = (int)(t % c.cols);
-    int r, cc;
-    if (c.mode == 3) {  // lower entry (i, k), k <= i, read along k; written to both halves
-      if (k > i) continue;
-      const TD v = (TD)(c.sign * (double)src[c.src_off + (long long)(c.r0 + i) * c.src_ld + c.c0 + k]);
-      dst[c.dst_off + (long long)i * c.dst_ld + k] = v;
-      dst[c.dst_off + (long long)k * c.dst_ld + i] = v;
-      continue;
+  __shared__ TS tD[32][33], tT[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int ntr = (c.rows + 31) / 32, ntc = (c.cols + 31) / 32;
+  const bool sym = c.mode >= 2;
+  const bool neg = c.sign < 0.0;
+  for (int tile = blockIdx.x; tile < ntr * ntc; tile += gridDim.x) {
+    const int i0 = (tile / ntc) * 32, k0 = (tile % ntc) * 32;
+    const bool need_d = c.mode == 0 || (sym && i0 + 31 >= k0);
+    const bool need_t = c.mode == 1 || (sym && k0 + 31 > i0);
+    __syncthreads();
+    if (need_d) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int i = i0 + ty + 8 * q, k = k0 + tx;
+        if (i < c.rows && k < c.cols && (!sym || i >= k))
+          tD[ty + 8 * q][tx] = src[c.src_off + (long long)(c.r0 + i) * c.src_ld + c.c0 + k];
+      }
     }
-    if (c.mode == 0) { r = c.r0 + i; cc = c.c0 + k; }
-    else if (c.mode == 1) { r = c.r0 + k; cc = c.c0 + i; }
-    else { r = c.r0 + max(i, k); cc = c.c0 + min(i, k); }
-    dst[c.dst_off + (long long)i * c.dst_ld + k] = (TD)(c.sign * (double)src[c.src_off + (long long)r * c.src_ld + cc]);
+    if (need_t) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int kk = k0 + ty + 8 * q, ii = i0 + tx;  // element (ii, kk) of dst
+        if (ii < c.rows && kk < c.cols && (!sym || kk > ii))
+          tT[ty + 8 * q][tx] = src[c.src_off + (long long)(c.r0 + kk) * c.src_ld + c.c0 + ii];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int i = i0 + ty + 8 * q, k = k0 + tx;
+      if (i < c.rows && k < c.cols) {
+        const bool direct = c.mode == 0 || (sym && i >= k);
+        const TS v = direct ? tD[ty + 8 * q][tx] : tT[tx][ty + 8 * q];
+        dst[c.dst_off + (long long)i * c.dst_ld + k] = (TD)(neg ? -v : v);
+      }
+    }
   }
 }
 
 // ---- augmented matrix of the constrained local problem ------------------------
 // Aug = [[Sb_DD, Sb_DP, I], [Sb_PD, Sb_PP, 0], [I, 0, 0]] with Sb = T^T S T
 // (change of basis for the primal averages), S read from the full symmetric
-// copy of S_Gamma.  T_loc is CSC by transformed dof.  One thread per entry.
+// copy of S_Gamma.  T_loc is CSC by transformed dof.  One warp per row a, lanes
+// over the columns b <= a (the factorisation and the copies read the lower
+// triangle only); sums in the matrix precision.
 template <typename T>
-__global__ void k_build_aug(const MatDesc *__restrict__ sdesc, const T *__restrict__ sbase,
-                            const MatDesc *__restrict__ adesc, T *__restrict__ abase,
-                            const int *__restrict__ nD, const int *__restrict__ tptr_off,
-                            const int *__restrict__ tptr, const int *__restrict__ trow,
-                            const double *__restrict__ tval) {
+__global__ void __launch_bounds__(256) k_build_aug(const MatDesc *__restrict__ sdesc, const T *__restrict__ sbase,
+                                                   const MatDesc *__restrict__ adesc, T *__restrict__ abase,
+                                                   const int *__restrict__ nD, const int *__restrict__ tptr_off,
+                                                   const int *__restrict__ tptr, const int *__restrict__ trow,
+                                                   const T *__restrict__ tval) {
   const int j = blockIdx.y;
   const MatDesc ad = adesc[j];
-  const long long tot = (long long)ad.m * ad.m;
+  const int a = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (a >= ad.m) return;
   const MatDesc sd = sdesc[j];
   const int nd = nD[j];
   const int nt = ad.m - nd;  // nD + nP
   const int *P = tptr + tptr_off[j];
   const T *S = sbase + sd.off;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < tot; t += (long long)gridDim.x * blockDim.x) {
-    const int a = (int)(t / ad.m), b = (int)(t % ad.m);
-    if (b > a) continue;  // the factorisation and the copies read the lower triangle only
-    double v = 0.0;
+  T *arow = abase + ad.off + (long long)a * ad.ld;
+  const int pa0 = a < nt ? P[a] : 0, pa1 = a < nt ? P[a + 1] : 0;
+  for (int b = lane; b <= a; b += 32) {
+    T v = T(0);
     if (a < nt && b < nt) {
-      for (int p = P[a]; p < P[a + 1]; ++p)
-        for (int q = P[b]; q < P[b + 1]; ++q) {
-          v += tval[p] * tval[q] * (double)S[(long long)trow[p] * sd.ld + trow[q]];
-        }
+      const int pb0 = P[b], pb1 = P[b + 1];
+      for (int p = pa0; p < pa1; ++p) {
+        const T *srow = S + (long long)trow[p] * sd.ld;
+        T acc = T(0);
+        for (int q = pb0; q < pb1; ++q) acc += tval[q] * srow[trow[q]];
+        v += tval[p] * acc;
+      }
     } else if (a >= nt && b < nd) {
-      v = (a - nt == b) ? 1.0 : 0.0;
-    } else if (b >= nt && a < nd) {
-      v = (b - nt == a) ? 1.0 : 0.0;
+      v = (a - nt == b) ? T(1) : T(0);
     }
-    abase[ad.off + (long long)a * ad.ld + b] = (T)v;
+    arow[b] = v;
   }
 }
 
@@ -153,9 +183,10 @@ __global__ void k_spmv(int n, const int *__restrict__ ptr, const int *__restrict
 }
 
 // y[g] = sum of the listed local values (interface assembly R^T), y[zero] = 0.
+// The addend may instead be a sparse product evaluated on the fly (add_csr.ptr set).
 __global__ void k_gather_sum(int n, const int *__restrict__ ptr, const int *__restrict__ idx,
                              const double *__restrict__ src, double *__restrict__ y, int zero, double alpha,
-                             const double *__restrict__ addend, const int *__restrict__ done) {
+                             const double *__restrict__ addend, const int *__restrict__ done, const CsrIn add_csr) {
   if (done && *done) return;
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
@@ -163,6 +194,7 @@ __global__ void k_gather_sum(int n, const int *__restrict__ ptr, const int *__re
   for (int k = ptr[r]; k < ptr[r + 1]; ++k) acc += src[idx[k]];
   double v = alpha * acc;
   if (addend) v += addend[r];
+  else if (add_csr.ptr) v += csr_row(add_csr, r);
   y[r] = (r == zero) ? 0.0 : v;
 }
 
@@ -423,20 +455,13 @@ __global__ void k_pcg_p(int n, const KrylovState *__restrict__ ks, const double 
 
 // Fused PCG reductions: every block writes its partial sums; the last block to
 // finish (counter) adds the partials in block order (deterministic) and applies
-// the scalar recurrence.  which = 0: p.q -> alpha; which = 1: (r.z, z.z) -> beta and
-// the convergence test.
-__global__ void k_pcg_dot_step(int n, int which, const double *__restrict__ a0, const double *__restrict__ b0,
-                               const double *__restrict__ a1, const double *__restrict__ b1,
-                               double *__restrict__ partial, unsigned int *__restrict__ counter,
-                               KrylovState *__restrict__ ks, double *__restrict__ hist) {
-  if (ks->done) return;
+// the scalar recurrence.  which = 0: s0 = p.q -> alpha; which = 1: s0 = r.z,
+// s1 = z.z -> beta and the convergence test.  Every thread of the block calls it.
+__device__ void pcg_dot_tail(int which, double s0, double s1, double *__restrict__ partial,
+                             unsigned int *__restrict__ counter, KrylovState *__restrict__ ks,
+                             double *__restrict__ hist) {
   __shared__ double sh[32];
   __shared__ bool last;
-  double s0 = 0.0, s1 = 0.0;
-  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
-    s0 += a0[x] * b0[x];
-    if (a1) s1 += a1[x] * b1[x];
-  }
   s0 = block_sum(s0, sh);
   s1 = block_sum(s1, sh);
   if (threadIdx.x == 0) {
@@ -472,6 +497,53 @@ __global__ void k_pcg_dot_step(int n, int which, const double *__restrict__ a0, 
   ks->beta = t0 / ks->rz;
   if (ks->it - 1 < ks->hist_cap) hist[ks->hist_cap + ks->it - 1] = ks->beta;
   ks->rz = t0;
+}
+
+__global__ void k_pcg_dot_step(int n, int which, const double *__restrict__ a0, const double *__restrict__ b0,
+                               const double *__restrict__ a1, const double *__restrict__ b1,
+                               double *__restrict__ partial, unsigned int *__restrict__ counter,
+                               KrylovState *__restrict__ ks, double *__restrict__ hist) {
+  if (ks->done) return;
+  double s0 = 0.0, s1 = 0.0;
+  for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+    s0 += a0[x] * b0[x];
+    if (a1) s1 += a1[x] * b1[x];
+  }
+  pcg_dot_tail(which, s0, s1, partial, counter, ks, hist);
+}
+
+// y = interface assembly (as k_gather_sum, alpha = 1, no addend) fused with the PCG
+// reduction of the operator output: s0 = a.y (and s1 = y.y when which = 1).
+__global__ void k_gather_sum_dot(int n, const int *__restrict__ ptr, const int *__restrict__ idx,
+                                 const double *__restrict__ src, double *__restrict__ y, int zero, DotFuse f) {
+  if (f.ks->done) return;
+  double s0 = 0.0, s1 = 0.0;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int k = ptr[r]; k < ptr[r + 1]; ++k) acc += src[idx[k]];
+    const double v = (r == zero) ? 0.0 : acc;
+    y[r] = v;
+    s0 += f.a[r] * v;
+    s1 += v * v;
+  }
+  pcg_dot_tail(f.which, s0, f.which ? s1 : 0.0, f.partial, f.counter, f.ks, f.hist);
+}
+
+// y = A x (CSR, as k_spmv) fused with the PCG reduction of the output.
+__global__ void k_spmv_dot(int n, const int *__restrict__ ptr, const int *__restrict__ col,
+                           const double *__restrict__ val, const double *__restrict__ x, double *__restrict__ y,
+                           int zero, DotFuse f) {
+  if (f.ks->done) return;
+  double s0 = 0.0, s1 = 0.0;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int k = ptr[r]; k < ptr[r + 1]; ++k) acc += val[k] * x[col[k]];
+    const double v = (r == zero) ? 0.0 : acc;
+    y[r] = v;
+    s0 += f.a[r] * v;
+    s1 += v * v;
+  }
+  pcg_dot_tail(f.which, s0, f.which ? s1 : 0.0, f.partial, f.counter, f.ks, f.hist);
 }
 
 // dots with an early exit (Krylov loop): partial sums then a fixed-order finalize
@@ -521,16 +593,16 @@ void launch_assemble_local(int nq, const int *q_sub, const int *q_loc, const int
 template <typename TS, typename TD>
 void launch_copy(int ntasks, long long max_elems, const CopyTask *tasks, const TS *src, TD *dst, cudaStream_t s) {
   if (ntasks == 0 || max_elems == 0) return;
-  const int gx = (int)std::min<long long>((max_elems + 255) / 256, 4096);
+  const int gx = (int)std::min<long long>((max_elems + 1023) / 1024, 4096);
   k_copy<TS, TD><<<dim3(gx, ntasks), 256, 0, s>>>(tasks, src, dst);
   count_launch();
 }
 
 template <typename T>
-void launch_build_aug(int nsub, long long max_elems, const MatDesc *sdesc, const T *sbase, const MatDesc *adesc,
+void launch_build_aug(int nsub, int max_m, const MatDesc *sdesc, const T *sbase, const MatDesc *adesc,
                       T *abase, const int *nD, const int *tptr_off, const int *tptr, const int *trow,
-                      const double *tval, cudaStream_t s) {
-  const int gx = (int)std::min<long long>((max_elems + 255) / 256, 8192);
+                      const T *tval, cudaStream_t s) {
+  const int gx = ceil_div(max_m, 8);
   k_build_aug<T><<<dim3(gx, nsub), 256, 0, s>>>(sdesc, sbase, adesc, abase, nD, tptr_off, tptr, trow, tval);
   count_launch();
 }
@@ -561,6 +633,18 @@ void launch_small_gemm(int ntasks, int max_n, const GemmTask *tasks, const T *A,
   count_launch();
 }
 
+void launch_gather_sum_dot(int n, const int *ptr, const int *idx, const double *src, double *y, int zero,
+                           const DotFuse &f, cudaStream_t s) {
+  if (n == 0) return;
+  k_gather_sum_dot<<<std::min(ceil_div(n, 256), kRedBlocks), 256, 0, s>>>(n, ptr, idx, src, y, zero, f);
+  count_launch();
+}
+void launch_spmv_dot(int n, const int *ptr, const int *col, const double *val, const double *x, double *y, int zero,
+                     const DotFuse &f, cudaStream_t s) {
+  if (n == 0) return;
+  k_spmv_dot<<<std::min(ceil_div(n, 256), kRedBlocks), 256, 0, s>>>(n, ptr, col, val, x, y, zero, f);
+  count_launch();
+}
 void launch_spmv(int n, const int *ptr, const int *col, const double *val, const double *x, double *y, int zero,
                  const int *done, cudaStream_t s) {
   if (n == 0) return;
@@ -569,9 +653,9 @@ void launch_spmv(int n, const int *ptr, const int *col, const double *val, const
 }
 
 void launch_gather_sum(int n, const int *ptr, const int *idx, const double *src, double *y, int zero, double alpha,
-                       const double *addend, const int *done, cudaStream_t s) {
+                       const double *addend, const int *done, cudaStream_t s, const CsrIn *add_csr) {
   if (n == 0) return;
-  k_gather_sum<<<GRID1(n)>>>(n, ptr, idx, src, y, zero, alpha, addend, done);
+  k_gather_sum<<<GRID1(n)>>>(n, ptr, idx, src, y, zero, alpha, addend, done, add_csr ? *add_csr : CsrIn{});
   count_launch();
 }
 
@@ -696,9 +780,8 @@ void launch_dot2(int n, const double *a0, const double *b0, const double *a1, co
   template void launch_assemble_local<T>(int, const int *, const int *, const int *, const int *, const double *, \
                                          const double *, const double *, double, const MatDesc *, T *,         \
                                          cudaStream_t);                                                        \
-  template void launch_build_aug<T>(int, long long, const MatDesc *, const T *, const MatDesc *, T *,           \
-                                    const int *, const int *, const int *, const int *, const double *,         \
-                                    cudaStream_t);                                                             \
+  template void launch_build_aug<T>(int, int, const MatDesc *, const T *, const MatDesc *, T *, const int *,    \
+                                    const int *, const int *, const int *, const T *, cudaStream_t);                                                             \
   template void launch_small_gemm<T>(int, int, const GemmTask *, const T *, const T *, T *, cudaStream_t);      \
   template void launch_class_aug<T>(int, int, const ClassTask *, const PairTask *, const T *, const MatDesc *,  \
                                     T *, cudaStream_t);                                                        \

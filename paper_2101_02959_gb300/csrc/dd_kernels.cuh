@@ -13,6 +13,17 @@ struct KrylovState {
   int it, done, reason, maxit, hist_cap, pad;
 };
 
+// A PCG reduction fused into the kernel that produces its second operand y:
+// which = 0: a.y -> alpha; which = 1: (a.y, y.y) -> beta and the convergence test.
+struct DotFuse {
+  int which;
+  const double *a;
+  double *partial;
+  unsigned int *counter;
+  KrylovState *ks;
+  double *hist;
+};
+
 // Device-resident GMRES(m) state (m <= kMaxRestart).
 constexpr int kMaxRestart = 64;
 struct GmresState {
@@ -34,9 +45,9 @@ void launch_assemble_local(int nq, const int *q_sub, const int *q_loc, const int
 template <typename TS, typename TD>
 void launch_copy(int ntasks, long long max_elems, const CopyTask *tasks, const TS *src, TD *dst, cudaStream_t s);
 template <typename T>
-void launch_build_aug(int nsub, long long max_elems, const MatDesc *sdesc, const T *sbase, const MatDesc *adesc,
+void launch_build_aug(int nsub, int max_m, const MatDesc *sdesc, const T *sbase, const MatDesc *adesc,
                       T *abase, const int *nD, const int *tptr_off, const int *tptr, const int *trow,
-                      const double *tval, cudaStream_t s);
+                      const T *tval, cudaStream_t s);
 template <typename T>
 void launch_small_gemm(int ntasks, int max_n, const GemmTask *tasks, const T *A, const T *B, T *C, cudaStream_t s);
 template <typename T>
@@ -49,7 +60,12 @@ void launch_coarse_aug(int np, int gauge, const int *ptr, const long long *src, 
 void launch_spmv(int n, const int *ptr, const int *col, const double *val, const double *x, double *y, int zero,
                  const int *done, cudaStream_t s);
 void launch_gather_sum(int n, const int *ptr, const int *idx, const double *src, double *y, int zero, double alpha,
-                       const double *addend, const int *done, cudaStream_t s);
+                       const double *addend, const int *done, cudaStream_t s, const CsrIn *add_csr = nullptr);
+// fused with the PCG reduction f (alpha = 1, no addend; y[zero] = 0)
+void launch_gather_sum_dot(int n, const int *ptr, const int *idx, const double *src, double *y, int zero,
+                           const DotFuse &f, cudaStream_t s);
+void launch_spmv_dot(int n, const int *ptr, const int *col, const double *val, const double *x, double *y, int zero,
+                     const DotFuse &f, cudaStream_t s);
 void launch_jump(int nlt, int max_n, const LamTask *lt, const PairTask *pairs, const double *w, double *lam,
                  const int *done, cudaStream_t s);
 void launch_jump_t(int nwt, int max_n, const WTask *wt, const WEnt *ent, const double *lam, double *w,

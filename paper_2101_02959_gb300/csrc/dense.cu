@@ -634,12 +634,14 @@ __global__ void __launch_bounds__(256) k_gemv(const GemvDesc *__restrict__ tasks
 }
 
 // y[a] = (acc ? y[a] : 0) + alpha sum_p A[p][a] x[p]: one CTA per (task, 32 columns);
+// x may instead be a sparse product evaluated while staging (csr.ptr set).
 // lane = column (coalesced rows), the 8 warps split the rows with 4 loads in flight
 // each and add up their partial sums in shared memory in a fixed order.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gemv_t(const GemvDesc *__restrict__ tasks, const T *__restrict__ A,
                                                 const double *__restrict__ x, const int *__restrict__ xidx,
-                                                double *__restrict__ y, double alpha, const int *__restrict__ done) {
+                                                double *__restrict__ y, double alpha, const int *__restrict__ done,
+                                                const CsrIn csr) {
   if (done && *done) return;
   const GemvDesc t = tasks[blockIdx.y];
   const int c0 = blockIdx.x * 32;
@@ -648,7 +650,7 @@ __global__ void __launch_bounds__(256) k_gemv_t(const GemvDesc *__restrict__ tas
   T *xs = reinterpret_cast<T *>(smem_raw);
   __shared__ T part[8][33];
   for (int p = threadIdx.x; p < t.rows; p += blockDim.x)
-    xs[p] = (T)((t.flags & 1) ? x[xidx[t.x_off + p]] : x[t.x_off + p]);
+    xs[p] = (T)(csr.ptr ? csr_row(csr, t.x_off + p) : (t.flags & 1) ? x[xidx[t.x_off + p]] : x[t.x_off + p]);
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int a = c0 + lane;
@@ -687,11 +689,11 @@ void launch_gemv(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks
 
 template <typename T>
 void launch_gemv_t(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks, const T *A, const double *x,
-                   const int *xidx, double *y, double alpha, const int *done, cudaStream_t s) {
+                   const int *xidx, double *y, double alpha, const int *done, cudaStream_t s, const CsrIn *csr) {
   if (ntasks == 0 || max_cols == 0) return;
   dim3 g(ceil_div(max_cols, 32), ntasks);
   const size_t sm = sizeof(T) * (size_t)std::max(1, max_rows);
-  k_gemv_t<T><<<g, 256, sm, s>>>(d_tasks, A, x, xidx, y, alpha, done);
+  k_gemv_t<T><<<g, 256, sm, s>>>(d_tasks, A, x, xidx, y, alpha, done, csr ? *csr : CsrIn{});
   count_launch();
 }
 
@@ -872,7 +874,7 @@ bool dense_configure() {
   template void launch_gemv<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *,        \
                                double *, double, const int *, cudaStream_t);                                   \
   template void launch_gemv_t<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *,      \
-                                 double *, double, const int *, cudaStream_t);                                 \
+                                 double *, double, const int *, cudaStream_t, const CsrIn *);                  \
   template void launch_trsv<T>(int, int, const MatDesc *, const int *, const T *, const T *, const double *,   \
                                double *, bool, cudaStream_t);
 BD_INST(float)

@@ -83,7 +83,8 @@ void launch_gemv(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks
 // y[a] = (accumulate ? y[a] : 0) + alpha * sum_p A[p][a] x[p]  (x gathered through xidx when flagged)
 template <typename T>
 void launch_gemv_t(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks, const T *A, const double *x,
-                   const int *xidx, double *y, double alpha, const int *done, cudaStream_t s);
+                   const int *xidx, double *y, double alpha, const int *done, cudaStream_t s,
+                   const CsrIn *csr = nullptr);
 // Batched triangular solves with the leading n x n lower triangles (MatDesc.e = n) left
 // by the engine (off-diagonal blocks in base, diagonal blocks in the engine's store):
 // y = L^-1 b (lower) or y = L^-T b (upper); b and y are concatenated vectors at vec_off[b].
