@@ -7,8 +7,8 @@ stimulus; 20 time steps.  A "step" is one time step: gating, then Newton with
 the Jacobian solved by PCG + BDDC deluxe (or FETI-DP), at the paper's
 tolerances (KSP rtol 1e-8, SNES rtol 1e-4).
 
-The chosen solver (mixed precision: float32 local factors and Schur
-complements, float64 Krylov / Newton / coarse) is timed next to the plain
+The chosen solver (mixed precision: float32 local factors, Schur complements
+and coarse problem, float64 Krylov / Newton) is timed next to the plain
 float64 GPU solver on the same mesh.  Inputs are resident in HBM for `value`;
 `e2e` repeats the chosen run through the C-ABI with host buffers (state copied
 in and out every step).  With --gpus N > 1 every rank runs an independent
@@ -172,6 +172,8 @@ def run_gpu(args, w, rank, world):
     s.set_state(*hs, 0.0)
     for _ in range(args.warmup):
         s.step(synth.STIMULUS)
+    if args.autotune:
+        s.autotune()
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -199,7 +201,25 @@ def run_gpu(args, w, rank, world):
     return out
 
 
-def roofline(prof, precision):
+# DRAM bytes per launch of k_rankk128, averaged over every launch of a slab32 run
+# (ncu dram__bytes_read.sum + dram__bytes_write.sum; profiles/rankk128_slab32_mixed_bddc.md).
+# It stands only while the kernel's source text is the one it was measured on.
+RANKK128_TRAFFIC = {"bytes_per_launch": 52.28e6, "source_sha256_16": "9511215a957c252b"}
+
+
+def rankk128_traffic():
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_2101_02959_gb300", "csrc", "dense.cu")).read()
+    try:
+        a = src.index("__global__ void __launch_bounds__(256) k_rankk128(")
+        b = src.index("template <typename T>\nstatic void launch_rankk(")
+    except ValueError:
+        return None
+    h = hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
+    return RANKK128_TRAFFIC["bytes_per_launch"] if h == RANKK128_TRAFFIC["source_sha256_16"] else None
+
+
+def roofline(prof, precision, tc_used=False):
     """Dominant profiled kernel class against its roofline."""
     pk = peaks()
     dom = max(prof, key=lambda k: prof[k]["ms"])
@@ -209,8 +229,12 @@ def roofline(prof, precision):
     if dom in ("rankk", "panel"):
         achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12
         peak = FP32_SIMT_PEAK if precision == "mixed" else FP64_PEAK
+        traffic = rankk128_traffic() if (dom == "rankk" and precision == "mixed" and not tc_used) else None
         r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-             "traffic": None, "kernel": "k_rankk" if dom == "rankk" else "k_potrf+k_trsm",
+             "traffic": traffic,
+             "kernel": ("k_rankk128" if precision == "mixed" and not tc_used else
+                        "k_rankk_tc" if precision == "mixed" else "k_rankk<double>") if dom == "rankk"
+             else "k_bigpanel",
              "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz" if precision == "mixed"
                              else "nominal GB300 FP64 (recipe table)")}
     else:
@@ -342,7 +366,10 @@ def main():
     K, ch, pl = r["K"], r["chosen"], r["plain"]
     ms = ch["ms"] / K
     sec = ch["ms"] * 1e-3
-    roof, dom = roofline(ch["prof"], args.precision)
+    tc_used = bool(args.tc and args.precision == "mixed")
+    if ch["tune"] is not None:
+        tc_used = bool(ch["tune"]["tensor_cores"])
+    roof, dom = roofline(ch["prof"], args.precision, tc_used)
     cpu = None
     if world == 1 and args.cpu_steps > 0:
         c = cpu_baseline(w, args.cpu_steps)
@@ -353,11 +380,11 @@ def main():
     line = {
         "metric": METRIC, "value": ms, "unit": "ms/time step", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 local factors + f64 Krylov/Newton/coarse" if args.precision == "mixed"
+        "vs_baseline": None, "dtype": "f32 local and coarse factors + f64 Krylov/Newton" if args.precision == "mixed"
         else "f64", "data": "synthetic",
         "config": {"workload": describe(w), "unknowns": 2 * r["N"], "method": args.method + "-deluxe",
                    "krylov": "pcg", "precision": args.precision, "learned_guess": bool(args.learned),
-                   "tensor_cores": bool(args.tc and args.precision == "mixed"),
+                   "tensor_cores": tc_used,
                    "chord_newton": bool(args.lag and args.precision == "mixed"), "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "per-step working set > 129 MB L2 (local matrices 0.27 GB f32 / 0.54 GB f64)"},
         "krylov_solves_per_s": ch["newton"] / sec,

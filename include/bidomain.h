@@ -257,11 +257,12 @@ int krylov_solve(bd_handle *h, const double *f, double *s, int on_device, bd_sol
 /* ---- autotuner (not in the paper) ----------------------------------------------
  * Times the whole factorisation sequence of bidomain_linearize (CUDA events,
  * best of two after a warm-up) at the current Jacobian for every combination of
- * the number of subdomain groups the batch is factorised in {1, 2, 4, 8} and, in
- * BD_MIXED, tensor cores on/off; keeps the fastest for the handle and leaves the
- * Jacobian factorised with it.  outer_panel reports the engine's fixed outer panel
- * width (128).  Requires bidomain_linearize (or a step) first.  Results are
- * identical up to rounding for every choice. */
+ * outer block width {128, 256, 512} (columns per long-K trailing update; panels
+ * are 128 columns), number of subdomain groups the batch is factorised in
+ * {1, 2, 4} and, in BD_MIXED, tensor cores on/off; keeps the fastest for the
+ * handle and leaves the Jacobian factorised with it.  Requires
+ * bidomain_linearize (or a step) first.  Results are identical up to rounding for
+ * every choice. */
 typedef struct {
   int outer_panel, groups, tensor_cores, candidates;
   double best_ms, default_ms;

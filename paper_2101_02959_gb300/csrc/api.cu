@@ -256,7 +256,7 @@ struct bd_handle {
   double *d_uh1i, *d_uh1e, *d_uh2i, *d_uh2e, *d_gi, *d_ge;
   double rtol_scale = 1.0;
   // factorisation tuning (bidomain_autotune): outer panel width, batch groups, tensor cores
-  int tune_groups = 1;
+  int tune_ob = 256, tune_groups = 1;
   cudaGraphExec_t pcg_exec[2] = {nullptr, nullptr};  // captured PCG chunk per method
   size_t pcg_nodes[2] = {0, 0};
   double gemv_schur_flops = 0, gemv_schur_bytes = 0, gemv_local_flops = 0, gemv_local_bytes = 0;
@@ -765,6 +765,7 @@ void setup_handle(bd_handle &h) {
     for (const GemvSet *g : {&h.gv_schur, &h.gv_local, &h.gv_psit, &h.gv_coarse, &h.gv_sdd, &h.gv_lgi, &h.gv_lgit,
                              &h.gv_drest, &h.gv_dext})
       need = std::max(need, el * (size_t)std::max(g->max_rows, g->max_cols));
+    need = std::max(need, el * ((size_t)h.np + h.gv_psit.max_rows));  // fused coarse solve
     if (need > dense_smem_limit())
       throw Status(BD_ERR_ARG, "local problem too large for the shared-memory staging of the dense kernels (" +
                                    std::to_string(need) + " bytes); use more subdomains");
@@ -836,6 +837,7 @@ void run_engine_groups(bd_handle &h, const EngineShape &all, const MatDesc *d_de
   for (int a = 0; a < all.count; a += per) {
     const int b = std::min(all.count, a + per);
     EngineShape g{b - a, 0, 0, {}, {}};
+    g.ob = h.tune_ob;
     for (int q = a; q < b; ++q) {
       g.m.push_back(all.m[q]);
       g.e.push_back(all.e[q]);
@@ -899,17 +901,15 @@ void st_inv_t(bd_handle &h, Dense<T> &D, const double *rP, const double *rD, con
   launch_gemv<T>(h.gv_local.n, h.gv_local.max_rows, h.gv_local.max_cols, h.gv_local.d, D.Z, rD, nullptr, h.d_ydc,
                  1.0, done, h.s);
   h.prof.end(PROF_GEMV, h.s, h.gemv_local_flops, h.gemv_local_bytes * sizeof(T));
-  launch_gather_sum(h.np, h.d_pl_ptr, h.d_pl_idx, h.d_ydc + h.nD_tot, h.d_crhs, h.gauge_primal, -1.0,
-                    rP_csr ? nullptr : rP, done, h.s, rP_csr);
-  launch_gemv<T>(1, h.np, h.np, h.gv_coarse.d, D.CoInv, h.d_crhs, nullptr, h.d_zbar, 1.0, done, h.s);
-  launch_gemv_t<T>(h.gv_psit.n, h.gv_psit.max_rows, h.gv_psit.max_cols, h.gv_psit.d, D.Z, h.d_zbar, h.d_prim_x,
-                   h.d_ydc, -1.0, done, h.s);
+  launch_coarse_psit<T>(h.gv_psit.n, h.gv_psit.max_rows, h.gv_psit.max_cols, h.gv_psit.d, D.Z, D.CoInv, h.np,
+                        h.gauge_primal, h.d_pl_ptr, h.d_pl_idx, h.d_ydc + h.nD_tot, rP_csr ? nullptr : rP, rP_csr,
+                        h.d_prim_x, h.nd, h.d_zbar, h.d_ydc, done, h.s);
 }
 
-template <class T>
 // rbar = T^T r is never stored: the deluxe restriction evaluates its dual rows while
 // staging, the coarse right-hand side its primal rows (row nd + gauge_primal is
 // zeroed there).  f: the PCG reduction to fuse into the last kernel.
+template <class T>
 void bddc_t(bd_handle &h, Dense<T> &D, const double *r, double *z, const int *done, const DotFuse *f = nullptr) {
   const CsrIn rbar{h.d_Tt_ptr, h.d_Tt_col, h.d_Tt_val, r};
   const CsrIn rbar_p{h.d_Tt_ptr + h.nd, h.d_Tt_col, h.d_Tt_val, r};
@@ -1735,7 +1735,7 @@ int bidomain_autotune(bd_handle *h, bd_tune_result *out) {
     ck(cudaEventCreate(&e1), "event");
     const bool prof_on = h->prof.on;
     h->prof.on = false;
-    const int tc0 = h->opt.use_tensor_cores, g0 = h->tune_groups;
+    const int tc0 = h->opt.use_tensor_cores, ob0 = h->tune_ob, g0 = h->tune_groups;
     auto time_it = [&]() {
       linearize(*h);  // warm
       float best = 1e30f;
@@ -1752,19 +1752,22 @@ int bidomain_autotune(bd_handle *h, bd_tune_result *out) {
     };
     const float base_ms = time_it();
     float best_ms = base_ms;
-    int best_g = g0, best_tc = tc0, n = 0;
+    int best_ob = ob0, best_g = g0, best_tc = tc0, n = 0;
     const int tcs[2] = {0, 1};
     for (int tc : tcs) {
       if (tc && !h->mixed()) continue;
-      for (int g : {1, 2, 4, 8}) {
-        h->opt.use_tensor_cores = tc;
-        h->tune_groups = g;
-        const float ms = time_it();
-        ++n;
-        if (ms < best_ms) { best_ms = ms; best_g = g; best_tc = tc; }
-      }
+      for (int ob : {128, 256, 512})
+        for (int g : {1, 2, 4}) {
+          h->opt.use_tensor_cores = tc;
+          h->tune_ob = ob;
+          h->tune_groups = g;
+          const float ms = time_it();
+          ++n;
+          if (ms < best_ms) { best_ms = ms; best_ob = ob; best_g = g; best_tc = tc; }
+        }
     }
     h->opt.use_tensor_cores = best_tc;
+    h->tune_ob = best_ob;
     h->tune_groups = best_g;
     linearize(*h);
     h->prof.on = prof_on;
@@ -1772,7 +1775,7 @@ int bidomain_autotune(bd_handle *h, bd_tune_result *out) {
     cudaEventDestroy(e1);
     int st = h->check_err();
     if (out) {
-      out->outer_panel = kEnginePanel;
+      out->outer_panel = best_ob;
       out->groups = best_g;
       out->tensor_cores = best_tc;
       out->candidates = n;

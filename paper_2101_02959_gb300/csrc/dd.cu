@@ -171,6 +171,91 @@ __global__ void k_coarse_aug(int np, int gauge, const int *__restrict__ ptr, con
   }
 }
 
+// ---- coarse correction fused with the local primal correction -----------------
+// Every CTA assembles the coarse right-hand side c = rP - sum_j (Psi^T r_D)_j
+// (c[gauge] = 0; rP as a vector, a sparse product, or absent) in shared memory,
+// solves only the rows of its own subdomain's primal dofs, z = S_PiPi^-1 c with the
+// explicit inverse (one warp per row), and then applies ydc -= Psi z to its 32
+// dual columns like k_gemv_t.  The CTAs of column block 0 also store their z
+// entries in zbar[nd + q]; a dof shared by several subdomains gets the same value
+// from each of them (same inputs, same arithmetic).
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_psit(const GemvDesc *__restrict__ tasks, const T *__restrict__ Z,
+                                                     const T *__restrict__ coinv, int np, int gauge,
+                                                     const int *__restrict__ pl_ptr, const int *__restrict__ pl_idx,
+                                                     const double *__restrict__ yprim, const double *__restrict__ rP,
+                                                     const CsrIn rPc, const int *__restrict__ prim_x, int nd,
+                                                     double *__restrict__ zbar, double *__restrict__ ydc,
+                                                     const int *__restrict__ done) {
+  if (done && *done) return;
+  const GemvDesc t = tasks[blockIdx.y];
+  const int c0 = blockIdx.x * 32;
+  if (c0 >= t.cols) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *cr = reinterpret_cast<T *>(smem_raw);  // [np] coarse right-hand side
+  T *xs = cr + np;                          // [t.rows] this subdomain's z_Pi
+  __shared__ T part[8][33];
+  for (int q = threadIdx.x; q < np; q += blockDim.x) {
+    double acc = 0.0;
+    for (int k = pl_ptr[q]; k < pl_ptr[q + 1]; ++k) acc += yprim[pl_idx[k]];
+    double v = -acc;
+    if (rP) v += rP[q];
+    else if (rPc.ptr) v += csr_row(rPc, q);
+    cr[q] = (T)((q == gauge) ? 0.0 : v);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int p = wid; p < t.rows; p += 8) {
+    const int q = prim_x[t.x_off + p] - nd;
+    const T *row = coinv + (long long)q * np;
+    T a0 = T(0), a1 = T(0);
+    int c = lane;
+    for (; c + 32 < np; c += 64) {
+      a0 += row[c] * cr[c];
+      a1 += row[c + 32] * cr[c + 32];
+    }
+    if (c < np) a0 += row[c] * cr[c];
+    const T z = warp_sum(a0 + a1);
+    if (lane == 0) {
+      xs[p] = z;
+      if (blockIdx.x == 0) zbar[nd + q] = (double)z;
+    }
+  }
+  __syncthreads();
+  const int a = c0 + lane;
+  const bool va = a < t.cols;
+  const T *col = Z + t.a_off + (va ? a : c0);
+  const long long ld = t.ld;
+  T s0 = T(0), s1 = T(0);
+  int p = wid;
+  for (; p + 8 < t.rows; p += 16) {
+    s0 += col[p * ld] * xs[p];
+    s1 += col[(p + 8) * ld] * xs[p + 8];
+  }
+  for (; p < t.rows; p += 8) s0 += col[p * ld] * xs[p];
+  part[wid][lane] = s0 + s1;
+  __syncthreads();
+  if (wid == 0 && va) {
+    T sum = T(0);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sum += part[k][lane];
+    const double v = -(double)sum;
+    ydc[t.y_off + a] = (t.flags & 2) ? ydc[t.y_off + a] + v : v;
+  }
+}
+
+template <typename T>
+void launch_coarse_psit(int ntasks, int max_rows, int max_cols, const GemvDesc *tasks, const T *Z, const T *coinv,
+                        int np, int gauge, const int *pl_ptr, const int *pl_idx, const double *yprim,
+                        const double *rP, const CsrIn *rPc, const int *prim_x, int nd, double *zbar, double *ydc,
+                        const int *done, cudaStream_t s) {
+  if (ntasks == 0 || max_cols == 0) return;
+  const size_t sm = sizeof(T) * ((size_t)np + std::max(1, max_rows));
+  k_coarse_psit<T><<<dim3(ceil_div(max_cols, 32), ntasks), 256, sm, s>>>(
+      tasks, Z, coinv, np, gauge, pl_ptr, pl_idx, yprim, rP, rPc ? *rPc : CsrIn{}, prim_x, nd, zbar, ydc, done);
+  count_launch();
+}
+
 // ---- sparse (CSR) matrix-vector product y = A x, y[zero] = 0 --------------------
 __global__ void k_spmv(int n, const int *__restrict__ ptr, const int *__restrict__ col, const double *__restrict__ val,
                        const double *__restrict__ x, double *__restrict__ y, int zero, const int *__restrict__ done) {
@@ -791,7 +876,10 @@ void launch_dot2(int n, const double *a0, const double *b0, const double *a1, co
                                   double *, const int *, cudaStream_t);                                        \
   template void launch_jump_d<T>(int, int, const LamTask *, const PairTask *, const T *, const T *,             \
                                  const double *, double *, const int *, cudaStream_t);                         \
-  template void launch_copy<T, T>(int, long long, const CopyTask *, const T *, T *, cudaStream_t);
+  template void launch_copy<T, T>(int, long long, const CopyTask *, const T *, T *, cudaStream_t);            \
+  template void launch_coarse_psit<T>(int, int, int, const GemvDesc *, const T *, const T *, int, int,          \
+                                      const int *, const int *, const double *, const double *, const CsrIn *, \
+                                      const int *, int, double *, double *, const int *, cudaStream_t);
 BD_DD_INST(float)
 BD_DD_INST(double)
 template void launch_copy<float, double>(int, long long, const CopyTask *, const float *, double *, cudaStream_t);

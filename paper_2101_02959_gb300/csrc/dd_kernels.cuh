@@ -61,6 +61,13 @@ void launch_spmv(int n, const int *ptr, const int *col, const double *val, const
                  const int *done, cudaStream_t s);
 void launch_gather_sum(int n, const int *ptr, const int *idx, const double *src, double *y, int zero, double alpha,
                        const double *addend, const int *done, cudaStream_t s, const CsrIn *add_csr = nullptr);
+// coarse solve fused into the primal correction: c = rP (vector, sparse product or
+// absent) - sum_j (Psi^T r_D)_j, z_Pi = S_PiPi^-1 c into zbar[nd:], ydc -= Psi z_Pi
+template <typename T>
+void launch_coarse_psit(int ntasks, int max_rows, int max_cols, const GemvDesc *tasks, const T *Z, const T *coinv,
+                        int np, int gauge, const int *pl_ptr, const int *pl_idx, const double *yprim,
+                        const double *rP, const CsrIn *rPc, const int *prim_x, int nd, double *zbar, double *ydc,
+                        const int *done, cudaStream_t s);
 // fused with the PCG reduction f (alpha = 1, no addend; y[zero] = 0)
 void launch_gather_sum_dot(int n, const int *ptr, const int *idx, const double *src, double *y, int zero,
                            const DotFuse &f, cudaStream_t s);

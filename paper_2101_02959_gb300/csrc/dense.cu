@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(256, ROWS ? 2 : 1) k_bigpanel(const MatDesc *_
 // ---- rank-k update of lower tiles --------------------------------------------
 // Two-level right-looking blocking: inner panels of kNB columns inside outer
 // panels [K0, K1) of kOB columns.
-// mode 0 (inner): rows [k0+w, m), cols [k0+w, min(K1, e)), K = [k0, k0+w)
+// mode 0 (inner): rows [k0+w, m), cols [k0+w, min(K1, e)), K = [k0, k0+w), w = one engine panel
 // mode 2 (outer): rows [K1, m),   cols [K1, e),            K = [K0, K1)
 // mode 1 (final): rows [e, m),    cols [e, m),             K = [0, e)
 // C[r][c] -= sum_k A[r][k] A[c][k]; 64x64 tiles, 256 threads, 4x4 per thread.
@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(256) k_rankk(const MatDesc *__restrict__ desc,
   int row0, colend, kb, ke;
   if (mode == 0) {
     if (k0 >= d.e) return;
-    const int w = min(kNB, d.e - k0);
+    const int w = min(kEnginePanel, d.e - k0);
     row0 = k0 + w;
     colend = min(K1, d.e);
     kb = k0;
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(256) k_rankk128(const MatDesc *__restrict__ de
   int row0, colend, kb, ke;
   if (mode == 0) {
     if (k0 >= d.e) return;
-    const int w = min(kNB, d.e - k0);
+    const int w = min(kEnginePanel, d.e - k0);
     row0 = k0 + w; colend = min(K1, d.e); kb = k0; ke = k0 + w;
   } else if (mode == 2) {
     if (K1 >= d.e) return;
@@ -521,26 +521,40 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
                              T *store, ProfHook *prof, bool tc) {
   if (sh.count == 0) return;
   constexpr int RB = PanelRows<T>::RB;
-  for (int K0 = 0; K0 < sh.max_e; K0 += kPW) {
-    const int K1 = K0 + kPW;
-    int max_below = 0;
-    double fl_panel = 0.0;
-    for (int b = 0; b < sh.count; ++b) {
-      if (K0 >= sh.e[b]) continue;
-      const int w = std::min(kPW, sh.e[b] - K0);
-      const int below = sh.m[b] - K0 - w;
-      max_below = std::max(max_below, below);
-      fl_panel += (double)w * w * w / 3.0 + (double)below * w * w;
-    }
-    if (prof) prof->begin(PROF_PANEL, s);
-    k_bigpanel<T, false><<<dim3(1, sh.count), 256, bigpanel_smem<T, false>(), s>>>(d_desc, base, K0, d_err, store);
-    count_launch();
-    if (max_below > 0) {
-      k_bigpanel<T, true><<<dim3(ceil_div(max_below, RB), sh.count), 256, bigpanel_smem<T, true>(), s>>>(
-          d_desc, base, K0, d_err, store);
+  const int ob = std::max(kPW, (sh.ob / kPW) * kPW);  // outer block: columns per long-K trailing update
+  for (int K0 = 0; K0 < sh.max_e; K0 += ob) {
+    const int K1 = K0 + ob;
+    for (int k0 = K0; k0 < std::min(K1, sh.max_e); k0 += kPW) {
+      int max_below = 0, max_cols = 0;
+      double fl_panel = 0.0, fl_in = 0.0, by_in = 0.0;
+      for (int b = 0; b < sh.count; ++b) {
+        if (k0 >= sh.e[b]) continue;
+        const int w = std::min(kPW, sh.e[b] - k0);
+        const int below = sh.m[b] - k0 - w;
+        const int cend = std::min(K1, sh.e[b]);
+        max_below = std::max(max_below, below);
+        max_cols = std::max(max_cols, cend - k0 - w);
+        fl_panel += (double)w * w * w / 3.0 + (double)below * w * w;
+        const double ent = trapezoid(k0 + w, cend, sh.m[b]);
+        fl_in += 2.0 * w * ent;
+        by_in += sizeof(T) * (2.0 * ent + (double)w * (below + cend - k0 - w));
+      }
+      if (prof) prof->begin(PROF_PANEL, s);
+      k_bigpanel<T, false><<<dim3(1, sh.count), 256, bigpanel_smem<T, false>(), s>>>(d_desc, base, k0, d_err, store);
       count_launch();
+      if (max_below > 0) {
+        k_bigpanel<T, true><<<dim3(ceil_div(max_below, RB), sh.count), 256, bigpanel_smem<T, true>(), s>>>(
+            d_desc, base, k0, d_err, store);
+        count_launch();
+      }
+      if (prof) prof->end(PROF_PANEL, s, fl_panel, 0.0);
+      // the rest of the outer block: rows [k0 + w, m), columns [k0 + w, min(K1, e))
+      if (max_below > 0 && max_cols > 0) {
+        if (prof) prof->begin(PROF_RANKK, s);
+        launch_rankk<T>(d_desc, base, 0, k0, K0, K1, max_below, max_cols, sh.count, s);
+        if (prof) prof->end(PROF_RANKK, s, fl_in, by_in);
+      }
     }
-    if (prof) prof->end(PROF_PANEL, s, fl_panel, 0.0);
     // outer update of the trailing columns [K1, e) with the finished outer panel
     int max_rows = 0, max_cols = 0;
     double fl = 0.0, by = 0.0;
@@ -549,8 +563,8 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
       max_rows = std::max(max_rows, sh.m[b] - K1);
       max_cols = std::max(max_cols, sh.e[b] - K1);
       const double ent = trapezoid(K1, sh.e[b], sh.m[b]);
-      fl += 2.0 * kPW * ent;
-      by += sizeof(T) * (2.0 * ent + (double)kPW * (sh.m[b] - K1));
+      fl += 2.0 * ob * ent;
+      by += sizeof(T) * (2.0 * ent + (double)ob * (sh.m[b] - K1));
     }
     if (max_rows > 0 && max_cols > 0) {
       if (prof) prof->begin(PROF_RANKK, s);

@@ -57,9 +57,11 @@ struct EngineShape {
   int count;
   int max_e, max_m;
   std::vector<int> m, e;  // host copies for per-step grid sizes
+  int ob = 256;           // outer block: columns per long-K trailing update (multiple of 128)
 };
-// The engine works through outer panels of kEnginePanel columns (k_bigpanel), each
-// followed by one long-K update of the trailing columns.  store: block store
+// The engine works through outer blocks of sh.ob columns: panels of kEnginePanel
+// columns (k_bigpanel), each followed by an update of the rest of its block, then
+// one long-K (K = ob) update of the trailing columns.  store: block store
 // receiving the factored kNB x kNB diagonal blocks L_kk; matrix b uses slots
 // [desc[b].dblk, desc[b].dblk + ceil(e_b / kNB)) (row-major, identity outside the last
 // block's width).  tc: FP32 only, run the long-K updates on the tensor cores (tc.cu).

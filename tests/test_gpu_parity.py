@@ -228,8 +228,8 @@ def test_autotune_keeps_results(precision):
     x = synth.random_vector(prob.dofs.n_iface, 9)
     y0 = s.schur_apply(x)
     r = s.autotune()
-    assert r["candidates"] >= 4 and r["best_ms"] <= r["default_ms"]
-    assert r["outer_panel"] == 128 and r["groups"] in (1, 2, 4, 8)
+    assert r["candidates"] >= 9 and r["best_ms"] <= r["default_ms"]
+    assert r["outer_panel"] in (128, 256, 512) and r["groups"] in (1, 2, 4)
     y1 = s.schur_apply(x)
     assert _rel(y1, y0) < (1e-12 if precision == "fp64" else 2e-5)
 
