@@ -127,7 +127,7 @@ def run_gpu(args, w, rank, world):
         tune = s.autotune() if args.autotune else None
         s.set_state(*dstate, 0.0)
         if profile:
-            s.profile(True)
+            s.profile(profile)
         stats = []
         barrier()
         torch.cuda.synchronize()
@@ -144,14 +144,15 @@ def run_gpu(args, w, rank, world):
         launches = binding.launch_count() - l0
         clk = clocks.stop() if clocks else None
         ms = max_over_ranks(e0.elapsed_time(e1))
-        prof = {k: s.profile_read(k) for k in binding.PROF} if profile else None
+        prof = {k: s.profile_read(k) for k in binding.PROF} if profile == 1 or profile is True else None
+        regs = {k: s.profile_read(k) for k in binding.REGIONS} if profile else None
         final = s.get_state(like=dstate[0])
         s.close()
         newton = sum(st["newton_its"] for st in stats)
         kry = sum(st["krylov_its"] for st in stats)
         bad = [st["reason"] for st in stats if st["reason"] != 0]
         used = sum(st.get("guess_used", 0) for st in stats)
-        return dict(ms=ms, newton=newton, krylov=kry, launches=launches, prof=prof, clocks=clk, bad=bad,
+        return dict(ms=ms, newton=newton, krylov=kry, launches=launches, prof=prof, regions=regs, clocks=clk, bad=bad,
                     cond=max(st["cond_max"] for st in stats), final=final, guess_used=used, tune=tune)
 
     chosen = timed(args.precision, args.method, clocks=ClockSampler(dev), learned=args.learned)
@@ -160,6 +161,10 @@ def run_gpu(args, w, rank, world):
     profiled = timed(args.precision, args.method, profile=True, graphs=0, learned=args.learned)
     chosen["prof"] = profiled["prof"]
     chosen["prof_ms"] = profiled["ms"]
+    # where a graph-replayed step spends its time: region timers only (a third pass)
+    regions = timed(args.precision, args.method, profile=2, learned=args.learned)
+    chosen["regions"] = regions["regions"]
+    chosen["regions_ms"] = regions["ms"]
     plain = timed("fp64", args.method) if not args.no_plain else None
 
     # e2e: the same chosen run through host buffers, state copied in and out every step
@@ -226,7 +231,19 @@ def roofline(prof, precision, tc_used=False):
     p = prof[dom]
     if p["launches"] == 0 or p["ms"] <= 0:
         return None, dom
-    if dom in ("rankk", "panel"):
+    if dom == "rankk" and precision == "mixed" and tc_used:
+        # tcgen05 kind::tf32 with operands split in hi + lo TF32 parts: three MMAs per
+        # FP32-accurate product, so the peak for algorithmic FP32 flops is the TF32 peak
+        # (measured sustained bf16 x the nominal tf32 / bf16 ratio 1.1 / 2.25) / 3
+        achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12
+        src = "bf16_tflops_sustained" if "bf16_tflops_sustained" in pk else None
+        tf32 = (pk[src] if src else 1700.0) * 1.1 / 2.25
+        peak = tf32 / 3.0
+        r = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+             "traffic": None, "kernel": "k_rankk_tc",
+             "peak_source": ("of measured: bf16_tflops_sustained x 1.1/2.25 (tf32) / 3 (hi/lo split)" if src
+                             else "of fallback: 1.7 PF bf16 sustained x 1.1/2.25 / 3")}
+    elif dom in ("rankk", "panel"):
         achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12
         peak = FP32_SIMT_PEAK if precision == "mixed" else FP64_PEAK
         traffic = rankk128_traffic() if (dom == "rankk" and precision == "mixed" and not tc_used) else None
@@ -401,6 +418,9 @@ def main():
         "autotune": ch["tune"],
         "roofline": roof,
         "profiled_pass_ms_per_step": ch["prof_ms"] / K,
+        "regions_ms_per_step": {"pass_ms_per_step": ch["regions_ms"] / K,
+                                **{k: v["ms"] / K for k, v in ch["regions"].items()}},
+        "region_calls_per_step": {k: v["launches"] / K for k, v in ch["regions"].items()},
         "kernels": {k: dict(v, avg_us=(v["ms"] * 1e3 / v["launches"] if v["launches"] else 0.0))
                     for k, v in ch["prof"].items()},
         "clocks": ch["clocks"],

@@ -314,9 +314,18 @@ int schur_apply_noalloc(bd_handle *h, const double *x, double *y);
 #define BD_PROF_PANEL 1  /* diagonal-block factorisation and panel solves */
 #define BD_PROF_GEMV 2   /* dense local matvecs of every Krylov iteration (S_Gamma, S_DD^-1, Psi) */
 #define BD_PROF_RESID 3  /* Newton residual F(u) - G */
+/* Regions of a step, each timed as a whole (with enable = 2 also while the Krylov
+ * iterations replay as CUDA graphs): */
+#define BD_PROF_LINEARIZE 4  /* the Jacobian and every factorisation (Sections 4.1-4.4) */
+#define BD_PROF_KRYLOV 5     /* one Krylov solve (PCG or GMRES, all iterations) */
+#define BD_PROF_TRSV 6       /* interior condensation / recovery triangular solves */
+#define BD_PROF_MLP 7        /* learned initial guess: prediction and online training */
+#define BD_PROF_STEP 8       /* one whole bidomain_step */
 
 /* enable = 1 records a CUDA event pair on the handle's stream around every
- * launch of the classes above (and clears the totals); 0 stops recording. */
+ * launch of the kernel classes and around every region above (and clears the
+ * totals); enable = 2 records the regions only; 0 stops recording.  Per-launch
+ * events are not recorded inside captured CUDA graphs. */
 int bidomain_profile(bd_handle *h, int enable);
 /* out[4] = {launches, total milliseconds, algorithmic flops, algorithmic bytes}
  * summed over the launches of class `which` since profiling was enabled.

@@ -34,7 +34,8 @@ EXPORTED = ["bd_plan_create", "bd_plan_sizes", "bd_plan_index_sets", "bd_plan_de
             "bidomain_profile_read", "bidomain_launch_count", "schur_apply_noalloc", "bidomain_mlp_sizes",
             "bidomain_mlp_params", "bidomain_mlp_loss_grad", "bidomain_autotune", "bidomain_destroy",
             "bidomain_strerror"]
-PROF = dict(rankk=0, panel=1, gemv=2, resid=3)
+PROF = dict(rankk=0, panel=1, gemv=2, resid=3)                    # kernel classes
+REGIONS = dict(linearize=4, krylov=5, trsv=6, mlp=7, step=8)      # regions of a step
 
 
 class BdMesh(C.Structure):
@@ -328,11 +329,14 @@ class Solver:
         return self._apply(self._lib.fetidp_operator, lam, self.sizes["n_lambda"], "fetidp_operator")
 
     def profile(self, enable=True):
-        _check(self._lib.bidomain_profile(self._h, 1 if enable else 0), "bidomain_profile")
+        """True / 1: kernel classes and regions; 2: regions only; False / 0: off."""
+        mode = 2 if enable == 2 else (1 if enable else 0)
+        _check(self._lib.bidomain_profile(self._h, mode), "bidomain_profile")
 
     def profile_read(self, which):
         out = (C.c_double * 4)()
-        _check(self._lib.bidomain_profile_read(self._h, PROF[which], out), "bidomain_profile_read")
+        idx = PROF[which] if which in PROF else REGIONS[which]
+        _check(self._lib.bidomain_profile_read(self._h, idx, out), "bidomain_profile_read")
         return dict(launches=int(out[0]), ms=out[1], flops=out[2], bytes=out[3])
 
     def autotune(self):

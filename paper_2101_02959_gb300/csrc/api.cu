@@ -115,13 +115,15 @@ double tridiag_cond(const std::vector<double> &d, const std::vector<double> &e) 
 
 // Per-launch CUDA-event timing of selected kernel classes.
 struct Profiler : ProfHook {
-  bool on = false;
+  int on = 0;  // 0 off, 1 kernel classes and regions, 2 regions only
   struct Rec {
     int id;
     cudaEvent_t a, b;
     double flops, bytes;
   };
   std::vector<Rec> recs;
+  std::vector<size_t> open;  // records begun and not yet ended (regions nest)
+  bool wants(int id) const { return on == 1 || (on == 2 && id >= PROF_FIRST_REGION); }
   std::vector<cudaEvent_t> pool;
   size_t used = 0;
   double tot[PROF_NCLASS][4] = {};
@@ -134,20 +136,24 @@ struct Profiler : ProfHook {
     return pool[used++];
   }
   void begin(int id, cudaStream_t s) override {
-    if (!on) return;
+    if (!wants(id)) return;
     cudaEvent_t a = get();
     ck(cudaEventRecord(a, s), "event");
+    open.push_back(recs.size());
     recs.push_back(Rec{id, a, nullptr, 0.0, 0.0});
   }
   void end(int id, cudaStream_t s, double flops, double bytes) override {
-    if (!on) return;
+    if (!wants(id) || open.empty()) return;
     cudaEvent_t b = get();
     ck(cudaEventRecord(b, s), "event");
-    recs.back().b = b;
-    recs.back().flops = flops;
-    recs.back().bytes = bytes;
+    Rec &r = recs[open.back()];
+    open.pop_back();
+    r.b = b;
+    r.flops = flops;
+    r.bytes = bytes;
   }
   void harvest() {
+    if (!open.empty()) return;  // only between regions
     for (auto &r : recs) {
       float ms = 0.f;
       ck(cudaEventSynchronize(r.b), "event sync");
@@ -162,6 +168,9 @@ struct Profiler : ProfHook {
   }
   void reset() {
     harvest();
+    open.clear();
+    recs.clear();
+    used = 0;
     for (auto &t : tot) for (double &v : t) v = 0.0;
   }
   ~Profiler() {
@@ -256,7 +265,7 @@ struct bd_handle {
   double *d_uh1i, *d_uh1e, *d_uh2i, *d_uh2e, *d_gi, *d_ge;
   double rtol_scale = 1.0;
   // factorisation tuning (bidomain_autotune): outer panel width, batch groups, tensor cores
-  int tune_ob = 256, tune_groups = 1;
+  int tune_ob = 512, tune_groups = 1;
   cudaGraphExec_t pcg_exec[2] = {nullptr, nullptr};  // captured PCG chunk per method
   size_t pcg_nodes[2] = {0, 0};
   double gemv_schur_flops = 0, gemv_schur_bytes = 0, gemv_local_flops = 0, gemv_local_bytes = 0;
@@ -875,8 +884,10 @@ void linearize_t(bd_handle &h, Dense<T> &D) {
 }
 
 void linearize(bd_handle &h) {
+  h.prof.begin(PROF_LINEARIZE, h.s);
   if (h.mixed()) linearize_t(h, h.df);
   else linearize_t(h, h.dd);
+  h.prof.end(PROF_LINEARIZE, h.s, 0.0, 0.0);
   h.linearized = true;
 }
 
@@ -983,8 +994,8 @@ int pcg(bd_handle &h, int n, const double *b, double *x, Op A, Pc M, bd_solve_st
   const int key = h.opt.method == BD_FETIDP ? 1 : 0;
   if (h.opt.use_graphs && !h.pcg_exec[key]) {
     // capture one chunk of iterations once; every launch reads fixed handle buffers
-    const bool prof_on = h.prof.on;
-    h.prof.on = false;
+    const int prof_on = h.prof.on;
+    h.prof.on = 0;
     const long long l0 = launch_count();
     cudaGraph_t g = nullptr;
     ck(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal), "capture");
@@ -1085,7 +1096,9 @@ int solve_t(bd_handle &h, Dense<T> &D, const double *fi, const double *fe, doubl
   cudaStream_t s = h.s;
   // interior data: y_I = L_II^-1 f_I
   launch_gather_pairs(h.nint_nodes, h.d_int_node, fi, fe, h.d_fI, 1.0, nullptr, s);
+  h.prof.begin(PROF_TRSV, s);
   launch_trsv<T>(h.nsub, h.shK.max_e, h.d_Kdesc, h.d_vec_off_I, D.K, D.LdK, h.d_fI, h.d_yI, false, s);
+  h.prof.end(PROF_TRSV, s, 0.0, 0.0);
   launch_gemv<T>(h.gv_lgi.n, h.gv_lgi.max_rows, h.gv_lgi.max_cols, h.gv_lgi.d, D.K, h.d_yI, nullptr, h.d_yloc, 1.0,
                  nullptr, s);
   launch_gather_pairs(h.nif / 2, h.d_iface_node, fi, fe, h.d_fG, 1.0, nullptr, s);
@@ -1103,8 +1116,10 @@ int solve_t(bd_handle &h, Dense<T> &D, const double *fi, const double *fe, doubl
       bddc_t(h, D, x, y, dn, &f);
       return true;
     };
+    h.prof.begin(PROF_KRYLOV, s);
     reason = h.opt.krylov == BD_GMRES ? gmres(h, h.nif, h.d_fhat, h.d_uG, A, M, st)
                                       : pcg(h, h.nif, h.d_fhat, h.d_uG, A, M, st, AF, MF);
+    h.prof.end(PROF_KRYLOV, s, 0.0, 0.0);
   } else {
     // f~: local g = f_G[R] / mult - L_GI y_I, gbar = T_loc^T g -> (rD, gP); rP = sum gP
     launch_gather_scale_sub(h.nG_tot, h.d_R, h.d_fG, h.d_mult_iface, h.d_yloc, s);
@@ -1116,8 +1131,10 @@ int solve_t(bd_handle &h, Dense<T> &D, const double *fi, const double *fe, doubl
     auto A = [&](const double *x, double *y, const int *dn) { feti_F_t(h, D, x, y, dn); };
     auto M = [&](const double *x, double *y, const int *dn) { feti_M_t(h, D, x, y, dn); };
     auto unfused = [](const double *, double *, const int *, const DotFuse &) { return false; };
+    h.prof.begin(PROF_KRYLOV, s);
     reason = h.opt.krylov == BD_GMRES ? gmres(h, h.nlam, h.d_kb, h.d_kx, A, M, st)
                                       : pcg(h, h.nlam, h.d_kb, h.d_kx, A, M, st, unfused, unfused);
+    h.prof.end(PROF_KRYLOV, s, 0.0, 0.0);
     // w = St^-1 (f~ - B^T lambda); u_G = T (dual mean, primal)
     launch_jump_t(h.nwt, h.max_nc, h.d_wt, h.d_went, h.d_kx, h.d_w1, nullptr, s);
     launch_axpby(h.nD_tot, 1.0, h.d_rD2, -1.0, h.d_w1, s);
@@ -1128,7 +1145,9 @@ int solve_t(bd_handle &h, Dense<T> &D, const double *fi, const double *fe, doubl
   // interior recovery: u_I = L_II^-T (y_I - L_GI^T u_G)
   launch_gemv_t<T>(h.gv_lgit.n, h.gv_lgit.max_rows, h.gv_lgit.max_cols, h.gv_lgit.d, D.K, h.d_uG, h.d_R, h.d_yI, -1.0,
                    nullptr, s);
+  h.prof.begin(PROF_TRSV, s);
   launch_trsv<T>(h.nsub, h.shK.max_e, h.d_Kdesc, h.d_vec_off_I, D.K, D.LdK, h.d_yI, h.d_fI, true, s);
+  h.prof.end(PROF_TRSV, s, 0.0, 0.0);
   launch_scatter_pairs(h.nint_nodes, h.d_int_node, h.d_fI, si, se, s);
   launch_scatter_pairs(h.nif / 2, h.d_iface_node, h.d_uG, si, se, s);
   ck(cudaGetLastError(), "solve");
@@ -1173,6 +1192,7 @@ int step(bd_handle &h, const bd_stimulus *stim, bd_step_stats *out) {
   const double t_next = (h.step_n + 1) * h.tau;
   const StimParams sp = stim_params(h, stim, t_next);
   bd_step_stats st{};
+  h.prof.begin(PROF_STEP, s);
   launch_gating(h.N, h.d_uin, h.d_uen, h.d_w, h.d_wn, h.fp, s);
   // u^0 = u^n (the fallback)
   ck(cudaMemcpyAsync(h.d_ui, h.d_uin, sizeof(double) * h.N, cudaMemcpyDeviceToDevice, s), "copy");
@@ -1186,10 +1206,12 @@ int step(bd_handle &h, const bd_stimulus *stim, bd_step_stats *out) {
   h.rtol_scale = 1.0;
   if (h.mlp_on && h.hist_count >= 2) {
     // learned guess u^n + MLP(traces of u^n, u^{n-1}, u^{n-2}); kept only if its residual is smaller
+    h.prof.begin(PROF_MLP, s);
     mlp_features(h.mlp, h.nq, h.d_q_sub, h.d_q_loc, h.d_q_node, h.d_uin, h.d_uen, h.d_uh1i, h.d_uh1e, h.d_uh2i,
                  h.d_uh2e, nullptr, nullptr, s);
     mlp_forward(h.mlp, h.mlp.batch, s);
     mlp_guess(h.mlp, h.N, h.d_node_ptr, h.d_node_ent, h.d_uin, h.d_uen, h.d_gi, h.d_ge, s);
+    h.prof.end(PROF_MLP, s, 0.0, 0.0);
     std::swap(h.d_ui, h.d_gi); std::swap(h.d_ue, h.d_ge);  // residual at the guess
     const double g2 = trial_residual(h, sp, nullptr, nullptr, 0.0);
     std::swap(h.d_ui, h.d_gi); std::swap(h.d_ue, h.d_ge);
@@ -1271,12 +1293,14 @@ int step(bd_handle &h, const bd_stimulus *stim, bd_step_stats *out) {
   st.res_final = std::sqrt(fn2);
   if (h.mlp_on && h.hist_count >= 2 && h.step_n < h.opt.mlp_train_steps && reason == BD_OK) {
     // online training on (traces, u^{n+1} - u^n), before the gauge shift
+    h.prof.begin(PROF_MLP, s);
     MlpDev &M = h.mlp;
     ck(cudaMemsetAsync(M.T, 0, sizeof(float) * M.batch * M.n_out, s), "memset");
     ck(cudaMemsetAsync(M.mask, 0, sizeof(float) * M.batch * M.n_out, s), "memset");
     mlp_features(M, h.nq, h.d_q_sub, h.d_q_loc, h.d_q_node, h.d_uin, h.d_uen, h.d_uh1i, h.d_uh1e, h.d_uh2i,
                  h.d_uh2e, h.d_ui, h.d_ue, s);
     for (int ep = 0; ep < std::max(1, h.opt.mlp_epochs); ++ep) mlp_train_once(h, ep == 0);
+    h.prof.end(PROF_MLP, s, 0.0, 0.0);
     st.mlp_loss = read_scalar(h, h.d_scal + 4);
     h.mlp_steps_trained += 1;
   }
@@ -1294,6 +1318,7 @@ int step(bd_handle &h, const bd_stimulus *stim, bd_step_stats *out) {
   ck(cudaMemcpyAsync(h.d_uin, h.d_ui, sizeof(double) * h.N, cudaMemcpyDeviceToDevice, s), "copy");
   ck(cudaMemcpyAsync(h.d_uen, h.d_ue, sizeof(double) * h.N, cudaMemcpyDeviceToDevice, s), "copy");
   ck(cudaMemcpyAsync(h.d_w, h.d_wn, sizeof(double) * h.N, cudaMemcpyDeviceToDevice, s), "copy");
+  h.prof.end(PROF_STEP, s, 0.0, 0.0);
   ck(cudaStreamSynchronize(s), "step");
   if (h.prof.on) h.prof.harvest();
   h.step_n += 1;
@@ -1733,8 +1758,8 @@ int bidomain_autotune(bd_handle *h, bd_tune_result *out) {
     cudaEvent_t e0, e1;
     ck(cudaEventCreate(&e0), "event");
     ck(cudaEventCreate(&e1), "event");
-    const bool prof_on = h->prof.on;
-    h->prof.on = false;
+    const int prof_on = h->prof.on;
+    h->prof.on = 0;
     const int tc0 = h->opt.use_tensor_cores, ob0 = h->tune_ob, g0 = h->tune_groups;
     auto time_it = [&]() {
       linearize(*h);  // warm
@@ -1791,7 +1816,7 @@ int bidomain_profile(bd_handle *h, int enable) {
   return guard(h, [&] {
     ck(cudaStreamSynchronize(h->s), "sync");
     h->prof.reset();
-    h->prof.on = enable != 0;
+    h->prof.on = (enable == 1 || enable == 2) ? enable : 0;
     return BD_OK;
   });
 }

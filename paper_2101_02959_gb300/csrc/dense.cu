@@ -526,7 +526,7 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
     const int K1 = K0 + ob;
     for (int k0 = K0; k0 < std::min(K1, sh.max_e); k0 += kPW) {
       int max_below = 0, max_cols = 0;
-      double fl_panel = 0.0, fl_in = 0.0, by_in = 0.0;
+      double fl_panel = 0.0, fl_in = 0.0;
       for (int b = 0; b < sh.count; ++b) {
         if (k0 >= sh.e[b]) continue;
         const int w = std::min(kPW, sh.e[b] - k0);
@@ -537,7 +537,6 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
         fl_panel += (double)w * w * w / 3.0 + (double)below * w * w;
         const double ent = trapezoid(k0 + w, cend, sh.m[b]);
         fl_in += 2.0 * w * ent;
-        by_in += sizeof(T) * (2.0 * ent + (double)w * (below + cend - k0 - w));
       }
       if (prof) prof->begin(PROF_PANEL, s);
       k_bigpanel<T, false><<<dim3(1, sh.count), 256, bigpanel_smem<T, false>(), s>>>(d_desc, base, k0, d_err, store);
@@ -548,11 +547,12 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
         count_launch();
       }
       if (prof) prof->end(PROF_PANEL, s, fl_panel, 0.0);
-      // the rest of the outer block: rows [k0 + w, m), columns [k0 + w, min(K1, e))
+      // the rest of the outer block: rows [k0 + w, m), columns [k0 + w, min(K1, e)); timed
+      // with the panels (the long-K class holds only the trailing updates)
       if (max_below > 0 && max_cols > 0) {
-        if (prof) prof->begin(PROF_RANKK, s);
+        if (prof) prof->begin(PROF_PANEL, s);
         launch_rankk<T>(d_desc, base, 0, k0, K0, K1, max_below, max_cols, sh.count, s);
-        if (prof) prof->end(PROF_RANKK, s, fl_in, by_in);
+        if (prof) prof->end(PROF_PANEL, s, fl_in, 0.0);
       }
     }
     // outer update of the trailing columns [K1, e) with the finished outer panel

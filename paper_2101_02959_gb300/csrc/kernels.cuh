@@ -11,7 +11,13 @@ constexpr int kNB = 32;          // panel width of the partial Cholesky
 
 // Per-launch timing hook (CUDA events recorded on the launch stream) and
 // the library-wide kernel launch counter.
-enum { PROF_RANKK = 0, PROF_PANEL = 1, PROF_GEMV = 2, PROF_RESID = 3, PROF_NCLASS = 4 };
+// Kernel classes (timed per launch) and regions of a step (timed as a whole, also
+// while the Krylov iterations replay as CUDA graphs).
+enum {
+  PROF_RANKK = 0, PROF_PANEL = 1, PROF_GEMV = 2, PROF_RESID = 3,
+  PROF_LINEARIZE = 4, PROF_KRYLOV = 5, PROF_TRSV = 6, PROF_MLP = 7, PROF_STEP = 8,
+  PROF_NCLASS = 9, PROF_FIRST_REGION = 4
+};
 struct ProfHook {
   virtual void begin(int id, cudaStream_t s) = 0;
   virtual void end(int id, cudaStream_t s, double flops, double bytes) = 0;
@@ -57,7 +63,7 @@ struct EngineShape {
   int count;
   int max_e, max_m;
   std::vector<int> m, e;  // host copies for per-step grid sizes
-  int ob = 256;           // outer block: columns per long-K trailing update (multiple of 128)
+  int ob = 512;           // outer block: columns per long-K trailing update (multiple of 128)
 };
 // The engine works through outer blocks of sh.ob columns: panels of kEnginePanel
 // columns (k_bigpanel), each followed by an update of the rest of its block, then

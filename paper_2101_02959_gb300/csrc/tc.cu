@@ -7,12 +7,13 @@
 // (three MMAs per K step, FP32 accumulation in tensor memory), which keeps the
 // Schur complement at FP32 accuracy.
 //
-// Per K chunk of 32: 128 threads load the two 128 x 32 tiles (coalesced),
-// split them and store hi / lo copies in shared memory in the K-major layout
-// with the 128-byte swizzle; one thread issues the MMAs and commits them to an
-// mbarrier; the CTA waits on it (bounded) before reusing the buffers.  The
-// epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM lanes
-// 32w .. 32w+31 = tile rows) and subtracts it from C.
+// Per K chunk of 32: 128 threads load the two 128 x 32 tiles (cp.async, two
+// chunks ahead), split them and store hi / lo copies in shared memory in the
+// K-major layout with the 128-byte swizzle; one thread issues the MMAs and
+// commits them to an mbarrier; the CTA waits on it (bounded) before reusing the
+// buffers.  The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
+// lanes 32w .. 32w+31 = tile rows), stages it in shared memory and subtracts it
+// from C row by row (coalesced).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -25,6 +26,7 @@ namespace {
 constexpr int kTM = 128;          // tile rows (MMA M) and columns (MMA N)
 constexpr int kKc = 32;           // fp32 K elements per chunk = one 128-byte swizzle row
 constexpr int kTileBytes = kTM * kKc * 4;  // 16 KB per operand copy
+constexpr int kRawStages = 3;              // FP32 load stages (prefetch distance 2 chunks)
 constexpr uint32_t kTmemCols = 128;
 constexpr long long kWaitLimit = 1LL << 22;
 
@@ -86,10 +88,10 @@ __device__ inline void cp_async16(uint32_t dst, const void *src, uint32_t bytes)
 }
 
 // mode 1: rows/cols [e, m), K = [0, e); mode 2: rows [K1, m), cols [K1, e), K = [K0, K1).
-// Pipeline per K chunk i (buffers b = i % 2):
-//   raw[b] (FP32 A and B tiles, cp.async, swizzled) -> split into hi/lo[b] -> 12 MMAs on hi/lo[b]
-// with chunk i+1's loads in flight during the split of chunk i and the MMAs of chunk i
-// running while chunk i+1 is split (mbar[b] guards hi/lo[b] against reuse).
+// Pipeline per K chunk i (raw stage i % 3, operand buffer b = i % 2):
+//   raw (FP32 A and B tiles, cp.async, swizzled) -> split into hi/lo[b] -> 12 MMAs on hi/lo[b]
+// with the loads of chunks i+1 and i+2 in flight during the split of chunk i and the
+// MMAs of chunk i running while chunk i+1 is split (mbar[b] guards hi/lo[b] against reuse).
 __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__ desc, float *__restrict__ base,
                                                      int mode, int K0, int K1, int nct, int *__restrict__ err) {
   const MatDesc d = desc[blockIdx.y];
@@ -112,9 +114,9 @@ __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__
   const uint32_t raw0 = smem_addr(smem_raw);
   const uint32_t tiles = (raw0 + 1023u) & ~1023u;
   unsigned char *tp = smem_raw + (tiles - raw0);
-  // layout: raw A/B per buffer (2 x 2 x 16 KB), then hi/lo A/B per buffer (2 x 4 x 16 KB)
+  // layout: raw A/B per stage (kRawStages x 2 x 16 KB), then hi/lo A/B per buffer (2 x 4 x 16 KB)
   auto raw_off = [](int b, int op) { return (uint32_t)((b * 2 + op) * kTileBytes); };
-  auto op_off = [](int b, int q) { return (uint32_t)(4 * kTileBytes + (b * 4 + q) * kTileBytes); };
+  auto op_off = [](int b, int q) { return (uint32_t)(2 * kRawStages * kTileBytes + (b * 4 + q) * kTileBytes); };
   const int tid = threadIdx.x, warp = tid >> 5;
 
   if (warp == 0) {
@@ -156,11 +158,16 @@ __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__
   uint32_t phase[2] = {0u, 0u};
   int pending[2] = {0, 0};  // an MMA batch is in flight on hi/lo[b]
   bool ok = true;
+  // raw stages: chunk i lands in stage i % kRawStages, loaded kRawStages - 1 chunks ahead
   load(kb, 0);
+  if (nchunk > 1) load(kb + kKc, 1);
   for (int i = 0; i < nchunk && ok; ++i) {
-    const int b = i & 1;
-    if (i + 1 < nchunk) {
-      load(kb + (i + 1) * kKc, b ^ 1);
+    const int b = i & 1, rs = i % kRawStages;
+    // stage (i + 2) % 3 was last read by the split of chunk i - 1 (before its barrier)
+    if (i + 2 < nchunk) {
+      load(kb + (i + 2) * kKc, (i + 2) % kRawStages);
+      asm volatile("cp.async.wait_group 2;");
+    } else if (i + 1 < nchunk) {
       asm volatile("cp.async.wait_group 1;");
     } else {
       asm volatile("cp.async.wait_group 0;");
@@ -184,7 +191,7 @@ __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__
       const uint32_t off = (uint32_t)r * 128u + (uint32_t)((j ^ (r & 7)) * 16);
 #pragma unroll
       for (int op = 0; op < 2; ++op) {
-        const float4 x = *reinterpret_cast<const float4 *>(tp + raw_off(b, op) + off);
+        const float4 x = *reinterpret_cast<const float4 *>(tp + raw_off(rs, op) + off);
         const float4 hi = make_float4(tf32_round(x.x), tf32_round(x.y), tf32_round(x.z), tf32_round(x.w));
         const float4 lo = make_float4(tf32_round(x.x - hi.x), tf32_round(x.y - hi.y), tf32_round(x.z - hi.z),
                                       tf32_round(x.w - hi.w));
@@ -225,8 +232,12 @@ __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__
   }
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
-    // epilogue: warp w reads TMEM lanes 32w + lane (tile row), 32 columns per load
-    const int r = r0 + warp * 32 + (tid & 31);
+    // epilogue: warp w reads TMEM lanes 32w + lane (tile rows), 32 columns per load,
+    // stages them in shared memory (the operand buffers are free now) and updates C
+    // one row per instruction (coalesced 128-byte rows)
+    __syncthreads();
+    float *stage = reinterpret_cast<float *>(tp) + warp * 32 * 33;
+    const int lane = tid & 31;
     for (int cc = 0; cc < kTM; cc += 32) {
       uint32_t v[32];
       const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cc;
@@ -241,14 +252,25 @@ __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__
             "=r"(v[30]), "=r"(v[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if (r < d.m) {
-        float *crow = A + (long long)r * d.ld;
 #pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const int c = c0 + cc + q;
-          if (c < colend) crow[c] -= __uint_as_float(v[q]);
+      for (int q = 0; q < 32; ++q) stage[lane * 33 + q] = __uint_as_float(v[q]);
+      __syncwarp();
+      const int c = c0 + cc + lane;
+      const bool vc = c < colend;
+      {  // all 32 rows' loads in flight, then their stores
+        float cv[32];
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          const int r = r0 + warp * 32 + u;
+          cv[u] = (vc && r < d.m) ? A[(long long)r * d.ld + c] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          const int r = r0 + warp * 32 + u;
+          if (vc && r < d.m) A[(long long)r * d.ld + c] = cv[u] - stage[u * 33 + lane];
         }
       }
+      __syncwarp();
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -259,7 +281,7 @@ __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__
   }
 }
 
-static constexpr int kTcSmem = 12 * kTileBytes + 1024;  // 2 x raw A/B + 2 x hi/lo A/B + alignment
+static constexpr int kTcSmem = (2 * kRawStages + 8) * kTileBytes + 1024;  // raw stages + 2 x hi/lo A/B + alignment
 
 bool tc_configure() {
   return cudaFuncSetAttribute(k_rankk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) == cudaSuccess;

@@ -245,3 +245,23 @@ def test_not_spd_is_reported():
     with pytest.raises(binding.BidomainError) as e:
         s.linearize(ui, z, z)
     assert e.value.code == -2
+
+
+def test_profile_regions_nest_and_add_up():
+    """Region timers (also with graph replay) nest inside the step and account for it."""
+    prob = oracle_problem("cube8ve")
+    ui, ue, w = synth.initial_state(prob.N, 0)
+    s = _solver("cube8ve", precision="mixed", use_graphs=1)
+    s.set_state(ui, ue, w, 0.0)
+    s.step(synth.STIMULUS)
+    s.profile(2)
+    for _ in range(2):
+        assert s.step(synth.STIMULUS)["reason"] == 0
+    r = {k: s.profile_read(k) for k in ("step", "linearize", "krylov", "trsv", "mlp")}
+    assert r["step"]["launches"] == 2
+    assert r["linearize"]["launches"] >= 2 and r["krylov"]["launches"] >= 2
+    assert r["trsv"]["launches"] == 2 * r["krylov"]["launches"]
+    inner = r["linearize"]["ms"] + r["krylov"]["ms"] + r["trsv"]["ms"]
+    assert 0.0 < inner <= r["step"]["ms"] * 1.001
+    assert s.profile_read("rankk")["launches"] == 0  # kernel classes stay off in region mode
+    s.close()
