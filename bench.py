@@ -118,7 +118,7 @@ def run_gpu(args, w, rank, world):
     def timed(precision, method, profile=False, clocks=None, graphs=1, learned=0):
         s = binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, stream=stream.cuda_stream,
                            precision=precision, method=method, use_graphs=graphs, learned_guess=learned,
-                           mlp_train_steps=args.steps + args.warmup + 1,
+                           mlp_train_steps=args.steps + args.warmup + 1, mlp_epochs=args.mlp_epochs,
                            use_tensor_cores=int(precision == "mixed" and args.tc),
                            lag_jacobian=int(precision == "mixed" and args.lag))
         s.set_state(*dstate, 0.0)
@@ -170,7 +170,7 @@ def run_gpu(args, w, rank, world):
     # e2e: the same chosen run through host buffers, state copied in and out every step
     s = binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, stream=stream.cuda_stream,
                        precision=args.precision, method=args.method, use_graphs=1, learned_guess=args.learned,
-                       mlp_train_steps=args.steps + args.warmup + 1,
+                       mlp_train_steps=args.steps + args.warmup + 1, mlp_epochs=args.mlp_epochs,
                        use_tensor_cores=int(args.precision == "mixed" and args.tc),
                        lag_jacobian=int(args.precision == "mixed" and args.lag))
     hs = (ui0.copy(), ue0.copy(), w0.copy())
@@ -342,6 +342,7 @@ def main():
     ap.add_argument("--tc", type=int, default=1, help="1: tensor-core (tcgen05) Schur updates in mixed precision")
     ap.add_argument("--lag", type=int, default=1, help="1: chord Newton (one factorisation per time step), mixed only")
     ap.add_argument("--autotune", type=int, default=1, help="1: autotune the factorisation after the warm-up")
+    ap.add_argument("--mlp-epochs", type=int, default=4, help="training passes of the learned guess per step")
     ap.add_argument("--cpu-steps", type=int, default=1, help="oracle time steps in the CPU baseline (0: skip)")
     ap.add_argument("--sweep", action="store_true", help="H/h optimality sweep instead of the benchmark")
     ap.add_argument("--sweep-hh", type=int, nargs="*", default=[4, 8, 12, 16])

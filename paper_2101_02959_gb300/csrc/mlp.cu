@@ -9,19 +9,33 @@
 
 namespace bd {
 
-// C[m][n] = act(sum_k A[m][k] W[n][k] + b[n]); one warp per output, lanes over k.
+// C[m][n] = act(sum_k A[m][k] W[n][k] + b[n]); one warp per (m, 4 consecutive n), lanes
+// over k: every A value is loaded once for the four outputs.
 __global__ void k_mlp_fwd(int M, int N, int K, const float *__restrict__ A, const __nv_bfloat16 *__restrict__ W,
                           const float *__restrict__ b, float *__restrict__ Z, float *__restrict__ H, int relu) {
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (gw >= M * N) return;
-  const int m = gw / N, n = gw % N;
+  const int nq = (N + 3) / 4;
+  if (gw >= M * nq) return;
+  const int m = gw / nq, n0 = (gw % nq) * 4;
   const float *a = A + (long long)m * K;
-  const __nv_bfloat16 *w = W + (long long)n * K;
-  float acc = 0.f;
-  for (int k = lane; k < K; k += 32) acc += a[k] * __bfloat162float(w[k]);
-  acc = warp_sum(acc);
-  if (lane == 0) {
-    const float z = acc + b[n];
+  const __nv_bfloat16 *w[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) w[j] = W + (long long)min(n0 + j, N - 1) * K;
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int k = lane; k < K; k += 32) {
+    const float av = a[k];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] += av * __bfloat162float(w[j][k]);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) acc[j] = warp_sum(acc[j]);
+  if (lane < 4 && n0 + lane < N) {
+    float v = acc[0];
+#pragma unroll
+    for (int j = 1; j < 4; ++j)
+      if (lane == j) v = acc[j];
+    const int n = n0 + lane;
+    const float z = v + b[n];
     if (Z) Z[(long long)m * N + n] = z;
     H[(long long)m * N + n] = relu ? fmaxf(z, 0.f) : z;
   }
@@ -42,31 +56,57 @@ __global__ void k_mlp_loss(int total, const float *__restrict__ Y, const float *
   if (threadIdx.x == 0) partial[blockIdx.x] = acc * inv_cnt;
 }
 
-// dW[n][k] = sum_m dZ[m][n] A[m][k]; db[n] = sum_m dZ[m][n]  (M = batch, small)
+// dW[n][k] = sum_m dZ[m][n] A[m][k]; db[n] = sum_m dZ[m][n]  (M = batch, small).
+// One thread per (k, 4 consecutive n): every A value is loaded once for four outputs.
 __global__ void k_mlp_wgrad(int M, int N, int K, const float *__restrict__ dZ, const float *__restrict__ A,
                             float *__restrict__ dW, float *__restrict__ db) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)N * (K + 1)) return;
-  const int n = (int)(t / (K + 1)), k = (int)(t % (K + 1));
-  float acc = 0.f;
-  if (k < K) {
-    for (int m = 0; m < M; ++m) acc += dZ[(long long)m * N + n] * A[(long long)m * K + k];
-    dW[(long long)n * K + k] = acc;
-  } else {
-    for (int m = 0; m < M; ++m) acc += dZ[(long long)m * N + n];
-    db[n] = acc;
+  const int nq = (N + 3) / 4;
+  if (t >= (long long)nq * (K + 1)) return;
+  const int n0 = (int)(t / (K + 1)) * 4, k = (int)(t % (K + 1));
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int m = 0; m < M; ++m) {
+    const float av = (k < K) ? A[(long long)m * K + k] : 1.f;
+    const float *dz = dZ + (long long)m * N;
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (n0 + j < N) acc[j] += dz[n0 + j] * av;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (n0 + j >= N) continue;
+    if (k < K) dW[(long long)(n0 + j) * K + k] = acc[j];
+    else db[n0 + j] = acc[j];
   }
 }
 
-// dA[m][k] = (sum_n dZ[m][n] W[n][k]) * (Zprev[m][k] > 0)   (ReLU backward of the previous layer)
-__global__ void k_mlp_bgrad(int M, int N, int K, const float *__restrict__ dZ, const __nv_bfloat16 *__restrict__ W,
-                            const float *__restrict__ Zprev, float *__restrict__ dA) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)M * K) return;
-  const int m = (int)(t / K), k = (int)(t % K);
-  float acc = 0.f;
-  for (int n = 0; n < N; ++n) acc += dZ[(long long)m * N + n] * __bfloat162float(W[(long long)n * K + k]);
-  dA[t] = Zprev[t] > 0.f ? acc : 0.f;
+// dA[m][k] = (sum_n dZ[m][n] W[n][k]) * (Zprev[m][k] > 0)   (ReLU backward of the previous layer).
+// One CTA per (m, 32 consecutive k): the 8 warps split the n range, lane = k, and their
+// partial sums are added in a fixed order.
+__global__ void __launch_bounds__(256) k_mlp_bgrad(int M, int N, int K, const float *__restrict__ dZ,
+                                                   const __nv_bfloat16 *__restrict__ W,
+                                                   const float *__restrict__ Zprev, float *__restrict__ dA) {
+  __shared__ float part[8][33];
+  const int m = blockIdx.y, k = blockIdx.x * 32 + (threadIdx.x & 31), wid = threadIdx.x >> 5;
+  const float *dz = dZ + (long long)m * N;
+  float a0 = 0.f, a1 = 0.f;
+  if (k < K) {
+    int n = wid;
+    for (; n + 8 < N; n += 16) {
+      a0 += dz[n] * __bfloat162float(W[(long long)n * K + k]);
+      a1 += dz[n + 8] * __bfloat162float(W[(long long)(n + 8) * K + k]);
+    }
+    for (; n < N; n += 8) a0 += dz[n] * __bfloat162float(W[(long long)n * K + k]);
+  }
+  part[wid][threadIdx.x & 31] = a0 + a1;
+  __syncthreads();
+  if (wid == 0 && k < K) {
+    float acc = 0.f;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc += part[q][threadIdx.x];
+    const long long t = (long long)m * K + k;
+    dA[t] = Zprev[t] > 0.f ? acc : 0.f;
+  }
 }
 
 // Adam with bias correction; refreshes the bfloat16 copy used by the forward pass.
@@ -140,7 +180,7 @@ __global__ void k_mlp_guess(int n, int maxq, const int *__restrict__ ptr, const 
 void mlp_forward(const MlpDev &m, int B, cudaStream_t s) {
   const int H = m.n_hidden;
   auto fwd = [&](int N, int K, const float *A, const __nv_bfloat16 *W, const float *b, float *Z, float *Hh, int relu) {
-    const long long warps = (long long)B * N;
+    const long long warps = (long long)B * ((N + 3) / 4);
     k_mlp_fwd<<<(int)((warps * 32 + 255) / 256), 256, 0, s>>>(B, N, K, A, W, b, Z, Hh, relu);
     count_launch();
   };
@@ -154,12 +194,11 @@ void mlp_backward(const MlpDev &m, int B, float inv_cnt, double *partial, cudaSt
   const int total = B * m.n_out;
   k_mlp_loss<<<kRedBlocks, 256, 0, s>>>(total, m.Y, m.T, m.mask, inv_cnt, m.dY, partial);
   auto wg = [&](int N, int K, const float *dZ, const float *A, float *dW, float *db) {
-    const long long t = (long long)N * (K + 1);
+    const long long t = (long long)((N + 3) / 4) * (K + 1);
     k_mlp_wgrad<<<(int)((t + 255) / 256), 256, 0, s>>>(B, N, K, dZ, A, dW, db);
   };
   auto bg = [&](int N, int K, const float *dZ, const __nv_bfloat16 *W, const float *Zp, float *dA) {
-    const long long t = (long long)B * K;
-    k_mlp_bgrad<<<(int)((t + 255) / 256), 256, 0, s>>>(B, N, K, dZ, W, Zp, dA);
+    k_mlp_bgrad<<<dim3(ceil_div(K, 32), B), 256, 0, s>>>(B, N, K, dZ, W, Zp, dA);
   };
   wg(m.n_out, H, m.dY, m.H2, m.g + m.off_W3, m.g + m.off_b3);
   bg(m.n_out, H, m.dY, m.Wb3, m.Z2, m.dZ2);
