@@ -206,22 +206,39 @@ def run_gpu(args, w, rank, world):
     return out
 
 
-# DRAM bytes per launch of k_rankk128, averaged over every launch of a slab32 run
-# (ncu dram__bytes_read.sum + dram__bytes_write.sum; profiles/rankk128_slab32_mixed_bddc.md).
-# It stands only while the kernel's source text is the one it was measured on.
-RANKK128_TRAFFIC = {"bytes_per_launch": 52.28e6, "source_sha256_16": "9511215a957c252b"}
+# DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, averaged over every
+# launch of a slab32 run; profiles/*_slab32_mixed_bddc.md).  A figure stands only while its
+# kernel's source text is the one it was measured on (first 16 hex digits of its sha256).
+TRAFFIC = {
+    "k_rankk128": {"bytes_per_launch": 21.11e6, "sha": "69ca1105c88785a7",
+                   "span": ("__global__ void __launch_bounds__(256) k_rankk128(",
+                            "template <typename T>\nstatic void launch_rankk(")},
+    "k_bigpanel": {"bytes_per_launch": 7.78e6, "sha": "a3c19f2ca59fb23c",
+                   "span": ("template <typename T, bool ROWS>\n__global__ void __launch_bounds__(256, ROWS ? 2 : 1) "
+                            "k_bigpanel(", "// ---- rank-k update of lower tiles")},
+    "k_rankk_tc": {"bytes_per_launch": 72.36e6, "sha": "f793e17009497dfe", "file": "tc.cu",
+                   "span": ("__global__ void __launch_bounds__(128, 1) k_rankk_tc(",
+                            "static constexpr int kTcSmem")},
+}
 
 
-def rankk128_traffic():
+def kernel_sha(name):
     import hashlib
-    src = open(os.path.join(ROOT, "paper_2101_02959_gb300", "csrc", "dense.cu")).read()
+    src = open(os.path.join(ROOT, "paper_2101_02959_gb300", "csrc", TRAFFIC[name].get("file", "dense.cu"))).read()
+    a_txt, b_txt = TRAFFIC[name]["span"]
     try:
-        a = src.index("__global__ void __launch_bounds__(256) k_rankk128(")
-        b = src.index("template <typename T>\nstatic void launch_rankk(")
+        a = src.index(a_txt)
+        b = src.index(b_txt, a)
     except ValueError:
         return None
-    h = hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
-    return RANKK128_TRAFFIC["bytes_per_launch"] if h == RANKK128_TRAFFIC["source_sha256_16"] else None
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
+
+
+def traffic(name):
+    t = TRAFFIC.get(name)
+    if not t or t["bytes_per_launch"] is None:
+        return None
+    return t["bytes_per_launch"] if kernel_sha(name) == t["sha"] else None
 
 
 def roofline(prof, precision, tc_used=False):
@@ -240,18 +257,20 @@ def roofline(prof, precision, tc_used=False):
         tf32 = (pk[src] if src else 1700.0) * 1.1 / 2.25
         peak = tf32 / 3.0
         r = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-             "traffic": None, "kernel": "k_rankk_tc",
+             "traffic": traffic("k_rankk_tc"), "kernel": "k_rankk_tc",
              "peak_source": ("of measured: bf16_tflops_sustained x 1.1/2.25 (tf32) / 3 (hi/lo split)" if src
                              else "of fallback: 1.7 PF bf16 sustained x 1.1/2.25 / 3")}
     elif dom in ("rankk", "panel"):
         achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12
         peak = FP32_SIMT_PEAK if precision == "mixed" else FP64_PEAK
-        traffic = rankk128_traffic() if (dom == "rankk" and precision == "mixed" and not tc_used) else None
+        if dom == "rankk":
+            kern = "k_rankk128" if precision == "mixed" and not tc_used else \
+                "k_rankk_tc" if precision == "mixed" else "k_rankk<double>"
+        else:
+            kern = "k_bigpanel"  # diagonal + rows launches (the class also times the in-block updates)
         r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-             "traffic": traffic,
-             "kernel": ("k_rankk128" if precision == "mixed" and not tc_used else
-                        "k_rankk_tc" if precision == "mixed" else "k_rankk<double>") if dom == "rankk"
-             else "k_bigpanel",
+             "traffic": traffic(kern) if precision == "mixed" else None,
+             "kernel": kern,
              "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz" if precision == "mixed"
                              else "nominal GB300 FP64 (recipe table)")}
     else:

@@ -265,7 +265,7 @@ struct bd_handle {
   double *d_uh1i, *d_uh1e, *d_uh2i, *d_uh2e, *d_gi, *d_ge;
   double rtol_scale = 1.0;
   // factorisation tuning (bidomain_autotune): outer panel width, batch groups, tensor cores
-  int tune_ob = 512, tune_groups = 1;
+  int tune_ob = 256, tune_groups = 1;
   cudaGraphExec_t pcg_exec[2] = {nullptr, nullptr};  // captured PCG chunk per method
   size_t pcg_nodes[2] = {0, 0};
   double gemv_schur_flops = 0, gemv_schur_bytes = 0, gemv_local_flops = 0, gemv_local_bytes = 0;

@@ -63,7 +63,7 @@ struct EngineShape {
   int count;
   int max_e, max_m;
   std::vector<int> m, e;  // host copies for per-step grid sizes
-  int ob = 512;           // outer block: columns per long-K trailing update (multiple of 128)
+  int ob = 256;           // outer block: columns per long-K trailing update (multiple of 128)
 };
 // The engine works through outer blocks of sh.ob columns: panels of kEnginePanel
 // columns (k_bigpanel), each followed by an update of the rest of its block, then
