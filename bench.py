@@ -7,8 +7,8 @@ stimulus; 20 time steps.  A "step" is one time step: gating, then Newton with
 the Jacobian solved by PCG + BDDC deluxe (or FETI-DP), at the paper's
 tolerances (KSP rtol 1e-8, SNES rtol 1e-4).
 
-The chosen solver (mixed precision: float32 local factors, Schur complements
-and coarse problem, float64 Krylov / Newton) is timed next to the plain
+The chosen solver (mixed precision: float32 local factors and Schur
+complements, float64 Krylov / Newton / coarse solve) is timed next to the plain
 float64 GPU solver on the same mesh.  Inputs are resident in HBM for `value`;
 `e2e` repeats the chosen run through the C-ABI with host buffers (state copied
 in and out every step).  With --gpus N > 1 every rank runs an independent
@@ -419,7 +419,7 @@ def main():
     line = {
         "metric": METRIC, "value": ms, "unit": "ms/time step", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 local and coarse factors + f64 Krylov/Newton" if args.precision == "mixed"
+        "vs_baseline": None, "dtype": "f32 local factors (tf32 tensor cores) + f64 Krylov/Newton/coarse solve" if args.precision == "mixed"
         else "f64", "data": "synthetic",
         "config": {"workload": describe(w), "unknowns": 2 * r["N"], "method": args.method + "-deluxe",
                    "krylov": "pcg", "precision": args.precision, "learned_guess": bool(args.learned),

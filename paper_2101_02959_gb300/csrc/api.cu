@@ -227,6 +227,7 @@ struct bd_handle {
   long long K_el = 0, A_el = 0, So_el = 0, Z_el = 0, SDD_el = 0, Blk_el = 0, CA_el = 0, Sinv_el = 0, Dd_el = 0;
   int K_blk = 0, A_blk = 0, C_blk = 0;  // slots of the diagonal-block stores
   int ld_co = 0;
+  double *d_Co64 = nullptr, *d_CoInv64 = nullptr, *d_CoW = nullptr, *d_CoY = nullptr;  // FP64 coarse
   GemvSet gv_schur, gv_local, gv_psit, gv_coarse, gv_sdd, gv_lgi, gv_lgit, gv_drest, gv_dext;
   GemmTask *d_gemm = nullptr;
   int n_gemm = 0;
@@ -701,6 +702,10 @@ void setup_handle(bd_handle &h) {
     std::vector<long long> src;
     for (auto &l : lists) { for (long long v : l) src.push_back(v); ptr.push_back((int)src.size()); }
     h.d_co_ptr = m.upload(ptr, s);
+    h.d_Co64 = m.alloc<double>((size_t)np * np);
+    h.d_CoInv64 = m.alloc<double>((size_t)np * np);
+    h.d_CoW = m.alloc<double>((size_t)np * np);
+    h.d_CoY = m.alloc<double>((size_t)np * np);
     h.d_co_src = m.upload(src, s);
 
   }
@@ -774,7 +779,7 @@ void setup_handle(bd_handle &h) {
     for (const GemvSet *g : {&h.gv_schur, &h.gv_local, &h.gv_psit, &h.gv_coarse, &h.gv_sdd, &h.gv_lgi, &h.gv_lgit,
                              &h.gv_drest, &h.gv_dext})
       need = std::max(need, el * (size_t)std::max(g->max_rows, g->max_cols));
-    need = std::max(need, el * ((size_t)h.np + h.gv_psit.max_rows));  // fused coarse solve
+    need = std::max(need, sizeof(double) * (size_t)h.np + el * h.gv_psit.max_rows);  // fused coarse solve
     if (need > dense_smem_limit())
       throw Status(BD_ERR_ARG, "local problem too large for the shared-memory staging of the dense kernels (" +
                                    std::to_string(need) + " bytes); use more subdomains");
@@ -878,9 +883,11 @@ void linearize_t(bd_handle &h, Dense<T> &D) {
   engine_partial_cholesky<T>(h.shC, h.d_Cdesc, D.CA, h.d_err, s, D.Linv);
   launch_copy<T, T>(h.cp_sinv.n, h.cp_sinv.max_elems, h.cp_sinv.d, D.CA, D.Sinv, s);
   launch_small_gemm<T>(h.n_gemm, h.max_nc, h.d_gemm, D.Sinv, D.Blk, D.Dd, s);
-  launch_coarse_aug<T>(h.np, h.gauge_primal, h.d_co_ptr, h.d_co_src, D.Aug, D.Co, h.ld_co, s);
+  // coarse: S_PiPi assembled in FP64, factored in the local precision, inverse refined to FP64
+  launch_coarse_aug<T>(h.np, h.gauge_primal, h.d_co_ptr, h.d_co_src, D.Aug, D.Co, h.ld_co, s, h.d_Co64);
   engine_partial_cholesky<T>(h.shCo, h.d_Codesc, D.Co, h.d_err, s, D.LdCo);
   launch_copy<T, T>(h.cp_coinv.n, h.cp_coinv.max_elems, h.cp_coinv.d, D.Co, D.CoInv, s);
+  coarse_refine64<T>(h.np, D.CoInv, h.d_Co64, h.d_CoInv64, h.d_CoW, h.d_CoY, s);
 }
 
 void linearize(bd_handle &h) {
@@ -912,7 +919,7 @@ void st_inv_t(bd_handle &h, Dense<T> &D, const double *rP, const double *rD, con
   launch_gemv<T>(h.gv_local.n, h.gv_local.max_rows, h.gv_local.max_cols, h.gv_local.d, D.Z, rD, nullptr, h.d_ydc,
                  1.0, done, h.s);
   h.prof.end(PROF_GEMV, h.s, h.gemv_local_flops, h.gemv_local_bytes * sizeof(T));
-  launch_coarse_psit<T>(h.gv_psit.n, h.gv_psit.max_rows, h.gv_psit.max_cols, h.gv_psit.d, D.Z, D.CoInv, h.np,
+  launch_coarse_psit<T>(h.gv_psit.n, h.gv_psit.max_rows, h.gv_psit.max_cols, h.gv_psit.d, D.Z, h.d_CoInv64, h.np,
                         h.gauge_primal, h.d_pl_ptr, h.d_pl_idx, h.d_ydc + h.nD_tot, rP_csr ? nullptr : rP, rP_csr,
                         h.d_prim_x, h.nd, h.d_zbar, h.d_ydc, done, h.s);
 }

@@ -152,7 +152,7 @@ __global__ void k_class_aug(const ClassTask *__restrict__ cls, const PairTask *_
 // column become a unit row and column.  Written as AugCo = [[S_PP, I], [I, 0]].
 template <typename T>
 __global__ void k_coarse_aug(int np, int gauge, const int *__restrict__ ptr, const long long *__restrict__ src,
-                             const T *__restrict__ abase, T *__restrict__ co, int ld) {
+                             const T *__restrict__ abase, T *__restrict__ co, int ld, double *__restrict__ co64) {
   const int m = 2 * np;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)m * m;
        t += (long long)gridDim.x * blockDim.x) {
@@ -168,7 +168,52 @@ __global__ void k_coarse_aug(int np, int gauge, const int *__restrict__ ptr, con
       v = (b - np == a) ? 1.0 : 0.0;
     }
     co[(long long)a * ld + b] = (T)v;
+    if (co64 && a < np && b < np) co64[(long long)a * np + b] = v;  // S_PiPi in FP64 (gauge row pinned)
   }
+}
+
+// C = alpha A B + beta D for n x n FP64 matrices (row-major, leading dimension n): the
+// coarse inverse refinement.  16 x 16 output tiles, operands staged in shared memory.
+__global__ void __launch_bounds__(256) k_gemm64(int n, const double *__restrict__ A, const double *__restrict__ B,
+                                                const double *__restrict__ D, double alpha, double beta,
+                                                double *__restrict__ C) {
+  __shared__ double As[16][17], Bs[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i = blockIdx.y * 16 + ty, j = blockIdx.x * 16 + tx;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < n; k0 += 16) {
+    As[ty][tx] = (i < n && k0 + tx < n) ? A[(long long)i * n + k0 + tx] : 0.0;
+    Bs[ty][tx] = (k0 + ty < n && j < n) ? B[(long long)(k0 + ty) * n + j] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc += As[ty][k] * Bs[k][tx];
+    __syncthreads();
+  }
+  if (i < n && j < n) C[(long long)i * n + j] = alpha * acc + (D ? beta * D[(long long)i * n + j] : 0.0);
+}
+
+// X <- 2X - X C X, twice, from the local-precision inverse of C: the FP64 coarse inverse
+// (Newton-Schulz; the error squares each step).  X0 in T, result in X (FP64), W scratch.
+// Coarse problems above kRefineMaxNp keep the widened local-precision inverse.
+constexpr int kRefineMaxNp = 1024;
+template <typename T>
+__global__ void k_widen(long long n, const T *__restrict__ x, double *__restrict__ y) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    y[t] = (double)x[t];
+}
+template <typename T>
+void coarse_refine64(int np, const T *x0, const double *C, double *X, double *W, double *Y, cudaStream_t s) {
+  if (np == 0) return;
+  const long long nn = (long long)np * np;
+  k_widen<T><<<(int)std::min<long long>((nn + 255) / 256, 4096), 256, 0, s>>>(nn, x0, X);
+  const dim3 g(ceil_div(np, 16), ceil_div(np, 16));
+  const int iters = np <= kRefineMaxNp ? 2 : 0;  // O(np^3) FP64: beyond the limit X stays at x0
+  for (int it = 0; it < iters; ++it) {
+    k_gemm64<<<g, 256, 0, s>>>(np, C, X, nullptr, 1.0, 0.0, W);  // W = C X
+    k_gemm64<<<g, 256, 0, s>>>(np, X, W, X, -1.0, 2.0, Y);       // Y = 2X - X W
+    cudaMemcpyAsync(X, Y, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s);
+  }
+  count_launch(1 + 2 * iters);
 }
 
 // ---- coarse correction fused with the local primal correction -----------------
@@ -181,7 +226,7 @@ __global__ void k_coarse_aug(int np, int gauge, const int *__restrict__ ptr, con
 // from each of them (same inputs, same arithmetic).
 template <typename T>
 __global__ void __launch_bounds__(256) k_coarse_psit(const GemvDesc *__restrict__ tasks, const T *__restrict__ Z,
-                                                     const T *__restrict__ coinv, int np, int gauge,
+                                                     const double *__restrict__ coinv, int np, int gauge,
                                                      const int *__restrict__ pl_ptr, const int *__restrict__ pl_idx,
                                                      const double *__restrict__ yprim, const double *__restrict__ rP,
                                                      const CsrIn rPc, const int *__restrict__ prim_x, int nd,
@@ -192,8 +237,8 @@ __global__ void __launch_bounds__(256) k_coarse_psit(const GemvDesc *__restrict_
   const int c0 = blockIdx.x * 32;
   if (c0 >= t.cols) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T *cr = reinterpret_cast<T *>(smem_raw);  // [np] coarse right-hand side
-  T *xs = cr + np;                          // [t.rows] this subdomain's z_Pi
+  double *cr = reinterpret_cast<double *>(smem_raw);  // [np] coarse right-hand side (FP64)
+  T *xs = reinterpret_cast<T *>(cr + np);             // [t.rows] this subdomain's z_Pi
   __shared__ T part[8][33];
   for (int q = threadIdx.x; q < np; q += blockDim.x) {
     double acc = 0.0;
@@ -201,24 +246,24 @@ __global__ void __launch_bounds__(256) k_coarse_psit(const GemvDesc *__restrict_
     double v = -acc;
     if (rP) v += rP[q];
     else if (rPc.ptr) v += csr_row(rPc, q);
-    cr[q] = (T)((q == gauge) ? 0.0 : v);
+    cr[q] = (q == gauge) ? 0.0 : v;
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int p = wid; p < t.rows; p += 8) {
     const int q = prim_x[t.x_off + p] - nd;
-    const T *row = coinv + (long long)q * np;
-    T a0 = T(0), a1 = T(0);
+    const double *row = coinv + (long long)q * np;
+    double a0 = 0.0, a1 = 0.0;
     int c = lane;
     for (; c + 32 < np; c += 64) {
       a0 += row[c] * cr[c];
       a1 += row[c + 32] * cr[c + 32];
     }
     if (c < np) a0 += row[c] * cr[c];
-    const T z = warp_sum(a0 + a1);
+    const double z = warp_sum(a0 + a1);
     if (lane == 0) {
-      xs[p] = z;
-      if (blockIdx.x == 0) zbar[nd + q] = (double)z;
+      xs[p] = (T)z;
+      if (blockIdx.x == 0) zbar[nd + q] = z;
     }
   }
   __syncthreads();
@@ -245,12 +290,12 @@ __global__ void __launch_bounds__(256) k_coarse_psit(const GemvDesc *__restrict_
 }
 
 template <typename T>
-void launch_coarse_psit(int ntasks, int max_rows, int max_cols, const GemvDesc *tasks, const T *Z, const T *coinv,
+void launch_coarse_psit(int ntasks, int max_rows, int max_cols, const GemvDesc *tasks, const T *Z, const double *coinv,
                         int np, int gauge, const int *pl_ptr, const int *pl_idx, const double *yprim,
                         const double *rP, const CsrIn *rPc, const int *prim_x, int nd, double *zbar, double *ydc,
                         const int *done, cudaStream_t s) {
   if (ntasks == 0 || max_cols == 0) return;
-  const size_t sm = sizeof(T) * ((size_t)np + std::max(1, max_rows));
+  const size_t sm = sizeof(double) * (size_t)np + sizeof(T) * (size_t)std::max(1, max_rows);
   k_coarse_psit<T><<<dim3(ceil_div(max_cols, 32), ntasks), 256, sm, s>>>(
       tasks, Z, coinv, np, gauge, pl_ptr, pl_idx, yprim, rP, rPc ? *rPc : CsrIn{}, prim_x, nd, zbar, ydc, done);
   count_launch();
@@ -703,10 +748,10 @@ void launch_class_aug(int ncls, int max_n, const ClassTask *cls, const PairTask 
 
 template <typename T>
 void launch_coarse_aug(int np, int gauge, const int *ptr, const long long *src, const T *abase, T *co, int ld,
-                       cudaStream_t s) {
+                       cudaStream_t s, double *co64) {
   const long long tot = 4LL * np * np;
   const int gx = (int)std::min<long long>((tot + 255) / 256, 8192);
-  k_coarse_aug<T><<<std::max(gx, 1), 256, 0, s>>>(np, gauge, ptr, src, abase, co, ld);
+  k_coarse_aug<T><<<std::max(gx, 1), 256, 0, s>>>(np, gauge, ptr, src, abase, co, ld, co64);
   count_launch();
 }
 
@@ -871,13 +916,14 @@ void launch_dot2(int n, const double *a0, const double *b0, const double *a1, co
   template void launch_class_aug<T>(int, int, const ClassTask *, const PairTask *, const T *, const MatDesc *,  \
                                     T *, cudaStream_t);                                                        \
   template void launch_coarse_aug<T>(int, int, const int *, const long long *, const T *, T *, int,             \
-                                     cudaStream_t);                                                            \
+                                     cudaStream_t, double *);                                                  \
+  template void coarse_refine64<T>(int, const T *, const double *, double *, double *, double *, cudaStream_t);  \
   template void launch_jump_dt<T>(int, int, const WTask *, const WEnt *, const T *, const T *, const double *,  \
                                   double *, const int *, cudaStream_t);                                        \
   template void launch_jump_d<T>(int, int, const LamTask *, const PairTask *, const T *, const T *,             \
                                  const double *, double *, const int *, cudaStream_t);                         \
   template void launch_copy<T, T>(int, long long, const CopyTask *, const T *, T *, cudaStream_t);            \
-  template void launch_coarse_psit<T>(int, int, int, const GemvDesc *, const T *, const T *, int, int,          \
+  template void launch_coarse_psit<T>(int, int, int, const GemvDesc *, const T *, const double *, int, int,     \
                                       const int *, const int *, const double *, const double *, const CsrIn *, \
                                       const int *, int, double *, double *, const int *, cudaStream_t);
 BD_DD_INST(float)

@@ -56,15 +56,18 @@ void launch_class_aug(int ncls, int max_n, const ClassTask *cls, const PairTask 
 template <typename T>
 // coarse augmented matrix [[S_PiPi, I], [I, 0]] (assembled in FP64, stored as T)
 void launch_coarse_aug(int np, int gauge, const int *ptr, const long long *src, const T *abase, T *co, int ld,
-                       cudaStream_t s);
+                       cudaStream_t s, double *co64 = nullptr);
+// FP64 coarse inverse: X = (double) x0, then X <- 2X - X C X twice (Newton-Schulz); W, Y scratch
+template <typename T>
+void coarse_refine64(int np, const T *x0, const double *C, double *X, double *W, double *Y, cudaStream_t s);
 void launch_spmv(int n, const int *ptr, const int *col, const double *val, const double *x, double *y, int zero,
                  const int *done, cudaStream_t s);
 void launch_gather_sum(int n, const int *ptr, const int *idx, const double *src, double *y, int zero, double alpha,
                        const double *addend, const int *done, cudaStream_t s, const CsrIn *add_csr = nullptr);
 // coarse solve fused into the primal correction: c = rP (vector, sparse product or
-// absent) - sum_j (Psi^T r_D)_j, z_Pi = S_PiPi^-1 c into zbar[nd:], ydc -= Psi z_Pi
+// absent) - sum_j (Psi^T r_D)_j, z_Pi = S_PiPi^-1 c (FP64) into zbar[nd:], ydc -= Psi z_Pi
 template <typename T>
-void launch_coarse_psit(int ntasks, int max_rows, int max_cols, const GemvDesc *tasks, const T *Z, const T *coinv,
+void launch_coarse_psit(int ntasks, int max_rows, int max_cols, const GemvDesc *tasks, const T *Z, const double *coinv,
                         int np, int gauge, const int *pl_ptr, const int *pl_idx, const double *yprim,
                         const double *rP, const CsrIn *rPc, const int *prim_x, int nd, double *zbar, double *ydc,
                         const int *done, cudaStream_t s);
