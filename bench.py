@@ -87,6 +87,23 @@ def peaks():
         return {"hbm_gbs": 6800.0, "fallback": True}
 
 
+def rank_barrier(world):
+    """Barrier over the replicas (no-op for one process)."""
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+
+
+def rank_max(x, world, device="cuda"):
+    """Max of a scalar over the replicas: every rank gets the slowest rank's time."""
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_gpu(args, w, rank, world):
     import numpy as np
     import torch
@@ -105,15 +122,10 @@ def run_gpu(args, w, rank, world):
     dstate = [torch.from_numpy(a).cuda() for a in (ui0, ue0, w0)]
 
     def barrier():
-        if world > 1:
-            torch.distributed.barrier()
+        rank_barrier(world)
 
     def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return rank_max(x, world, "cuda")
 
     def timed(precision, method, profile=False, clocks=None, graphs=1, learned=0):
         s = binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, stream=stream.cuda_stream,
