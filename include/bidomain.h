@@ -57,6 +57,7 @@ extern "C" {
 #define BD_GMRES 1
 #define BD_PRIMAL_V 0   /* vertex values (Section 6, Test 3 "V") */
 #define BD_PRIMAL_VE 1  /* vertex values and edge averages ("V+E") */
+#define BD_PRIMAL_VEF 2 /* vertex values, edge and face averages ("V+E+F", Section 6, Table 7) */
 #define BD_FP64 0       /* every step in float64 */
 #define BD_MIXED 1      /* local factors, Schur and deluxe blocks in float32;
                            Newton, Krylov vectors, dots and coarse in float64 */
@@ -121,7 +122,7 @@ typedef struct {
 typedef struct {
   int method;        /* BD_BDDC | BD_FETIDP */
   int krylov;        /* BD_PCG | BD_GMRES */
-  int primal;        /* BD_PRIMAL_V | BD_PRIMAL_VE */
+  int primal;        /* BD_PRIMAL_V | BD_PRIMAL_VE | BD_PRIMAL_VEF */
   int precision;     /* BD_FP64 | BD_MIXED */
   int gmres_restart; /* GMRES restart length (default 30) */
   int ksp_max_it;    /* default 1000 */
@@ -180,7 +181,7 @@ typedef struct {
 /* ---- host-only plan (no GPU) ------------------------------------------- */
 
 /* Section 4.1: grid, subdomains, N_x, face/edge/vertex classes, primal set
- * (primal = BD_PRIMAL_V or BD_PRIMAL_VE) and dof maps, built on the host.
+ * (primal = BD_PRIMAL_V, BD_PRIMAL_VE or BD_PRIMAL_VEF) and dof maps, built on the host.
  * Fails with BD_ERR_ARG when a subdomain has no primal constraint or the
  * partition has no vertex (no gauge). */
 int bd_plan_create(const bd_mesh *mesh, int primal, bd_plan **out);

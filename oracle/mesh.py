@@ -14,8 +14,9 @@ Readings (the paper leaves these open):
 * nodes on the outer boundary belong to the class of their N_x (the paper
   counts Neumann-boundary nodes as ordinary, not special);
 * classes are ordered by (type, smallest node id) with vertex < edge < face;
-* primal sets: "V" = vertex classes, "VE" = vertices and edges (Section 6,
-  Test 3).
+* primal sets: "V" = vertex classes, "VE" = vertices and edges, "VEF" =
+  vertices, edges and faces (Section 6, Test 3 and Table 7); an edge or face
+  class holds its average as the primal dof and n - 1 deviations as dual dofs.
 
 Pinned by hand counts (a 2x2x2 partition of an 8^3 grid has one vertex, six
 edges and twelve faces holding 217 interface nodes) and by a brute-force
@@ -153,7 +154,7 @@ class Partition:
             self.node_cls[nodes] = c
 
     def _primal(self):
-        kinds = {"V": (VERTEX,), "VE": (VERTEX, EDGE)}[self.primal_kind]
+        kinds = {"V": (VERTEX,), "VE": (VERTEX, EDGE), "VEF": (VERTEX, EDGE, FACE)}[self.primal_kind]
         self.cls_primal = np.array([t in kinds for t in self.cls_type], bool)
         self.primal_cls = np.nonzero(self.cls_primal)[0]
         # global primal dofs: per primal class, field i then field e
@@ -243,7 +244,7 @@ class DofMaps:
         for c in range(p.n_cls):
             nodes = p.cls_nodes[c]
             if p.cls_primal[c]:
-                dn = nodes[:-1] if p.cls_type[c] == EDGE else nodes[:0]
+                dn = nodes[:0] if p.cls_type[c] == VERTEX else nodes[:-1]  # averaged class: n - 1 deviations
             else:
                 dn = nodes
             self.cls_dual_nodes.append(dn)
@@ -263,7 +264,7 @@ class DofMaps:
                     col_a = self.n_dual + 2 * p.primal_index[c] + f
                     for x in nodes:
                         T[2 * self.gnode_to_iface[x] + f, col_a] = 1.0
-                    if p.cls_type[c] == EDGE:
+                    if p.cls_type[c] != VERTEX:  # edge or face average: u(x_k) = a + d_k, u(x_last) = a - sum d_k
                         last = nodes[-1]
                         for k, x in enumerate(nodes[:-1]):
                             col = self.cls_dual_start[c] + 2 * k + f

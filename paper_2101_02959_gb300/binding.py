@@ -20,7 +20,7 @@ ERRORS = {-1: "BD_ERR_ARG", -2: "BD_ERR_NOT_SPD", -3: "BD_ERR_KRYLOV_MAXIT", -4:
           -10: "BD_ERR_STATE", -11: "BD_ERR_SCRATCH"}
 BDDC, FETIDP = 0, 1
 PCG, GMRES = 0, 1
-PRIMAL = {"V": 0, "VE": 1}
+PRIMAL = {"V": 0, "VE": 1, "VEF": 2}
 FP64, MIXED = 0, 1
 
 IDX = dict(ELEM_SUB=0, NODE_MULT=1, IFACE_NODES=2, CLS_TYPE=3, CLS_PTR=4, CLS_NODES=5, CLS_SUB_PTR=6,

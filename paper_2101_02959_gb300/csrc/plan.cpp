@@ -31,7 +31,7 @@ std::string build_plan(Plan &p, const int n[3], const double l[3], const int s[3
     if (n[d] < 1 || s[d] < 1 || !(l[d] > 0)) return "mesh sizes, lengths and subdomain sizes must be positive";
     p.n[d] = n[d]; p.l[d] = l[d]; p.s[d] = s[d]; p.h[d] = l[d] / n[d];
   }
-  if (primal_kind != PRIMAL_V && primal_kind != PRIMAL_VE) return "unknown primal space";
+  if (primal_kind != PRIMAL_V && primal_kind != PRIMAL_VE && primal_kind != PRIMAL_VEF) return "unknown primal space";
   p.primal_kind = primal_kind;
   const int nx = n[0], ny = n[1], nz = n[2];
   const int gx = nx + 1, gy = ny + 1, gz = nz + 1;
@@ -182,7 +182,8 @@ std::string build_plan(Plan &p, const int n[3], const double l[3], const int s[3
   p.primal_index.assign(p.n_cls, -1);
   int np = 0;
   for (int c = 0; c < p.n_cls; ++c) {
-    bool pr = p.cls_type[c] == CLS_VERTEX || (primal_kind == PRIMAL_VE && p.cls_type[c] == CLS_EDGE);
+    bool pr = p.cls_type[c] == CLS_VERTEX || (primal_kind != PRIMAL_V && p.cls_type[c] == CLS_EDGE) ||
+              (primal_kind == PRIMAL_VEF && p.cls_type[c] == CLS_FACE);
     if (pr) { p.cls_primal[c] = 1; p.primal_index[c] = np++; }
   }
   p.n_primal = 2 * np;
@@ -197,7 +198,8 @@ std::string build_plan(Plan &p, const int n[3], const double l[3], const int s[3
   int nd = 0;
   for (int c = 0; c < p.n_cls; ++c) {
     int cnt = p.cls_ptr[c + 1] - p.cls_ptr[c];
-    int dn = p.cls_primal[c] ? (p.cls_type[c] == CLS_EDGE ? cnt - 1 : 0) : cnt;
+    // a primal edge or face keeps its average as the primal dof and cnt - 1 deviations as dual dofs
+    int dn = p.cls_primal[c] ? (p.cls_type[c] == CLS_VERTEX ? 0 : cnt - 1) : cnt;
     p.cls_dual_start[c] = nd;
     p.cls_dual_nodes[c] = dn;
     nd += 2 * dn;
@@ -255,7 +257,7 @@ std::string build_plan(Plan &p, const int n[3], const double l[3], const int s[3
       if (p.cls_primal[c]) {
         int col_a = p.n_dual + 2 * p.primal_index[c] + f;
         for (int k = 0; k < cnt; ++k) rows[2 * p.node_to_iface[nodes[k]] + f].push_back({col_a, 1.0});
-        if (p.cls_type[c] == CLS_EDGE) {
+        if (p.cls_type[c] != CLS_VERTEX) {  // average: u(x_k) = a + d_k, u(x_last) = a - sum_k d_k
           int last = nodes[cnt - 1];
           for (int k = 0; k < cnt - 1; ++k) {
             int col = p.cls_dual_start[c] + 2 * k + f;

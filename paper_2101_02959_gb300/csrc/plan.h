@@ -13,7 +13,7 @@
 namespace bd {
 
 enum { CLS_VERTEX = 0, CLS_EDGE = 1, CLS_FACE = 2 };
-enum { PRIMAL_V = 0, PRIMAL_VE = 1 };
+enum { PRIMAL_V = 0, PRIMAL_VE = 1, PRIMAL_VEF = 2 };
 
 struct SubPlan {
   std::vector<int> nodes;     // local node order: interior (sorted) then interface (sorted)

@@ -35,6 +35,7 @@ WORKLOADS = {
     "ragged": dict(n=(10, 9, 7), l=(0.5, 0.45, 0.35), s=(4, 4, 4), primal="VE", steps=2),
     "cube8": dict(n=(8, 8, 8), l=(0.4, 0.4, 0.4), s=(4, 4, 4), primal="V", steps=1),
     "cube8ve": dict(n=(8, 8, 8), l=(0.4, 0.4, 0.4), s=(4, 4, 4), primal="VE", steps=1),
+    "cube8vef": dict(n=(8, 8, 8), l=(0.4, 0.4, 0.4), s=(4, 4, 4), primal="VEF", steps=1),
     "slab32": dict(n=(32, 32, 16), l=(1.6, 1.6, 0.8), s=(8, 8, 8), primal="VE", steps=20),
     "slab128": dict(n=(128, 128, 32), l=(3.2, 3.2, 0.8), s=(8, 8, 8), primal="VE", steps=400),
 }

@@ -69,7 +69,7 @@ def _oracle_sets(prob):
     return out
 
 
-@pytest.mark.parametrize("name", ["tiny", "cube8", "cube8ve", "ragged", "opt4"])
+@pytest.mark.parametrize("name", ["tiny", "cube8", "cube8ve", "cube8vef", "ragged", "opt4"])
 def test_index_sets_bit_exact(lib, name):
     prob = oracle_problem(name)
     plan = binding.Plan(prob.workload)

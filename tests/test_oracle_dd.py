@@ -91,15 +91,40 @@ def test_bddc_fetidp_spectra(name):
 
 
 def test_primal_space_ordering_of_cond():
-    """A richer primal space gives a smaller condition number (Table 7, V vs V+E)."""
-    conds = {}
-    for prim in ("V", "VE"):
+    """A richer primal space gives a smaller condition number (Table 7: V > V+E >= V+E+F)."""
+    conds, sols = {}, {}
+    for prim in ("V", "VE", "VEF"):
         prob = oracle_problem("cube8", prim)
         kc, f_i, f_e = _jacobian_system(prob)
         dd = DDSolver(prob, rtol=1e-10, atol=0.0)
-        _, _, info = dd.solve(kc / prob.fem.M, f_i, f_e)
+        si, se, info = dd.solve(kc / prob.fem.M, f_i, f_e)
         conds[prim] = info["cond"]
-    assert 1.0 <= conds["VE"] < conds["V"]
+        sols[prim] = np.concatenate([si, se])
+    assert 1.0 <= conds["VEF"] <= conds["VE"] * (1 + 1e-6) and conds["VE"] < conds["V"]
+    # every primal space solves the same Jacobian system
+    for prim in ("V", "VEF"):
+        assert np.linalg.norm(sols[prim] - sols["VE"]) <= 1e-8 * np.linalg.norm(sols["VE"])
+
+
+def test_vef_primal_counts_and_change_of_basis():
+    """V+E+F on the 8^3 grid with 2x2x2 subdomains: 1 vertex, 6 edges (4 nodes), 12 faces
+    (16 nodes) -> 19 primal classes (38 primal dofs) and 12*15 + 6*3 = 198 dual nodes; the
+    change of basis reproduces nodal values: T [d; a] has class mean a and deviations d."""
+    prob = oracle_problem("cube8", "VEF")
+    part, dofs = prob.part, prob.dofs
+    assert part.n_primal == 38
+    assert dofs.n_dual == 2 * 198
+    T = dofs.T
+    # a constant field on every class maps to its own average with zero deviations
+    rng = np.random.default_rng(3)
+    z = rng.standard_normal(T.shape[1])
+    u = T @ z
+    for c in part.primal_cls:
+        nodes = part.cls_nodes[c]
+        for f in range(2):
+            vals = u[2 * dofs.gnode_to_iface[nodes] + f]
+            a = z[dofs.n_dual + 2 * part.primal_index[c] + f]
+            assert abs(vals.mean() - a) < 1e-12
 
 
 def test_pcg_gmres_lanczos_small_spd():
