@@ -13,6 +13,7 @@ Follows Sections 4.1-4.4 of the paper, written with dense numpy/scipy blocks:
 * deluxe scaling (Section 4.2): for a dual class C shared by the subdomains
   in N_C, S_C^(j) is the principal minor of the transformed S_Gamma^(j) on
   the dual dofs of C and D_C^(j) = (sum_{m in N_C} S_C^(m))^-1 S_C^(j);
+  with scaling="rho" D_C^(j) is the diagonal rho-scaling of Section 4.2 instead;
 * BDDC (Section 4.4): M^-1 = Rt_D^T St^-1 Rt_D with St^-1 from the paper's
   block-Cholesky formula: local solves with [[K_II, K_ID], [K_DI, K_DD]]
   plus the coarse term Phi S_PP^-1 Phi^T;
@@ -43,9 +44,12 @@ class DDSolver:
     """Per-Newton-step BDDC / FETI-DP solver of J s = f (SoA vectors)."""
 
     def __init__(self, prob, method="bddc", krylov="pcg", rtol=1e-8, atol=1e-10,
-                 dtol=1e4, maxit=1000, restart=30):
+                 dtol=1e4, maxit=1000, restart=30, scaling="deluxe"):
         self.prob = prob
         self.method, self.krylov = method, krylov
+        if scaling not in ("deluxe", "rho"):
+            raise ValueError(scaling)
+        self.scaling = scaling
         self.kw = dict(rtol=rtol, atol=atol, dtol=dtol, maxit=maxit)
         self.restart = restart
         p, d = prob.part, prob.dofs
@@ -115,8 +119,25 @@ class DDSolver:
                 L = self.loc[j]
                 r = self._class_range(j, c)
                 blocks[j] = L["Sbar"][r, r]
+            if self.scaling == "rho":
+                self.Dc[c] = self._rho_blocks(c, subs, blocks)
+                continue
             Ssum = sum(blocks.values())
             self.Dc[c] = {j: np.linalg.solve(Ssum, blocks[j]) for j in subs}
+
+    def _rho_blocks(self, c, subs, blocks):
+        """rho-scaling (Section 4.2): at a node of class c, field f in {i, e},
+        delta_j = sigma_M^(j) / sum_{k in N_x} sigma_M^(k) with sigma_M the largest
+        principal conductivity of that medium in subdomain k.  The conductivities are
+        the same in every subdomain here, so delta_j = 1 / |N_x| for both fields."""
+        fem = self.prob.fem
+        sig = {0: max(fem.sigma_i), 1: max(fem.sigma_e)}  # per field, identical in every subdomain
+        out = {}
+        for j in subs:
+            n = blocks[j].shape[0]
+            w = np.array([sig[k % 2] / sum(sig[k % 2] for _ in subs) for k in range(n)])
+            out[j] = np.diag(w)
+        return out
 
     def _class_range(self, j, c):
         d = self.prob.dofs

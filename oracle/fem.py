@@ -65,6 +65,7 @@ class FEM:
     """Global and per-subdomain (subassembled) Q1 matrices for one partition."""
 
     def __init__(self, mesh, sigma_i, sigma_e):
+        self.sigma_i, self.sigma_e = tuple(sigma_i), tuple(sigma_e)  # (l, t, n) per medium
         import scipy.sparse as sp
         self.mesh = mesh
         m = mesh

@@ -19,14 +19,15 @@ def _jacobian_system(prob, seed=0):
     return kc, -r_i, -r_e
 
 
-@pytest.mark.parametrize("name", ["tiny", "cube8", "cube8ve", "ragged"])
+@pytest.mark.parametrize("name,scaling", [("tiny", "deluxe"), ("cube8", "deluxe"), ("cube8ve", "deluxe"),
+                                          ("ragged", "deluxe"), ("cube8ve", "rho")])
 @pytest.mark.parametrize("method", ["bddc", "fetidp"])
 @pytest.mark.parametrize("krylov", ["pcg", "gmres"])
-def test_dd_matches_direct(name, method, krylov):
+def test_dd_matches_direct(name, scaling, method, krylov):
     prob = oracle_problem(name)
     kc, f_i, f_e = _jacobian_system(prob)
     si, se, _ = direct_solve(prob, kc, f_i, f_e)
-    dd = DDSolver(prob, method=method, krylov=krylov, rtol=1e-13, atol=0.0)
+    dd = DDSolver(prob, method=method, krylov=krylov, rtol=1e-13, atol=0.0, scaling=scaling)
     ai, ae, info = dd.solve(kc / prob.fem.M, f_i, f_e)
     assert info["reason"] == "converged"
     err = np.linalg.norm(np.r_[ai - si, ae - se]) / np.linalg.norm(np.r_[si, se])
@@ -38,11 +39,12 @@ def _local_dual_vectors(dd, seed):
     return [rng.standard_normal(len(L["dual"])) for L in dd.loc]
 
 
-@pytest.mark.parametrize("name", ["cube8", "cube8ve", "ragged"])
-def test_deluxe_projection_and_pd(name):
+@pytest.mark.parametrize("name,scaling", [("cube8", "deluxe"), ("cube8ve", "deluxe"), ("ragged", "deluxe"),
+                                          ("cube8ve", "rho"), ("ragged", "rho")])
+def test_deluxe_projection_and_pd(name, scaling):
     prob = oracle_problem(name)
     kc, _, _ = _jacobian_system(prob)
-    dd = DDSolver(prob)
+    dd = DDSolver(prob, scaling=scaling)
     dd.setup(kc / prob.fem.M)
     w = _local_dual_vectors(dd, 5)
     e1 = dd.e_d(w)
@@ -65,12 +67,12 @@ def _dense(apply, n, keep):
     return A[np.ix_(keep, keep)]
 
 
-@pytest.mark.parametrize("name", ["cube8", "cube8ve"])
-def test_bddc_fetidp_spectra(name):
+@pytest.mark.parametrize("name,scaling", [("cube8", "deluxe"), ("cube8ve", "deluxe"), ("cube8ve", "rho")])
+def test_bddc_fetidp_spectra(name, scaling):
     """BDDC eigenvalues are >= 1; FETI-DP has the same ones apart from 0 and 1."""
     prob = oracle_problem(name)
     kc, _, _ = _jacobian_system(prob)
-    dd = DDSolver(prob)
+    dd = DDSolver(prob, scaling=scaling)
     dd.setup(kc / prob.fem.M)
     n = prob.dofs.n_iface
     keep = np.ones(n, bool)
@@ -143,3 +145,16 @@ def test_pcg_gmres_lanczos_small_spd():
     N = rng.standard_normal((n, n)) + 5 * np.eye(n)
     x, info = gmres(lambda v: N @ v, lambda v: v, b, rtol=1e-13, atol=0.0, restart=5, maxit=200)
     np.testing.assert_allclose(x, np.linalg.solve(N, b), rtol=1e-8)
+
+
+def test_rho_scaling_is_multiplicity_here():
+    """With equal conductivities in every subdomain the rho weights are 1 / |N_x|
+    (Section 4.2): on the 8^3 cube a face is shared by 2, an edge by 4 subdomains."""
+    prob = oracle_problem("cube8ve")
+    kc, _, _ = _jacobian_system(prob)
+    dd = DDSolver(prob, scaling="rho")
+    dd.setup(kc / prob.fem.M)
+    for c, D in dd.Dc.items():
+        k = len(prob.part.cls_subs[c])
+        for Dj in D.values():
+            np.testing.assert_allclose(Dj, np.eye(Dj.shape[0]) / k, rtol=0, atol=1e-15)
