@@ -58,6 +58,8 @@ extern "C" {
 #define BD_PRIMAL_V 0   /* vertex values (Section 6, Test 3 "V") */
 #define BD_PRIMAL_VE 1  /* vertex values and edge averages ("V+E") */
 #define BD_PRIMAL_VEF 2 /* vertex values, edge and face averages ("V+E+F", Section 6, Table 7) */
+#define BD_SCALING_DELUXE 0
+#define BD_SCALING_RHO 1
 #define BD_FP64 0       /* every step in float64 */
 #define BD_MIXED 1      /* local factors, Schur and deluxe blocks in float32;
                            Newton, Krylov vectors, dots and coarse in float64 */
@@ -148,6 +150,11 @@ typedef struct {
    * iterate and the iteration repeated); 0 = factorise at every Newton iterate
    * (the paper's setting, the default). */
   int lag_jacobian;
+  /* scaling of the dual variables (Section 4.2): BD_SCALING_DELUXE (default) or
+   * BD_SCALING_RHO (delta_j = sigma_M^(j) / sum over N_x of sigma_M^(k), sigma_M the
+   * largest principal conductivity of the medium; 1 / |N_x| here, where every
+   * subdomain has the same conductivities) */
+  int scaling;
 } bd_options;
 
 typedef struct {

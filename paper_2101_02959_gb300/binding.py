@@ -21,6 +21,7 @@ ERRORS = {-1: "BD_ERR_ARG", -2: "BD_ERR_NOT_SPD", -3: "BD_ERR_KRYLOV_MAXIT", -4:
 BDDC, FETIDP = 0, 1
 PCG, GMRES = 0, 1
 PRIMAL = {"V": 0, "VE": 1, "VEF": 2}
+SCALING = {"deluxe": 0, "rho": 1}
 FP64, MIXED = 0, 1
 
 IDX = dict(ELEM_SUB=0, NODE_MULT=1, IFACE_NODES=2, CLS_TYPE=3, CLS_PTR=4, CLS_NODES=5, CLS_SUB_PTR=6,
@@ -60,7 +61,8 @@ class BdOptions(C.Structure):
                [(k, C.c_double) for k in ("ksp_rtol", "ksp_atol", "ksp_dtol", "snes_rtol", "snes_atol",
                                           "snes_stol")] + \
                [(k, C.c_int) for k in ("learned_guess", "mlp_train_steps", "mlp_warmup", "mlp_epochs")] + \
-               [("mlp_lr", C.c_double), ("use_tensor_cores", C.c_int), ("lag_jacobian", C.c_int)]
+               [("mlp_lr", C.c_double), ("use_tensor_cores", C.c_int), ("lag_jacobian", C.c_int),
+                ("scaling", C.c_int)]
 
 
 class BdSolveStats(C.Structure):
@@ -234,7 +236,7 @@ def options(method="bddc", krylov="pcg", primal="VE", precision="fp64", **kw):
     o.primal = PRIMAL[primal]
     o.precision = {"fp64": FP64, "mixed": MIXED}[precision]
     for k, v in kw.items():
-        setattr(o, k, v)
+        setattr(o, k, SCALING[v] if k == "scaling" and isinstance(v, str) else v)
     return o
 
 

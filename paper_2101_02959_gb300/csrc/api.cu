@@ -882,6 +882,11 @@ void linearize_t(bd_handle &h, Dense<T> &D) {
   launch_class_aug<T>(h.ncls, h.max_nc, h.d_cls, h.d_pairs, D.Blk, h.d_Cdesc, D.CA, s);
   engine_partial_cholesky<T>(h.shC, h.d_Cdesc, D.CA, h.d_err, s, D.Linv);
   launch_copy<T, T>(h.cp_sinv.n, h.cp_sinv.max_elems, h.cp_sinv.d, D.CA, D.Sinv, s);
+  if (h.opt.scaling == BD_SCALING_RHO) {
+    const double si = std::max({h.fp.sigma_i[0], h.fp.sigma_i[1], h.fp.sigma_i[2]});
+    const double se = std::max({h.fp.sigma_e[0], h.fp.sigma_e[1], h.fp.sigma_e[2]});
+    launch_rho_blocks<T>(h.ncls, h.d_cls, h.d_pairs, si, se, D.Sinv, D.Blk, s);
+  }
   launch_small_gemm<T>(h.n_gemm, h.max_nc, h.d_gemm, D.Sinv, D.Blk, D.Dd, s);
   // coarse: S_PiPi assembled in FP64, factored in the local precision, inverse refined to FP64
   launch_coarse_aug<T>(h.np, h.gauge_primal, h.d_co_ptr, h.d_co_src, D.Aug, D.Co, h.ld_co, s, h.d_Co64);
@@ -1520,6 +1525,7 @@ int bd_options_default(bd_options *o) {
   o->learned_guess = 0; o->mlp_train_steps = 200; o->mlp_warmup = 5; o->mlp_epochs = 4; o->mlp_lr = 1e-3;
   o->use_tensor_cores = 0;
   o->lag_jacobian = 0;
+  o->scaling = BD_SCALING_DELUXE;
   return BD_OK;
 }
 
@@ -1532,7 +1538,8 @@ int bidomain_setup(const bd_mesh *mesh, const bd_conductivity *cond, const bd_io
     else bd_options_default(&h->opt);
     const bd_options &o = h->opt;
     if ((o.method != BD_BDDC && o.method != BD_FETIDP) || (o.krylov != BD_PCG && o.krylov != BD_GMRES) ||
-        (o.precision != BD_FP64 && o.precision != BD_MIXED) || o.ksp_max_it < 1 || o.newton_max_it < 1)
+        (o.precision != BD_FP64 && o.precision != BD_MIXED) || o.ksp_max_it < 1 || o.newton_max_it < 1 ||
+        (o.scaling != BD_SCALING_DELUXE && o.scaling != BD_SCALING_RHO))
       return BD_ERR_ARG;
     std::string err = build_plan(h->plan, mesh->n, mesh->l, mesh->s, mesh->elem_mask, o.primal);
     if (!err.empty()) { g_last_error = err; return BD_ERR_ARG; }

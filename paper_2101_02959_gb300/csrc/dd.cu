@@ -216,6 +216,32 @@ void coarse_refine64(int np, const T *x0, const double *C, double *X, double *W,
   count_launch(1 + 2 * iters);
 }
 
+// ---- rho-scaling (Section 4.2) --------------------------------------------------
+// The deluxe kernels form D_C^(j) = Sinv_C Blk_C^(j); writing Sinv_C = diag(1 / sum_k
+// sigma_M^(k)) and Blk_C^(j) = diag(sigma_M^(j)) (field i on even, e on odd dual dofs)
+// turns every one of them into the rho-scaling weights, with no other change.  The
+// conductivities are equal in every subdomain, so the weights are 1 / |N_C|.  One CTA
+// per class.
+template <typename T>
+__global__ void k_rho_blocks(const ClassTask *__restrict__ cls, const PairTask *__restrict__ pairs, double sig_i,
+                             double sig_e, T *__restrict__ sinv, T *__restrict__ blk) {
+  const ClassTask c = cls[blockIdx.x];
+  const int n = c.n, k = c.pair_end - c.pair_beg;
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int a = t / n, b = t % n;
+    const double sm = (a % 2 == 0) ? sig_i : sig_e;
+    sinv[c.sinv_off + t] = (a == b) ? (T)(1.0 / (k * sm)) : T(0);
+    for (int q = c.pair_beg; q < c.pair_end; ++q) blk[pairs[q].blk_off + t] = (a == b) ? (T)sm : T(0);
+  }
+}
+template <typename T>
+void launch_rho_blocks(int ncls, const ClassTask *cls, const PairTask *pairs, double sig_i, double sig_e, T *sinv,
+                       T *blk, cudaStream_t s) {
+  if (ncls == 0) return;
+  k_rho_blocks<T><<<ncls, 256, 0, s>>>(cls, pairs, sig_i, sig_e, sinv, blk);
+  count_launch();
+}
+
 // ---- coarse correction fused with the local primal correction -----------------
 // Every CTA assembles the coarse right-hand side c = rP - sum_j (Psi^T r_D)_j
 // (c[gauge] = 0; rP as a vector, a sparse product, or absent) in shared memory,
@@ -923,6 +949,8 @@ void launch_dot2(int n, const double *a0, const double *b0, const double *a1, co
   template void launch_jump_d<T>(int, int, const LamTask *, const PairTask *, const T *, const T *,             \
                                  const double *, double *, const int *, cudaStream_t);                         \
   template void launch_copy<T, T>(int, long long, const CopyTask *, const T *, T *, cudaStream_t);            \
+  template void launch_rho_blocks<T>(int, const ClassTask *, const PairTask *, double, double, T *, T *,        \
+                                     cudaStream_t);                                                            \
   template void launch_coarse_psit<T>(int, int, int, const GemvDesc *, const T *, const double *, int, int,     \
                                       const int *, const int *, const double *, const double *, const CsrIn *, \
                                       const int *, int, double *, double *, const int *, cudaStream_t);

@@ -64,6 +64,10 @@ void launch_spmv(int n, const int *ptr, const int *col, const double *val, const
                  const int *done, cudaStream_t s);
 void launch_gather_sum(int n, const int *ptr, const int *idx, const double *src, double *y, int zero, double alpha,
                        const double *addend, const int *done, cudaStream_t s, const CsrIn *add_csr = nullptr);
+// rho-scaling: Sinv_C = diag(1 / sum sigma_M), Blk_C^(j) = diag(sigma_M) for every class
+template <typename T>
+void launch_rho_blocks(int ncls, const ClassTask *cls, const PairTask *pairs, double sig_i, double sig_e, T *sinv,
+                       T *blk, cudaStream_t s);
 // coarse solve fused into the primal correction: c = rP (vector, sparse product or
 // absent) - sum_j (Psi^T r_D)_j, z_Pi = S_PiPi^-1 c (FP64) into zbar[nd:], ydc -= Psi z_Pi
 template <typename T>

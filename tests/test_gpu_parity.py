@@ -57,14 +57,16 @@ def _linearized(name, **opt):
     ui, ue, w = _state(prob)
     wn = ionic.gating_step(ui - ue, w, prob.tau, prob.p)
     s.linearize(ui, ue, wn)
-    dd = DDSolver(prob)
+    dd = DDSolver(prob, scaling=opt.get("scaling", "deluxe"))
     dd.setup(prob.p["chi_cm"] + prob.tau * ionic.di_ion_dv(ui - ue, wn, prob.p))
     return prob, s, dd, (ui, ue, wn)
 
 
-@pytest.mark.parametrize("name", ["tiny", "cube8", "cube8ve", "cube8vef", "ragged"])
-def test_operators_match_oracle(name):
-    prob, s, dd, _ = _linearized(name, precision="fp64")
+@pytest.mark.parametrize("name,scaling", [("tiny", "deluxe"), ("cube8", "deluxe"), ("cube8ve", "deluxe"),
+                                          ("cube8vef", "deluxe"), ("ragged", "deluxe"), ("cube8ve", "rho"),
+                                          ("ragged", "rho")])
+def test_operators_match_oracle(name, scaling):
+    prob, s, dd, _ = _linearized(name, precision="fp64", scaling=scaling)
     n = prob.dofs.n_iface
     x = synth.random_vector(n, 3)
     x[dd.g_iface] = 0.0
@@ -267,3 +269,28 @@ def test_profile_regions_nest_and_add_up():
     assert 0.0 < inner <= r["step"]["ms"] * 1.001
     assert s.profile_read("rankk")["launches"] == 0  # kernel classes stay off in region mode
     s.close()
+
+
+@pytest.mark.parametrize("method", ["bddc", "fetidp"])
+def test_rho_scaling_jacobian_solve(method):
+    """rho-scaling (Section 4.2): the solve reaches the direct solution and the oracle's
+    iteration count within 1, for BDDC and FETI-DP."""
+    name = "cube8ve"
+    prob = oracle_problem(name)
+    ui, ue, w = _state(prob)
+    wn = ionic.gating_step(ui - ue, w, prob.tau, prob.p)
+    r_i, r_e = prob.residual(ui, ue, wn, ui - 1.0, ue, prob.tau)
+    kc = prob.kc(ui, ue, wn)
+    si, se, _ = direct_solve(prob, kc, -r_i, -r_e)
+    f = -np.concatenate([r_i, r_e])
+    s = _solver(name, method=method, precision="fp64", scaling="rho", ksp_rtol=1e-13, ksp_atol=0.0)
+    s.linearize(ui, ue, wn)
+    x, st = s.krylov_solve(f)
+    assert st["reason"] == 0
+    assert _rel(x, np.concatenate([si, se])) < 1e-10
+    s2 = _solver(name, method=method, precision="fp64", scaling="rho")
+    s2.linearize(ui, ue, wn)
+    _, st2 = s2.krylov_solve(f)
+    dd = DDSolver(prob, method=method, scaling="rho")
+    _, _, info = dd.solve(kc / prob.fem.M, -r_i, -r_e)
+    assert abs(st2["its"] - info["its"]) <= 1
