@@ -11,7 +11,9 @@ Stimulus reading: the paper puts I_app only in the u_e equation yet asks its
 integral to vanish and applies 100 mA/cm^3 locally.  It is read here as a
 transmembrane current entering both equations with opposite signs, which keeps
 (1,1)^T G = 0, active while t_on <= t_{n+1} < t_off on the nodes inside the
-stimulus box.
+stimulus box.  The box is in the grid's parametric coordinates: cm for a box
+geometry, (phi, theta, r) for the ellipsoid, where r = 0 selects the
+endocardial surface that Section 6 stimulates.
 
 Jacobian (Section 3c, exact Newton at the current iterate):
   J = [[Kc + tau A_i, -Kc], [-Kc, Kc + tau A_e]],  Kc = diag(M_l (chi Cm + tau dI_ion/dv)).
@@ -40,7 +42,7 @@ from .mesh import DofMaps, Mesh, Partition
 class Problem:
     def __init__(self, w, sigma_i, sigma_e, ionic_p, tau, stimulus):
         self.workload = w
-        self.mesh = Mesh(w["n"], w["l"])
+        self.mesh = Mesh(w["n"], w.get("l"), ellipsoid=w.get("ellipsoid"))
         self.part = Partition(self.mesh, w["s"], w.get("primal", "V"))
         self.dofs = DofMaps(self.part)
         self.fem = FEM(self.mesh, sigma_i, sigma_e)
@@ -48,7 +50,7 @@ class Problem:
         self.tau = float(tau)
         self.stim = dict(stimulus)
         b = self.stim["box"]
-        c = self.mesh.coords
+        c = self.mesh.pcoords  # the box is in parametric coordinates (the grid's own for a box)
         eps = 1e-12
         self.stim_mask = ((c[:, 0] >= b[0] - eps) & (c[:, 0] <= b[1] + eps)
                           & (c[:, 1] >= b[2] - eps) & (c[:, 1] <= b[3] + eps)

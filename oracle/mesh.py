@@ -34,12 +34,43 @@ HEX_EDGES = [(0, 1), (2, 3), (4, 5), (6, 7),
              (0, 4), (1, 5), (2, 6), (3, 7)]
 
 
-class Mesh:
-    """Box grid of nx*ny*nz Q1 elements of size h, with an optional element mask."""
+def ellipsoid_map(p, axes):
+    """Truncated ellipsoid of Section 6: parametric (phi, theta, r) -> (x, y, z) cm.
 
-    def __init__(self, n, l, elem_mask=None):
+    x = a(r) cos(theta) cos(phi), y = b(r) cos(theta) sin(phi), z = c(r) sin(theta),
+    with a(r) = a1 + r (a2 - a1) and likewise b, c; r = 0 is the endocardium, r = 1
+    the epicardium.  The printed z component reads sin(phi); with it the surfaces
+    r = const would not be ellipsoids, so sin(theta) (the standard ellipsoidal
+    coordinates) is taken.  ``axes`` = (a1, a2, b1, b2, c1, c2).
+    """
+    a1, a2, b1, b2, c1, c2 = axes
+    p = np.asarray(p, float)
+    phi, th, r = p[..., 0], p[..., 1], p[..., 2]
+    a, b, c = a1 + r * (a2 - a1), b1 + r * (b2 - b1), c1 + r * (c2 - c1)
+    return np.stack([a * np.cos(th) * np.cos(phi), b * np.cos(th) * np.sin(phi), c * np.sin(th)], axis=-1)
+
+
+class Mesh:
+    """Structured grid of nx*ny*nz Q1 elements with an optional element mask.
+
+    Box geometry: the grid spans [0, l0] x [0, l1] x [0, l2] cm.  Ellipsoid
+    geometry (``ellipsoid`` = dict(axes, phi, theta), Section 6): the grid is
+    uniform in the parametric coordinates (phi, theta, r) over
+    [phi0, phi1] x [theta0, theta1] x [0, 1] and the nodes are mapped by
+    ``ellipsoid_map`` (isoparametric Q1 elements).  ``pcoords`` holds the
+    parametric coordinates origin + ijk h (equal to ``coords`` for a box).
+    """
+
+    def __init__(self, n, l=None, elem_mask=None, ellipsoid=None):
         self.n = tuple(int(v) for v in n)
-        self.l = tuple(float(v) for v in l)
+        self.ellipsoid = None if ellipsoid is None else dict(ellipsoid)
+        if self.ellipsoid is None:
+            self.l = tuple(float(v) for v in l)
+            self.origin = (0.0, 0.0, 0.0)
+        else:
+            (p0, p1), (t0, t1) = self.ellipsoid["phi"], self.ellipsoid["theta"]
+            self.l = (float(p1) - float(p0), float(t1) - float(t0), 1.0)
+            self.origin = (float(p0), float(t0), 0.0)
         nx, ny, nz = self.n
         self.h = (self.l[0] / nx, self.l[1] / ny, self.l[2] / nz)
         ne_full = nx * ny * nz
@@ -67,7 +98,12 @@ class Mesh:
         gi = self.grid_index
         ijk = np.stack([gi % gx, (gi // gx) % gy, gi // (gx * gy)], axis=1)
         self.node_ijk = ijk
-        self.coords = ijk * np.array(self.h)[None, :]
+        if self.ellipsoid is None:
+            self.pcoords = ijk * np.array(self.h)[None, :]
+            self.coords = self.pcoords
+        else:
+            self.pcoords = np.array(self.origin)[None, :] + ijk * np.array(self.h)[None, :]
+            self.coords = ellipsoid_map(self.pcoords, self.ellipsoid["axes"])
 
 
 class Partition:

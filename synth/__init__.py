@@ -16,6 +16,16 @@ Workloads (all Q1 hexahedral slabs, h = element size):
 * ``opt<k>``   (4k)^3 elements of a 0.8 cm cube, 4x4x4 subdomains, H/h = k.
 * ``slab128``  128x128x32 elements of a 3.2x3.2x0.8 cm slab, 16x16x4
                subdomains, H/h = 8 (1,098,306 unknowns).
+* ``ell8``     8x8x8 isoparametric elements of the truncated ellipsoid of
+               Section 6 (phi in [-pi/2, 0], theta in [-3pi/8, pi/8], the wall
+               r in [0, 1]), 2x2x2 subdomains, V+E primal space.
+* ``ell10``    10x9x6 elements of the same ellipsoid, 4^3-element blocks with
+               ragged last blocks.
+* ``ell32``    32x32x16 elements of the same ellipsoid, 4x4x2 subdomains, H/h = 8.
+
+The ellipsoid's axes are not printed in the paper: a1 = b1 = 1.5, a2 = b2 =
+2.7, c1 = 4.4, c2 = 5.0 cm (a 1.2 cm wall, an idealised left ventricle) are
+taken.  Its stimulus is the endocardial surface r = 0 (Section 6).
 """
 from __future__ import annotations
 
@@ -30,6 +40,13 @@ TAU = 0.05  # ms
 # Section 6: 100 mA/cm^3 for 1 ms in a slab corner (here a 0.1 cm corner cube).
 STIMULUS = dict(amp=100.0, t_on=0.0, t_off=1.0, box=(0.0, 0.1, 0.0, 0.1, 0.0, 0.1))
 
+# Section 6 (Test 4): the portion of ellipsoid; axes a1, a2, b1, b2, c1, c2 in cm.
+ELLIPSOID = dict(axes=(1.5, 2.7, 1.5, 2.7, 4.4, 5.0), phi=(-np.pi / 2, 0.0), theta=(-3 * np.pi / 8, np.pi / 8))
+# Section 6: on the ellipsoid the endocardium (r = 0) is stimulated; the box is
+# in the parametric coordinates (phi, theta, r).
+STIMULUS_ELLIPSOID = dict(amp=100.0, t_on=0.0, t_off=1.0,
+                          box=(-np.pi / 2, 0.0, -3 * np.pi / 8, np.pi / 8, 0.0, 0.0))
+
 WORKLOADS = {
     "tiny": dict(n=(2, 2, 2), l=(0.1, 0.1, 0.1), s=(1, 1, 1), primal="V", steps=1),
     "ragged": dict(n=(10, 9, 7), l=(0.5, 0.45, 0.35), s=(4, 4, 4), primal="VE", steps=2),
@@ -39,6 +56,9 @@ WORKLOADS = {
     "slab32": dict(n=(32, 32, 16), l=(1.6, 1.6, 0.8), s=(8, 8, 8), primal="VE", steps=20),
     "slab128": dict(n=(128, 128, 32), l=(3.2, 3.2, 0.8), s=(8, 8, 8), primal="VE", steps=400),
 }
+for _name, _n, _s in (("ell8", (8, 8, 8), (4, 4, 4)), ("ell10", (10, 9, 6), (4, 4, 4)),
+                      ("ell32", (32, 32, 16), (8, 8, 8))):
+    WORKLOADS[_name] = dict(n=_n, ellipsoid=ELLIPSOID, s=_s, primal="VE", steps=2)
 for _k in (4, 8, 12, 16, 20):
     WORKLOADS[f"opt{_k}"] = dict(n=(4 * _k,) * 3, l=(0.8, 0.8, 0.8), s=(_k,) * 3,
                                  primal="VE", steps=40)
@@ -49,6 +69,11 @@ def workload(name: str) -> dict:
     w = dict(WORKLOADS[name])
     w["name"] = name
     return w
+
+
+def stimulus(w: dict) -> dict:
+    """The stimulus of a workload: a corner box of a slab, the endocardium of the ellipsoid."""
+    return dict(STIMULUS_ELLIPSOID if "ellipsoid" in w else STIMULUS)
 
 
 def n_nodes(w: dict) -> int:

@@ -26,7 +26,7 @@ def oracle_problem(name, primal=None):
         if primal is not None:
             w["primal"] = primal
         _PROBLEMS[key] = Problem(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU,
-                                 synth.STIMULUS)
+                                 synth.stimulus(w))
     return _PROBLEMS[key]
 
 
