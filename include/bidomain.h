@@ -86,15 +86,30 @@ extern "C" {
 typedef struct bd_plan bd_plan;
 typedef struct bd_handle bd_handle;
 
-/* Box grid of n[0] x n[1] x n[2] Q1 hexahedra over [0,l0]x[0,l1]x[0,l2] cm,
- * split into box blocks of s[0] x s[1] x s[2] elements (Section 4.1).
- * elem_mask (host, nullable): one byte per grid element, x fastest, 1 = keep;
- * each block is split into node-connected components. */
+/* Structured grid of n[0] x n[1] x n[2] Q1 hexahedra, split into blocks of
+ * s[0] x s[1] x s[2] elements (Section 4.1).  elem_mask (host, nullable): one
+ * byte per grid element, x fastest, 1 = keep; each block is split into
+ * node-connected components.
+ * geometry BD_GEOM_BOX (0, what a zero-filled struct gives): the grid spans
+ *   [0,l0]x[0,l1]x[0,l2] cm; the slab fibres of Section 6.
+ * geometry BD_GEOM_ELLIPSOID: the truncated ellipsoid of Section 6, a grid
+ *   uniform in (phi, theta, r) over [phi0,phi1]x[theta0,theta1]x[0,1] (l is
+ *   ignored) mapped by x = a(r) cos(theta) cos(phi), y = b(r) cos(theta) sin(phi),
+ *   z = c(r) sin(theta) with a(r) = a1 + r (a2 - a1), likewise b and c
+ *   (axes = a1, a2, b1, b2, c1, c2 in cm, all positive; -pi/2 < theta0 <
+ *   theta1 < pi/2); isoparametric Q1 elements, fibres rotating 120 degrees
+ *   with the depth r.  Stimulus boxes are then given in (phi, theta, r).
+ * Invalid sizes or ranges give BD_ERR_ARG. */
+#define BD_GEOM_BOX 0
+#define BD_GEOM_ELLIPSOID 1
 typedef struct {
   int n[3];
   double l[3];
   int s[3];
   const unsigned char *elem_mask;
+  int geometry;
+  double axes[6];
+  double phi[2], theta[2];
 } bd_mesh;
 
 /* Conductivity coefficients (S/cm) along fibre, cross-fibre and sheet normal
@@ -112,7 +127,8 @@ typedef struct {
 } bd_ionic;
 
 /* Transmembrane stimulus of amplitude amp (mA/cm^3) on the nodes inside the
- * box {x0,x1,y0,y1,z0,z1} (cm), active for t_on <= t_{n+1} < t_off (ms). */
+ * box {x0,x1,y0,y1,z0,z1} of the grid's coordinates (cm for a box; phi, theta,
+ * r for the ellipsoid), active for t_on <= t_{n+1} < t_off (ms). */
 typedef struct {
   double amp, t_on, t_off;
   double box[6];

@@ -22,6 +22,7 @@ BDDC, FETIDP = 0, 1
 PCG, GMRES = 0, 1
 PRIMAL = {"V": 0, "VE": 1, "VEF": 2}
 SCALING = {"deluxe": 0, "rho": 1}
+GEOM_BOX, GEOM_ELLIPSOID = 0, 1
 FP64, MIXED = 0, 1
 
 IDX = dict(ELEM_SUB=0, NODE_MULT=1, IFACE_NODES=2, CLS_TYPE=3, CLS_PTR=4, CLS_NODES=5, CLS_SUB_PTR=6,
@@ -40,7 +41,9 @@ REGIONS = dict(linearize=4, krylov=5, trsv=6, mlp=7, step=8)      # regions of a
 
 
 class BdMesh(C.Structure):
-    _fields_ = [("n", C.c_int * 3), ("l", C.c_double * 3), ("s", C.c_int * 3), ("elem_mask", C.c_void_p)]
+    _fields_ = [("n", C.c_int * 3), ("l", C.c_double * 3), ("s", C.c_int * 3), ("elem_mask", C.c_void_p),
+                ("geometry", C.c_int), ("axes", C.c_double * 6), ("phi", C.c_double * 2),
+                ("theta", C.c_double * 2)]
 
 
 class BdConductivity(C.Structure):
@@ -159,8 +162,15 @@ def _check(code, where):
 def _mesh(w, mask=None):
     m = BdMesh()
     m.n[:] = list(w["n"])
-    m.l[:] = list(w["l"])
     m.s[:] = list(w["s"])
+    ell = w.get("ellipsoid")
+    if ell is None:
+        m.l[:] = list(w["l"])
+    else:
+        m.geometry = GEOM_ELLIPSOID
+        m.axes[:] = list(ell["axes"])
+        m.phi[:] = list(ell["phi"])
+        m.theta[:] = list(ell["theta"])
     m.elem_mask = None if mask is None else mask.ctypes.data
     return m
 

@@ -401,15 +401,24 @@ void setup_handle(bd_handle &h) {
   for (int x = 0; x < N; ++x)
     for (int sl = 0; sl < 27; ++sl) nbr_soa[(long)sl * N + x] = p.nbr27[27L * x + sl];
   h.d_nbr = m.upload(nbr_soa, s);
-  std::vector<double> mass(N, 0.0);
-  const double vol8 = p.h[0] * p.h[1] * p.h[2] / 8.0;
-  for (int e = 0; e < h.NE; ++e)
-    for (int a = 0; a < 8; ++a) mass[p.conn[8 * e + a]] += vol8;
-  h.sum_mass = 0.0;
-  for (double v : mass) h.sum_mass += v;
-  h.d_mass = m.upload(mass, s);
+  // element matrices and lumped masses, then node masses gathered from them
+  GeoParams geo{};
+  geo.kind = p.geo.kind;
+  geo.lz = p.l[2];
+  for (int d = 0; d < 3; ++d) { geo.h[d] = p.h[d]; geo.o[d] = p.origin[d]; }
+  for (int k = 0; k < 6; ++k) geo.axes[k] = p.geo.axes[k];
   h.d_Ke = m.alloc<double>(128L * h.NE);
-  launch_element_matrices(h.NE, h.d_elem_ijk, p.h, p.l[2], h.fp, h.d_Ke, s);
+  double *d_Me = m.alloc<double>(8L * h.NE);
+  launch_element_matrices(h.NE, h.d_elem_ijk, geo, h.fp, h.d_Ke, d_Me, s);
+  h.d_mass = m.alloc<double>(N);
+  launch_mass_gather(N, nullptr, nullptr, h.d_node_ijk, h.d_elem_grid, h.d_elem_sub, p.n, d_Me, h.d_mass, s);
+  {
+    std::vector<double> mass(N);
+    ck(cudaMemcpyAsync(mass.data(), h.d_mass, sizeof(double) * N, cudaMemcpyDeviceToHost, s), "mass");
+    ck(cudaStreamSynchronize(s), "mass");
+    h.sum_mass = 0.0;
+    for (double v : mass) h.sum_mass += v;
+  }
   h.d_stencil = m.alloc<double>(54L * N);
   std::vector<int> all_nodes(N);
   for (int x = 0; x < N; ++x) all_nodes[x] = x;
@@ -431,7 +440,6 @@ void setup_handle(bd_handle &h) {
   h.nI.resize(S); h.nG.resize(S); h.nD.resize(S); h.nP.resize(S);
   h.int_off.resize(S); h.giff_off.resize(S); h.ldual_off.resize(S); h.lprim_off.resize(S);
   std::vector<int> q_sub, q_loc, q_node, q_nbr, int_node, R, prim_x, vec_off_I(S);
-  std::vector<double> q_mass;
   for (int j = 0; j < S; ++j) {
     const SubPlan &sp = p.subs[j];
     h.nI[j] = sp.nI(); h.nG[j] = sp.nG(); h.nD[j] = sp.nD(); h.nP[j] = sp.nP();
@@ -441,7 +449,7 @@ void setup_handle(bd_handle &h) {
     h.ldual_off[j] = h.nD_tot;
     h.lprim_off[j] = h.nP_tot;
     for (int a = 0; a < (int)sp.nodes.size(); ++a) {
-      q_sub.push_back(j); q_loc.push_back(a); q_node.push_back(sp.nodes[a]); q_mass.push_back(sp.mass[a]);
+      q_sub.push_back(j); q_loc.push_back(a); q_node.push_back(sp.nodes[a]);
       for (int sl = 0; sl < 27; ++sl) q_nbr.push_back(sp.nbr[27 * a + sl]);
     }
     for (int a = 0; a < sp.n_interior; ++a) int_node.push_back(sp.nodes[a]);
@@ -458,7 +466,9 @@ void setup_handle(bd_handle &h) {
   h.nI_tot = 2 * h.nint_nodes;
   h.nq = (int)q_sub.size();
   h.d_q_sub = m.upload(q_sub, s); h.d_q_loc = m.upload(q_loc, s); h.d_q_node = m.upload(q_node, s);
-  h.d_q_nbr = m.upload(q_nbr, s); h.d_q_mass = m.upload(q_mass, s);
+  h.d_q_nbr = m.upload(q_nbr, s);
+  h.d_q_mass = m.alloc<double>(h.nq);
+  launch_mass_gather(h.nq, h.d_q_node, h.d_q_sub, h.d_node_ijk, h.d_elem_grid, h.d_elem_sub, p.n, d_Me, h.d_q_mass, s);
   h.d_q_stencil = m.alloc<double>(54L * h.nq);
   launch_stencil_gather(h.nq, h.d_q_node, h.d_q_sub, h.d_node_ijk, h.d_elem_grid, h.d_elem_sub, p.n, h.d_Ke,
                         h.d_q_stencil, 0, s);
@@ -1172,7 +1182,7 @@ int solve(bd_handle &h, const double *fi, const double *fe, double *si, double *
 
 StimParams stim_params(const bd_handle &h, const bd_stimulus *st, double t_next) {
   StimParams sp{};
-  for (int d = 0; d < 3; ++d) sp.h[d] = h.plan.h[d];
+  for (int d = 0; d < 3; ++d) { sp.h[d] = h.plan.h[d]; sp.o[d] = h.plan.origin[d]; }
   if (st) {
     sp.amp = st->amp;
     for (int k = 0; k < 6; ++k) sp.box[k] = st->box[k];
@@ -1431,11 +1441,19 @@ extern "C" int schur_apply_noalloc(bd_handle *h, const double *x, double *y) {
 // ===========================================================================
 extern "C" {
 
+static Geometry mesh_geometry(const bd_mesh &m) {
+  Geometry g;
+  g.kind = m.geometry;
+  for (int k = 0; k < 6; ++k) g.axes[k] = m.axes[k];
+  for (int k = 0; k < 2; ++k) { g.phi[k] = m.phi[k]; g.theta[k] = m.theta[k]; }
+  return g;
+}
+
 int bd_plan_create(const bd_mesh *mesh, int primal, bd_plan **out) {
   if (!mesh || !out) return BD_ERR_ARG;
   return guard(nullptr, [&] {
     auto pl = std::make_unique<bd_plan>();
-    std::string err = build_plan(pl->p, mesh->n, mesh->l, mesh->s, mesh->elem_mask, primal);
+    std::string err = build_plan(pl->p, mesh->n, mesh->l, mesh->s, mesh->elem_mask, primal, mesh_geometry(*mesh));
     if (!err.empty()) { g_last_error = err; return BD_ERR_ARG; }
     *out = pl.release();
     return BD_OK;
@@ -1541,7 +1559,8 @@ int bidomain_setup(const bd_mesh *mesh, const bd_conductivity *cond, const bd_io
         (o.precision != BD_FP64 && o.precision != BD_MIXED) || o.ksp_max_it < 1 || o.newton_max_it < 1 ||
         (o.scaling != BD_SCALING_DELUXE && o.scaling != BD_SCALING_RHO))
       return BD_ERR_ARG;
-    std::string err = build_plan(h->plan, mesh->n, mesh->l, mesh->s, mesh->elem_mask, o.primal);
+    std::string err = build_plan(h->plan, mesh->n, mesh->l, mesh->s, mesh->elem_mask, o.primal,
+                                 mesh_geometry(*mesh));
     if (!err.empty()) { g_last_error = err; return BD_ERR_ARG; }
     h->tau = tau;
     for (int d = 0; d < 3; ++d) { h->fp.sigma_i[d] = cond->sigma_i[d]; h->fp.sigma_e[d] = cond->sigma_e[d]; }

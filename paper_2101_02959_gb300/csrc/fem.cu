@@ -31,9 +31,11 @@ __device__ inline void slab_tensor(const double sig[3], double z, double lz, dou
 }
 
 __global__ void k_element_matrices(int ne, const int *__restrict__ elem_ijk, double hx, double hy, double hz,
-                                   double lz, FemParams fp, double *__restrict__ Ke) {
+                                   double lz, FemParams fp, double *__restrict__ Ke, double *__restrict__ Me) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= ne) return;
+  const double vol8 = hx * hy * hz / 8.0;
+  for (int a = 0; a < 8; ++a) Me[8LL * e + a] = vol8;
   const double zc = (elem_ijk[3 * e + 2] + 0.5) * hz;
   const double h[3] = {hx, hy, hz};
   for (int f = 0; f < 2; ++f) {
@@ -55,6 +57,157 @@ __global__ void k_element_matrices(int ne, const int *__restrict__ elem_ijk, dou
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Truncated ellipsoid (Section 6).  Parametric (phi, theta, r) maps to
+// (a cos(theta) cos(phi), b cos(theta) sin(phi), c sin(theta)) with a, b, c
+// linear in the wall depth r.  The fibre frame at a point: a_n the outward unit
+// normal of the surface r = const, t1 the unit tangent along phi, t2 = a_n x t1,
+// a_l = cos(alpha) t1 + sin(alpha) t2 with alpha = -60 + 120 (1 - r) degrees,
+// a_t = a_n x a_l.
+// ---------------------------------------------------------------------------
+__device__ inline void ell_radii(const double ax[6], double r, double &a, double &b, double &c) {
+  a = ax[0] + r * (ax[1] - ax[0]);
+  b = ax[2] + r * (ax[3] - ax[2]);
+  c = ax[4] + r * (ax[5] - ax[4]);
+}
+
+__device__ inline void ell_point(const double ax[6], double phi, double th, double r, double X[3]) {
+  double a, b, c, sp, cp, st, ct;
+  ell_radii(ax, r, a, b, c);
+  sincos(phi, &sp, &cp);
+  sincos(th, &st, &ct);
+  X[0] = a * ct * cp;
+  X[1] = b * ct * sp;
+  X[2] = c * st;
+}
+
+__device__ inline void cross3(const double u[3], const double v[3], double w[3]) {
+  w[0] = u[1] * v[2] - u[2] * v[1];
+  w[1] = u[2] * v[0] - u[0] * v[2];
+  w[2] = u[0] * v[1] - u[1] * v[0];
+}
+
+__device__ inline void ell_tensor(const double sig[3], const double ax[6], double phi, double th, double r,
+                                  double D[3][3]) {
+  double a, b, c, sp, cp, st, ct;
+  ell_radii(ax, r, a, b, c);
+  sincos(phi, &sp, &cp);
+  sincos(th, &st, &ct);
+  const double x_phi[3] = {-a * ct * sp, b * ct * cp, 0.0};
+  const double x_th[3] = {-a * st * cp, -b * st * sp, c * ct};
+  const double x_r[3] = {(ax[1] - ax[0]) * ct * cp, (ax[3] - ax[2]) * ct * sp, (ax[5] - ax[4]) * st};
+  double n[3];
+  cross3(x_phi, x_th, n);
+  const double sgn = (n[0] * x_r[0] + n[1] * x_r[1] + n[2] * x_r[2]) < 0.0 ? -1.0 : 1.0;
+  const double nn = sgn / sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+  const double tn = 1.0 / sqrt(x_phi[0] * x_phi[0] + x_phi[1] * x_phi[1]);
+  double an[3], t1[3], t2[3], al[3], at[3];
+  for (int p = 0; p < 3; ++p) { an[p] = n[p] * nn; t1[p] = x_phi[p] * tn; }
+  cross3(an, t1, t2);
+  double sa, ca;
+  sincos((-60.0 + 120.0 * (1.0 - r)) * (M_PI / 180.0), &sa, &ca);
+  for (int p = 0; p < 3; ++p) al[p] = ca * t1[p] + sa * t2[p];
+  cross3(an, al, at);
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q) D[p][q] = sig[0] * al[p] * al[q] + sig[1] * at[p] * at[q] + sig[2] * an[p] * an[q];
+}
+
+// Isoparametric Q1 element (Section 3a) on the mapped hexahedron: stiffness
+// int grad(phi_a)^T D grad(phi_b) and lumped masses int phi_a by 2x2x2 Gauss on
+// the reference cube, physical gradients J^-T times the reference ones; D is
+// taken at the element's parametric centroid.  One thread per element
+// (setup only).
+__global__ void k_element_matrices_iso(int ne, const int *__restrict__ elem_ijk, GeoParams g, FemParams fp,
+                                       double *__restrict__ Ke, double *__restrict__ Me) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const int ie[3] = {elem_ijk[3 * e], elem_ijk[3 * e + 1], elem_ijk[3 * e + 2]};
+  double X[8][3];
+  for (int a = 0; a < 8; ++a) {
+    const int c[3] = {ie[0] + (a & 1), ie[1] + ((a >> 1) & 1), ie[2] + ((a >> 2) & 1)};
+    ell_point(g.axes, g.o[0] + c[0] * g.h[0], g.o[1] + c[1] * g.h[1], g.o[2] + c[2] * g.h[2], X[a]);
+  }
+  double D[2][3][3];
+  const double pc[3] = {g.o[0] + (ie[0] + 0.5) * g.h[0], g.o[1] + (ie[1] + 0.5) * g.h[1],
+                        g.o[2] + (ie[2] + 0.5) * g.h[2]};
+  ell_tensor(fp.sigma_i, g.axes, pc[0], pc[1], pc[2], D[0]);
+  ell_tensor(fp.sigma_e, g.axes, pc[0], pc[1], pc[2], D[1]);
+  double *K = Ke + (long long)e * 128;
+  double *M = Me + 8LL * e;
+  for (int t = 0; t < 128; ++t) K[t] = 0.0;
+  for (int a = 0; a < 8; ++a) M[a] = 0.0;
+  const double gp[2] = {0.5 - 0.5 / sqrt(3.0), 0.5 + 0.5 / sqrt(3.0)};
+  for (int q = 0; q < 8; ++q) {
+    const double xi[3] = {gp[q & 1], gp[(q >> 1) & 1], gp[(q >> 2) & 1]};
+    double N[8], dN[8][3];
+    for (int a = 0; a < 8; ++a) {
+      const int b[3] = {a & 1, (a >> 1) & 1, (a >> 2) & 1};
+      double l[3], sd[3];
+      for (int d = 0; d < 3; ++d) { l[d] = b[d] ? xi[d] : 1.0 - xi[d]; sd[d] = b[d] ? 1.0 : -1.0; }
+      N[a] = l[0] * l[1] * l[2];
+      dN[a][0] = sd[0] * l[1] * l[2];
+      dN[a][1] = l[0] * sd[1] * l[2];
+      dN[a][2] = l[0] * l[1] * sd[2];
+    }
+    double J[3][3];  // J[p][d] = d x_p / d xi_d
+    for (int p = 0; p < 3; ++p)
+      for (int d = 0; d < 3; ++d) {
+        double v = 0.0;
+        for (int a = 0; a < 8; ++a) v += X[a][p] * dN[a][d];
+        J[p][d] = v;
+      }
+    double C[3][3];  // cofactors: J^-1[d][p] = C[p][d] / det
+    C[0][0] = J[1][1] * J[2][2] - J[1][2] * J[2][1];
+    C[0][1] = J[1][2] * J[2][0] - J[1][0] * J[2][2];
+    C[0][2] = J[1][0] * J[2][1] - J[1][1] * J[2][0];
+    C[1][0] = J[0][2] * J[2][1] - J[0][1] * J[2][2];
+    C[1][1] = J[0][0] * J[2][2] - J[0][2] * J[2][0];
+    C[1][2] = J[0][1] * J[2][0] - J[0][0] * J[2][1];
+    C[2][0] = J[0][1] * J[1][2] - J[0][2] * J[1][1];
+    C[2][1] = J[0][2] * J[1][0] - J[0][0] * J[1][2];
+    C[2][2] = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+    const double det = J[0][0] * C[0][0] + J[0][1] * C[0][1] + J[0][2] * C[0][2];
+    const double w = det / 8.0, inv = 1.0 / det;
+    double G[8][3];  // physical gradients: G[a][p] = sum_d dN[a][d] J^-1[d][p]
+    for (int a = 0; a < 8; ++a)
+      for (int p = 0; p < 3; ++p) G[a][p] = (dN[a][0] * C[p][0] + dN[a][1] * C[p][1] + dN[a][2] * C[p][2]) * inv;
+    for (int a = 0; a < 8; ++a) M[a] += w * N[a];
+    for (int f = 0; f < 2; ++f) {
+      double DG[8][3];
+      for (int b = 0; b < 8; ++b)
+        for (int p = 0; p < 3; ++p) DG[b][p] = D[f][p][0] * G[b][0] + D[f][p][1] * G[b][1] + D[f][p][2] * G[b][2];
+      for (int a = 0; a < 8; ++a)
+        for (int b = 0; b < 8; ++b)
+          K[f * 64 + a * 8 + b] += w * (G[a][0] * DG[b][0] + G[a][1] * DG[b][1] + G[a][2] * DG[b][2]);
+    }
+  }
+}
+
+// Lumped node masses: the sum over the elements around x (those of one
+// subdomain, when given) of their corner mass at x, in the stencil's element order.
+__global__ void k_mass_gather(int nrows, const int *__restrict__ row_node, const int *__restrict__ row_sub,
+                              const int *__restrict__ node_ijk, const int *__restrict__ elem_grid,
+                              const int *__restrict__ elem_sub, int nx, int ny, int nz, const double *__restrict__ Me,
+                              double *__restrict__ out) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= nrows) return;
+  const int x = row_node ? row_node[r] : r;
+  const int sub = row_sub ? row_sub[r] : -1;
+  const int i = node_ijk[3 * x], j = node_ijk[3 * x + 1], k = node_ijk[3 * x + 2];
+  double acc = 0.0;
+  for (int ez = 0; ez < 2; ++ez)
+    for (int ey = 0; ey < 2; ++ey)
+      for (int ex = 0; ex < 2; ++ex) {
+        const int gi = i - 1 + ex, gj = j - 1 + ey, gk = k - 1 + ez;
+        if (gi < 0 || gj < 0 || gk < 0 || gi >= nx || gj >= ny || gk >= nz) continue;
+        const int e = elem_grid[gi + nx * (gj + ny * gk)];
+        if (e < 0) continue;
+        if (sub >= 0 && elem_sub[e] != sub) continue;
+        acc += Me[8LL * e + (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez)];
+      }
+  out[r] = acc;
 }
 
 // Stencil rows: for node x (optionally restricted to the elements of one
@@ -150,7 +303,8 @@ __global__ void k_residual(int n, const double *__restrict__ stencil, const int 
     const double ion = p.tau * M * rmc_iion(v, wn[x], p);
     double app = 0.0;
     if (st.active) {
-      const double cx = node_ijk[3 * x] * st.h[0], cy = node_ijk[3 * x + 1] * st.h[1], cz = node_ijk[3 * x + 2] * st.h[2];
+      const double cx = st.o[0] + node_ijk[3 * x] * st.h[0], cy = st.o[1] + node_ijk[3 * x + 1] * st.h[1],
+                   cz = st.o[2] + node_ijk[3 * x + 2] * st.h[2];
       const double eps = 1e-12;
       if (cx >= st.box[0] - eps && cx <= st.box[1] + eps && cy >= st.box[2] - eps && cy <= st.box[3] + eps &&
           cz >= st.box[4] - eps && cz <= st.box[5] + eps)
@@ -210,9 +364,22 @@ __global__ void k_gauge_shift(int n, double *__restrict__ ui, double *__restrict
 }
 
 // ---- host launchers --------------------------------------------------------
-void launch_element_matrices(int ne, const int *elem_ijk, const double h[3], double lz, const FemParams &fp,
-                             double *Ke, cudaStream_t s) {
-  k_element_matrices<<<ceil_div(ne, 128), 128, 0, s>>>(ne, elem_ijk, h[0], h[1], h[2], lz, fp, Ke);
+void launch_element_matrices(int ne, const int *elem_ijk, const GeoParams &g, const FemParams &fp, double *Ke,
+                             double *Me, cudaStream_t s) {
+  if (ne <= 0) return;
+  if (g.kind == 1)
+    k_element_matrices_iso<<<ceil_div(ne, 64), 64, 0, s>>>(ne, elem_ijk, g, fp, Ke, Me);
+  else
+    k_element_matrices<<<ceil_div(ne, 128), 128, 0, s>>>(ne, elem_ijk, g.h[0], g.h[1], g.h[2], g.lz, fp, Ke, Me);
+  count_launch();
+}
+
+void launch_mass_gather(int nrows, const int *row_node, const int *row_sub, const int *node_ijk,
+                        const int *elem_grid, const int *elem_sub, const int n[3], const double *Me, double *out,
+                        cudaStream_t s) {
+  if (nrows <= 0) return;
+  k_mass_gather<<<ceil_div(nrows, 256), 256, 0, s>>>(nrows, row_node, row_sub, node_ijk, elem_grid, elem_sub, n[0],
+                                                      n[1], n[2], Me, out);
   count_launch();
 }
 

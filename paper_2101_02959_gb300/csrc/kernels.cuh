@@ -36,11 +36,27 @@ struct StimParams {
   double amp;
   double box[6];
   double h[3];
+  double o[3];  // grid origin in the parametric coordinates
+};
+
+// Element geometry: kind 0 = box (spacing h, slab depth lz), 1 = truncated
+// ellipsoid (Section 6) over the parametric grid origin + ijk h with
+// axes a1, a2, b1, b2, c1, c2.
+struct GeoParams {
+  int kind;
+  double h[3], o[3], lz;
+  double axes[6];
 };
 
 // fem.cu
-void launch_element_matrices(int ne, const int *elem_ijk, const double h[3], double lz, const FemParams &fp,
-                             double *Ke, cudaStream_t s);
+// Ke: 2 x 64 per element (intra, extra); Me: 8 lumped masses per element.
+void launch_element_matrices(int ne, const int *elem_ijk, const GeoParams &g, const FemParams &fp, double *Ke,
+                             double *Me, cudaStream_t s);
+// out[r] = lumped mass of node row_node[r] (r itself when row_node is null),
+// summed over its elements (those of subdomain row_sub[r] when row_sub is given).
+void launch_mass_gather(int nrows, const int *row_node, const int *row_sub, const int *node_ijk,
+                        const int *elem_grid, const int *elem_sub, const int n[3], const double *Me, double *out,
+                        cudaStream_t s);
 void launch_stencil_gather(int nrows, const int *row_node, const int *row_sub, const int *node_ijk,
                            const int *elem_grid, const int *elem_sub, const int n[3], const double *Ke,
                            double *out, int soa_stride, cudaStream_t s);

@@ -26,10 +26,28 @@ struct DSU {
 }  // namespace
 
 std::string build_plan(Plan &p, const int n[3], const double l[3], const int s[3],
-                       const unsigned char *elem_mask, int primal_kind) {
+                       const unsigned char *elem_mask, int primal_kind, const Geometry &geo) {
+  double ext[3] = {l[0], l[1], l[2]};
+  p.geo = geo;
+  p.origin[0] = p.origin[1] = p.origin[2] = 0.0;
+  if (geo.kind == GEOM_ELLIPSOID) {
+    const double half_pi = 1.5707963267948966;
+    for (int k = 0; k < 6; ++k)
+      if (!(geo.axes[k] > 0)) return "ellipsoid axes must be positive";
+    if (!(geo.phi[1] > geo.phi[0]) || !(geo.theta[1] > geo.theta[0]) || !(geo.theta[0] > -half_pi) ||
+        !(geo.theta[1] < half_pi))
+      return "ellipsoid ranges need phi0 < phi1 and -pi/2 < theta0 < theta1 < pi/2";
+    ext[0] = geo.phi[1] - geo.phi[0];
+    ext[1] = geo.theta[1] - geo.theta[0];
+    ext[2] = 1.0;
+    p.origin[0] = geo.phi[0];
+    p.origin[1] = geo.theta[0];
+  } else if (geo.kind != GEOM_BOX) {
+    return "unknown geometry";
+  }
   for (int d = 0; d < 3; ++d) {
-    if (n[d] < 1 || s[d] < 1 || !(l[d] > 0)) return "mesh sizes, lengths and subdomain sizes must be positive";
-    p.n[d] = n[d]; p.l[d] = l[d]; p.s[d] = s[d]; p.h[d] = l[d] / n[d];
+    if (n[d] < 1 || s[d] < 1 || !(ext[d] > 0)) return "mesh sizes, lengths and subdomain sizes must be positive";
+    p.n[d] = n[d]; p.l[d] = ext[d]; p.s[d] = s[d]; p.h[d] = ext[d] / n[d];
   }
   if (primal_kind != PRIMAL_V && primal_kind != PRIMAL_VE && primal_kind != PRIMAL_VEF) return "unknown primal space";
   p.primal_kind = primal_kind;
@@ -59,7 +77,9 @@ std::string build_plan(Plan &p, const int n[3], const double l[3], const int s[3
     int x = node_of_full[g];
     int i = g % gx, j = (g / gx) % gy, k = g / ((long)gx * gy);
     p.node_ijk[3 * x] = i; p.node_ijk[3 * x + 1] = j; p.node_ijk[3 * x + 2] = k;
-    p.coords[3 * x] = i * p.h[0]; p.coords[3 * x + 1] = j * p.h[1]; p.coords[3 * x + 2] = k * p.h[2];
+    p.coords[3 * x] = p.origin[0] + i * p.h[0];
+    p.coords[3 * x + 1] = p.origin[1] + j * p.h[1];
+    p.coords[3 * x + 2] = p.origin[2] + k * p.h[2];
   }
   p.conn.clear(); p.elem_ijk.clear();
   int ne = 0;
@@ -210,7 +230,6 @@ std::string build_plan(Plan &p, const int n[3], const double l[3], const int s[3
   std::vector<std::vector<int>> sub_cls(nsub);
   for (int c = 0; c < p.n_cls; ++c)
     for (int q = p.cls_sub_ptr[c]; q < p.cls_sub_ptr[c + 1]; ++q) sub_cls[p.cls_subs[q]].push_back(c);
-  const double vol8 = p.h[0] * p.h[1] * p.h[2] / 8.0;
   for (int j = 0; j < nsub; ++j) {
     SubPlan &sp = p.subs[j];
     sp.elems = sub_elems[j];
@@ -231,11 +250,10 @@ std::string build_plan(Plan &p, const int n[3], const double l[3], const int s[3
     for (int c : sp.classes)
       if (p.cls_primal[c]) { sp.primal.push_back(2 * p.primal_index[c]); sp.primal.push_back(2 * p.primal_index[c] + 1); }
     if (!has_primal) return "subdomain " + std::to_string(j) + " has no primal constraint";
-    // local neighbour table and subassembled lumped mass
+    // local neighbour table
     std::map<int, int> loc;
     for (int q = 0; q < (int)sp.nodes.size(); ++q) loc[sp.nodes[q]] = q;
     sp.nbr.assign(27 * sp.nodes.size(), -1);
-    sp.mass.assign(sp.nodes.size(), 0.0);
     for (int q = 0; q < (int)sp.nodes.size(); ++q) {
       int x = sp.nodes[q];
       for (int sl = 0; sl < 27; ++sl) {
@@ -245,7 +263,6 @@ std::string build_plan(Plan &p, const int n[3], const double l[3], const int s[3
         if (it != loc.end()) sp.nbr[27 * q + sl] = it->second;
       }
     }
-    for (int e : sp.elems) for (int a = 0; a < 8; ++a) sp.mass[loc[p.conn[8 * e + a]]] += vol8;
   }
   // global change of basis T: nodal interface dof <- transformed dof
   const int nif = p.n_iface();

@@ -37,6 +37,13 @@ def test_strerror_and_bad_args(lib):
     # a 2x1x1 split has no vertex: no gauge, no primal constraint
     with pytest.raises(binding.BidomainError):
         binding.Plan(dict(w, s=(4, 8, 8)))
+    # ellipsoid ranges must avoid the poles and have positive axes
+    e = synth.workload("ell8")
+    for bad in (dict(e["ellipsoid"], theta=(-1.0, 1.6)), dict(e["ellipsoid"], phi=(0.5, 0.0)),
+                dict(e["ellipsoid"], axes=(1.5, 2.7, 0.0, 2.7, 4.4, 5.0))):
+        with pytest.raises(binding.BidomainError):
+            binding.Plan(dict(e, ellipsoid=bad))
+    binding.Plan(e)
 
 
 def _oracle_sets(prob):
@@ -69,7 +76,7 @@ def _oracle_sets(prob):
     return out
 
 
-@pytest.mark.parametrize("name", ["tiny", "cube8", "cube8ve", "cube8vef", "ragged", "opt4"])
+@pytest.mark.parametrize("name", ["tiny", "cube8", "cube8ve", "cube8vef", "ragged", "opt4", "ell8", "ell10"])
 def test_index_sets_bit_exact(lib, name):
     prob = oracle_problem(name)
     plan = binding.Plan(prob.workload)
