@@ -171,6 +171,14 @@ typedef struct {
    * largest principal conductivity of the medium; 1 / |N_x| here, where every
    * subdomain has the same conductivities) */
   int scaling;
+  /* BD_BDDC only: rebuild the preconditioner (transformed local matrices, deluxe
+   * blocks, coarse problem) at every precond_every-th Jacobian evaluation, counted
+   * from setup; in between, the Krylov solve applies the current Schur operator
+   * with the older preconditioner (not in the paper, which rebuilds it each time).
+   * 1 = every evaluation (the default).  Values below 1, or above 1 with
+   * BD_FETIDP, whose operator contains the preconditioner's local solves, give
+   * BD_ERR_ARG.  Evaluations inside bidomain_autotune rebuild it and do not count. */
+  int precond_every;
 } bd_options;
 
 typedef struct {
@@ -253,7 +261,9 @@ int bidomain_residual(bd_handle *h, const bd_stimulus *stim, double t_next, cons
 /* Jacobian of Section 3c at (ui, ue, w_next): updates the local matrices,
  * factorises them, forms the local Schur complements, deluxe blocks and the
  * coarse problem (Sections 4.1-4.4).  Required before the three calls below
- * and before krylov_solve. */
+ * and before krylov_solve.  Counts as a Jacobian evaluation of the
+ * precond_every schedule: between rebuilds only the local factors and Schur
+ * complements are updated. */
 int bidomain_linearize(bd_handle *h, const double *ui, const double *ue, const double *w_next,
                        int on_device);
 

@@ -24,6 +24,18 @@ Follows Sections 4.1-4.4 of the paper, written with dense numpy/scipy blocks:
   Omega_m, so that B_D^T B = P_D (eq. PdDeluxe).  f~ splits the global
   interface right-hand side equally among the subdomains sharing each node.
 
+Lagged preconditioner (option, BDDC only; the paper rebuilds it at every
+Newton step): with precond_every = k the local Schur operator is rebuilt at
+every setup but the preconditioner (transformed local matrices, deluxe
+blocks, coarse problem) only at every k-th, so PCG runs with the current
+S_hat and an older BDDC preconditioner.  Two Jacobians differ only in the
+lumped reaction term Kc = M (chi Cm + tau dI_ion/dv): with rho = Kc_new /
+Kc_old nodewise (Kc > 0), alpha J_old <= J_new <= beta J_old for alpha =
+min(1, min rho) and beta = max(1, max rho); the interface Schur complements
+inherit the bounds (each is a minimum of the energy over interior
+extensions), so cond(M_old^-1 S_new) <= (beta / alpha) cond(M_old^-1 S_old).
+FETI-DP's operator contains St^-1 itself, so it cannot lag.
+
 Gauge: the u_e dof of the gauge vertex is removed from the coarse problem
 (fixed at zero), which makes S_hat and the coarse matrix nonsingular.
 
@@ -44,11 +56,16 @@ class DDSolver:
     """Per-Newton-step BDDC / FETI-DP solver of J s = f (SoA vectors)."""
 
     def __init__(self, prob, method="bddc", krylov="pcg", rtol=1e-8, atol=1e-10,
-                 dtol=1e4, maxit=1000, restart=30, scaling="deluxe"):
+                 dtol=1e4, maxit=1000, restart=30, scaling="deluxe", precond_every=1):
         self.prob = prob
         self.method, self.krylov = method, krylov
         if scaling not in ("deluxe", "rho"):
             raise ValueError(scaling)
+        if precond_every < 1 or (precond_every > 1 and method != "bddc"):
+            raise ValueError("a lagged preconditioner needs BDDC and precond_every >= 1")
+        self.precond_every = int(precond_every)
+        self.n_setup = 0          # setups so far
+        self.precond_fresh = False  # whether the last setup rebuilt the preconditioner
         self.scaling = scaling
         self.kw = dict(rtol=rtol, atol=atol, dtol=dtol, maxit=maxit)
         self.restart = restart
@@ -69,6 +86,9 @@ class DDSolver:
         """``factor`` = chi Cm + tau dI_ion/dv at every node."""
         prob, p, d = self.prob, self.prob.part, self.prob.dofs
         tau = prob.tau
+        fresh = self.n_setup % self.precond_every == 0
+        self.n_setup += 1
+        self.precond_fresh = fresh
         for L in self.loc:
             n = len(L["nodes"])
             kc = L["Ml"] * factor[L["nodes"]]
@@ -83,6 +103,8 @@ class DDSolver:
             nI = L["nI"]
             L["K"] = K
             L["KII"] = sla.cho_factor(K[:nI, :nI])
+            if not fresh:
+                continue  # operator only: the preconditioner below stays from an older setup
             KIG, KGG = K[:nI, nI:], K[nI:, nI:]
             S = KGG - KIG.T @ sla.cho_solve(L["KII"], KIG)
             L["S"] = S
@@ -100,6 +122,8 @@ class DDSolver:
             Y = sla.cho_solve(L["KbIDID"], KX)
             L["PhiD"] = -Y[nI:, :]
             L["SPPj"] = Kb[nID:, nID:] - KX.T @ Y
+        if not fresh:
+            return
         # coarse matrix, gauge dof removed
         nP = p.n_primal
         SPP = np.zeros((nP, nP))
@@ -367,6 +391,7 @@ class DDSolver:
             uG[self.g_iface] = 0.0
         if self.krylov == "pcg" and info["its"] > 0:
             info["cond"] = lanczos_cond(info["alphas"], info["betas"])
+        info["precond_fresh"] = self.precond_fresh
         s_i, s_e = self.recover(uG, fI)
         self.last = info
         return s_i, s_e, info

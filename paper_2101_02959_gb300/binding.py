@@ -65,7 +65,7 @@ class BdOptions(C.Structure):
                                           "snes_stol")] + \
                [(k, C.c_int) for k in ("learned_guess", "mlp_train_steps", "mlp_warmup", "mlp_epochs")] + \
                [("mlp_lr", C.c_double), ("use_tensor_cores", C.c_int), ("lag_jacobian", C.c_int),
-                ("scaling", C.c_int)]
+                ("scaling", C.c_int), ("precond_every", C.c_int)]
 
 
 class BdSolveStats(C.Structure):

@@ -256,6 +256,7 @@ struct bd_handle {
   Dense<double> dd;
 
   bool linearized = false;
+  long long n_jac = 0;  // counted Jacobian evaluations (the precond_every schedule)
   std::string last_error;
   Profiler prof;
   // learned initial guess
@@ -872,14 +873,17 @@ void run_engine_groups(bd_handle &h, const EngineShape &all, const MatDesc *d_de
   }
 }
 
+// precond = false: only the operator (local factors and Schur complements); the
+// BDDC preconditioner built from an earlier Jacobian stays in place.
 template <class T>
-void linearize_t(bd_handle &h, Dense<T> &D) {
+void linearize_t(bd_handle &h, Dense<T> &D, bool precond) {
   cudaStream_t s = h.s;
   ck(cudaMemsetAsync(D.K, 0, sizeof(T) * h.K_el, s), "memset K");
   launch_assemble_local<T>(h.nq, h.d_q_sub, h.d_q_loc, h.d_q_node, h.d_q_nbr, h.d_q_stencil, h.d_q_mass, h.d_factor,
                            h.tau, h.d_Kdesc, D.K, s);
   run_engine_groups<T>(h, h.shK, h.d_Kdesc, D.K, D.LdK);
   launch_copy<T, T>(h.cp_sorig.n, h.cp_sorig.max_elems, h.cp_sorig.d, D.K, D.Sorig, s);
+  if (!precond) return;
   const T *tval;
   if constexpr (std::is_same<T, float>::value) tval = h.d_tl_valf;
   else tval = h.d_tl_val;
@@ -905,10 +909,17 @@ void linearize_t(bd_handle &h, Dense<T> &D) {
   coarse_refine64<T>(h.np, D.CoInv, h.d_Co64, h.d_CoInv64, h.d_CoW, h.d_CoY, s);
 }
 
-void linearize(bd_handle &h) {
+// counted = true for the Jacobian evaluations of the solve (Newton, bidomain_linearize):
+// with precond_every = k the preconditioner is rebuilt when their count is a multiple of k.
+void linearize(bd_handle &h, bool counted = false) {
   h.prof.begin(PROF_LINEARIZE, h.s);
-  if (h.mixed()) linearize_t(h, h.df);
-  else linearize_t(h, h.dd);
+  bool precond = true;
+  if (counted) {
+    precond = h.n_jac % std::max(1, h.opt.precond_every) == 0;
+    ++h.n_jac;
+  }
+  if (h.mixed()) linearize_t(h, h.df, precond);
+  else linearize_t(h, h.dd, precond);
   h.prof.end(PROF_LINEARIZE, h.s, 0.0, 0.0);
   h.linearized = true;
 }
@@ -1254,7 +1265,7 @@ int step(bd_handle &h, const bd_stimulus *stim, bd_step_stats *out) {
     if (std::sqrt(fn2) <= std::max(h.opt.snes_atol, h.opt.snes_rtol * fn0)) break;
     const bool fresh = refresh || !h.opt.lag_jacobian;
     if (fresh) {
-      linearize(h);
+      linearize(h, true);
       int e = h.check_err();
       if (e) { reason = e; break; }
       refresh = false;
@@ -1544,6 +1555,7 @@ int bd_options_default(bd_options *o) {
   o->use_tensor_cores = 0;
   o->lag_jacobian = 0;
   o->scaling = BD_SCALING_DELUXE;
+  o->precond_every = 1;
   return BD_OK;
 }
 
@@ -1557,7 +1569,8 @@ int bidomain_setup(const bd_mesh *mesh, const bd_conductivity *cond, const bd_io
     const bd_options &o = h->opt;
     if ((o.method != BD_BDDC && o.method != BD_FETIDP) || (o.krylov != BD_PCG && o.krylov != BD_GMRES) ||
         (o.precision != BD_FP64 && o.precision != BD_MIXED) || o.ksp_max_it < 1 || o.newton_max_it < 1 ||
-        (o.scaling != BD_SCALING_DELUXE && o.scaling != BD_SCALING_RHO))
+        (o.scaling != BD_SCALING_DELUXE && o.scaling != BD_SCALING_RHO) || o.precond_every < 1 ||
+        (o.precond_every > 1 && o.method != BD_BDDC))
       return BD_ERR_ARG;
     std::string err = build_plan(h->plan, mesh->n, mesh->l, mesh->s, mesh->elem_mask, o.primal,
                                  mesh_geometry(*mesh));
@@ -1667,7 +1680,7 @@ int bidomain_linearize(bd_handle *h, const double *ui, const double *ue, const d
     launch_residual(h->N, h->d_stencil, h->d_nbr, h->d_mass, h->d_node_ijk, a, b, nullptr, nullptr, 0.0, c, a, b,
                     h->fp, stim_params(*h, nullptr, 0.0), h->d_rit, h->d_ret, h->d_factor, nullptr, nullptr,
                     h->d_partial, nullptr, h->s);
-    linearize(*h);
+    linearize(*h, true);
     return h->check_err();
   });
 }

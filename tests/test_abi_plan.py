@@ -100,3 +100,13 @@ def test_slab32_sizes(lib):
     assert sz["n_primal"] == 102
     t = plan.index_set("CLS_TYPE")
     assert [int((t == k).sum()) for k in range(3)] == [9, 42, 64]
+
+
+@pytest.mark.parametrize("bad", [dict(method="fetidp", precond_every=2), dict(precond_every=0),
+                                 dict(scaling=7)])
+def test_setup_rejects_bad_options_before_touching_the_device(lib, bad):
+    """Option checks run before any CUDA call, so they hold on a machine without a GPU."""
+    w = synth.workload("cube8ve")
+    with pytest.raises(binding.BidomainError) as e:
+        binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, **bad)
+    assert binding.ERRORS[e.value.code] == "BD_ERR_ARG"

@@ -301,3 +301,32 @@ def test_rho_scaling_jacobian_solve(method):
     dd = DDSolver(prob, method=method, scaling="rho")
     _, _, info = dd.solve(kc / prob.fem.M, -r_i, -r_e)
     assert abs(st2["its"] - info["its"]) <= 1
+
+
+def test_lagged_preconditioner_time_steps():
+    """precond_every = 3 (BDDC): the GPU's states equal the oracle's at tight tolerances
+    (the preconditioner does not change the solution), and at the paper's tolerances its
+    Krylov iteration counts follow the oracle's run on the same rebuild schedule."""
+    name = "cube8ve"
+    prob = oracle_problem(name)
+    ref = _oracle_steps(prob, 3)
+    s = _solver(name, precision="fp64", ksp_rtol=1e-12, ksp_atol=0.0, snes_rtol=1e-10, snes_atol=1e-16,
+                precond_every=3)
+    ui, ue, w = synth.initial_state(prob.N, 0)
+    s.set_state(ui, ue, w, 0.0)
+    for n in range(3):
+        st = s.step(synth.STIMULUS)
+        assert st["reason"] == 0
+        gui, gue, _, _ = s.get_state()
+        assert _rel(gui - gue, ref[n][0] - ref[n][1]) < 1e-9
+        assert _rel(gue, ref[n][1]) < 1e-9
+    # paper tolerances: the same schedule on both sides
+    dd = DDSolver(prob, precond_every=3)
+    s2 = _solver(name, precision="fp64", precond_every=3)
+    s2.set_state(ui, ue, w, 0.0)
+    oui, oue, ow = ui, ue, w
+    for n in range(3):
+        oui, oue, ow, ost = time_step(prob, oui, oue, ow, n, dd.linsolve())
+        st = s2.step(synth.STIMULUS)
+        assert st["reason"] == 0 and st["newton_its"] == ost["newton_its"]
+        assert abs(st["krylov_its"] - sum(ost["krylov_its"])) <= ost["newton_its"]

@@ -5,7 +5,7 @@ import pytest
 import synth
 from conftest import oracle_problem
 from oracle import ionic
-from oracle.bidomain import direct_solve
+from oracle.bidomain import direct_solve, time_step
 from oracle.dd import DDSolver
 from oracle.krylov import gmres, lanczos_cond, pcg
 
@@ -158,3 +158,84 @@ def test_rho_scaling_is_multiplicity_here():
         k = len(prob.part.cls_subs[c])
         for Dj in D.values():
             np.testing.assert_allclose(Dj, np.eye(Dj.shape[0]) / k, rtol=0, atol=1e-15)
+
+
+def _factor(prob, seed, bump):
+    ui, ue, w = synth.initial_state(prob.N, seed)
+    ui = ui + bump * np.exp(-np.sum(prob.mesh.coords ** 2, axis=1) / 0.01)
+    w1 = ionic.gating_step(ui - ue, w, prob.tau, prob.p)
+    r_i, r_e = prob.residual(ui, ue, w1, ui - 1.0, ue, prob.tau)
+    return prob.kc(ui, ue, w1), -r_i, -r_e
+
+
+def test_lagged_preconditioner_solution_and_spectral_bound():
+    """precond_every = 2: the second solve runs the current Schur operator with the first
+    setup's preconditioner.  It still reaches the direct solution, and its eigenvalues lie
+    in [alpha lmin, beta lmax] of the fresh pair, alpha, beta from the ratio of the
+    lumped reaction terms (Loewner bounds inherited by the Schur complements)."""
+    prob = oracle_problem("cube8ve")
+    kc_old, _, _ = _factor(prob, 0, 0.0)
+    kc_new, f_i, f_e = _factor(prob, 1, 60.0)
+    rho = kc_new / kc_old
+    assert rho.min() > 0
+    alpha, beta = min(1.0, rho.min()), max(1.0, rho.max())
+    # chi Cm + tau dI_ion/dv stays within about 0.8 .. 1.07 for tau = 0.05 ms, which is why
+    # an older preconditioner stays close; the upstroke bump uses most of that range
+    assert beta / alpha > 1.2
+    lag = DDSolver(prob, rtol=1e-13, atol=0.0, precond_every=2)
+    lag.solve(kc_old / prob.fem.M, f_i, f_e)
+    assert lag.last["precond_fresh"]
+    ai, ae, info = lag.solve(kc_new / prob.fem.M, f_i, f_e)
+    assert not info["precond_fresh"] and info["reason"] == "converged"
+    si, se, _ = direct_solve(prob, kc_new, f_i, f_e)
+    assert np.linalg.norm(np.r_[ai - si, ae - se]) < 1e-10 * np.linalg.norm(np.r_[si, se])
+    # dense spectra: M_old^-1 S_new against M_old^-1 S_old
+    old = DDSolver(prob)
+    old.setup(kc_old / prob.fem.M)
+    n = prob.dofs.n_iface
+    keep = np.ones(n, bool)
+    keep[old.g_iface] = False
+    Minv = _dense(old.bddc_apply, n, keep)
+    ev_old = np.sort(np.linalg.eigvals(Minv @ _dense(old.schur_apply, n, keep)).real)
+    ev_new = np.sort(np.linalg.eigvals(Minv @ _dense(lag.schur_apply, n, keep)).real)
+    assert ev_new[0] >= alpha * ev_old[0] * (1 - 1e-8)
+    assert ev_new[-1] <= beta * ev_old[-1] * (1 + 1e-8)
+    assert info["cond"] <= (ev_new[-1] / ev_new[0]) * (1 + 1e-6)
+    # the third setup rebuilds it again
+    lag.solve(kc_new / prob.fem.M, f_i, f_e)
+    assert lag.last["precond_fresh"]
+
+
+def test_lagged_preconditioner_only_for_bddc():
+    prob = oracle_problem("cube8ve")
+    with pytest.raises(ValueError):
+        DDSolver(prob, method="fetidp", precond_every=2)
+    with pytest.raises(ValueError):
+        DDSolver(prob, precond_every=0)
+
+
+def test_lagged_preconditioner_time_steps():
+    """Through the stimulus-driven upstroke, rebuilding the preconditioner only every
+    4th Jacobian gives the same states (Krylov and Newton tightened) and, at the paper's
+    tolerances, at most a few more Krylov iterations per solve."""
+    prob = oracle_problem("cube8ve")
+    states, its = {}, {}
+    for k in (1, 4):
+        for tight in (True, False):
+            kw = dict(rtol=1e-12, atol=0.0) if tight else {}
+            nkw = dict(rtol=1e-10, atol=1e-16) if tight else {}
+            dd = DDSolver(prob, precond_every=k, **kw)
+            ui, ue, w = synth.initial_state(prob.N, 0)
+            lits = []
+            for n in range(4):
+                ui, ue, w, st = time_step(prob, ui, ue, w, n, dd.linsolve(), **nkw)
+                lits += st["krylov_its"]
+            states[k, tight] = (ui, ue)
+            its[k, tight] = np.array(lits)
+            assert dd.n_setup == len(lits)
+    a, b = states[1, True], states[4, True]
+    assert np.linalg.norm(a[0] - b[0]) < 1e-9 * np.linalg.norm(a[0])
+    assert np.linalg.norm(a[1] - b[1]) < 1e-9 * np.linalg.norm(a[1])
+    fresh, lag = its[1, False], its[4, False]
+    assert len(fresh) == len(lag)
+    assert lag.max() <= fresh.max() + 3
