@@ -1,0 +1,94 @@
+"""Whole-beat runs (Section 6, Test 4 and Table 11): many consecutive time steps
+through activation and recovery, with the per-step statistics the paper reports.
+
+``run`` advances one solver handle for ``steps`` time steps from the seeded
+resting state and yields one record per step: the Newton iterations, the Krylov
+iterations summed over them, the status and the wall time of the step (each
+``bidomain_step`` call returns after its stream has synchronised).  ``summarize``
+turns the records into Table 11's columns: nlit (Newton iterations per time
+step), lit (Krylov iterations per Newton iteration) and the time per step.
+
+    python -m paper_2101_02959_gb300.beat --workload beat_slab_half --steps 2400 \\
+        --method bddc --precision mixed --out beat.jsonl
+
+Every step runs in the CUDA library; this module only loops and records.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import time
+
+import synth
+
+from . import binding, build
+
+
+def summarize(records):
+    """Table 11's columns from per-step records."""
+    n = len(records)
+    if n == 0:
+        return dict(steps=0, nlit=0.0, lit=0.0, time_s=0.0, failed=0)
+    newton = sum(r["newton_its"] for r in records)
+    krylov = sum(r["krylov_its"] for r in records)
+    return dict(steps=n, nlit=newton / n, lit=krylov / max(newton, 1),
+                time_s=sum(r["ms"] for r in records) / n / 1e3,
+                max_lit_step=max(r["krylov_its"] / max(r["newton_its"], 1) for r in records),
+                failed=sum(1 for r in records if r["reason"] != 0))
+
+
+def run(w, steps, seed=0, **opt):
+    """Yield one record per time step of workload ``w`` (a synth workload dict)."""
+    s = binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, **opt)
+    try:
+        ui, ue, wg = synth.initial_state(s.N, seed)
+        s.set_state(ui, ue, wg, 0.0)
+        stim = synth.stimulus(w)
+        for n in range(steps):
+            t0 = time.perf_counter()
+            st = s.step(stim)
+            ms = (time.perf_counter() - t0) * 1e3
+            yield dict(step=n + 1, t=(n + 1) * synth.TAU, newton_its=st["newton_its"],
+                       krylov_its=st["krylov_its"], reason=st["reason"], ms=ms)
+            if st["reason"] != 0:
+                return
+    finally:
+        s.close()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--workload", default="beat_slab_half")
+    ap.add_argument("--steps", type=int, default=None, help="default: the workload's own step count")
+    ap.add_argument("--method", default="bddc", choices=("bddc", "fetidp"))
+    ap.add_argument("--krylov", default="pcg", choices=("pcg", "gmres"))
+    ap.add_argument("--precision", default="mixed", choices=("fp64", "mixed"))
+    ap.add_argument("--scaling", default="deluxe", choices=("deluxe", "rho"))
+    ap.add_argument("--precond-every", type=int, default=1)
+    ap.add_argument("--graphs", type=int, default=1)
+    ap.add_argument("--out", default=None, help="JSONL file: one line per step, then the summary")
+    a = ap.parse_args(argv)
+    w = synth.workload(a.workload)
+    steps = a.steps if a.steps is not None else w["steps"]
+    build.build()
+    records = []
+    out = open(a.out, "w") if a.out else None
+    try:
+        for r in run(w, steps, method=a.method, krylov=a.krylov, precision=a.precision, scaling=a.scaling,
+                     precond_every=a.precond_every, use_graphs=a.graphs):
+            records.append(r)
+            if out:
+                out.write(json.dumps(r) + "\n")
+        summary = dict(summarize(records), workload=a.workload, method=a.method, precision=a.precision,
+                       scaling=a.scaling, precond_every=a.precond_every)
+        if out:
+            out.write(json.dumps(dict(summary=summary)) + "\n")
+    finally:
+        if out:
+            out.close()
+    print(json.dumps(summary))
+    return 0 if summary["failed"] == 0 and summary["steps"] == steps else 1
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

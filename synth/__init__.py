@@ -22,6 +22,9 @@ Workloads (all Q1 hexahedral slabs, h = element size):
 * ``ell10``    10x9x6 elements of the same ellipsoid, 4^3-element blocks with
                ragged last blocks.
 * ``ell32``    32x32x16 elements of the same ellipsoid, 4x4x2 subdomains, H/h = 8.
+* ``beat_slab`` / ``beat_ell``  the whole-beat runs of Test 4: 192x96x24 elements,
+               8x8x2 subdomains (8,450 dofs each), 2,400 / 3,400 steps;
+               ``beat_*_half`` halve each mesh direction.
 
 The ellipsoid's axes are not printed in the paper: a1 = b1 = 1.5, a2 = b2 =
 2.7, c1 = 4.4, c2 = 5.0 cm (a 1.2 cm wall, an idealised left ventricle) are
@@ -59,6 +62,13 @@ WORKLOADS = {
 for _name, _n, _s in (("ell8", (8, 8, 8), (4, 4, 4)), ("ell10", (10, 9, 6), (4, 4, 4)),
                       ("ell32", (32, 32, 16), (8, 8, 8))):
     WORKLOADS[_name] = dict(n=_n, ellipsoid=ELLIPSOID, s=_s, primal="VE", steps=2)
+# Section 6, Test 4 (Table 11): a whole beat on 8x8x2 subdomains of a 192x96x24 mesh
+# (8,450 dofs per subdomain), the slab for 2,400 steps and the ellipsoid for 3,400;
+# the *_half variants halve every mesh direction (1,274 dofs per subdomain).
+WORKLOADS["beat_slab"] = dict(n=(192, 96, 24), l=(1.92, 1.92, 0.48), s=(24, 12, 12), primal="VE", steps=2400)
+WORKLOADS["beat_ell"] = dict(n=(192, 96, 24), ellipsoid=ELLIPSOID, s=(24, 12, 12), primal="VE", steps=3400)
+WORKLOADS["beat_slab_half"] = dict(n=(96, 48, 12), l=(1.92, 1.92, 0.48), s=(12, 6, 6), primal="VE", steps=2400)
+WORKLOADS["beat_ell_half"] = dict(n=(96, 48, 12), ellipsoid=ELLIPSOID, s=(12, 6, 6), primal="VE", steps=3400)
 for _k in (4, 8, 12, 16, 20):
     WORKLOADS[f"opt{_k}"] = dict(n=(4 * _k,) * 3, l=(0.8, 0.8, 0.8), s=(_k,) * 3,
                                  primal="VE", steps=40)

@@ -1,0 +1,40 @@
+"""Whole-beat runner on the GPU (Section 6, Test 4): many consecutive steps through the
+stimulus and the upstroke, against the oracle's own run of the same steps."""
+import numpy as np
+import pytest
+
+import synth
+from conftest import oracle_problem
+from oracle.bidomain import time_step
+from oracle.dd import DDSolver
+
+pytestmark = pytest.mark.gpu
+
+
+def test_runner_follows_the_oracle_through_the_upstroke():
+    from paper_2101_02959_gb300 import beat, binding, build
+    build.build()
+    name, steps = "cube8ve", 24  # 1.2 ms: the 1 ms stimulus and the start of propagation
+    prob = oracle_problem(name)
+    dd = DDSolver(prob, rtol=1e-12, atol=0.0)
+    ui, ue, w = synth.initial_state(prob.N, 0)
+    newton = []
+    for n in range(steps):
+        ui, ue, w, st = time_step(prob, ui, ue, w, n, dd.linsolve(), rtol=1e-10, atol=1e-16)
+        newton.append(st["newton_its"])
+    opt = dict(precision="fp64", ksp_rtol=1e-12, ksp_atol=0.0, snes_rtol=1e-10, snes_atol=1e-16)
+    recs = list(beat.run(synth.workload(name), steps, **opt))
+    assert len(recs) == steps and all(r["reason"] == 0 for r in recs)
+    summ = beat.summarize(recs)
+    assert abs(summ["nlit"] - np.mean(newton)) <= 0.25
+    # the same steps through the public handle give the oracle's state at the end
+    s = binding.Solver(synth.workload(name), synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, **opt)
+    u0 = synth.initial_state(prob.N, 0)
+    s.set_state(*u0, 0.0)
+    for n in range(steps):
+        assert s.step(synth.stimulus(prob.workload))["reason"] == 0
+    gui, gue, _, _ = s.get_state()
+    s.close()
+    v, gv = ui - ue, gui - gue
+    assert np.linalg.norm(gv - v) <= 1e-8 * np.linalg.norm(v)
+    assert np.linalg.norm(gue - ue) <= 1e-8 * np.linalg.norm(ue)
