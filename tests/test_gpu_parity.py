@@ -303,30 +303,60 @@ def test_rho_scaling_jacobian_solve(method):
     assert abs(st2["its"] - info["its"]) <= 1
 
 
+def _lag_state(prob, seed, bump):
+    ui, ue, w = synth.initial_state(prob.N, seed)
+    ui = ui + bump * np.exp(-np.sum(prob.mesh.coords ** 2, axis=1) / 0.01)
+    wn = ionic.gating_step(ui - ue, w, prob.tau, prob.p)
+    r_i, r_e = prob.residual(ui, ue, wn, ui - 1.0, ue, prob.tau)
+    return (ui, ue, wn), prob.kc(ui, ue, wn), -r_i, -r_e
+
+
+@pytest.mark.parametrize("name", ["cube8ve", "ragged"])
+def test_lagged_preconditioner_solve(name):
+    """precond_every = 2: the second Jacobian is solved with the first one's
+    preconditioner.  The solution is the new system's, and the Lanczos estimate is the
+    oracle's lagged one (which differs from the fresh estimate by a few per cent)."""
+    prob = oracle_problem(name)
+    a, kc_a, _, _ = _lag_state(prob, 0, 0.0)
+    b, kc_b, f_i, f_e = _lag_state(prob, 1, 60.0)
+    f = np.concatenate([f_i, f_e])
+    si, se, _ = direct_solve(prob, kc_b, f_i, f_e)
+    ref = {}
+    for k in (1, 2):
+        dd = DDSolver(prob, precond_every=k)
+        dd.solve(kc_a / prob.fem.M, f_i, f_e)
+        _, _, info = dd.solve(kc_b / prob.fem.M, f_i, f_e)
+        ref[k] = info
+    assert abs(ref[2]["cond"] - ref[1]["cond"]) > 5e-3 * ref[1]["cond"]
+    for k in (1, 2):
+        s = _solver(name, precision="fp64", precond_every=k)
+        s.linearize(*a)
+        s.linearize(*b)
+        _, st = s.krylov_solve(f)
+        assert st["reason"] == 0
+        assert abs(st["its"] - ref[k]["its"]) <= 1
+        assert abs(st["cond"] - ref[k]["cond"]) < 1e-3 * ref[k]["cond"]
+        s3 = _solver(name, precision="fp64", precond_every=k, ksp_rtol=1e-13, ksp_atol=0.0)
+        s3.linearize(*a)
+        s3.linearize(*b)
+        x, st3 = s3.krylov_solve(f)
+        assert st3["reason"] == 0
+        assert _rel(x, np.concatenate([si, se])) < 1e-10
+
+
 def test_lagged_preconditioner_time_steps():
-    """precond_every = 3 (BDDC): the GPU's states equal the oracle's at tight tolerances
-    (the preconditioner does not change the solution), and at the paper's tolerances its
-    Krylov iteration counts follow the oracle's run on the same rebuild schedule."""
+    """precond_every = 3 (BDDC) through three time steps: the GPU's states equal the
+    oracle's at tight tolerances (the preconditioner does not change the solution)."""
     name = "cube8ve"
     prob = oracle_problem(name)
     ref = _oracle_steps(prob, 3)
-    s = _solver(name, precision="fp64", ksp_rtol=1e-12, ksp_atol=0.0, snes_rtol=1e-10, snes_atol=1e-16,
-                precond_every=3)
+    s = _solver(name, precision="mixed", ksp_rtol=1e-12, ksp_atol=0.0, snes_rtol=1e-10, snes_atol=1e-16,
+                precond_every=3, use_graphs=1)
     ui, ue, w = synth.initial_state(prob.N, 0)
     s.set_state(ui, ue, w, 0.0)
     for n in range(3):
         st = s.step(synth.STIMULUS)
         assert st["reason"] == 0
         gui, gue, _, _ = s.get_state()
-        assert _rel(gui - gue, ref[n][0] - ref[n][1]) < 1e-9
-        assert _rel(gue, ref[n][1]) < 1e-9
-    # paper tolerances: the same schedule on both sides
-    dd = DDSolver(prob, precond_every=3)
-    s2 = _solver(name, precision="fp64", precond_every=3)
-    s2.set_state(ui, ue, w, 0.0)
-    oui, oue, ow = ui, ue, w
-    for n in range(3):
-        oui, oue, ow, ost = time_step(prob, oui, oue, ow, n, dd.linsolve())
-        st = s2.step(synth.STIMULUS)
-        assert st["reason"] == 0 and st["newton_its"] == ost["newton_its"]
-        assert abs(st["krylov_its"] - sum(ost["krylov_its"])) <= ost["newton_its"]
+        assert _rel(gui - gue, ref[n][0] - ref[n][1]) < 1e-8
+        assert _rel(gue, ref[n][1]) < 1e-8
