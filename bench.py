@@ -135,7 +135,7 @@ def run_gpu(args, w, rank, world):
                            lag_jacobian=int(precision == "mixed" and args.lag))
         s.set_state(*dstate, 0.0)
         for _ in range(args.warmup):
-            s.step(synth.STIMULUS)
+            s.step(synth.stimulus(w))
         tune = s.autotune() if args.autotune else None
         s.set_state(*dstate, 0.0)
         if profile:
@@ -149,7 +149,7 @@ def run_gpu(args, w, rank, world):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.steps):
-            stats.append(s.step(synth.STIMULUS))
+            stats.append(s.step(synth.stimulus(w)))
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -188,7 +188,7 @@ def run_gpu(args, w, rank, world):
     hs = (ui0.copy(), ue0.copy(), w0.copy())
     s.set_state(*hs, 0.0)
     for _ in range(args.warmup):
-        s.step(synth.STIMULUS)
+        s.step(synth.stimulus(w))
     if args.autotune:
         s.autotune()
     barrier()
@@ -198,7 +198,7 @@ def run_gpu(args, w, rank, world):
     e2e_newton = 0
     for _ in range(args.steps):
         s.set_state(*state, t)
-        st = s.step(synth.STIMULUS)
+        st = s.step(synth.stimulus(w))
         e2e_newton += st["newton_its"]
         ui, ue, wv, t = s.get_state()
         state = (ui, ue, wv)
@@ -304,7 +304,7 @@ def cpu_baseline(w, steps=1):
     import synth
     from oracle.bidomain import Problem, time_step
     from oracle.dd import DDSolver
-    prob = Problem(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, synth.STIMULUS)
+    prob = Problem(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, synth.stimulus(w))
     ui, ue, wv = synth.initial_state(prob.N, 0)
     dd = DDSolver(prob)
     newton = 0
@@ -345,11 +345,11 @@ def sweep(args):
                                precision=prec, use_graphs=1, use_tensor_cores=int(prec == "mixed"))
             ui, ue, wv = synth.initial_state(s.N, 0)
             s.set_state(ui, ue, wv, 0.0)
-            s.step(synth.STIMULUS)
+            s.step(synth.stimulus(w))
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            st = s.step(synth.STIMULUS)
+            st = s.step(synth.stimulus(w))
             e1.record(stream)
             torch.cuda.synchronize()
             rows.append(dict(hh=k, precision=prec, unknowns=2 * s.N, newton=st["newton_its"],

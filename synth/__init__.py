@@ -24,7 +24,9 @@ Workloads (all Q1 hexahedral slabs, h = element size):
 * ``ell32``    32x32x16 elements of the same ellipsoid, 4x4x2 subdomains, H/h = 8.
 * ``beat_slab`` / ``beat_ell``  the whole-beat runs of Test 4: 192x96x24 elements,
                8x8x2 subdomains (8,450 dofs each), 2,400 / 3,400 steps;
-               ``beat_*_half`` halve each mesh direction.
+               ``beat_*_half`` halve each mesh direction; ``beat_mini`` is a
+               0.2x0.2x0.05 cm slab at h = 0.0125 cm (2,890 unknowns) for a
+               whole beat the oracle can follow.
 
 The ellipsoid's axes are not printed in the paper: a1 = b1 = 1.5, a2 = b2 =
 2.7, c1 = 4.4, c2 = 5.0 cm (a 1.2 cm wall, an idealised left ventricle) are
@@ -67,6 +69,9 @@ for _name, _n, _s in (("ell8", (8, 8, 8), (4, 4, 4)), ("ell10", (10, 9, 6), (4, 
 # the *_half variants halve every mesh direction (1,274 dofs per subdomain).
 WORKLOADS["beat_slab"] = dict(n=(192, 96, 24), l=(1.92, 1.92, 0.48), s=(24, 12, 12), primal="VE", steps=2400)
 WORKLOADS["beat_ell"] = dict(n=(192, 96, 24), ellipsoid=ELLIPSOID, s=(24, 12, 12), primal="VE", steps=3400)
+# a whole beat small enough for the oracle: h = 0.0125 cm (at h = 0.05 cm, as in cube8,
+# the front from the corner stimulus does not propagate), 2x2x2 subdomains
+WORKLOADS["beat_mini"] = dict(n=(16, 16, 4), l=(0.2, 0.2, 0.05), s=(8, 8, 2), primal="VE", steps=2400)
 WORKLOADS["beat_slab_half"] = dict(n=(96, 48, 12), l=(1.92, 1.92, 0.48), s=(12, 6, 6), primal="VE", steps=2400)
 WORKLOADS["beat_ell_half"] = dict(n=(96, 48, 12), ellipsoid=ELLIPSOID, s=(12, 6, 6), primal="VE", steps=3400)
 for _k in (4, 8, 12, 16, 20):

@@ -64,3 +64,23 @@ def test_ellipsoid_optimality_against_table8():
     for prim in ("V", "VE", "VEF"):
         a, b = ours[prim, "deluxe"][1], ours[prim, "rho"][1]
         assert abs(a - b) <= 0.05 * a
+
+
+def test_whole_beat_trace_activates_and_recovers():
+    """The oracle's stored whole beat (tests/golden/make_whole_beat_trace.py) on a
+    0.2 x 0.2 x 0.05 cm slab: the corner stimulus activates the whole domain within a few
+    ms, the plateau stays below v_p = 100 mV (the excited rest point of Rogers-McCulloch),
+    and by 120 ms the tissue is back at rest, the activation-recovery interval Section 6
+    gives for the slab's whole beat with this model."""
+    rows = []
+    for line in open(os.path.join(HERE, "golden", "whole_beat_beat_mini.txt")):
+        if line.strip() and not line.startswith("#"):
+            rows.append([float(x) for x in line.split()])
+    rows = np.array(rows)
+    t, nit, vmin, vmax = rows[:, 0], rows[:, 1], rows[:, 2], rows[:, 3]
+    assert abs(t[-1] - 120.0) < 1e-9 and len(rows) == 60
+    active = np.nonzero(vmin > 50.0)[0]
+    assert len(active) > 0 and t[active[0]] <= 10.0
+    assert vmax.max() < 100.0 and vmax.max() > 90.0
+    assert vmax[-1] < 1.0 and abs(vmin[-1]) < 1.0
+    assert nit.max() <= 3

@@ -38,3 +38,48 @@ def test_runner_follows_the_oracle_through_the_upstroke():
     v, gv = ui - ue, gui - gue
     assert np.linalg.norm(gv - v) <= 1e-8 * np.linalg.norm(v)
     assert np.linalg.norm(gue - ue) <= 1e-8 * np.linalg.norm(ue)
+
+
+def _trace(name):
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", f"whole_beat_{name}.txt")
+    nodes, rows = None, []
+    for line in open(path):
+        if line.startswith("# nodes:"):
+            nodes = [int(x) for x in line.split(":")[1].split()]
+        elif line.strip() and not line.startswith("#"):
+            rows.append([float(x) for x in line.split()])
+    return nodes, np.array(rows)
+
+
+def test_whole_beat_against_the_oracle_trace():
+    """A whole activation-recovery beat (2,400 steps, 120 ms) on the GPU against the
+    oracle's stored run (direct solves, tight Newton): v and u_e at five nodes and the
+    extremes and mean of v every 2 ms, and the Newton iteration counts."""
+    from paper_2101_02959_gb300 import binding, build
+    build.build()
+    name = "beat_mini"
+    nodes, ref = _trace(name)
+    prob = oracle_problem(name)
+    s = binding.Solver(synth.workload(name), synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU,
+                       precision="fp64", ksp_rtol=1e-12, ksp_atol=0.0, snes_rtol=1e-10, snes_atol=1e-16)
+    s.set_state(*synth.initial_state(prob.N, 0), 0.0)
+    stim = synth.stimulus(prob.workload)
+    M = prob.fem.M
+    every = int(round(ref[0, 0] / synth.TAU))
+    k = 0
+    for n in range(int(round(ref[-1, 0] / synth.TAU))):
+        st = s.step(stim)
+        assert st["reason"] == 0
+        if (n + 1) % every:
+            continue
+        ui, ue, _, t = s.get_state()
+        row = ref[k]
+        k += 1
+        assert abs(t - row[0]) < 1e-9
+        assert abs(st["newton_its"] - row[1]) <= 1
+        v = ui - ue
+        got = np.r_[v.min(), v.max(), float(M @ v) / M.sum(), v[nodes], ue[nodes]]
+        assert np.abs(got - row[2:]).max() < 1e-3, (t, np.abs(got - row[2:]).max())
+    s.close()
+    assert k == len(ref)
