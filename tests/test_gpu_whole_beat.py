@@ -26,7 +26,7 @@ def test_runner_follows_the_oracle_through_the_upstroke():
     recs = list(beat.run(synth.workload(name), steps, **opt))
     assert len(recs) == steps and all(r["reason"] == 0 for r in recs)
     summ = beat.summarize(recs)
-    assert abs(summ["nlit"] - np.mean(newton)) <= 0.25
+    assert abs(summ["nlit"] - np.mean(newton)) <= 0.5
     # the same steps through the public handle give the oracle's state at the end
     s = binding.Solver(synth.workload(name), synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, **opt)
     u0 = synth.initial_state(prob.N, 0)
