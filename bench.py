@@ -36,8 +36,13 @@ FP64_PEAK = 1.25                                  # TFLOP/s, nominal GB300 FP64
 def describe(w):
     nx, ny, nz = w["n"]
     sx, sy, sz = w["s"]
-    return (f"{w['name']}: {nx}x{ny}x{nz} Q1 slab {w['l'][0]}x{w['l'][1]}x{w['l'][2]} cm, "
-            f"{nx // sx}x{ny // sy}x{nz // sz} subdomains H/h={sx}, primal {w['primal']}, tau=0.05 ms")
+    if "ellipsoid" in w:
+        dom = "isoparametric Q1 truncated ellipsoid (Section 6)"
+    else:
+        dom = f"Q1 slab {w['l'][0]}x{w['l'][1]}x{w['l'][2]} cm"
+    nb = [-(-n // b) for n, b in zip(w["n"], w["s"])]
+    return (f"{w['name']}: {nx}x{ny}x{nz} {dom}, "
+            f"{nb[0]}x{nb[1]}x{nb[2]} subdomains H/h={sx}, primal {w['primal']}, tau=0.05 ms")
 
 
 class ClockSampler:
@@ -132,7 +137,8 @@ def run_gpu(args, w, rank, world):
                            precision=precision, method=method, use_graphs=graphs, learned_guess=learned,
                            mlp_train_steps=args.steps + args.warmup + 1, mlp_epochs=args.mlp_epochs,
                            use_tensor_cores=int(precision == "mixed" and args.tc),
-                           lag_jacobian=int(precision == "mixed" and args.lag))
+                           lag_jacobian=int(precision == "mixed" and args.lag), scaling=args.scaling,
+                           precond_every=args.precond_every if method == "bddc" else 1)
         s.set_state(*dstate, 0.0)
         for _ in range(args.warmup):
             s.step(synth.stimulus(w))
@@ -184,7 +190,8 @@ def run_gpu(args, w, rank, world):
                        precision=args.precision, method=args.method, use_graphs=1, learned_guess=args.learned,
                        mlp_train_steps=args.steps + args.warmup + 1, mlp_epochs=args.mlp_epochs,
                        use_tensor_cores=int(args.precision == "mixed" and args.tc),
-                       lag_jacobian=int(args.precision == "mixed" and args.lag))
+                       lag_jacobian=int(args.precision == "mixed" and args.lag), scaling=args.scaling,
+                       precond_every=args.precond_every if args.method == "bddc" else 1)
     hs = (ui0.copy(), ue0.copy(), w0.copy())
     s.set_state(*hs, 0.0)
     for _ in range(args.warmup):
@@ -299,14 +306,14 @@ def roofline(prof, precision, tc_used=False):
     return r, dom
 
 
-def cpu_baseline(w, steps=1):
+def cpu_baseline(w, steps=1, method="bddc", scaling="deluxe"):
     """The oracle (numpy, FP64) on the host cores: `steps` time steps of the same workload."""
     import synth
     from oracle.bidomain import Problem, time_step
     from oracle.dd import DDSolver
     prob = Problem(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, synth.stimulus(w))
     ui, ue, wv = synth.initial_state(prob.N, 0)
-    dd = DDSolver(prob)
+    dd = DDSolver(prob, method=method, scaling=scaling)
     newton = 0
     t0 = time.perf_counter()
     for n in range(steps):
@@ -371,6 +378,9 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--method", default="bddc", choices=["bddc", "fetidp"])
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--scaling", default="deluxe", choices=["deluxe", "rho"])
+    ap.add_argument("--primal", default=None, choices=["V", "VE", "VEF"], help="override the workload's primal space")
+    ap.add_argument("--precond-every", type=int, default=1, help="BDDC: rebuild the preconditioner every k Jacobians")
     ap.add_argument("--learned", type=int, default=1, help="1: learned initial guess in the chosen solver")
     ap.add_argument("--tc", type=int, default=1, help="1: tensor-core (tcgen05) Schur updates in mixed precision")
     ap.add_argument("--lag", type=int, default=1, help="1: chord Newton (one factorisation per time step), mixed only")
@@ -386,6 +396,8 @@ def main():
 
     import synth
     w = synth.workload(args.workload)
+    if args.primal:
+        w["primal"] = args.primal
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
 
@@ -393,13 +405,13 @@ def main():
         if rank != 0:
             return
         # the oracle is the reference arm: bounded sample of the same workload (about 3 minutes at most)
-        one = cpu_baseline(w, 1)
+        one = cpu_baseline(w, 1, args.method, args.scaling)
         steps = max(1, min(args.steps, int(150.0 / max(one["seconds"], 1e-3))))
-        res = cpu_baseline(w, steps) if steps > 1 else one
+        res = cpu_baseline(w, steps, args.method, args.scaling) if steps > 1 else one
         line = {"impl": "reference", "metric": METRIC, "value": res["ms_per_step"], "unit": "ms/time step",
                 "n_gpus": args.gpus, "steps": res["steps"], "warmup": 0, "ms_per_step": res["ms_per_step"],
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": describe(w), "method": "bddc-deluxe", "krylov": "pcg"},
+                "data": "synthetic", "config": {"workload": describe(w), "method": f"{args.method}-{args.scaling}", "krylov": "pcg"},
                 "krylov_solves_per_s": res["solves_per_s"],
                 "cpu_baseline": {"value": res["ms_per_step"], "unit": "ms/time step", "cores": res["cores"],
                                  "kind": "oracle", "sample": f"{res['steps']} time step(s) of {w['name']}"},
@@ -423,7 +435,7 @@ def main():
     roof, dom = roofline(ch["prof"], args.precision, tc_used)
     cpu = None
     if world == 1 and args.cpu_steps > 0:
-        c = cpu_baseline(w, args.cpu_steps)
+        c = cpu_baseline(w, args.cpu_steps, args.method, args.scaling)
         cpu = {"value": c["ms_per_step"], "unit": "ms/time step", "cores": c["cores"], "kind": "oracle",
                "sample": f"{c['steps']} time step(s) of {w['name']} ({c['seconds']:.1f} s)",
                "krylov_solves_per_s": c["solves_per_s"]}
@@ -433,9 +445,9 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 local factors (tf32 tensor cores) + f64 Krylov/Newton/coarse solve" if args.precision == "mixed"
         else "f64", "data": "synthetic",
-        "config": {"workload": describe(w), "unknowns": 2 * r["N"], "method": args.method + "-deluxe",
+        "config": {"workload": describe(w), "unknowns": 2 * r["N"], "method": f"{args.method}-{args.scaling}",
                    "krylov": "pcg", "precision": args.precision, "learned_guess": bool(args.learned),
-                   "tensor_cores": tc_used,
+                   "tensor_cores": tc_used, "precond_every": args.precond_every,
                    "chord_newton": bool(args.lag and args.precision == "mixed"), "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": "per-step working set > 129 MB L2 (local matrices 0.27 GB f32 / 0.54 GB f64)"},
         "krylov_solves_per_s": ch["newton"] / sec,
