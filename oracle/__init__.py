@@ -9,14 +9,17 @@ FETI-DP deluxe solvers for implicit time discretizations of the cardiac
 Bidomain equations" (arXiv 2101.02959):
 
 * ``mesh``     Section 4.1: structured Q1 grid, subdomains, the sets N_x and
-               the face / edge / vertex equivalence classes, primal sets.
+               the face / edge / vertex equivalence classes, primal sets;
+               Section 6: the truncated-ellipsoid map.
 * ``fem``      Section 3a: fibre field, conductivity tensors D_{i,e},
-               Q1 stiffness A_{i,e} and the lumped mass M.
+               Q1 stiffness A_{i,e} and the lumped mass M, on box elements
+               and on isoparametric (ellipsoid) elements.
 * ``ionic``    Section 2: Rogers-McCulloch I_ion and R; Section 3b Step 1.
 * ``bidomain`` Section 3b Step 2 (F, G), Section 3c (Jacobian, Newton),
                direct sparse solve of the Jacobian system.
 * ``dd``       Sections 4.1-4.4: local matrices, Schur complements, deluxe
-               scaling, BDDC and FETI-DP operators.
+               and rho scaling, BDDC and FETI-DP operators, and the option of
+               a lagged BDDC preconditioner.
 * ``krylov``   PCG, GMRES and the Lanczos condition-number estimate.
 * ``mlp``      FP64 forward / backward of the initial-guess network.
 
