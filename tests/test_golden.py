@@ -84,3 +84,17 @@ def test_whole_beat_trace_activates_and_recovers():
     assert vmax.max() < 100.0 and vmax.max() > 90.0
     assert vmax[-1] < 1.0 and abs(vmin[-1]) < 1.0
     assert nit.max() <= 3
+
+
+def test_ellipsoid_optimality_growth_to_h12():
+    """From H/h = 8 to 12 (Table 8, V+E deluxe) the condition number grows like the
+    (1 + log(H/h))^2 bound: the oracle's growth ratio is within 10 % of the table's, and
+    its H/h = 12 values within 30 % (cond) and 3 iterations of the printed ones."""
+    p8, p12 = _rows("table8_ellipsoid_h8.txt"), _rows("table8_ellipsoid_h12.txt")
+    o8, o12 = _rows("ellipsoid_optimality_h8.txt"), _rows("ellipsoid_optimality_h12.txt")
+    k = ("VE", "deluxe")
+    paper_growth = p12[k][1] / p8[k][1]
+    ours_growth = o12[k][1] / o8[k][1]
+    assert ours_growth > 1.0 and abs(ours_growth - paper_growth) <= 0.1 * paper_growth
+    assert abs(o12[k][1] - p12[k][1]) <= 0.3 * p12[k][1]
+    assert abs(o12[k][0] - p12[k][0]) <= 3
