@@ -7,6 +7,9 @@ iterations summed over them, the status and the wall time of the step (each
 ``bidomain_step`` call returns after its stream has synchronised).  ``summarize``
 turns the records into Table 11's columns: nlit (Newton iterations per time
 step), lit (Krylov iterations per Newton iteration) and the time per step.
+With ``record_every = k`` the state is read back every k steps, and each node's
+activation and recovery times are kept in ``maps``: the first sampled time v
+reaches ``threshold`` mV, and the first sampled time after that it is below it.
 
     python -m paper_2101_02959_gb300.beat --workload beat_slab_half --steps 2400 \\
         --method bddc --precision mixed --out beat.jsonl
@@ -18,6 +21,8 @@ from __future__ import annotations
 import argparse
 import json
 import time
+
+import numpy as np
 
 import synth
 
@@ -37,13 +42,37 @@ def summarize(records):
                 failed=sum(1 for r in records if r["reason"] != 0))
 
 
-def run(w, steps, seed=0, **opt):
-    """Yield one record per time step of workload ``w`` (a synth workload dict)."""
+def update_maps(maps, v, t, threshold):
+    """Activation (first v >= threshold) and recovery (first v < threshold after it) times."""
+    act, rec = maps["activation"], maps["recovery"]
+    rec[~np.isnan(act) & np.isnan(rec) & (v < threshold)] = t
+    act[np.isnan(act) & (v >= threshold)] = t
+
+
+def activation_summary(maps):
+    """Time by which every node has activated (NaN if some never did), the fraction of
+    nodes activated and the mean activation-recovery interval of the nodes that recovered."""
+    act, rec = maps["activation"], maps["recovery"]
+    done = ~np.isnan(rec)
+    return dict(all_active_ms=float(np.max(act)) if not np.isnan(act).any() else float("nan"),
+                active_fraction=float(np.mean(~np.isnan(act))),
+                mean_ari_ms=float(np.mean(rec[done] - act[done])) if done.any() else float("nan"))
+
+
+def run(w, steps, seed=0, maps=None, record_every=0, threshold=50.0, **opt):
+    """Yield one record per time step of workload ``w`` (a synth workload dict).
+
+    maps: a dict that receives "activation" and "recovery" (ms per node, NaN where the
+    event was not seen) when record_every > 0."""
     s = binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, **opt)
     try:
         ui, ue, wg = synth.initial_state(s.N, seed)
         s.set_state(ui, ue, wg, 0.0)
         stim = synth.stimulus(w)
+        record = bool(record_every) and maps is not None
+        if record:
+            maps["activation"] = np.full(s.N, np.nan)
+            maps["recovery"] = np.full(s.N, np.nan)
         for n in range(steps):
             t0 = time.perf_counter()
             st = s.step(stim)
@@ -52,6 +81,9 @@ def run(w, steps, seed=0, **opt):
                        krylov_its=st["krylov_its"], reason=st["reason"], ms=ms)
             if st["reason"] != 0:
                 return
+            if record and (n + 1) % record_every == 0:
+                gui, gue, _, t = s.get_state()
+                update_maps(maps, np.asarray(gui) - np.asarray(gue), t, threshold)
     finally:
         s.close()
 
@@ -67,20 +99,25 @@ def main(argv=None):
     ap.add_argument("--precond-every", type=int, default=1)
     ap.add_argument("--graphs", type=int, default=1)
     ap.add_argument("--out", default=None, help="JSONL file: one line per step, then the summary")
+    ap.add_argument("--record-every", type=int, default=0,
+                    help="read the state back every k steps for activation / recovery times (0: off)")
     a = ap.parse_args(argv)
     w = synth.workload(a.workload)
     steps = a.steps if a.steps is not None else w["steps"]
     build.build()
-    records = []
+    records, maps = [], {}
     out = open(a.out, "w") if a.out else None
     try:
-        for r in run(w, steps, method=a.method, krylov=a.krylov, precision=a.precision, scaling=a.scaling,
-                     precond_every=a.precond_every, use_graphs=a.graphs):
+        for r in run(w, steps, maps=maps, record_every=a.record_every, method=a.method, krylov=a.krylov,
+                     precision=a.precision, scaling=a.scaling, precond_every=a.precond_every,
+                     use_graphs=a.graphs):
             records.append(r)
             if out:
                 out.write(json.dumps(r) + "\n")
         summary = dict(summarize(records), workload=a.workload, method=a.method, precision=a.precision,
                        scaling=a.scaling, precond_every=a.precond_every)
+        if maps:
+            summary.update(activation_summary(maps))
         if out:
             out.write(json.dumps(dict(summary=summary)) + "\n")
     finally:

@@ -1,5 +1,7 @@
 """Host logic of the whole-beat runner (Section 6, Test 4): the loop, the records and
 Table 11's summary columns, with a stand-in solver handle (no GPU)."""
+import numpy as np
+
 import synth
 from paper_2101_02959_gb300 import beat
 
@@ -23,6 +25,13 @@ class _FakeSolver:
         self.stims.append(stim)
         fail = self.opt.get("fail_at") == self.steps
         return dict(newton_its=1 + self.steps % 2, krylov_its=10 * (1 + self.steps % 2), reason=-3 if fail else 0)
+
+    def get_state(self):
+        # node x activates at step 3 + x and recovers at step 20 + 2 x (v in mV)
+        k = self.steps
+        x = np.arange(self.N)
+        v = np.where((k >= 3 + x) & (k < 20 + 2 * x), 90.0, 0.0)
+        return v + 1.0, np.ones(self.N), np.zeros(self.N), k * synth.TAU
 
     def close(self):
         self.closed = True
@@ -60,3 +69,27 @@ def test_whole_beat_workloads_match_test4():
         nb = [w["n"][d] // w["s"][d] for d in range(3)]
         assert nb == [8, 8, 2]
         assert 2 * (w["s"][0] + 1) * (w["s"][1] + 1) * (w["s"][2] + 1) == 8450
+
+
+def test_activation_and_recovery_maps(monkeypatch):
+    """Sampled every 2 steps, node x (activating at step 3 + x, recovering at 20 + 2x)
+    gets the first sample at or after each event; nodes still active keep NaN recovery."""
+    monkeypatch.setattr(beat.binding, "Solver", _FakeSolver)
+    w = dict(synth.workload("tiny"))
+    maps = {}
+    recs = list(beat.run(w, 40, maps=maps, record_every=2))
+    assert len(recs) == 40
+    act, rec = maps["activation"], maps["recovery"]
+    N = len(act)
+    x = np.arange(N)
+    first = lambda k: 2 * np.ceil(k / 2.0)  # noqa: E731  first even step >= k
+    seen = first(3 + x) <= 40
+    np.testing.assert_allclose(act[seen], first(3 + x)[seen] * synth.TAU)
+    assert np.all(np.isnan(act[~seen]))
+    back = seen & (first(20 + 2 * x) <= 40)
+    np.testing.assert_allclose(rec[back], first(20 + 2 * x)[back] * synth.TAU)
+    assert np.all(np.isnan(rec[~back]))
+    summ = beat.activation_summary(maps)
+    assert np.isnan(summ["all_active_ms"]) == (not seen.all())
+    assert abs(summ["active_fraction"] - seen.mean()) < 1e-15
+    np.testing.assert_allclose(summ["mean_ari_ms"], np.mean((rec - act)[back]))

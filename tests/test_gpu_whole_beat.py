@@ -83,3 +83,20 @@ def test_whole_beat_against_the_oracle_trace():
         assert np.abs(got - row[2:]).max() < 1e-3, (t, np.abs(got - row[2:]).max())
     s.close()
     assert k == len(ref)
+
+
+def test_runner_activation_time_matches_the_oracle_beat():
+    """The runner's activation map (sampled every 2 ms) on beat_mini: the time by which the
+    whole slab is active is the first sample of the oracle's stored beat with v_min >= 50 mV."""
+    from paper_2101_02959_gb300 import beat, build
+    build.build()
+    _, ref = _trace("beat_mini")
+    t_all = ref[np.nonzero(ref[:, 2] >= 50.0)[0][0], 0]
+    maps = {}
+    steps = int(round((t_all + 4.0) / synth.TAU))
+    recs = list(beat.run(synth.workload("beat_mini"), steps, maps=maps, record_every=40, precision="fp64",
+                         ksp_rtol=1e-12, ksp_atol=0.0, snes_rtol=1e-10, snes_atol=1e-16))
+    assert all(r["reason"] == 0 for r in recs)
+    summ = beat.activation_summary(maps)
+    assert summ["active_fraction"] == 1.0
+    assert abs(summ["all_active_ms"] - t_all) < 1e-9
