@@ -10,6 +10,13 @@ step), lit (Krylov iterations per Newton iteration) and the time per step.
 With ``record_every = k`` the state is read back every k steps, and each node's
 activation and recovery times are kept in ``maps``: the first sampled time v
 reaches ``threshold`` mV, and the first sampled time after that it is below it.
+With ``checkpoint`` (a path) and ``checkpoint_every = k`` the run saves, every k
+steps, the state (u_i, u_e, w, t), the step count and the maps to that .npz file
+(written to a temporary name, then renamed); ``resume`` (a path) continues from
+such a file.  The solver carries no other state from step to step with the
+options the runner allows for checkpointing (no learned guess, the
+preconditioner rebuilt at every Jacobian), so a resumed run repeats the
+uninterrupted one bit for bit.
 
     python -m paper_2101_02959_gb300.beat --workload beat_slab_half --steps 2400 \\
         --method bddc --precision mixed --out beat.jsonl
@@ -20,6 +27,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
 import time
 
 import numpy as np
@@ -59,21 +67,44 @@ def activation_summary(maps):
                 mean_ari_ms=float(np.mean(rec[done] - act[done])) if done.any() else float("nan"))
 
 
-def run(w, steps, seed=0, maps=None, record_every=0, threshold=50.0, **opt):
-    """Yield one record per time step of workload ``w`` (a synth workload dict).
+def save_checkpoint(path, s, step, maps):
+    """State, step count and maps of a run to ``path`` (.npz), replaced atomically."""
+    ui, ue, wg, t = s.get_state()
+    extra = {k: v for k, v in (maps or {}).items()}
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, ui=np.asarray(ui), ue=np.asarray(ue), w=np.asarray(wg), t=t, step=step, **extra)
+    os.replace(tmp, path)
+
+
+def run(w, steps, seed=0, maps=None, record_every=0, threshold=50.0, checkpoint=None, checkpoint_every=0,
+        resume=None, **opt):
+    """Yield one record per time step of workload ``w`` (a synth workload dict), for the
+    steps up to ``steps`` (a resumed run starts after its checkpoint's step).
 
     maps: a dict that receives "activation" and "recovery" (ms per node, NaN where the
     event was not seen) when record_every > 0."""
+    if (checkpoint or resume) and (opt.get("learned_guess") or opt.get("precond_every", 1) > 1):
+        raise ValueError("checkpoints hold the state only: no learned guess, precond_every = 1")
     s = binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, **opt)
     try:
-        ui, ue, wg = synth.initial_state(s.N, seed)
-        s.set_state(ui, ue, wg, 0.0)
-        stim = synth.stimulus(w)
         record = bool(record_every) and maps is not None
         if record:
             maps["activation"] = np.full(s.N, np.nan)
             maps["recovery"] = np.full(s.N, np.nan)
-        for n in range(steps):
+        start = 0
+        if resume:
+            z = np.load(resume)
+            s.set_state(z["ui"], z["ue"], z["w"], float(z["t"]))
+            start = int(z["step"])
+            if record:
+                for k in ("activation", "recovery"):
+                    if k in z:
+                        maps[k][:] = z[k]
+        else:
+            ui, ue, wg = synth.initial_state(s.N, seed)
+            s.set_state(ui, ue, wg, 0.0)
+        stim = synth.stimulus(w)
+        for n in range(start, steps):
             t0 = time.perf_counter()
             st = s.step(stim)
             ms = (time.perf_counter() - t0) * 1e3
@@ -84,6 +115,8 @@ def run(w, steps, seed=0, maps=None, record_every=0, threshold=50.0, **opt):
             if record and (n + 1) % record_every == 0:
                 gui, gue, _, t = s.get_state()
                 update_maps(maps, np.asarray(gui) - np.asarray(gue), t, threshold)
+            if checkpoint and checkpoint_every and (n + 1) % checkpoint_every == 0:
+                save_checkpoint(checkpoint, s, n + 1, maps if record else None)
     finally:
         s.close()
 
@@ -101,14 +134,19 @@ def main(argv=None):
     ap.add_argument("--out", default=None, help="JSONL file: one line per step, then the summary")
     ap.add_argument("--record-every", type=int, default=0,
                     help="read the state back every k steps for activation / recovery times (0: off)")
+    ap.add_argument("--checkpoint", default=None, help=".npz file the run saves its state to")
+    ap.add_argument("--checkpoint-every", type=int, default=0)
+    ap.add_argument("--resume", default=None, help=".npz checkpoint to continue from")
     a = ap.parse_args(argv)
     w = synth.workload(a.workload)
     steps = a.steps if a.steps is not None else w["steps"]
     build.build()
+    expected = steps - (int(np.load(a.resume)["step"]) if a.resume else 0)
     records, maps = [], {}
     out = open(a.out, "w") if a.out else None
     try:
-        for r in run(w, steps, maps=maps, record_every=a.record_every, method=a.method, krylov=a.krylov,
+        for r in run(w, steps, maps=maps, record_every=a.record_every, checkpoint=a.checkpoint,
+                     checkpoint_every=a.checkpoint_every, resume=a.resume, method=a.method, krylov=a.krylov,
                      precision=a.precision, scaling=a.scaling, precond_every=a.precond_every,
                      use_graphs=a.graphs):
             records.append(r)
@@ -124,7 +162,7 @@ def main(argv=None):
         if out:
             out.close()
     print(json.dumps(summary))
-    return 0 if summary["failed"] == 0 and summary["steps"] == steps else 1
+    return 0 if summary["failed"] == 0 and summary["steps"] == expected else 1
 
 
 if __name__ == "__main__":

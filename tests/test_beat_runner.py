@@ -93,3 +93,51 @@ def test_activation_and_recovery_maps(monkeypatch):
     assert np.isnan(summ["all_active_ms"]) == (not seen.all())
     assert abs(summ["active_fraction"] - seen.mean()) < 1e-15
     np.testing.assert_allclose(summ["mean_ari_ms"], np.mean((rec - act)[back]))
+
+
+class _StateSolver(_FakeSolver):
+    """Stand-in whose step is a deterministic function of the state alone."""
+
+    def set_state(self, ui, ue, w, t):
+        self.u = [np.array(ui, float), np.array(ue, float), np.array(w, float), float(t)]
+
+    def step(self, stim):
+        ui, ue, w, t = self.u
+        self.u = [np.sin(ui) + 0.5 * ue, np.cos(ue) * 0.9, w * 0.99 + 0.01 * ui, t + synth.TAU]
+        self.steps += 1
+        return dict(newton_its=2, krylov_its=20, reason=0)
+
+    def get_state(self):
+        ui, ue, w, t = self.u
+        return ui.copy(), ue.copy(), w.copy(), t
+
+
+def test_checkpoint_and_resume_repeat_the_run(monkeypatch, tmp_path):
+    monkeypatch.setattr(beat.binding, "Solver", _StateSolver)
+    w = synth.workload("tiny")
+    full_maps, part_maps = {}, {}
+    full = list(beat.run(w, 12, maps=full_maps, record_every=2))
+    ref = _StateSolver.instances[-1].get_state()
+    ck = str(tmp_path / "beat.npz")
+    first = list(beat.run(w, 12, maps=part_maps, record_every=2, checkpoint=ck, checkpoint_every=5))
+    z = np.load(ck)
+    assert int(z["step"]) == 10 and abs(float(z["t"]) - 10 * synth.TAU) < 1e-15
+    resumed_maps = {}
+    rest = list(beat.run(w, 12, maps=resumed_maps, record_every=2, resume=ck))
+    assert [r["step"] for r in rest] == [11, 12]
+    got = _StateSolver.instances[-1].get_state()
+    for a, b in zip(got[:3], ref[:3]):
+        np.testing.assert_array_equal(a, b)
+    assert got[3] == ref[3]
+    for k in ("activation", "recovery"):
+        np.testing.assert_array_equal(resumed_maps[k], full_maps[k])
+    assert len(full) == len(first) == 12
+
+
+def test_checkpoint_refuses_hidden_state():
+    import pytest
+    w = synth.workload("tiny")
+    with pytest.raises(ValueError):
+        list(beat.run(w, 2, checkpoint="x.npz", checkpoint_every=1, learned_guess=1))
+    with pytest.raises(ValueError):
+        list(beat.run(w, 2, resume="x.npz", precond_every=2))

@@ -100,3 +100,26 @@ def test_runner_activation_time_matches_the_oracle_beat():
     summ = beat.activation_summary(maps)
     assert summ["active_fraction"] == 1.0
     assert abs(summ["all_active_ms"] - t_all) < 1e-9
+
+
+def test_checkpoint_resume_is_bit_exact(tmp_path):
+    """A run checkpointed at step 5 and resumed in a new handle ends, after step 10, in
+    exactly the state of the uninterrupted run (the solver keeps no hidden state across
+    steps without the learned guess or a lagged preconditioner)."""
+    from paper_2101_02959_gb300 import beat, binding, build
+    build.build()
+    w = synth.workload("cube8ve")
+    opt = dict(precision="mixed", use_graphs=1)
+    list(beat.run(w, 10, checkpoint=str(tmp_path / "full.npz"), checkpoint_every=10, **opt))
+    list(beat.run(w, 10, checkpoint=str(tmp_path / "half.npz"), checkpoint_every=5, **opt))
+    half = np.load(tmp_path / "half.npz")
+    assert int(half["step"]) == 10
+    import shutil
+    list(beat.run(w, 5, checkpoint=str(tmp_path / "five.npz"), checkpoint_every=5, **opt))
+    shutil.copy(tmp_path / "five.npz", tmp_path / "resume.npz")
+    list(beat.run(w, 10, resume=str(tmp_path / "resume.npz"), checkpoint=str(tmp_path / "resumed.npz"),
+                  checkpoint_every=5, **opt))
+    full, resumed = np.load(tmp_path / "full.npz"), np.load(tmp_path / "resumed.npz")
+    for k in ("ui", "ue", "w"):
+        np.testing.assert_array_equal(resumed[k], full[k])
+    assert float(resumed["t"]) == float(full["t"]) and int(resumed["step"]) == 10
