@@ -130,6 +130,7 @@ def main(argv=None):
     ap.add_argument("--precision", default="mixed", choices=("fp64", "mixed"))
     ap.add_argument("--scaling", default="deluxe", choices=("deluxe", "rho"))
     ap.add_argument("--precond-every", type=int, default=1)
+    ap.add_argument("--primal", default=None, choices=("V", "VE", "VEF"), help="override the workload's primal space")
     ap.add_argument("--graphs", type=int, default=1)
     ap.add_argument("--out", default=None, help="JSONL file: one line per step, then the summary")
     ap.add_argument("--record-every", type=int, default=0,
@@ -139,6 +140,8 @@ def main(argv=None):
     ap.add_argument("--resume", default=None, help=".npz checkpoint to continue from")
     a = ap.parse_args(argv)
     w = synth.workload(a.workload)
+    if a.primal:
+        w["primal"] = a.primal
     steps = a.steps if a.steps is not None else w["steps"]
     build.build()
     expected = steps - (int(np.load(a.resume)["step"]) if a.resume else 0)
@@ -153,7 +156,7 @@ def main(argv=None):
             if out:
                 out.write(json.dumps(r) + "\n")
         summary = dict(summarize(records), workload=a.workload, method=a.method, precision=a.precision,
-                       scaling=a.scaling, precond_every=a.precond_every)
+                       scaling=a.scaling, primal=w["primal"], precond_every=a.precond_every)
         if maps:
             summary.update(activation_summary(maps))
         if out:
