@@ -3,8 +3,9 @@ through activation and recovery, with the per-step statistics the paper reports.
 
 ``run`` advances one solver handle for ``steps`` time steps from the seeded
 resting state and yields one record per step: the Newton iterations, the Krylov
-iterations summed over them, the status and the wall time of the step (each
-``bidomain_step`` call returns after its stream has synchronised).  ``summarize``
+iterations summed over them, the status, the initial and final nonlinear residual
+norms, the largest Lanczos condition estimate of the step and the wall time of
+the step (each ``bidomain_step`` call returns after its stream has synchronised).  ``summarize``
 turns the records into Table 11's columns: nlit (Newton iterations per time
 step), lit (Krylov iterations per Newton iteration) and the time per step.
 With ``record_every = k`` the state is read back every k steps, and each node's
@@ -38,14 +39,17 @@ from . import binding, build
 
 
 def summarize(records):
-    """Table 11's columns from per-step records."""
+    """Table 11's columns from per-step records, and the mean per-step condition
+    estimate (the cond column of Tables 7-8) where the solver reports one."""
     n = len(records)
     if n == 0:
         return dict(steps=0, nlit=0.0, lit=0.0, time_s=0.0, failed=0)
     newton = sum(r["newton_its"] for r in records)
     krylov = sum(r["krylov_its"] for r in records)
+    conds = [r["cond_max"] for r in records if r.get("cond_max")]
     return dict(steps=n, nlit=newton / n, lit=krylov / max(newton, 1),
                 time_s=sum(r["ms"] for r in records) / n / 1e3,
+                cond=sum(conds) / len(conds) if conds else None,
                 max_lit_step=max(r["krylov_its"] / max(r["newton_its"], 1) for r in records),
                 failed=sum(1 for r in records if r["reason"] != 0))
 
@@ -109,7 +113,8 @@ def run(w, steps, seed=0, maps=None, record_every=0, threshold=50.0, checkpoint=
             st = s.step(stim)
             ms = (time.perf_counter() - t0) * 1e3
             yield dict(step=n + 1, t=(n + 1) * synth.TAU, newton_its=st["newton_its"],
-                       krylov_its=st["krylov_its"], reason=st["reason"], ms=ms)
+                       krylov_its=st["krylov_its"], reason=st["reason"], ms=ms,
+                       res0=st.get("res0"), res_final=st.get("res_final"), cond_max=st.get("cond_max"))
             if st["reason"] != 0:
                 return
             if record and (n + 1) % record_every == 0:
