@@ -44,7 +44,8 @@ extern "C" {
 #define BD_ERR_KRYLOV_DIVERGED (-4)  /* ||M^-1 r|| > dtol ||M^-1 b|| */
 #define BD_ERR_NEWTON (-5)           /* Newton or its line search failed */
 #define BD_ERR_NAN (-6)              /* NaN / Inf met in a residual or a norm */
-#define BD_ERR_TIMEOUT (-7)          /* a device-side wait exhausted its budget */
+#define BD_ERR_TIMEOUT (-7)          /* a device-side wait exhausted its budget; the handle's device
+                                        work may still be running: destroy the handle */
 #define BD_ERR_CUDA (-8)             /* a CUDA runtime call failed */
 #define BD_ERR_NOMEM (-9)            /* device allocation failed */
 #define BD_ERR_STATE (-10)           /* call made in the wrong order (e.g. no Jacobian yet) */
@@ -235,7 +236,10 @@ int bidomain_setup(const bd_mesh *mesh, const bd_conductivity *cond, const bd_io
 int bidomain_sizes(const bd_handle *h, bd_sizes *out);
 int bidomain_index_sets(const bd_handle *h, int which, int64_t *out, int64_t cap, int64_t *len);
 
-/* State (u_i, u_e, w) at time t (ms); t sets the step counter n = round(t/tau). */
+/* State (u_i, u_e, w) at time t (ms); t sets the step counter n = round(t/tau).
+ * With the learned initial guess, the history of earlier states it reads is kept
+ * when n equals the handle's own step counter (the caller hands back the state of
+ * the current step, e.g. after a host round trip) and restarts otherwise. */
 int bidomain_set_state(bd_handle *h, const double *ui, const double *ue, const double *w,
                        double t, int on_device);
 int bidomain_get_state(bd_handle *h, double *ui, double *ue, double *w, double *t, int on_device);
@@ -318,6 +322,14 @@ int bidomain_mlp_params(bd_handle *h, float *w, int set);
  * inputs X (batch x n_in), targets T and mask (batch x n_out). */
 int bidomain_mlp_loss_grad(bd_handle *h, const float *X, const float *T, const float *mask, double *loss,
                            float *grad);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias correction; Kingma and Ba,
+ * Algorithm 1) of the packed parameters with the packed host gradient `grad` and
+ * learning rate lr: the update the online training applies after each backward pass. */
+int bidomain_mlp_adam_step(bd_handle *h, const float *grad, double lr);
+/* Back to the untrained network: the initial weights (the fixed seeded He-uniform
+ * draw of bidomain_setup), zero Adam moments and step count, no training steps
+ * counted, and no state history. */
+int bidomain_mlp_reset(bd_handle *h);
 
 /* ---- no-allocation variant ------------------------------------------------
  * The paper has no counterpart: this is a deployment variant of schur_apply.
@@ -328,7 +340,9 @@ int bidomain_mlp_loss_grad(bd_handle *h, const float *X, const float *T, const f
  * memory when they apply the operator: code running under a fixed device-
  * memory budget, or inside a host framework that owns every allocation.
  *   - x, y: device pointers to interface vectors (n_iface doubles).
- *   - The handle must have been linearised (BD_ERR_STATE otherwise).
+ *   - The handle must have been linearised (BD_ERR_STATE otherwise), and the
+ *     device current at the call must be the one the handle was set up on
+ *     (BD_ERR_STATE otherwise: the array's address differs from device to device).
  *   - Capacity: the sum over subdomains of their interface unknowns must not
  *     exceed 524288 doubles (4 MiB); larger problems get BD_ERR_SCRATCH.
  *     Every GPU that loads the library holds this 4 MiB until the process exits.
@@ -370,6 +384,11 @@ int64_t bidomain_launch_count(void);
 
 int bidomain_destroy(bd_handle *h);
 const char *bidomain_strerror(int status);
+/* The message of the last failure recorded on handle h (the failing CUDA call or
+ * argument check), or, with h == NULL, of the last failure on this thread before a
+ * handle existed (bd_plan_create, bidomain_setup).  Empty when there is none.  The
+ * pointer stays valid until the next call on the same handle or thread. */
+const char *bidomain_last_error(const bd_handle *h);
 
 #ifdef __cplusplus
 }

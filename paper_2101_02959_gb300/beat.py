@@ -12,9 +12,11 @@ With ``record_every = k`` the state is read back every k steps, and each node's
 activation and recovery times are kept in ``maps``: the first sampled time v
 reaches ``threshold`` mV, and the first sampled time after that it is below it.
 With ``checkpoint`` (a path) and ``checkpoint_every = k`` the run saves, every k
-steps, the state (u_i, u_e, w, t), the step count and the maps to that .npz file
-(written to a temporary name, then renamed); ``resume`` (a path) continues from
-such a file.  The solver carries no other state from step to step with the
+steps, the state (u_i, u_e, w, t), the step count, the maps and the run's
+description (workload, node count, solver options) to that .npz file (written to
+a temporary name, then renamed); ``resume`` (a path) continues from such a file
+and refuses one written by a different run.  A step that fails (Krylov or Newton
+limit, NaN) still yields its record, with the status, and ends the run.  The solver carries no other state from step to step with the
 options the runner allows for checkpointing (no learned guess, the
 preconditioner rebuilt at every Jacobian), so a resumed run repeats the
 uninterrupted one bit for bit.
@@ -71,13 +73,40 @@ def activation_summary(maps):
                 mean_ari_ms=float(np.mean(rec[done] - act[done])) if done.any() else float("nan"))
 
 
-def save_checkpoint(path, s, step, maps):
-    """State, step count and maps of a run to ``path`` (.npz), replaced atomically."""
+# solver options a checkpoint records; a resumed run must use the same ones
+CHECKPOINT_KEYS = ("method", "krylov", "precision", "scaling", "primal")
+
+
+def _run_meta(w, s, opt):
+    meta = {k: str(opt.get(k, "")) for k in CHECKPOINT_KEYS}
+    meta["primal"] = str(opt.get("primal", w.get("primal", "")))
+    meta.update(workload=str(w.get("name", "")), n_node=str(s.N))
+    return meta
+
+
+def save_checkpoint(path, s, step, maps, meta=None):
+    """State, step count, maps and the run's description (workload, node count, solver
+    options) to ``path`` (.npz), replaced atomically."""
     ui, ue, wg, t = s.get_state()
     extra = {k: v for k, v in (maps or {}).items()}
+    extra.update({"meta_" + k: np.array(v) for k, v in (meta or {}).items()})
     tmp = path + ".tmp.npz"
     np.savez(tmp, ui=np.asarray(ui), ue=np.asarray(ue), w=np.asarray(wg), t=t, step=step, **extra)
     os.replace(tmp, path)
+
+
+def check_resume(z, meta, record):
+    """Refuse a checkpoint written by a different run: another workload, node count or
+    solver options, or one without activation maps when this run records them."""
+    for k, v in meta.items():
+        key = "meta_" + k
+        if key not in z.files:
+            raise ValueError(f"checkpoint has no {k!r}: written by an older runner, cannot verify it")
+        if str(z[key]) != v:
+            raise ValueError(f"checkpoint {k} = {str(z[key])!r}, this run {k} = {v!r}")
+    if record and not all(k in z.files for k in ("activation", "recovery")):
+        raise ValueError("checkpoint holds no activation / recovery maps but this run records them: "
+                         "resume with record_every = 0 or restart the run")
 
 
 def run(w, steps, seed=0, maps=None, record_every=0, threshold=50.0, checkpoint=None, checkpoint_every=0,
@@ -92,28 +121,32 @@ def run(w, steps, seed=0, maps=None, record_every=0, threshold=50.0, checkpoint=
     s = binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, **opt)
     try:
         record = bool(record_every) and maps is not None
+        meta = _run_meta(w, s, opt)
         if record:
             maps["activation"] = np.full(s.N, np.nan)
             maps["recovery"] = np.full(s.N, np.nan)
         start = 0
         if resume:
             z = np.load(resume)
+            check_resume(z, meta, record)
             s.set_state(z["ui"], z["ue"], z["w"], float(z["t"]))
             start = int(z["step"])
             if record:
                 for k in ("activation", "recovery"):
-                    if k in z:
-                        maps[k][:] = z[k]
+                    maps[k][:] = z[k]
         else:
             ui, ue, wg = synth.initial_state(s.N, seed)
             s.set_state(ui, ue, wg, 0.0)
         stim = synth.stimulus(w)
         for n in range(start, steps):
             t0 = time.perf_counter()
-            st = s.step(stim)
+            try:
+                st = s.step(stim)
+            except binding.BidomainError as e:  # a failed step: its record ends the run
+                st = dict(e.stats or {}, reason=e.code)
             ms = (time.perf_counter() - t0) * 1e3
-            yield dict(step=n + 1, t=(n + 1) * synth.TAU, newton_its=st["newton_its"],
-                       krylov_its=st["krylov_its"], reason=st["reason"], ms=ms,
+            yield dict(step=n + 1, t=(n + 1) * synth.TAU, newton_its=st.get("newton_its", 0),
+                       krylov_its=st.get("krylov_its", 0), reason=st["reason"], ms=ms,
                        res0=st.get("res0"), res_final=st.get("res_final"), cond_max=st.get("cond_max"))
             if st["reason"] != 0:
                 return
@@ -121,7 +154,7 @@ def run(w, steps, seed=0, maps=None, record_every=0, threshold=50.0, checkpoint=
                 gui, gue, _, t = s.get_state()
                 update_maps(maps, np.asarray(gui) - np.asarray(gue), t, threshold)
             if checkpoint and checkpoint_every and (n + 1) % checkpoint_every == 0:
-                save_checkpoint(checkpoint, s, n + 1, maps if record else None)
+                save_checkpoint(checkpoint, s, n + 1, maps if record else None, meta)
     finally:
         s.close()
 

@@ -34,8 +34,9 @@ EXPORTED = ["bd_plan_create", "bd_plan_sizes", "bd_plan_index_sets", "bd_plan_de
             "bidomain_get_state", "bidomain_step", "bidomain_gating", "bidomain_residual", "bidomain_linearize",
             "schur_apply", "bddc_apply", "fetidp_apply", "fetidp_operator", "krylov_solve", "bidomain_profile",
             "bidomain_profile_read", "bidomain_launch_count", "schur_apply_noalloc", "bidomain_mlp_sizes",
-            "bidomain_mlp_params", "bidomain_mlp_loss_grad", "bidomain_autotune", "bidomain_destroy",
-            "bidomain_strerror"]
+            "bidomain_mlp_params", "bidomain_mlp_loss_grad", "bidomain_mlp_adam_step",
+            "bidomain_mlp_reset", "bidomain_autotune", "bidomain_destroy",
+            "bidomain_strerror", "bidomain_last_error"]
 PROF = dict(rankk=0, panel=1, gemv=2, resid=3)                    # kernel classes
 REGIONS = dict(linearize=4, krylov=5, trsv=6, mlp=7, step=8)      # regions of a step
 
@@ -131,9 +132,12 @@ def load(build_if_missing: bool = False):
         "bidomain_mlp_sizes": (I, [P, C.POINTER(I), C.POINTER(I), C.POINTER(I), C.POINTER(I)]),
         "bidomain_mlp_params": (I, [P, P, I]),
         "bidomain_mlp_loss_grad": (I, [P, P, P, P, C.POINTER(D), P]),
+        "bidomain_mlp_adam_step": (I, [P, P, D]),
+        "bidomain_mlp_reset": (I, [P]),
         "bidomain_autotune": (I, [P, C.POINTER(BdTuneResult)]),
         "bidomain_destroy": (I, [P]),
         "bidomain_strerror": (C.c_char_p, [I]),
+        "bidomain_last_error": (C.c_char_p, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -148,15 +152,24 @@ def launch_count():
 
 
 class BidomainError(RuntimeError):
-    def __init__(self, code, where):
+    """A non-zero status of the C-ABI; ``stats`` holds the call's statistics when it
+    returns any (bidomain_step reports the failed step's Newton and Krylov counts)."""
+
+    def __init__(self, code, where, handle=None, stats=None):
         self.code = code
-        msg = load().bidomain_strerror(code).decode()
-        super().__init__(f"{where}: {ERRORS.get(code, code)} ({msg})")
+        self.stats = stats
+        try:
+            lib = load()
+            msg = lib.bidomain_strerror(code).decode()
+            detail = lib.bidomain_last_error(handle).decode()
+        except (OSError, RuntimeError):  # library not built: the code alone
+            msg, detail = "", ""
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({msg})" + (f": {detail}" if detail else ""))
 
 
-def _check(code, where):
+def _check(code, where, handle=None):
     if code != BD_OK:
-        raise BidomainError(code, where)
+        raise BidomainError(code, where, handle)
 
 
 def _mesh(w, mask=None):
@@ -265,12 +278,15 @@ class Solver:
         ion = BdIonic(*[ionic[k] for k in ("G", "eta1", "eta2", "vth", "vp", "chi_cm")])
         self._h = C.c_void_p()
         st = None if stream is None else C.c_void_p(stream)
-        _check(lib.bidomain_setup(C.byref(_mesh(w)), C.byref(cond), C.byref(ion), float(tau), C.byref(self.opts),
+        self._check(lib.bidomain_setup(C.byref(_mesh(w)), C.byref(cond), C.byref(ion), float(tau), C.byref(self.opts),
                                   st, C.byref(self._h)), "bidomain_setup")
         s = BdSizes()
-        _check(lib.bidomain_sizes(self._h, C.byref(s)), "bidomain_sizes")
+        self._check(lib.bidomain_sizes(self._h, C.byref(s)), "bidomain_sizes")
         self.sizes = {k: getattr(s, k) for k, _ in BdSizes._fields_}
         self.N = self.sizes["n_node"]
+
+    def _check(self, code, where):
+        _check(code, where, getattr(self, "_h", None))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -285,14 +301,14 @@ class Solver:
 
     def set_state(self, ui, ue, w, t=0.0):
         (a, d), (b, _), (c, _) = _ptr(ui, self.N), _ptr(ue, self.N), _ptr(w, self.N)
-        _check(self._lib.bidomain_set_state(self._h, a, b, c, float(t), d), "bidomain_set_state")
+        self._check(self._lib.bidomain_set_state(self._h, a, b, c, float(t), d), "bidomain_set_state")
 
     def get_state(self, like=None):
         like = np.zeros(1) if like is None else like
         ui, ue, w = (_same_kind(like, self.N) for _ in range(3))
         t = C.c_double()
         d = _ptr(ui)[1]
-        _check(self._lib.bidomain_get_state(self._h, _ptr(ui)[0], _ptr(ue)[0], _ptr(w)[0], C.byref(t), d),
+        self._check(self._lib.bidomain_get_state(self._h, _ptr(ui)[0], _ptr(ue)[0], _ptr(w)[0], C.byref(t), d),
                "bidomain_get_state")
         return ui, ue, w, t.value
 
@@ -301,31 +317,32 @@ class Solver:
         s = _stim(stim)
         code = self._lib.bidomain_step(self._h, None if s is None else C.byref(s), C.byref(st))
         out = {k: getattr(st, k) for k, _ in BdStepStats._fields_ if not k.startswith("pad")}
-        _check(code, "bidomain_step")
+        if code != BD_OK:
+            raise BidomainError(code, "bidomain_step", self._h, stats=out)
         return out
 
     def gating(self, ui, ue, w):
         out = _same_kind(ui, self.N)
         (a, d), (b, _), (c, _), (o, _) = _ptr(ui, self.N), _ptr(ue, self.N), _ptr(w, self.N), _ptr(out, self.N)
-        _check(self._lib.bidomain_gating(self._h, a, b, c, o, d), "bidomain_gating")
+        self._check(self._lib.bidomain_gating(self._h, a, b, c, o, d), "bidomain_gating")
         return out
 
     def residual(self, stim, t_next, ui, ue, w_next, ui_n, ue_n):
         out = _same_kind(ui, 2 * self.N)
         ps = [_ptr(x, self.N) for x in (ui, ue, w_next, ui_n, ue_n)]
         s = _stim(stim)
-        _check(self._lib.bidomain_residual(self._h, None if s is None else C.byref(s), float(t_next),
+        self._check(self._lib.bidomain_residual(self._h, None if s is None else C.byref(s), float(t_next),
                                            *[p for p, _ in ps], _ptr(out)[0], ps[0][1]), "bidomain_residual")
         return out
 
     def linearize(self, ui, ue, w_next):
         (a, d), (b, _), (c, _) = _ptr(ui, self.N), _ptr(ue, self.N), _ptr(w_next, self.N)
-        _check(self._lib.bidomain_linearize(self._h, a, b, c, d), "bidomain_linearize")
+        self._check(self._lib.bidomain_linearize(self._h, a, b, c, d), "bidomain_linearize")
 
     def _apply(self, fn, x, n, name):
         out = _same_kind(x, n)
         p, d = _ptr(x, n)
-        _check(fn(self._h, p, _ptr(out)[0], d), name)
+        self._check(fn(self._h, p, _ptr(out)[0], d), name)
         return out
 
     def schur_apply(self, x):
@@ -343,35 +360,35 @@ class Solver:
     def profile(self, enable=True):
         """True / 1: kernel classes and regions; 2: regions only; False / 0: off."""
         mode = 2 if enable == 2 else (1 if enable else 0)
-        _check(self._lib.bidomain_profile(self._h, mode), "bidomain_profile")
+        self._check(self._lib.bidomain_profile(self._h, mode), "bidomain_profile")
 
     def profile_read(self, which):
         out = (C.c_double * 4)()
         idx = PROF[which] if which in PROF else REGIONS[which]
-        _check(self._lib.bidomain_profile_read(self._h, idx, out), "bidomain_profile_read")
+        self._check(self._lib.bidomain_profile_read(self._h, idx, out), "bidomain_profile_read")
         return dict(launches=int(out[0]), ms=out[1], flops=out[2], bytes=out[3])
 
     def autotune(self):
         r = BdTuneResult()
-        _check(self._lib.bidomain_autotune(self._h, C.byref(r)), "bidomain_autotune")
+        self._check(self._lib.bidomain_autotune(self._h, C.byref(r)), "bidomain_autotune")
         return {k: getattr(r, k) for k, _ in BdTuneResult._fields_}
 
     def mlp_sizes(self):
         v = [C.c_int() for _ in range(4)]
-        _check(self._lib.bidomain_mlp_sizes(self._h, *[C.byref(x) for x in v]), "bidomain_mlp_sizes")
+        self._check(self._lib.bidomain_mlp_sizes(self._h, *[C.byref(x) for x in v]), "bidomain_mlp_sizes")
         return dict(zip(("n_in", "n_hidden", "n_out", "batch"), (x.value for x in v)))
 
     def mlp_params(self, w=None):
         """Packed float32 parameters: upload `w` when given, else download."""
         if w is not None:
             w = np.ascontiguousarray(w, dtype=np.float32)
-            _check(self._lib.bidomain_mlp_params(self._h, w.ctypes.data, 1), "bidomain_mlp_params")
+            self._check(self._lib.bidomain_mlp_params(self._h, w.ctypes.data, 1), "bidomain_mlp_params")
             return w
         sz = self.mlp_sizes()
         n = sz["n_hidden"] * (sz["n_in"] + 1) + sz["n_hidden"] * (sz["n_hidden"] + 1) + \
             sz["n_out"] * (sz["n_hidden"] + 1)
         out = np.zeros(n, np.float32)
-        _check(self._lib.bidomain_mlp_params(self._h, out.ctypes.data, 0), "bidomain_mlp_params")
+        self._check(self._lib.bidomain_mlp_params(self._h, out.ctypes.data, 0), "bidomain_mlp_params")
         return out
 
     def mlp_loss_grad(self, X, T, mask):
@@ -379,9 +396,18 @@ class Solver:
         w = self.mlp_params()
         g = np.zeros_like(w)
         loss = C.c_double()
-        _check(self._lib.bidomain_mlp_loss_grad(self._h, X.ctypes.data, T.ctypes.data, mask.ctypes.data,
+        self._check(self._lib.bidomain_mlp_loss_grad(self._h, X.ctypes.data, T.ctypes.data, mask.ctypes.data,
                                                 C.byref(loss), g.ctypes.data), "bidomain_mlp_loss_grad")
         return loss.value, g
+
+    def mlp_adam_step(self, grad, lr):
+        """One Adam step of the packed parameters with the packed gradient ``grad``."""
+        g = np.ascontiguousarray(grad, dtype=np.float32)
+        self._check(self._lib.bidomain_mlp_adam_step(self._h, g.ctypes.data, float(lr)), "bidomain_mlp_adam_step")
+
+    def mlp_reset(self):
+        """Back to the untrained network (initial weights, zero Adam state, no history)."""
+        self._check(self._lib.bidomain_mlp_reset(self._h), "bidomain_mlp_reset")
 
     def krylov_solve(self, f):
         out = _same_kind(f, 2 * self.N)
@@ -389,5 +415,5 @@ class Solver:
         p, d = _ptr(f, 2 * self.N)
         code = self._lib.krylov_solve(self._h, p, _ptr(out)[0], d, C.byref(st))
         stats = {k: getattr(st, k) for k, _ in BdSolveStats._fields_}
-        _check(code, "krylov_solve")
+        self._check(code, "krylov_solve")
         return out, stats

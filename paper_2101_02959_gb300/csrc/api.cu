@@ -191,6 +191,7 @@ struct bd_handle {
   double tau = 0.0;
   cudaStream_t s = nullptr;
   bool own_stream = false;
+  int device = -1;  // the device current at bidomain_setup: every buffer of the handle lives there
   long step_n = 0;
   DevMem mem;
   int N = 0, NE = 0, nsub = 0, nif = 0, nd = 0, np = 0, nlam = 0;
@@ -227,8 +228,13 @@ struct bd_handle {
   long long K_el = 0, A_el = 0, So_el = 0, Z_el = 0, SDD_el = 0, Blk_el = 0, CA_el = 0, Sinv_el = 0, Dd_el = 0;
   int K_blk = 0, A_blk = 0, C_blk = 0;  // slots of the diagonal-block stores
   int ld_co = 0;
-  double *d_Co64 = nullptr, *d_CoInv64 = nullptr, *d_CoW = nullptr, *d_CoY = nullptr;  // FP64 coarse
-  GemvSet gv_schur, gv_local, gv_psit, gv_coarse, gv_sdd, gv_lgi, gv_lgit, gv_drest, gv_dext;
+  // coarse problem: S_PP as FP64 CSR (entries sum the listed local values), solve scratch
+  int co_nnz = 0;
+  int *d_co_rptr = nullptr, *d_co_row = nullptr, *d_co_col = nullptr, *d_co_sptr = nullptr;
+  long long *d_co_src = nullptr;
+  double *d_Co64 = nullptr, *d_co_c = nullptr, *d_co_rho = nullptr;
+  CoarseSolve cs;
+  GemvSet gv_schur, gv_local, gv_psit, gv_coarse, gv_coarse_acc, gv_sdd, gv_lgi, gv_lgit, gv_drest, gv_dext;
   GemmTask *d_gemm = nullptr;
   int n_gemm = 0;
   int *d_ext_idx = nullptr;
@@ -240,8 +246,6 @@ struct bd_handle {
   LamTask *d_lt;
   WTask *d_wt;
   WEnt *d_went;
-  int *d_co_ptr;
-  long long *d_co_src;
   // work vectors
   double *d_fI, *d_yI, *d_fG, *d_fhat, *d_uG, *d_yloc, *d_rbar, *d_zbar, *d_rD, *d_ydc, *d_w1, *d_w2, *d_gP,
       *d_crhs, *d_rP, *d_rD2;
@@ -290,6 +294,38 @@ namespace {
 // ---------------------------------------------------------------------------
 // learned initial guess: buffers, deterministic He-uniform initialisation
 // ---------------------------------------------------------------------------
+// The untrained network: He-uniform weights from a fixed splitmix64 stream, zero
+// biases, last layer scaled by 0.1; Adam moments and counters at zero.
+void mlp_init_weights(bd_handle &h) {
+  MlpDev &M = h.mlp;
+  cudaStream_t s = h.s;
+  const int H = M.n_hidden;
+  std::vector<float> w(M.n_params, 0.f);
+  uint64_t st = 0x9E3779B97F4A7C15ULL;
+  auto uni = [&]() {
+    st += 0x9E3779B97F4A7C15ULL;
+    uint64_t z = st;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+  };
+  auto fill = [&](long long off, long long n, int fan_in, double scale) {
+    const double lim = std::sqrt(6.0 / fan_in) * scale;
+    for (long long i = 0; i < n; ++i) w[off + i] = (float)((2.0 * uni() - 1.0) * lim);
+  };
+  fill(M.off_W1, (long long)H * M.n_in, M.n_in, 1.0);
+  fill(M.off_W2, (long long)H * H, H, 1.0);
+  fill(M.off_W3, (long long)M.n_out * H, H, 0.1);
+  ck(cudaMemcpyAsync(M.w, w.data(), sizeof(float) * M.n_params, cudaMemcpyHostToDevice, s), "mlp init");
+  mlp_refresh_bf16(M, s);
+  ck(cudaMemsetAsync(M.am, 0, sizeof(float) * M.n_params, s), "memset");
+  ck(cudaMemsetAsync(M.av, 0, sizeof(float) * M.n_params, s), "memset");
+  M.t = 0;
+  h.mlp_steps_trained = 0;
+  h.hist_count = 0;
+}
+
 void setup_mlp(bd_handle &h) {
   DevMem &m = h.mem;
   cudaStream_t s = h.s;
@@ -332,26 +368,7 @@ void setup_mlp(bd_handle &h) {
   M.dZ1 = m.alloc<float>((size_t)B * H);
   M.dZ2 = m.alloc<float>((size_t)B * H);
   ck(cudaMemsetAsync(M.X, 0, sizeof(float) * B * M.n_in, s), "memset");
-  // He-uniform weights from a fixed splitmix64 stream, zero biases, last layer scaled by 0.1
-  std::vector<float> w(M.n_params, 0.f);
-  uint64_t st = 0x9E3779B97F4A7C15ULL;
-  auto uni = [&]() {
-    st += 0x9E3779B97F4A7C15ULL;
-    uint64_t z = st;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
-    z ^= z >> 31;
-    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
-  };
-  auto fill = [&](long long off, long long n, int fan_in, double scale) {
-    const double lim = std::sqrt(6.0 / fan_in) * scale;
-    for (long long i = 0; i < n; ++i) w[off + i] = (float)((2.0 * uni() - 1.0) * lim);
-  };
-  fill(M.off_W1, (long long)H * M.n_in, M.n_in, 1.0);
-  fill(M.off_W2, (long long)H * H, H, 1.0);
-  fill(M.off_W3, (long long)M.n_out * H, H, 0.1);
-  ck(cudaMemcpyAsync(M.w, w.data(), sizeof(float) * M.n_params, cudaMemcpyHostToDevice, s), "mlp init");
-  mlp_refresh_bf16(M, s);
+  mlp_init_weights(h);
   // node -> (subdomain, local node) entries for the prediction average
   std::vector<std::vector<int>> lists(h.N);
   for (int j = 0; j < h.nsub; ++j) {
@@ -699,26 +716,38 @@ void setup_handle(bd_handle &h) {
     MatDesc co{0, h.ld_co, 2 * np, np, 0};
     h.d_Codesc = m.upload(std::vector<MatDesc>{co}, s);
     h.shCo = EngineShape{1, np, 2 * np, {2 * np}, {np}};
-    std::vector<std::vector<long long>> lists((size_t)np * np);
+    // sparse pattern of S_PP: the (p, q) pairs that some subdomain couples, with the
+    // offsets of their local contributions in the augmented matrices (subdomain order)
+    std::map<std::pair<int, int>, std::vector<long long>> ent;
     for (int j = 0; j < S; ++j) {
       const SubPlan &sp = p.subs[j];
       const int nd = h.nD[j];
       for (int a = 0; a < h.nP[j]; ++a)
         for (int b = 0; b < h.nP[j]; ++b) {
           const int hi = std::max(a, b), lo = std::min(a, b);
-          lists[(size_t)sp.primal[a] * np + sp.primal[b]].push_back(ad[j].off + (long long)(nd + hi) * ad[j].ld + nd + lo);
+          ent[{sp.primal[a], sp.primal[b]}].push_back(ad[j].off + (long long)(nd + hi) * ad[j].ld + nd + lo);
         }
     }
-    std::vector<int> ptr(1, 0);
+    for (int q = 0; q < np; ++q) ent[{q, q}];  // every diagonal entry is stored (the gauge's is pinned)
+    std::vector<int> rptr(np + 1, 0), row, col, sptr(1, 0);
     std::vector<long long> src;
-    for (auto &l : lists) { for (long long v : l) src.push_back(v); ptr.push_back((int)src.size()); }
-    h.d_co_ptr = m.upload(ptr, s);
-    h.d_Co64 = m.alloc<double>((size_t)np * np);
-    h.d_CoInv64 = m.alloc<double>((size_t)np * np);
-    h.d_CoW = m.alloc<double>((size_t)np * np);
-    h.d_CoY = m.alloc<double>((size_t)np * np);
+    for (auto &kv : ent) {  // std::map order = row-major, columns ascending
+      row.push_back(kv.first.first);
+      col.push_back(kv.first.second);
+      rptr[kv.first.first + 1] += 1;
+      for (long long v : kv.second) src.push_back(v);
+      sptr.push_back((int)src.size());
+    }
+    for (int q = 0; q < np; ++q) rptr[q + 1] += rptr[q];
+    h.co_nnz = (int)row.size();
+    h.d_co_rptr = m.upload(rptr, s);
+    h.d_co_row = m.upload(row, s);
+    h.d_co_col = m.upload(col, s);
+    h.d_co_sptr = m.upload(sptr, s);
     h.d_co_src = m.upload(src, s);
-
+    h.d_Co64 = m.alloc<double>(h.co_nnz);
+    h.d_co_c = m.alloc<double>(np);
+    h.d_co_rho = m.alloc<double>(np);
   }
   // ---- GEMV and copy task sets
   auto gset = [&](const std::vector<GemvDesc> &v) {
@@ -772,7 +801,23 @@ void setup_handle(bd_handle &h) {
   h.gv_sdd = gset(g_sdd);
   h.gv_lgi = gset(g_lgi);
   h.gv_lgit = gset(g_lgit);
-  h.gv_coarse = gset({GemvDesc{0, h.np, h.np, h.np, 0, h.nd, 0}});
+  h.gv_coarse = gset({GemvDesc{0, h.np, h.np, h.np, 0, 0, 0}});
+  h.gv_coarse_acc = gset({GemvDesc{0, h.np, h.np, h.np, 0, 0, 2}});
+  {
+    CoarseSolve &c = h.cs;
+    c.np = h.np;
+    c.gauge = h.gauge_primal;
+    // refinement steps: one restores FP64 backward stability of the FP64 explicit
+    // inverse; from an FP32 inverse each step gains about -log10(u32 cond(S_PP)) digits
+    c.nref = h.mixed() ? 3 : 1;
+    c.pl_ptr = h.d_pl_ptr;
+    c.pl_idx = h.d_pl_idx;
+    c.sptr = h.d_co_rptr;
+    c.scol = h.d_co_col;
+    c.sval = h.d_Co64;
+    c.gv = h.gv_coarse.d;
+    c.gv_acc = h.gv_coarse_acc.d;
+  }
   h.cp_sorig = cset(c_sorig);
   h.cp_sdd = cset(c_sdd);
   h.cp_zx = cset(c_zx);
@@ -790,7 +835,6 @@ void setup_handle(bd_handle &h) {
     for (const GemvSet *g : {&h.gv_schur, &h.gv_local, &h.gv_psit, &h.gv_coarse, &h.gv_sdd, &h.gv_lgi, &h.gv_lgit,
                              &h.gv_drest, &h.gv_dext})
       need = std::max(need, el * (size_t)std::max(g->max_rows, g->max_cols));
-    need = std::max(need, sizeof(double) * (size_t)h.np + el * h.gv_psit.max_rows);  // fused coarse solve
     if (need > dense_smem_limit())
       throw Status(BD_ERR_ARG, "local problem too large for the shared-memory staging of the dense kernels (" +
                                    std::to_string(need) + " bytes); use more subdomains");
@@ -902,11 +946,13 @@ void linearize_t(bd_handle &h, Dense<T> &D, bool precond) {
     launch_rho_blocks<T>(h.ncls, h.d_cls, h.d_pairs, si, se, D.Sinv, D.Blk, s);
   }
   launch_small_gemm<T>(h.n_gemm, h.max_nc, h.d_gemm, D.Sinv, D.Blk, D.Dd, s);
-  // coarse: S_PiPi assembled in FP64, factored in the local precision, inverse refined to FP64
-  launch_coarse_aug<T>(h.np, h.gauge_primal, h.d_co_ptr, h.d_co_src, D.Aug, D.Co, h.ld_co, s, h.d_Co64);
+  // coarse: S_PiPi assembled in FP64 (sparse) and, in the local precision, into the augmented
+  // matrix whose partial Cholesky leaves the explicit inverse; the solve refines against FP64
+  ck(cudaMemsetAsync(D.Co, 0, sizeof(T) * (size_t)h.ld_co * 2 * h.np, s), "memset coarse");
+  launch_coarse_assemble<T>(h.co_nnz, h.np, h.gauge_primal, h.d_co_row, h.d_co_col, h.d_co_sptr, h.d_co_src, D.Aug,
+                            h.d_Co64, D.Co, h.ld_co, s);
   engine_partial_cholesky<T>(h.shCo, h.d_Codesc, D.Co, h.d_err, s, D.LdCo);
   launch_copy<T, T>(h.cp_coinv.n, h.cp_coinv.max_elems, h.cp_coinv.d, D.Co, D.CoInv, s);
-  coarse_refine64<T>(h.np, D.CoInv, h.d_Co64, h.d_CoInv64, h.d_CoW, h.d_CoY, s);
 }
 
 // counted = true for the Jacobian evaluations of the solve (Newton, bidomain_linearize):
@@ -945,9 +991,11 @@ void st_inv_t(bd_handle &h, Dense<T> &D, const double *rP, const double *rD, con
   launch_gemv<T>(h.gv_local.n, h.gv_local.max_rows, h.gv_local.max_cols, h.gv_local.d, D.Z, rD, nullptr, h.d_ydc,
                  1.0, done, h.s);
   h.prof.end(PROF_GEMV, h.s, h.gemv_local_flops, h.gemv_local_bytes * sizeof(T));
-  launch_coarse_psit<T>(h.gv_psit.n, h.gv_psit.max_rows, h.gv_psit.max_cols, h.gv_psit.d, D.Z, h.d_CoInv64, h.np,
-                        h.gauge_primal, h.d_pl_ptr, h.d_pl_idx, h.d_ydc + h.nD_tot, rP_csr ? nullptr : rP, rP_csr,
-                        h.d_prim_x, h.nd, h.d_zbar, h.d_ydc, done, h.s);
+  // z_Pi = S_PiPi^-1 (rP - sum_j Psi^T r_D) into zbar[nd:], then ydc_Delta -= Psi z_Pi
+  launch_coarse_solve<T>(h.cs, D.CoInv, h.d_ydc + h.nD_tot, rP_csr ? nullptr : rP, rP_csr, h.d_zbar + h.nd,
+                         h.d_co_c, h.d_co_rho, done, h.s);
+  launch_gemv_t<T>(h.gv_psit.n, h.gv_psit.max_rows, h.gv_psit.max_cols, h.gv_psit.d, D.Z, h.d_zbar, h.d_prim_x,
+                   h.d_ydc, -1.0, done, h.s);
 }
 
 // rbar = T^T r is never stored: the deluxe restriction evaluates its dual rows while
@@ -1406,13 +1454,11 @@ static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratch];
 
 namespace {
 
-// Device address of the scratch array, looked up once per device with that
-// device current (the host-side symbol is only a stand-in, not an address).
-int noalloc_scratch(double **out) {
+// Device address of the scratch array on device `dev`, looked up once per device
+// with that device current (the host-side symbol is only a stand-in, not an address).
+int noalloc_scratch(int dev, double **out) {
   static std::mutex mu;
   static std::map<int, double *> addr;
-  int dev = -1;
-  if (cudaGetDevice(&dev) != cudaSuccess) return BD_ERR_CUDA;
   std::lock_guard<std::mutex> lock(mu);
   auto it = addr.find(dev);
   if (it == addr.end()) {
@@ -1435,15 +1481,28 @@ void schur_noalloc_t(bd_handle &h, Dense<T> &D, const double *x, double *y, doub
 
 extern "C" int schur_apply_noalloc(bd_handle *h, const double *x, double *y) {
   if (!h || !x || !y) return BD_ERR_ARG;
-  if (!h->linearized) return BD_ERR_STATE;
-  if ((long long)h->nG_tot > kNoAllocScratch) return BD_ERR_SCRATCH;
+  auto fail = [&](int code, const std::string &msg) {
+    h->last_error = "schur_apply_noalloc: " + msg;
+    return code;
+  };
+  if (!h->linearized) return fail(BD_ERR_STATE, "no Jacobian yet (call bidomain_linearize or bidomain_step)");
+  if ((long long)h->nG_tot > kNoAllocScratch)
+    return fail(BD_ERR_SCRATCH, std::to_string(h->nG_tot) + " interface unknowns over the subdomains exceed " +
+                                    std::to_string(kNoAllocScratch));
+  // the scratch address is per device: it must be the handle's, which must be current
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(BD_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev != h->device)
+    return fail(BD_ERR_STATE, "device " + std::to_string(dev) + " is current, the handle lives on device " +
+                                  std::to_string(h->device));
   double *scratch = nullptr;
-  int st = noalloc_scratch(&scratch);
-  if (st != BD_OK) return st;
+  if (noalloc_scratch(dev, &scratch) != BD_OK) return fail(BD_ERR_CUDA, "cudaGetSymbolAddress failed");
   if (h->mixed()) schur_noalloc_t(*h, h->df, x, y, scratch);
   else schur_noalloc_t(*h, h->dd, x, y, scratch);
-  if (cudaGetLastError() != cudaSuccess) return BD_ERR_CUDA;
-  if (cudaStreamSynchronize(h->s) != cudaSuccess) return BD_ERR_CUDA;
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->s);
+  if (e != cudaSuccess) return fail(BD_ERR_CUDA, cudaGetErrorString(e));
   return BD_OK;
 }
 
@@ -1579,6 +1638,7 @@ int bidomain_setup(const bd_mesh *mesh, const bd_conductivity *cond, const bd_io
     for (int d = 0; d < 3; ++d) { h->fp.sigma_i[d] = cond->sigma_i[d]; h->fp.sigma_e[d] = cond->sigma_e[d]; }
     h->fp.G = ionic->G; h->fp.eta1 = ionic->eta1; h->fp.eta2 = ionic->eta2; h->fp.vth = ionic->vth;
     h->fp.vp = ionic->vp; h->fp.chi_cm = ionic->chi_cm; h->fp.tau = tau;
+    ck(cudaGetDevice(&h->device), "cudaGetDevice");
     if (stream) h->s = (cudaStream_t)stream;
     else { ck(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking), "stream"); h->own_stream = true; }
     if (h->opt.use_tensor_cores && h->opt.precision == BD_MIXED && !tc_configure()) {
@@ -1615,8 +1675,9 @@ int bidomain_set_state(bd_handle *h, const double *ui, const double *ue, const d
     ck(cudaMemcpyAsync(h->d_uen, ue, n * sizeof(double), k, h->s), "state");
     ck(cudaMemcpyAsync(h->d_w, w, n * sizeof(double), k, h->s), "state");
     ck(cudaStreamSynchronize(h->s), "sync");
-    h->step_n = std::lround(t / h->tau);
-    h->hist_count = 0;
+    const long step = std::lround(t / h->tau);
+    if (step != h->step_n) h->hist_count = 0;  // the learned guess's history belongs to another time
+    h->step_n = step;
     return BD_OK;
   });
 }
@@ -1796,6 +1857,28 @@ int bidomain_mlp_loss_grad(bd_handle *h, const float *X, const float *T, const f
   });
 }
 
+int bidomain_mlp_adam_step(bd_handle *h, const float *grad, double lr) {
+  if (!h || !grad) return BD_ERR_ARG;
+  if (!h->mlp_on) return BD_ERR_STATE;
+  return guard(h, [&] {
+    MlpDev &M = h->mlp;
+    ck(cudaMemcpyAsync(M.g, grad, sizeof(float) * M.n_params, cudaMemcpyHostToDevice, h->s), "mlp grad");
+    mlp_adam(M, (float)lr, h->s);
+    ck(cudaStreamSynchronize(h->s), "sync");
+    return BD_OK;
+  });
+}
+
+int bidomain_mlp_reset(bd_handle *h) {
+  if (!h) return BD_ERR_ARG;
+  if (!h->mlp_on) return BD_ERR_STATE;
+  return guard(h, [&] {
+    mlp_init_weights(*h);
+    ck(cudaStreamSynchronize(h->s), "sync");
+    return BD_OK;
+  });
+}
+
 int bidomain_autotune(bd_handle *h, bd_tune_result *out) {
   if (!h) return BD_ERR_ARG;
   if (!h->linearized) return BD_ERR_STATE;
@@ -1889,6 +1972,10 @@ int bidomain_destroy(bd_handle *h) {
   delete h;
   if (own) cudaStreamDestroy(s);
   return BD_OK;
+}
+
+const char *bidomain_last_error(const bd_handle *h) {
+  return h ? h->last_error.c_str() : g_last_error.c_str();
 }
 
 const char *bidomain_strerror(int status) {

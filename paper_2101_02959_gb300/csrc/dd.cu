@@ -148,72 +148,115 @@ __global__ void k_class_aug(const ClassTask *__restrict__ cls, const PairTask *_
 }
 
 // ---- coarse matrix S_PP = sum_j R_P^T S_PP^(j) R_P (Section 4.4) ---------------
-// Entry (p, q) sums the listed local entries (fixed order); the gauge row and
-// column become a unit row and column.  Written as AugCo = [[S_PP, I], [I, 0]].
+// One thread per stored entry e of the sparse pattern of S_PP (CSR, row crow[e],
+// column ccol[e]): the listed local entries are summed in FP64 in a fixed order
+// into val64[e]; the gauge row and column become a unit row and column.  The same
+// value goes into the dense augmented matrix AugCo = [[S_PP, I], [I, 0]] (in the
+// local precision, zeroed beforehand) whose partial Cholesky gives the explicit
+// inverse; threads e >= nnz write the two identity blocks.
 template <typename T>
-__global__ void k_coarse_aug(int np, int gauge, const int *__restrict__ ptr, const long long *__restrict__ src,
-                             const T *__restrict__ abase, T *__restrict__ co, int ld, double *__restrict__ co64) {
-  const int m = 2 * np;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < (long long)m * m;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int a = (int)(t / m), b = (int)(t % m);
+__global__ void k_coarse_assemble(int nnz, int np, int gauge, const int *__restrict__ crow,
+                                  const int *__restrict__ ccol, const int *__restrict__ sptr,
+                                  const long long *__restrict__ src, const T *__restrict__ abase,
+                                  double *__restrict__ val64, T *__restrict__ co, int ld) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < nnz) {
+    const int a = crow[e], b = ccol[e];
     double v = 0.0;
-    if (a < np && b < np) {
-      if (a == gauge || b == gauge) v = (a == b) ? 1.0 : 0.0;
-      else
-        for (int k = ptr[(long long)a * np + b]; k < ptr[(long long)a * np + b + 1]; ++k) v += (double)abase[src[k]];
-    } else if (a >= np && b < np) {
-      v = (a - np == b) ? 1.0 : 0.0;
-    } else if (b >= np && a < np) {
-      v = (b - np == a) ? 1.0 : 0.0;
-    }
+    if (a == gauge || b == gauge) v = (a == b) ? 1.0 : 0.0;
+    else
+      for (int k = sptr[e]; k < sptr[e + 1]; ++k) v += (double)abase[src[k]];
+    val64[e] = v;
     co[(long long)a * ld + b] = (T)v;
-    if (co64 && a < np && b < np) co64[(long long)a * np + b] = v;  // S_PiPi in FP64 (gauge row pinned)
+  } else if (e < nnz + np) {
+    const int q = e - nnz;
+    co[(long long)(np + q) * ld + q] = T(1);
+    co[(long long)q * ld + np + q] = T(1);
   }
 }
 
-// C = alpha A B + beta D for n x n FP64 matrices (row-major, leading dimension n): the
-// coarse inverse refinement.  16 x 16 output tiles, operands staged in shared memory.
-__global__ void __launch_bounds__(256) k_gemm64(int n, const double *__restrict__ A, const double *__restrict__ B,
-                                                const double *__restrict__ D, double alpha, double beta,
-                                                double *__restrict__ C) {
-  __shared__ double As[16][17], Bs[16][17];
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int i = blockIdx.y * 16 + ty, j = blockIdx.x * 16 + tx;
+// ---- coarse right-hand side c = rP - sum_j (Psi^T r_D)_j, c[gauge] = 0 ------------
+// rP is a vector, a sparse product (rPc.ptr set) or absent; yprim holds the local
+// products Psi^T r_D, assembled through the lists (pl_ptr, pl_idx) in a fixed order.
+__device__ __forceinline__ double coarse_rhs_row(int q, int gauge, const int *__restrict__ pl_ptr,
+                                                 const int *__restrict__ pl_idx, const double *__restrict__ yprim,
+                                                 const double *__restrict__ rP, const CsrIn &rPc) {
   double acc = 0.0;
-  for (int k0 = 0; k0 < n; k0 += 16) {
-    As[ty][tx] = (i < n && k0 + tx < n) ? A[(long long)i * n + k0 + tx] : 0.0;
-    Bs[ty][tx] = (k0 + ty < n && j < n) ? B[(long long)(k0 + ty) * n + j] : 0.0;
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < 16; ++k) acc += As[ty][k] * Bs[k][tx];
-    __syncthreads();
-  }
-  if (i < n && j < n) C[(long long)i * n + j] = alpha * acc + (D ? beta * D[(long long)i * n + j] : 0.0);
+  for (int k = pl_ptr[q]; k < pl_ptr[q + 1]; ++k) acc += yprim[pl_idx[k]];
+  double v = -acc;
+  if (rP) v += rP[q];
+  else if (rPc.ptr) v += csr_row(rPc, q);
+  return q == gauge ? 0.0 : v;
 }
 
-// X <- 2X - X C X, twice, from the local-precision inverse of C: the FP64 coarse inverse
-// (Newton-Schulz; the error squares each step).  X0 in T, result in X (FP64), W scratch.
-// Coarse problems above kRefineMaxNp keep the widened local-precision inverse.
-constexpr int kRefineMaxNp = 1024;
-template <typename T>
-__global__ void k_widen(long long n, const T *__restrict__ x, double *__restrict__ y) {
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
-    y[t] = (double)x[t];
+__global__ void k_coarse_rhs(int np, int gauge, const int *__restrict__ pl_ptr, const int *__restrict__ pl_idx,
+                             const double *__restrict__ yprim, const double *__restrict__ rP, const CsrIn rPc,
+                             double *__restrict__ c, const int *__restrict__ done) {
+  if (done && *done) return;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < np) c[q] = coarse_rhs_row(q, gauge, pl_ptr, pl_idx, yprim, rP, rPc);
 }
+
+// rho = c - S_PP z (FP64 CSR), one thread per row
+__global__ void k_coarse_resid(int np, const int *__restrict__ ptr, const int *__restrict__ col,
+                               const double *__restrict__ val, const double *__restrict__ c,
+                               const double *__restrict__ z, double *__restrict__ rho, const int *__restrict__ done) {
+  if (done && *done) return;
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= np) return;
+  double acc = 0.0;
+  for (int k = ptr[q]; k < ptr[q + 1]; ++k) acc += val[k] * z[col[k]];
+  rho[q] = c[q] - acc;
+}
+
+// The whole coarse solve of a small coarse problem in one CTA: c (as k_coarse_rhs),
+// z = X c with the explicit inverse X (local precision, FP64 accumulation), then nref
+// steps of iterative refinement z += X (c - S_PP z) with the FP64 sparse S_PP.  The
+// refinement makes the solve backward stable in FP64 whatever the precision of X
+// (the explicit inverse alone is not: its error grows with cond(S_PP) times the size
+// of X, and the (u_i, u_e) constant mode that the gauge alone holds is where it shows).
 template <typename T>
-void coarse_refine64(int np, const T *x0, const double *C, double *X, double *W, double *Y, cudaStream_t s) {
-  if (np == 0) return;
-  const long long nn = (long long)np * np;
-  k_widen<T><<<(int)std::min<long long>((nn + 255) / 256, 4096), 256, 0, s>>>(nn, x0, X);
-  const dim3 g(ceil_div(np, 16), ceil_div(np, 16));
-  const int iters = np <= kRefineMaxNp ? 2 : 0;  // O(np^3) FP64: beyond the limit X stays at x0
-  for (int it = 0; it < iters; ++it) {
-    k_gemm64<<<g, 256, 0, s>>>(np, C, X, nullptr, 1.0, 0.0, W);  // W = C X
-    k_gemm64<<<g, 256, 0, s>>>(np, X, W, X, -1.0, 2.0, Y);       // Y = 2X - X W
-    cudaMemcpyAsync(X, Y, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s);
+__global__ void __launch_bounds__(1024) k_coarse_solve_small(
+    int np, int gauge, const int *__restrict__ pl_ptr, const int *__restrict__ pl_idx,
+    const double *__restrict__ yprim, const double *__restrict__ rP, const CsrIn rPc, const T *__restrict__ X,
+    const int *__restrict__ sptr, const int *__restrict__ scol, const double *__restrict__ sval, int nref,
+    double *__restrict__ z_out, const int *__restrict__ done) {
+  if (done && *done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double *c = reinterpret_cast<double *>(smem_raw);
+  double *z = c + np;
+  double *r = z + np;
+  for (int q = threadIdx.x; q < np; q += blockDim.x) {
+    c[q] = coarse_rhs_row(q, gauge, pl_ptr, pl_idx, yprim, rP, rPc);
+    r[q] = c[q];
+    z[q] = 0.0;
   }
-  count_launch(1 + 2 * iters);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int pass = 0; pass <= nref; ++pass) {
+    // z += X r (r = c on the first pass)
+    for (int q = wid; q < np; q += nw) {
+      const T *row = X + (long long)q * np;
+      double a0 = 0.0, a1 = 0.0;
+      int k = lane;
+      for (; k + 32 < np; k += 64) {
+        a0 += (double)row[k] * r[k];
+        a1 += (double)row[k + 32] * r[k + 32];
+      }
+      if (k < np) a0 += (double)row[k] * r[k];
+      const double v = warp_sum(a0 + a1);
+      if (lane == 0) z[q] += v;
+    }
+    __syncthreads();
+    if (pass == nref) break;
+    for (int q = threadIdx.x; q < np; q += blockDim.x) {
+      double acc = 0.0;
+      for (int k = sptr[q]; k < sptr[q + 1]; ++k) acc += sval[k] * z[scol[k]];
+      r[q] = c[q] - acc;
+    }
+    __syncthreads();
+  }
+  for (int q = threadIdx.x; q < np; q += blockDim.x) z_out[q] = z[q];
 }
 
 // ---- rho-scaling (Section 4.2) --------------------------------------------------
@@ -239,91 +282,6 @@ void launch_rho_blocks(int ncls, const ClassTask *cls, const PairTask *pairs, do
                        T *blk, cudaStream_t s) {
   if (ncls == 0) return;
   k_rho_blocks<T><<<ncls, 256, 0, s>>>(cls, pairs, sig_i, sig_e, sinv, blk);
-  count_launch();
-}
-
-// ---- coarse correction fused with the local primal correction -----------------
-// Every CTA assembles the coarse right-hand side c = rP - sum_j (Psi^T r_D)_j
-// (c[gauge] = 0; rP as a vector, a sparse product, or absent) in shared memory,
-// solves only the rows of its own subdomain's primal dofs, z = S_PiPi^-1 c with the
-// explicit inverse (one warp per row), and then applies ydc -= Psi z to its 32
-// dual columns like k_gemv_t.  The CTAs of column block 0 also store their z
-// entries in zbar[nd + q]; a dof shared by several subdomains gets the same value
-// from each of them (same inputs, same arithmetic).
-template <typename T>
-__global__ void __launch_bounds__(256) k_coarse_psit(const GemvDesc *__restrict__ tasks, const T *__restrict__ Z,
-                                                     const double *__restrict__ coinv, int np, int gauge,
-                                                     const int *__restrict__ pl_ptr, const int *__restrict__ pl_idx,
-                                                     const double *__restrict__ yprim, const double *__restrict__ rP,
-                                                     const CsrIn rPc, const int *__restrict__ prim_x, int nd,
-                                                     double *__restrict__ zbar, double *__restrict__ ydc,
-                                                     const int *__restrict__ done) {
-  if (done && *done) return;
-  const GemvDesc t = tasks[blockIdx.y];
-  const int c0 = blockIdx.x * 32;
-  if (c0 >= t.cols) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double *cr = reinterpret_cast<double *>(smem_raw);  // [np] coarse right-hand side (FP64)
-  T *xs = reinterpret_cast<T *>(cr + np);             // [t.rows] this subdomain's z_Pi
-  __shared__ T part[8][33];
-  for (int q = threadIdx.x; q < np; q += blockDim.x) {
-    double acc = 0.0;
-    for (int k = pl_ptr[q]; k < pl_ptr[q + 1]; ++k) acc += yprim[pl_idx[k]];
-    double v = -acc;
-    if (rP) v += rP[q];
-    else if (rPc.ptr) v += csr_row(rPc, q);
-    cr[q] = (q == gauge) ? 0.0 : v;
-  }
-  __syncthreads();
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int p = wid; p < t.rows; p += 8) {
-    const int q = prim_x[t.x_off + p] - nd;
-    const double *row = coinv + (long long)q * np;
-    double a0 = 0.0, a1 = 0.0;
-    int c = lane;
-    for (; c + 32 < np; c += 64) {
-      a0 += row[c] * cr[c];
-      a1 += row[c + 32] * cr[c + 32];
-    }
-    if (c < np) a0 += row[c] * cr[c];
-    const double z = warp_sum(a0 + a1);
-    if (lane == 0) {
-      xs[p] = (T)z;
-      if (blockIdx.x == 0) zbar[nd + q] = z;
-    }
-  }
-  __syncthreads();
-  const int a = c0 + lane;
-  const bool va = a < t.cols;
-  const T *col = Z + t.a_off + (va ? a : c0);
-  const long long ld = t.ld;
-  T s0 = T(0), s1 = T(0);
-  int p = wid;
-  for (; p + 8 < t.rows; p += 16) {
-    s0 += col[p * ld] * xs[p];
-    s1 += col[(p + 8) * ld] * xs[p + 8];
-  }
-  for (; p < t.rows; p += 8) s0 += col[p * ld] * xs[p];
-  part[wid][lane] = s0 + s1;
-  __syncthreads();
-  if (wid == 0 && va) {
-    T sum = T(0);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) sum += part[k][lane];
-    const double v = -(double)sum;
-    ydc[t.y_off + a] = (t.flags & 2) ? ydc[t.y_off + a] + v : v;
-  }
-}
-
-template <typename T>
-void launch_coarse_psit(int ntasks, int max_rows, int max_cols, const GemvDesc *tasks, const T *Z, const double *coinv,
-                        int np, int gauge, const int *pl_ptr, const int *pl_idx, const double *yprim,
-                        const double *rP, const CsrIn *rPc, const int *prim_x, int nd, double *zbar, double *ydc,
-                        const int *done, cudaStream_t s) {
-  if (ntasks == 0 || max_cols == 0) return;
-  const size_t sm = sizeof(double) * (size_t)np + sizeof(T) * (size_t)std::max(1, max_rows);
-  k_coarse_psit<T><<<dim3(ceil_div(max_cols, 32), ntasks), 256, sm, s>>>(
-      tasks, Z, coinv, np, gauge, pl_ptr, pl_idx, yprim, rP, rPc ? *rPc : CsrIn{}, prim_x, nd, zbar, ydc, done);
   count_launch();
 }
 
@@ -773,12 +731,34 @@ void launch_class_aug(int ncls, int max_n, const ClassTask *cls, const PairTask 
 }
 
 template <typename T>
-void launch_coarse_aug(int np, int gauge, const int *ptr, const long long *src, const T *abase, T *co, int ld,
-                       cudaStream_t s, double *co64) {
-  const long long tot = 4LL * np * np;
-  const int gx = (int)std::min<long long>((tot + 255) / 256, 8192);
-  k_coarse_aug<T><<<std::max(gx, 1), 256, 0, s>>>(np, gauge, ptr, src, abase, co, ld, co64);
+void launch_coarse_assemble(int nnz, int np, int gauge, const int *crow, const int *ccol, const int *sptr,
+                            const long long *src, const T *abase, double *val64, T *co, int ld, cudaStream_t s) {
+  const int tot = nnz + np;
+  if (tot == 0) return;
+  k_coarse_assemble<T><<<ceil_div(tot, 256), 256, 0, s>>>(nnz, np, gauge, crow, ccol, sptr, src, abase, val64, co,
+                                                          ld);
   count_launch();
+}
+
+template <typename T>
+void launch_coarse_solve(const CoarseSolve &cs, const T *X, const double *yprim, const double *rP, const CsrIn *rPc,
+                         double *z, double *c, double *rho, const int *done, cudaStream_t s) {
+  if (cs.np == 0) return;
+  const CsrIn rc = rPc ? *rPc : CsrIn{};
+  if (cs.np <= kCoarseSmall) {
+    k_coarse_solve_small<T><<<1, 1024, 3 * sizeof(double) * cs.np, s>>>(
+        cs.np, cs.gauge, cs.pl_ptr, cs.pl_idx, yprim, rP, rc, X, cs.sptr, cs.scol, cs.sval, cs.nref, z, done);
+    count_launch();
+    return;
+  }
+  k_coarse_rhs<<<ceil_div(cs.np, 256), 256, 0, s>>>(cs.np, cs.gauge, cs.pl_ptr, cs.pl_idx, yprim, rP, rc, c, done);
+  count_launch();
+  launch_gemv<T>(1, cs.np, cs.np, cs.gv, X, c, nullptr, z, 1.0, done, s);
+  for (int it = 0; it < cs.nref; ++it) {
+    k_coarse_resid<<<ceil_div(cs.np, 256), 256, 0, s>>>(cs.np, cs.sptr, cs.scol, cs.sval, c, z, rho, done);
+    count_launch();
+    launch_gemv<T>(1, cs.np, cs.np, cs.gv_acc, X, rho, nullptr, z, 1.0, done, s);
+  }
 }
 
 template <typename T>
@@ -941,19 +921,17 @@ void launch_dot2(int n, const double *a0, const double *b0, const double *a1, co
   template void launch_small_gemm<T>(int, int, const GemmTask *, const T *, const T *, T *, cudaStream_t);      \
   template void launch_class_aug<T>(int, int, const ClassTask *, const PairTask *, const T *, const MatDesc *,  \
                                     T *, cudaStream_t);                                                        \
-  template void launch_coarse_aug<T>(int, int, const int *, const long long *, const T *, T *, int,             \
-                                     cudaStream_t, double *);                                                  \
-  template void coarse_refine64<T>(int, const T *, const double *, double *, double *, double *, cudaStream_t);  \
+  template void launch_coarse_assemble<T>(int, int, int, const int *, const int *, const int *,                 \
+                                          const long long *, const T *, double *, T *, int, cudaStream_t);     \
+  template void launch_coarse_solve<T>(const CoarseSolve &, const T *, const double *, const double *,         \
+                                       const CsrIn *, double *, double *, double *, const int *, cudaStream_t); \
   template void launch_jump_dt<T>(int, int, const WTask *, const WEnt *, const T *, const T *, const double *,  \
                                   double *, const int *, cudaStream_t);                                        \
   template void launch_jump_d<T>(int, int, const LamTask *, const PairTask *, const T *, const T *,             \
                                  const double *, double *, const int *, cudaStream_t);                         \
   template void launch_copy<T, T>(int, long long, const CopyTask *, const T *, T *, cudaStream_t);            \
   template void launch_rho_blocks<T>(int, const ClassTask *, const PairTask *, double, double, T *, T *,        \
-                                     cudaStream_t);                                                            \
-  template void launch_coarse_psit<T>(int, int, int, const GemvDesc *, const T *, const double *, int, int,     \
-                                      const int *, const int *, const double *, const double *, const CsrIn *, \
-                                      const int *, int, double *, double *, const int *, cudaStream_t);
+                                     cudaStream_t);
 BD_DD_INST(float)
 BD_DD_INST(double)
 template void launch_copy<float, double>(int, long long, const CopyTask *, const float *, double *, cudaStream_t);

@@ -53,13 +53,32 @@ void launch_small_gemm(int ntasks, int max_n, const GemmTask *tasks, const T *A,
 template <typename T>
 void launch_class_aug(int ncls, int max_n, const ClassTask *cls, const PairTask *pairs, const T *blk,
                       const MatDesc *cdesc, T *cbase, cudaStream_t s);
+// ---- coarse problem (Section 4.4) ------------------------------------------------
+// S_PP is kept as an FP64 CSR matrix (pattern of the local primal couplings, gauge row
+// and column pinned to the unit vector) and, in the local precision, as the dense
+// augmented matrix [[S_PP, I], [I, 0]] whose partial Cholesky leaves -S_PP^-1.
+// Entry e of the CSR sums the local entries src[sptr[e] .. sptr[e + 1]) of the
+// augmented local matrices.
 template <typename T>
-// coarse augmented matrix [[S_PiPi, I], [I, 0]] (assembled in FP64, stored as T)
-void launch_coarse_aug(int np, int gauge, const int *ptr, const long long *src, const T *abase, T *co, int ld,
-                       cudaStream_t s, double *co64 = nullptr);
-// FP64 coarse inverse: X = (double) x0, then X <- 2X - X C X twice (Newton-Schulz); W, Y scratch
+void launch_coarse_assemble(int nnz, int np, int gauge, const int *crow, const int *ccol, const int *sptr,
+                            const long long *src, const T *abase, double *val64, T *co, int ld, cudaStream_t s);
+
+// The coarse solve z = S_PP^-1 c with c = rP - sum_j (Psi^T r_D)_j: the explicit
+// inverse X (local precision) followed by nref steps of iterative refinement
+// z += X (c - S_PP z) against the FP64 CSR, so the result is the FP64 solution.
+// np <= kCoarseSmall: one CTA; otherwise one GEMV per pass over the whole grid.
+constexpr int kCoarseSmall = 320;
+struct CoarseSolve {
+  int np = 0, gauge = -1, nref = 1;
+  const int *pl_ptr = nullptr, *pl_idx = nullptr;  // assembly lists of the local primal products
+  const int *sptr = nullptr, *scol = nullptr;      // S_PP (CSR, FP64)
+  const double *sval = nullptr;
+  const GemvDesc *gv = nullptr, *gv_acc = nullptr;  // one np x np task: y = X x / y += X x
+};
+// c and rho: np-long scratch (large problems only); z: np-long output
 template <typename T>
-void coarse_refine64(int np, const T *x0, const double *C, double *X, double *W, double *Y, cudaStream_t s);
+void launch_coarse_solve(const CoarseSolve &cs, const T *X, const double *yprim, const double *rP, const CsrIn *rPc,
+                         double *z, double *c, double *rho, const int *done, cudaStream_t s);
 void launch_spmv(int n, const int *ptr, const int *col, const double *val, const double *x, double *y, int zero,
                  const int *done, cudaStream_t s);
 void launch_gather_sum(int n, const int *ptr, const int *idx, const double *src, double *y, int zero, double alpha,
@@ -68,13 +87,6 @@ void launch_gather_sum(int n, const int *ptr, const int *idx, const double *src,
 template <typename T>
 void launch_rho_blocks(int ncls, const ClassTask *cls, const PairTask *pairs, double sig_i, double sig_e, T *sinv,
                        T *blk, cudaStream_t s);
-// coarse solve fused into the primal correction: c = rP (vector, sparse product or
-// absent) - sum_j (Psi^T r_D)_j, z_Pi = S_PiPi^-1 c (FP64) into zbar[nd:], ydc -= Psi z_Pi
-template <typename T>
-void launch_coarse_psit(int ntasks, int max_rows, int max_cols, const GemvDesc *tasks, const T *Z, const double *coinv,
-                        int np, int gauge, const int *pl_ptr, const int *pl_idx, const double *yprim,
-                        const double *rP, const CsrIn *rPc, const int *prim_x, int nd, double *zbar, double *ydc,
-                        const int *done, cudaStream_t s);
 // fused with the PCG reduction f (alpha = 1, no addend; y[zero] = 0)
 void launch_gather_sum_dot(int n, const int *ptr, const int *idx, const double *src, double *y, int zero,
                            const DotFuse &f, cudaStream_t s);

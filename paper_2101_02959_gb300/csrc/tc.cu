@@ -172,16 +172,18 @@ __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__
     } else {
       asm volatile("cp.async.wait_group 0;");
     }
-    // hi/lo[b] was last read by the MMAs of chunk i - 2
+    // hi/lo[b] was last read by the MMAs of chunk i - 2; a batch that has not completed
+    // within the wait budget stays pending, and the drain below waits for it once more
     bool late = false;
     if (pending[b]) {
       late = !mbar_wait(smem_addr(&mbar[b]), phase[b]);
-      phase[b] ^= 1u;
-      pending[b] = 0;
+      if (!late) {
+        phase[b] ^= 1u;
+        pending[b] = 0;
+      }
     }
     if (__syncthreads_or(late ? 1 : 0)) {
       ok = false;
-      if (tid == 0) atomicOr(err, DEV_ERR_TIMEOUT);
       break;
     }
     // split raw[b] into TF32 hi and lo parts (same swizzled offsets)
@@ -219,14 +221,18 @@ __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__
     pending[b] = 1;
   }
   asm volatile("cp.async.wait_group 0;");
-  // drain: wait for every MMA batch still in flight
+  // drain: wait for every MMA batch still in flight (also one that timed out above), so
+  // that no MMA still reads this CTA's shared memory or writes its tensor memory when the
+  // CTA releases them.  A batch that misses this bounded wait too is reported
+  // (DEV_ERR_TIMEOUT, skipped epilogue); the caller must then treat the whole handle as
+  // lost (bidomain_destroy), since the tensor pipe may still be running on it.
   bool late = false;
   for (int b = 0; b < 2; ++b)
     if (pending[b]) {
       late |= !mbar_wait(smem_addr(&mbar[b]), phase[b]);
       phase[b] ^= 1u;
     }
-  if (__syncthreads_or(late ? 1 : 0)) {
+  if (__syncthreads_or(late ? 1 : 0) || !ok) {
     ok = false;
     if (tid == 0) atomicOr(err, DEV_ERR_TIMEOUT);
   }

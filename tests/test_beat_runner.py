@@ -23,8 +23,10 @@ class _FakeSolver:
     def step(self, stim):
         self.steps += 1
         self.stims.append(stim)
-        fail = self.opt.get("fail_at") == self.steps
-        return dict(newton_its=1 + self.steps % 2, krylov_its=10 * (1 + self.steps % 2), reason=-3 if fail else 0)
+        out = dict(newton_its=1 + self.steps % 2, krylov_its=10 * (1 + self.steps % 2), reason=0)
+        if self.opt.get("fail_at") == self.steps:  # as the binding does: raise, with the step's stats
+            raise beat.binding.BidomainError(-3, "bidomain_step", stats=dict(out, reason=-3))
+        return out
 
     def get_state(self):
         # node x activates at step 3 + x and recovers at step 20 + 2 x (v in mV)
@@ -56,6 +58,7 @@ def test_run_stops_at_a_failed_step(monkeypatch):
     monkeypatch.setattr(beat.binding, "Solver", _FakeSolver)
     recs = list(beat.run(synth.workload("cube8ve"), 10, fail_at=3))
     assert len(recs) == 3 and recs[-1]["reason"] == -3
+    assert recs[-1]["newton_its"] == 2 and recs[-1]["krylov_its"] == 20  # the failed step's own counts
     assert _FakeSolver.instances[-1].closed
     assert beat.summarize(recs)["failed"] == 1
     assert beat.summarize([])["steps"] == 0
@@ -141,3 +144,21 @@ def test_checkpoint_refuses_hidden_state():
         list(beat.run(w, 2, checkpoint="x.npz", checkpoint_every=1, learned_guess=1))
     with pytest.raises(ValueError):
         list(beat.run(w, 2, resume="x.npz", precond_every=2))
+
+
+def test_resume_refuses_another_run(monkeypatch, tmp_path):
+    """A checkpoint carries its workload, node count and options; resuming it with other
+    ones, or recording maps it does not hold, is refused."""
+    import pytest
+    monkeypatch.setattr(beat.binding, "Solver", _StateSolver)
+    w = synth.workload("tiny")
+    ck = str(tmp_path / "beat.npz")
+    list(beat.run(w, 4, checkpoint=ck, checkpoint_every=2, method="bddc"))
+    rest = list(beat.run(w, 6, resume=ck, method="bddc"))
+    assert [r["step"] for r in rest] == [5, 6]
+    with pytest.raises(ValueError, match="method"):
+        list(beat.run(w, 6, resume=ck, method="fetidp"))
+    with pytest.raises(ValueError, match="workload"):
+        list(beat.run(synth.workload("cube8"), 6, resume=ck, method="bddc"))
+    with pytest.raises(ValueError, match="maps"):
+        list(beat.run(w, 6, resume=ck, method="bddc", maps={}, record_every=2))

@@ -46,8 +46,32 @@ def test_mlp_loss_and_gradients_match_oracle():
         got = g[off:off + n].astype(np.float64)
         ref = gr[k].ravel()
         assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref), k
+        # entry by entry, against the block's largest entry
+        assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref)), k
         off += n
     assert off == g.size
+
+
+def test_adam_matches_oracle_over_steps():
+    """The GPU's Adam update (FP32) against the oracle's adam_step (FP64) over six steps
+    with gradients spanning three decades, entry by entry."""
+    s = _solver("cube8ve", learned_guess=1)
+    w0 = s.mlp_params()
+    rng = np.random.default_rng(11)
+    p = {"w": w0.astype(np.float64)}
+    st = {}
+    for _ in range(6):
+        g = (rng.choice([-1.0, 1.0], w0.size) * 10.0 ** rng.uniform(-3, 0, w0.size)).astype(np.float32)
+        s.mlp_adam_step(g, 1e-3)
+        mlp.adam_step(p, {"w": g.astype(np.float64)}, st, lr=1e-3)
+    got = s.mlp_params().astype(np.float64)
+    moved = np.abs(p["w"] - w0)
+    assert np.median(moved) > 1e-3  # the steps really moved the weights (about lr each)
+    # FP32 weights: a few units in the last place of each weight
+    ulp = np.spacing(np.abs(w0).astype(np.float32)).astype(np.float64)
+    assert np.all(np.abs(got - p["w"]) <= 8 * ulp + 1e-9)
+    s.mlp_reset()
+    np.testing.assert_array_equal(s.mlp_params(), w0)  # back to the initial draw
 
 
 def _run(name, steps, **opt):

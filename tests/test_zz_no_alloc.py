@@ -41,4 +41,5 @@ def test_noalloc_matches_schur_apply(name, precision):
         assert code == 0, binding.ERRORS.get(code, code)
         rel = float(torch.linalg.norm(y - ref) / torch.linalg.norm(ref))
         assert rel < 1e-9
+        assert float((y - ref).abs().max() / ref.abs().max()) < 1e-9  # entry-wise too
     s.close()
