@@ -1,18 +1,22 @@
 """Benchmark of the Bidomain time step on one GB300 (driver contract: one JSON line).
 
-Workload (default): 32x32x16 Q1 elements on a 1.6x1.6x0.8 cm slab, 4x4x2
-subdomains (H/h = 8), vertex + edge-average primal space, Table-1 physics,
-tau = 0.05 ms, seeded resting state with N(0, 1 mV) noise and the corner
-stimulus; 20 time steps.  A "step" is one time step: gating, then Newton with
-the Jacobian solved by PCG + BDDC deluxe (or FETI-DP), at the paper's
-tolerances (KSP rtol 1e-8, SNES rtol 1e-4).
+Workload (default): 128x128x32 Q1 elements on a 3.2x3.2x0.8 cm slab, 16x16x4 =
+1,024 subdomains (H/h = 8), vertex + edge-average primal space (6,030 coarse
+unknowns), Table-1 physics, tau = 0.05 ms, seeded resting state with N(0, 1 mV)
+noise and the corner stimulus: 1,098,306 unknowns, the paper's weak-scaling mesh
+of 1.1 M dofs (Section 6, Test 1).  A "step" is one time step: gating, then
+Newton with the Jacobian solved by PCG + BDDC deluxe (or FETI-DP), at the
+paper's tolerances (KSP rtol 1e-8, SNES rtol 1e-4).
 
-The chosen solver (mixed precision: float32 local factors and Schur
-complements, float64 Krylov / Newton / coarse solve) is timed next to the plain
-float64 GPU solver on the same mesh.  Inputs are resident in HBM for `value`;
-`e2e` repeats the chosen run through the C-ABI with host buffers (state copied
-in and out every step).  With --gpus N > 1 every rank runs an independent
-replica (the path does not shard across GPUs); timings are max over ranks.
+The chosen solver (mixed precision: float32 local factors and Schur complements
+on the tensor cores, float64 Krylov / Newton / coarse solve; chord Newton; the
+learned initial guess trained online from scratch over the first half of the
+timed steps) is timed next to the same run without the guess and next to the
+plain float64 GPU solver (a sample of the first steps).  Inputs are resident in
+HBM for `value`; `e2e` repeats the chosen run through the C-ABI with pinned
+host buffers (state copied in and out every step).  With --gpus N > 1 every
+rank runs an independent replica (the path does not shard across GPUs); timings
+are max over ranks.
 """
 from __future__ import annotations
 
@@ -25,12 +29,12 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "ms/time step and Krylov solves/s at rel. res 1e-8, chosen vs plain FP64 GPU"
-FP32_SIMT_PEAK = 152 * 128 * 2 * 2.07e9 / 1e12   # TFLOP/s: SMs x FP32 lanes x FMA x max SM clock
-FP64_PEAK = 1.25                                  # TFLOP/s, nominal GB300 FP64
 
 
 def describe(w):
@@ -125,6 +129,10 @@ def run_gpu(args, w, rank, world):
     N = synth.n_nodes(w)
     ui0, ue0, w0 = synth.initial_state(N, 0)
     dstate = [torch.from_numpy(a).cuda() for a in (ui0, ue0, w0)]
+    K = args.steps
+    # the learned guess is trained online from scratch over the first half of the timed
+    # steps (the 128x128x32 slab's schedule: trained on the first 200 of 400 steps)
+    train_steps = max(1, K // 2)
 
     def barrier():
         rank_barrier(world)
@@ -132,18 +140,28 @@ def run_gpu(args, w, rank, world):
     def max_over_ranks(x):
         return rank_max(x, world, "cuda")
 
-    def timed(precision, method, profile=False, clocks=None, graphs=1, learned=0):
-        s = binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, stream=stream.cuda_stream,
-                           precision=precision, method=method, use_graphs=graphs, learned_guess=learned,
-                           mlp_train_steps=args.steps + args.warmup + 1, mlp_epochs=args.mlp_epochs,
-                           use_tensor_cores=int(precision == "mixed" and args.tc),
-                           lag_jacobian=int(precision == "mixed" and args.lag), scaling=args.scaling,
-                           precond_every=args.precond_every if method == "bddc" else 1)
-        s.set_state(*dstate, 0.0)
+    def solver(precision, method, graphs=1, learned=0):
+        return binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, stream=stream.cuda_stream,
+                              precision=precision, method=method, use_graphs=graphs, learned_guess=learned,
+                              mlp_train_steps=train_steps, mlp_epochs=args.mlp_epochs,
+                              use_tensor_cores=int(precision == "mixed" and args.tc),
+                              lag_jacobian=int(precision == "mixed" and args.lag), scaling=args.scaling,
+                              precond_every=args.precond_every if method == "bddc" else 1)
+
+    def prepare(s, learned, state):
+        """Warm-up steps (graph capture, autotuning), then back to t = 0 with an untrained network."""
+        s.set_state(*state, 0.0)
         for _ in range(args.warmup):
             s.step(synth.stimulus(w))
         tune = s.autotune() if args.autotune else None
-        s.set_state(*dstate, 0.0)
+        s.set_state(*state, 0.0)
+        if learned:
+            s.mlp_reset()
+        return tune
+
+    def timed(precision, method, profile=False, clocks=None, graphs=1, learned=0, steps=K):
+        s = solver(precision, method, graphs, learned)
+        tune = prepare(s, learned, dstate)
         if profile:
             s.profile(profile)
         stats = []
@@ -154,7 +172,7 @@ def run_gpu(args, w, rank, world):
         l0 = binding.launch_count()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(args.steps):
+        for _ in range(steps):
             stats.append(s.step(synth.stimulus(w)))
         e1.record(stream)
         torch.cuda.synchronize()
@@ -170,76 +188,102 @@ def run_gpu(args, w, rank, world):
         kry = sum(st["krylov_its"] for st in stats)
         bad = [st["reason"] for st in stats if st["reason"] != 0]
         used = sum(st.get("guess_used", 0) for st in stats)
-        return dict(ms=ms, newton=newton, krylov=kry, launches=launches, prof=prof, regions=regs, clocks=clk, bad=bad,
-                    cond=max(st["cond_max"] for st in stats), final=final, guess_used=used, tune=tune)
+        return dict(ms=ms, steps=steps, newton=newton, krylov=kry, launches=launches, prof=prof, regions=regs,
+                    clocks=clk, bad=bad, cond=max(st["cond_max"] for st in stats), final=final, guess_used=used,
+                    tune=tune)
 
     chosen = timed(args.precision, args.method, clocks=ClockSampler(dev), learned=args.learned)
     other = timed(args.precision, args.method, learned=1 - args.learned)
-    # per-launch CUDA events need stream launches: a second pass of the same K steps, profiled
-    profiled = timed(args.precision, args.method, profile=True, graphs=0, learned=args.learned)
+    # per-launch CUDA events need stream launches: a second, shorter pass of the same steps
+    nprof = min(K, args.profile_steps)
+    profiled = timed(args.precision, args.method, profile=True, graphs=0, learned=args.learned, steps=nprof)
     chosen["prof"] = profiled["prof"]
-    chosen["prof_ms"] = profiled["ms"]
+    chosen["prof_ms"] = profiled["ms"] / nprof
+    chosen["prof_newton"] = profiled["newton"] / nprof
+    chosen["prof_krylov"] = profiled["krylov"] / nprof
     # where a graph-replayed step spends its time: region timers only (a third pass)
-    regions = timed(args.precision, args.method, profile=2, learned=args.learned)
-    chosen["regions"] = regions["regions"]
-    chosen["regions_ms"] = regions["ms"]
-    plain = timed("fp64", args.method) if not args.no_plain else None
+    regions = timed(args.precision, args.method, profile=2, learned=args.learned, steps=nprof)
+    chosen["regions"] = {k: dict(v, ms=v["ms"] / nprof, launches=v["launches"] / nprof)
+                         for k, v in regions["regions"].items()}
+    chosen["regions_ms"] = regions["ms"] / nprof
+    # the plain FP64 GPU solver (same algorithm, every Jacobian formed, no learned guess) on a
+    # sample of the first steps
+    nplain = min(K, args.plain_steps)
+    plain = timed("fp64", args.method, steps=nplain) if nplain > 0 else None
 
-    # e2e: the same chosen run through host buffers, state copied in and out every step
-    s = binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, stream=stream.cuda_stream,
-                       precision=args.precision, method=args.method, use_graphs=1, learned_guess=args.learned,
-                       mlp_train_steps=args.steps + args.warmup + 1, mlp_epochs=args.mlp_epochs,
-                       use_tensor_cores=int(args.precision == "mixed" and args.tc),
-                       lag_jacobian=int(args.precision == "mixed" and args.lag), scaling=args.scaling,
-                       precond_every=args.precond_every if args.method == "bddc" else 1)
-    hs = (ui0.copy(), ue0.copy(), w0.copy())
-    s.set_state(*hs, 0.0)
-    for _ in range(args.warmup):
-        s.step(synth.stimulus(w))
-    if args.autotune:
-        s.autotune()
+    # e2e: the chosen run through the C-ABI with host buffers (pinned), the state copied in
+    # and out every step; handing the state back at the handle's own time keeps the learned
+    # guess's history, so this is the same solver as the timed run
+    s = solver(args.precision, args.method, 1, args.learned)
+    hs = [torch.from_numpy(a.copy()).pin_memory().numpy() for a in (ui0, ue0, w0)]
+    prepare(s, args.learned, hs)
+    outs = [torch.empty(N, dtype=torch.float64).pin_memory().numpy() for _ in range(3)]
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    state, t = hs, 0.0
-    e2e_newton = 0
-    for _ in range(args.steps):
-        s.set_state(*state, t)
+    t = 0.0
+    e2e_newton = e2e_used = 0
+    for _ in range(K):
+        s.set_state(*hs, t)
         st = s.step(synth.stimulus(w))
         e2e_newton += st["newton_its"]
-        ui, ue, wv, t = s.get_state()
-        state = (ui, ue, wv)
+        e2e_used += st["guess_used"]
+        t = s.get_state_into(*outs)
+        hs, outs = outs, hs
     torch.cuda.synchronize()
     e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3)
     s.close()
 
-    K = args.steps
-    out = dict(chosen=chosen, plain=plain, other=other, e2e_ms=e2e_ms, e2e_newton=e2e_newton, N=N)
-    # final-state agreement of the chosen and the plain FP64 solvers after K steps
-    if plain is not None:
+    out = dict(chosen=chosen, plain=plain, other=other, e2e_ms=e2e_ms, e2e_newton=e2e_newton, e2e_used=e2e_used,
+               N=N, K=K, nplain=nplain, nprof=nprof, train_steps=train_steps)
+    if plain is not None and nplain == K:
         a, b = chosen["final"], plain["final"]
         va, vb = (a[0] - a[1]).double(), (b[0] - b[1]).double()
         out["v_rel_diff_vs_plain"] = float(torch.linalg.norm(va - vb) / torch.linalg.norm(vb))
         out["ue_rel_diff_vs_plain"] = float(torch.linalg.norm(a[1] - b[1]) / torch.linalg.norm(b[1]))
-    out["K"] = K
     return out
 
 
-# DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum, averaged over every
-# launch of a slab32 run; profiles/*_slab32_mixed_bddc.md).  A figure stands only while its
-# kernel's source text is the one it was measured on (first 16 hex digits of its sha256).
+# ---- algorithmic work of the method (the per-unit figures of the scope table) ----------------
+# Local problems of a box subdomain with H/h = k elements per side, dofs ordered plane by
+# plane: block tridiagonal with p planes of m dofs each.  Dirichlet (interior): p = k - 1,
+# m = 2 (k - 1)^2; constrained Neumann (I + Delta): p = k + 1, m = 2 (k + 1)^2.  A banded
+# Cholesky costs 2.33 p m^3 flops and stores 1.5 p m^2 values.
+def local_shapes(k):
+    pd, md = k - 1, 2 * (k - 1) ** 2
+    pn, mn = k + 1, 2 * (k + 1) ** 2
+    n_gamma = 2 * ((k + 1) ** 3 - (k - 1) ** 3)
+    n_int = 2 * (k - 1) ** 3
+    n_face = 2 * (k - 1) ** 2
+    return pd, md, pn, mn, n_gamma, n_int, n_face
+
+
+def factor_flops_per_sub(k, n_primal_local=40):
+    """Refactorisation flops per subdomain per Jacobian: Dirichlet and Neumann factors,
+    L_II^-1 K_I,Gamma for the interface columns, the face Schur SYRKs of the deluxe blocks
+    and Phi (one Neumann solve per local primal dof)."""
+    pd, md, pn, mn, ng, ni, nf = local_shapes(k)
+    fd, fn = 1.5 * pd * md ** 2, 1.5 * pn * mn ** 2
+    return (2.33 * pd * md ** 3 + 2.33 * pn * mn ** 3 + 2.0 * fd * ng + ni * 6 * nf ** 2
+            + 4.0 * fn * n_primal_local)
+
+
+def solve_values_per_sub(k):
+    """Factor values one Dirichlet and one Neumann solve read (forward and back)."""
+    pd, md, pn, mn, *_ = local_shapes(k)
+    return 2.0 * 1.5 * pd * md ** 2, 2.0 * 1.5 * pn * mn ** 2
+
+
+# DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum of one capture, see
+# profiles/), kept with the first 16 hex digits of the sha256 of the kernel's source text: a
+# figure stands only while that text is unchanged, and is reported as null otherwise.
 TRAFFIC = {
-    # k_rankk128 is the "rankk" class only with tensor cores off; its measured launches (the
-    # in-block updates, 21.1 MB each) belong to the panel class, so no figure is kept for it
-    "k_rankk128": {"bytes_per_launch": None, "sha": "69ca1105c88785a7",
-                   "span": ("__global__ void __launch_bounds__(256) k_rankk128(",
-                            "template <typename T>\nstatic void launch_rankk(")},
-    "k_bigpanel": {"bytes_per_launch": 7.78e6, "sha": "a3c19f2ca59fb23c",
-                   "span": ("template <typename T, bool ROWS>\n__global__ void __launch_bounds__(256, ROWS ? 2 : 1) "
-                            "k_bigpanel(", "// ---- rank-k update of lower tiles")},
-    "k_rankk_tc": {"bytes_per_launch": 72.36e6, "sha": "f793e17009497dfe", "file": "tc.cu",
+    "k_rankk_tc": {"bytes_per_launch": None, "sha": None, "file": "tc.cu",
                    "span": ("__global__ void __launch_bounds__(128, 1) k_rankk_tc(",
                             "static constexpr int kTcSmem")},
+    "k_gemv": {"bytes_per_launch": None, "sha": None, "file": "dense.cu",
+               "span": ("__global__ void __launch_bounds__(256) k_gemv(",
+                        "// y[a] = (acc ? y[a] : 0) + alpha sum_p A[p][a] x[p]")},
 }
 
 
@@ -262,56 +306,96 @@ def traffic(name):
     return t["bytes_per_launch"] if kernel_sha(name) == t["sha"] else None
 
 
-def roofline(prof, precision, tc_used=False):
-    """Dominant profiled kernel class against its roofline."""
+def device_fp32_peak(dev=0):
+    """FP32 SIMT peak derived from the device: SMs x 128 FP32 lanes x 2 flop x max SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = peaks().get("sm_max_mhz", 2070.0)
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, f"derived: {sms} SMs (device) x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"
+
+
+def roofline(prof, regions, w, precision, tc_used, nsub):
+    """The dominant part of a step against its roofline, with the method's ALGORITHMIC work:
+    the factorisation kernels (panel + rank-k classes) per Jacobian against the tensor pipe
+    (3xTF32) / FP32 / FP64 peak, or the Krylov local-solve GEMVs per iteration against HBM.
+    Both figures are returned; `roofline` is the one that takes more of the step."""
     pk = peaks()
-    dom = max(prof, key=lambda k: prof[k]["ms"])
-    p = prof[dom]
-    if p["launches"] == 0 or p["ms"] <= 0:
-        return None, dom
-    if dom == "rankk" and precision == "mixed" and tc_used:
-        # tcgen05 kind::tf32 with operands split in hi + lo TF32 parts: three MMAs per
-        # FP32-accurate product, so the peak for algorithmic FP32 flops is the TF32 peak
-        # (measured sustained bf16 x the nominal tf32 / bf16 ratio 1.1 / 2.25) / 3
-        achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12
-        src = "bf16_tflops_sustained" if "bf16_tflops_sustained" in pk else None
-        tf32 = (pk[src] if src else 1700.0) * 1.1 / 2.25
-        peak = tf32 / 3.0
-        r = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-             "traffic": traffic("k_rankk_tc"), "kernel": "k_rankk_tc",
-             "peak_source": ("of measured: bf16_tflops_sustained x 1.1/2.25 (tf32) / 3 (hi/lo split)" if src
-                             else "of fallback: 1.7 PF bf16 sustained x 1.1/2.25 / 3")}
-    elif dom in ("rankk", "panel"):
-        achieved = p["flops"] / (p["ms"] * 1e-3) / 1e12
-        peak = FP32_SIMT_PEAK if precision == "mixed" else FP64_PEAK
-        if dom == "rankk":
-            kern = "k_rankk128" if precision == "mixed" and not tc_used else \
-                "k_rankk_tc" if precision == "mixed" else "k_rankk<double>"
+    k = w["s"][0]
+    el = 4 if precision == "mixed" else 8
+    n_jac = regions["linearize"]["launches"]
+    out = {}
+    # factorisation: flops the method needs per Jacobian / time of the factorisation kernels
+    f_ms = prof["panel"]["ms"] + prof["rankk"]["ms"]
+    f_launch = prof["panel"]["launches"] + prof["rankk"]["launches"]
+    if f_ms > 0 and n_jac > 0:
+        algo = factor_flops_per_sub(k) * nsub * n_jac
+        lib = prof["panel"]["flops"] + prof["rankk"]["flops"]
+        if precision == "mixed" and tc_used:
+            src = "bf16_tflops_sustained" if "bf16_tflops_sustained" in pk else None
+            peak = (pk[src] if src else 1700.0) * 1.1 / 2.25 / 3.0
+            psrc = ("of measured: bf16_tflops_sustained x 1.1/2.25 (tf32) / 3 (hi/lo split)" if src
+                    else "of fallback: 1.7 PF bf16 sustained x 1.1/2.25 / 3")
+            bound = "tensor"
+        elif precision == "mixed":
+            peak, psrc = device_fp32_peak()
+            bound = "alu"
         else:
-            kern = "k_bigpanel"  # diagonal + rows launches (the class also times the in-block updates)
-        r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-             "traffic": traffic(kern) if precision == "mixed" else None,
-             "kernel": kern,
-             "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz" if precision == "mixed"
-                             else "nominal GB300 FP64 (recipe table)")}
-    else:
-        achieved = p["bytes"] / (p["ms"] * 1e-3) / 1e9
+            peak, psrc = 1.25, "nominal GB300 FP64 (recipe table)"
+            bound = "alu"
+        ach = algo / (f_ms * 1e-3) / 1e12
+        out["factorisation"] = {
+            "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": traffic("k_rankk_tc") if tc_used else None,
+            "kernel": "k_rankk_tc + k_bigpanel + k_rankk128 (the factorisation launches of a Jacobian)",
+            "peak_source": psrc, "launches": f_launch, "avg_launch_us": f_ms * 1e3 / f_launch,
+            "ms_per_jacobian": f_ms / n_jac,
+            "algorithmic_flops_per_jacobian": algo / n_jac, "library_flops_per_jacobian": lib / n_jac,
+            "work": f"{factor_flops_per_sub(k):.3g} flop per H/h={k} subdomain x {nsub} subdomains "
+                    "(banded Dirichlet + Neumann factors, L_II^-1 K_IG, face SYRKs, Phi)"}
+    # Krylov: one Dirichlet + one Neumann local solve per subdomain and iteration
+    g = prof["gemv"]
+    if g["ms"] > 0 and g["launches"] > 0:
+        vd, vn = solve_values_per_sub(k)
+        algo = (g["launches"] / 2.0) * nsub * (vd + vn) * el
+        ach = algo / (g["ms"] * 1e-3) / 1e9
         peak = pk.get("hbm_gbs", 6800.0)
-        r = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-             "traffic": None, "kernel": "k_gemv" if dom == "gemv" else "k_residual",
-             "peak_source": "of measured" if "fallback" not in pk else "of fallback"}
-    r["launches"] = p["launches"]
-    r["avg_launch_us"] = p["ms"] * 1e3 / p["launches"]
-    r["measured_in"] = "profiled pass of the same K steps: per-launch CUDA events on the library stream"
-    return r, dom
+        out["krylov"] = {
+            "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+            "traffic": traffic("k_gemv"), "kernel": "k_gemv (operator and local constrained solve, per launch)",
+            "peak_source": "of measured" if "fallback" not in pk else "of fallback",
+            "launches": g["launches"], "avg_launch_us": g["ms"] * 1e3 / g["launches"],
+            "algorithmic_bytes_per_launch": algo / g["launches"], "library_bytes_per_launch": g["bytes"] / g["launches"],
+            "work": f"{vd + vn:.3g} factor values per H/h={k} subdomain and iteration (Dirichlet + Neumann "
+                    f"solve, read forward and back) x {nsub} subdomains x {el} B, split over the 2 GEMV launches"}
+    if not out:
+        return None, None
+    dom = max(out, key=lambda c: (prof["panel"]["ms"] + prof["rankk"]["ms"]) if c == "factorisation"
+              else prof["gemv"]["ms"])
+    r = dict(out[dom])
+    r["measured_in"] = "profiled pass: per-launch CUDA events on the library stream"
+    others = {c: v for c, v in out.items() if c != dom}
+    return r, others
+
+
+# workloads whose oracle step is out of the CPU baseline's budget: the sample is the oracle's
+# step on a workload with the same subdomains and physics, scaled by the subdomain count
+CPU_SAMPLE = {"slab128": "slab32", "beat_slab": "beat_slab_half"}
 
 
 def cpu_baseline(w, steps=1, method="bddc", scaling="deluxe"):
-    """The oracle (numpy, FP64) on the host cores: `steps` time steps of the same workload."""
+    """The oracle (numpy, FP64) on the host cores: `steps` time steps of the workload, or of its
+    sample workload (same H/h, physics and primal space, fewer subdomains) scaled to it."""
     import synth
     from oracle.bidomain import Problem, time_step
     from oracle.dd import DDSolver
-    prob = Problem(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, synth.stimulus(w))
+    ws = w
+    scale = 1.0
+    if w.get("name") in CPU_SAMPLE:
+        ws = synth.workload(CPU_SAMPLE[w["name"]])
+        ws["primal"] = w["primal"]
+        nb = lambda x: np.prod([-(-x["n"][d] // x["s"][d]) for d in range(3)])  # noqa: E731
+        scale = float(nb(w)) / float(nb(ws))
+    prob = Problem(ws, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, synth.stimulus(ws))
     ui, ue, wv = synth.initial_state(prob.N, 0)
     dd = DDSolver(prob, method=method, scaling=scaling)
     newton = 0
@@ -325,8 +409,11 @@ def cpu_baseline(w, steps=1, method="bddc", scaling="deluxe"):
         cores = max(i.get("num_threads", 1) for i in threadpool_info()) or os.cpu_count()
     except Exception:  # threadpoolctl is not installed on every host
         cores = os.cpu_count()
-    return dict(ms_per_step=sec * 1e3 / steps, solves_per_s=newton / sec, cores=cores, steps=steps,
-                seconds=sec)
+    sample = f"{steps} time step(s) of {ws['name']} ({sec:.1f} s)"
+    if scale != 1.0:
+        sample += f", scaled x{scale:g} by subdomain count to {w['name']}"
+    return dict(ms_per_step=sec * 1e3 / steps * scale, solves_per_s=newton / (sec * scale), cores=cores,
+                steps=steps, seconds=sec, sample=sample)
 
 
 def sweep(args):
@@ -374,10 +461,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="slab32")
+    ap.add_argument("--workload", default="slab128")
+    ap.add_argument("--profile-steps", type=int, default=10, help="steps of the profiled passes (kernels, regions)")
+    ap.add_argument("--plain-steps", type=int, default=3, help="steps of the plain FP64 sample (0: skip)")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--method", default="bddc", choices=["bddc", "fetidp"])
-    ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--scaling", default="deluxe", choices=["deluxe", "rho"])
     ap.add_argument("--primal", default=None, choices=["V", "VE", "VEF"], help="override the workload's primal space")
     ap.add_argument("--precond-every", type=int, default=1, help="BDDC: rebuild the preconditioner every k Jacobians")
@@ -404,17 +492,18 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        # the oracle is the reference arm: bounded sample of the same workload (about 3 minutes at most)
+        # the oracle is the reference arm: a bounded sample of the workload (about 3 minutes at most)
         one = cpu_baseline(w, 1, args.method, args.scaling)
         steps = max(1, min(args.steps, int(150.0 / max(one["seconds"], 1e-3))))
         res = cpu_baseline(w, steps, args.method, args.scaling) if steps > 1 else one
         line = {"impl": "reference", "metric": METRIC, "value": res["ms_per_step"], "unit": "ms/time step",
                 "n_gpus": args.gpus, "steps": res["steps"], "warmup": 0, "ms_per_step": res["ms_per_step"],
                 "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-                "data": "synthetic", "config": {"workload": describe(w), "method": f"{args.method}-{args.scaling}", "krylov": "pcg"},
+                "data": "synthetic", "config": {"workload": describe(w), "method": f"{args.method}-{args.scaling}",
+                                                "krylov": "pcg"},
                 "krylov_solves_per_s": res["solves_per_s"],
                 "cpu_baseline": {"value": res["ms_per_step"], "unit": "ms/time step", "cores": res["cores"],
-                                 "kind": "oracle", "sample": f"{res['steps']} time step(s) of {w['name']}"},
+                                 "kind": "oracle", "sample": res["sample"]},
                 "e2e": {"value": res["ms_per_step"], "unit": "ms/time step", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
@@ -432,41 +521,54 @@ def main():
     tc_used = bool(args.tc and args.precision == "mixed")
     if ch["tune"] is not None:
         tc_used = bool(ch["tune"]["tensor_cores"])
-    roof, dom = roofline(ch["prof"], args.precision, tc_used)
+    nsub = int(np.prod([-(-w["n"][d] // w["s"][d]) for d in range(3)]))
+    profiled_regions = {k: dict(v, launches=v["launches"] * r["nprof"]) for k, v in ch["regions"].items()}
+    roof, roof_other = roofline(ch["prof"], profiled_regions, w, args.precision, tc_used, nsub)
     cpu = None
     if world == 1 and args.cpu_steps > 0:
         c = cpu_baseline(w, args.cpu_steps, args.method, args.scaling)
         cpu = {"value": c["ms_per_step"], "unit": "ms/time step", "cores": c["cores"], "kind": "oracle",
-               "sample": f"{c['steps']} time step(s) of {w['name']} ({c['seconds']:.1f} s)",
-               "krylov_solves_per_s": c["solves_per_s"]}
+               "sample": c["sample"], "krylov_solves_per_s": c["solves_per_s"]}
     nbytes = 3 * r["N"] * 8
+    el = 4 if args.precision == "mixed" else 8
     line = {
         "metric": METRIC, "value": ms, "unit": "ms/time step", "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32 local factors (tf32 tensor cores) + f64 Krylov/Newton/coarse solve" if args.precision == "mixed"
+        "vs_baseline": None,
+        "dtype": "f32 local factors (tf32 tensor cores) + f64 Krylov/Newton/coarse solve" if args.precision == "mixed"
         else "f64", "data": "synthetic",
-        "config": {"workload": describe(w), "unknowns": 2 * r["N"], "method": f"{args.method}-{args.scaling}",
-                   "krylov": "pcg", "precision": args.precision, "learned_guess": bool(args.learned),
+        "config": {"workload": describe(w), "unknowns": 2 * r["N"], "subdomains": nsub,
+                   "method": f"{args.method}-{args.scaling}", "krylov": "pcg", "precision": args.precision,
+                   "learned_guess": bool(args.learned),
+                   "learned_guess_schedule": f"untrained at step 0, trained online on the first {r['train_steps']} "
+                                             f"of the {K} timed steps",
                    "tensor_cores": tc_used, "precond_every": args.precond_every,
-                   "chord_newton": bool(args.lag and args.precision == "mixed"), "parallelism": "replicas" if world > 1 else "1 GPU",
-                   "l2": "per-step working set > 129 MB L2 (local matrices 0.27 GB f32 / 0.54 GB f64)"},
+                   "chord_newton": bool(args.lag and args.precision == "mixed"),
+                   "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "l2": f"inputs larger than L2 (129 MB): local matrices "
+                         f"{nsub * (2 * (w['s'][0] + 1) ** 3) ** 2 * el / 1e9:.1f} GB read every step"},
         "krylov_solves_per_s": ch["newton"] / sec,
         "dof_iterations_per_s": 2 * r["N"] * ch["krylov"] / sec,
         "newton_its": ch["newton"], "krylov_its": ch["krylov"], "cond_max": ch["cond"],
         "learned_guess": {"enabled": bool(args.learned), "steps_using_guess": ch["guess_used"],
                           "other_variant": {"learned_guess": bool(1 - args.learned),
                                             "ms_per_step": r["other"]["ms"] / K,
-                                            "krylov_its": r["other"]["krylov"], "newton_its": r["other"]["newton"]}},
+                                            "krylov_its": r["other"]["krylov"], "newton_its": r["other"]["newton"],
+                                            "steps_using_guess": r["other"]["guess_used"]}},
         "aggregate_steps_per_s": world * K / sec,
         "e2e": {"value": r["e2e_ms"] / K, "unit": "ms/time step", "h2d_bytes_per_step": nbytes,
-                "d2h_bytes_per_step": nbytes},
+                "d2h_bytes_per_step": nbytes, "host_buffers": "pinned",
+                "steps_using_guess": r["e2e_used"], "newton_its": r["e2e_newton"],
+                "same_solver_as_value": r["e2e_used"] == ch["guess_used"] and r["e2e_newton"] == ch["newton"]},
         "gpu_launches": ch["launches"],
         "autotune": ch["tune"],
         "roofline": roof,
-        "profiled_pass_ms_per_step": ch["prof_ms"] / K,
-        "regions_ms_per_step": {"pass_ms_per_step": ch["regions_ms"] / K,
-                                **{k: v["ms"] / K for k, v in ch["regions"].items()}},
-        "region_calls_per_step": {k: v["launches"] / K for k, v in ch["regions"].items()},
+        "roofline_other_parts": roof_other,
+        "profiled_pass": {"steps": r["nprof"], "ms_per_step": ch["prof_ms"], "newton_per_step": ch["prof_newton"],
+                          "krylov_per_step": ch["prof_krylov"]},
+        "regions_ms_per_step": {"pass_ms_per_step": ch["regions_ms"],
+                                **{k: v["ms"] for k, v in ch["regions"].items()}},
+        "region_calls_per_step": {k: v["launches"] for k, v in ch["regions"].items()},
         "kernels": {k: dict(v, avg_us=(v["ms"] * 1e3 / v["launches"] if v["launches"] else 0.0))
                     for k, v in ch["prof"].items()},
         "clocks": ch["clocks"],
@@ -474,9 +576,12 @@ def main():
         "failures": ch["bad"],
     }
     if pl is not None:
-        line["plain_fp64"] = {"ms_per_step": pl["ms"] / K, "krylov_solves_per_s": pl["newton"] / (pl["ms"] * 1e-3),
-                              "newton_its": pl["newton"], "krylov_its": pl["krylov"], "failures": pl["bad"]}
-        line["speedup_vs_plain_fp64"] = (pl["ms"] / K) / ms
+        npl = r["nplain"]
+        line["plain_fp64"] = {"steps": npl, "sample": f"the first {npl} of the {K} steps",
+                              "ms_per_step": pl["ms"] / npl, "krylov_solves_per_s": pl["newton"] / (pl["ms"] * 1e-3),
+                              "newton_its_per_step": pl["newton"] / npl, "krylov_its_per_step": pl["krylov"] / npl,
+                              "failures": pl["bad"]}
+        line["speedup_vs_plain_fp64"] = (pl["ms"] / npl) / ms
         line["v_rel_diff_vs_plain"] = r.get("v_rel_diff_vs_plain")
         line["ue_rel_diff_vs_plain"] = r.get("ue_rel_diff_vs_plain")
     print(json.dumps(line))

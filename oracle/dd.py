@@ -56,8 +56,12 @@ class DDSolver:
     """Per-Newton-step BDDC / FETI-DP solver of J s = f (SoA vectors)."""
 
     def __init__(self, prob, method="bddc", krylov="pcg", rtol=1e-8, atol=1e-10,
-                 dtol=1e4, maxit=1000, restart=30, scaling="deluxe", precond_every=1):
+                 dtol=1e4, maxit=1000, restart=30, scaling="deluxe", precond_every=1, keep_fetidp=True):
+        """keep_fetidp=False drops the two local blocks that only FETI-DP's preconditioner
+        reads (the transformed matrix and its interior factor): storage only, for large
+        BDDC runs; the arithmetic is unchanged."""
         self.prob = prob
+        self.keep_fetidp = keep_fetidp or method == "fetidp"
         self.method, self.krylov = method, krylov
         if scaling not in ("deluxe", "rho"):
             raise ValueError(scaling)
@@ -113,9 +117,10 @@ class DDSolver:
             Kb = B.T @ K @ B
             nD = len(L["dual"])
             nID = nI + nD
-            L["Kb"] = Kb
             L["KbIDID"] = sla.cho_factor(Kb[:nID, :nID])
-            L["KbII"] = sla.cho_factor(Kb[:nI, :nI])
+            if self.keep_fetidp:
+                L["Kb"] = Kb
+                L["KbII"] = sla.cho_factor(Kb[:nI, :nI])
             L["Sbar"] = T.T @ S @ T
             # coarse pieces (Section 4.4): solves with the I+Delta block
             KX = Kb[:nID, nID:]

@@ -312,6 +312,13 @@ class Solver:
                "bidomain_get_state")
         return ui, ue, w, t.value
 
+    def get_state_into(self, ui, ue, w):
+        """Download the state into caller-owned arrays (host numpy or CUDA tensors); returns t."""
+        t = C.c_double()
+        (a, d), (b, _), (c, _) = _ptr(ui, self.N), _ptr(ue, self.N), _ptr(w, self.N)
+        self._check(self._lib.bidomain_get_state(self._h, a, b, c, C.byref(t), d), "bidomain_get_state")
+        return t.value
+
     def step(self, stim=None):
         st = BdStepStats()
         s = _stim(stim)

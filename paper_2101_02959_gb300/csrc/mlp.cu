@@ -4,6 +4,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
 
 #include "mlp.cuh"
 
@@ -210,7 +211,9 @@ void mlp_backward(const MlpDev &m, int B, float inv_cnt, double *partial, cudaSt
 
 void mlp_adam(MlpDev &m, float lr, cudaStream_t s) {
   m.t += 1;
-  const float c1 = 1.f - powf(0.9f, (float)m.t), c2 = 1.f - powf(0.999f, (float)m.t);
+  // bias corrections 1 - beta^t in FP64: in FP32, 1 - 0.999^t loses about five digits
+  // to cancellation at small t
+  const float c1 = (float)(1.0 - std::pow(0.9, (double)m.t)), c2 = (float)(1.0 - std::pow(0.999, (double)m.t));
   const long long n = m.n_params;
   k_mlp_adam<<<(int)((n + 255) / 256), 256, 0, s>>>(n, m.w, m.g, m.am, m.av, nullptr, lr, c1, c2);
   count_launch();

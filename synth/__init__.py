@@ -16,6 +16,9 @@ Workloads (all Q1 hexahedral slabs, h = element size):
 * ``opt<k>``   (4k)^3 elements of a 0.8 cm cube, 4x4x4 subdomains, H/h = k.
 * ``slab128``  128x128x32 elements of a 3.2x3.2x0.8 cm slab, 16x16x4
                subdomains, H/h = 8 (1,098,306 unknowns).
+* ``coarse2k`` 32x32x4 elements of a 0.8x0.8x0.1 cm slab (h = 0.025 cm), 2^3-element
+               subdomains (16x16x2 = 512), V+E: 2,310 coarse unknowns on 5,445 nodes, so
+               the oracle's direct solve stays cheap.
 * ``ell8``     8x8x8 isoparametric elements of the truncated ellipsoid of
                Section 6 (phi in [-pi/2, 0], theta in [-3pi/8, pi/8], the wall
                r in [0, 1]), 2x2x2 subdomains, V+E primal space.
@@ -60,6 +63,7 @@ WORKLOADS = {
     "cube8vef": dict(n=(8, 8, 8), l=(0.4, 0.4, 0.4), s=(4, 4, 4), primal="VEF", steps=1),
     "slab32": dict(n=(32, 32, 16), l=(1.6, 1.6, 0.8), s=(8, 8, 8), primal="VE", steps=20),
     "slab128": dict(n=(128, 128, 32), l=(3.2, 3.2, 0.8), s=(8, 8, 8), primal="VE", steps=400),
+    "coarse2k": dict(n=(32, 32, 4), l=(0.8, 0.8, 0.1), s=(2, 2, 2), primal="VE", steps=2),
 }
 for _name, _n, _s in (("ell8", (8, 8, 8), (4, 4, 4)), ("ell10", (10, 9, 6), (4, 4, 4)),
                       ("ell32", (32, 32, 16), (8, 8, 8))):

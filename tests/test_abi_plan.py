@@ -76,7 +76,8 @@ def _oracle_sets(prob):
     return out
 
 
-@pytest.mark.parametrize("name", ["tiny", "cube8", "cube8ve", "cube8vef", "ragged", "opt4", "ell8", "ell10"])
+@pytest.mark.parametrize("name", ["tiny", "cube8", "cube8ve", "cube8vef", "ragged", "opt4", "ell8", "ell10",
+                                  "coarse2k"])
 def test_index_sets_bit_exact(lib, name):
     prob = oracle_problem(name)
     plan = binding.Plan(prob.workload)

@@ -67,9 +67,10 @@ def test_adam_matches_oracle_over_steps():
     got = s.mlp_params().astype(np.float64)
     moved = np.abs(p["w"] - w0)
     assert np.median(moved) > 1e-3  # the steps really moved the weights (about lr each)
-    # FP32 weights: a few units in the last place of each weight
-    ulp = np.spacing(np.abs(w0).astype(np.float32)).astype(np.float64)
-    assert np.all(np.abs(got - p["w"]) <= 8 * ulp + 1e-9)
+    # FP32 weights: a few units in the last place of each weight, plus FP32 rounding of
+    # the updates (each about lr in size)
+    ulp = np.spacing(np.maximum(np.abs(w0), np.abs(got)).astype(np.float32)).astype(np.float64)
+    assert np.all(np.abs(got - p["w"]) <= 8 * ulp + 6 * 1e-3 * 1e-6)
     s.mlp_reset()
     np.testing.assert_array_equal(s.mlp_params(), w0)  # back to the initial draw
 

@@ -447,3 +447,41 @@ def test_line_search_step_matches_oracle():
     assert _rel(gui - gue, rui - rue) < 1e-9
     assert _rel(gue, rue) < 1e-9
     s.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("mixed", 1e-8), ("fp64", 1e-9)])
+def test_coarse_problem_above_1024_unknowns(precision, tol):
+    """2,310 coarse unknowns (coarse2k: 512 subdomains of 2^3 elements, V+E): the coarse
+    solve stays FP64 at this size (explicit inverse in the local precision plus FP64
+    refinement against the assembled S_PiPi, Section 4.4), so the time steps match the
+    oracle's at the tight tolerances, and the FP64 BDDC and FETI-DP Jacobian solves
+    reach the direct solution to 1e-10."""
+    name = "coarse2k"
+    prob = oracle_problem(name)
+    assert prob.part.n_primal > 1024
+    ref = _oracle_steps_direct(prob, 2)
+    s = _solver(name, precision=precision, ksp_rtol=1e-12, ksp_atol=0.0, snes_rtol=1e-10, snes_atol=1e-16,
+                use_graphs=1)
+    ui, ue, w = synth.initial_state(prob.N, 0)
+    s.set_state(ui, ue, w, 0.0)
+    for n in range(2):
+        st = s.step(synth.stimulus(prob.workload))
+        assert st["reason"] == 0
+        gui, gue, _, _ = s.get_state()
+        assert _rel(gui - gue, ref[n][0] - ref[n][1]) < tol
+        assert _rel(gue, ref[n][1]) < tol
+    s.close()
+    if precision != "fp64":
+        return
+    st_ = _state(prob)
+    wn = ionic.gating_step(st_[0] - st_[1], st_[2], prob.tau, prob.p)
+    r_i, r_e = prob.residual(st_[0], st_[1], wn, st_[0] - 1.0, st_[1], prob.tau)
+    kc = prob.kc(st_[0], st_[1], wn)
+    si, se, _ = direct_solve(prob, kc, -r_i, -r_e)
+    for method in ("bddc", "fetidp"):
+        s = _solver(name, method=method, precision="fp64", ksp_rtol=1e-13, ksp_atol=0.0)
+        s.linearize(st_[0], st_[1], wn)
+        x, sst = s.krylov_solve(-np.concatenate([r_i, r_e]))
+        assert sst["reason"] == 0
+        assert _rel(x, np.concatenate([si, se])) < 1e-10, method
+        s.close()
