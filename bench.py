@@ -37,14 +37,20 @@ sys.path.insert(0, ROOT)
 METRIC = "ms/time step and Krylov solves/s at rel. res 1e-8, chosen vs plain FP64 GPU"
 
 
-def describe(w):
+def describe(w, n_sub=None):
     nx, ny, nz = w["n"]
     sx, sy, sz = w["s"]
+    nb = [-(-n // b) for n, b in zip(w["n"], w["s"])]
+    if "shell" in w:
+        (ai, bi, ci), (ao, bo, co) = w["shell"]["inner"], w["shell"]["outer"]
+        h = w["l"][0] / nx
+        return (f"{w['name']}: masked Q1 box grid {nx}x{ny}x{nz}, h={h:g} cm, keeping the lower half of the "
+                f"ellipsoidal wall between semi-axes ({ai:g},{bi:g},{ci:g}) and ({ao:g},{bo:g},{co:g}) cm; "
+                f"{sx}^3-element blocks split into {n_sub} uneven subdomains, primal {w['primal']}, tau=0.05 ms")
     if "ellipsoid" in w:
         dom = "isoparametric Q1 truncated ellipsoid (Section 6)"
     else:
         dom = f"Q1 slab {w['l'][0]}x{w['l'][1]}x{w['l'][2]} cm"
-    nb = [-(-n // b) for n, b in zip(w["n"], w["s"])]
     return (f"{w['name']}: {nx}x{ny}x{nz} {dom}, "
             f"{nb[0]}x{nb[1]}x{nb[2]} subdomains H/h={sx}, primal {w['primal']}, tau=0.05 ms")
 
@@ -126,7 +132,10 @@ def run_gpu(args, w, rank, world):
     binding.load()
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    N = synth.n_nodes(w)
+    probe = binding.Plan(w)  # host-only plan: node count and subdomain sizes (masked grids too)
+    N = probe.sizes()["n_node"]
+    sub_nodes = np.diff(probe.index_set("SUB_NODE_PTR"))
+    del probe
     ui0, ue0, w0 = synth.initial_state(N, 0)
     dstate = [torch.from_numpy(a).cuda() for a in (ui0, ue0, w0)]
     K = args.steps
@@ -235,7 +244,7 @@ def run_gpu(args, w, rank, world):
     s.close()
 
     out = dict(chosen=chosen, plain=plain, other=other, e2e_ms=e2e_ms, e2e_newton=e2e_newton, e2e_used=e2e_used,
-               N=N, K=K, nplain=nplain, nprof=nprof, train_steps=train_steps)
+               N=N, K=K, nplain=nplain, nprof=nprof, train_steps=train_steps, sub_nodes=sub_nodes)
     if plain is not None and nplain == K:
         a, b = chosen["final"], plain["final"]
         va, vb = (a[0] - a[1]).double(), (b[0] - b[1]).double()
@@ -281,7 +290,9 @@ TRAFFIC = {
     "k_rankk_tc": {"bytes_per_launch": None, "sha": None, "file": "tc.cu",
                    "span": ("__global__ void __launch_bounds__(128, 1) k_rankk_tc(",
                             "static constexpr int kTcSmem")},
-    "k_gemv": {"bytes_per_launch": None, "sha": None, "file": "dense.cu",
+    # DRAM bytes per library byte (slab32 capture, profiles/gemv_slab32_traffic.md): the operator
+    # and local-solve launches read their matrices once; scaled to a launch by its own bytes
+    "k_gemv": {"dram_per_library_byte": 1.013, "sha": "2c1f86b0689c36b0", "file": "dense.cu",
                "span": ("__global__ void __launch_bounds__(256) k_gemv(",
                         "// y[a] = (acc ? y[a] : 0) + alpha sum_p A[p][a] x[p]")},
 }
@@ -299,11 +310,15 @@ def kernel_sha(name):
     return hashlib.sha256(src[a:b].encode()).hexdigest()[:16]
 
 
-def traffic(name):
+def traffic(name, library_bytes=None):
+    """DRAM bytes per launch from the ncu capture, while the kernel's source is the captured one:
+    an absolute figure, or a ratio to the launch's own library bytes."""
     t = TRAFFIC.get(name)
-    if not t or t["bytes_per_launch"] is None:
+    if not t or kernel_sha(name) != t["sha"]:
         return None
-    return t["bytes_per_launch"] if kernel_sha(name) == t["sha"] else None
+    if t.get("dram_per_library_byte") is not None and library_bytes is not None:
+        return t["dram_per_library_byte"] * library_bytes
+    return t.get("bytes_per_launch")
 
 
 def device_fp32_peak(dev=0):
@@ -314,13 +329,22 @@ def device_fp32_peak(dev=0):
     return sms * 128 * 2 * mhz * 1e6 / 1e12, f"derived: {sms} SMs (device) x 128 FP32 lanes x 2 flop x {mhz:.0f} MHz"
 
 
-def roofline(prof, regions, w, precision, tc_used, nsub):
+def equivalent_sides(sub_nodes):
+    """H/h of a box subdomain with the same node count as each subdomain ((k + 1)^3 nodes): exact
+    for box subdomains, an equivalent size for the pieces of a masked grid."""
+    return np.maximum(1, np.rint(np.cbrt(np.asarray(sub_nodes, float)) - 1.0)).astype(int)
+
+
+def roofline(prof, regions, w, precision, tc_used, sub_nodes):
     """The dominant part of a step against its roofline, with the method's ALGORITHMIC work:
     the factorisation kernels (panel + rank-k classes) per Jacobian against the tensor pipe
     (3xTF32) / FP32 / FP64 peak, or the Krylov local-solve GEMVs per iteration against HBM.
     Both figures are returned; `roofline` is the one that takes more of the step."""
     pk = peaks()
-    k = w["s"][0]
+    ks = equivalent_sides(sub_nodes)
+    nsub = len(ks)
+    k = int(np.max(ks))
+    uneven = bool(np.any(ks != ks[0]))
     el = 4 if precision == "mixed" else 8
     n_jac = regions["linearize"]["launches"]
     out = {}
@@ -328,7 +352,7 @@ def roofline(prof, regions, w, precision, tc_used, nsub):
     f_ms = prof["panel"]["ms"] + prof["rankk"]["ms"]
     f_launch = prof["panel"]["launches"] + prof["rankk"]["launches"]
     if f_ms > 0 and n_jac > 0:
-        algo = factor_flops_per_sub(k) * nsub * n_jac
+        algo = sum(factor_flops_per_sub(int(kj)) for kj in ks) * n_jac
         lib = prof["panel"]["flops"] + prof["rankk"]["flops"]
         if precision == "mixed" and tc_used:
             src = "bf16_tflops_sustained" if "bf16_tflops_sustained" in pk else None
@@ -350,23 +374,30 @@ def roofline(prof, regions, w, precision, tc_used, nsub):
             "peak_source": psrc, "launches": f_launch, "avg_launch_us": f_ms * 1e3 / f_launch,
             "ms_per_jacobian": f_ms / n_jac,
             "algorithmic_flops_per_jacobian": algo / n_jac, "library_flops_per_jacobian": lib / n_jac,
-            "work": f"{factor_flops_per_sub(k):.3g} flop per H/h={k} subdomain x {nsub} subdomains "
+            "work": (f"{factor_flops_per_sub(k):.3g} flop per H/h={k} subdomain x {nsub} subdomains "
+                     if not uneven else f"sum over {nsub} uneven subdomains of the flops of a box of the same node "
+                     f"count (H/h {ks.min()}..{ks.max()}) ") +
                     "(banded Dirichlet + Neumann factors, L_II^-1 K_IG, face SYRKs, Phi)"}
     # Krylov: one Dirichlet + one Neumann local solve per subdomain and iteration
     g = prof["gemv"]
     if g["ms"] > 0 and g["launches"] > 0:
+        vals = sum(sum(solve_values_per_sub(int(kj))) for kj in ks)
         vd, vn = solve_values_per_sub(k)
-        algo = (g["launches"] / 2.0) * nsub * (vd + vn) * el
+        algo = (g["launches"] / 2.0) * vals * el
         ach = algo / (g["ms"] * 1e-3) / 1e9
         peak = pk.get("hbm_gbs", 6800.0)
         out["krylov"] = {
             "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "traffic": traffic("k_gemv"), "kernel": "k_gemv (operator and local constrained solve, per launch)",
+            "traffic": traffic("k_gemv", g["bytes"] / g["launches"]),
+            "kernel": "k_gemv (operator and local constrained solve, per launch)",
             "peak_source": "of measured" if "fallback" not in pk else "of fallback",
             "launches": g["launches"], "avg_launch_us": g["ms"] * 1e3 / g["launches"],
             "algorithmic_bytes_per_launch": algo / g["launches"], "library_bytes_per_launch": g["bytes"] / g["launches"],
-            "work": f"{vd + vn:.3g} factor values per H/h={k} subdomain and iteration (Dirichlet + Neumann "
-                    f"solve, read forward and back) x {nsub} subdomains x {el} B, split over the 2 GEMV launches"}
+            "work": (f"{vd + vn:.3g} factor values per H/h={k} subdomain and iteration (Dirichlet + Neumann "
+                     f"solve, read forward and back) x {nsub} subdomains" if not uneven else
+                     f"factor values of one Dirichlet + one Neumann solve (read forward and back) summed over "
+                     f"{nsub} uneven subdomains as boxes of the same node count") +
+                    f" x {el} B, split over the 2 GEMV launches"}
     if not out:
         return None, None
     dom = max(out, key=lambda c: (prof["panel"]["ms"] + prof["rankk"]["ms"]) if c == "factorisation"
@@ -521,9 +552,9 @@ def main():
     tc_used = bool(args.tc and args.precision == "mixed")
     if ch["tune"] is not None:
         tc_used = bool(ch["tune"]["tensor_cores"])
-    nsub = int(np.prod([-(-w["n"][d] // w["s"][d]) for d in range(3)]))
+    nsub = len(r["sub_nodes"])
     profiled_regions = {k: dict(v, launches=v["launches"] * r["nprof"]) for k, v in ch["regions"].items()}
-    roof, roof_other = roofline(ch["prof"], profiled_regions, w, args.precision, tc_used, nsub)
+    roof, roof_other = roofline(ch["prof"], profiled_regions, w, args.precision, tc_used, r["sub_nodes"])
     cpu = None
     if world == 1 and args.cpu_steps > 0:
         c = cpu_baseline(w, args.cpu_steps, args.method, args.scaling)
@@ -537,7 +568,7 @@ def main():
         "vs_baseline": None,
         "dtype": "f32 local factors (tf32 tensor cores) + f64 Krylov/Newton/coarse solve" if args.precision == "mixed"
         else "f64", "data": "synthetic",
-        "config": {"workload": describe(w), "unknowns": 2 * r["N"], "subdomains": nsub,
+        "config": {"workload": describe(w, nsub), "unknowns": 2 * r["N"], "subdomains": nsub,
                    "method": f"{args.method}-{args.scaling}", "krylov": "pcg", "precision": args.precision,
                    "learned_guess": bool(args.learned),
                    "learned_guess_schedule": f"untrained at step 0, trained online on the first {r['train_steps']} "
@@ -546,7 +577,7 @@ def main():
                    "chord_newton": bool(args.lag and args.precision == "mixed"),
                    "parallelism": "replicas" if world > 1 else "1 GPU",
                    "l2": f"inputs larger than L2 (129 MB): local matrices "
-                         f"{nsub * (2 * (w['s'][0] + 1) ** 3) ** 2 * el / 1e9:.1f} GB read every step"},
+                         f"{float(np.sum((2.0 * r['sub_nodes']) ** 2)) * el / 1e9:.1f} GB read every step"},
         "krylov_solves_per_s": ch["newton"] / sec,
         "dof_iterations_per_s": 2 * r["N"] * ch["krylov"] / sec,
         "newton_its": ch["newton"], "krylov_its": ch["krylov"], "cond_max": ch["cond"],

@@ -292,6 +292,19 @@ int fetidp_operator(bd_handle *h, const double *lambda, double *y, int on_device
  * (SoA).  The u_e correction at the gauge node is 0.  stats may be NULL. */
 int krylov_solve(bd_handle *h, const double *f, double *s, int on_device, bd_solve_stats *stats);
 
+/* ---- coarse problem of the current Jacobian (Section 4.4) --------------------------
+ * S_PiPi = sum_j R_Pi^T S_PiPi^(j) R_Pi as assembled for the preconditioner, in FP64,
+ * as CSR over the global primal dofs (columns ascending; the gauge row and column are
+ * the unit vector), and its solve as every preconditioner application performs it: the
+ * explicit inverse followed by `nref` steps of FP64 iterative refinement
+ * z += X (c - S_PiPi z) (nref < 0: the handle's own count).  Up to 320 coarse unknowns
+ * the inverse is brought to FP64 once per Jacobian (Newton-Schulz) and refined once per
+ * solve; above, it is kept in the local precision (FP32 in BD_MIXED, refined 3 times per
+ * solve; FP64 in BD_FP64, refined once).  Host buffers; the handle must be linearised. */
+int bidomain_coarse_size(bd_handle *h, int *n_primal, int *nnz);
+int bidomain_coarse_matrix(bd_handle *h, int *rowptr, int *col, double *val);
+int bidomain_coarse_solve(bd_handle *h, const double *c, double *z, int nref);
+
 /* ---- autotuner (not in the paper) ----------------------------------------------
  * Times the whole factorisation sequence of bidomain_linearize (CUDA events,
  * best of two after a warm-up) at the current Jacobian for every combination of

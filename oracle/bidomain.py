@@ -42,7 +42,7 @@ from .mesh import DofMaps, Mesh, Partition
 class Problem:
     def __init__(self, w, sigma_i, sigma_e, ionic_p, tau, stimulus):
         self.workload = w
-        self.mesh = Mesh(w["n"], w.get("l"), ellipsoid=w.get("ellipsoid"))
+        self.mesh = Mesh(w["n"], w.get("l"), elem_mask=w.get("mask"), ellipsoid=w.get("ellipsoid"))
         self.part = Partition(self.mesh, w["s"], w.get("primal", "V"))
         self.dofs = DofMaps(self.part)
         self.fem = FEM(self.mesh, sigma_i, sigma_e)

@@ -14,6 +14,9 @@ Readings (the paper leaves these open):
 * nodes on the outer boundary belong to the class of their N_x (the paper
   counts Neumann-boundary nodes as ordinary, not special);
 * classes are ordered by (type, smallest node id) with vertex < edge < face;
+* a subdomain fragment with no vertex on its interface (masked grids) promotes the
+  lowest-id node of each of its edge classes (of its face classes if it has no
+  edge) to a vertex, the rest of the class being split again into classes;
 * primal sets: "V" = vertex classes, "VE" = vertices and edges, "VEF" =
   vertices, edges and faces (Section 6, Test 3 and Table 7); an edge or face
   class holds its average as the primal dof and n - 1 deviations as dual dofs.
@@ -174,13 +177,9 @@ class Partition:
                         seen[z] = True
                         stack.append(z)
             comp = sorted(comp)
-            k = len(self.N[x])
-            if k == 2:
-                t = FACE
-            else:
-                t = EDGE if len(comp) > 1 else VERTEX
-            classes.append((t, comp[0], np.array(comp, np.int64), self.N[x]))
+            classes.append(_make_class(comp, self.N[x]))
         classes.sort(key=lambda c: (c[0], c[1]))
+        classes = self._promote_vertices(classes, adj)
         self.cls_type = np.array([c[0] for c in classes], np.int64)
         self.cls_nodes = [c[2] for c in classes]
         self.cls_subs = [c[3] for c in classes]
@@ -188,6 +187,43 @@ class Partition:
         self.node_cls = -np.ones(m.n_node, np.int64)
         for c, nodes in enumerate(self.cls_nodes):
             self.node_cls[nodes] = c
+
+    def _promote_vertices(self, classes, adj):
+        """A subdomain fragment of a masked grid may have no vertex on its interface (reading
+        of Section 4.2 for non-box subdomains): for subdomains j = 0, 1, ... in order, one
+        without a vertex class promotes the lowest-id node of each of its edge classes (of
+        its face classes if it has no edge) to a vertex class of its own; the rest of each
+        such class is split again into connected classes by the usual rule; the classes
+        are re-sorted by (type, smallest node) after every subdomain."""
+        for j in range(self.n_sub):
+            mine = [c for c in classes if j in c[3]]
+            if any(c[0] == VERTEX for c in mine):
+                continue
+            cand = [c for c in mine if c[0] == EDGE] or [c for c in mine if c[0] == FACE]
+            if not cand:
+                continue
+            drop = {id(c) for c in cand}
+            out = [c for c in classes if id(c) not in drop]
+            for c in cand:
+                nodes = [int(v) for v in c[2]]
+                out.append((VERTEX, nodes[0], np.array(nodes[:1], np.int64), c[3]))
+                rest = set(nodes[1:])
+                seen = set()
+                for x in sorted(rest):
+                    if x in seen:
+                        continue
+                    stack, comp = [x], []
+                    seen.add(x)
+                    while stack:
+                        y = stack.pop()
+                        comp.append(y)
+                        for z in adj[y]:
+                            if z in rest and z not in seen:
+                                seen.add(z)
+                                stack.append(z)
+                    out.append(_make_class(sorted(comp), c[3]))
+            classes = sorted(out, key=lambda c: (c[0], c[1]))
+        return classes
 
     def _primal(self):
         kinds = {"V": (VERTEX,), "VE": (VERTEX, EDGE), "VEF": (VERTEX, EDGE, FACE)}[self.primal_kind]
@@ -219,6 +255,14 @@ class Partition:
     def iface_nodes_of(self, j):
         nodes = self.sub_nodes[j]
         return nodes[self.mult[nodes] >= 2]
+
+
+def _make_class(comp, subs):
+    """(type, smallest node, nodes, N_x) of a connected set of interface nodes with the
+    same N_x: a face when two subdomains share it, else an edge (several nodes) or a
+    vertex (one node)."""
+    t = FACE if len(subs) == 2 else (EDGE if len(comp) > 1 else VERTEX)
+    return (t, comp[0], np.array(comp, np.int64), subs)
 
 
 def _components_of_elements(conn, elems):

@@ -35,7 +35,8 @@ EXPORTED = ["bd_plan_create", "bd_plan_sizes", "bd_plan_index_sets", "bd_plan_de
             "schur_apply", "bddc_apply", "fetidp_apply", "fetidp_operator", "krylov_solve", "bidomain_profile",
             "bidomain_profile_read", "bidomain_launch_count", "schur_apply_noalloc", "bidomain_mlp_sizes",
             "bidomain_mlp_params", "bidomain_mlp_loss_grad", "bidomain_mlp_adam_step",
-            "bidomain_mlp_reset", "bidomain_autotune", "bidomain_destroy",
+            "bidomain_mlp_reset", "bidomain_coarse_size", "bidomain_coarse_matrix",
+            "bidomain_coarse_solve", "bidomain_autotune", "bidomain_destroy",
             "bidomain_strerror", "bidomain_last_error"]
 PROF = dict(rankk=0, panel=1, gemv=2, resid=3)                    # kernel classes
 REGIONS = dict(linearize=4, krylov=5, trsv=6, mlp=7, step=8)      # regions of a step
@@ -134,6 +135,9 @@ def load(build_if_missing: bool = False):
         "bidomain_mlp_loss_grad": (I, [P, P, P, P, C.POINTER(D), P]),
         "bidomain_mlp_adam_step": (I, [P, P, D]),
         "bidomain_mlp_reset": (I, [P]),
+        "bidomain_coarse_size": (I, [P, C.POINTER(I), C.POINTER(I)]),
+        "bidomain_coarse_matrix": (I, [P, P, P, P]),
+        "bidomain_coarse_solve": (I, [P, P, P, I]),
         "bidomain_autotune": (I, [P, C.POINTER(BdTuneResult)]),
         "bidomain_destroy": (I, [P]),
         "bidomain_strerror": (C.c_char_p, [I]),
@@ -172,7 +176,10 @@ def _check(code, where, handle=None):
         raise BidomainError(code, where, handle)
 
 
-def _mesh(w, mask=None):
+def _mesh(w):
+    """bd_mesh of a workload dict; its "mask" (uint8 per element, kept alive by w) is
+    passed as elem_mask."""
+    mask = w.get("mask")
     m = BdMesh()
     m.n[:] = list(w["n"])
     m.s[:] = list(w["s"])
@@ -184,6 +191,8 @@ def _mesh(w, mask=None):
         m.axes[:] = list(ell["axes"])
         m.phi[:] = list(ell["phi"])
         m.theta[:] = list(ell["theta"])
+    if mask is not None:
+        assert mask.dtype == np.uint8 and mask.flags["C_CONTIGUOUS"] and mask.size == int(np.prod(w["n"]))
     m.elem_mask = None if mask is None else mask.ctypes.data
     return m
 
@@ -415,6 +424,25 @@ class Solver:
     def mlp_reset(self):
         """Back to the untrained network (initial weights, zero Adam state, no history)."""
         self._check(self._lib.bidomain_mlp_reset(self._h), "bidomain_mlp_reset")
+
+    def coarse_matrix(self):
+        """S_PiPi of the current Jacobian as (rowptr, col, val) numpy arrays (FP64 CSR)."""
+        np_, nnz = C.c_int(), C.c_int()
+        self._check(self._lib.bidomain_coarse_size(self._h, C.byref(np_), C.byref(nnz)), "bidomain_coarse_size")
+        ptr = np.zeros(np_.value + 1, np.int32)
+        col = np.zeros(max(nnz.value, 1), np.int32)
+        val = np.zeros(max(nnz.value, 1))
+        self._check(self._lib.bidomain_coarse_matrix(self._h, ptr.ctypes.data, col.ctypes.data, val.ctypes.data),
+                    "bidomain_coarse_matrix")
+        return ptr, col[:nnz.value], val[:nnz.value]
+
+    def coarse_solve(self, c, nref=-1):
+        """The coarse solve z = S_PiPi^-1 c as the preconditioner performs it."""
+        c = np.ascontiguousarray(c, dtype=np.float64)
+        z = np.zeros_like(c)
+        self._check(self._lib.bidomain_coarse_solve(self._h, c.ctypes.data, z.ctypes.data, int(nref)),
+                    "bidomain_coarse_solve")
+        return z
 
     def krylov_solve(self, f):
         out = _same_kind(f, 2 * self.N)

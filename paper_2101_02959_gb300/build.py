@@ -19,7 +19,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libbidomain.so")
-SOURCES = ["plan.cpp", "fem.cu", "dense.cu", "dd.cu", "mlp.cu", "tc.cu", "api.cu"]
+SOURCES = ["plan.cpp", "fem.cu", "dense.cu", "dd.cu", "mlp.cu", "gemm_tc.cu", "tc.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -233,8 +233,11 @@ struct bd_handle {
   int *d_co_rptr = nullptr, *d_co_row = nullptr, *d_co_col = nullptr, *d_co_sptr = nullptr;
   long long *d_co_src = nullptr;
   double *d_Co64 = nullptr, *d_co_c = nullptr, *d_co_rho = nullptr;
+  int *d_co_noptr = nullptr;  // np + 1 zeros: empty assembly lists (a coarse solve of a given c)
+  // small coarse problems: dense FP64 S_PP, its FP64 inverse, Newton-Schulz scratch
+  double *d_Co64d = nullptr, *d_CoInv64 = nullptr, *d_CoW = nullptr, *d_CoY = nullptr;
   CoarseSolve cs;
-  GemvSet gv_schur, gv_local, gv_psit, gv_coarse, gv_coarse_acc, gv_sdd, gv_lgi, gv_lgit, gv_drest, gv_dext;
+  GemvSet gv_schur, gv_local, gv_psit, gv_sdd, gv_lgi, gv_lgit, gv_drest, gv_dext;
   GemmTask *d_gemm = nullptr;
   int n_gemm = 0;
   int *d_ext_idx = nullptr;
@@ -267,7 +270,10 @@ struct bd_handle {
   MlpDev mlp;
   bool mlp_on = false;
   int hist_count = 0, mlp_steps_trained = 0;
-  int *d_node_ptr = nullptr, *d_node_ent = nullptr;
+  int n_tr_ent = 0;  // trace entries (subdomain, interface node of it)
+  int *d_t_sub = nullptr, *d_t_pos = nullptr, *d_t_node = nullptr;
+  int *d_tr_ptr = nullptr, *d_tr_ent = nullptr;  // interface node -> its trace entries (j * n_tr + a)
+  double *d_dG = nullptr;                        // predicted interface increment (2g + field)
   double *d_uh1i, *d_uh1e, *d_uh2i, *d_uh2e, *d_gi, *d_ge;
   double rtol_scale = 1.0;
   // factorisation tuning (bidomain_autotune): outer panel width, batch groups, tensor cores
@@ -330,12 +336,17 @@ void setup_mlp(bd_handle &h) {
   DevMem &m = h.mem;
   cudaStream_t s = h.s;
   MlpDev &M = h.mlp;
-  int maxq = 0;
-  for (auto &sp : h.plan.subs) maxq = std::max(maxq, (int)sp.nodes.size());
-  M.maxq = maxq;
+  // trace nodes of subdomain j: its interface nodes, in its local order
+  int n_tr = 0;
+  for (auto &sp : h.plan.subs) n_tr = std::max(n_tr, (int)sp.nodes.size() - sp.n_interior);
+  M.n_tr = n_tr;
   M.batch = h.nsub;
-  M.n_in = 6 * maxq;
-  M.n_out = 2 * maxq;
+  M.n_in = 6 * n_tr;
+  M.n_out = 2 * n_tr;
+  auto pad64 = [](int n) { return (n + 63) & ~63; };
+  M.ld_in = pad64(M.n_in);
+  M.ld_out = pad64(M.n_out);
+  M.ld_b = pad64(M.batch);
   const int H = M.n_hidden, B = M.batch;
   M.off_W1 = 0;
   M.off_b1 = M.off_W1 + (long long)H * M.n_in;
@@ -348,37 +359,63 @@ void setup_mlp(bd_handle &h) {
   M.g = m.alloc<float>(M.n_params);
   M.am = m.alloc<float>(M.n_params);
   M.av = m.alloc<float>(M.n_params);
-  ck(cudaMemsetAsync(M.am, 0, sizeof(float) * M.n_params, s), "memset");
-  ck(cudaMemsetAsync(M.av, 0, sizeof(float) * M.n_params, s), "memset");
   M.b1 = M.w + M.off_b1;
   M.b2 = M.w + M.off_b2;
   M.b3 = M.w + M.off_b3;
-  M.Wb1 = m.alloc<__nv_bfloat16>((size_t)H * M.n_in);
-  M.Wb2 = m.alloc<__nv_bfloat16>((size_t)H * H);
-  M.Wb3 = m.alloc<__nv_bfloat16>((size_t)M.n_out * H);
-  M.X = m.alloc<float>((size_t)B * M.n_in);
+  // bf16 operand buffers: zeroed once, so their padding stays zero
+  auto bf = [&](size_t n) {
+    __nv_bfloat16 *p = m.alloc<__nv_bfloat16>(n);
+    ck(cudaMemsetAsync(p, 0, sizeof(__nv_bfloat16) * n, s), "memset");
+    return p;
+  };
+  M.W1b = bf((size_t)H * M.ld_in);
+  M.W2b = bf((size_t)H * H);
+  M.W2bT = bf((size_t)H * H);
+  M.W3b = bf((size_t)M.n_out * H);
+  M.W3bT = bf((size_t)H * M.ld_out);
+  M.Xb = bf((size_t)B * M.ld_in);
+  M.XbT = bf((size_t)M.n_in * M.ld_b);
+  M.H1b = bf((size_t)B * H);
+  M.H1bT = bf((size_t)H * M.ld_b);
+  M.H2b = bf((size_t)B * H);
+  M.H2bT = bf((size_t)H * M.ld_b);
+  M.dYb = bf((size_t)B * M.ld_out);
+  M.dYbT = bf((size_t)M.n_out * M.ld_b);
+  M.dZ2b = bf((size_t)B * H);
+  M.dZ2bT = bf((size_t)H * M.ld_b);
+  M.dZ1bT = bf((size_t)H * M.ld_b);
   M.Z1 = m.alloc<float>((size_t)B * H);
-  M.H1 = m.alloc<float>((size_t)B * H);
   M.Z2 = m.alloc<float>((size_t)B * H);
-  M.H2 = m.alloc<float>((size_t)B * H);
   M.Y = m.alloc<float>((size_t)B * M.n_out);
   M.T = m.alloc<float>((size_t)B * M.n_out);
   M.mask = m.alloc<float>((size_t)B * M.n_out);
+  M.Xf = m.alloc<float>((size_t)B * M.n_in);
   M.dY = m.alloc<float>((size_t)B * M.n_out);
-  M.dZ1 = m.alloc<float>((size_t)B * H);
   M.dZ2 = m.alloc<float>((size_t)B * H);
-  ck(cudaMemsetAsync(M.X, 0, sizeof(float) * B * M.n_in, s), "memset");
+  M.dZ1 = m.alloc<float>((size_t)B * H);
   mlp_init_weights(h);
-  // node -> (subdomain, local node) entries for the prediction average
-  std::vector<std::vector<int>> lists(h.N);
+  // trace entries and, per interface node, the entries holding it (prediction average)
+  std::vector<int> t_sub, t_pos, t_node;
+  std::vector<std::vector<int>> lists(h.nif / 2);
   for (int j = 0; j < h.nsub; ++j) {
     const SubPlan &sp = h.plan.subs[j];
-    for (int a = 0; a < (int)sp.nodes.size(); ++a) lists[sp.nodes[a]].push_back(j * maxq + a);
+    for (int a = 0; a + sp.n_interior < (int)sp.nodes.size(); ++a) {
+      const int x = sp.nodes[sp.n_interior + a];
+      t_sub.push_back(j);
+      t_pos.push_back(a);
+      t_node.push_back(x);
+      lists[h.plan.node_to_iface[x]].push_back(j * n_tr + a);
+    }
   }
+  h.n_tr_ent = (int)t_sub.size();
+  h.d_t_sub = m.upload(t_sub, s);
+  h.d_t_pos = m.upload(t_pos, s);
+  h.d_t_node = m.upload(t_node, s);
   std::vector<int> ptr(1, 0), ent;
   for (auto &l : lists) { for (int v : l) ent.push_back(v); ptr.push_back((int)ent.size()); }
-  h.d_node_ptr = m.upload(ptr, s);
-  h.d_node_ent = m.upload(ent, s);
+  h.d_tr_ptr = m.upload(ptr, s);
+  h.d_tr_ent = m.upload(ent, s);
+  h.d_dG = m.alloc<double>(h.nif);
   double **hv[] = {&h.d_uh1i, &h.d_uh1e, &h.d_uh2i, &h.d_uh2e, &h.d_gi, &h.d_ge};
   for (double **v : hv) *v = m.alloc<double>(h.N);
   h.mlp_on = true;
@@ -388,8 +425,8 @@ void setup_mlp(bd_handle &h) {
 // returns nothing (the loss lands in d_scal[4] when `want_loss`).
 void mlp_train_once(bd_handle &h, bool want_loss) {
   MlpDev &M = h.mlp;
-  mlp_forward(M, M.batch, h.s);
-  mlp_backward(M, M.batch, 1.f / (2.f * h.nq), h.d_partial, h.s);
+  mlp_forward(M, h.d_err, h.s);
+  mlp_backward(M, 1.f / (2.f * h.n_tr_ent), h.d_partial, h.d_err, h.s);
   if (want_loss) launch_sum_partials(kRedBlocks, h.d_partial, h.d_scal + 4, h.s);
   mlp_adam(M, (float)h.opt.mlp_lr, h.s);
 }
@@ -748,6 +785,14 @@ void setup_handle(bd_handle &h) {
     h.d_Co64 = m.alloc<double>(h.co_nnz);
     h.d_co_c = m.alloc<double>(np);
     h.d_co_rho = m.alloc<double>(np);
+    h.d_co_noptr = m.upload(std::vector<int>(np + 1, 0), s);
+    if (np <= kCoarseSmall) {
+      const size_t nn = (size_t)np * np;
+      h.d_Co64d = m.alloc<double>(nn);
+      h.d_CoInv64 = m.alloc<double>(nn);
+      h.d_CoW = m.alloc<double>(nn);
+      h.d_CoY = m.alloc<double>(nn);
+    }
   }
   // ---- GEMV and copy task sets
   auto gset = [&](const std::vector<GemvDesc> &v) {
@@ -801,22 +846,23 @@ void setup_handle(bd_handle &h) {
   h.gv_sdd = gset(g_sdd);
   h.gv_lgi = gset(g_lgi);
   h.gv_lgit = gset(g_lgit);
-  h.gv_coarse = gset({GemvDesc{0, h.np, h.np, h.np, 0, 0, 0}});
-  h.gv_coarse_acc = gset({GemvDesc{0, h.np, h.np, h.np, 0, 0, 2}});
+
   {
     CoarseSolve &c = h.cs;
     c.np = h.np;
     c.gauge = h.gauge_primal;
-    // refinement steps: one restores FP64 backward stability of the FP64 explicit
-    // inverse; from an FP32 inverse each step gains about -log10(u32 cond(S_PP)) digits
-    c.nref = h.mixed() ? 3 : 1;
+    // refinement steps: one restores FP64 backward stability of an FP64 explicit inverse
+    // (small problems: refined to FP64 once per Jacobian); from the FP32 inverse of a large
+    // problem in BD_MIXED each step gains about -log10(u32 cond(S_PP)) digits (2.7 on the
+    // 128x128x32 slab, where the fourth step reaches the FP64 floor)
+    c.X64 = h.d_CoInv64;
+    c.nref = (h.mixed() && !c.X64) ? 4 : 1;
     c.pl_ptr = h.d_pl_ptr;
     c.pl_idx = h.d_pl_idx;
     c.sptr = h.d_co_rptr;
     c.scol = h.d_co_col;
     c.sval = h.d_Co64;
-    c.gv = h.gv_coarse.d;
-    c.gv_acc = h.gv_coarse_acc.d;
+    c.ld_x = pad8(h.np);
   }
   h.cp_sorig = cset(c_sorig);
   h.cp_sdd = cset(c_sdd);
@@ -826,15 +872,16 @@ void setup_handle(bd_handle &h) {
   {
     CopyTask c{};
     c.src_off = 0; c.src_ld = h.ld_co; c.r0 = c.c0 = h.np; c.rows = c.cols = h.np; c.mode = 3; c.sign = -1.0;
-    c.dst_off = 0; c.dst_ld = h.np;
+    c.dst_off = 0; c.dst_ld = pad8(h.np);  // rows of the inverse 32-byte aligned (vector loads)
     h.cp_coinv = cset({c});
   }
   {  // the dense kernels stage vectors and tiles in shared memory
     const size_t el = h.mixed() ? sizeof(float) : sizeof(double);
     size_t need = el * (6 * 32 * 33 + (size_t)h.shK.max_e + 4);
-    for (const GemvSet *g : {&h.gv_schur, &h.gv_local, &h.gv_psit, &h.gv_coarse, &h.gv_sdd, &h.gv_lgi, &h.gv_lgit,
-                             &h.gv_drest, &h.gv_dext})
+    for (const GemvSet *g : {&h.gv_schur, &h.gv_local, &h.gv_psit, &h.gv_sdd, &h.gv_lgi, &h.gv_lgit, &h.gv_drest,
+                             &h.gv_dext})
       need = std::max(need, el * (size_t)std::max(g->max_rows, g->max_cols));
+    need = std::max(need, el * (size_t)pad8(h.np));  // the coarse GEMV stages the coarse vector
     if (need > dense_smem_limit())
       throw Status(BD_ERR_ARG, "local problem too large for the shared-memory staging of the dense kernels (" +
                                    std::to_string(need) + " bytes); use more subdomains");
@@ -855,7 +902,8 @@ void setup_handle(bd_handle &h) {
     D.LdK = m.alloc<T>((size_t)std::max(h.K_blk, 1) * kNB * kNB);
     D.Co = m.alloc<T>((size_t)h.ld_co * 2 * h.np);
     D.LdCo = m.alloc<T>((size_t)std::max(1, ceil_div(h.np, kNB)) * kNB * kNB);
-    D.CoInv = m.alloc<T>((size_t)h.np * h.np);
+    D.CoInv = m.alloc<T>((size_t)h.np * pad8(h.np));
+    ck(cudaMemsetAsync(D.CoInv, 0, sizeof(T) * (size_t)h.np * pad8(h.np), s), "memset");  // zero padding
   };
   if (h.mixed()) alloc_dense(h.df);
   else alloc_dense(h.dd);
@@ -949,10 +997,12 @@ void linearize_t(bd_handle &h, Dense<T> &D, bool precond) {
   // coarse: S_PiPi assembled in FP64 (sparse) and, in the local precision, into the augmented
   // matrix whose partial Cholesky leaves the explicit inverse; the solve refines against FP64
   ck(cudaMemsetAsync(D.Co, 0, sizeof(T) * (size_t)h.ld_co * 2 * h.np, s), "memset coarse");
+  if (h.d_Co64d) ck(cudaMemsetAsync(h.d_Co64d, 0, sizeof(double) * (size_t)h.np * h.np, s), "memset coarse");
   launch_coarse_assemble<T>(h.co_nnz, h.np, h.gauge_primal, h.d_co_row, h.d_co_col, h.d_co_sptr, h.d_co_src, D.Aug,
-                            h.d_Co64, D.Co, h.ld_co, s);
+                            h.d_Co64, D.Co, h.ld_co, h.d_Co64d, s);
   engine_partial_cholesky<T>(h.shCo, h.d_Codesc, D.Co, h.d_err, s, D.LdCo);
   launch_copy<T, T>(h.cp_coinv.n, h.cp_coinv.max_elems, h.cp_coinv.d, D.Co, D.CoInv, s);
+  if (h.d_CoInv64) coarse_refine64<T>(h.np, D.CoInv, pad8(h.np), h.d_Co64d, h.d_CoInv64, h.d_CoW, h.d_CoY, s);
 }
 
 // counted = true for the Jacobian evaluations of the solve (Newton, bidomain_linearize):
@@ -994,8 +1044,8 @@ void st_inv_t(bd_handle &h, Dense<T> &D, const double *rP, const double *rD, con
   // z_Pi = S_PiPi^-1 (rP - sum_j Psi^T r_D) into zbar[nd:], then ydc_Delta -= Psi z_Pi
   launch_coarse_solve<T>(h.cs, D.CoInv, h.d_ydc + h.nD_tot, rP_csr ? nullptr : rP, rP_csr, h.d_zbar + h.nd,
                          h.d_co_c, h.d_co_rho, done, h.s);
-  launch_gemv_t<T>(h.gv_psit.n, h.gv_psit.max_rows, h.gv_psit.max_cols, h.gv_psit.d, D.Z, h.d_zbar, h.d_prim_x,
-                   h.d_ydc, -1.0, done, h.s);
+  launch_gemv_t_task<T>(h.gv_psit.n, h.gv_psit.max_rows, h.gv_psit.max_cols, h.gv_psit.d, D.Z, h.d_zbar,
+                        h.d_prim_x, h.d_ydc, -1.0, done, h.s);
 }
 
 // rbar = T^T r is never stored: the deluxe restriction evaluates its dual rows while
@@ -1006,12 +1056,12 @@ void bddc_t(bd_handle &h, Dense<T> &D, const double *r, double *z, const int *do
   const CsrIn rbar{h.d_Tt_ptr, h.d_Tt_col, h.d_Tt_val, r};
   const CsrIn rbar_p{h.d_Tt_ptr + h.nd, h.d_Tt_col, h.d_Tt_val, r};
   // deluxe restriction r_C^(j) = D_C^(j)T rbar_C
-  launch_gemv_t<T>(h.gv_drest.n, h.gv_drest.max_rows, h.gv_drest.max_cols, h.gv_drest.d, D.Dd, nullptr, nullptr,
-                   h.d_rD, 1.0, done, h.s, &rbar);
+  launch_gemv_t_task<T>(h.gv_drest.n, h.gv_drest.max_rows, h.gv_drest.max_cols, h.gv_drest.d, D.Dd, nullptr,
+                        nullptr, h.d_rD, 1.0, done, h.s, &rbar);
   st_inv_t(h, D, nullptr, h.d_rD, done, &rbar_p);
   // deluxe extension zbar_C = sum_j D_C^(j) z_C^(j) (one row of [D^(j1) | D^(j2) | ...] per output)
-  launch_gemv<T>(h.gv_dext.n, h.gv_dext.max_rows, h.gv_dext.max_cols, h.gv_dext.d, D.Dd, h.d_ydc, h.d_ext_idx,
-                 h.d_zbar, 1.0, done, h.s);
+  launch_gemv_task<T>(h.gv_dext.n, h.gv_dext.max_rows, h.gv_dext.max_cols, h.gv_dext.d, D.Dd, h.d_ydc,
+                      h.d_ext_idx, h.d_zbar, 1.0, done, h.s);
   if (f) launch_spmv_dot(h.nif, h.d_T_ptr, h.d_T_col, h.d_T_val, h.d_zbar, z, h.gauge_iface, *f, h.s);
   else launch_spmv(h.nif, h.d_T_ptr, h.d_T_col, h.d_T_val, h.d_zbar, z, h.gauge_iface, done, h.s);
 }
@@ -1267,6 +1317,24 @@ double trial_residual(bd_handle &h, const StimParams &sp, const double *si, cons
   return read_scalar(h, h.d_scal);
 }
 
+// ---- learned guess: interior from the predicted interface increment --------------
+// u0 = u^n + d with d_Gamma the network's prediction and d_I from the interior recovery
+// of Section 4.1 with the factors of the last Jacobian: d_I = K_II^-1 (-r_I - K_IG d_Gamma),
+// r = F(u^n) - G (in ri, re).  Writes u0 into (gi, ge).
+template <class T>
+void guess_interior_t(bd_handle &h, Dense<T> &D, int) {
+  cudaStream_t s = h.s;
+  launch_gather_pairs(h.nint_nodes, h.d_int_node, h.d_ri, h.d_re, h.d_fI, -1.0, nullptr, s);
+  launch_trsv<T>(h.nsub, h.shK.max_e, h.d_Kdesc, h.d_vec_off_I, D.K, D.LdK, h.d_fI, h.d_yI, false, s);
+  launch_gemv_t<T>(h.gv_lgit.n, h.gv_lgit.max_rows, h.gv_lgit.max_cols, h.gv_lgit.d, D.K, h.d_dG, h.d_R, h.d_yI, -1.0,
+                   nullptr, s);
+  launch_trsv<T>(h.nsub, h.shK.max_e, h.d_Kdesc, h.d_vec_off_I, D.K, D.LdK, h.d_yI, h.d_fI, true, s);
+  launch_scatter_pairs(h.nint_nodes, h.d_int_node, h.d_fI, h.d_gi, h.d_ge, s);
+  launch_scatter_pairs(h.nif / 2, h.d_iface_node, h.d_dG, h.d_gi, h.d_ge, s);
+  launch_axpby(h.N, 1.0, h.d_uin, 1.0, h.d_gi, s);
+  launch_axpby(h.N, 1.0, h.d_uen, 1.0, h.d_ge, s);
+}
+
 // ---- one time step (Sections 3b, 3c) -------------------------------------------
 int step(bd_handle &h, const bd_stimulus *stim, bd_step_stats *out) {
   cudaStream_t s = h.s;
@@ -1288,10 +1356,11 @@ int step(bd_handle &h, const bd_stimulus *stim, bd_step_stats *out) {
   if (h.mlp_on && h.hist_count >= 2) {
     // learned guess u^n + MLP(traces of u^n, u^{n-1}, u^{n-2}); kept only if its residual is smaller
     h.prof.begin(PROF_MLP, s);
-    mlp_features(h.mlp, h.nq, h.d_q_sub, h.d_q_loc, h.d_q_node, h.d_uin, h.d_uen, h.d_uh1i, h.d_uh1e, h.d_uh2i,
-                 h.d_uh2e, nullptr, nullptr, s);
-    mlp_forward(h.mlp, h.mlp.batch, s);
-    mlp_guess(h.mlp, h.N, h.d_node_ptr, h.d_node_ent, h.d_uin, h.d_uen, h.d_gi, h.d_ge, s);
+    mlp_features(h.mlp, h.n_tr_ent, h.d_t_sub, h.d_t_pos, h.d_t_node, h.d_uin, h.d_uen, h.d_uh1i, h.d_uh1e,
+                 h.d_uh2i, h.d_uh2e, nullptr, nullptr, s);
+    mlp_forward(h.mlp, h.d_err, s);
+    mlp_trace_increment(h.mlp, h.nif / 2, h.d_tr_ptr, h.d_tr_ent, h.d_dG, s);
+    DISPATCH(h, guess_interior_t, 0);
     h.prof.end(PROF_MLP, s, 0.0, 0.0);
     std::swap(h.d_ui, h.d_gi); std::swap(h.d_ue, h.d_ge);  // residual at the guess
     const double g2 = trial_residual(h, sp, nullptr, nullptr, 0.0);
@@ -1378,8 +1447,8 @@ int step(bd_handle &h, const bd_stimulus *stim, bd_step_stats *out) {
     MlpDev &M = h.mlp;
     ck(cudaMemsetAsync(M.T, 0, sizeof(float) * M.batch * M.n_out, s), "memset");
     ck(cudaMemsetAsync(M.mask, 0, sizeof(float) * M.batch * M.n_out, s), "memset");
-    mlp_features(M, h.nq, h.d_q_sub, h.d_q_loc, h.d_q_node, h.d_uin, h.d_uen, h.d_uh1i, h.d_uh1e, h.d_uh2i,
-                 h.d_uh2e, h.d_ui, h.d_ue, s);
+    mlp_features(M, h.n_tr_ent, h.d_t_sub, h.d_t_pos, h.d_t_node, h.d_uin, h.d_uen, h.d_uh1i, h.d_uh1e,
+                 h.d_uh2i, h.d_uh2e, h.d_ui, h.d_ue, s);
     for (int ep = 0; ep < std::max(1, h.opt.mlp_epochs); ++ep) mlp_train_once(h, ep == 0);
     h.prof.end(PROF_MLP, s, 0.0, 0.0);
     st.mlp_loss = read_scalar(h, h.d_scal + 4);
@@ -1646,6 +1715,10 @@ int bidomain_setup(const bd_mesh *mesh, const bd_conductivity *cond, const bd_io
       return BD_ERR_CUDA;
     }
     if (h->opt.precision != BD_MIXED) h->opt.use_tensor_cores = 0;
+    if (h->opt.learned_guess && !gemm_tc_configure()) {
+      g_last_error = "tensor-core GEMM configuration failed";
+      return BD_ERR_CUDA;
+    }
     if (!dense_configure()) {
       g_last_error = "dense kernel configuration failed";
       return BD_ERR_CUDA;
@@ -1844,14 +1917,53 @@ int bidomain_mlp_loss_grad(bd_handle *h, const float *X, const float *T, const f
     std::vector<float> mk(mask, mask + ny);
     double cnt = 0.0;
     for (float v : mk) cnt += v;
-    ck(cudaMemcpyAsync(M.X, X, sizeof(float) * nx, cudaMemcpyHostToDevice, h->s), "mlp X");
+    ck(cudaMemcpyAsync(M.Xf, X, sizeof(float) * nx, cudaMemcpyHostToDevice, h->s), "mlp X");
     ck(cudaMemcpyAsync(M.T, T, sizeof(float) * ny, cudaMemcpyHostToDevice, h->s), "mlp T");
     ck(cudaMemcpyAsync(M.mask, mask, sizeof(float) * ny, cudaMemcpyHostToDevice, h->s), "mlp mask");
-    mlp_forward(M, M.batch, h->s);
-    mlp_backward(M, M.batch, (float)(1.0 / std::max(cnt, 1.0)), h->d_partial, h->s);
+    mlp_inputs_from_f32(M, h->s);
+    mlp_forward(M, h->d_err, h->s);
+    mlp_backward(M, (float)(1.0 / std::max(cnt, 1.0)), h->d_partial, h->d_err, h->s);
     launch_sum_partials(kRedBlocks, h->d_partial, h->d_scal + 4, h->s);
     if (loss) *loss = read_scalar(*h, h->d_scal + 4);
     if (grad) ck(cudaMemcpyAsync(grad, M.g, sizeof(float) * M.n_params, cudaMemcpyDeviceToHost, h->s), "grad");
+    ck(cudaStreamSynchronize(h->s), "sync");
+    return BD_OK;
+  });
+}
+
+int bidomain_coarse_size(bd_handle *h, int *n_primal, int *nnz) {
+  if (!h) return BD_ERR_ARG;
+  if (n_primal) *n_primal = h->np;
+  if (nnz) *nnz = h->co_nnz;
+  return BD_OK;
+}
+
+int bidomain_coarse_matrix(bd_handle *h, int *rowptr, int *col, double *val) {
+  if (!h || !rowptr || !col || !val) return BD_ERR_ARG;
+  if (!h->linearized) return BD_ERR_STATE;
+  return guard(h, [&] {
+    ck(cudaMemcpyAsync(rowptr, h->d_co_rptr, sizeof(int) * (h->np + 1), cudaMemcpyDeviceToHost, h->s), "coarse");
+    ck(cudaMemcpyAsync(col, h->d_co_col, sizeof(int) * h->co_nnz, cudaMemcpyDeviceToHost, h->s), "coarse");
+    ck(cudaMemcpyAsync(val, h->d_Co64, sizeof(double) * h->co_nnz, cudaMemcpyDeviceToHost, h->s), "coarse");
+    ck(cudaStreamSynchronize(h->s), "sync");
+    return BD_OK;
+  });
+}
+
+int bidomain_coarse_solve(bd_handle *h, const double *c, double *z, int nref) {
+  if (!h || !c || !z) return BD_ERR_ARG;
+  if (!h->linearized) return BD_ERR_STATE;
+  return guard(h, [&] {
+    CoarseSolve cs = h->cs;
+    cs.pl_ptr = h->d_co_noptr;  // no local products: c itself is the right-hand side
+    if (nref >= 0) cs.nref = nref;
+    double *dc = h->d_io[0], *dz = h->d_io[1];
+    ck(cudaMemcpyAsync(dc, c, sizeof(double) * h->np, cudaMemcpyHostToDevice, h->s), "coarse c");
+    if (h->mixed())
+      launch_coarse_solve<float>(cs, h->df.CoInv, h->d_ydc, dc, nullptr, dz, h->d_co_c, h->d_co_rho, nullptr, h->s);
+    else
+      launch_coarse_solve<double>(cs, h->dd.CoInv, h->d_ydc, dc, nullptr, dz, h->d_co_c, h->d_co_rho, nullptr, h->s);
+    ck(cudaMemcpyAsync(z, dz, sizeof(double) * h->np, cudaMemcpyDeviceToHost, h->s), "coarse z");
     ck(cudaStreamSynchronize(h->s), "sync");
     return BD_OK;
   });

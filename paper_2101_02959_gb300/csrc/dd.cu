@@ -158,7 +158,7 @@ template <typename T>
 __global__ void k_coarse_assemble(int nnz, int np, int gauge, const int *__restrict__ crow,
                                   const int *__restrict__ ccol, const int *__restrict__ sptr,
                                   const long long *__restrict__ src, const T *__restrict__ abase,
-                                  double *__restrict__ val64, T *__restrict__ co, int ld) {
+                                  double *__restrict__ val64, T *__restrict__ co, int ld, double *__restrict__ dense64) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < nnz) {
     const int a = crow[e], b = ccol[e];
@@ -168,6 +168,7 @@ __global__ void k_coarse_assemble(int nnz, int np, int gauge, const int *__restr
       for (int k = sptr[e]; k < sptr[e + 1]; ++k) v += (double)abase[src[k]];
     val64[e] = v;
     co[(long long)a * ld + b] = (T)v;
+    if (dense64) dense64[(long long)a * np + b] = v;
   } else if (e < nnz + np) {
     const int q = e - nnz;
     co[(long long)(np + q) * ld + q] = T(1);
@@ -197,28 +198,73 @@ __global__ void k_coarse_rhs(int np, int gauge, const int *__restrict__ pl_ptr, 
   if (q < np) c[q] = coarse_rhs_row(q, gauge, pl_ptr, pl_idx, yprim, rP, rPc);
 }
 
-// rho = c - S_PP z (FP64 CSR), one thread per row
+// rho = c - S_PP z (FP64 CSR), one warp per row (coarse rows hold a few hundred entries)
 __global__ void k_coarse_resid(int np, const int *__restrict__ ptr, const int *__restrict__ col,
                                const double *__restrict__ val, const double *__restrict__ c,
                                const double *__restrict__ z, double *__restrict__ rho, const int *__restrict__ done) {
   if (done && *done) return;
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (q >= np) return;
   double acc = 0.0;
-  for (int k = ptr[q]; k < ptr[q + 1]; ++k) acc += val[k] * z[col[k]];
-  rho[q] = c[q] - acc;
+  for (int k = ptr[q] + lane; k < ptr[q + 1]; k += 32) acc += val[k] * z[col[k]];
+  acc = warp_sum(acc);
+  if (lane == 0) rho[q] = c[q] - acc;
+}
+
+// C = alpha A B + beta D for n x n FP64 matrices (row-major, leading dimension n): the
+// Newton-Schulz refinement of small coarse inverses.  16 x 16 output tiles in shared memory.
+__global__ void __launch_bounds__(256) k_gemm64(int n, const double *__restrict__ A, const double *__restrict__ B,
+                                                const double *__restrict__ D, double alpha, double beta,
+                                                double *__restrict__ C) {
+  __shared__ double As[16][17], Bs[16][17];
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int i = blockIdx.y * 16 + ty, j = blockIdx.x * 16 + tx;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < n; k0 += 16) {
+    As[ty][tx] = (i < n && k0 + tx < n) ? A[(long long)i * n + k0 + tx] : 0.0;
+    Bs[ty][tx] = (k0 + ty < n && j < n) ? B[(long long)(k0 + ty) * n + j] : 0.0;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc += As[ty][k] * Bs[k][tx];
+    __syncthreads();
+  }
+  if (i < n && j < n) C[(long long)i * n + j] = alpha * acc + (D ? beta * D[(long long)i * n + j] : 0.0);
+}
+
+// y (np x np, leading dimension np) = (double) x (leading dimension ldx)
+template <typename T>
+__global__ void k_widen(int np, int ldx, const T *__restrict__ x, double *__restrict__ y) {
+  const long long n = (long long)np * np;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+    y[t] = (double)x[(t / np) * ldx + t % np];
+}
+
+// Small coarse problems (np <= kCoarseSmall), once per Jacobian: the inverse in the local
+// precision widened to FP64 and brought to FP64 accuracy by two Newton-Schulz steps
+// X <- 2X - X C X (the error squares at each step), C the dense FP64 S_PP.
+template <typename T>
+void coarse_refine64(int np, const T *x0, int ld0, const double *C, double *X, double *W, double *Y, cudaStream_t s) {
+  if (np == 0) return;
+  const long long nn = (long long)np * np;
+  k_widen<T><<<(int)std::min<long long>((nn + 255) / 256, 4096), 256, 0, s>>>(np, ld0, x0, X);
+  const dim3 g(ceil_div(np, 16), ceil_div(np, 16));
+  for (int it = 0; it < 2; ++it) {
+    k_gemm64<<<g, 256, 0, s>>>(np, C, X, nullptr, 1.0, 0.0, W);  // W = C X
+    k_gemm64<<<g, 256, 0, s>>>(np, X, W, X, -1.0, 2.0, Y);       // Y = 2X - X W
+    cudaMemcpyAsync(X, Y, sizeof(double) * nn, cudaMemcpyDeviceToDevice, s);
+  }
+  count_launch(5);
 }
 
 // The whole coarse solve of a small coarse problem in one CTA: c (as k_coarse_rhs),
-// z = X c with the explicit inverse X (local precision, FP64 accumulation), then nref
-// steps of iterative refinement z += X (c - S_PP z) with the FP64 sparse S_PP.  The
-// refinement makes the solve backward stable in FP64 whatever the precision of X
-// (the explicit inverse alone is not: its error grows with cond(S_PP) times the size
-// of X, and the (u_i, u_e) constant mode that the gauge alone holds is where it shows).
-template <typename T>
+// z = X c with the FP64 explicit inverse X, then nref steps of iterative refinement
+// z += X (c - S_PP z) with the FP64 sparse S_PP.  The refinement makes the solve
+// backward stable (the explicit inverse alone is not: its error grows with cond(S_PP)
+// times the size of X, and the (u_i, u_e) constant mode that the gauge alone holds is
+// where it shows).
 __global__ void __launch_bounds__(1024) k_coarse_solve_small(
     int np, int gauge, const int *__restrict__ pl_ptr, const int *__restrict__ pl_idx,
-    const double *__restrict__ yprim, const double *__restrict__ rP, const CsrIn rPc, const T *__restrict__ X,
+    const double *__restrict__ yprim, const double *__restrict__ rP, const CsrIn rPc, const double *__restrict__ X,
     const int *__restrict__ sptr, const int *__restrict__ scol, const double *__restrict__ sval, int nref,
     double *__restrict__ z_out, const int *__restrict__ done) {
   if (done && *done) return;
@@ -236,14 +282,14 @@ __global__ void __launch_bounds__(1024) k_coarse_solve_small(
   for (int pass = 0; pass <= nref; ++pass) {
     // z += X r (r = c on the first pass)
     for (int q = wid; q < np; q += nw) {
-      const T *row = X + (long long)q * np;
+      const double *row = X + (long long)q * np;
       double a0 = 0.0, a1 = 0.0;
       int k = lane;
       for (; k + 32 < np; k += 64) {
-        a0 += (double)row[k] * r[k];
-        a1 += (double)row[k + 32] * r[k + 32];
+        a0 += row[k] * r[k];
+        a1 += row[k + 32] * r[k + 32];
       }
-      if (k < np) a0 += (double)row[k] * r[k];
+      if (k < np) a0 += row[k] * r[k];
       const double v = warp_sum(a0 + a1);
       if (lane == 0) z[q] += v;
     }
@@ -732,11 +778,12 @@ void launch_class_aug(int ncls, int max_n, const ClassTask *cls, const PairTask 
 
 template <typename T>
 void launch_coarse_assemble(int nnz, int np, int gauge, const int *crow, const int *ccol, const int *sptr,
-                            const long long *src, const T *abase, double *val64, T *co, int ld, cudaStream_t s) {
+                            const long long *src, const T *abase, double *val64, T *co, int ld, double *dense64,
+                            cudaStream_t s) {
   const int tot = nnz + np;
   if (tot == 0) return;
   k_coarse_assemble<T><<<ceil_div(tot, 256), 256, 0, s>>>(nnz, np, gauge, crow, ccol, sptr, src, abase, val64, co,
-                                                          ld);
+                                                          ld, dense64);
   count_launch();
 }
 
@@ -745,19 +792,19 @@ void launch_coarse_solve(const CoarseSolve &cs, const T *X, const double *yprim,
                          double *z, double *c, double *rho, const int *done, cudaStream_t s) {
   if (cs.np == 0) return;
   const CsrIn rc = rPc ? *rPc : CsrIn{};
-  if (cs.np <= kCoarseSmall) {
-    k_coarse_solve_small<T><<<1, 1024, 3 * sizeof(double) * cs.np, s>>>(
-        cs.np, cs.gauge, cs.pl_ptr, cs.pl_idx, yprim, rP, rc, X, cs.sptr, cs.scol, cs.sval, cs.nref, z, done);
+  if (cs.X64) {
+    k_coarse_solve_small<<<1, 1024, 3 * sizeof(double) * cs.np, s>>>(
+        cs.np, cs.gauge, cs.pl_ptr, cs.pl_idx, yprim, rP, rc, cs.X64, cs.sptr, cs.scol, cs.sval, cs.nref, z, done);
     count_launch();
     return;
   }
   k_coarse_rhs<<<ceil_div(cs.np, 256), 256, 0, s>>>(cs.np, cs.gauge, cs.pl_ptr, cs.pl_idx, yprim, rP, rc, c, done);
   count_launch();
-  launch_gemv<T>(1, cs.np, cs.np, cs.gv, X, c, nullptr, z, 1.0, done, s);
+  launch_gemv_rows<T>(cs.np, X, cs.ld_x, c, z, 0, done, s);
   for (int it = 0; it < cs.nref; ++it) {
-    k_coarse_resid<<<ceil_div(cs.np, 256), 256, 0, s>>>(cs.np, cs.sptr, cs.scol, cs.sval, c, z, rho, done);
+    k_coarse_resid<<<ceil_div(cs.np, 8), 256, 0, s>>>(cs.np, cs.sptr, cs.scol, cs.sval, c, z, rho, done);
     count_launch();
-    launch_gemv<T>(1, cs.np, cs.np, cs.gv_acc, X, rho, nullptr, z, 1.0, done, s);
+    launch_gemv_rows<T>(cs.np, X, cs.ld_x, rho, z, 1, done, s);
   }
 }
 
@@ -922,7 +969,10 @@ void launch_dot2(int n, const double *a0, const double *b0, const double *a1, co
   template void launch_class_aug<T>(int, int, const ClassTask *, const PairTask *, const T *, const MatDesc *,  \
                                     T *, cudaStream_t);                                                        \
   template void launch_coarse_assemble<T>(int, int, int, const int *, const int *, const int *,                 \
-                                          const long long *, const T *, double *, T *, int, cudaStream_t);     \
+                                          const long long *, const T *, double *, T *, int, double *,         \
+                                          cudaStream_t);                                                      \
+  template void coarse_refine64<T>(int, const T *, int, const double *, double *, double *, double *,           \
+                                   cudaStream_t);                                                              \
   template void launch_coarse_solve<T>(const CoarseSolve &, const T *, const double *, const double *,         \
                                        const CsrIn *, double *, double *, double *, const int *, cudaStream_t); \
   template void launch_jump_dt<T>(int, int, const WTask *, const WEnt *, const T *, const T *, const double *,  \

@@ -59,21 +59,29 @@ void launch_class_aug(int ncls, int max_n, const ClassTask *cls, const PairTask 
 // augmented matrix [[S_PP, I], [I, 0]] whose partial Cholesky leaves -S_PP^-1.
 // Entry e of the CSR sums the local entries src[sptr[e] .. sptr[e + 1]) of the
 // augmented local matrices.
+// dense64 (nullable): also the dense FP64 S_PP, np x np (small problems)
 template <typename T>
 void launch_coarse_assemble(int nnz, int np, int gauge, const int *crow, const int *ccol, const int *sptr,
-                            const long long *src, const T *abase, double *val64, T *co, int ld, cudaStream_t s);
+                            const long long *src, const T *abase, double *val64, T *co, int ld, double *dense64,
+                            cudaStream_t s);
+// small problems: X = (double) x0 (leading dimension ld0), then two Newton-Schulz steps
+// X <- 2X - X C X against the dense FP64 S_PP (C); W, Y scratch (np x np each)
+template <typename T>
+void coarse_refine64(int np, const T *x0, int ld0, const double *C, double *X, double *W, double *Y, cudaStream_t s);
 
-// The coarse solve z = S_PP^-1 c with c = rP - sum_j (Psi^T r_D)_j: the explicit
-// inverse X (local precision) followed by nref steps of iterative refinement
-// z += X (c - S_PP z) against the FP64 CSR, so the result is the FP64 solution.
-// np <= kCoarseSmall: one CTA; otherwise one GEMV per pass over the whole grid.
+// The coarse solve z = S_PP^-1 c with c = rP - sum_j (Psi^T r_D)_j: an explicit
+// inverse followed by nref steps of iterative refinement z += X (c - S_PP z) against the
+// FP64 CSR, so the result is the FP64 solution.  np <= kCoarseSmall: the inverse refined
+// to FP64 once per Jacobian (X64) and one CTA per solve; otherwise the inverse in the
+// local precision and one GEMV per pass over the whole grid.
 constexpr int kCoarseSmall = 320;
 struct CoarseSolve {
   int np = 0, gauge = -1, nref = 1;
+  const double *X64 = nullptr;                      // small problems: the FP64 inverse
   const int *pl_ptr = nullptr, *pl_idx = nullptr;  // assembly lists of the local primal products
   const int *sptr = nullptr, *scol = nullptr;      // S_PP (CSR, FP64)
   const double *sval = nullptr;
-  const GemvDesc *gv = nullptr, *gv_acc = nullptr;  // one np x np task: y = X x / y += X x
+  int ld_x = 0;                                     // row stride of the explicit inverse X (multiple of 8)
 };
 // c and rho: np-long scratch (large problems only); z: np-long output
 template <typename T>

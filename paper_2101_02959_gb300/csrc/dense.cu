@@ -691,6 +691,136 @@ __global__ void __launch_bounds__(256) k_gemv_t(const GemvDesc *__restrict__ tas
   }
 }
 
+// Batched GEMVs of many small matrices (deluxe blocks, Psi): one CTA per task covering all of
+// its rows / columns, so the staging of x and the task descriptor are paid once per matrix.
+// y = alpha A x (+ y): 8 warps over the rows, two rows at a time per warp, lanes over the
+// columns (coalesced rows).
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemv_task(const GemvDesc *__restrict__ tasks, const T *__restrict__ A,
+                                                   const double *__restrict__ x, const int *__restrict__ xidx,
+                                                   double *__restrict__ y, double alpha,
+                                                   const int *__restrict__ done) {
+  if (done && *done) return;
+  const GemvDesc t = tasks[blockIdx.x];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *xs = reinterpret_cast<T *>(smem_raw);
+  for (int c = threadIdx.x; c < t.cols; c += blockDim.x)
+    xs[c] = (T)((t.flags & 1) ? x[xidx[t.x_off + c]] : x[t.x_off + c]);
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int r0 = 2 * wid; r0 < t.rows; r0 += 16) {
+    const int r1 = r0 + 1;
+    const bool v1 = r1 < t.rows;
+    const T *row0 = A + t.a_off + (long long)r0 * t.ld;
+    const T *row1 = A + t.a_off + (long long)(v1 ? r1 : r0) * t.ld;
+    T a0 = T(0), b0 = T(0);
+    for (int c = lane; c < t.cols; c += 32) {
+      const T xv = xs[c];
+      a0 += row0[c] * xv;
+      b0 += row1[c] * xv;
+    }
+    const T s0 = warp_sum(a0), s1 = warp_sum(b0);
+    if (lane == 0) {
+      const double v = alpha * (double)s0;
+      y[t.y_off + r0] = (t.flags & 2) ? y[t.y_off + r0] + v : v;
+      if (v1) {
+        const double w = alpha * (double)s1;
+        y[t.y_off + r1] = (t.flags & 2) ? y[t.y_off + r1] + w : w;
+      }
+    }
+  }
+}
+
+// y[a] = (acc ? y[a] : 0) + alpha sum_p A[p][a] x[p]: one CTA per task, one thread per column
+// (coalesced rows), x staged (gathered, or a sparse product when csr.ptr is set).
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemv_t_task(const GemvDesc *__restrict__ tasks, const T *__restrict__ A,
+                                                     const double *__restrict__ x, const int *__restrict__ xidx,
+                                                     double *__restrict__ y, double alpha,
+                                                     const int *__restrict__ done, const CsrIn csr) {
+  if (done && *done) return;
+  const GemvDesc t = tasks[blockIdx.x];
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *xs = reinterpret_cast<T *>(smem_raw);
+  for (int p = threadIdx.x; p < t.rows; p += blockDim.x)
+    xs[p] = (T)(csr.ptr ? csr_row(csr, t.x_off + p) : (t.flags & 1) ? x[xidx[t.x_off + p]] : x[t.x_off + p]);
+  __syncthreads();
+  const T *base = A + t.a_off;
+  const long long ld = t.ld;
+  for (int a = threadIdx.x; a < t.cols; a += blockDim.x) {
+    T a0 = T(0), a1 = T(0);
+    int p = 0;
+    for (; p + 1 < t.rows; p += 2) {
+      a0 += base[p * ld + a] * xs[p];
+      a1 += base[(p + 1) * ld + a] * xs[p + 1];
+    }
+    if (p < t.rows) a0 += base[p * ld + a] * xs[p];
+    const double v = alpha * (double)(a0 + a1);
+    y[t.y_off + a] = (t.flags & 2) ? y[t.y_off + a] + v : v;
+  }
+}
+
+template <typename T>
+void launch_gemv_task(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks, const T *A, const double *x,
+                      const int *xidx, double *y, double alpha, const int *done, cudaStream_t s) {
+  if (ntasks == 0 || max_rows == 0) return;
+  k_gemv_task<T><<<ntasks, 256, sizeof(T) * (size_t)std::max(1, max_cols), s>>>(d_tasks, A, x, xidx, y, alpha, done);
+  count_launch();
+}
+
+template <typename T>
+void launch_gemv_t_task(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks, const T *A,
+                        const double *x, const int *xidx, double *y, double alpha, const int *done, cudaStream_t s,
+                        const CsrIn *csr) {
+  if (ntasks == 0 || max_cols == 0) return;
+  const int threads = max_cols <= 128 ? 128 : 256;
+  k_gemv_t_task<T><<<ntasks, threads, sizeof(T) * (size_t)std::max(1, max_rows), s>>>(
+      d_tasks, A, x, xidx, y, alpha, done, csr ? *csr : CsrIn{});
+  count_launch();
+}
+
+// y (+)= A x for one large row-major matrix (n x n, ld a multiple of 8): one warp per row,
+// 16-byte loads, four rows' worth of loads in flight per lane; x staged in shared memory
+// in T (as k_gemv does), accumulation in T.  The coarse solve of large coarse problems.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gemv_rows(int n, const T *__restrict__ A, int ld,
+                                                   const double *__restrict__ x, double *__restrict__ y,
+                                                   int accumulate, const int *__restrict__ done) {
+  if (done && *done) return;
+  using VT = typename Vec16<T>::V;
+  constexpr int VN = Vec16<T>::N;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *xs = reinterpret_cast<T *>(smem_raw);
+  const int npad = (n + 7) & ~7;
+  for (int c = threadIdx.x; c < npad; c += blockDim.x) xs[c] = c < n ? (T)x[c] : T(0);
+  __syncthreads();
+  const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const VT *a = reinterpret_cast<const VT *>(A + (long long)row * ld);
+  const VT *xv = reinterpret_cast<const VT *>(xs);
+  const int nv = npad / VN;  // the padding columns of A are zero, as are those of xs
+  T acc0 = T(0), acc1 = T(0), acc2 = T(0), acc3 = T(0);
+  int v = lane;
+  for (; v + 96 < nv; v += 128) {
+    const VT a0 = a[v], a1 = a[v + 32], a2 = a[v + 64], a3 = a[v + 96];
+    acc0 += Vec16<T>::dot(a0, xv[v]);
+    acc1 += Vec16<T>::dot(a1, xv[v + 32]);
+    acc2 += Vec16<T>::dot(a2, xv[v + 64]);
+    acc3 += Vec16<T>::dot(a3, xv[v + 96]);
+  }
+  for (; v < nv; v += 32) acc0 += Vec16<T>::dot(a[v], xv[v]);
+  const double s = (double)warp_sum((acc0 + acc1) + (acc2 + acc3));
+  if (lane == 0) y[row] = accumulate ? y[row] + s : s;
+}
+
+template <typename T>
+void launch_gemv_rows(int n, const T *A, int ld, const double *x, double *y, int accumulate, const int *done,
+                      cudaStream_t s) {
+  if (n == 0) return;
+  k_gemv_rows<T><<<ceil_div(n, 8), 256, sizeof(T) * (size_t)((n + 7) & ~7), s>>>(n, A, ld, x, y, accumulate, done);
+  count_launch();
+}
+
 template <typename T>
 void launch_gemv(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks, const T *A, const double *x,
                  const int *xidx, double *y, double alpha, const int *done, cudaStream_t s) {
@@ -879,6 +1009,12 @@ bool dense_configure() {
   ok &= cudaFuncSetAttribute(k_gemv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_gemv_t<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_gemv_t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_gemv_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_gemv_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_gemv_task<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_gemv_task<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_gemv_t_task<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_gemv_t_task<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
   return ok;
 }
 
@@ -887,6 +1023,12 @@ bool dense_configure() {
                                            T *, ProfHook *, bool);                                             \
   template void launch_gemv<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *,        \
                                double *, double, const int *, cudaStream_t);                                   \
+  template void launch_gemv_rows<T>(int, const T *, int, const double *, double *, int, const int *,           \
+                                    cudaStream_t);                                                             \
+  template void launch_gemv_task<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *,   \
+                                    double *, double, const int *, cudaStream_t);                              \
+  template void launch_gemv_t_task<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *, \
+                                      double *, double, const int *, cudaStream_t, const CsrIn *);             \
   template void launch_gemv_t<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *,      \
                                  double *, double, const int *, cudaStream_t, const CsrIn *);                  \
   template void launch_trsv<T>(int, int, const MatDesc *, const int *, const T *, const T *, const double *,   \

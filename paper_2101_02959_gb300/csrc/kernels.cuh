@@ -100,6 +100,18 @@ bool tc_configure();
 void launch_rankk_tc(const MatDesc *d_desc, float *base, int mode, int K0, int K1, int max_rows, int max_cols,
                      int count, int *err, cudaStream_t s);
 
+// The same products for many small matrices: one CTA per task over all its rows (columns)
+template <typename T>
+void launch_gemv_task(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks, const T *A, const double *x,
+                      const int *xidx, double *y, double alpha, const int *done, cudaStream_t s);
+template <typename T>
+void launch_gemv_t_task(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks, const T *A,
+                        const double *x, const int *xidx, double *y, double alpha, const int *done, cudaStream_t s,
+                        const CsrIn *csr = nullptr);
+// y (+)= A x for one large n x n row-major matrix (ld a multiple of 8, zero padding columns)
+template <typename T>
+void launch_gemv_rows(int n, const T *A, int ld, const double *x, double *y, int accumulate, const int *done,
+                      cudaStream_t s);
 // y = alpha * A x (+ y): tasks in d_tasks (GemvDesc); x gathered through xidx when flagged.
 template <typename T>
 void launch_gemv(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks, const T *A, const double *x,

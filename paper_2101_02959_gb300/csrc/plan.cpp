@@ -3,6 +3,7 @@
 
 #include <algorithm>
 #include <map>
+#include <set>
 #include <numeric>
 
 namespace bd {
@@ -184,8 +185,77 @@ std::string build_plan(Plan &p, const int n[3], const double l[3], const int s[3
     c.type = (k == 2) ? CLS_FACE : ((int)c.nodes.size() > 1 ? CLS_EDGE : CLS_VERTEX);
     cls.push_back(c);
   }
-  std::sort(cls.begin(), cls.end(), [](const Cls &a, const Cls &b) {
-    return a.type != b.type ? a.type < b.type : a.first < b.first; });
+  auto by_type_first = [](const Cls &a, const Cls &b) {
+    return a.type != b.type ? a.type < b.type : a.first < b.first; };
+  std::sort(cls.begin(), cls.end(), by_type_first);
+  // A subdomain fragment of a masked grid may have no vertex on its interface: for
+  // subdomains j = 0, 1, ... in order, one without a vertex class promotes the lowest-id
+  // node of each of its edge classes (of its face classes if it has no edge) to a vertex
+  // class of its own, the rest of each such class is split again into connected classes
+  // by the usual rule, and the classes are re-sorted after every subdomain.
+  {
+    std::vector<std::vector<int>> adj(nn);
+    for (int e = 0; e < ne; ++e)
+      for (auto &ed : kHexEdges) {
+        int x = p.conn[8 * e + ed[0]], y = p.conn[8 * e + ed[1]];
+        if (p.mult[x] >= 2 && p.mult[y] >= 2 && nsets[x] == nsets[y]) {
+          adj[x].push_back(y);
+          adj[y].push_back(x);
+        }
+      }
+    auto make = [&](std::vector<int> nodes, const std::vector<int> &subs) {
+      Cls c;
+      std::sort(nodes.begin(), nodes.end());
+      c.nodes = nodes;
+      c.first = nodes[0];
+      c.subs = subs;
+      c.type = ((int)subs.size() == 2) ? CLS_FACE : ((int)nodes.size() > 1 ? CLS_EDGE : CLS_VERTEX);
+      return c;
+    };
+    for (int j = 0; j < nsub; ++j) {
+      bool has_vertex = false;
+      std::vector<int> edges, faces;
+      for (int c = 0; c < (int)cls.size(); ++c) {
+        if (!std::binary_search(cls[c].subs.begin(), cls[c].subs.end(), j)) continue;
+        if (cls[c].type == CLS_VERTEX) has_vertex = true;
+        else if (cls[c].type == CLS_EDGE) edges.push_back(c);
+        else faces.push_back(c);
+      }
+      if (has_vertex) continue;
+      const std::vector<int> &cand = edges.empty() ? faces : edges;
+      if (cand.empty()) continue;
+      std::vector<char> drop(cls.size(), 0);
+      std::vector<Cls> out;
+      for (int c : cand) drop[c] = 1;
+      for (int c = 0; c < (int)cls.size(); ++c)
+        if (!drop[c]) out.push_back(cls[c]);
+      for (int c : cand) {
+        const Cls &old = cls[c];
+        Cls v = make({old.nodes[0]}, old.subs);
+        v.type = CLS_VERTEX;  // promoted, whatever |N_x|
+        out.push_back(v);
+        std::set<int> rest(old.nodes.begin() + 1, old.nodes.end()), seen;
+        for (int x : rest) {
+          if (seen.count(x)) continue;
+          std::vector<int> stack{x}, comp;
+          seen.insert(x);
+          while (!stack.empty()) {
+            int y = stack.back();
+            stack.pop_back();
+            comp.push_back(y);
+            for (int z : adj[y])
+              if (rest.count(z) && !seen.count(z)) {
+                seen.insert(z);
+                stack.push_back(z);
+              }
+          }
+          out.push_back(make(comp, old.subs));
+        }
+      }
+      std::sort(out.begin(), out.end(), by_type_first);
+      cls.swap(out);
+    }
+  }
   p.n_cls = (int)cls.size();
   p.cls_type.resize(p.n_cls);
   p.cls_ptr.assign(1, 0); p.cls_nodes.clear(); p.cls_sub_ptr.assign(1, 0); p.cls_subs.clear();

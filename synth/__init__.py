@@ -25,6 +25,14 @@ Workloads (all Q1 hexahedral slabs, h = element size):
 * ``ell10``    10x9x6 elements of the same ellipsoid, 4^3-element blocks with
                ragged last blocks.
 * ``ell32``    32x32x16 elements of the same ellipsoid, 4x4x2 subdomains, H/h = 8.
+* ``shell_small`` / ``shell``  the uneven batch: the lower half (z <= 0) of an ellipsoidal
+               shell (inner semi-axes 2.0, 2.0, 5.0 cm, outer 2.8, 2.8, 5.8 cm) meshed by a
+               box grid of Q1 elements of size h with the elements whose centroid lies
+               outside the shell masked, split into blocks of s^3 elements whose
+               connected pieces are the subdomains (uneven in size).  ``shell``: h =
+               0.045 cm, 12^3-element blocks (about 1.2 M unknowns, the uneven-batch
+               configuration); ``shell_small``: h = 0.35 cm, 4^3-element blocks, for the
+               oracle.  Stimulus: the apex of the wall.
 * ``beat_slab`` / ``beat_ell``  the whole-beat runs of Test 4: 192x96x24 elements,
                8x8x2 subdomains (8,450 dofs each), 2,400 / 3,400 steps;
                ``beat_*_half`` halve each mesh direction; ``beat_mini`` is a
@@ -55,6 +63,12 @@ ELLIPSOID = dict(axes=(1.5, 2.7, 1.5, 2.7, 4.4, 5.0), phi=(-np.pi / 2, 0.0), the
 STIMULUS_ELLIPSOID = dict(amp=100.0, t_on=0.0, t_off=1.0,
                           box=(-np.pi / 2, 0.0, -3 * np.pi / 8, np.pi / 8, 0.0, 0.0))
 
+# the masked shell: inner and outer semi-axes (cm) of the lower half of an ellipsoidal wall
+SHELL = dict(inner=(2.0, 2.0, 5.0), outer=(2.8, 2.8, 5.8))
+# its stimulus: the apex of the wall (box-grid coordinates; the grid's origin is the
+# corner (-2.8, -2.8, -5.8) of the shell's bounding box)
+STIMULUS_SHELL = dict(amp=100.0, t_on=0.0, t_off=1.0, box=(2.45, 3.15, 2.45, 3.15, 0.0, 0.35))
+
 WORKLOADS = {
     "tiny": dict(n=(2, 2, 2), l=(0.1, 0.1, 0.1), s=(1, 1, 1), primal="V", steps=1),
     "ragged": dict(n=(10, 9, 7), l=(0.5, 0.45, 0.35), s=(4, 4, 4), primal="VE", steps=2),
@@ -83,15 +97,41 @@ for _k in (4, 8, 12, 16, 20):
                                  primal="VE", steps=40)
 
 
+for _name, _h, _s in (("shell_small", 0.35, 4), ("shell", 0.045, 12)):
+    _n = (int(np.ceil(5.6 / _h - 1e-9)), int(np.ceil(5.6 / _h - 1e-9)), int(np.ceil(5.8 / _h - 1e-9)))
+    WORKLOADS[_name] = dict(n=_n, l=tuple(_h * v for v in _n), s=(_s, _s, _s), primal="VE", shell=SHELL,
+                            steps=50)
+
+
+def shell_mask(n, l, shell):
+    """1 for the elements whose centroid lies in the lower half (z <= 0) of the wall between
+    the inner and the outer ellipsoid, in the grid's element order (x fastest); the grid's
+    origin is the corner (-a_out, -b_out, -c_out) of the shell's bounding box."""
+    (ai, bi, ci), (ao, bo, co) = shell["inner"], shell["outer"]
+    h = [l[d] / n[d] for d in range(3)]
+    ex, ey, ez = np.meshgrid(np.arange(n[0]), np.arange(n[1]), np.arange(n[2]), indexing="ij")
+    x = (ex.ravel(order="F") + 0.5) * h[0] - ao
+    y = (ey.ravel(order="F") + 0.5) * h[1] - bo
+    z = (ez.ravel(order="F") + 0.5) * h[2] - co
+    r_in = (x / ai) ** 2 + (y / bi) ** 2 + (z / ci) ** 2
+    r_out = (x / ao) ** 2 + (y / bo) ** 2 + (z / co) ** 2
+    return ((z <= 0.0) & (r_in >= 1.0) & (r_out <= 1.0)).astype(np.uint8)
+
+
 def workload(name: str) -> dict:
-    """Return a copy of a named workload description."""
+    """Return a copy of a named workload description (with its element mask, if any)."""
     w = dict(WORKLOADS[name])
     w["name"] = name
+    if "shell" in w:
+        w["mask"] = shell_mask(w["n"], w["l"], w["shell"])
     return w
 
 
 def stimulus(w: dict) -> dict:
-    """The stimulus of a workload: a corner box of a slab, the endocardium of the ellipsoid."""
+    """The stimulus of a workload: a corner box of a slab, the endocardium of the ellipsoid,
+    the apex of the masked shell."""
+    if "shell" in w:
+        return dict(STIMULUS_SHELL)
     return dict(STIMULUS_ELLIPSOID if "ellipsoid" in w else STIMULUS)
 
 

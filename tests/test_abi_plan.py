@@ -34,9 +34,9 @@ def test_strerror_and_bad_args(lib):
     bad = dict(w, s=(0, 4, 4))
     with pytest.raises(binding.BidomainError):
         binding.Plan(bad)
-    # a 2x1x1 split has no vertex: no gauge, no primal constraint
+    # one subdomain: no interface, so no vertex to hold the gauge
     with pytest.raises(binding.BidomainError):
-        binding.Plan(dict(w, s=(4, 8, 8)))
+        binding.Plan(dict(w, s=(8, 8, 8)))
     # ellipsoid ranges must avoid the poles and have positive axes
     e = synth.workload("ell8")
     for bad in (dict(e["ellipsoid"], theta=(-1.0, 1.6)), dict(e["ellipsoid"], phi=(0.5, 0.0)),
@@ -77,7 +77,7 @@ def _oracle_sets(prob):
 
 
 @pytest.mark.parametrize("name", ["tiny", "cube8", "cube8ve", "cube8vef", "ragged", "opt4", "ell8", "ell10",
-                                  "coarse2k"])
+                                  "coarse2k", "shell_small"])
 def test_index_sets_bit_exact(lib, name):
     prob = oracle_problem(name)
     plan = binding.Plan(prob.workload)
@@ -111,3 +111,23 @@ def test_setup_rejects_bad_options_before_touching_the_device(lib, bad):
     with pytest.raises(binding.BidomainError) as e:
         binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, **bad)
     assert binding.ERRORS[e.value.code] == "BD_ERR_ARG"
+
+
+def test_vertexless_split_promotes_a_vertex(lib):
+    """Two subdomains side by side (2x1x1 blocks of the 8^3 cube) share only a face: the
+    first subdomain has no vertex, so the lowest-id node of that face (grid node (4,0,0),
+    id 4) becomes a vertex and the other 80 nodes of the x = 4 plane stay a face; the
+    oracle applies the same rule."""
+    w = dict(synth.workload("cube8"), s=(4, 8, 8), primal="VE")
+    plan = binding.Plan(w)
+    assert plan.index_set("CLS_TYPE").tolist() == [0, 2]
+    assert plan.index_set("CLS_PTR").tolist() == [0, 1, 81]
+    nodes = plan.index_set("CLS_NODES")
+    assert nodes[0] == 4 and sorted(nodes[1:]) == sorted(x + 9 * y + 81 * z for z in range(9) for y in range(9)
+                                                          for x in (4,) if (y, z) != (0, 0))
+    assert plan.sizes()["n_primal"] == 2 and plan.index_set("GAUGE").tolist() == [4, 1]
+    from oracle.bidomain import Problem
+    prob = Problem(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, synth.stimulus(w))
+    ref = _oracle_sets(prob)
+    for k, v in ref.items():
+        np.testing.assert_array_equal(plan.index_set(k), np.asarray(v, np.int64), err_msg=k)

@@ -14,42 +14,49 @@ def _solver(name, **opt):
     return binding.Solver(synth.workload(name), synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, **opt)
 
 
-def _bf16(a):
-    """Round float32 values to bfloat16 (round to nearest even), as the GPU weights are."""
-    b = np.ascontiguousarray(a, np.float32).view(np.uint32)
-    r = ((b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000).astype(np.uint32)
-    return r.view(np.float32)
-
-
-def test_mlp_loss_and_gradients_match_oracle():
-    s = _solver("cube8ve", learned_guess=1)
+@pytest.mark.parametrize("name", ["ragged", "slab128"])
+def test_mlp_loss_and_gradients_match_oracle(name):
+    """The tensor-core network (bf16 operands, FP32 accumulation) against the oracle's
+    FP64 network with the same bf16 rounding points: loss, and every gradient entry
+    against its block's largest entry.  What remains is FP32 accumulation order and the
+    rare bf16 rounding of an activation that lands on the other side of a midpoint."""
+    s = _solver(name, learned_guess=1, precision="mixed")
     sz = s.mlp_sizes()
     n_in, H, n_out, B = sz["n_in"], sz["n_hidden"], sz["n_out"], sz["batch"]
+    assert n_in % 6 == 0 and n_out * 3 == n_in
+    if name == "slab128":  # the 128x128x32 slab: 386 interface nodes per H/h = 8 subdomain
+        assert (n_in, H, n_out, B) == (2316, 256, 772, 1024)
     rng = np.random.default_rng(7)
     p = mlp.init_params(n_in, H, n_out, seed=3)
     for k in ("b1", "b2", "b3"):
         p[k] = 0.01 * rng.standard_normal(p[k].shape)
     for k in ("W1", "W2", "W3"):
-        p[k] = _bf16(p[k]).astype(np.float64)  # the oracle runs on the bfloat16 weights
+        p[k] = mlp.bf16(p[k])  # the GPU's masters are FP32; these are exact in bf16 already
     w = np.concatenate([p["W1"].ravel(), p["b1"], p["W2"].ravel(), p["b2"], p["W3"].ravel(), p["b3"]])
     s.mlp_params(w.astype(np.float32))
     X = rng.standard_normal((B, n_in)).astype(np.float32)
-    T = rng.standard_normal((B, n_out)).astype(np.float32)
+    T = (0.1 * rng.standard_normal((B, n_out))).astype(np.float32)
     mask = (rng.random((B, n_out)) < 0.8).astype(np.float32)
     loss, g = s.mlp_loss_grad(X, T, mask)
-    L, gr = mlp.loss_and_grads(p, X.astype(np.float64), T.astype(np.float64), mask.astype(np.float64))
-    assert abs(loss - L) < 1e-5 * L
+    L, gr = mlp.loss_and_grads(p, X.astype(np.float64), T.astype(np.float64), mask.astype(np.float64), bf=True)
+    assert abs(loss - L) < 1e-4 * L
+    # bars: a bf16 rounding point whose FP32 value (GPU) and FP64 value (oracle) fall on the
+    # two sides of a rounding midpoint rounds 2^-8 apart; over a batch the number of such
+    # flips grows, and a numpy FP32 run of the same network differs from the oracle by
+    # 1e-8 (batch 18) and 2.3e-4 (batch 1,024, 2,316 inputs) in the W1 gradient's norm;
+    # the tensor cores' FP32 accumulation order adds a factor of about 3
+    tol_norm, tol_max = (5e-4, 2e-3) if B <= 64 else (2e-3, 5e-3)
     off = 0
     for k, shape in (("W1", (H, n_in)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (n_out, H)),
                      ("b3", (n_out,))):
         n = int(np.prod(shape))
         got = g[off:off + n].astype(np.float64)
         ref = gr[k].ravel()
-        assert np.linalg.norm(got - ref) <= 1e-4 * np.linalg.norm(ref), k
-        # entry by entry, against the block's largest entry
-        assert np.max(np.abs(got - ref)) <= 1e-4 * np.max(np.abs(ref)), k
+        assert np.linalg.norm(got - ref) <= tol_norm * np.linalg.norm(ref), k
+        assert np.max(np.abs(got - ref)) <= tol_max * np.max(np.abs(ref)), k  # entry by entry
         off += n
     assert off == g.size
+    s.close()
 
 
 def test_adam_matches_oracle_over_steps():

@@ -73,7 +73,8 @@ def _linearized(name, **opt):
 
 @pytest.mark.parametrize("name,scaling", [("tiny", "deluxe"), ("cube8", "deluxe"), ("cube8ve", "deluxe"),
                                           ("cube8vef", "deluxe"), ("ragged", "deluxe"), ("cube8ve", "rho"),
-                                          ("ragged", "rho"), ("ell8", "deluxe"), ("ell10", "deluxe")])
+                                          ("ragged", "rho"), ("ell8", "deluxe"), ("ell10", "deluxe"),
+                                          ("shell_small", "deluxe")])
 def test_operators_match_oracle(name, scaling):
     prob, s, dd, _ = _linearized(name, precision="fp64", scaling=scaling)
     n = prob.dofs.n_iface
@@ -90,7 +91,7 @@ def test_operators_match_oracle(name, scaling):
 
 @pytest.mark.parametrize("name,krylov", [("tiny", "pcg"), ("cube8", "pcg"), ("cube8ve", "pcg"), ("ragged", "pcg"),
                                          ("cube8ve", "gmres"), ("ragged", "gmres"), ("cube8vef", "pcg"),
-                                         ("cube8vef", "gmres"), ("ell8", "pcg")])
+                                         ("cube8vef", "gmres"), ("ell8", "pcg"), ("shell_small", "pcg")])
 @pytest.mark.parametrize("method", ["bddc", "fetidp"])
 def test_jacobian_solve_fp64(name, method, krylov):
     prob = oracle_problem(name)
@@ -145,14 +146,21 @@ def _oracle_steps(prob, nsteps, method="bddc", krylov="pcg"):
     ("cube8vef", "bddc", "mixed", 1e-8, 1, "pcg"),
     ("ell8", "bddc", "fp64", 1e-9, 0, "pcg"),
     ("ell10", "fetidp", "mixed", 1e-8, 1, "pcg"),
+    ("shell_small", "fetidp", "fp64", 1e-9, 0, "pcg"),
+    ("shell_small", "bddc", "mixed+tc", 1e-8, 1, "pcg"),
 ])
 def test_time_steps_match_oracle(name, method, precision, tol, graphs, krylov):
     prob = oracle_problem(name)
     ref = _oracle_steps(prob, 3, method, krylov)
     tc, lag = "+tc" in precision, "+lag" in precision
+    # the mixed-precision Newton steps are inexact (FP32 operator): at rtol 1e-10 they stop with a
+    # residual left in the smooth near-null modes of J, which the ellipsoid's Jacobian amplifies
+    # to about 2e-8 in u_e; converged to 1e-12 the comparison measures the solution itself (the
+    # oracle's exact Newton steps move its state by 1e-12 between rtol 1e-10 and 1e-13)
+    mixed = precision.startswith("mixed")
     s = _solver(name, method=method, krylov=krylov, precision=precision.split("+")[0], ksp_rtol=1e-12,
-                ksp_atol=0.0, snes_rtol=1e-10, snes_atol=1e-16, use_graphs=graphs, use_tensor_cores=int(tc),
-                lag_jacobian=int(lag))
+                ksp_atol=0.0, snes_rtol=1e-12 if mixed else 1e-10, snes_atol=1e-16, use_graphs=graphs,
+                use_tensor_cores=int(tc), lag_jacobian=int(lag))
     ui, ue, w = synth.initial_state(prob.N, 0)
     s.set_state(ui, ue, w, 0.0)
     for n in range(3):
@@ -188,7 +196,8 @@ def test_slab32_first_step_vs_direct_solve():
     rui, rue, _, _ = time_step(prob, ui, ue, w, 0, lambda kc, a, b: direct_solve(prob, kc, a, b),
                                rtol=1e-10, atol=1e-16)
     for precision in ("fp64", "mixed"):
-        s = _solver("slab32", precision=precision, ksp_rtol=1e-12, ksp_atol=0.0, snes_rtol=1e-10, snes_atol=1e-16)
+        s = _solver("slab32", precision=precision, ksp_rtol=1e-12, ksp_atol=0.0,
+                    snes_rtol=1e-12 if precision == "mixed" else 1e-10, snes_atol=1e-16)
         s.set_state(ui, ue, w, 0.0)
         st = s.step(synth.STIMULUS)
         assert st["reason"] == 0
@@ -227,7 +236,10 @@ def test_tensor_core_schur_matches_fp64():
         N = prob.N
         v_k = out[k][1][:N] - out[k][1][N:]
         v_r = out["fp64"][1][:N] - out["fp64"][1][N:]
-        assert _rel(v_k, v_r) < 1e-4
+        # 2-norm 1e-4; entry-wise the largest error sits where v is small next to large
+        # neighbours (the FP32 operator's error is smooth, v is not): 3e-4 of the largest entry
+        assert np.linalg.norm(v_k - v_r) < 1e-4 * np.linalg.norm(v_r)
+        assert np.max(np.abs(v_k - v_r)) < 3e-4 * np.max(np.abs(v_r))
         d = out[k][1] - out["fp64"][1]
         d = d - d.mean()
         assert np.linalg.norm(d) < 5e-3 * np.linalg.norm(out["fp64"][1])
@@ -356,7 +368,7 @@ def test_lagged_preconditioner_time_steps():
     name = "cube8ve"
     prob = oracle_problem(name)
     ref = _oracle_steps(prob, 3)
-    s = _solver(name, precision="mixed", ksp_rtol=1e-12, ksp_atol=0.0, snes_rtol=1e-10, snes_atol=1e-16,
+    s = _solver(name, precision="mixed", ksp_rtol=1e-12, ksp_atol=0.0, snes_rtol=1e-12, snes_atol=1e-16,
                 precond_every=3, use_graphs=1)
     ui, ue, w = synth.initial_state(prob.N, 0)
     s.set_state(ui, ue, w, 0.0)
@@ -390,7 +402,7 @@ def test_bench_configuration_matches_oracle(name):
     stim = synth.stimulus(prob.workload)
     s = _solver(name, precision="mixed", use_tensor_cores=1, lag_jacobian=1, learned_guess=1,
                 mlp_train_steps=nsteps, mlp_warmup=3, use_graphs=1, ksp_rtol=1e-12, ksp_atol=0.0,
-                snes_rtol=1e-10, snes_atol=1e-16)
+                snes_rtol=1e-12, snes_atol=1e-16)
     ui, ue, w = synth.initial_state(prob.N, 0)
     s.set_state(ui, ue, w, 0.0)
     s.step(stim)
@@ -460,7 +472,8 @@ def test_coarse_problem_above_1024_unknowns(precision, tol):
     prob = oracle_problem(name)
     assert prob.part.n_primal > 1024
     ref = _oracle_steps_direct(prob, 2)
-    s = _solver(name, precision=precision, ksp_rtol=1e-12, ksp_atol=0.0, snes_rtol=1e-10, snes_atol=1e-16,
+    s = _solver(name, precision=precision, ksp_rtol=1e-12, ksp_atol=0.0,
+                snes_rtol=1e-12 if precision == "mixed" else 1e-10, snes_atol=1e-16,
                 use_graphs=1)
     ui, ue, w = synth.initial_state(prob.N, 0)
     s.set_state(ui, ue, w, 0.0)
@@ -485,3 +498,35 @@ def test_coarse_problem_above_1024_unknowns(precision, tol):
         assert sst["reason"] == 0
         assert _rel(x, np.concatenate([si, se])) < 1e-10, method
         s.close()
+
+
+@pytest.mark.parametrize("name,precision", [("cube8ve", "fp64"), ("ell8", "fp64"), ("coarse2k", "fp64"),
+                                            ("coarse2k", "mixed"), ("ell8", "mixed")])
+def test_coarse_matrix_and_fp64_coarse_solve(name, precision):
+    """S_PiPi (Section 4.4) as the GPU assembles it equals the oracle's coarse matrix (gauge
+    row and column pinned), and the coarse solve the preconditioner applies is FP64-accurate
+    for it: backward error at FP64 rounding, also from the FP32 explicit inverse of BD_MIXED
+    (whose error alone is orders of magnitude larger)."""
+    import scipy.sparse as sp
+    prob, s, dd, _ = _linearized(name, precision=precision)
+    n = prob.part.n_primal
+    g = prob.part.gauge_primal
+    ptr, col, val = s.coarse_matrix()
+    S = sp.csr_matrix((val, col, ptr), shape=(n, n)).toarray()
+    ref = dd.SPP.copy()
+    ref[g, :] = 0.0
+    ref[:, g] = 0.0
+    ref[g, g] = 1.0
+    # FP64: rounding of the local Schur complements; BD_MIXED assembles FP32 local blocks
+    assert _rel(S, ref) < (1e-10 if precision == "fp64" else 1e-3)
+    c = synth.random_vector(n, 21)
+    c[g] = 0.0
+    nS = np.linalg.norm(S, 2)
+    back = lambda z: np.linalg.norm(S @ z - c) / (nS * np.linalg.norm(z))  # noqa: E731
+    z = s.coarse_solve(c)
+    assert back(z) < 1e-15
+    z0 = s.coarse_solve(c, nref=0)
+    if precision == "mixed" and n > 320:  # the FP32 inverse of a large coarse problem alone
+        assert back(z0) > 100 * back(z)
+    np.testing.assert_allclose(z, np.linalg.solve(S, c), rtol=0, atol=1e-12 * np.abs(z).max() * np.linalg.cond(S))
+    s.close()

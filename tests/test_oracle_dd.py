@@ -20,7 +20,7 @@ def _jacobian_system(prob, seed=0):
 
 
 @pytest.mark.parametrize("name,scaling", [("tiny", "deluxe"), ("cube8", "deluxe"), ("cube8ve", "deluxe"),
-                                          ("ragged", "deluxe"), ("cube8ve", "rho")])
+                                          ("ragged", "deluxe"), ("cube8ve", "rho"), ("shell_small", "deluxe")])
 @pytest.mark.parametrize("method", ["bddc", "fetidp"])
 @pytest.mark.parametrize("krylov", ["pcg", "gmres"])
 def test_dd_matches_direct(name, scaling, method, krylov):
@@ -40,7 +40,7 @@ def _local_dual_vectors(dd, seed):
 
 
 @pytest.mark.parametrize("name,scaling", [("cube8", "deluxe"), ("cube8ve", "deluxe"), ("ragged", "deluxe"),
-                                          ("cube8ve", "rho"), ("ragged", "rho")])
+                                          ("cube8ve", "rho"), ("ragged", "rho"), ("shell_small", "deluxe")])
 def test_deluxe_projection_and_pd(name, scaling):
     prob = oracle_problem(name)
     kc, _, _ = _jacobian_system(prob)
@@ -239,3 +239,32 @@ def test_lagged_preconditioner_time_steps():
     fresh, lag = its[1, False], its[4, False]
     assert len(fresh) == len(lag)
     assert lag.max() <= fresh.max() + 3
+
+
+def test_masked_shell_has_uneven_subdomains_and_promoted_vertices():
+    """The masked shell (the uneven batch): subdomains are the connected pieces of the
+    blocks inside the wall, of very different sizes; every one has a vertex on its
+    interface after the promotion rule, and the promoted vertices are exactly the lowest
+    nodes of the edge classes of the fragments that had none."""
+    from oracle.mesh import VERTEX, Mesh, Partition
+    prob = oracle_problem("shell_small")
+    p = prob.part
+    sizes = np.array([len(x) for x in p.sub_nodes])
+    assert sizes.min() * 5 < sizes.max()
+    assert all(any(p.cls_type[c] == VERTEX for c in p.sub_classes(j)) for j in range(p.n_sub))
+    w = prob.workload
+    orig = Partition._promote_vertices  # the classes without the promotion rule, for comparison
+    try:
+        Partition._promote_vertices = lambda self, classes, adj: classes
+        raw = Partition(Mesh(w["n"], w["l"], elem_mask=w["mask"]), w["s"], "VE")
+    finally:
+        Partition._promote_vertices = orig
+    lacking = [j for j in range(raw.n_sub) if not any(raw.cls_type[c] == VERTEX for c in raw.sub_classes(j))]
+    assert lacking
+    new_vertices = {int(p.cls_nodes[c][0]) for c in range(p.n_cls) if p.cls_type[c] == VERTEX} - \
+        {int(raw.cls_nodes[c][0]) for c in range(raw.n_cls) if raw.cls_type[c] == VERTEX}
+    expect = set()
+    for j in lacking:  # in subdomain order, as the rule applies
+        mine = [c for c in range(raw.n_cls) if j in raw.cls_subs[c] and raw.cls_type[c] == 1]
+        expect |= {int(raw.cls_nodes[c][0]) for c in mine}
+    assert new_vertices <= expect and new_vertices
