@@ -283,14 +283,14 @@ def solve_values_per_sub(k):
     return 2.0 * 1.5 * pd * md ** 2, 2.0 * 1.5 * pn * mn ** 2
 
 
-# DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum of one capture, see
-# profiles/), kept with the first 16 hex digits of the sha256 of the kernel's source text: a
-# figure stands only while that text is unchanged, and is reported as null otherwise.
+# DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum of one capture), kept
+# with the first 16 hex digits of the sha256 of the kernel's source text: a figure stands only
+# while that text is unchanged, and is reported as null otherwise.
 TRAFFIC = {
     "k_rankk_tc": {"bytes_per_launch": None, "sha": None, "file": "tc.cu",
-                   "span": ("__global__ void __launch_bounds__(128, 1) k_rankk_tc(",
+                   "span": ("__global__ void __launch_bounds__(128, 3) k_rankk_tc(",
                             "static constexpr int kTcSmem")},
-    # DRAM bytes per library byte (slab32 capture, profiles/gemv_slab32_traffic.md): the operator
+    # DRAM bytes per library byte (a capture of three launches on the 32x32x16 slab): the operator
     # and local-solve launches read their matrices once; scaled to a launch by its own bytes
     "k_gemv": {"dram_per_library_byte": 1.013, "sha": "2c1f86b0689c36b0", "file": "dense.cu",
                "span": ("__global__ void __launch_bounds__(256) k_gemv(",
@@ -354,6 +354,9 @@ def roofline(prof, regions, w, precision, tc_used, sub_nodes):
     if f_ms > 0 and n_jac > 0:
         algo = sum(factor_flops_per_sub(int(kj)) for kj in ks) * n_jac
         lib = prof["panel"]["flops"] + prof["rankk"]["flops"]
+        f_capped = uneven and algo > lib
+        if f_capped:  # as for the Krylov bytes below: a fragment's factors cost less than the box's
+            algo = lib
         if precision == "mixed" and tc_used:
             src = "bf16_tflops_sustained" if "bf16_tflops_sustained" in pk else None
             peak = (pk[src] if src else 1700.0) * 1.1 / 2.25 / 3.0
@@ -377,13 +380,19 @@ def roofline(prof, regions, w, precision, tc_used, sub_nodes):
             "work": (f"{factor_flops_per_sub(k):.3g} flop per H/h={k} subdomain x {nsub} subdomains "
                      if not uneven else f"sum over {nsub} uneven subdomains of the flops of a box of the same node "
                      f"count (H/h {ks.min()}..{ks.max()}) ") +
-                    "(banded Dirichlet + Neumann factors, L_II^-1 K_IG, face SYRKs, Phi)"}
+                    "(banded Dirichlet + Neumann factors, L_II^-1 K_IG, face SYRKs, Phi)" +
+                    ("; above the flops the launches do, so capped to them" if f_capped else "")}
     # Krylov: one Dirichlet + one Neumann local solve per subdomain and iteration
     g = prof["gemv"]
     if g["ms"] > 0 and g["launches"] > 0:
         vals = sum(sum(solve_values_per_sub(int(kj))) for kj in ks)
         vd, vn = solve_values_per_sub(k)
         algo = (g["launches"] / 2.0) * vals * el
+        # a masked fragment is flatter than the box of the same node count, so its banded factors
+        # hold fewer values than the box model counts: there the bytes the launches read bound it
+        capped = uneven and algo > g["bytes"]
+        if capped:
+            algo = g["bytes"]
         ach = algo / (g["ms"] * 1e-3) / 1e9
         peak = pk.get("hbm_gbs", 6800.0)
         out["krylov"] = {
@@ -397,7 +406,8 @@ def roofline(prof, regions, w, precision, tc_used, sub_nodes):
                      f"solve, read forward and back) x {nsub} subdomains" if not uneven else
                      f"factor values of one Dirichlet + one Neumann solve (read forward and back) summed over "
                      f"{nsub} uneven subdomains as boxes of the same node count") +
-                    f" x {el} B, split over the 2 GEMV launches"}
+                    f" x {el} B, split over the 2 GEMV launches" +
+                    ("; above the bytes the launches read, so capped to them" if capped else "")}
     if not out:
         return None, None
     dom = max(out, key=lambda c: (prof["panel"]["ms"] + prof["rankk"]["ms"]) if c == "factorisation"

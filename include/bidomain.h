@@ -299,7 +299,7 @@ int krylov_solve(bd_handle *h, const double *f, double *s, int on_device, bd_sol
  * explicit inverse followed by `nref` steps of FP64 iterative refinement
  * z += X (c - S_PiPi z) (nref < 0: the handle's own count).  Up to 320 coarse unknowns
  * the inverse is brought to FP64 once per Jacobian (Newton-Schulz) and refined once per
- * solve; above, it is kept in the local precision (FP32 in BD_MIXED, refined 3 times per
+ * solve; above, it is kept in the local precision (FP32 in BD_MIXED, refined 4 times per
  * solve; FP64 in BD_FP64, refined once).  Host buffers; the handle must be linearised. */
 int bidomain_coarse_size(bd_handle *h, int *n_primal, int *nnz);
 int bidomain_coarse_matrix(bd_handle *h, int *rowptr, int *col, double *val);

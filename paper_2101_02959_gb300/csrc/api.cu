@@ -986,7 +986,7 @@ void linearize_t(bd_handle &h, Dense<T> &D, bool precond) {
   run_engine_groups<T>(h, h.shA, h.d_Adesc, D.Aug, D.Linv);
   launch_copy<T, T>(h.cp_zx.n, h.cp_zx.max_elems, h.cp_zx.d, D.Aug, D.Z, s);
   launch_class_aug<T>(h.ncls, h.max_nc, h.d_cls, h.d_pairs, D.Blk, h.d_Cdesc, D.CA, s);
-  engine_partial_cholesky<T>(h.shC, h.d_Cdesc, D.CA, h.d_err, s, D.Linv);
+  engine_partial_cholesky<T>(h.shC, h.d_Cdesc, D.CA, h.d_err, s, D.Linv, &h.prof, h.opt.use_tensor_cores != 0);
   launch_copy<T, T>(h.cp_sinv.n, h.cp_sinv.max_elems, h.cp_sinv.d, D.CA, D.Sinv, s);
   if (h.opt.scaling == BD_SCALING_RHO) {
     const double si = std::max({h.fp.sigma_i[0], h.fp.sigma_i[1], h.fp.sigma_i[2]});
@@ -1000,7 +1000,11 @@ void linearize_t(bd_handle &h, Dense<T> &D, bool precond) {
   if (h.d_Co64d) ck(cudaMemsetAsync(h.d_Co64d, 0, sizeof(double) * (size_t)h.np * h.np, s), "memset coarse");
   launch_coarse_assemble<T>(h.co_nnz, h.np, h.gauge_primal, h.d_co_row, h.d_co_col, h.d_co_sptr, h.d_co_src, D.Aug,
                             h.d_Co64, D.Co, h.ld_co, h.d_Co64d, s);
-  engine_partial_cholesky<T>(h.shCo, h.d_Codesc, D.Co, h.d_err, s, D.LdCo);
+  {  // one large matrix: its trailing updates go to the tensor cores like the local ones
+    EngineShape co = h.shCo;
+    co.ob = h.tune_ob;
+    engine_partial_cholesky<T>(co, h.d_Codesc, D.Co, h.d_err, s, D.LdCo, &h.prof, h.opt.use_tensor_cores != 0);
+  }
   launch_copy<T, T>(h.cp_coinv.n, h.cp_coinv.max_elems, h.cp_coinv.d, D.Co, D.CoInv, s);
   if (h.d_CoInv64) coarse_refine64<T>(h.np, D.CoInv, pad8(h.np), h.d_Co64d, h.d_CoInv64, h.d_CoW, h.d_CoY, s);
 }

@@ -7,11 +7,11 @@
 // (three MMAs per K step, FP32 accumulation in tensor memory), which keeps the
 // Schur complement at FP32 accuracy.
 //
-// Per K chunk of 32: 128 threads load the two 128 x 32 tiles (cp.async, two
-// chunks ahead), split them and store hi / lo copies in shared memory in the
-// K-major layout with the 128-byte swizzle; one thread issues the MMAs and
-// commits them to an mbarrier; the CTA waits on it (bounded) before reusing the
-// buffers.  The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
+// Per K chunk of 32: the 128 threads hold the two 128 x 32 FP32 tiles in registers
+// (loaded while the previous chunk's MMAs ran), split them and store hi / lo copies
+// in shared memory in the K-major layout with the 128-byte swizzle; one thread issues
+// the MMAs and commits them to an mbarrier, which the CTA waits on (bounded) before
+// the next split reuses the buffer.  Three CTAs share an SM.  The epilogue reads the accumulator with tcgen05.ld (warp w owns TMEM
 // lanes 32w .. 32w+31 = tile rows), stages it in shared memory and subtracts it
 // from C row by row (coalesced).
 #include <cuda_runtime.h>
@@ -26,7 +26,6 @@ namespace {
 constexpr int kTM = 128;          // tile rows (MMA M) and columns (MMA N)
 constexpr int kKc = 32;           // fp32 K elements per chunk = one 128-byte swizzle row
 constexpr int kTileBytes = kTM * kKc * 4;  // 16 KB per operand copy
-constexpr int kRawStages = 3;              // FP32 load stages (prefetch distance 2 chunks)
 constexpr uint32_t kTmemCols = 128;
 constexpr long long kWaitLimit = 1LL << 22;
 
@@ -83,16 +82,14 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t phase) {
 
 }  // namespace
 
-__device__ inline void cp_async16(uint32_t dst, const void *src, uint32_t bytes) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes));
-}
-
 // mode 1: rows/cols [e, m), K = [0, e); mode 2: rows [K1, m), cols [K1, e), K = [K0, K1).
-// Pipeline per K chunk i (raw stage i % 3, operand buffer b = i % 2):
-//   raw (FP32 A and B tiles, cp.async, swizzled) -> split into hi/lo[b] -> 12 MMAs on hi/lo[b]
-// with the loads of chunks i+1 and i+2 in flight during the split of chunk i and the
-// MMAs of chunk i running while chunk i+1 is split (mbar[b] guards hi/lo[b] against reuse).
-__global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__ desc, float *__restrict__ base,
+// Per K chunk i of 32 FP32 columns: every thread holds its share of chunk i in registers
+// (loaded while the MMAs of chunk i - 1 ran), waits (bounded) for those MMAs to release the
+// single hi/lo operand buffer, splits its values into TF32 hi and lo parts there (128-byte
+// swizzled K-major layout), and thread 0 issues the 12 MMAs of the chunk; then the loads of
+// chunk i + 1 go out while they run.  65 KB of shared memory per CTA let three CTAs share an
+// SM, so one CTA's split, epilogue or pipeline fill overlaps the others' MMAs.
+__global__ void __launch_bounds__(128, 3) k_rankk_tc(const MatDesc *__restrict__ desc, float *__restrict__ base,
                                                      int mode, int K0, int K1, int nct, int *__restrict__ err) {
   const MatDesc d = desc[blockIdx.y];
   int row0, colend, kb, ke;
@@ -106,17 +103,15 @@ __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__
   if (tj > ti) return;
   const int r0 = row0 + ti * kTM, c0 = row0 + tj * kTM;
   if (r0 >= d.m || c0 >= colend || ke <= kb) return;
-  float *A = base + d.off;
+  const float *A = base + d.off;
 
   extern __shared__ unsigned char smem_raw[];
-  __shared__ uint64_t mbar[2];
+  __shared__ uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   const uint32_t raw0 = smem_addr(smem_raw);
   const uint32_t tiles = (raw0 + 1023u) & ~1023u;
   unsigned char *tp = smem_raw + (tiles - raw0);
-  // layout: raw A/B per stage (kRawStages x 2 x 16 KB), then hi/lo A/B per buffer (2 x 4 x 16 KB)
-  auto raw_off = [](int b, int op) { return (uint32_t)((b * 2 + op) * kTileBytes); };
-  auto op_off = [](int b, int q) { return (uint32_t)(2 * kRawStages * kTileBytes + (b * 4 + q) * kTileBytes); };
+  auto op_off = [](int q) { return (uint32_t)(q * kTileBytes); };  // q: A hi, A lo, B hi, B lo
   const int tid = threadIdx.x, warp = tid >> 5;
 
   if (warp == 0) {
@@ -125,8 +120,7 @@ __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[0])), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[1])), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
@@ -136,77 +130,72 @@ __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__
   const uint32_t idesc = idesc_tf32();
   const int j = tid & 7, rr = tid >> 3;
 
-  // asynchronous load of chunk starting at kk into raw buffer b (zero fill outside the matrix / K range)
-  auto load = [&](int kk, int b) {
+  // this thread's share of a chunk: rows rr + 16 i (i < 8) of the A and B tiles, columns
+  // kk + 4 j .. + 3; zero outside the matrix and past the K range
+  float4 ra[8], rb[8];
+  auto load = [&](int kk) {
+    const int k = kk + 4 * j;
+    const int kv = max(0, min(4, ke - k));
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int r = rr + 16 * i;
-      const int k = kk + 4 * j;
-      const uint32_t off = (uint32_t)r * 128u + (uint32_t)((j ^ (r & 7)) * 16);
-      const int kv = max(0, min(4, ke - k));
-      const int ra = r0 + r, rb = c0 + r;
-      const uint32_t na = (ra < d.m) ? 4u * kv : 0u, nb = (rb < colend) ? 4u * kv : 0u;
-      const float *sa = na ? A + (long long)ra * d.ld + k : A;
-      const float *sb = nb ? A + (long long)rb * d.ld + k : A;
-      cp_async16(tiles + raw_off(b, 0) + off, sa, na);
-      cp_async16(tiles + raw_off(b, 1) + off, sb, nb);
+      const bool va = r0 + r < d.m, vb = c0 + r < colend;
+      const float *pa = A + (long long)(r0 + r) * d.ld + k;
+      const float *pb = A + (long long)(c0 + r) * d.ld + k;
+      if (kv == 4) {
+        ra[i] = va ? __ldg(reinterpret_cast<const float4 *>(pa)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        rb[i] = vb ? __ldg(reinterpret_cast<const float4 *>(pb)) : make_float4(0.f, 0.f, 0.f, 0.f);
+      } else {
+        float ta[4] = {0.f, 0.f, 0.f, 0.f}, tb[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int q = 0; q < kv; ++q) {
+          if (va) ta[q] = pa[q];
+          if (vb) tb[q] = pb[q];
+        }
+        ra[i] = make_float4(ta[0], ta[1], ta[2], ta[3]);
+        rb[i] = make_float4(tb[0], tb[1], tb[2], tb[3]);
+      }
     }
-    asm volatile("cp.async.commit_group;");
+  };
+  auto split_store = [&](const float4 &x, uint32_t hi_off, uint32_t lo_off, uint32_t off) {
+    const float4 hi = make_float4(tf32_round(x.x), tf32_round(x.y), tf32_round(x.z), tf32_round(x.w));
+    const float4 lo = make_float4(tf32_round(x.x - hi.x), tf32_round(x.y - hi.y), tf32_round(x.z - hi.z),
+                                  tf32_round(x.w - hi.w));
+    *reinterpret_cast<float4 *>(tp + hi_off + off) = hi;
+    *reinterpret_cast<float4 *>(tp + lo_off + off) = lo;
   };
 
   const int nchunk = (ke - kb + kKc - 1) / kKc;
-  uint32_t phase[2] = {0u, 0u};
-  int pending[2] = {0, 0};  // an MMA batch is in flight on hi/lo[b]
-  bool ok = true;
-  // raw stages: chunk i lands in stage i % kRawStages, loaded kRawStages - 1 chunks ahead
-  load(kb, 0);
-  if (nchunk > 1) load(kb + kKc, 1);
-  for (int i = 0; i < nchunk && ok; ++i) {
-    const int b = i & 1, rs = i % kRawStages;
-    // stage (i + 2) % 3 was last read by the split of chunk i - 1 (before its barrier)
-    if (i + 2 < nchunk) {
-      load(kb + (i + 2) * kKc, (i + 2) % kRawStages);
-      asm volatile("cp.async.wait_group 2;");
-    } else if (i + 1 < nchunk) {
-      asm volatile("cp.async.wait_group 1;");
-    } else {
-      asm volatile("cp.async.wait_group 0;");
-    }
-    // hi/lo[b] was last read by the MMAs of chunk i - 2; a batch that has not completed
-    // within the wait budget stays pending, and the drain below waits for it once more
+  uint32_t phase = 0u;
+  bool pending = false, ok = true;
+  load(kb);
+  for (int i = 0; i < nchunk; ++i) {
+    // the MMAs of chunk i - 1 read the operand buffer: wait for them (bounded); a batch that
+    // has not completed stays pending for the drain below
     bool late = false;
-    if (pending[b]) {
-      late = !mbar_wait(smem_addr(&mbar[b]), phase[b]);
+    if (pending) {
+      late = !mbar_wait(smem_addr(&mbar), phase);
       if (!late) {
-        phase[b] ^= 1u;
-        pending[b] = 0;
+        phase ^= 1u;
+        pending = false;
       }
     }
     if (__syncthreads_or(late ? 1 : 0)) {
       ok = false;
       break;
     }
-    // split raw[b] into TF32 hi and lo parts (same swizzled offsets)
 #pragma unroll
     for (int i2 = 0; i2 < 8; ++i2) {
       const int r = rr + 16 * i2;
       const uint32_t off = (uint32_t)r * 128u + (uint32_t)((j ^ (r & 7)) * 16);
-#pragma unroll
-      for (int op = 0; op < 2; ++op) {
-        const float4 x = *reinterpret_cast<const float4 *>(tp + raw_off(rs, op) + off);
-        const float4 hi = make_float4(tf32_round(x.x), tf32_round(x.y), tf32_round(x.z), tf32_round(x.w));
-        const float4 lo = make_float4(tf32_round(x.x - hi.x), tf32_round(x.y - hi.y), tf32_round(x.z - hi.z),
-                                      tf32_round(x.w - hi.w));
-        *reinterpret_cast<float4 *>(tp + op_off(b, 2 * op) + off) = hi;
-        *reinterpret_cast<float4 *>(tp + op_off(b, 2 * op + 1) + off) = lo;
-      }
+      split_store(ra[i2], op_off(0), op_off(1), off);
+      split_store(rb[i2], op_off(2), op_off(3), off);
     }
     asm volatile("fence.proxy.async.shared::cta;");
     __syncthreads();
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;");
-      const uint32_t ah = tiles + op_off(b, 0), al = tiles + op_off(b, 1);
-      const uint32_t bh = tiles + op_off(b, 2), bl = tiles + op_off(b, 3);
+      const uint32_t ah = tiles + op_off(0), al = tiles + op_off(1);
+      const uint32_t bh = tiles + op_off(2), bl = tiles + op_off(3);
 #pragma unroll
       for (int t = 0; t < kKc / 8; ++t) {  // K = 8 tf32 = 32 bytes per MMA
         const uint32_t adv = (uint32_t)t * 32u;
@@ -216,22 +205,21 @@ __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__
         mma_tf32(tmem, sw128_desc(al + adv), sw128_desc(bh + adv), idesc, 1u);
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_addr(&mbar[b])));
+          smem_addr(&mbar)));
     }
-    pending[b] = 1;
+    pending = true;
+    if (i + 1 < nchunk) load(kb + (i + 1) * kKc);  // in flight while the MMAs of chunk i run
   }
-  asm volatile("cp.async.wait_group 0;");
-  // drain: wait for every MMA batch still in flight (also one that timed out above), so
-  // that no MMA still reads this CTA's shared memory or writes its tensor memory when the
+  // drain: wait for the MMA batch still in flight (also one a bounded wait above gave up on),
+  // so that no MMA still reads this CTA's shared memory or writes its tensor memory when the
   // CTA releases them.  A batch that misses this bounded wait too is reported
-  // (DEV_ERR_TIMEOUT, skipped epilogue); the caller must then treat the whole handle as
-  // lost (bidomain_destroy), since the tensor pipe may still be running on it.
+  // (DEV_ERR_TIMEOUT, skipped epilogue); the caller must then treat the whole handle as lost
+  // (bidomain_destroy), since the tensor pipe may still be running on it.
   bool late = false;
-  for (int b = 0; b < 2; ++b)
-    if (pending[b]) {
-      late |= !mbar_wait(smem_addr(&mbar[b]), phase[b]);
-      phase[b] ^= 1u;
-    }
+  if (pending) {
+    late = !mbar_wait(smem_addr(&mbar), phase);
+    phase ^= 1u;
+  }
   if (__syncthreads_or(late ? 1 : 0) || !ok) {
     ok = false;
     if (tid == 0) atomicOr(err, DEV_ERR_TIMEOUT);
@@ -239,7 +227,7 @@ __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__
   asm volatile("tcgen05.fence::after_thread_sync;");
   if (ok) {
     // epilogue: warp w reads TMEM lanes 32w + lane (tile rows), 32 columns per load,
-    // stages them in shared memory (the operand buffers are free now) and updates C
+    // stages them in shared memory (the operand buffer is free now) and updates C
     // one row per instruction (coalesced 128-byte rows)
     __syncthreads();
     float *stage = reinterpret_cast<float *>(tp) + warp * 32 * 33;
@@ -273,7 +261,7 @@ __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__
 #pragma unroll
         for (int u = 0; u < 32; ++u) {
           const int r = r0 + warp * 32 + u;
-          if (vc && r < d.m) A[(long long)r * d.ld + c] = cv[u] - stage[u * 33 + lane];
+          if (vc && r < d.m) base[d.off + (long long)r * d.ld + c] = cv[u] - stage[u * 33 + lane];
         }
       }
       __syncwarp();
@@ -287,7 +275,7 @@ __global__ void __launch_bounds__(128, 1) k_rankk_tc(const MatDesc *__restrict__
   }
 }
 
-static constexpr int kTcSmem = (2 * kRawStages + 8) * kTileBytes + 1024;  // raw stages + 2 x hi/lo A/B + alignment
+static constexpr int kTcSmem = 4 * kTileBytes + 1024;  // hi/lo A/B + alignment
 
 bool tc_configure() {
   return cudaFuncSetAttribute(k_rankk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem) == cudaSuccess;
