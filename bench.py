@@ -135,6 +135,10 @@ def run_gpu(args, w, rank, world):
     probe = binding.Plan(w)  # host-only plan: node count and subdomain sizes (masked grids too)
     N = probe.sizes()["n_node"]
     sub_nodes = np.diff(probe.index_set("SUB_NODE_PTR"))
+    # packed values of the explicit symmetric operators of each subdomain (S_Gamma, X, Psi)
+    sub_explicit = np.array([explicit_values_per_sub(2 * (nn - ni), nd, npr) for nn, ni, nd, npr in zip(
+        sub_nodes, probe.index_set("SUB_NINT"), np.diff(probe.index_set("SUB_DUAL_PTR")),
+        np.diff(probe.index_set("SUB_PRIMAL_PTR")))])
     del probe
     ui0, ue0, w0 = synth.initial_state(N, 0)
     dstate = [torch.from_numpy(a).cuda() for a in (ui0, ue0, w0)]
@@ -199,10 +203,15 @@ def run_gpu(args, w, rank, world):
         used = sum(st.get("guess_used", 0) for st in stats)
         return dict(ms=ms, steps=steps, newton=newton, krylov=kry, launches=launches, prof=prof, regions=regs,
                     clocks=clk, bad=bad, cond=max(st["cond_max"] for st in stats), final=final, guess_used=used,
-                    tune=tune)
+                    tune=tune, stats=stats)
 
     chosen = timed(args.precision, args.method, clocks=ClockSampler(dev), learned=args.learned)
     other = timed(args.precision, args.method, learned=1 - args.learned)
+    if args.step_log and rank == 0:  # per-step statistics of both variants (JSON lines)
+        with open(args.step_log, "w") as fh:
+            for name, run in (("chosen", chosen), ("other", other)):
+                for i, st in enumerate(run["stats"]):
+                    fh.write(json.dumps(dict(variant=name, step=i, **st)) + "\n")
     # per-launch CUDA events need stream launches: a second, shorter pass of the same steps
     nprof = min(K, args.profile_steps)
     profiled = timed(args.precision, args.method, profile=True, graphs=0, learned=args.learned, steps=nprof)
@@ -244,7 +253,8 @@ def run_gpu(args, w, rank, world):
     s.close()
 
     out = dict(chosen=chosen, plain=plain, other=other, e2e_ms=e2e_ms, e2e_newton=e2e_newton, e2e_used=e2e_used,
-               N=N, K=K, nplain=nplain, nprof=nprof, train_steps=train_steps, sub_nodes=sub_nodes)
+               N=N, K=K, nplain=nplain, nprof=nprof, train_steps=train_steps, sub_nodes=sub_nodes,
+               sub_explicit=sub_explicit)
     if plain is not None and nplain == K:
         a, b = chosen["final"], plain["final"]
         va, vb = (a[0] - a[1]).double(), (b[0] - b[1]).double()
@@ -283,6 +293,12 @@ def solve_values_per_sub(k):
     return 2.0 * 1.5 * pd * md ** 2, 2.0 * 1.5 * pn * mn ** 2
 
 
+def explicit_values_per_sub(n_gamma, n_delta, n_primal):
+    """Values of the explicit symmetric operators one iteration reads, packed: the lower
+    triangles of S_Gamma (n_Gamma) and of S_DeltaDelta^-1 (n_Delta), and Psi (n_Primal x n_Delta)."""
+    return n_gamma * (n_gamma + 1) / 2.0 + n_delta * (n_delta + 1) / 2.0 + float(n_primal) * n_delta
+
+
 # DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum of one capture), kept
 # with the first 16 hex digits of the sha256 of the kernel's source text: a figure stands only
 # while that text is unchanged, and is reported as null otherwise.
@@ -292,9 +308,9 @@ TRAFFIC = {
                             "static constexpr int kTcSmem")},
     # DRAM bytes per library byte (a capture of three launches on the 32x32x16 slab): the operator
     # and local-solve launches read their matrices once; scaled to a launch by its own bytes
-    "k_gemv": {"dram_per_library_byte": 1.013, "sha": "2c1f86b0689c36b0", "file": "dense.cu",
-               "span": ("__global__ void __launch_bounds__(256) k_gemv(",
-                        "// y[a] = (acc ? y[a] : 0) + alpha sum_p A[p][a] x[p]")},
+    "k_symv_batched": {"dram_per_library_byte": None, "sha": None, "file": "dense.cu",
+                       "span": ("__global__ void __launch_bounds__(256) k_symv_batched(",
+                                "template <typename T>\nsize_t symv_smem(")},
 }
 
 
@@ -335,7 +351,7 @@ def equivalent_sides(sub_nodes):
     return np.maximum(1, np.rint(np.cbrt(np.asarray(sub_nodes, float)) - 1.0)).astype(int)
 
 
-def roofline(prof, regions, w, precision, tc_used, sub_nodes):
+def roofline(prof, regions, w, precision, tc_used, sub_nodes, sub_explicit=None):
     """The dominant part of a step against its roofline, with the method's ALGORITHMIC work:
     the factorisation kernels (panel + rank-k classes) per Jacobian against the tensor pipe
     (3xTF32) / FP32 / FP64 peak, or the Krylov local-solve GEMVs per iteration against HBM.
@@ -385,8 +401,13 @@ def roofline(prof, regions, w, precision, tc_used, sub_nodes):
     # Krylov: one Dirichlet + one Neumann local solve per subdomain and iteration
     g = prof["gemv"]
     if g["ms"] > 0 and g["launches"] > 0:
-        vals = sum(sum(solve_values_per_sub(int(kj))) for kj in ks)
+        banded = np.array([sum(solve_values_per_sub(int(kj))) for kj in ks])
         vd, vn = solve_values_per_sub(k)
+        # the method's least data per iteration: the banded factors of the two local solves, or
+        # the packed lower triangles of the explicit operators these kernels read, whichever is less
+        explicit = np.asarray(sub_explicit, float) if sub_explicit is not None else np.full(nsub, np.inf)
+        vals = float(np.sum(np.minimum(banded, explicit)))
+        use_explicit = bool(np.all(explicit < banded))
         algo = (g["launches"] / 2.0) * vals * el
         # a masked fragment is flatter than the box of the same node count, so its banded factors
         # hold fewer values than the box model counts: there the bytes the launches read bound it
@@ -397,16 +418,20 @@ def roofline(prof, regions, w, precision, tc_used, sub_nodes):
         peak = pk.get("hbm_gbs", 6800.0)
         out["krylov"] = {
             "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "traffic": traffic("k_gemv", g["bytes"] / g["launches"]),
-            "kernel": "k_gemv (operator and local constrained solve, per launch)",
+            "traffic": traffic("k_symv_batched", g["bytes"] / g["launches"]),
+            "kernel": "k_symv_batched (operator S_Gamma and local constrained solve [X; Psi^T], per launch)",
             "peak_source": "of measured" if "fallback" not in pk else "of fallback",
             "launches": g["launches"], "avg_launch_us": g["ms"] * 1e3 / g["launches"],
             "algorithmic_bytes_per_launch": algo / g["launches"], "library_bytes_per_launch": g["bytes"] / g["launches"],
-            "work": (f"{vd + vn:.3g} factor values per H/h={k} subdomain and iteration (Dirichlet + Neumann "
-                     f"solve, read forward and back) x {nsub} subdomains" if not uneven else
-                     f"factor values of one Dirichlet + one Neumann solve (read forward and back) summed over "
-                     f"{nsub} uneven subdomains as boxes of the same node count") +
-                    f" x {el} B, split over the 2 GEMV launches" +
+            "work": ((f"{vals / nsub:.3g} values per subdomain and iteration: the packed lower triangles of "
+                      f"S_Gamma and S_DeltaDelta^-1 plus Psi, fewer than the {vd + vn:.3g} banded factor values of a "
+                      f"Dirichlet + Neumann solve (read forward and back) at H/h={k}, x {nsub} subdomains")
+                     if use_explicit else
+                     (f"{vd + vn:.3g} factor values per H/h={k} subdomain and iteration (Dirichlet + Neumann "
+                      f"solve, read forward and back) x {nsub} subdomains" if not uneven else
+                      f"per uneven subdomain the lesser of the packed explicit operators and the factor values of "
+                      f"one Dirichlet + one Neumann solve of a box of the same node count, summed over {nsub}")) +
+                    f" x {el} B, split over the 2 launches" +
                     ("; above the bytes the launches read, so capped to them" if capped else "")}
     if not out:
         return None, None
@@ -474,7 +499,7 @@ def sweep(args):
     for k in args.sweep_hh:
         w = synth.workload(f"opt{k}")
         for prec in ("mixed", "fp64"):
-            if prec == "fp64" and k > 12:  # ~20 s per FP64 factorisation at this size: mixed only
+            if prec == "fp64" and k > 16:  # FP64 factorisations above H/h = 16 take minutes: mixed only
                 continue
             s = binding.Solver(w, synth.SIGMA_I, synth.SIGMA_E, synth.IONIC, synth.TAU, stream=stream.cuda_stream,
                                precision=prec, use_graphs=1, use_tensor_cores=int(prec == "mixed"))
@@ -516,6 +541,7 @@ def main():
     ap.add_argument("--autotune", type=int, default=1, help="1: autotune the factorisation after the warm-up")
     ap.add_argument("--mlp-epochs", type=int, default=4, help="training passes of the learned guess per step")
     ap.add_argument("--cpu-steps", type=int, default=1, help="oracle time steps in the CPU baseline (0: skip)")
+    ap.add_argument("--step-log", default=None, help="write the per-step statistics of both variants here (JSONL)")
     ap.add_argument("--sweep", action="store_true", help="H/h optimality sweep instead of the benchmark")
     ap.add_argument("--sweep-hh", type=int, nargs="*", default=[4, 8, 12, 16])
     args = ap.parse_args()
@@ -564,7 +590,8 @@ def main():
         tc_used = bool(ch["tune"]["tensor_cores"])
     nsub = len(r["sub_nodes"])
     profiled_regions = {k: dict(v, launches=v["launches"] * r["nprof"]) for k, v in ch["regions"].items()}
-    roof, roof_other = roofline(ch["prof"], profiled_regions, w, args.precision, tc_used, r["sub_nodes"])
+    roof, roof_other = roofline(ch["prof"], profiled_regions, w, args.precision, tc_used, r["sub_nodes"],
+                                r.get("sub_explicit"))
     cpu = None
     if world == 1 and args.cpu_steps > 0:
         c = cpu_baseline(w, args.cpu_steps, args.method, args.scaling)

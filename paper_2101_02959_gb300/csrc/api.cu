@@ -72,6 +72,29 @@ struct GemvSet {
   GemvDesc *d = nullptr;
   int n = 0, max_rows = 0, max_cols = 0;
 };
+// entries of the lower block triangle of 32 x 32 tiles of an n x n matrix, clipped to n
+static inline long long sym_tile_entries(int n) {
+  const long long nb = (n + 31) / 32;
+  long long tot = 0;
+  for (long long I = 0; I < nb; ++I) {
+    const long long rows = std::min<long long>(32, n - 32 * I);
+    tot += rows * std::min<long long>(n, 32 * (I + 1));
+  }
+  return tot;
+}
+struct SymvSet {  // batched symmetric GEMV tasks; n = 0 when their shared memory does not fit
+  SymvTask *d = nullptr;
+  int n = 0, max_n = 0;
+  int split = 1, ld_scr = 0;  // CTAs per task; partial-sum rows (split > 1)
+  void *scratch = nullptr;    // n x split x ld_scr values of the local precision
+  int *counter = nullptr;     // n zeroed ints
+};
+template <class T>
+void launch_symv(const SymvSet &g, const T *A, const double *x, const int *xidx, double *y, const int *done,
+                 cudaStream_t s) {
+  launch_symv_batched<T>(g.n, g.max_n, g.split, g.d, A, x, xidx, y, 1.0, done, static_cast<T *>(g.scratch),
+                         g.counter, g.ld_scr, s);
+}
 struct CopySet {
   CopyTask *d = nullptr;
   int n = 0;
@@ -191,6 +214,10 @@ struct bd_handle {
   double tau = 0.0;
   cudaStream_t s = nullptr;
   bool own_stream = false;
+  // a second stream for the coarse solve of a preconditioner application, which runs beside
+  // the local constrained solve (fork / join events; captured into the Krylov graphs too)
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int device = -1;  // the device current at bidomain_setup: every buffer of the handle lives there
   long step_n = 0;
   DevMem mem;
@@ -213,6 +240,7 @@ struct bd_handle {
   // interior / interface / dual / primal layouts
   int nI_tot = 0, nG_tot = 0, nD_tot = 0, nP_tot = 0, nint_nodes = 0;
   std::vector<int> nI, nG, nD, nP, int_off, giff_off, ldual_off, lprim_off;
+  std::vector<int> band_I;  // dof half-bandwidth of each interior block (nodes ordered by global id)
   int *d_int_node, *d_iface_node, *d_R, *d_Rt_ptr, *d_Rt_idx, *d_vec_off_I;
   int *d_ldual_off, *d_lprim_off, *d_nD, *d_nI, *d_prim_x, *d_pl_ptr, *d_pl_idx, *d_giff_off;
   double *d_mult_iface;
@@ -238,6 +266,13 @@ struct bd_handle {
   double *d_Co64d = nullptr, *d_CoInv64 = nullptr, *d_CoW = nullptr, *d_CoY = nullptr;
   CoarseSolve cs;
   GemvSet gv_schur, gv_local, gv_psit, gv_sdd, gv_lgi, gv_lgit, gv_drest, gv_dext;
+  GemvSet gv_psi;  // Psi^T r_Delta alone (the coarse right-hand side's local parts)
+  // the operator S_Gamma and the local solve [X; Psi^T] as symmetric products (X, S_Gamma
+  // symmetric: each lower tile read once); used instead of gv_schur / gv_local when set
+  SymvSet sv_schur, sv_local;
+  // FP32 with tensor cores: the inverse of every matrix's current 128 x 128 diagonal block
+  // (128 x 128 floats per matrix of the largest batch), for the panel solves
+  float *d_pinv = nullptr;
   GemmTask *d_gemm = nullptr;
   int n_gemm = 0;
   int *d_ext_idx = nullptr;
@@ -492,7 +527,7 @@ void setup_handle(bd_handle &h) {
   ck(cudaMemsetAsync(h.d_err, 0, sizeof(int), s), "memset");
   // ---- local node tables and layouts
   const int S = h.nsub;
-  h.nI.resize(S); h.nG.resize(S); h.nD.resize(S); h.nP.resize(S);
+  h.nI.resize(S); h.nG.resize(S); h.nD.resize(S); h.nP.resize(S); h.band_I.resize(S);
   h.int_off.resize(S); h.giff_off.resize(S); h.ldual_off.resize(S); h.lprim_off.resize(S);
   std::vector<int> q_sub, q_loc, q_node, q_nbr, int_node, R, prim_x, vec_off_I(S);
   for (int j = 0; j < S; ++j) {
@@ -503,10 +538,17 @@ void setup_handle(bd_handle &h) {
     h.giff_off[j] = h.nG_tot;
     h.ldual_off[j] = h.nD_tot;
     h.lprim_off[j] = h.nP_tot;
+    int nband = 0;  // node half-bandwidth of the interior block (nodes ordered by global id)
     for (int a = 0; a < (int)sp.nodes.size(); ++a) {
       q_sub.push_back(j); q_loc.push_back(a); q_node.push_back(sp.nodes[a]);
-      for (int sl = 0; sl < 27; ++sl) q_nbr.push_back(sp.nbr[27 * a + sl]);
+      for (int sl = 0; sl < 27; ++sl) {
+        const int b = sp.nbr[27 * a + sl];
+        q_nbr.push_back(b);
+        if (a < sp.n_interior && b >= 0 && b < sp.n_interior) nband = std::max(nband, std::abs(a - b));
+      }
     }
+    // dofs 2a + field: the couplings of nodes a, b lie within |2a - 2b| + 1 of the diagonal
+    h.band_I[j] = 2 * nband + 1;
     for (int a = 0; a < sp.n_interior; ++a) int_node.push_back(sp.nodes[a]);
     for (int a = sp.n_interior; a < (int)sp.nodes.size(); ++a) {
       const int g = p.node_to_iface[sp.nodes[a]];
@@ -593,10 +635,12 @@ void setup_handle(bd_handle &h) {
   for (int j = 0; j < S; ++j) {
     const int n = h.nI[j] + h.nG[j];
     kd[j] = MatDesc{h.K_el, pad8(n), n, h.nI[j], h.K_blk};
+    kd[j].band = h.band_I[j];  // the interior block is banded: its updates skip the zeros past the band
     h.K_blk += ceil_div(h.nI[j], kNB);
     h.K_el += pad32((long long)pad8(n) * n);
     const int ma = 2 * h.nD[j] + h.nP[j];
     ad[j] = MatDesc{h.A_el, pad8(ma), ma, h.nD[j], h.A_blk};
+    ad[j].id0 = h.nD[j] + h.nP[j];  // [[Sb_DD, Sb_DP, I], [Sb_PD, Sb_PP, 0], [I, 0, 0]]
     h.A_blk += ceil_div(h.nD[j], kNB);
     h.A_el += pad32((long long)pad8(ma) * ma);
     ldg[j] = pad8(h.nG[j]);
@@ -609,8 +653,8 @@ void setup_handle(bd_handle &h) {
     h.Z_el += pad32((long long)ldx[j] * h.nP[j]);
     sdd_off[j] = h.SDD_el;
     h.SDD_el += pad32((long long)ldx[j] * h.nD[j]);
-    h.shK.m.push_back(n); h.shK.e.push_back(h.nI[j]);
-    h.shA.m.push_back(ma); h.shA.e.push_back(h.nD[j]);
+    h.shK.m.push_back(n); h.shK.e.push_back(h.nI[j]); h.shK.band.push_back(h.band_I[j]);
+    h.shA.m.push_back(ma); h.shA.e.push_back(h.nD[j]); h.shA.id0.push_back(ad[j].id0);
     h.shK.max_m = std::max(h.shK.max_m, n); h.shK.max_e = std::max(h.shK.max_e, h.nI[j]);
     h.shA.max_m = std::max(h.shA.max_m, ma); h.shA.max_e = std::max(h.shA.max_e, h.nD[j]);
   }
@@ -672,10 +716,11 @@ void setup_handle(bd_handle &h) {
       }
     const int mc = 2 * n;
     MatDesc md{h.CA_el, pad8(mc), mc, n, h.C_blk};
+    md.id0 = n;  // [[sum_j S_C^(j), I], [I, 0]]
     h.C_blk += ceil_div(n, kNB);
     h.CA_el += pad32((long long)pad8(mc) * mc);
     cdesc.push_back(md);
-    h.shC.m.push_back(mc); h.shC.e.push_back(n);
+    h.shC.m.push_back(mc); h.shC.e.push_back(n); h.shC.id0.push_back(n);
     h.shC.max_m = std::max(h.shC.max_m, mc); h.shC.max_e = std::max(h.shC.max_e, n);
     CopyTask cs{};
     cs.src_off = md.off; cs.src_ld = md.ld; cs.r0 = cs.c0 = n; cs.rows = cs.cols = n; cs.mode = 3; cs.sign = -1.0;
@@ -751,8 +796,14 @@ void setup_handle(bd_handle &h) {
     const int np = h.np;
     h.ld_co = pad8(2 * np);
     MatDesc co{0, h.ld_co, 2 * np, np, 0};
+    co.id0 = np;  // [[S_PP, I], [I, 0]]
     h.d_Codesc = m.upload(std::vector<MatDesc>{co}, s);
     h.shCo = EngineShape{1, np, 2 * np, {2 * np}, {np}};
+    h.shCo.id0 = {np};
+    if (h.mixed() && h.opt.use_tensor_cores) {
+      const int most = std::max({h.shK.count, h.shA.count, h.shC.count, 1});
+      h.d_pinv = m.alloc<float>((size_t)most * 128 * 128);
+    }
     // sparse pattern of S_PP: the (p, q) pairs that some subdomain couples, with the
     // offsets of their local contributions in the augmented matrices (subdomain order)
     std::map<std::pair<int, int>, std::vector<long long>> ent;
@@ -810,10 +861,15 @@ void setup_handle(bd_handle &h) {
     return c;
   };
   std::vector<GemvDesc> g_schur, g_local, g_psit, g_sdd, g_lgi, g_lgit;
+  std::vector<SymvTask> s_schur, s_local;
+  std::vector<GemvDesc> g_psi;
   std::vector<CopyTask> c_sorig, c_sdd, c_zx;
   for (int j = 0; j < S; ++j) {
     const int ng = h.nG[j], ni = h.nI[j], nd = h.nD[j], npj = h.nP[j];
     g_schur.push_back(GemvDesc{so_off[j], ldg[j], ng, ng, h.giff_off[j], h.giff_off[j], 1});
+    s_schur.push_back(SymvTask{so_off[j], 0, ldg[j], ng, 0, h.giff_off[j], h.giff_off[j], 0, 1});
+    s_local.push_back(SymvTask{zx_off[j], 0, ldx[j], nd, 0, h.ldual_off[j], h.ldual_off[j], 0, 0});
+    g_psi.push_back(GemvDesc{zp_off[j], ldx[j], npj, nd, h.ldual_off[j], h.nD_tot + h.lprim_off[j], 0});
     g_local.push_back(GemvDesc{zx_off[j], ldx[j], nd, nd, h.ldual_off[j], h.ldual_off[j], 0});
     g_local.push_back(GemvDesc{zp_off[j], ldx[j], npj, nd, h.ldual_off[j], h.nD_tot + h.lprim_off[j], 0});
     g_psit.push_back(GemvDesc{zp_off[j], ldx[j], npj, nd, h.lprim_off[j], h.ldual_off[j], 3});
@@ -842,6 +898,42 @@ void setup_handle(bd_handle &h) {
   for (auto &t : g_local) { h.gemv_local_flops += 2.0 * t.rows * t.cols; h.gemv_local_bytes += (double)t.rows * t.cols; }
   h.gv_schur = gset(g_schur);
   h.gv_local = gset(g_local);
+  h.gv_psi = gset(g_psi);
+  {
+    const size_t el = h.mixed() ? sizeof(float) : sizeof(double);
+    int sms = 0;
+    ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h.device), "SM count");
+    auto sset = [&](const std::vector<SymvTask> &v) {
+      SymvSet g;
+      for (auto &t : v) g.max_n = std::max(g.max_n, t.n);
+      const size_t np = (size_t)ceil_div(g.max_n, 32) * 32;
+      if (el * (9 * np + 8 * 32 * 33) > dense_smem_limit()) return SymvSet{};  // the full GEMV then
+      g.n = (int)v.size();
+      g.d = m.upload(v, s);
+      // split every matrix over enough CTAs to fill the resident slots evenly
+      const int occ = h.mixed() ? symv_occupancy<float>(g.max_n) : symv_occupancy<double>(g.max_n);
+      g.split = symv_split(g.n, g.max_n, sms * occ);
+      if (g.split > 1) {
+        g.ld_scr = (int)np;
+        g.scratch = m.alloc<unsigned char>(el * (size_t)g.n * g.split * g.ld_scr);
+        g.counter = m.alloc<int>(g.n);
+        ck(cudaMemsetAsync(g.counter, 0, sizeof(int) * g.n, s), "memset counters");
+      }
+      return g;
+    };
+    h.sv_schur = sset(s_schur);
+    h.sv_local = sset(s_local);
+    // bytes read by the products of one application (the profile's library bytes)
+    if (h.sv_schur.n) {
+      h.gemv_schur_bytes = 0.0;
+      for (auto &t : s_schur) h.gemv_schur_bytes += (double)sym_tile_entries(t.n);
+    }
+    if (h.sv_local.n) {
+      h.gemv_local_bytes = 0.0;
+      for (auto &t : s_local) h.gemv_local_bytes += (double)sym_tile_entries(t.n);
+      for (auto &t : g_psi) h.gemv_local_bytes += (double)t.rows * t.cols;
+    }
+  }
   h.gv_psit = gset(g_psit);
   h.gv_sdd = gset(g_sdd);
   h.gv_lgi = gset(g_lgi);
@@ -893,7 +985,7 @@ void setup_handle(bd_handle &h) {
     D.Aug = m.alloc<T>(h.A_el);
     D.Sorig = m.alloc<T>(h.So_el);
     D.Z = m.alloc<T>(h.Z_el);
-    D.SDD = m.alloc<T>(h.SDD_el);
+    if (h.opt.method == BD_FETIDP) D.SDD = m.alloc<T>(h.SDD_el);
     D.Blk = m.alloc<T>(h.Blk_el);
     D.CA = m.alloc<T>(h.CA_el);
     D.Sinv = m.alloc<T>(h.Sinv_el);
@@ -958,10 +1050,13 @@ void run_engine_groups(bd_handle &h, const EngineShape &all, const MatDesc *d_de
     for (int q = a; q < b; ++q) {
       g.m.push_back(all.m[q]);
       g.e.push_back(all.e[q]);
+      if (!all.band.empty()) g.band.push_back(all.band[q]);
+      if (!all.id0.empty()) g.id0.push_back(all.id0[q]);
       g.max_m = std::max(g.max_m, all.m[q]);
       g.max_e = std::max(g.max_e, all.e[q]);
     }
-    engine_partial_cholesky<T>(g, d_desc + a, base, h.d_err, h.s, linv, &h.prof, h.opt.use_tensor_cores != 0);
+    engine_partial_cholesky<T>(g, d_desc + a, base, h.d_err, h.s, linv, &h.prof, h.opt.use_tensor_cores != 0,
+                               h.d_pinv);
   }
 }
 
@@ -981,12 +1076,14 @@ void linearize_t(bd_handle &h, Dense<T> &D, bool precond) {
   else tval = h.d_tl_val;
   launch_build_aug<T>(h.nsub, h.shA.max_m, h.d_Sdesc, D.Sorig, h.d_Adesc, D.Aug, h.d_nD, h.d_tl_off, h.d_tl_ptr,
                       h.d_tl_row, tval, s);
-  launch_copy<T, T>(h.cp_sdd.n, h.cp_sdd.max_elems, h.cp_sdd.d, D.Aug, D.SDD, s);
+  if (h.opt.method == BD_FETIDP)  // S_DeltaDelta itself: only the FETI-DP preconditioner applies it
+    launch_copy<T, T>(h.cp_sdd.n, h.cp_sdd.max_elems, h.cp_sdd.d, D.Aug, D.SDD, s);
   launch_copy<T, T>(h.cp_blk.n, h.cp_blk.max_elems, h.cp_blk.d, D.Aug, D.Blk, s);
   run_engine_groups<T>(h, h.shA, h.d_Adesc, D.Aug, D.Linv);
   launch_copy<T, T>(h.cp_zx.n, h.cp_zx.max_elems, h.cp_zx.d, D.Aug, D.Z, s);
   launch_class_aug<T>(h.ncls, h.max_nc, h.d_cls, h.d_pairs, D.Blk, h.d_Cdesc, D.CA, s);
-  engine_partial_cholesky<T>(h.shC, h.d_Cdesc, D.CA, h.d_err, s, D.Linv, &h.prof, h.opt.use_tensor_cores != 0);
+  engine_partial_cholesky<T>(h.shC, h.d_Cdesc, D.CA, h.d_err, s, D.Linv, &h.prof, h.opt.use_tensor_cores != 0,
+                             h.d_pinv);
   launch_copy<T, T>(h.cp_sinv.n, h.cp_sinv.max_elems, h.cp_sinv.d, D.CA, D.Sinv, s);
   if (h.opt.scaling == BD_SCALING_RHO) {
     const double si = std::max({h.fp.sigma_i[0], h.fp.sigma_i[1], h.fp.sigma_i[2]});
@@ -1003,7 +1100,8 @@ void linearize_t(bd_handle &h, Dense<T> &D, bool precond) {
   {  // one large matrix: its trailing updates go to the tensor cores like the local ones
     EngineShape co = h.shCo;
     co.ob = h.tune_ob;
-    engine_partial_cholesky<T>(co, h.d_Codesc, D.Co, h.d_err, s, D.LdCo, &h.prof, h.opt.use_tensor_cores != 0);
+    engine_partial_cholesky<T>(co, h.d_Codesc, D.Co, h.d_err, s, D.LdCo, &h.prof, h.opt.use_tensor_cores != 0,
+                               h.d_pinv);
   }
   launch_copy<T, T>(h.cp_coinv.n, h.cp_coinv.max_elems, h.cp_coinv.d, D.Co, D.CoInv, s);
   if (h.d_CoInv64) coarse_refine64<T>(h.np, D.CoInv, pad8(h.np), h.d_Co64d, h.d_CoInv64, h.d_CoW, h.d_CoY, s);
@@ -1029,8 +1127,11 @@ template <class T>
 // f: the PCG reduction to fuse into the last kernel (nullptr: none)
 void schur_t(bd_handle &h, Dense<T> &D, const double *x, double *y, const int *done, const DotFuse *f = nullptr) {
   h.prof.begin(PROF_GEMV, h.s);
-  launch_gemv<T>(h.gv_schur.n, h.gv_schur.max_rows, h.gv_schur.max_cols, h.gv_schur.d, D.Sorig, x, h.d_R, h.d_yloc,
-                 1.0, done, h.s);
+  if (h.sv_schur.n)
+    launch_symv<T>(h.sv_schur, D.Sorig, x, h.d_R, h.d_yloc, done, h.s);
+  else
+    launch_gemv<T>(h.gv_schur.n, h.gv_schur.max_rows, h.gv_schur.max_cols, h.gv_schur.d, D.Sorig, x, h.d_R,
+                   h.d_yloc, 1.0, done, h.s);
   h.prof.end(PROF_GEMV, h.s, h.gemv_schur_flops, h.gemv_schur_bytes * sizeof(T));
   if (f) launch_gather_sum_dot(h.nif, h.d_Rt_ptr, h.d_Rt_idx, h.d_yloc, y, h.gauge_iface, *f, h.s);
   else launch_gather_sum(h.nif, h.d_Rt_ptr, h.d_Rt_idx, h.d_yloc, y, h.gauge_iface, 1.0, nullptr, done, h.s);
@@ -1042,12 +1143,28 @@ template <class T>
 void st_inv_t(bd_handle &h, Dense<T> &D, const double *rP, const double *rD, const int *done,
               const CsrIn *rP_csr = nullptr) {
   h.prof.begin(PROF_GEMV, h.s);
-  launch_gemv<T>(h.gv_local.n, h.gv_local.max_rows, h.gv_local.max_cols, h.gv_local.d, D.Z, rD, nullptr, h.d_ydc,
-                 1.0, done, h.s);
-  h.prof.end(PROF_GEMV, h.s, h.gemv_local_flops, h.gemv_local_bytes * sizeof(T));
-  // z_Pi = S_PiPi^-1 (rP - sum_j Psi^T r_D) into zbar[nd:], then ydc_Delta -= Psi z_Pi
-  launch_coarse_solve<T>(h.cs, D.CoInv, h.d_ydc + h.nD_tot, rP_csr ? nullptr : rP, rP_csr, h.d_zbar + h.nd,
-                         h.d_co_c, h.d_co_rho, done, h.s);
+  if (h.sv_local.n) {
+    // Psi^T r_Delta first: the coarse solve needs only it, so it runs on the second stream
+    // while X r_Delta (the symmetric product) runs here
+    launch_gemv<T>(h.gv_psi.n, h.gv_psi.max_rows, h.gv_psi.max_cols, h.gv_psi.d, D.Z, rD, nullptr, h.d_ydc, 1.0,
+                   done, h.s);
+    ck(cudaEventRecord(h.ev_fork, h.s), "record");
+    ck(cudaStreamWaitEvent(h.s2, h.ev_fork, 0), "wait");
+    launch_coarse_solve<T>(h.cs, D.CoInv, h.d_ydc + h.nD_tot, rP_csr ? nullptr : rP, rP_csr, h.d_zbar + h.nd,
+                           h.d_co_c, h.d_co_rho, done, h.s2);
+    ck(cudaEventRecord(h.ev_join, h.s2), "record");
+    launch_symv<T>(h.sv_local, D.Z, rD, nullptr, h.d_ydc, done, h.s);
+    h.prof.end(PROF_GEMV, h.s, h.gemv_local_flops, h.gemv_local_bytes * sizeof(T));
+    ck(cudaStreamWaitEvent(h.s, h.ev_join, 0), "wait");
+  } else {
+    launch_gemv<T>(h.gv_local.n, h.gv_local.max_rows, h.gv_local.max_cols, h.gv_local.d, D.Z, rD, nullptr,
+                   h.d_ydc, 1.0, done, h.s);
+    h.prof.end(PROF_GEMV, h.s, h.gemv_local_flops, h.gemv_local_bytes * sizeof(T));
+    // z_Pi = S_PiPi^-1 (rP - sum_j Psi^T r_D) into zbar[nd:]
+    launch_coarse_solve<T>(h.cs, D.CoInv, h.d_ydc + h.nD_tot, rP_csr ? nullptr : rP, rP_csr, h.d_zbar + h.nd,
+                           h.d_co_c, h.d_co_rho, done, h.s);
+  }
+  // ydc_Delta -= Psi z_Pi
   launch_gemv_t_task<T>(h.gv_psit.n, h.gv_psit.max_rows, h.gv_psit.max_cols, h.gv_psit.d, D.Z, h.d_zbar,
                         h.d_prim_x, h.d_ydc, -1.0, done, h.s);
 }
@@ -1545,8 +1662,11 @@ int noalloc_scratch(int dev, double **out) {
 
 template <class T>
 void schur_noalloc_t(bd_handle &h, Dense<T> &D, const double *x, double *y, double *scratch) {
-  launch_gemv<T>(h.gv_schur.n, h.gv_schur.max_rows, h.gv_schur.max_cols, h.gv_schur.d, D.Sorig, x, h.d_R, scratch,
-                 1.0, nullptr, h.s);
+  if (h.sv_schur.n)
+    launch_symv<T>(h.sv_schur, D.Sorig, x, h.d_R, scratch, nullptr, h.s);
+  else
+    launch_gemv<T>(h.gv_schur.n, h.gv_schur.max_rows, h.gv_schur.max_cols, h.gv_schur.d, D.Sorig, x, h.d_R,
+                   scratch, 1.0, nullptr, h.s);
   launch_gather_sum(h.nif, h.d_Rt_ptr, h.d_Rt_idx, scratch, y, h.gauge_iface, 1.0, nullptr, nullptr, h.s);
 }
 
@@ -1714,6 +1834,9 @@ int bidomain_setup(const bd_mesh *mesh, const bd_conductivity *cond, const bd_io
     ck(cudaGetDevice(&h->device), "cudaGetDevice");
     if (stream) h->s = (cudaStream_t)stream;
     else { ck(cudaStreamCreateWithFlags(&h->s, cudaStreamNonBlocking), "stream"); h->own_stream = true; }
+    ck(cudaStreamCreateWithFlags(&h->s2, cudaStreamNonBlocking), "stream");
+    ck(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming), "event");
+    ck(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming), "event");
     if (h->opt.use_tensor_cores && h->opt.precision == BD_MIXED && !tc_configure()) {
       g_last_error = "tensor-core kernel configuration failed";
       return BD_ERR_CUDA;
@@ -2081,11 +2204,16 @@ int64_t bidomain_launch_count(void) { return (int64_t)launch_count(); }
 int bidomain_destroy(bd_handle *h) {
   if (!h) return BD_ERR_ARG;
   cudaStreamSynchronize(h->s);
-  cudaStream_t s = h->s;
+  if (h->s2) cudaStreamSynchronize(h->s2);
+  cudaStream_t s = h->s, s2 = h->s2;
+  cudaEvent_t e1 = h->ev_fork, e2 = h->ev_join;
   const bool own = h->own_stream;
   for (auto &g : h->pcg_exec)
     if (g) cudaGraphExecDestroy(g);
   delete h;
+  if (e1) cudaEventDestroy(e1);
+  if (e2) cudaEventDestroy(e2);
+  if (s2) cudaStreamDestroy(s2);
   if (own) cudaStreamDestroy(s);
   return BD_OK;
 }

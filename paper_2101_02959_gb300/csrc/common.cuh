@@ -40,6 +40,52 @@ struct MatDesc {
   int m;          // order
   int e;          // columns to eliminate (partial Cholesky) / rows used
   int dblk;       // first slot of this matrix in the block store of factored kNB x kNB diagonal blocks
+  // half-bandwidth of the eliminated block: entries (i, k), i, k < e, with |i - k| > band are
+  // structurally zero, so the partial Cholesky leaves them zero (no fill outside the band) and
+  // its updates skip the rows and columns past the band (band >= e: dense)
+  int band = 1 << 30;
+  // first row of an identity block below the eliminated columns (row id0 + i holds a single 1
+  // in column i, as in the augmented matrices [[A, I], [I, 0]] whose partial Cholesky leaves
+  // -A^-1): row id0 + i of L is zero left of column i, so an update whose K range ends at ke
+  // reaches only the rows id0 .. id0 + ke - 1 of that block (id0 >= m: none)
+  int id0 = 1 << 30;
+};
+
+// Rows [row0, m) that an update of the partial Cholesky with K range ending at ke reaches:
+// the interior rows up to ke + band (the L entries of later interior rows vanish in that K
+// range), then the dense rows from max(row0, e) up to the identity block, then the first ke
+// rows of the identity block.  Virtual row v in [0, nv) -> matrix row.
+struct BandRows {
+  int row0, ni, mid0, nmid, idr, nv;
+  __host__ __device__ int row(int v) const {
+    return v < ni ? row0 + v : (v - ni < nmid ? mid0 + (v - ni) : idr + (v - ni - nmid));
+  }
+};
+__host__ __device__ inline int band_limit(const MatDesc &d, int ke) {
+  return d.band >= d.e ? d.e : (ke + d.band < d.e ? ke + d.band : d.e);
+}
+__host__ __device__ inline BandRows band_rows(const MatDesc &d, int row0, int ke) {
+  BandRows b;
+  b.row0 = row0;
+  const int lim = band_limit(d, ke);
+  b.ni = lim > row0 ? lim - row0 : 0;
+  b.mid0 = row0 > d.e ? row0 : d.e;
+  const int idb = d.id0 < d.m ? d.id0 : d.m;  // start of the identity block (m: none)
+  b.nmid = idb > b.mid0 ? idb - b.mid0 : 0;
+  b.idr = idb > b.mid0 ? idb : b.mid0;
+  const long long idend = (long long)idb + ke;  // rows of the block reached so far
+  const int iend = idend < d.m ? (int)idend : d.m;
+  const int nid = iend > b.idr ? iend - b.idr : 0;
+  b.nv = b.ni + b.nmid + nid;
+  return b;
+}
+
+// Batched symmetric GEMV task: y = alpha A x for a symmetric n x n matrix stored in full
+// (row-major, ld a multiple of 8, 16-byte aligned), plus optional plain rows yb = alpha B x
+// (B: nb x n at b_off, same ld).  flags bit0: x gathered through xidx; bit1: accumulate.
+struct SymvTask {
+  long long a_off, b_off;
+  int ld, n, nb, x_off, y_off, yb_off, flags;
 };
 
 // Generic batched GEMV task: y[y_idx?] = alpha * op(A) x + beta * y.

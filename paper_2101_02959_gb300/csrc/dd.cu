@@ -800,11 +800,11 @@ void launch_coarse_solve(const CoarseSolve &cs, const T *X, const double *yprim,
   }
   k_coarse_rhs<<<ceil_div(cs.np, 256), 256, 0, s>>>(cs.np, cs.gauge, cs.pl_ptr, cs.pl_idx, yprim, rP, rc, c, done);
   count_launch();
-  launch_gemv_rows<T>(cs.np, X, cs.ld_x, c, z, 0, done, s);
+  launch_symv_rows<T>(cs.np, X, cs.ld_x, c, z, 0, done, s);
   for (int it = 0; it < cs.nref; ++it) {
     k_coarse_resid<<<ceil_div(cs.np, 8), 256, 0, s>>>(cs.np, cs.sptr, cs.scol, cs.sval, c, z, rho, done);
     count_launch();
-    launch_gemv_rows<T>(cs.np, X, cs.ld_x, rho, z, 1, done, s);
+    launch_symv_rows<T>(cs.np, X, cs.ld_x, rho, z, 1, done, s);
   }
 }
 

@@ -106,9 +106,11 @@ __global__ void __launch_bounds__(256, ROWS ? 2 : 1) k_bigpanel(const MatDesc *_
   const MatDesc d = desc[blockIdx.y];
   if (K0 >= d.e) return;
   const int w = min(kPW, d.e - K0);
-  const int rbeg = K0 + w + blockIdx.x * RB;
-  if (ROWS && rbeg >= d.m) return;
-  const int nrows = ROWS ? min(RB, d.m - rbeg) : 0;
+  // rows launch: the rows below the panel that it reaches (interior rows up to the band)
+  const BandRows br = band_rows(d, K0 + w, K0 + w);
+  const int v0 = blockIdx.x * RB;
+  if (ROWS && v0 >= br.nv) return;
+  const int nrows = ROWS ? min(RB, br.nv - v0) : 0;
   T *A = base + d.off;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *P = reinterpret_cast<T *>(smem_raw);  // [NS][kLDP]: (diagonal rows,) own rows
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(256, ROWS ? 2 : 1) k_bigpanel(const MatDesc *_
       const int sr = idx / VPP, cv = idx % VPP;
       const bool diag = !ROWS && sr < kPW;
       const bool ok = idx < kVec && cv * VN < w && (diag ? sr < w : sr - OWN0 < nrows);
-      const long long grow = diag ? K0 + sr : rbeg + sr - OWN0;
+      const long long grow = diag ? K0 + sr : (ok ? br.row(v0 + sr - OWN0) : 0);
       buf[u] = ok ? *reinterpret_cast<const VT *>(A + grow * d.ld + K0 + cv * VN) : VT{};
     }
 #pragma unroll
@@ -287,7 +289,7 @@ __global__ void __launch_bounds__(256, ROWS ? 2 : 1) k_bigpanel(const MatDesc *_
     const int q = idx / VPP, cv = idx % VPP;
     if (cv * VN >= w) continue;
     const T *src = P + (OWN0 + q) * kLDP + cv * VN;
-    T *dst = A + (long long)(rbeg + q) * d.ld + K0 + cv * VN;
+    T *dst = A + (long long)br.row(v0 + q) * d.ld + K0 + cv * VN;
     if (cv * VN + VN <= w) {
       *reinterpret_cast<VT *>(dst) = *reinterpret_cast<const VT *>(src);
     } else {
@@ -299,6 +301,78 @@ __global__ void __launch_bounds__(256, ROWS ? 2 : 1) k_bigpanel(const MatDesc *_
       const int i = idx / w, j = idx % w;
       if (j <= i) A[(long long)(K0 + i) * d.ld + K0 + j] = P[i * kLDP + j];
     }
+  }
+}
+
+// ---- inverse of a factored diagonal block (tensor-core panel solve) -------------
+// L_11^-1 for the w x w factored diagonal block at [K0, K0 + w) of every matrix (one CTA
+// each), into pinv (128 x 128 per matrix, row-major, zero outside the lower w x w part), so
+// that the rows below the panel become one product L_21 = A_21 L_11^-T on the tensor cores.
+// 32 x 32 blocks: the four diagonal blocks by substitution (warp b, lane = column, the column
+// in registers), then the blocks at distance 1, 2, 3 below the diagonal,
+// Y_ij = -Y_ii (sum_{k=j}^{i-1} L_ik Y_kj), all threads over the entries of one distance.
+constexpr int kInvLD = kPW + 1;
+constexpr size_t kInvSmem = sizeof(float) * (2 * (size_t)kPW * kInvLD + 3 * 32 * 33);
+
+__global__ void __launch_bounds__(256, 1) k_diag_inverse(const MatDesc *__restrict__ desc,
+                                                         const float *__restrict__ base, int K0,
+                                                         float *__restrict__ pinv) {
+  const MatDesc d = desc[blockIdx.y];
+  if (K0 >= d.e) return;
+  const int w = min(kPW, d.e - K0), nbk = (w + 31) / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float *Ls = reinterpret_cast<float *>(smem_raw);  // [128][129] L_11, lower, identity past w
+  float *Ys = Ls + kPW * kInvLD;                      // [128][129] the inverse
+  float *Tm = Ys + kPW * kInvLD;                      // [3][32][33] sums of one distance
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float *A = base + d.off + (long long)K0 * d.ld + K0;
+  for (int e = tid; e < kPW * kPW; e += 256) {
+    const int i = e / kPW, j = e % kPW;
+    float v = 0.f;
+    if (i < w && j < w) v = j <= i ? A[(long long)i * d.ld + j] : 0.f;
+    else if (i == j) v = 1.f;
+    Ls[i * kInvLD + j] = v;
+    Ys[i * kInvLD + j] = 0.f;
+  }
+  __syncthreads();
+  if (warp < 4) {  // diagonal block b = warp: lane = column j, forward substitution down the rows
+    const int b0 = 32 * warp;
+    float y[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+      float sacc = (i == lane) ? 1.f : 0.f;
+#pragma unroll
+      for (int k = 0; k < i; ++k) sacc -= Ls[(b0 + i) * kInvLD + b0 + k] * y[k];
+      y[i] = sacc / Ls[(b0 + i) * kInvLD + b0 + i];
+    }
+#pragma unroll
+    for (int i = 0; i < 32; ++i) Ys[(b0 + i) * kInvLD + b0 + lane] = i >= lane ? y[i] : 0.f;
+  }
+  __syncthreads();
+  for (int dist = 1; dist < nbk; ++dist) {
+    const int nblk = nbk - dist;  // output blocks (j + dist, j), j < nblk
+    for (int e = tid; e < nblk * 1024; e += 256) {
+      const int j = e / 1024, r = (e % 1024) / 32, c = e % 32, i = j + dist;
+      float t = 0.f;
+      for (int k = j; k < i; ++k)
+#pragma unroll 8
+        for (int q = 0; q < 32; ++q) t += Ls[(32 * i + r) * kInvLD + 32 * k + q] * Ys[(32 * k + q) * kInvLD + 32 * j + c];
+      Tm[(j * 32 + r) * 33 + c] = t;
+    }
+    __syncthreads();
+    for (int e = tid; e < nblk * 1024; e += 256) {
+      const int j = e / 1024, r = (e % 1024) / 32, c = e % 32, i = j + dist;
+      float t = 0.f;
+#pragma unroll 8
+      for (int q = 0; q < 32; ++q) t += Ys[(32 * i + r) * kInvLD + 32 * i + q] * Tm[(j * 32 + q) * 33 + c];
+      Ys[(32 * i + r) * kInvLD + 32 * j + c] = -t;
+    }
+    __syncthreads();
+  }
+  float *out = pinv + (long long)blockIdx.y * kPW * kPW;
+  for (int e = tid; e < kPW * kPW; e += 256) {
+    const int i = e / kPW, j = e % kPW;
+    out[e] = (i < w && j < w && j <= i) ? Ys[i * kInvLD + j] : 0.f;
   }
 }
 
@@ -335,10 +409,12 @@ __global__ void __launch_bounds__(256) k_rankk(const MatDesc *__restrict__ desc,
     kb = 0;
     ke = d.e;
   }
+  const BandRows br = band_rows(d, row0, ke);  // rows past the band hold zeros in K = [kb, ke)
+  if (mode != 1) colend = min(colend, band_limit(d, ke));
   const int ti = blockIdx.x / nct, tj = blockIdx.x % nct;
   if (tj > ti) return;
-  const int r0 = row0 + ti * kTB, c0 = row0 + tj * kTB;
-  if (r0 >= d.m || c0 >= colend || ke <= kb) return;
+  const int v0 = ti * kTB, c0 = row0 + tj * kTB;
+  if (v0 >= br.nv || c0 >= colend || ke <= kb) return;
   T *A = base + d.off;
   __shared__ T As[kKC][kTB + 1];  // row pad 65: the strided stores below hit distinct banks
   __shared__ T Bs[kKC][kTB + 1];
@@ -351,11 +427,12 @@ __global__ void __launch_bounds__(256) k_rankk(const MatDesc *__restrict__ desc,
   const int lr = tid >> 2, lk = (tid & 3) * 8;
   for (int kk = kb; kk < ke; kk += kKC) {
     {
-      const int ra = r0 + lr, rb = c0 + lr;
+      const bool va = v0 + lr < br.nv;
+      const int ra = va ? br.row(v0 + lr) : 0, rb = c0 + lr;
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const int k = kk + lk + q;
-        As[lk + q][lr] = (ra < d.m && k < ke) ? A[(long long)ra * d.ld + k] : T(0);
+        As[lk + q][lr] = (va && k < ke) ? A[(long long)ra * d.ld + k] : T(0);
         Bs[lk + q][lr] = (rb < colend && k < ke) ? A[(long long)rb * d.ld + k] : T(0);
       }
     }
@@ -376,8 +453,9 @@ __global__ void __launch_bounds__(256) k_rankk(const MatDesc *__restrict__ desc,
   }
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
-    const int r = r0 + ty + 16 * i;
-    if (r >= d.m) continue;
+    const int v = v0 + ty + 16 * i;
+    if (v >= br.nv) continue;
+    const int r = br.row(v);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int c = c0 + tx + 16 * j;
@@ -390,11 +468,6 @@ std::atomic<long long> g_launches{0};
 void count_launch(int n) { g_launches += n; }
 long long launch_count() { return g_launches.load(); }
 
-// Lower-triangle entries updated by a rank-k launch: panel mode rows [t0, m) x cols [t0, e), c <= r.
-static double trapezoid(long long t0, long long e, long long m) {
-  const long long k = e - t0;
-  return (double)(k * (m - t0) - k * (k - 1) / 2);
-}
 
 // ---- FP32 rank-k update: 128x128 CTA tiles, 8x8 outputs per thread ----------
 // Same modes and index ranges as k_rankk.  K is consumed in chunks of 16 with
@@ -415,18 +488,21 @@ __global__ void __launch_bounds__(256) k_rankk128(const MatDesc *__restrict__ de
   } else {
     row0 = d.e; colend = d.m; kb = 0; ke = d.e;
   }
+  const BandRows br = band_rows(d, row0, ke);  // rows past the band hold zeros in K = [kb, ke)
+  if (mode != 1) colend = min(colend, band_limit(d, ke));
   const int ti = blockIdx.x / nct, tj = blockIdx.x % nct;
   if (tj > ti) return;
-  const int r0 = row0 + ti * kTB2, c0 = row0 + tj * kTB2;
-  if (r0 >= d.m || c0 >= colend || ke <= kb) return;
+  const int v0 = ti * kTB2, c0 = row0 + tj * kTB2;
+  if (v0 >= br.nv || c0 >= colend || ke <= kb) return;
   float *A = base + d.off;
   __shared__ __align__(16) float As[2][kKC2][kTB2 + 4];
   __shared__ __align__(16) float Bs[2][kKC2][kTB2 + 4];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   // loader: thread -> (row lr, k offset lk): 128 rows x 16 k = 2 x 4 floats per thread per operand
   const int lr = tid >> 1, lk = (tid & 1) * 8;
-  const int ra = r0 + lr, rb = c0 + lr;
-  const bool va = ra < d.m, vb = rb < colend;
+  const bool va = v0 + lr < br.nv;
+  const int ra = va ? br.row(v0 + lr) : 0, rb = c0 + lr;
+  const bool vb = rb < colend;
   const float *pa = A + (long long)ra * d.ld, *pb = A + (long long)rb * d.ld;
   float la[8], lb[8];
   auto load = [&](int kk) {
@@ -488,9 +564,9 @@ __global__ void __launch_bounds__(256) k_rankk128(const MatDesc *__restrict__ de
   // thread owns rows {ty*4 + i, 64 + ty*4 + i} and columns {tx*4 + j, 64 + tx*4 + j}
 #pragma unroll
   for (int i = 0; i < 8; ++i) {
-    const int r = r0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
-    if (r >= d.m) continue;
-    float *crow = A + (long long)r * d.ld;
+    const int v = v0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+    if (v >= br.nv) continue;
+    float *crow = A + (long long)br.row(v) * d.ld;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int c = c0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
@@ -516,12 +592,34 @@ void launch_rankk<float>(const MatDesc *d_desc, float *base, int mode, int k0, i
   count_launch();
 }
 
+// Lower-triangle entries that a band-limited update of rows band_rows(hd, t0, ke) x columns
+// [t0, cend) touches: the interior rows up to the band (a trapezoid), then every column of
+// the rows from e on (for a dense matrix: rows [t0, m) x columns [t0, cend), c <= r).
+static double band_entries(const MatDesc &hd, int t0, int ke, int cend) {
+  const long long k = cend - t0;
+  if (k <= 0) return 0.0;
+  const BandRows br = band_rows(hd, t0, ke);
+  const long long iend = t0 + br.ni;
+  const long long a = std::max(0LL, std::min(iend, (long long)cend) - t0);
+  const long long b = std::max(0LL, iend - cend);
+  return (double)(a * (a + 1) / 2 + b * k + (long long)(br.nv - br.ni) * k);
+}
+
 template <typename T>
 void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s,
-                             T *store, ProfHook *prof, bool tc) {
+                             T *store, ProfHook *prof, bool tc, float *pinv) {
   if (sh.count == 0) return;
   constexpr int RB = PanelRows<T>::RB;
   const int ob = std::max(kPW, (sh.ob / kPW) * kPW);  // outer block: columns per long-K trailing update
+  // host copies of the descriptors' sizes and bands: the grids cover the rows and columns
+  // the band lets an update reach (the kernels apply the same limits per matrix)
+  std::vector<MatDesc> hd(sh.count);
+  for (int b = 0; b < sh.count; ++b) {
+    hd[b].m = sh.m[b];
+    hd[b].e = sh.e[b];
+    if (!sh.band.empty()) hd[b].band = sh.band[b];
+    if (!sh.id0.empty()) hd[b].id0 = sh.id0[b];
+  }
   for (int K0 = 0; K0 < sh.max_e; K0 += ob) {
     const int K1 = K0 + ob;
     for (int k0 = K0; k0 < std::min(K1, sh.max_e); k0 += kPW) {
@@ -530,28 +628,44 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
       for (int b = 0; b < sh.count; ++b) {
         if (k0 >= sh.e[b]) continue;
         const int w = std::min(kPW, sh.e[b] - k0);
-        const int below = sh.m[b] - k0 - w;
-        const int cend = std::min(K1, sh.e[b]);
+        const int below = band_rows(hd[b], k0 + w, k0 + w).nv;
+        const int cend = std::min({K1, sh.e[b], band_limit(hd[b], k0 + w)});
         max_below = std::max(max_below, below);
         max_cols = std::max(max_cols, cend - k0 - w);
         fl_panel += (double)w * w * w / 3.0 + (double)below * w * w;
-        const double ent = trapezoid(k0 + w, cend, sh.m[b]);
-        fl_in += 2.0 * w * ent;
+        fl_in += 2.0 * w * band_entries(hd[b], k0 + w, k0 + w, cend);
       }
       if (prof) prof->begin(PROF_PANEL, s);
       k_bigpanel<T, false><<<dim3(1, sh.count), 256, bigpanel_smem<T, false>(), s>>>(d_desc, base, k0, d_err, store);
       count_launch();
       if (max_below > 0) {
-        k_bigpanel<T, true><<<dim3(ceil_div(max_below, RB), sh.count), 256, bigpanel_smem<T, true>(), s>>>(
-            d_desc, base, k0, d_err, store);
-        count_launch();
+        bool done_rows = false;
+        if constexpr (std::is_same<T, float>::value) {
+          if (tc && pinv) {  // L_21 = A_21 L_11^-T as one tensor-core product with the block's inverse
+            k_diag_inverse<<<dim3(1, sh.count), 256, kInvSmem, s>>>(d_desc, base, k0, pinv);
+            count_launch();
+            launch_rankk_tc(d_desc, base, 3, k0, 0, max_below, kPW, sh.count, d_err, s, pinv);
+            done_rows = true;
+          }
+        }
+        if (!done_rows) {
+          k_bigpanel<T, true><<<dim3(ceil_div(max_below, RB), sh.count), 256, bigpanel_smem<T, true>(), s>>>(
+              d_desc, base, k0, d_err, store);
+          count_launch();
+        }
       }
       if (prof) prof->end(PROF_PANEL, s, fl_panel, 0.0);
       // the rest of the outer block: rows [k0 + w, m), columns [k0 + w, min(K1, e)); timed
       // with the panels (the long-K class holds only the trailing updates)
       if (max_below > 0 && max_cols > 0) {
         if (prof) prof->begin(PROF_PANEL, s);
-        launch_rankk<T>(d_desc, base, 0, k0, K0, K1, max_below, max_cols, sh.count, s);
+        if constexpr (std::is_same<T, float>::value) {
+          static_assert(kPW == 128, "the tensor-core in-block update takes 128-column panels");
+          if (tc) launch_rankk_tc(d_desc, base, 0, k0, K1, max_below, max_cols, sh.count, d_err, s);
+          else launch_rankk<T>(d_desc, base, 0, k0, K0, K1, max_below, max_cols, sh.count, s);
+        } else {
+          launch_rankk<T>(d_desc, base, 0, k0, K0, K1, max_below, max_cols, sh.count, s);
+        }
         if (prof) prof->end(PROF_PANEL, s, fl_in, 0.0);
       }
     }
@@ -560,11 +674,12 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
     double fl = 0.0, by = 0.0;
     for (int b = 0; b < sh.count; ++b) {
       if (K1 >= sh.e[b]) continue;
-      max_rows = std::max(max_rows, sh.m[b] - K1);
-      max_cols = std::max(max_cols, sh.e[b] - K1);
-      const double ent = trapezoid(K1, sh.e[b], sh.m[b]);
+      const int rows = band_rows(hd[b], K1, K1).nv, cend = band_limit(hd[b], K1);
+      max_rows = std::max(max_rows, rows);
+      max_cols = std::max(max_cols, cend - K1);
+      const double ent = band_entries(hd[b], K1, K1, cend);
       fl += 2.0 * ob * ent;
-      by += sizeof(T) * (2.0 * ent + (double)ob * (sh.m[b] - K1));
+      by += sizeof(T) * (2.0 * ent + (double)ob * rows);
     }
     if (max_rows > 0 && max_cols > 0) {
       if (prof) prof->begin(PROF_RANKK, s);
@@ -645,6 +760,166 @@ __global__ void __launch_bounds__(256) k_gemv(const GemvDesc *__restrict__ tasks
       y[t.y_off + r1] = (t.flags & 2) ? y[t.y_off + r1] + v : v;
     }
   }
+}
+
+// ---- batched symmetric GEMV: S CTAs (8 warps each) per matrix ---------------
+// The matrix is read as 32 x 32 tiles of its lower block triangle, each once: tile (I, J),
+// J < I, serves both y_I += A_IJ x_J and y_J += A_IJ^T x_I; a diagonal tile serves
+// y_I += A_II x_I.  CTA s of a matrix takes the s-th of S contiguous runs of the row-major
+// tile order and splits it over its warps the same way; a warp holds the next tile in
+// registers (16-byte loads, a 128-byte row segment per 32 / VN lanes) while it multiplies
+// the current one from its shared-memory copy (row sums: lane = tile row; column sums:
+// lane = tile column) and adds both into its own partial vector, so no two warps write the
+// same word.  The CTA adds its warps' vectors in warp order; with S > 1 it stores the sum in
+// `scratch` and the last CTA of the matrix to finish (counter per matrix, reset by that CTA)
+// adds the S sums in order s = 0 .. S-1.  Deterministic; half the bytes of a full GEMV.
+// Plain rows of B go to the CTAs round-robin.
+template <typename T>
+__global__ void __launch_bounds__(256) k_symv_batched(const SymvTask *__restrict__ tasks, const T *__restrict__ A,
+                                                      const double *__restrict__ x, const int *__restrict__ xidx,
+                                                      double *__restrict__ y, double alpha, const int *__restrict__ done,
+                                                      T *__restrict__ scratch, int *__restrict__ counter, int ld_scr) {
+  if (done && *done) return;
+  using VT = typename Vec16<T>::V;
+  constexpr int VN = Vec16<T>::N;
+  constexpr int LPR = 32 / VN;       // lanes per 32-wide tile row
+  constexpr int RPI = 32 / LPR;      // tile rows per warp instruction
+  constexpr int TPL = 32 / RPI;      // vectors per lane per tile
+  const SymvTask t = tasks[blockIdx.y];
+  const int S = gridDim.x, sidx = blockIdx.x;
+  const int n = t.n, nb = (n + 31) >> 5, np = nb * 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T *xs = reinterpret_cast<T *>(smem_raw);  // [np]
+  T *part = xs + np;                         // [8][np]
+  T *tiles = part + 8 * np;                  // [8][32][33]
+  __shared__ int last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int c = tid; c < np; c += 256)
+    xs[c] = c < n ? (T)((t.flags & 1) ? x[xidx[t.x_off + c]] : x[t.x_off + c]) : T(0);
+  for (int c = tid; c < 8 * np; c += 256) part[c] = T(0);
+  __syncthreads();
+  const T *a = A + t.a_off;
+  T *tile = tiles + warp * 32 * 33;
+  T *mine = part + warp * np;
+  const long long ntiles = (long long)nb * (nb + 1) / 2;
+  const long long c0 = ntiles * sidx / S, c1 = ntiles * (sidx + 1) / S;  // this CTA's run
+  const int s0 = (int)(c0 + (c1 - c0) * warp / 8), s1 = (int)(c0 + (c1 - c0) * (warp + 1) / 8);
+  // tile index s = I (I + 1) / 2 + J  ->  (I, J)
+  int I = 0;
+  while ((I + 1) * (I + 2) / 2 <= s0) ++I;
+  int J = s0 - I * (I + 1) / 2;
+  const int lr = lane / LPR, lc = (lane % LPR) * VN;  // this lane's row in a group and column
+  VT buf[TPL];
+  auto load = [&](int ti, int tj) {
+#pragma unroll
+    for (int i = 0; i < TPL; ++i) {
+      const int r = 32 * ti + i * RPI + lr, c = 32 * tj + lc;
+      VT v = (r < n && c < n) ? *reinterpret_cast<const VT *>(a + (long long)r * t.ld + c) : VT{};
+#pragma unroll
+      for (int q = 0; q < VN; ++q)
+        if (c + q >= n) Vec16<T>::set(v, q, T(0));
+      buf[i] = v;
+    }
+  };
+  if (s0 < s1) load(I, J);
+  for (int s = s0; s < s1; ++s) {
+#pragma unroll
+    for (int i = 0; i < TPL; ++i)
+#pragma unroll
+      for (int q = 0; q < VN; ++q) tile[(i * RPI + lr) * 33 + lc + q] = Vec16<T>::get(buf[i], q);
+    __syncwarp();
+    const int ci = I, cj = J;
+    if (++J > I) { ++I; J = 0; }
+    if (s + 1 < s1) load(I, J);  // in flight while this tile is multiplied
+    T rsum = T(0);
+#pragma unroll 8
+    for (int c = 0; c < 32; ++c) rsum += tile[lane * 33 + c] * xs[32 * cj + c];
+    mine[32 * ci + lane] += rsum;
+    if (cj < ci) {
+      T csum = T(0);
+#pragma unroll 8
+      for (int r = 0; r < 32; ++r) csum += tile[r * 33 + lane] * xs[32 * ci + r];
+      mine[32 * cj + lane] += csum;
+    }
+    __syncwarp();
+  }
+  // plain rows of B: one warp per row, rows dealt to the CTAs round-robin
+  for (int r = sidx + S * warp; r < t.nb; r += 8 * S) {
+    const T *brow = A + t.b_off + (long long)r * t.ld;
+    T acc = T(0);
+    for (int c = lane; c < n; c += 32) acc += brow[c] * xs[c];
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      const double v = alpha * (double)acc;
+      y[t.yb_off + r] = (t.flags & 2) ? y[t.yb_off + r] + v : v;
+    }
+  }
+  __syncthreads();
+  if (S == 1) {
+    for (int r = tid; r < n; r += 256) {
+      T v = part[r];
+#pragma unroll
+      for (int w = 1; w < 8; ++w) v += part[w * np + r];
+      const double o = alpha * (double)v;
+      y[t.y_off + r] = (t.flags & 2) ? y[t.y_off + r] + o : o;
+    }
+    return;
+  }
+  T *mysum = scratch + ((long long)blockIdx.y * S + sidx) * ld_scr;
+  for (int r = tid; r < n; r += 256) {
+    T v = part[r];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) v += part[w * np + r];
+    mysum[r] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) last = (atomicAdd(&counter[blockIdx.y], 1) == S - 1);
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const T *sums = scratch + (long long)blockIdx.y * S * ld_scr;
+  for (int r = tid; r < n; r += 256) {
+    T v = __ldcg(sums + r);
+    for (int q = 1; q < S; ++q) v += __ldcg(sums + (long long)q * ld_scr + r);
+    const double o = alpha * (double)v;
+    y[t.y_off + r] = (t.flags & 2) ? y[t.y_off + r] + o : o;
+  }
+  if (tid == 0) counter[blockIdx.y] = 0;  // ready for the next launch
+}
+
+template <typename T>
+size_t symv_smem(int max_n) {
+  const size_t np = (size_t)((max_n + 31) / 32) * 32;
+  return sizeof(T) * (9 * np + 8 * 32 * 33);
+}
+
+// CTAs per matrix: one while the matrices alone fill the resident slots (a split costs a
+// partial-sum round trip and shorter prefetch runs), else enough to fill one wave, with at
+// least 8 tiles per CTA (one per warp) and at most 16.  slots = 0: one CTA per matrix.
+int symv_split(int ntasks, int max_n, int slots) {
+  if (slots <= 0 || ntasks <= 0 || ntasks >= slots) return 1;
+  const long long nb = (max_n + 31) / 32, ntiles = nb * (nb + 1) / 2;
+  const int smax = (int)std::max<long long>(1, std::min<long long>(16, ntiles / 8));
+  return std::max(1, std::min(smax, (slots + ntasks - 1) / ntasks));
+}
+
+template <typename T>
+int symv_occupancy(int max_n) {
+  int occ = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_symv_batched<T>, 256, symv_smem<T>(max_n)) != cudaSuccess)
+    return 0;
+  return occ;
+}
+
+template <typename T>
+void launch_symv_batched(int ntasks, int max_n, int split, const SymvTask *d_tasks, const T *A, const double *x,
+                         const int *xidx, double *y, double alpha, const int *done, T *scratch, int *counter,
+                         int ld_scr, cudaStream_t s) {
+  if (ntasks == 0 || max_n == 0) return;
+  k_symv_batched<T><<<dim3(split, ntasks), 256, symv_smem<T>(max_n), s>>>(d_tasks, A, x, xidx, y, alpha, done,
+                                                                          scratch, counter, ld_scr);
+  count_launch();
 }
 
 // y[a] = (acc ? y[a] : 0) + alpha sum_p A[p][a] x[p]: one CTA per (task, 32 columns);
@@ -779,45 +1054,96 @@ void launch_gemv_t_task(int ntasks, int max_rows, int max_cols, const GemvDesc *
   count_launch();
 }
 
-// y (+)= A x for one large row-major matrix (n x n, ld a multiple of 8): one warp per row,
-// 16-byte loads, four rows' worth of loads in flight per lane; x staged in shared memory
-// in T (as k_gemv does), accumulation in T.  The coarse solve of large coarse problems.
+// y (+)= A x for one large symmetric matrix stored in full (n x n, row-major, ld a multiple
+// of 8, zero padding columns), reading only its lower block triangle.  The CTA of rows
+// [I0, I0 + 8) takes
+//   the row strip     A[I0 .. I0+8)[0 .. I0+8)   (diagonal 8 x 8 block included; one warp
+//                     per row, 16-byte loads, four in flight per lane), and
+//   the column strip  A[I0+8 .. n)[I0 .. I0+8)   (the symmetric images of the same rows'
+//                     entries right of the diagonal block; 16-byte loads, 32 / (8 / VN) rows
+//                     per warp instruction, four instructions in flight),
+// so every CTA reads n x 8 values and the kernel touches half the matrix: the repeated
+// products of an iterative refinement find it in L2.  x staged in shared memory in T,
+// accumulation in T, partial sums added in a fixed order.  The coarse solve of large
+// coarse problems.
 template <typename T>
-__global__ void __launch_bounds__(256) k_gemv_rows(int n, const T *__restrict__ A, int ld,
+__global__ void __launch_bounds__(256) k_symv_rows(int n, const T *__restrict__ A, int ld,
                                                    const double *__restrict__ x, double *__restrict__ y,
                                                    int accumulate, const int *__restrict__ done) {
   if (done && *done) return;
   using VT = typename Vec16<T>::V;
   constexpr int VN = Vec16<T>::N;
+  constexpr int LPR = 8 / VN;    // lanes per 8-wide row segment of the column strip
+  constexpr int RPI = 32 / LPR;  // column-strip rows per warp instruction
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *xs = reinterpret_cast<T *>(smem_raw);
+  __shared__ T part[8][8];  // [warp][column of the block]: column-strip sums
   const int npad = (n + 7) & ~7;
   for (int c = threadIdx.x; c < npad; c += blockDim.x) xs[c] = c < n ? (T)x[c] : T(0);
   __syncthreads();
-  const int row = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-  if (row >= n) return;
-  const VT *a = reinterpret_cast<const VT *>(A + (long long)row * ld);
-  const VT *xv = reinterpret_cast<const VT *>(xs);
-  const int nv = npad / VN;  // the padding columns of A are zero, as are those of xs
-  T acc0 = T(0), acc1 = T(0), acc2 = T(0), acc3 = T(0);
-  int v = lane;
-  for (; v + 96 < nv; v += 128) {
-    const VT a0 = a[v], a1 = a[v + 32], a2 = a[v + 64], a3 = a[v + 96];
-    acc0 += Vec16<T>::dot(a0, xv[v]);
-    acc1 += Vec16<T>::dot(a1, xv[v + 32]);
-    acc2 += Vec16<T>::dot(a2, xv[v + 64]);
-    acc3 += Vec16<T>::dot(a3, xv[v + 96]);
+  const int I0 = blockIdx.x * 8, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int row = I0 + warp;
+  // row strip: columns [0, I0 + 8) (I0 + 8 <= npad; padding columns are zero)
+  T rs = T(0);
+  if (row < n) {
+    const VT *a = reinterpret_cast<const VT *>(A + (long long)row * ld);
+    const VT *xv = reinterpret_cast<const VT *>(xs);
+    const int nv = (I0 + 8) / VN;
+    T acc0 = T(0), acc1 = T(0), acc2 = T(0), acc3 = T(0);
+    int v = lane;
+    for (; v + 96 < nv; v += 128) {
+      const VT a0 = a[v], a1 = a[v + 32], a2 = a[v + 64], a3 = a[v + 96];
+      acc0 += Vec16<T>::dot(a0, xv[v]);
+      acc1 += Vec16<T>::dot(a1, xv[v + 32]);
+      acc2 += Vec16<T>::dot(a2, xv[v + 64]);
+      acc3 += Vec16<T>::dot(a3, xv[v + 96]);
+    }
+    for (; v < nv; v += 32) acc0 += Vec16<T>::dot(a[v], xv[v]);
+    rs = warp_sum((acc0 + acc1) + (acc2 + acc3));
   }
-  for (; v < nv; v += 32) acc0 += Vec16<T>::dot(a[v], xv[v]);
-  const double s = (double)warp_sum((acc0 + acc1) + (acc2 + acc3));
-  if (lane == 0) y[row] = accumulate ? y[row] + s : s;
+  // column strip: rows [I0 + 8, n), columns [I0, I0 + 8); lane -> (row in the group, vector)
+  T cs[VN];
+#pragma unroll
+  for (int q = 0; q < VN; ++q) cs[q] = T(0);
+  {
+    const int sub = lane / LPR, seg = lane % LPR;
+    const T *col = A + I0 + seg * VN;
+    constexpr int kStride = 8 * RPI;  // rows between a warp's consecutive instructions
+    for (int j = I0 + 8 + warp * RPI + sub; j < n; j += 4 * kStride) {
+      VT v[4];
+      T xj[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int jj = j + u * kStride;
+        v[u] = jj < n ? *reinterpret_cast<const VT *>(col + (long long)jj * ld) : VT{};
+        xj[u] = jj < n ? xs[jj] : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) Vec16<T>::axpy(cs, v[u], xj[u]);
+    }
+#pragma unroll
+    for (int q = 0; q < VN; ++q)
+#pragma unroll
+      for (int off = LPR; off < 32; off <<= 1) cs[q] += __shfl_xor_sync(0xffffffffu, cs[q], off);
+    if (sub == 0) {
+#pragma unroll
+      for (int q = 0; q < VN; ++q) part[warp][seg * VN + q] = cs[q];
+    }
+  }
+  __syncthreads();
+  if (lane == 0 && row < n) {
+    T t = rs;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) t += part[w][warp];
+    y[row] = accumulate ? y[row] + (double)t : (double)t;
+  }
 }
 
 template <typename T>
-void launch_gemv_rows(int n, const T *A, int ld, const double *x, double *y, int accumulate, const int *done,
+void launch_symv_rows(int n, const T *A, int ld, const double *x, double *y, int accumulate, const int *done,
                       cudaStream_t s) {
   if (n == 0) return;
-  k_gemv_rows<T><<<ceil_div(n, 8), 256, sizeof(T) * (size_t)((n + 7) & ~7), s>>>(n, A, ld, x, y, accumulate, done);
+  k_symv_rows<T><<<ceil_div(n, 8), 256, sizeof(T) * (size_t)((n + 7) & ~7), s>>>(n, A, ld, x, y, accumulate, done);
   count_launch();
 }
 
@@ -929,8 +1255,10 @@ __global__ void __launch_bounds__(1024) k_trsv(const MatDesc *__restrict__ desc,
               const VT *Lv = reinterpret_cast<const VT *>(Lr);
               const VT *vv = reinterpret_cast<const VT *>(v);
               const int nv = r0 / VN;
+              // columns left of rn - band hold zeros (banded factor): start at the band
+              const int i0 = d.band >= n ? 0 : max(0, rn - d.band) / VN;
               T a0 = T(0), a1 = T(0), a2 = T(0), a3 = T(0);
-              int i = lane;
+              int i = i0 + lane;
               for (; i + 96 < nv; i += 128) {
                 const VT l0 = Lv[i], l1 = Lv[i + 32], l2 = Lv[i + 64], l3 = Lv[i + 96];
                 a0 += Vec16<T>::dot(l0, vv[i]);
@@ -952,8 +1280,10 @@ __global__ void __launch_bounds__(1024) k_trsv(const MatDesc *__restrict__ desc,
           for (int u = 0; u < VN; ++u) acc[u] = T(0);
           const T *Lc = L + r0n + VN * cq;
           constexpr int kStep = 31 * RPW;
+          // rows past the band of the block's last column hold zeros there (banded factor)
+          const int cend = d.band >= n ? n : min(n, r0n + 32 + d.band);
           int c = r1 + RPW * (wid - 1) + rq;
-          for (; c + 3 * kStep < n; c += 4 * kStep) {
+          for (; c + 3 * kStep < cend; c += 4 * kStep) {
             const VT l0 = *reinterpret_cast<const VT *>(Lc + (long long)c * d.ld);
             const VT l1 = *reinterpret_cast<const VT *>(Lc + (long long)(c + kStep) * d.ld);
             const VT l2 = *reinterpret_cast<const VT *>(Lc + (long long)(c + 2 * kStep) * d.ld);
@@ -963,7 +1293,8 @@ __global__ void __launch_bounds__(1024) k_trsv(const MatDesc *__restrict__ desc,
             Vec16<T>::axpy(acc, l2, v[c + 2 * kStep]);
             Vec16<T>::axpy(acc, l3, v[c + 3 * kStep]);
           }
-          for (; c < n; c += kStep) Vec16<T>::axpy(acc, *reinterpret_cast<const VT *>(Lc + (long long)c * d.ld), v[c]);
+          for (; c < cend; c += kStep)
+            Vec16<T>::axpy(acc, *reinterpret_cast<const VT *>(Lc + (long long)c * d.ld), v[c]);
 #pragma unroll
           for (int u = 0; u < VN; ++u)
 #pragma unroll
@@ -995,6 +1326,8 @@ size_t dense_smem_limit() { return 200 * 1024; }
 bool dense_configure() {
   const int lim = (int)dense_smem_limit();
   bool ok = true;
+  ok &= cudaFuncSetAttribute(k_diag_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kInvSmem) ==
+        cudaSuccess;
   ok &= cudaFuncSetAttribute(k_bigpanel<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)bigpanel_smem<float, false>()) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_bigpanel<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1009,8 +1342,11 @@ bool dense_configure() {
   ok &= cudaFuncSetAttribute(k_gemv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_gemv_t<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_gemv_t<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
-  ok &= cudaFuncSetAttribute(k_gemv_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
-  ok &= cudaFuncSetAttribute(k_gemv_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_symv_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_symv_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_symv_batched<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) ==
+        cudaSuccess;
+  ok &= cudaFuncSetAttribute(k_symv_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_gemv_task<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_gemv_task<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
   ok &= cudaFuncSetAttribute(k_gemv_t_task<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess;
@@ -1020,11 +1356,15 @@ bool dense_configure() {
 
 #define BD_INST(T)                                                                                              \
   template void engine_partial_cholesky<T>(const EngineShape &, const MatDesc *, T *, int *, cudaStream_t,    \
-                                           T *, ProfHook *, bool);                                             \
+                                           T *, ProfHook *, bool, float *);                                    \
   template void launch_gemv<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *,        \
                                double *, double, const int *, cudaStream_t);                                   \
-  template void launch_gemv_rows<T>(int, const T *, int, const double *, double *, int, const int *,           \
+  template void launch_symv_rows<T>(int, const T *, int, const double *, double *, int, const int *,           \
                                     cudaStream_t);                                                             \
+  template size_t symv_smem<T>(int);                                                                           \
+  template int symv_occupancy<T>(int);                                                                         \
+  template void launch_symv_batched<T>(int, int, int, const SymvTask *, const T *, const double *, const int *,\
+                                       double *, double, const int *, T *, int *, int, cudaStream_t);          \
   template void launch_gemv_task<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *,   \
                                     double *, double, const int *, cudaStream_t);                              \
   template void launch_gemv_t_task<T>(int, int, int, const GemvDesc *, const T *, const double *, const int *, \

@@ -80,6 +80,8 @@ struct EngineShape {
   int max_e, max_m;
   std::vector<int> m, e;  // host copies for per-step grid sizes
   int ob = 256;           // outer block: columns per long-K trailing update (multiple of 128)
+  std::vector<int> band;  // host copies of MatDesc::band (empty: every matrix dense)
+  std::vector<int> id0;   // host copies of MatDesc::id0 (empty: no identity block)
 };
 // The engine works through outer blocks of sh.ob columns: panels of kEnginePanel
 // columns (k_bigpanel), each followed by an update of the rest of its block, then
@@ -88,9 +90,11 @@ struct EngineShape {
 // [desc[b].dblk, desc[b].dblk + ceil(e_b / kNB)) (row-major, identity outside the last
 // block's width).  tc: FP32 only, run the long-K updates on the tensor cores (tc.cu).
 constexpr int kEnginePanel = 128;
+// pinv (FP32 with tc only): 128 x 128 floats per matrix of scratch; with it, the rows below
+// every panel are solved as one tensor-core product with the inverse of the diagonal block.
 template <typename T>
 void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *base, int *d_err, cudaStream_t s,
-                             T *store, ProfHook *prof = nullptr, bool tc = false);
+                             T *store, ProfHook *prof = nullptr, bool tc = false, float *pinv = nullptr);
 
 bool dense_configure();
 size_t dense_smem_limit();  // bytes of shared memory the dense kernels may stage per CTA
@@ -98,7 +102,7 @@ size_t dense_smem_limit();  // bytes of shared memory the dense kernels may stag
 // tc.cu
 bool tc_configure();
 void launch_rankk_tc(const MatDesc *d_desc, float *base, int mode, int K0, int K1, int max_rows, int max_cols,
-                     int count, int *err, cudaStream_t s);
+                     int count, int *err, cudaStream_t s, const float *pinv = nullptr);
 
 // The same products for many small matrices: one CTA per task over all its rows (columns)
 template <typename T>
@@ -108,9 +112,24 @@ template <typename T>
 void launch_gemv_t_task(int ntasks, int max_rows, int max_cols, const GemvDesc *d_tasks, const T *A,
                         const double *x, const int *xidx, double *y, double alpha, const int *done, cudaStream_t s,
                         const CsrIn *csr = nullptr);
-// y (+)= A x for one large n x n row-major matrix (ld a multiple of 8, zero padding columns)
+// Batched symmetric GEMV over SymvTask (split CTAs per task, lower block triangle read once);
+// symv_smem: its shared memory for matrices up to max_n (above dense_smem_limit: not usable);
+// symv_occupancy: resident CTAs per SM at that size; symv_split: CTAs per task for a number of
+// resident slots.  With split > 1, scratch holds ntasks x split rows of ld_scr >= max_n values
+// and counter ntasks zeroed ints (left zeroed by every launch).
 template <typename T>
-void launch_gemv_rows(int n, const T *A, int ld, const double *x, double *y, int accumulate, const int *done,
+size_t symv_smem(int max_n);
+template <typename T>
+int symv_occupancy(int max_n);
+int symv_split(int ntasks, int max_n, int slots);
+template <typename T>
+void launch_symv_batched(int ntasks, int max_n, int split, const SymvTask *d_tasks, const T *A, const double *x,
+                         const int *xidx, double *y, double alpha, const int *done, T *scratch, int *counter,
+                         int ld_scr, cudaStream_t s);
+// y (+)= A x for one large symmetric n x n row-major matrix (ld a multiple of 8, zero padding
+// columns), reading only its lower block triangle
+template <typename T>
+void launch_symv_rows(int n, const T *A, int ld, const double *x, double *y, int accumulate, const int *done,
                       cudaStream_t s);
 // y = alpha * A x (+ y): tasks in d_tasks (GemvDesc); x gathered through xidx when flagged.
 template <typename T>

@@ -82,6 +82,11 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t phase) {
 
 }  // namespace
 
+// mode 3: the panel solve L_21 = A_21 Linv^T below the factored diagonal block [K0, K0 + w)
+// (w = min(128, e - K0)): rows as the band lets them reach, output columns K0 .. K0 + w - 1,
+// the B operand from pinv (128 x 128 per matrix, the inverse of L_11), result stored;
+// mode 0: the update of an outer block by its finished 128-column panel [K0, K0 + 128):
+// rows [K0 + 128, m), cols [K0 + 128, min(K1, e)), K = [K0, min(K0 + 128, e));
 // mode 1: rows/cols [e, m), K = [0, e); mode 2: rows [K1, m), cols [K1, e), K = [K0, K1).
 // Per K chunk i of 32 FP32 columns: every thread holds its share of chunk i in registers
 // (loaded while the MMAs of chunk i - 1 ran), waits (bounded) for those MMAs to release the
@@ -90,19 +95,30 @@ __device__ inline bool mbar_wait(uint32_t bar, uint32_t phase) {
 // chunk i + 1 go out while they run.  65 KB of shared memory per CTA let three CTAs share an
 // SM, so one CTA's split, epilogue or pipeline fill overlaps the others' MMAs.
 __global__ void __launch_bounds__(128, 3) k_rankk_tc(const MatDesc *__restrict__ desc, float *__restrict__ base,
-                                                     int mode, int K0, int K1, int nct, int *__restrict__ err) {
+                                                     int mode, int K0, int K1, int nct, int *__restrict__ err,
+                                                     const float *__restrict__ pinv) {
   const MatDesc d = desc[blockIdx.y];
   int row0, colend, kb, ke;
-  if (mode == 2) {
+  if (mode == 3) {
+    if (K0 >= d.e) return;
+    const int w = min(kTM, d.e - K0);
+    row0 = K0 + w; colend = w; kb = K0; ke = K0 + w;  // colend, c0: columns of the panel (relative)
+  } else if (mode == 0) {
+    if (K0 + kTM >= d.e) return;
+    row0 = K0 + kTM; colend = min(K1, d.e); kb = K0; ke = K0 + kTM;
+  } else if (mode == 2) {
     if (K1 >= d.e) return;
     row0 = K1; colend = d.e; kb = K0; ke = K1;
   } else {
     row0 = d.e; colend = d.m; kb = 0; ke = d.e;
   }
+  const BandRows br = band_rows(d, row0, ke);  // rows past the band hold zeros in K = [kb, ke)
+  if (mode == 0 || mode == 2) colend = min(colend, band_limit(d, ke));
   const int ti = blockIdx.x / nct, tj = blockIdx.x % nct;
   if (tj > ti) return;
-  const int r0 = row0 + ti * kTM, c0 = row0 + tj * kTM;
-  if (r0 >= d.m || c0 >= colend || ke <= kb) return;
+  const int v0 = ti * kTM, c0 = (mode == 3 ? 0 : row0) + tj * kTM;
+  const float *B = mode == 3 ? pinv + (long long)blockIdx.y * kTM * kTM : nullptr;  // rows c, K from kb
+  if (v0 >= br.nv || c0 >= colend || ke <= kb) return;
   const float *A = base + d.off;
 
   extern __shared__ unsigned char smem_raw[];
@@ -139,9 +155,9 @@ __global__ void __launch_bounds__(128, 3) k_rankk_tc(const MatDesc *__restrict__
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int r = rr + 16 * i;
-      const bool va = r0 + r < d.m, vb = c0 + r < colend;
-      const float *pa = A + (long long)(r0 + r) * d.ld + k;
-      const float *pb = A + (long long)(c0 + r) * d.ld + k;
+      const bool va = v0 + r < br.nv, vb = c0 + r < colend;
+      const float *pa = A + (long long)(va ? br.row(v0 + r) : 0) * d.ld + k;
+      const float *pb = B ? B + (long long)(c0 + r) * kTM + (k - kb) : A + (long long)(c0 + r) * d.ld + k;
       if (kv == 4) {
         ra[i] = va ? __ldg(reinterpret_cast<const float4 *>(pa)) : make_float4(0.f, 0.f, 0.f, 0.f);
         rb[i] = vb ? __ldg(reinterpret_cast<const float4 *>(pb)) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -251,17 +267,23 @@ __global__ void __launch_bounds__(128, 3) k_rankk_tc(const MatDesc *__restrict__
       __syncwarp();
       const int c = c0 + cc + lane;
       const bool vc = c < colend;
-      {  // all 32 rows' loads in flight, then their stores
+      if (mode == 3) {  // the panel solve stores its product
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          const int v = v0 + warp * 32 + u;
+          if (vc && v < br.nv) base[d.off + (long long)br.row(v) * d.ld + K0 + c] = stage[u * 33 + lane];
+        }
+      } else {  // all 32 rows' loads in flight, then their stores
         float cv[32];
 #pragma unroll
         for (int u = 0; u < 32; ++u) {
-          const int r = r0 + warp * 32 + u;
-          cv[u] = (vc && r < d.m) ? A[(long long)r * d.ld + c] : 0.f;
+          const int v = v0 + warp * 32 + u;
+          cv[u] = (vc && v < br.nv) ? A[(long long)br.row(v) * d.ld + c] : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < 32; ++u) {
-          const int r = r0 + warp * 32 + u;
-          if (vc && r < d.m) base[d.off + (long long)r * d.ld + c] = cv[u] - stage[u * 33 + lane];
+          const int v = v0 + warp * 32 + u;
+          if (vc && v < br.nv) base[d.off + (long long)br.row(v) * d.ld + c] = cv[u] - stage[u * 33 + lane];
         }
       }
       __syncwarp();
@@ -282,10 +304,10 @@ bool tc_configure() {
 }
 
 void launch_rankk_tc(const MatDesc *d_desc, float *base, int mode, int K0, int K1, int max_rows, int max_cols,
-                     int count, int *err, cudaStream_t s) {
+                     int count, int *err, cudaStream_t s, const float *pinv) {
   const int nrt = ceil_div(max_rows, kTM), nct = ceil_div(max_cols, kTM);
   if (nrt == 0 || nct == 0) return;
-  k_rankk_tc<<<dim3(nrt * nct, count), 128, kTcSmem, s>>>(d_desc, base, mode, K0, K1, nct, err);
+  k_rankk_tc<<<dim3(nrt * nct, count), 128, kTcSmem, s>>>(d_desc, base, mode, K0, K1, nct, err, pinv);
   count_launch();
 }
 
