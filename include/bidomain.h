@@ -310,10 +310,12 @@ int bidomain_coarse_solve(bd_handle *h, const double *c, double *z, int nref);
  * best of two after a warm-up) at the current Jacobian for every combination of
  * outer block width {128, 256, 512} (columns per long-K trailing update; panels
  * are 128 columns), number of subdomain groups the batch is factorised in
- * {1, 2, 4} and, in BD_MIXED, tensor cores on/off; keeps the fastest for the
- * handle and leaves the Jacobian factorised with it.  Requires
- * bidomain_linearize (or a step) first.  Results are identical up to rounding for
- * every choice. */
+ * {1, 2, 4} and, in BD_MIXED, the arithmetic: SIMT FP32 (tensor_cores = 0), the
+ * rank-k updates on the tensor cores (1), or also the rows below every panel solved on
+ * the tensor cores as one product with the inverse of the 128 x 128 diagonal block (2);
+ * keeps the fastest for the handle and leaves the Jacobian factorised with it.
+ * Requires bidomain_linearize (or a step) first.  Results are identical up to rounding
+ * for every choice. */
 typedef struct {
   int outer_panel, groups, tensor_cores, candidates;
   double best_ms, default_ms;

@@ -241,6 +241,8 @@ struct bd_handle {
   int nI_tot = 0, nG_tot = 0, nD_tot = 0, nP_tot = 0, nint_nodes = 0;
   std::vector<int> nI, nG, nD, nP, int_off, giff_off, ldual_off, lprim_off;
   std::vector<int> band_I;  // dof half-bandwidth of each interior block (nodes ordered by global id)
+  std::vector<std::vector<int>> ifirst_I;  // per K matrix: first interior column of each interface row
+  int *d_ifirst = nullptr;
   int *d_int_node, *d_iface_node, *d_R, *d_Rt_ptr, *d_Rt_idx, *d_vec_off_I;
   int *d_ldual_off, *d_lprim_off, *d_nD, *d_nI, *d_prim_x, *d_pl_ptr, *d_pl_idx, *d_giff_off;
   double *d_mult_iface;
@@ -313,6 +315,7 @@ struct bd_handle {
   double rtol_scale = 1.0;
   // factorisation tuning (bidomain_autotune): outer panel width, batch groups, tensor cores
   int tune_ob = 256, tune_groups = 1;
+  int tune_panel_tc = 0;  // 1: panel solves on the tensor cores too (with d_pinv; tensor cores on)
   cudaGraphExec_t pcg_exec[2] = {nullptr, nullptr};  // captured PCG chunk per method
   size_t pcg_nodes[2] = {0, 0};
   double gemv_schur_flops = 0, gemv_schur_bytes = 0, gemv_local_flops = 0, gemv_local_bytes = 0;
@@ -527,7 +530,7 @@ void setup_handle(bd_handle &h) {
   ck(cudaMemsetAsync(h.d_err, 0, sizeof(int), s), "memset");
   // ---- local node tables and layouts
   const int S = h.nsub;
-  h.nI.resize(S); h.nG.resize(S); h.nD.resize(S); h.nP.resize(S); h.band_I.resize(S);
+  h.nI.resize(S); h.nG.resize(S); h.nD.resize(S); h.nP.resize(S); h.band_I.resize(S); h.ifirst_I.resize(S);
   h.int_off.resize(S); h.giff_off.resize(S); h.ldual_off.resize(S); h.lprim_off.resize(S);
   std::vector<int> q_sub, q_loc, q_node, q_nbr, int_node, R, prim_x, vec_off_I(S);
   for (int j = 0; j < S; ++j) {
@@ -549,6 +552,22 @@ void setup_handle(bd_handle &h) {
     }
     // dofs 2a + field: the couplings of nodes a, b lie within |2a - 2b| + 1 of the diagonal
     h.band_I[j] = 2 * nband + 1;
+    // interface rows of K: the first interior column each couples to (its L row is zero
+    // left of it), as a suffix minimum so the bound is non-decreasing
+    {
+      const int ng = (int)sp.nodes.size() - sp.n_interior;
+      std::vector<int> first(2 * ng, 2 * sp.n_interior);
+      for (int a = sp.n_interior; a < (int)sp.nodes.size(); ++a) {
+        int fb = sp.n_interior;
+        for (int sl = 0; sl < 27; ++sl) {
+          const int b = sp.nbr[27 * a + sl];
+          if (b >= 0 && b < sp.n_interior) fb = std::min(fb, b);
+        }
+        first[2 * (a - sp.n_interior)] = first[2 * (a - sp.n_interior) + 1] = 2 * fb;
+      }
+      for (int g = 2 * ng - 2; g >= 0; --g) first[g] = std::min(first[g], first[g + 1]);
+      h.ifirst_I[j] = std::move(first);
+    }
     for (int a = 0; a < sp.n_interior; ++a) int_node.push_back(sp.nodes[a]);
     for (int a = sp.n_interior; a < (int)sp.nodes.size(); ++a) {
       const int g = p.node_to_iface[sp.nodes[a]];
@@ -628,6 +647,15 @@ void setup_handle(bd_handle &h) {
   }
   // ---- dense layouts
   std::vector<MatDesc> kd(S), ad(S);
+  std::vector<long long> ifirst_off(S);
+  {
+    std::vector<int> flat;
+    for (int j = 0; j < S; ++j) {
+      ifirst_off[j] = (long long)flat.size();
+      flat.insert(flat.end(), h.ifirst_I[j].begin(), h.ifirst_I[j].end());
+    }
+    h.d_ifirst = m.upload(flat, s);
+  }
   std::vector<long long> so_off(S), zx_off(S), zp_off(S), sdd_off(S);
   std::vector<int> ldx(S), ldg(S);
   h.shK = EngineShape{S, 0, 0, {}, {}};
@@ -636,6 +664,7 @@ void setup_handle(bd_handle &h) {
     const int n = h.nI[j] + h.nG[j];
     kd[j] = MatDesc{h.K_el, pad8(n), n, h.nI[j], h.K_blk};
     kd[j].band = h.band_I[j];  // the interior block is banded: its updates skip the zeros past the band
+    kd[j].ifirst = h.d_ifirst + ifirst_off[j];  // and the interface rows of L_GI start late
     h.K_blk += ceil_div(h.nI[j], kNB);
     h.K_el += pad32((long long)pad8(n) * n);
     const int ma = 2 * h.nD[j] + h.nP[j];
@@ -654,6 +683,7 @@ void setup_handle(bd_handle &h) {
     sdd_off[j] = h.SDD_el;
     h.SDD_el += pad32((long long)ldx[j] * h.nD[j]);
     h.shK.m.push_back(n); h.shK.e.push_back(h.nI[j]); h.shK.band.push_back(h.band_I[j]);
+    h.shK.ifirst.push_back(h.ifirst_I[j].data());  // ifirst_I is not resized after setup
     h.shA.m.push_back(ma); h.shA.e.push_back(h.nD[j]); h.shA.id0.push_back(ad[j].id0);
     h.shK.max_m = std::max(h.shK.max_m, n); h.shK.max_e = std::max(h.shK.max_e, h.nI[j]);
     h.shA.max_m = std::max(h.shA.max_m, ma); h.shA.max_e = std::max(h.shA.max_e, h.nD[j]);
@@ -800,7 +830,7 @@ void setup_handle(bd_handle &h) {
     h.d_Codesc = m.upload(std::vector<MatDesc>{co}, s);
     h.shCo = EngineShape{1, np, 2 * np, {2 * np}, {np}};
     h.shCo.id0 = {np};
-    if (h.mixed() && h.opt.use_tensor_cores) {
+    if (h.mixed()) {  // the autotuner may turn the tensor cores on
       const int most = std::max({h.shK.count, h.shA.count, h.shC.count, 1});
       h.d_pinv = m.alloc<float>((size_t)most * 128 * 128);
     }
@@ -985,7 +1015,7 @@ void setup_handle(bd_handle &h) {
     D.Aug = m.alloc<T>(h.A_el);
     D.Sorig = m.alloc<T>(h.So_el);
     D.Z = m.alloc<T>(h.Z_el);
-    if (h.opt.method == BD_FETIDP) D.SDD = m.alloc<T>(h.SDD_el);
+    D.SDD = m.alloc<T>(h.SDD_el);
     D.Blk = m.alloc<T>(h.Blk_el);
     D.CA = m.alloc<T>(h.CA_el);
     D.Sinv = m.alloc<T>(h.Sinv_el);
@@ -1052,11 +1082,12 @@ void run_engine_groups(bd_handle &h, const EngineShape &all, const MatDesc *d_de
       g.e.push_back(all.e[q]);
       if (!all.band.empty()) g.band.push_back(all.band[q]);
       if (!all.id0.empty()) g.id0.push_back(all.id0[q]);
+      if (!all.ifirst.empty()) g.ifirst.push_back(all.ifirst[q]);
       g.max_m = std::max(g.max_m, all.m[q]);
       g.max_e = std::max(g.max_e, all.e[q]);
     }
     engine_partial_cholesky<T>(g, d_desc + a, base, h.d_err, h.s, linv, &h.prof, h.opt.use_tensor_cores != 0,
-                               h.d_pinv);
+                               h.tune_panel_tc ? h.d_pinv : nullptr);
   }
 }
 
@@ -1076,14 +1107,13 @@ void linearize_t(bd_handle &h, Dense<T> &D, bool precond) {
   else tval = h.d_tl_val;
   launch_build_aug<T>(h.nsub, h.shA.max_m, h.d_Sdesc, D.Sorig, h.d_Adesc, D.Aug, h.d_nD, h.d_tl_off, h.d_tl_ptr,
                       h.d_tl_row, tval, s);
-  if (h.opt.method == BD_FETIDP)  // S_DeltaDelta itself: only the FETI-DP preconditioner applies it
-    launch_copy<T, T>(h.cp_sdd.n, h.cp_sdd.max_elems, h.cp_sdd.d, D.Aug, D.SDD, s);
+  launch_copy<T, T>(h.cp_sdd.n, h.cp_sdd.max_elems, h.cp_sdd.d, D.Aug, D.SDD, s);
   launch_copy<T, T>(h.cp_blk.n, h.cp_blk.max_elems, h.cp_blk.d, D.Aug, D.Blk, s);
   run_engine_groups<T>(h, h.shA, h.d_Adesc, D.Aug, D.Linv);
   launch_copy<T, T>(h.cp_zx.n, h.cp_zx.max_elems, h.cp_zx.d, D.Aug, D.Z, s);
   launch_class_aug<T>(h.ncls, h.max_nc, h.d_cls, h.d_pairs, D.Blk, h.d_Cdesc, D.CA, s);
   engine_partial_cholesky<T>(h.shC, h.d_Cdesc, D.CA, h.d_err, s, D.Linv, &h.prof, h.opt.use_tensor_cores != 0,
-                             h.d_pinv);
+                             h.tune_panel_tc ? h.d_pinv : nullptr);
   launch_copy<T, T>(h.cp_sinv.n, h.cp_sinv.max_elems, h.cp_sinv.d, D.CA, D.Sinv, s);
   if (h.opt.scaling == BD_SCALING_RHO) {
     const double si = std::max({h.fp.sigma_i[0], h.fp.sigma_i[1], h.fp.sigma_i[2]});
@@ -1101,7 +1131,7 @@ void linearize_t(bd_handle &h, Dense<T> &D, bool precond) {
     EngineShape co = h.shCo;
     co.ob = h.tune_ob;
     engine_partial_cholesky<T>(co, h.d_Codesc, D.Co, h.d_err, s, D.LdCo, &h.prof, h.opt.use_tensor_cores != 0,
-                               h.d_pinv);
+                               h.tune_panel_tc ? h.d_pinv : nullptr);
   }
   launch_copy<T, T>(h.cp_coinv.n, h.cp_coinv.max_elems, h.cp_coinv.d, D.Co, D.CoInv, s);
   if (h.d_CoInv64) coarse_refine64<T>(h.np, D.CoInv, pad8(h.np), h.d_Co64d, h.d_CoInv64, h.d_CoW, h.d_CoY, s);
@@ -2128,7 +2158,11 @@ int bidomain_autotune(bd_handle *h, bd_tune_result *out) {
     ck(cudaEventCreate(&e1), "event");
     const int prof_on = h->prof.on;
     h->prof.on = 0;
-    const int tc0 = h->opt.use_tensor_cores, ob0 = h->tune_ob, g0 = h->tune_groups;
+    const int tc0 = h->opt.use_tensor_cores ? 1 + h->tune_panel_tc : 0, ob0 = h->tune_ob, g0 = h->tune_groups;
+    auto set_tc = [&](int tc) {  // 0 SIMT, 1 tensor-core updates, 2 also the panel solves
+      h->opt.use_tensor_cores = tc > 0;
+      h->tune_panel_tc = tc == 2 && h->d_pinv;
+    };
     auto time_it = [&]() {
       linearize(*h);  // warm
       float best = 1e30f;
@@ -2146,12 +2180,12 @@ int bidomain_autotune(bd_handle *h, bd_tune_result *out) {
     const float base_ms = time_it();
     float best_ms = base_ms;
     int best_ob = ob0, best_g = g0, best_tc = tc0, n = 0;
-    const int tcs[2] = {0, 1};
-    for (int tc : tcs) {
+    for (int tc : {0, 1, 2}) {
       if (tc && !h->mixed()) continue;
+      if (tc == 2 && !h->d_pinv) continue;
       for (int ob : {128, 256, 512})
         for (int g : {1, 2, 4}) {
-          h->opt.use_tensor_cores = tc;
+          set_tc(tc);
           h->tune_ob = ob;
           h->tune_groups = g;
           const float ms = time_it();
@@ -2159,7 +2193,7 @@ int bidomain_autotune(bd_handle *h, bd_tune_result *out) {
           if (ms < best_ms) { best_ms = ms; best_ob = ob; best_g = g; best_tc = tc; }
         }
     }
-    h->opt.use_tensor_cores = best_tc;
+    set_tc(best_tc);
     h->tune_ob = best_ob;
     h->tune_groups = best_g;
     linearize(*h);

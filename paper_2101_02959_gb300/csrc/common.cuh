@@ -49,6 +49,12 @@ struct MatDesc {
   // -A^-1): row id0 + i of L is zero left of column i, so an update whose K range ends at ke
   // reaches only the rows id0 .. id0 + ke - 1 of that block (id0 >= m: none)
   int id0 = 1 << 30;
+  // first column of the eliminated block that each later row [e, m) reaches in L, as a
+  // non-decreasing bound (suffix minimum): row e + g of L is zero left of ifirst[g], so an
+  // update whose K range ends at ke reaches only the rows e .. e + #{g: ifirst[g] < ke} - 1 of
+  // them, and the final update of rows [e + g, ...) needs K from ifirst[g] on (nullptr: dense;
+  // a device pointer in the kernels' descriptors, a host pointer in the engine's host copies)
+  const int *ifirst = nullptr;
 };
 
 // Rows [row0, m) that an update of the partial Cholesky with K range ending at ke reaches:
@@ -64,6 +70,19 @@ struct BandRows {
 __host__ __device__ inline int band_limit(const MatDesc &d, int ke) {
   return d.band >= d.e ? d.e : (ke + d.band < d.e ? ke + d.band : d.e);
 }
+// rows e .. e + result - 1 of the later block are the ones whose L row reaches a K range
+// ending at ke (binary search over the non-decreasing ifirst; m - e when there is no profile)
+__host__ __device__ inline int profile_rows(const MatDesc &d, int ke) {
+  const int n = d.m - d.e;
+  if (!d.ifirst || n <= 0) return n > 0 ? n : 0;
+  int lo = 0, hi = n;  // first g with ifirst[g] >= ke
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (d.ifirst[mid] < ke) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
 __host__ __device__ inline BandRows band_rows(const MatDesc &d, int row0, int ke) {
   BandRows b;
   b.row0 = row0;
@@ -71,7 +90,12 @@ __host__ __device__ inline BandRows band_rows(const MatDesc &d, int row0, int ke
   b.ni = lim > row0 ? lim - row0 : 0;
   b.mid0 = row0 > d.e ? row0 : d.e;
   const int idb = d.id0 < d.m ? d.id0 : d.m;  // start of the identity block (m: none)
-  b.nmid = idb > b.mid0 ? idb - b.mid0 : 0;
+  int midend = idb;
+  if (d.ifirst && row0 <= d.e) {  // the later rows whose L row the K range does not reach yet
+    const int pend = d.e + profile_rows(d, ke);
+    midend = pend < midend ? pend : midend;
+  }
+  b.nmid = midend > b.mid0 ? midend - b.mid0 : 0;
   b.idr = idb > b.mid0 ? idb : b.mid0;
   const long long idend = (long long)idb + ke;  // rows of the block reached so far
   const int iend = idend < d.m ? (int)idend : d.m;

@@ -414,6 +414,7 @@ __global__ void __launch_bounds__(256) k_rankk(const MatDesc *__restrict__ desc,
   const int ti = blockIdx.x / nct, tj = blockIdx.x % nct;
   if (tj > ti) return;
   const int v0 = ti * kTB, c0 = row0 + tj * kTB;
+  if (mode == 1 && d.ifirst && v0 < br.nv) kb = max(kb, d.ifirst[v0] & ~3);  // rows' L starts there
   if (v0 >= br.nv || c0 >= colend || ke <= kb) return;
   T *A = base + d.off;
   __shared__ T As[kKC][kTB + 1];  // row pad 65: the strided stores below hit distinct banks
@@ -493,6 +494,7 @@ __global__ void __launch_bounds__(256) k_rankk128(const MatDesc *__restrict__ de
   const int ti = blockIdx.x / nct, tj = blockIdx.x % nct;
   if (tj > ti) return;
   const int v0 = ti * kTB2, c0 = row0 + tj * kTB2;
+  if (mode == 1 && d.ifirst && v0 < br.nv) kb = max(kb, d.ifirst[v0] & ~3);  // rows' L starts there
   if (v0 >= br.nv || c0 >= colend || ke <= kb) return;
   float *A = base + d.off;
   __shared__ __align__(16) float As[2][kKC2][kTB2 + 4];
@@ -619,6 +621,7 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
     hd[b].e = sh.e[b];
     if (!sh.band.empty()) hd[b].band = sh.band[b];
     if (!sh.id0.empty()) hd[b].id0 = sh.id0[b];
+    if (!sh.ifirst.empty()) hd[b].ifirst = sh.ifirst[b];
   }
   for (int K0 = 0; K0 < sh.max_e; K0 += ob) {
     const int K1 = K0 + ob;
@@ -695,11 +698,20 @@ void engine_partial_cholesky(const EngineShape &sh, const MatDesc *d_desc, T *ba
   int max_t = 0;
   double fl = 0.0, by = 0.0;
   for (int b = 0; b < sh.count; ++b) {
-    max_t = std::max(max_t, sh.m[b] - sh.e[b]);
+    const int rows = band_rows(hd[b], sh.e[b], sh.e[b]).nv;  // rows whose L row is not zero
+    max_t = std::max(max_t, rows);
     const double n2 = sh.m[b] - sh.e[b];
-    const double ent = n2 * (n2 + 1) / 2.0;
-    fl += 2.0 * sh.e[b] * ent;
-    by += sizeof(T) * (2.0 * ent + n2 * sh.e[b]);
+    if (hd[b].ifirst) {  // row g of the trailing block needs K from ifirst[g] on
+      for (int g = 0; g < rows; ++g) {
+        const double k = sh.e[b] - (hd[b].ifirst[g] & ~3);
+        fl += 2.0 * k * (g + 1);
+        by += sizeof(T) * (2.0 * (g + 1) + k);
+      }
+    } else {
+      const double ent = n2 * (n2 + 1) / 2.0;
+      fl += 2.0 * sh.e[b] * ent;
+      by += sizeof(T) * (2.0 * ent + n2 * sh.e[b]);
+    }
   }
   if (max_t > 0) {
     if (prof) prof->begin(PROF_RANKK, s);

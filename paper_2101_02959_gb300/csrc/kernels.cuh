@@ -82,6 +82,7 @@ struct EngineShape {
   int ob = 256;           // outer block: columns per long-K trailing update (multiple of 128)
   std::vector<int> band;  // host copies of MatDesc::band (empty: every matrix dense)
   std::vector<int> id0;   // host copies of MatDesc::id0 (empty: no identity block)
+  std::vector<const int *> ifirst;  // host copies of MatDesc::ifirst (empty or nullptr: dense)
 };
 // The engine works through outer blocks of sh.ob columns: panels of kEnginePanel
 // columns (k_bigpanel), each followed by an update of the rest of its block, then

@@ -117,6 +117,7 @@ __global__ void __launch_bounds__(128, 3) k_rankk_tc(const MatDesc *__restrict__
   const int ti = blockIdx.x / nct, tj = blockIdx.x % nct;
   if (tj > ti) return;
   const int v0 = ti * kTM, c0 = (mode == 3 ? 0 : row0) + tj * kTM;
+  if (mode == 1 && d.ifirst && v0 < br.nv) kb = max(kb, d.ifirst[v0] & ~3);  // rows' L starts there
   const float *B = mode == 3 ? pinv + (long long)blockIdx.y * kTM * kTM : nullptr;  // rows c, K from kb
   if (v0 >= br.nv || c0 >= colend || ke <= kb) return;
   const float *A = base + d.off;
