@@ -308,7 +308,9 @@ TRAFFIC = {
                             "static constexpr int kTcSmem")},
     # DRAM bytes per library byte (a capture of three launches on the 32x32x16 slab): the operator
     # and local-solve launches read their matrices once; scaled to a launch by its own bytes
-    "k_symv_batched": {"dram_per_library_byte": None, "sha": None, "file": "dense.cu",
+    # DRAM bytes per library byte of the symmetric operator and local-solve products (a capture of
+    # four launches on the 4x4x4-subdomain cube at H/h = 8, 0.5 GB of operators: larger than L2)
+    "k_symv_batched": {"dram_per_library_byte": 1.069, "sha": "00ea69ed6e692111", "file": "dense.cu",
                        "span": ("__global__ void __launch_bounds__(256) k_symv_batched(",
                                 "template <typename T>\nsize_t symv_smem(")},
 }
