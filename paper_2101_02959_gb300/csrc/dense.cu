@@ -96,7 +96,7 @@ constexpr size_t bigpanel_smem() {
 }
 
 template <typename T, bool ROWS>
-__global__ void __launch_bounds__(256, ROWS ? 2 : 1) k_bigpanel(const MatDesc *__restrict__ desc, T *__restrict__ base, int K0,
+__global__ void __launch_bounds__(256, 2) k_bigpanel(const MatDesc *__restrict__ desc, T *__restrict__ base, int K0,
                                                      int *__restrict__ err, T *__restrict__ store) {
   constexpr int RB = PanelRows<T>::RB, NR = kPW + RB;
   constexpr int NS = ROWS ? RB : kPW;         // staged rows
