@@ -157,8 +157,10 @@ typedef struct {
    * fallback residual. */
   int learned_guess, mlp_train_steps, mlp_warmup, mlp_epochs;
   double mlp_lr;
-  /* BD_MIXED only: 1 = the long-K Schur updates of the factorisations run on
-   * the tensor cores (tcgen05, TF32 split in hi + lo parts, FP32 accumulation) */
+  /* BD_MIXED only: 1 = the rank-k Schur updates of the factorisations run on
+   * the tensor cores (tcgen05, TF32 split in hi + lo parts, FP32 accumulation);
+   * 2 = also the rows below every 128-column panel, solved as one tensor-core
+   * product with the inverse of the panel's factored diagonal block */
   int use_tensor_cores;
   /* 1 = chord Newton: factorise the Jacobian at the first Newton iterate of a
    * time step and reuse it for the later iterations of that step (every iterate

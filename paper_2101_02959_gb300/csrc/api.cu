@@ -1872,6 +1872,7 @@ int bidomain_setup(const bd_mesh *mesh, const bd_conductivity *cond, const bd_io
       return BD_ERR_CUDA;
     }
     if (h->opt.precision != BD_MIXED) h->opt.use_tensor_cores = 0;
+    h->tune_panel_tc = h->opt.use_tensor_cores == 2 ? 1 : 0;
     if (h->opt.learned_guess && !gemm_tc_configure()) {
       g_last_error = "tensor-core GEMM configuration failed";
       return BD_ERR_CUDA;

@@ -221,13 +221,14 @@ def test_tensor_core_schur_matches_fp64():
     x = synth.random_vector(prob.dofs.n_iface, 5)
     out = {}
     for key, opt in (("fp64", dict(precision="fp64")), ("simt", dict(precision="mixed", use_tensor_cores=0)),
-                     ("tc", dict(precision="mixed", use_tensor_cores=1))):
+                     ("tc", dict(precision="mixed", use_tensor_cores=1)),
+                     ("tcpanel", dict(precision="mixed", use_tensor_cores=2))):
         s = _solver("slab32", **opt)
         s.linearize(ui, ue, wn)
         sol, st = s.krylov_solve(f)
         out[key] = (s.schur_apply(x), sol, st)
         s.close()
-    for k in ("simt", "tc"):
+    for k in ("simt", "tc", "tcpanel"):
         assert _rel(out[k][0], out["fp64"][0]) < 2e-5
         assert abs(out[k][2]["its"] - out["fp64"][2]["its"]) <= 2
         # an FP32 operator: FP32 rounding is amplified in the near-null modes of J (u_i ~ u_e, smooth,
@@ -244,6 +245,7 @@ def test_tensor_core_schur_matches_fp64():
         d = d - d.mean()
         assert np.linalg.norm(d) < 5e-3 * np.linalg.norm(out["fp64"][1])
     assert _rel(out["tc"][0], out["simt"][0]) < 2e-5
+    assert _rel(out["tcpanel"][0], out["simt"][0]) < 2e-5
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
