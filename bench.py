@@ -391,7 +391,11 @@ def roofline(prof, regions, w, precision, tc_used, sub_nodes, sub_explicit=None)
         out["factorisation"] = {
             "bound": bound, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
             "traffic": traffic("k_rankk_tc") if tc_used else None,
-            "kernel": "k_rankk_tc + k_bigpanel + k_rankk128 (the factorisation launches of a Jacobian)",
+            "traffic_note": ("null: the factorisation is a class of launches of several kernels and shapes; "
+                             "no per-launch DRAM count stands for it (the tensor-core kernel's own capture "
+                             "is summarised in the profiles)"),
+            "kernel": ("k_rankk_tc (or k_rankk128 without tensor cores) + k_bigpanel (+ k_diag_inverse with the "
+                       "tensor-core panel solve): the factorisation launches of a Jacobian"),
             "peak_source": psrc, "launches": f_launch, "avg_launch_us": f_ms * 1e3 / f_launch,
             "ms_per_jacobian": f_ms / n_jac,
             "algorithmic_flops_per_jacobian": algo / n_jac, "library_flops_per_jacobian": lib / n_jac,
