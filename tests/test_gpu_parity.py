@@ -120,7 +120,7 @@ def test_jacobian_solve_fp64(name, method, krylov):
     s.linearize(ui, ue, wn)
     x, st = s.krylov_solve(f)
     assert st["reason"] == 0
-    # the spec bar for the FP64 Jacobian solve, on every workload (the ellipsoid's
+    # the accuracy bar for the FP64 Jacobian solve, on every workload (the ellipsoid's
     # Jacobian has kappa 2.4e6: the coarse solve must be backward stable there, Section 4.4)
     assert _rel(x, np.concatenate([si, se])) < 1e-10
 
