@@ -70,11 +70,11 @@ def _rank(rank, world, port, name, out):
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("name", ["cube8ve", "ragged"])
-def test_sharded_operator_matches_one_rank(name):
+@pytest.mark.parametrize("name,world", [("cube8ve", 2), ("ragged", 2), ("cube8ve", 3)])
+def test_sharded_operator_matches_one_rank(name, world):
     import sys
     sys.path.insert(0, os.path.dirname(__file__))
-    world, port = 2, _free_port()
+    port = _free_port()
     out = mp.get_context("spawn").Manager().dict()
     mp.spawn(_rank, args=(world, port, name, out), nprocs=world, join=True)
     prob, dd, sub_dofs = _setup(name)
@@ -89,18 +89,22 @@ def test_sharded_operator_matches_one_rank(name):
     g = dd.g_iface
     subs = np.concatenate([out[r]["subs"] for r in range(world)])
     assert sorted(subs.tolist()) == list(range(prob.part.n_sub))
-    assert len(out[0]["subs"]) > 0 and len(out[1]["subs"]) > 0 and out[0]["shared"]
+    assert all(len(out[r]["subs"]) > 0 for r in range(world)) and out[0]["shared"]
     for r in range(world):
         t, a = out[r]["touched"], out[r]["assembled"]
         keep = t != g
         np.testing.assert_allclose(a[keep], ref[t[keep]], rtol=0, atol=1e-13 * np.abs(ref).max())
         assert abs(out[r]["dot"] - x @ y) <= 1e-12 * np.abs(x) @ np.abs(y)
-    # a dof shared by both ranks has the same value, bit for bit, on both
-    t0, a0 = out[0]["touched"], out[0]["assembled"]
-    t1, a1 = out[1]["touched"], out[1]["assembled"]
-    common, i0, i1 = np.intersect1d(t0, t1, return_indices=True)
-    assert common.size > 0
-    np.testing.assert_array_equal(a0[i0], a1[i1])
+    # a dof shared by two ranks has the same value, bit for bit, on both
+    pairs = 0
+    for ra in range(world):
+        for rb in range(ra + 1, world):
+            ta, aa = out[ra]["touched"], out[ra]["assembled"]
+            tb, ab = out[rb]["touched"], out[rb]["assembled"]
+            common, ia, ib = np.intersect1d(ta, tb, return_indices=True)
+            pairs += common.size > 0
+            np.testing.assert_array_equal(aa[ia], ab[ib])
+    assert pairs > 0
     # coarse right-hand side: the sum over all subdomains, replicated
     full = np.zeros(prob.part.n_primal)
     for L in dd.loc:
